@@ -1,0 +1,233 @@
+"""ctypes wrapper of the plain FP64 CPU oracle (fargo_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the package smoke check
+and by the CPU-baseline leg of the benchmark.  The product path never imports
+it.  It shares no code with the CUDA library.
+
+The oracle takes a `workloads.Workload`-like object (mesh, switches, tables)
+and a dict of FP64 field arrays of shape (nz_t+1, ny_t+1, nx).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "fargo_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+P = C.POINTER(C.c_double)
+
+
+class OrParams(C.Structure):
+    _fields_ = [("geom", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("g", C.c_int),
+                ("xmin", C.c_double), ("xmax", C.c_double), ("yf", P), ("zf", P),
+                ("gamma", C.c_double), ("iso", C.c_int), ("cs", P), ("nu", P),
+                ("cfl", C.c_double), ("cq", C.c_double), ("av_dt_literal", C.c_int),
+                ("omega_f", C.c_double), ("fargo", C.c_int),
+                ("bc_ylo", C.c_int), ("bc_yhi", C.c_int), ("bc_zlo", C.c_int), ("bc_zhi", C.c_int),
+                ("star_mass", C.c_double), ("planet_q", C.c_double), ("planet_a", C.c_double),
+                ("planet_eps", C.c_double), ("indirect", C.c_int)]
+
+
+class OrState(C.Structure):
+    _fields_ = [("rho", P), ("e", P), ("vx", P), ("vy", P), ("vz", P)]
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (no FMA contraction, IEEE double)."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
+            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "fargo_oracle.h"))):
+        return LIB
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", LIB + ".tmp", SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB)
+        pp, ps = C.POINTER(OrParams), C.POINTER(OrState)
+        L.or_step.argtypes = [pp, ps, C.c_double, C.c_double, C.c_double, P]
+        L.or_step.restype = C.c_int
+        for name in ("or_bc_fill",):
+            getattr(L, name).argtypes = [pp, ps]
+        L.or_v0.argtypes = [pp, ps, P]
+        L.or_cfl.argtypes = [pp, ps, P, C.c_double, C.c_double, P]
+        L.or_cfl.restype = C.c_int
+        L.or_potential.argtypes = [pp, C.c_double, P]
+        L.or_substep1.argtypes = [pp, ps, P, C.c_double]
+        for name in ("or_artificial_viscosity", "or_compression_heating", "or_viscosity"):
+            getattr(L, name).argtypes = [pp, ps, C.c_double]
+        PP6 = P * 6
+        L.or_momenta.argtypes = [pp, ps, PP6]
+        L.or_transport_x.argtypes = [pp, ps, PP6, P, C.c_double]
+        L.or_transport_y.argtypes = [pp, ps, PP6, C.c_double]
+        L.or_transport_z.argtypes = [pp, ps, PP6, C.c_double]
+        L.or_new_velocities.argtypes = [pp, ps, PP6]
+        L.or_geometry.argtypes = [pp, P, P, P, P, P, P]
+        L.or_vanleer_slope.argtypes = [C.c_double] * 5
+        L.or_vanleer_slope.restype = C.c_double
+        L.or_ppa_faces.argtypes = [C.c_int, P, C.c_double, P]
+        L.or_shift_ring.argtypes = [C.c_int, P, C.c_longlong]
+        L.or_nearest_int.argtypes = [C.c_double]
+        L.or_nearest_int.restype = C.c_longlong
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(P) if a is not None else None
+
+
+class Oracle:
+    """Holds the parameter block of one workload (keeps arrays alive)."""
+
+    def __init__(self, w):
+        self.w = w
+        self._keep = []
+
+        def arr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a
+
+        yf, zf, cs, nu = arr(w.yf), arr(w.zf), arr(w.cs), arr(w.nu)
+        self.p = OrParams(w.geom, w.nx, w.ny, w.nz, w.g, w.xmin, w.xmax, _ptr(yf), _ptr(zf),
+                          w.gamma, int(w.iso), _ptr(cs), _ptr(nu), w.cfl, w.cq, int(w.av_dt_literal),
+                          w.omega_f, int(w.fargo), w.bc_y[0], w.bc_y[1], w.bc_z[0], w.bc_z[1],
+                          w.star_mass, w.planet_q, w.planet_a, w.planet_eps, int(w.indirect))
+        self.shape = w.shape
+        self.nrings = w.nz_t * w.ny_t
+
+    def _state(self, st):
+        for k in ("rho", "e", "vx", "vy", "vz"):
+            a = st[k]
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == self.shape, k
+        return OrState(_ptr(st["rho"]), _ptr(st["e"]), _ptr(st["vx"]), _ptr(st["vy"]), _ptr(st["vz"]))
+
+    def step(self, st, t, t_end=1e30, dt_fixed=0.0):
+        """One full update in place; returns dt.  Raises on a nonzero status."""
+        dt = C.c_double(0.0)
+        rc = lib().or_step(C.byref(self.p), C.byref(self._state(st)), t, t_end, dt_fixed, C.byref(dt))
+        if rc:
+            raise RuntimeError(f"oracle step failed with status {rc}")
+        return dt.value
+
+    def run(self, st, t, t_end, max_steps=10 ** 9):
+        n = 0
+        while t < t_end and n < max_steps:
+            dt = self.step(st, t, t_end)
+            t = t + dt
+            n += 1
+        return t, n
+
+    def bc_fill(self, st):
+        lib().or_bc_fill(C.byref(self.p), C.byref(self._state(st)))
+
+    def v0(self, st):
+        v0 = np.zeros(self.nrings)
+        lib().or_v0(C.byref(self.p), C.byref(self._state(st)), _ptr(v0))
+        return v0.reshape(self.w.nz_t, self.w.ny_t)
+
+    def cfl(self, st, v0, t=0.0, t_end=1e30):
+        dt = C.c_double(0.0)
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        rc = lib().or_cfl(C.byref(self.p), C.byref(self._state(st)), _ptr(v0), t, t_end, C.byref(dt))
+        return rc, dt.value
+
+    def potential(self, t):
+        phi = np.zeros(self.shape)
+        lib().or_potential(C.byref(self.p), t, _ptr(phi))
+        return phi
+
+    def substep1(self, st, phi, dt):
+        lib().or_substep1(C.byref(self.p), C.byref(self._state(st)), _ptr(phi), dt)
+
+    def artificial_viscosity(self, st, dt):
+        lib().or_artificial_viscosity(C.byref(self.p), C.byref(self._state(st)), dt)
+
+    def compression_heating(self, st, dt):
+        lib().or_compression_heating(C.byref(self.p), C.byref(self._state(st)), dt)
+
+    def viscosity(self, st, dt):
+        lib().or_viscosity(C.byref(self.p), C.byref(self._state(st)), dt)
+
+    def momenta(self, st):
+        pis = [np.zeros(self.shape) for _ in range(6)]
+        arr = (P * 6)(*[_ptr(a) for a in pis])
+        lib().or_momenta(C.byref(self.p), C.byref(self._state(st)), arr)
+        return pis
+
+    def _pis(self, pis):
+        return (P * 6)(*[_ptr(a) for a in pis])
+
+    def transport_x(self, st, pis, v0, dt):
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        lib().or_transport_x(C.byref(self.p), C.byref(self._state(st)), self._pis(pis), _ptr(v0), dt)
+
+    def transport_y(self, st, pis, dt):
+        lib().or_transport_y(C.byref(self.p), C.byref(self._state(st)), self._pis(pis), dt)
+
+    def transport_z(self, st, pis, dt):
+        lib().or_transport_z(C.byref(self.p), C.byref(self._state(st)), self._pis(pis), dt)
+
+    def new_velocities(self, st, pis):
+        lib().or_new_velocities(C.byref(self.p), C.byref(self._state(st)), self._pis(pis))
+
+    def geometry(self):
+        n = (self.w.nz_t + 1) * (self.w.ny_t + 1)
+        out = [np.zeros(n) for _ in range(6)]
+        lib().or_geometry(C.byref(self.p), *[_ptr(a) for a in out])
+        return [a.reshape(self.w.nz_t + 1, self.w.ny_t + 1) for a in out]
+
+    def sums(self, st):
+        """Conserved totals (mass, internal energy, X momentum), exactly rounded sums.
+
+        Mass = sum rho V, energy = sum e V, X momentum = sum (Pi-_x + Pi+_x)/2 V
+        over active cells (flow-chart diagnostics, Sec. 4.2).
+        """
+        w = self.w
+        _, _, _, _, vol, _ = self.geometry()
+        V = vol[:w.nz_t, :w.ny_t][w.gz:w.gz + w.nz, w.gy:w.gy + w.ny][:, :, None]
+        rho = w.active(st["rho"])
+        pis = self.momenta(st)
+        mom = 0.5 * (w.active(pis[0]) + w.active(pis[1]))
+        m = math.fsum((rho * V).ravel())
+        e = math.fsum((w.active(st["e"]) * V).ravel())
+        lx = math.fsum((mom * V).ravel())
+        return m, e, lx
+
+
+def vanleer_slope(qm, q0, qp, dxm, dxp):
+    return lib().or_vanleer_slope(qm, q0, qp, dxm, dxp)
+
+
+def ppa_faces(q, xi):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros_like(q)
+    lib().or_ppa_faces(len(q), _ptr(q), xi, _ptr(out))
+    return out
+
+
+def shift_ring(q, n):
+    q = np.ascontiguousarray(q, dtype=np.float64).copy()
+    lib().or_shift_ring(len(q), _ptr(q), n)
+    return q
+
+
+def nearest_int(x):
+    return lib().or_nearest_int(x)

@@ -1,0 +1,1205 @@
+/*
+ * Plain FP64 CPU oracle of one FARGO3D hydrodynamic time step.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path.  Written from the
+ * paper (Benitez-Llambay & Masset 2016): every loop is a plain triple loop
+ * over the mesh in the order of the flow chart (Fig. 2), with no blocking or
+ * fusion.  Where the paper is silent the reading taken is stated at the spot.
+ *
+ * Compile with -ffp-contract=off so that no multiply-add is fused: the
+ * Courant step, the mean azimuthal velocity and the integer shift must be
+ * reproducible bit for bit.
+ */
+#include "fargo_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Mesh bookkeeping                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const or_params *p;
+    int nx, nyt, nzt, gy, gz, j0, j1, k0, k1;
+    int hasX, hasY, hasZ;
+    size_t sj, sk, n;
+    double dx;
+    double *ym, *dy, *zm, *dz;
+} mesh;
+
+static void mesh_init(mesh *m, const or_params *p)
+{
+    m->p = p;
+    m->nx = p->nx;
+    m->nyt = p->ny > 1 ? p->ny + 2 * p->g : 1;
+    m->nzt = p->nz > 1 ? p->nz + 2 * p->g : 1;
+    m->gy = p->ny > 1 ? p->g : 0;
+    m->gz = p->nz > 1 ? p->g : 0;
+    m->j0 = m->gy; m->j1 = m->gy + p->ny;
+    m->k0 = m->gz; m->k1 = m->gz + p->nz;
+    m->hasX = p->nx > 1; m->hasY = p->ny > 1; m->hasZ = p->nz > 1;
+    m->sj = (size_t)p->nx;
+    m->sk = (size_t)(m->nyt + 1) * p->nx;
+    m->n = (size_t)(m->nzt + 1) * m->sk;
+    m->dx = (p->xmax - p->xmin) / p->nx;
+    m->ym = malloc(sizeof(double) * m->nyt);
+    m->dy = malloc(sizeof(double) * m->nyt);
+    m->zm = malloc(sizeof(double) * m->nzt);
+    m->dz = malloc(sizeof(double) * m->nzt);
+    for (int j = 0; j < m->nyt; j++) {
+        m->ym[j] = 0.5 * (p->yf[j] + p->yf[j + 1]);
+        m->dy[j] = p->yf[j + 1] - p->yf[j];
+    }
+    for (int k = 0; k < m->nzt; k++) {
+        m->zm[k] = 0.5 * (p->zf[k] + p->zf[k + 1]);
+        m->dz[k] = p->zf[k + 1] - p->zf[k];
+    }
+}
+
+static void mesh_free(mesh *m)
+{
+    free(m->ym); free(m->dy); free(m->zm); free(m->dz);
+}
+
+#define IDX(m, i, j, k) ((size_t)(k) * (m)->sk + (size_t)(j) * (m)->sj + (size_t)(i))
+#define IP(m, i) (((i) + 1) % (m)->nx)
+#define IM(m, i) (((i) - 1 + (m)->nx) % (m)->nx)
+
+static double *zalloc(size_t n) { return calloc(n, sizeof(double)); }
+static double *dup(const double *a, size_t n)
+{
+    double *b = malloc(sizeof(double) * n);
+    memcpy(b, a, sizeof(double) * n);
+    return b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry (Appendix A, Tab. "geom", Eqs. 70-71)                            */
+/* ------------------------------------------------------------------------ */
+/* Cylindrical radius of ring (j,k): the lever arm of the azimuthal motion. */
+static double ring_R(const mesh *m, int j, int k)
+{
+    switch (m->p->geom) {
+    case OR_CYL: return m->ym[j];
+    case OR_SPH: return m->ym[j] * sin(m->zm[k]);
+    default: return 1.0;
+    }
+}
+/* Azimuthal (X) cell length of ring (j,k). */
+static double len_x(const mesh *m, int j, int k) { return ring_R(m, j, k) * m->dx; }
+/* Z cell length and centre-to-centre distance across Z face k. */
+static double len_z(const mesh *m, int j, int k)
+{
+    return m->p->geom == OR_SPH ? m->ym[j] * m->dz[k] : m->dz[k];
+}
+static double dist_z(const mesh *m, int j, int k)
+{
+    return m->p->geom == OR_SPH ? m->ym[j] * (m->zm[k] - m->zm[k - 1]) : m->zm[k] - m->zm[k - 1];
+}
+static double dist_y(const mesh *m, int j) { return m->ym[j] - m->ym[j - 1]; }
+
+static double sxj(const mesh *m, int j)
+{
+    const double *yf = m->p->yf;
+    if (m->p->geom == OR_SPH) return 0.5 * (yf[j + 1] * yf[j + 1] - yf[j] * yf[j]);
+    return yf[j + 1] - yf[j];
+}
+static double sxk(const mesh *m, int k) { return m->p->zf[k + 1] - m->p->zf[k]; }
+static double syj(const mesh *m, int j)
+{
+    const double *yf = m->p->yf;
+    switch (m->p->geom) {
+    case OR_CYL: return yf[j] * m->dx;
+    case OR_SPH: return yf[j] * yf[j] * m->dx;
+    default: return 1.0;
+    }
+}
+static double syk(const mesh *m, int k)
+{
+    const double *zf = m->p->zf;
+    switch (m->p->geom) {
+    case OR_CYL: return zf[k + 1] - zf[k];
+    case OR_SPH: return cos(zf[k]) - cos(zf[k + 1]);
+    default: return m->dx * (zf[k + 1] - zf[k]);
+    }
+}
+static double szj(const mesh *m, int j)
+{
+    const double *yf = m->p->yf;
+    if (m->p->geom == OR_CART) return m->dx * (yf[j + 1] - yf[j]);
+    return 0.5 * m->dx * (yf[j + 1] * yf[j + 1] - yf[j] * yf[j]);
+}
+static double szk(const mesh *m, int k)
+{
+    return m->p->geom == OR_SPH ? sin(m->p->zf[k]) : 1.0;
+}
+static double vjinv(const mesh *m, int j)
+{
+    const double *yf = m->p->yf;
+    switch (m->p->geom) {
+    case OR_CYL: return 2.0 / ((yf[j + 1] * yf[j + 1] - yf[j] * yf[j]) * m->dx);
+    case OR_SPH: return 3.0 / ((yf[j + 1] * yf[j + 1] * yf[j + 1] - yf[j] * yf[j] * yf[j]) * m->dx);
+    default: return 1.0 / (yf[j + 1] - yf[j]);
+    }
+}
+static double area_x(const mesh *m, int j, int k) { return sxj(m, j) * sxk(m, k); }
+static double area_y(const mesh *m, int j, int k) { return syj(m, j) * syk(m, k); }
+static double area_z(const mesh *m, int j, int k) { return szj(m, j) * szk(m, k); }
+static double inv_vol(const mesh *m, int j, int k) { return vjinv(m, j) / syk(m, k); }
+
+void or_geometry(const or_params *p, double *sx, double *sy, double *sz, double *vinv, double *vol, double *dxr)
+{
+    mesh m;
+    mesh_init(&m, p);
+    for (int k = 0; k <= m.nzt; k++)
+        for (int j = 0; j <= m.nyt; j++) {
+            size_t o = (size_t)k * (m.nyt + 1) + j;
+            if (j < m.nyt) sz[o] = area_z(&m, j, k);
+            if (k < m.nzt) sy[o] = area_y(&m, j, k);
+            if (j < m.nyt && k < m.nzt) {
+                sx[o] = area_x(&m, j, k);
+                vinv[o] = inv_vol(&m, j, k);
+                vol[o] = 1.0 / vinv[o];
+                dxr[o] = len_x(&m, j, k);
+            }
+        }
+    mesh_free(&m);
+}
+
+/* Pressure from the equation of state (Eqs. eos1, eos2; flow-chart cell 4). */
+static double pressure(const mesh *m, const or_state *s, size_t c, int j, int k)
+{
+    if (m->p->iso) {
+        double cs = m->p->cs[(size_t)k * m->nyt + j];
+        return cs * cs * s->rho[c];
+    }
+    return (m->p->gamma - 1.0) * s->e[c];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 2 / 9: ghost fill.  Reading: reflecting walls mirror scalars and     */
+/* tangential velocities about the wall and set the wall-normal velocity to  */
+/* zero on the wall face with odd mirroring beyond; frozen boundaries keep   */
+/* the values the ghosts were given; zero-gradient copies the last active    */
+/* cell (and the first interior normal face).                                */
+/* ------------------------------------------------------------------------ */
+static void fill_y(const mesh *m, double *a, int normal, int side, int bc, int k, int i)
+{
+    int g = m->p->g, j0 = m->j0, j1 = m->j1;
+    if (bc == OR_BC_FROZEN) return;
+    for (int mm = 0; mm < g; mm++) {
+        if (!normal) {
+            int dst = side == 0 ? j0 - 1 - mm : j1 + mm;
+            int src;
+            if (bc == OR_BC_REFLECT) src = side == 0 ? j0 + mm : j1 - 1 - mm;
+            else src = side == 0 ? j0 : j1 - 1;
+            a[IDX(m, i, dst, k)] = a[IDX(m, i, src, k)];
+        }
+    }
+    if (normal) {
+        if (bc == OR_BC_REFLECT) {
+            int w = side == 0 ? j0 : j1;
+            a[IDX(m, i, w, k)] = 0.0;
+            for (int mm = 1; mm <= g; mm++) {
+                if (side == 0) a[IDX(m, i, w - mm, k)] = -a[IDX(m, i, w + mm, k)];
+                else a[IDX(m, i, w + mm, k)] = -a[IDX(m, i, w - mm, k)];
+            }
+        } else { /* zero gradient */
+            if (side == 0)
+                for (int mm = 0; mm <= g; mm++) a[IDX(m, i, j0 - mm, k)] = a[IDX(m, i, j0 + 1, k)];
+            else
+                for (int mm = 0; mm <= g; mm++) a[IDX(m, i, j1 + mm, k)] = a[IDX(m, i, j1 - 1, k)];
+        }
+    }
+}
+
+static void fill_z(const mesh *m, double *a, int normal, int side, int bc, int j, int i)
+{
+    int g = m->p->g, k0 = m->k0, k1 = m->k1;
+    if (bc == OR_BC_FROZEN) return;
+    if (!normal) {
+        for (int mm = 0; mm < g; mm++) {
+            int dst = side == 0 ? k0 - 1 - mm : k1 + mm;
+            int src;
+            if (bc == OR_BC_REFLECT) src = side == 0 ? k0 + mm : k1 - 1 - mm;
+            else src = side == 0 ? k0 : k1 - 1;
+            a[IDX(m, i, j, dst)] = a[IDX(m, i, j, src)];
+        }
+    } else {
+        if (bc == OR_BC_REFLECT) {
+            int w = side == 0 ? k0 : k1;
+            a[IDX(m, i, j, w)] = 0.0;
+            for (int mm = 1; mm <= g; mm++) {
+                if (side == 0) a[IDX(m, i, j, w - mm)] = -a[IDX(m, i, j, w + mm)];
+                else a[IDX(m, i, j, w + mm)] = -a[IDX(m, i, j, w - mm)];
+            }
+        } else {
+            if (side == 0)
+                for (int mm = 0; mm <= g; mm++) a[IDX(m, i, j, k0 - mm)] = a[IDX(m, i, j, k0 + 1)];
+            else
+                for (int mm = 0; mm <= g; mm++) a[IDX(m, i, j, k1 + mm)] = a[IDX(m, i, j, k1 - 1)];
+        }
+    }
+}
+
+void or_bc_fill(const or_params *p, or_state *s)
+{
+    mesh m;
+    mesh_init(&m, p);
+    double *f[5] = { s->rho, p->iso ? NULL : s->e, s->vx, s->vy, s->vz };
+    if (m.hasY) {
+        int bcs[2] = { p->bc_ylo, p->bc_yhi };
+        for (int side = 0; side < 2; side++)
+            for (int q = 0; q < 5; q++) {
+                if (!f[q]) continue;
+                if (q == 4 && !m.hasZ) continue;
+                int kmax = (q == 4) ? m.nzt + 1 : m.nzt;
+                for (int k = 0; k < kmax; k++)
+                    for (int i = 0; i < m.nx; i++)
+                        fill_y(&m, f[q], q == 3, side, bcs[side], k, i);
+            }
+    }
+    if (m.hasZ) {
+        int bcs[2] = { p->bc_zlo, p->bc_zhi };
+        for (int side = 0; side < 2; side++)
+            for (int q = 0; q < 5; q++) {
+                if (!f[q]) continue;
+                if (q == 3 && !m.hasY) continue;
+                int jmax = (q == 3) ? m.nyt + 1 : m.nyt;
+                for (int j = 0; j < jmax; j++)
+                    for (int i = 0; i < m.nx; i++)
+                        fill_z(&m, f[q], q == 4, side, bcs[side], j, i);
+            }
+    }
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 3: bulk azimuthal velocity of each ring, Eq. 37 (minimises the L_inf */
+/* norm of the residual).  Zero for every ring when FARGO is off.            */
+/* ------------------------------------------------------------------------ */
+void or_v0(const or_params *p, const or_state *s, double *v0)
+{
+    mesh m;
+    mesh_init(&m, p);
+    for (size_t o = 0; o < (size_t)m.nzt * m.nyt; o++) v0[o] = 0.0;
+    if (p->fargo)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++) {
+                double mx = s->vx[IDX(&m, 0, j, k)], mn = mx;
+                for (int i = 1; i < m.nx; i++) {
+                    double v = s->vx[IDX(&m, i, j, k)];
+                    if (v > mx) mx = v;
+                    if (v < mn) mn = v;
+                }
+                v0[(size_t)k * m.nyt + j] = 0.5 * (mx + mn);
+            }
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 6: Courant time step, Eq. cfl2, with the items of Sec. 3.4 and the   */
+/* FARGO amendments of Sec. 3.4.2 (residual velocity, shear limit Eq. 38).   */
+/* Readings: each Delta t_i is the minimum over the active directions; the   */
+/* fluid-motion term uses the larger |v| of the two faces of the cell; the   */
+/* artificial-viscosity term is the ZEUS limit Delta/(4 C_q^2 |Delta v|) for  */
+/* compressions (printed form 4 sqrt2 |Delta/Delta v| under av_dt_literal);  */
+/* C_0 of Eq. 38 is the Courant number.  Terms are summed as inverse squares */
+/* in the order 1..4, and the last step is clipped to land on t_end.         */
+/* ------------------------------------------------------------------------ */
+int or_cfl(const or_params *p, const or_state *s, const double *v0, double t, double t_end, double *dt_out)
+{
+    mesh m;
+    mesh_init(&m, p);
+    double best = INFINITY;
+    int bad = 0;
+    const double g1 = p->gamma * (p->gamma - 1.0);
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++) {
+            double v0r = p->fargo ? v0[(size_t)k * m.nyt + j] : 0.0;
+            double lx = len_x(&m, j, k), ly = m.dy[j], lz = len_z(&m, j, k);
+            double dmin = INFINITY;
+            if (m.hasX && lx < dmin) dmin = lx;
+            if (m.hasY && ly < dmin) dmin = ly;
+            if (m.hasZ && lz < dmin) dmin = lz;
+            double nu = p->nu ? p->nu[(size_t)k * m.nyt + j] : 0.0;
+            for (int i = 0; i < m.nx; i++) {
+                size_t c = IDX(&m, i, j, k);
+                double rho = s->rho[c];
+                double cs;
+                if (p->iso) cs = p->cs[(size_t)k * m.nyt + j];
+                else {
+                    double e = s->e[c];
+                    if (!isfinite(e) || e < 0.0) bad = 1;
+                    cs = sqrt(g1 * e / rho);
+                }
+                if (!isfinite(rho) || rho <= 0.0) bad = 1;
+                double r1 = cs / dmin;
+                double r2 = 0.0, r3 = 0.0;
+                if (m.hasX) {
+                    double a = fabs(s->vx[c] - v0r), b = fabs(s->vx[IDX(&m, IP(&m, i), j, k)] - v0r);
+                    double v = a > b ? a : b;
+                    double r = v / lx;
+                    if (r > r2) r2 = r;
+                    double dv = s->vx[IDX(&m, IP(&m, i), j, k)] - s->vx[c];
+                    double ra = p->av_dt_literal ? fabs(dv) / (4.0 * sqrt(2.0) * lx)
+                                                  : (dv < 0.0 ? 4.0 * p->cq * p->cq * (-dv) / lx : 0.0);
+                    if (ra > r3) r3 = ra;
+                    if (!isfinite(s->vx[c])) bad = 1;
+                }
+                if (m.hasY) {
+                    double a = fabs(s->vy[c]), b = fabs(s->vy[c + m.sj]);
+                    double v = a > b ? a : b;
+                    double r = v / ly;
+                    if (r > r2) r2 = r;
+                    double dv = s->vy[c + m.sj] - s->vy[c];
+                    double ra = p->av_dt_literal ? fabs(dv) / (4.0 * sqrt(2.0) * ly)
+                                                  : (dv < 0.0 ? 4.0 * p->cq * p->cq * (-dv) / ly : 0.0);
+                    if (ra > r3) r3 = ra;
+                    if (!isfinite(s->vy[c])) bad = 1;
+                }
+                if (m.hasZ) {
+                    double a = fabs(s->vz[c]), b = fabs(s->vz[c + m.sk]);
+                    double v = a > b ? a : b;
+                    double r = v / lz;
+                    if (r > r2) r2 = r;
+                    double dv = s->vz[c + m.sk] - s->vz[c];
+                    double ra = p->av_dt_literal ? fabs(dv) / (4.0 * sqrt(2.0) * lz)
+                                                  : (dv < 0.0 ? 4.0 * p->cq * p->cq * (-dv) / lz : 0.0);
+                    if (ra > r3) r3 = ra;
+                    if (!isfinite(s->vz[c])) bad = 1;
+                }
+                if (p->cq <= 0.0) r3 = 0.0;
+                double r4 = nu > 0.0 ? 4.0 * nu / (dmin * dmin) : 0.0;
+                double sum = r1 * r1 + r2 * r2 + r3 * r3 + r4 * r4;
+                double local = 1.0 / sqrt(sum);
+                if (local < best) best = local;
+            }
+        }
+    double dt = p->cfl * best;
+    /* Shear limit, Eq. 38, between radially adjacent rings. */
+    if (p->fargo && m.hasY)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1 - 1; j++) {
+                double a = v0[(size_t)k * m.nyt + j] / len_x(&m, j, k);
+                double b = v0[(size_t)k * m.nyt + j + 1] / len_x(&m, j + 1, k);
+                double w = fabs(a - b);
+                if (w > 0.0) {
+                    double ds = p->cfl / w;
+                    if (ds < dt) dt = ds;
+                }
+            }
+    if (t + dt > t_end) dt = t_end - t;
+    mesh_free(&m);
+    *dt_out = dt;
+    if (bad) return -4;
+    if (!(dt > 0.0) || !isfinite(dt)) return -5;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 5: gravitational potential at cell centres at time t.  Reading: a    */
+/* central mass (Phi = -M/r with r the spherical radius), a planet of mass q */
+/* on a fixed circular orbit of radius a in the midplane at phase            */
+/* (Omega_p - Omega_f) t, Omega_p = sqrt((M+q)/a^3), Plummer smoothing eps,   */
+/* and the indirect term q (r . r_p)/a^3.                                     */
+/* ------------------------------------------------------------------------ */
+void or_potential(const or_params *p, double t, double *phi)
+{
+    mesh m;
+    mesh_init(&m, p);
+    double M = p->star_mass, q = p->planet_q, a = p->planet_a;
+    double om = q > 0.0 ? sqrt((M + q) / (a * a * a)) : 0.0;
+    double ph = (om - p->omega_f) * t;
+    double xp = a * cos(ph), yp = a * sin(ph);
+    for (int k = 0; k < m.nzt; k++)
+        for (int j = 0; j < m.nyt; j++)
+            for (int i = 0; i < m.nx; i++) {
+                double x = p->xmin + (i + 0.5) * m.dx;
+                double X, Y, Z, rs;
+                if (p->geom == OR_CYL) {
+                    double r = m.ym[j];
+                    X = r * cos(x); Y = r * sin(x); Z = m.zm[k];
+                    rs = sqrt(r * r + Z * Z);
+                } else if (p->geom == OR_SPH) {
+                    double r = m.ym[j], st = sin(m.zm[k]);
+                    X = r * st * cos(x); Y = r * st * sin(x); Z = r * cos(m.zm[k]);
+                    rs = r;
+                } else {
+                    X = x; Y = m.ym[j]; Z = m.zm[k];
+                    rs = 0.0;
+                }
+                double v = 0.0;
+                if (M > 0.0 && p->geom != OR_CART) v -= M / rs;
+                if (q > 0.0) {
+                    double d2 = (X - xp) * (X - xp) + (Y - yp) * (Y - yp) + Z * Z;
+                    v -= q / sqrt(d2 + p->planet_eps * p->planet_eps);
+                    if (p->indirect) v += q * (X * xp + Y * yp) / (a * a * a);
+                }
+                phi[IDX(&m, i, j, k)] = v;
+            }
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 7a, sub-step 1 (Sec. 3.3): pressure gradient with the two-point face */
+/* density of Eq. 20, potential gradient and the centrifugal / geometric     */
+/* terms, the inertial-frame velocity averaged over four faces before        */
+/* squaring (Eq. 12).  All components read the state at sub-step entry.     */
+/* Interior faces only: boundary faces belong to the boundary condition.     */
+/* ------------------------------------------------------------------------ */
+void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
+{
+    mesh m;
+    mesh_init(&m, p);
+    double *P = zalloc(m.n);
+    for (int k = 0; k < m.nzt; k++)
+        for (int j = 0; j < m.nyt; j++)
+            for (int i = 0; i < m.nx; i++) {
+                size_t c = IDX(&m, i, j, k);
+                P[c] = pressure(&m, s, c, j, k);
+            }
+    double *vx = dup(s->vx, m.n), *vy = dup(s->vy, m.n), *vz = dup(s->vz, m.n);
+    const double *rho = s->rho;
+    double om = p->omega_f;
+    if (m.hasX)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = IDX(&m, IM(&m, i), j, k);
+                    double d = len_x(&m, j, k);
+                    double acc = -2.0 * (P[c] - P[cm]) / (d * (rho[c] + rho[cm]));
+                    if (phi) acc -= (phi[c] - phi[cm]) / d;
+                    s->vx[c] = vx[c] + dt * acc;
+                }
+    if (m.hasY)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0 + 1; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = c - m.sj;
+                    double d = dist_y(&m, j);
+                    double acc = -2.0 * (P[c] - P[cm]) / (d * (rho[c] + rho[cm]));
+                    if (phi) acc -= (phi[c] - phi[cm]) / d;
+                    if (p->geom != OR_CART) {
+                        int ip = IP(&m, i);
+                        double Rj = ring_R(&m, j, k), Rm = ring_R(&m, j - 1, k);
+                        double vt = 0.25 * ((vx[c] + Rj * om) + (vx[IDX(&m, ip, j, k)] + Rj * om)
+                                            + (vx[cm] + Rm * om) + (vx[IDX(&m, ip, j - 1, k)] + Rm * om));
+                        double cen = vt * vt;
+                        if (p->geom == OR_SPH && m.hasZ) {
+                            double vth = 0.25 * (vz[c] + vz[c + m.sk] + vz[cm] + vz[cm + m.sk]);
+                            cen += vth * vth;
+                        }
+                        acc += cen / p->yf[j];
+                    }
+                    s->vy[c] = vy[c] + dt * acc;
+                }
+    if (m.hasZ)
+        for (int k = m.k0 + 1; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = c - m.sk;
+                    double d = dist_z(&m, j, k);
+                    double acc = -2.0 * (P[c] - P[cm]) / (d * (rho[c] + rho[cm]));
+                    if (phi) acc -= (phi[c] - phi[cm]) / d;
+                    if (p->geom == OR_SPH) {
+                        int ip = IP(&m, i);
+                        double Rk = ring_R(&m, j, k), Rm = ring_R(&m, j, k - 1);
+                        double vt = 0.25 * ((vx[c] + Rk * om) + (vx[IDX(&m, ip, j, k)] + Rk * om)
+                                            + (vx[cm] + Rm * om) + (vx[IDX(&m, ip, j, k - 1)] + Rm * om));
+                        acc += vt * vt * (cos(p->zf[k]) / sin(p->zf[k])) / m.ym[j];
+                    }
+                    s->vz[c] = vz[c] + dt * acc;
+                }
+    free(P); free(vx); free(vy); free(vz);
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 7b, sub-step 2: von Neumann-Richtmyer artificial viscosity, applied  */
+/* component-wise (Sec. 3.3).  The paper defers the formula to ZEUS-2D;      */
+/* reading: q_d = C_q^2 rho (Delta v_d)^2 for a compression Delta v_d < 0    */
+/* (else 0), its gradient accelerates the faces with the two-point density   */
+/* of Eq. 20, and it heats the gas by -q_d Delta v_d / Delta_d.  q is first  */
+/* computed everywhere (first pass), then applied (second pass).             */
+/* ------------------------------------------------------------------------ */
+void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
+{
+    if (p->cq <= 0.0) return;
+    mesh m;
+    mesh_init(&m, p);
+    double c2 = p->cq * p->cq;
+    double *qx = zalloc(m.n), *qy = zalloc(m.n), *qz = zalloc(m.n);
+    double *dvx = zalloc(m.n), *dvy = zalloc(m.n), *dvz = zalloc(m.n);
+    const double *rho = s->rho;
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++)
+            for (int i = 0; i < m.nx; i++) {
+                size_t c = IDX(&m, i, j, k);
+                if (m.hasX) {
+                    double dv = s->vx[IDX(&m, IP(&m, i), j, k)] - s->vx[c];
+                    dvx[c] = dv;
+                    qx[c] = dv < 0.0 ? c2 * rho[c] * dv * dv : 0.0;
+                }
+                if (m.hasY) {
+                    double dv = s->vy[c + m.sj] - s->vy[c];
+                    dvy[c] = dv;
+                    qy[c] = dv < 0.0 ? c2 * rho[c] * dv * dv : 0.0;
+                }
+                if (m.hasZ) {
+                    double dv = s->vz[c + m.sk] - s->vz[c];
+                    dvz[c] = dv;
+                    qz[c] = dv < 0.0 ? c2 * rho[c] * dv * dv : 0.0;
+                }
+            }
+    if (!p->iso)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k);
+                    double h = 0.0;
+                    if (m.hasX) h += qx[c] * dvx[c] / len_x(&m, j, k);
+                    if (m.hasY) h += qy[c] * dvy[c] / m.dy[j];
+                    if (m.hasZ) h += qz[c] * dvz[c] / len_z(&m, j, k);
+                    s->e[c] -= dt * h;
+                }
+    if (m.hasX)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = IDX(&m, IM(&m, i), j, k);
+                    s->vx[c] -= dt * 2.0 * (qx[c] - qx[cm]) / (len_x(&m, j, k) * (rho[c] + rho[cm]));
+                }
+    if (m.hasY)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0 + 1; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = c - m.sj;
+                    s->vy[c] -= dt * 2.0 * (qy[c] - qy[cm]) / (dist_y(&m, j) * (rho[c] + rho[cm]));
+                }
+    if (m.hasZ)
+        for (int k = m.k0 + 1; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = c - m.sk;
+                    s->vz[c] -= dt * 2.0 * (qz[c] - qz[cm]) / (dist_z(&m, j, k) * (rho[c] + rho[cm]));
+                }
+    free(qx); free(qy); free(qz); free(dvx); free(dvy); free(dvz);
+    mesh_free(&m);
+}
+
+/* Geometry-exact velocity divergence of cell (i,j,k): V^-1 sum of S v over */
+/* the six faces (Gauss theorem with the areas of Appendix A).               */
+static double divergence(const mesh *m, const or_state *s, int i, int j, int k)
+{
+    size_t c = IDX(m, i, j, k);
+    double f = 0.0;
+    if (m->hasX) f += area_x(m, j, k) * (s->vx[IDX(m, IP(m, i), j, k)] - s->vx[c]);
+    if (m->hasY) f += area_y(m, j + 1, k) * s->vy[c + m->sj] - area_y(m, j, k) * s->vy[c];
+    if (m->hasZ) f += area_z(m, j, k + 1) * s->vz[c + m->sk] - area_z(m, j, k) * s->vz[c];
+    return f * inv_vol(m, j, k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 7c, sub-step 3: compression heating -P div v for a gamma-law gas.    */
+/* Reading of "Eq. (40) of Stone & Norman": the time-centred implicit form   */
+/* e' = e (1 - theta)/(1 + theta), theta = dt (gamma - 1) div v / 2.         */
+/* ------------------------------------------------------------------------ */
+void or_compression_heating(const or_params *p, or_state *s, double dt)
+{
+    if (p->iso) return;
+    mesh m;
+    mesh_init(&m, p);
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++)
+            for (int i = 0; i < m.nx; i++) {
+                double th = 0.5 * dt * (p->gamma - 1.0) * divergence(&m, s, i, j, k);
+                size_t c = IDX(&m, i, j, k);
+                s->e[c] = s->e[c] * (1.0 - th) / (1.0 + th);
+            }
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 7d: viscous stress tensor and velocity update (Appendix B, Eqs.      */
+/* 72-77).  Diagonal components at cell centres, off-diagonal ones on the    */
+/* edges with the lowest coordinates (Fig. "stress"); derivatives are plain  */
+/* centred differences on the staggered mesh.  Readings: the density (and   */
+/* viscosity) of an edge is the mean over the cells sharing it; Eq. 75 is   */
+/* divided by the face density like Eqs. 76-77.  Every stress is computed    */
+/* from the velocities at sub-step entry, then all faces are updated.        */
+/* ------------------------------------------------------------------------ */
+void or_viscosity(const or_params *p, or_state *s, double dt)
+{
+    if (!p->nu) return;
+    mesh m;
+    mesh_init(&m, p);
+    const double *rho = s->rho;
+    const double *yf = p->yf, *zf = p->zf;
+    const double *ym = m.ym, *zm = m.zm, *dy = m.dy, *dz = m.dz;
+    double dx = m.dx;
+    int geom = p->geom;
+    or_state v0s = { s->rho, s->e, dup(s->vx, m.n), dup(s->vy, m.n), dup(s->vz, m.n) };
+    const double *vx = v0s.vx, *vy = v0s.vy, *vz = v0s.vz;
+    double *txx = zalloc(m.n), *tyy = zalloc(m.n), *tzz = zalloc(m.n);
+    double *txy = zalloc(m.n), *txz = zalloc(m.n), *tyz = zalloc(m.n);
+#define NU(j, k) (p->nu[(size_t)(k) * m.nyt + (j)])
+    /* diagonal components at active cell centres */
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++)
+            for (int i = 0; i < m.nx; i++) {
+                size_t c = IDX(&m, i, j, k), cxp = IDX(&m, IP(&m, i), j, k);
+                double dv = divergence(&m, &v0s, i, j, k);
+                double rn = rho[c] * NU(j, k);
+                double dxx = (vx[cxp] - vx[c]) / len_x(&m, j, k);
+                double dyy = m.hasY ? (vy[c + m.sj] - vy[c]) / dy[j] : 0.0;
+                double dzz = m.hasZ ? (vz[c + m.sk] - vz[c]) / len_z(&m, j, k) : 0.0;
+                if (geom == OR_CART) {
+                    txx[c] = -rn * (2.0 * dxx - 2.0 / 3.0 * dv);
+                    tyy[c] = -rn * (2.0 * dyy - 2.0 / 3.0 * dv);
+                    tzz[c] = -rn * (2.0 * dzz - 2.0 / 3.0 * dv);
+                } else if (geom == OR_CYL) {
+                    double r = ym[j];
+                    double vr = 0.5 * (vy[c] + vy[c + m.sj]);
+                    txx[c] = -rn * (2.0 * (dxx + vr / r) - 2.0 / 3.0 * dv);
+                    tyy[c] = -rn * (2.0 * dyy - 2.0 / 3.0 * dv);
+                    tzz[c] = -rn * (2.0 * dzz - 2.0 / 3.0 * dv);
+                } else {
+                    double r = ym[j], ct = cos(zm[k]) / sin(zm[k]);
+                    double vr = 0.5 * (vy[c] + vy[c + m.sj]);
+                    double vt = 0.5 * (vz[c] + vz[c + m.sk]);
+                    txx[c] = -rn * (2.0 * (dxx + vr / r + vt * ct / r) - 2.0 / 3.0 * dv);
+                    tyy[c] = -rn * (2.0 * dyy - 2.0 / 3.0 * dv);
+                    tzz[c] = -rn * (2.0 * (dzz + vr / r) - 2.0 / 3.0 * dv);
+                }
+            }
+    /* tau_xy on the z-directed edge (i-1/2, j-1/2, k) */
+    if (m.hasY)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0; j <= m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    int im = IM(&m, i);
+                    size_t c = IDX(&m, i, j, k), cm = IDX(&m, im, j, k);
+                    double rb = 0.25 * (rho[c] + rho[cm] + rho[c - m.sj] + rho[cm - m.sj]);
+                    double nb = 0.5 * (NU(j, k) + NU(j - 1, k));
+                    double dvx_dy = (vx[c] - vx[c - m.sj]) / (ym[j] - ym[j - 1]);
+                    double t;
+                    if (geom == OR_CART) {
+                        t = (vy[c] - vy[cm]) / dx + dvx_dy;
+                    } else if (geom == OR_CYL) {
+                        double rf = yf[j];
+                        t = dvx_dy - 0.5 * (vx[c] + vx[c - m.sj]) / rf + (vy[c] - vy[cm]) / (rf * dx);
+                    } else {
+                        double rf = yf[j], sn = sin(zm[k]);
+                        t = (vy[c] - vy[cm]) / (rf * sn * dx) + dvx_dy - 0.5 * (vx[c] + vx[c - m.sj]) / rf;
+                    }
+                    txy[c] = -rb * nb * t;
+                }
+    /* tau_xz on the y-directed edge (i-1/2, j, k-1/2) */
+    if (m.hasZ)
+        for (int k = m.k0; k <= m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    int im = IM(&m, i);
+                    size_t c = IDX(&m, i, j, k), cm = IDX(&m, im, j, k);
+                    double rb = 0.25 * (rho[c] + rho[cm] + rho[c - m.sk] + rho[cm - m.sk]);
+                    double nb = 0.5 * (NU(j, k) + NU(j, k - 1));
+                    double t;
+                    if (geom == OR_CART) {
+                        t = (vz[c] - vz[cm]) / dx + (vx[c] - vx[c - m.sk]) / (zm[k] - zm[k - 1]);
+                    } else if (geom == OR_CYL) {
+                        t = (vx[c] - vx[c - m.sk]) / (zm[k] - zm[k - 1]) + (vz[c] - vz[cm]) / (ym[j] * dx);
+                    } else {
+                        double r = ym[j], sf = sin(zf[k]);
+                        t = sf / r * (vx[c] / sin(zm[k]) - vx[c - m.sk] / sin(zm[k - 1])) / (zm[k] - zm[k - 1])
+                            + (vz[c] - vz[cm]) / (r * sf * dx);
+                    }
+                    txz[c] = -rb * nb * t;
+                }
+    /* tau_yz on the x-directed edge (i, j-1/2, k-1/2) */
+    if (m.hasY && m.hasZ)
+        for (int k = m.k0; k <= m.k1; k++)
+            for (int j = m.j0; j <= m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k);
+                    double rb = 0.25 * (rho[c] + rho[c - m.sj] + rho[c - m.sk] + rho[c - m.sj - m.sk]);
+                    double nb = 0.25 * (NU(j, k) + NU(j - 1, k) + NU(j, k - 1) + NU(j - 1, k - 1));
+                    double t;
+                    if (geom == OR_SPH) {
+                        double rf = yf[j];
+                        t = (vz[c] - vz[c - m.sj]) / (ym[j] - ym[j - 1]) - 0.5 * (vz[c] + vz[c - m.sj]) / rf
+                            + (vy[c] - vy[c - m.sk]) / (rf * (zm[k] - zm[k - 1]));
+                    } else {
+                        t = (vz[c] - vz[c - m.sj]) / (ym[j] - ym[j - 1]) + (vy[c] - vy[c - m.sk]) / (zm[k] - zm[k - 1]);
+                    }
+                    tyz[c] = -rb * nb * t;
+                }
+    /* v_x update on faces (i-1/2, j, k) */
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++)
+            for (int i = 0; i < m.nx; i++) {
+                int im = IM(&m, i), ip = IP(&m, i);
+                size_t c = IDX(&m, i, j, k), cm = IDX(&m, im, j, k);
+                (void)ip;
+                double rf = 0.5 * (rho[c] + rho[cm]);
+                double f = 0.0;
+                if (geom == OR_CART) {
+                    f += (txx[c] - txx[cm]) / dx;
+                    if (m.hasY) f += (txy[c + m.sj] - txy[c]) / dy[j];
+                    if (m.hasZ) f += (txz[c + m.sk] - txz[c]) / dz[k];
+                } else if (geom == OR_CYL) {
+                    double r = ym[j];
+                    if (m.hasY) f += (yf[j + 1] * yf[j + 1] * txy[c + m.sj] - yf[j] * yf[j] * txy[c]) / (r * r * dy[j]);
+                    f += (txx[c] - txx[cm]) / (r * dx);
+                    if (m.hasZ) f += (txz[c + m.sk] - txz[c]) / dz[k];
+                } else {
+                    double r = ym[j], sn = sin(zm[k]), ct = cos(zm[k]) / sin(zm[k]);
+                    if (m.hasY) f += (yf[j + 1] * yf[j + 1] * txy[c + m.sj] - yf[j] * yf[j] * txy[c]) / (r * r * dy[j]);
+                    if (m.hasZ) f += (txz[c + m.sk] - txz[c]) / (r * dz[k]);
+                    f += (txx[c] - txx[cm]) / (r * sn * dx);
+                    if (m.hasY) f += 0.5 * (txy[c] + txy[c + m.sj]) / r;
+                    if (m.hasZ) f += 2.0 * 0.5 * (txz[c] + txz[c + m.sk]) * ct / r;
+                }
+                s->vx[c] = vx[c] - dt * f / rf;
+            }
+    /* v_y update on interior faces (i, j-1/2, k) */
+    if (m.hasY)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0 + 1; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    int ip = IP(&m, i);
+                    size_t c = IDX(&m, i, j, k), cjm = c - m.sj, cp = IDX(&m, ip, j, k);
+                    double rf = 0.5 * (rho[c] + rho[cjm]);
+                    double f = 0.0;
+                    if (geom == OR_CART) {
+                        f += (txy[cp] - txy[c]) / dx;
+                        f += (tyy[c] - tyy[cjm]) / (ym[j] - ym[j - 1]);
+                        if (m.hasZ) f += (tyz[c + m.sk] - tyz[c]) / dz[k];
+                    } else if (geom == OR_CYL) {
+                        double r = yf[j];
+                        f += (ym[j] * tyy[c] - ym[j - 1] * tyy[cjm]) / (r * (ym[j] - ym[j - 1]));
+                        f += (txy[cp] - txy[c]) / (r * dx);
+                        f -= 0.5 * (txx[c] + txx[cjm]) / r;
+                        if (m.hasZ) f += (tyz[c + m.sk] - tyz[c]) / dz[k];
+                    } else {
+                        double r = yf[j], sn = sin(zm[k]);
+                        f += (ym[j] * ym[j] * tyy[c] - ym[j - 1] * ym[j - 1] * tyy[cjm]) / (r * r * (ym[j] - ym[j - 1]));
+                        if (m.hasZ) f += (tyz[c + m.sk] * sin(zf[k + 1]) - tyz[c] * sin(zf[k])) / (r * sn * dz[k]);
+                        f += (txy[cp] - txy[c]) / (r * sn * dx);
+                        f -= 0.5 * (tzz[c] + tzz[cjm] + txx[c] + txx[cjm]) / r;
+                    }
+                    s->vy[c] = vy[c] - dt * f / rf;
+                }
+    /* v_z update on interior faces (i, j, k-1/2) */
+    if (m.hasZ)
+        for (int k = m.k0 + 1; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    int ip = IP(&m, i);
+                    size_t c = IDX(&m, i, j, k), ckm = c - m.sk, cp = IDX(&m, ip, j, k);
+                    double rf = 0.5 * (rho[c] + rho[ckm]);
+                    double f = 0.0;
+                    if (geom == OR_CART) {
+                        f += (txz[cp] - txz[c]) / dx;
+                        if (m.hasY) f += (tyz[c + m.sj] - tyz[c]) / dy[j];
+                        f += (tzz[c] - tzz[ckm]) / (zm[k] - zm[k - 1]);
+                    } else if (geom == OR_CYL) {
+                        double r = ym[j];
+                        if (m.hasY) f += (yf[j + 1] * tyz[c + m.sj] - yf[j] * tyz[c]) / (r * dy[j]);
+                        f += (txz[cp] - txz[c]) / (r * dx);
+                        f += (tzz[c] - tzz[ckm]) / (zm[k] - zm[k - 1]);
+                    } else {
+                        double r = ym[j], sf = sin(zf[k]), ctf = cos(zf[k]) / sin(zf[k]);
+                        if (m.hasY) f += (yf[j + 1] * yf[j + 1] * yf[j + 1] * tyz[c + m.sj] - yf[j] * yf[j] * yf[j] * tyz[c]) / (r * r * r * dy[j]);
+                        f += (tzz[c] * sin(zm[k]) - tzz[ckm] * sin(zm[k - 1])) / (r * sf * (zm[k] - zm[k - 1]));
+                        f += (txz[cp] - txz[c]) / (r * sf * dx);
+                        f -= 0.5 * (txx[c] + txx[ckm]) * ctf / r;
+                    }
+                    s->vz[c] = vz[c] - dt * f / rf;
+                }
+#undef NU
+    free(txx); free(tyy); free(tzz); free(txy); free(txz); free(tyz);
+    free(v0s.vx); free(v0s.vy); free(v0s.vz);
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 12a: left and right momenta (Eqs. 16-17) with the geometric factors  */
+/* of Tab. "momenta": X carries rho (R v + R^2 Omega_f), Z in spherical       */
+/* geometry carries rho r v_theta.  Computed on every cell that has both     */
+/* faces in storage, ghosts included (the sweeps read ghost values).         */
+/* pi = { Pi-_x, Pi+_x, Pi-_y, Pi+_y, Pi-_z, Pi+_z }.                          */
+/* ------------------------------------------------------------------------ */
+void or_momenta(const or_params *p, const or_state *s, double *pi[6])
+{
+    mesh m;
+    mesh_init(&m, p);
+    for (int q = 0; q < 6; q++) memset(pi[q], 0, sizeof(double) * m.n);
+    for (int k = 0; k < m.nzt; k++)
+        for (int j = 0; j < m.nyt; j++) {
+            double R = ring_R(&m, j, k);
+            double w = R * R * p->omega_f;
+            double fz = p->geom == OR_SPH ? m.ym[j] : 1.0;
+            for (int i = 0; i < m.nx; i++) {
+                size_t c = IDX(&m, i, j, k);
+                double r = s->rho[c];
+                pi[0][c] = r * (R * s->vx[c] + w);
+                pi[1][c] = r * (R * s->vx[IDX(&m, IP(&m, i), j, k)] + w);
+                if (m.hasY) { pi[2][c] = r * s->vy[c]; pi[3][c] = r * s->vy[c + m.sj]; }
+                if (m.hasZ) { pi[4][c] = r * (fz * s->vz[c]); pi[5][c] = r * (fz * s->vz[c + m.sk]); }
+            }
+        }
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* van Leer slope (Sec. 3.5, below Eq. 15): the harmonic mean of the two     */
+/* one-sided differences divided by the centre-to-centre distances, zero     */
+/* when they differ in sign or one vanishes.                                 */
+/* ------------------------------------------------------------------------ */
+double or_vanleer_slope(double qm, double q0, double qp, double dxm, double dxp)
+{
+    double dp = (qp - q0) / dxp, dm = (q0 - qm) / dxm;
+    if (dp * dm > 0.0) return 2.0 * dp * dm / (dp + dm);
+    return 0.0;
+}
+
+/* One conservative 1D upwind sweep (Eqs. 1D-advection-X/Y/Z, flux Eq. 14,   */
+/* interface value Eq. 15) over one line of cells.  q[0] is the density;     */
+/* the other quantities are transported consistently (their ratio to the    */
+/* density is interpolated and multiplied by the mass flux).  Face f lies    */
+/* between cells f-1 and f; faces c0..c1 are used, cells c0..c1-1 updated.  */
+typedef struct {
+    int n, nq;
+    double **q;          /* nq lines of n values */
+    const double *cen;   /* centre coordinate of each cell */
+    const double *wid;   /* width of each cell */
+    const double *vel;   /* face velocity, face f at index f */
+    const double *area;  /* face area, face f at index f */
+    const double *vinv;  /* inverse volume per cell */
+} line_t;
+
+static double vl_face(const line_t *L, const double *f, int face, double v, double dt)
+{
+    if (v >= 0.0) {
+        int c = face - 1;
+        double a = or_vanleer_slope(f[c - 1], f[c], f[c + 1], L->cen[c] - L->cen[c - 1], L->cen[c + 1] - L->cen[c]);
+        return f[c] + a * (L->wid[c] - v * dt) / 2.0;
+    } else {
+        int c = face;
+        double a = or_vanleer_slope(f[c - 1], f[c], f[c + 1], L->cen[c] - L->cen[c - 1], L->cen[c + 1] - L->cen[c]);
+        return f[c] - a * (L->wid[c] + v * dt) / 2.0;
+    }
+}
+
+static void sweep_line(const line_t *L, int c0, int c1, double dt)
+{
+    int n = L->n, nq = L->nq;
+    double **ratio = malloc(sizeof(double *) * nq);
+    double **flux = malloc(sizeof(double *) * nq);
+    for (int q = 0; q < nq; q++) {
+        flux[q] = zalloc(n + 1);
+        ratio[q] = zalloc(n);
+        for (int c = 0; c < n; c++) ratio[q][c] = q == 0 ? L->q[0][c] : L->q[q][c] / L->q[0][c];
+    }
+    for (int f = c0; f <= c1; f++) {
+        double v = L->vel[f];
+        double fr = v * vl_face(L, ratio[0], f, v, dt) * L->area[f];
+        flux[0][f] = fr;
+        for (int q = 1; q < nq; q++) flux[q][f] = fr * vl_face(L, ratio[q], f, v, dt);
+    }
+    for (int q = 0; q < nq; q++)
+        for (int c = c0; c < c1; c++)
+            L->q[q][c] -= dt * L->vinv[c] * (flux[q][c + 1] - flux[q][c]);
+    for (int q = 0; q < nq; q++) { free(flux[q]); free(ratio[q]); }
+    free(flux); free(ratio);
+}
+
+/* Nearest integer E(X) of Sec. 3.4.1, ties away from zero. */
+long long or_nearest_int(double x) { return llround(x); }
+
+/* Integer shift, Eq. 32: circular permutation Q_i <- Q_{i-N}. */
+void or_shift_ring(int n, double *q, long long nshift)
+{
+    double *t = malloc(sizeof(double) * n);
+    long long N = ((nshift % n) + n) % n;
+    for (int i = 0; i < n; i++) t[i] = q[(i - N + n) % n];
+    memcpy(q, t, sizeof(double) * n);
+    free(t);
+}
+
+/* PPA interface values on a periodic ring (Eqs. 34-36 and the xi-weighted  */
+/* interface value of Sec. 3.4.1).  qstar[i] is the value on the face        */
+/* between cells i-1 and i for the uniform signed Courant number xi_signed. */
+void or_ppa_faces(int n, const double *q, double xs, double *qstar)
+{
+    double *dm = zalloc(n), *qr = zalloc(n), *L = zalloc(n), *R = zalloc(n);
+    for (int i = 0; i < n; i++) {
+        double qm = q[(i - 1 + n) % n], q0 = q[i], qp = q[(i + 1) % n];
+        double d = 0.5 * (qp - qm);
+        if ((qp - q0) * (q0 - qm) <= 0.0) dm[i] = 0.0;
+        else {
+            double a = 2.0 * fabs(q0 - qm), b = 2.0 * fabs(qp - q0), c = fabs(d);
+            double mn = a < b ? a : b;
+            if (c < mn) mn = c;
+            dm[i] = d > 0.0 ? mn : -mn;
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        int ip = (i + 1) % n;
+        qr[i] = q[i] + 0.5 * (q[ip] - q[i]) - (dm[ip] - dm[i]) / 6.0;   /* Eq. 35 */
+    }
+    for (int i = 0; i < n; i++) {
+        double qm = q[(i - 1 + n) % n], q0 = q[i], qp = q[(i + 1) % n];
+        double l = qr[(i - 1 + n) % n], r = qr[i];
+        if ((qp - q0) * (q0 - qm) <= 0.0) { l = q0; r = q0; }            /* Eq. 36 */
+        else {
+            double D = r - l, C = q0 - 0.5 * (l + r);
+            if (D * C > D * D / 6.0) l = 3.0 * q0 - 2.0 * r;
+            else if (-D * D / 6.0 > D * C) r = 3.0 * q0 - 2.0 * l;
+        }
+        L[i] = l; R[i] = r;
+    }
+    for (int f = 0; f < n; f++) {
+        if (xs >= 0.0) {
+            int d = (f - 1 + n) % n;
+            double xi = xs;
+            qstar[f] = R[d] + xi * (q[d] - R[d]) + xi * (1.0 - xi) * (2.0 * q[d] - R[d] - L[d]);
+        } else {
+            int d = f;
+            double xi = -xs;
+            qstar[f] = L[d] + xi * (q[d] - L[d]) + xi * (1.0 - xi) * (2.0 * q[d] - R[d] - L[d]);
+        }
+    }
+    free(dm); free(qr); free(L); free(R);
+}
+
+/* Quantities carried by the transport step (Sec. 3.2): density, internal   */
+/* energy (adiabatic), and the left/right momenta of each active direction. */
+static int gather_quantities(const mesh *m, or_state *s, double *pi[6], double **out)
+{
+    int nq = 0;
+    out[nq++] = s->rho;
+    if (!m->p->iso) out[nq++] = s->e;
+    out[nq++] = pi[0]; out[nq++] = pi[1];
+    if (m->hasY) { out[nq++] = pi[2]; out[nq++] = pi[3]; }
+    if (m->hasZ) { out[nq++] = pi[4]; out[nq++] = pi[5]; }
+    return nq;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cells 12b-c along X with orbital advection (Sec. 3.4.1): residual         */
+/* transport at delta v = v - v0 (Eq. fargo1) with van Leer interface values,*/
+/* then the integer shift by N = E(v0 dt / dX) (Eqs. 29-32), then the        */
+/* uniform fractional step at v_shift^R (Eqs. 31, 33) with PPA interface     */
+/* values.  The X length of ring (j,k) is R dx.  Active rings only.          */
+/* ------------------------------------------------------------------------ */
+void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double *v0, double dt)
+{
+    mesh m;
+    mesh_init(&m, p);
+    if (!m.hasX) { mesh_free(&m); return; }
+    double *fld[8];
+    int nq = gather_quantities(&m, s, pi, fld);
+    int nx = m.nx, n = nx + 4;
+    double **lq = malloc(sizeof(double *) * nq);
+    for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
+    double *cen = zalloc(n), *wid = zalloc(n), *vel = zalloc(n), *area = zalloc(n), *vinv = zalloc(n);
+    double *ring = zalloc(nx), *fs = zalloc(nx);
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++) {
+            double dX = len_x(&m, j, k);
+            double vr0 = p->fargo ? v0[(size_t)k * m.nyt + j] : 0.0;
+            double S = area_x(&m, j, k), Vi = inv_vol(&m, j, k);
+            /* (i) residual velocity sweep on a ring padded by periodic images */
+            for (int c = 0; c < n; c++) {
+                int i = ((c - 2) % nx + nx) % nx;
+                cen[c] = c * dX; wid[c] = dX; area[c] = S; vinv[c] = Vi;
+                vel[c] = s->vx[IDX(&m, i, j, k)] - vr0;
+                for (int q = 0; q < nq; q++) lq[q][c] = fld[q][IDX(&m, i, j, k)];
+            }
+            line_t L = { n, nq, lq, cen, wid, vel, area, vinv };
+            sweep_line(&L, 2, nx + 2, dt);
+            for (int q = 0; q < nq; q++)
+                for (int i = 0; i < nx; i++) fld[q][IDX(&m, i, j, k)] = lq[q][i + 2];
+            if (!p->fargo) continue;
+            /* (ii) integer shift */
+            double X = vr0 * dt / dX;
+            long long N = or_nearest_int(X);
+            double xs = X - (double)N;
+            for (int q = 0; q < nq; q++) {
+                for (int i = 0; i < nx; i++) ring[i] = fld[q][IDX(&m, i, j, k)];
+                or_shift_ring(nx, ring, N);
+                for (int i = 0; i < nx; i++) fld[q][IDX(&m, i, j, k)] = ring[i];
+            }
+            /* (iii) uniform fractional step with PPA interface values */
+            if (xs == 0.0) continue;
+            double vR = xs * dX / dt;
+            double *flux0 = zalloc(nx + 1), **fl = malloc(sizeof(double *) * nq);
+            for (int i = 0; i < nx; i++) ring[i] = fld[0][IDX(&m, i, j, k)];
+            or_ppa_faces(nx, ring, xs, fs);
+            for (int f = 0; f < nx; f++) flux0[f] = vR * fs[f] * S;
+            for (int q = 0; q < nq; q++) {
+                fl[q] = zalloc(nx + 1);
+                if (q == 0) { memcpy(fl[0], flux0, sizeof(double) * nx); continue; }
+                for (int i = 0; i < nx; i++) ring[i] = fld[q][IDX(&m, i, j, k)] / fld[0][IDX(&m, i, j, k)];
+                or_ppa_faces(nx, ring, xs, fs);
+                for (int f = 0; f < nx; f++) fl[q][f] = flux0[f] * fs[f];
+            }
+            for (int q = 0; q < nq; q++) {
+                for (int i = 0; i < nx; i++)
+                    fld[q][IDX(&m, i, j, k)] -= dt * Vi * (fl[q][(i + 1) % nx] - fl[q][i]);
+                free(fl[q]);
+            }
+            free(fl); free(flux0);
+        }
+    for (int q = 0; q < nq; q++) free(lq[q]);
+    free(lq); free(cen); free(wid); free(vel); free(area); free(vinv); free(ring); free(fs);
+    mesh_free(&m);
+}
+
+/* Cells 12b-c along Y (Eq. 1D-advection-Y): non-uniform radial spacing,     */
+/* face areas S_y(j,k) and inverse volumes of Appendix A.  Face velocities   */
+/* are the post-source v_y, unchanged during the transport step.           */
+void or_transport_y(const or_params *p, or_state *s, double *pi[6], double dt)
+{
+    mesh m;
+    mesh_init(&m, p);
+    if (!m.hasY) { mesh_free(&m); return; }
+    double *fld[8];
+    int nq = gather_quantities(&m, s, pi, fld);
+    int n = m.nyt;
+    double **lq = malloc(sizeof(double *) * nq);
+    for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
+    double *vel = zalloc(n + 1), *area = zalloc(n + 1), *vinv = zalloc(n);
+    for (int k = m.k0; k < m.k1; k++)
+        for (int i = 0; i < m.nx; i++) {
+            for (int j = 0; j < n; j++) {
+                size_t c = IDX(&m, i, j, k);
+                vel[j] = s->vy[c];
+                area[j] = area_y(&m, j, k);
+                vinv[j] = inv_vol(&m, j, k);
+                for (int q = 0; q < nq; q++) lq[q][j] = fld[q][c];
+            }
+            line_t L = { n, nq, lq, m.ym, m.dy, vel, area, vinv };
+            sweep_line(&L, m.j0, m.j1, dt);
+            for (int q = 0; q < nq; q++)
+                for (int j = m.j0; j < m.j1; j++) fld[q][IDX(&m, i, j, k)] = lq[q][j];
+        }
+    for (int q = 0; q < nq; q++) free(lq[q]);
+    free(lq); free(vel); free(area); free(vinv);
+    mesh_free(&m);
+}
+
+/* Cells 12b-c along Z (Eq. 1D-advection-Z); in spherical geometry the       */
+/* colatitude lengths are r dtheta.                                          */
+void or_transport_z(const or_params *p, or_state *s, double *pi[6], double dt)
+{
+    mesh m;
+    mesh_init(&m, p);
+    if (!m.hasZ) { mesh_free(&m); return; }
+    double *fld[8];
+    int nq = gather_quantities(&m, s, pi, fld);
+    int n = m.nzt;
+    double **lq = malloc(sizeof(double *) * nq);
+    for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
+    double *vel = zalloc(n + 1), *area = zalloc(n + 1), *vinv = zalloc(n), *cen = zalloc(n), *wid = zalloc(n);
+    for (int j = m.j0; j < m.j1; j++) {
+        double f = p->geom == OR_SPH ? m.ym[j] : 1.0;
+        for (int k = 0; k < n; k++) { cen[k] = f * m.zm[k]; wid[k] = f * m.dz[k]; }
+        for (int i = 0; i < m.nx; i++) {
+            for (int k = 0; k < n; k++) {
+                size_t c = IDX(&m, i, j, k);
+                vel[k] = s->vz[c];
+                area[k] = area_z(&m, j, k);
+                vinv[k] = inv_vol(&m, j, k);
+                for (int q = 0; q < nq; q++) lq[q][k] = fld[q][c];
+            }
+            line_t L = { n, nq, lq, cen, wid, vel, area, vinv };
+            sweep_line(&L, m.k0, m.k1, dt);
+            for (int q = 0; q < nq; q++)
+                for (int k = m.k0; k < m.k1; k++) fld[q][IDX(&m, i, j, k)] = lq[q][k];
+        }
+    }
+    for (int q = 0; q < nq; q++) free(lq[q]);
+    free(lq); free(vel); free(area); free(vinv); free(cen); free(wid);
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell 12d: new face velocities from the new momenta and densities, Eq. 18, */
+/* undoing the geometric factors of Tab. "momenta".  Interior faces only.    */
+/* ------------------------------------------------------------------------ */
+void or_new_velocities(const or_params *p, or_state *s, double *pi[6])
+{
+    mesh m;
+    mesh_init(&m, p);
+    const double *rho = s->rho;
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++) {
+            double R = ring_R(&m, j, k), w = R * R * p->omega_f;
+            for (int i = 0; i < m.nx; i++) {
+                size_t c = IDX(&m, i, j, k), cm = IDX(&m, IM(&m, i), j, k);
+                s->vx[c] = ((pi[1][cm] + pi[0][c]) / (rho[cm] + rho[c]) - w) / R;
+            }
+        }
+    if (m.hasY)
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0 + 1; j < m.j1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = c - m.sj;
+                    s->vy[c] = (pi[3][cm] + pi[2][c]) / (rho[cm] + rho[c]);
+                }
+    if (m.hasZ)
+        for (int k = m.k0 + 1; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++) {
+                double f = p->geom == OR_SPH ? m.ym[j] : 1.0;
+                for (int i = 0; i < m.nx; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = c - m.sk;
+                    s->vz[c] = (pi[5][cm] + pi[4][c]) / (rho[cm] + rho[c]) / f;
+                }
+            }
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One full update, in the order of the flow chart (Fig. 2).                 */
+/* ------------------------------------------------------------------------ */
+int or_step(const or_params *p, or_state *s, double t, double t_end, double dt_fixed, double *dt_out)
+{
+    mesh m;
+    mesh_init(&m, p);
+    size_t nr = (size_t)m.nzt * m.nyt;
+    double *v0 = zalloc(nr);
+    double dt;
+    int rc = 0;
+    or_bc_fill(p, s);                                     /* cell 2 */
+    or_v0(p, s, v0);                                      /* cell 3 */
+    if (dt_fixed > 0.0) dt = dt_fixed;
+    else rc = or_cfl(p, s, v0, t, t_end, &dt);            /* cells 4-6 */
+    if (rc) { free(v0); mesh_free(&m); *dt_out = dt; return rc; }
+    double *phi = NULL;
+    if (p->planet_q > 0.0 || (p->star_mass > 0.0 && p->geom != OR_CART)) {
+        phi = zalloc(m.n);
+        or_potential(p, t, phi);                          /* cell 5 */
+    }
+    or_substep1(p, s, phi, dt);                           /* cell 7a */
+    or_artificial_viscosity(p, s, dt);                    /* cell 7b */
+    or_compression_heating(p, s, dt);                     /* cell 7c */
+    or_viscosity(p, s, dt);                               /* cell 7d */
+    or_bc_fill(p, s);                                     /* cell 9 */
+    double *pi[6];
+    for (int q = 0; q < 6; q++) pi[q] = zalloc(m.n);
+    or_momenta(p, s, pi);                                 /* cell 12a */
+    or_transport_x(p, s, pi, v0, dt);                     /* cells 12b-c */
+    or_transport_y(p, s, pi, dt);
+    or_transport_z(p, s, pi, dt);
+    or_new_velocities(p, s, pi);                          /* cell 12d */
+    for (int q = 0; q < 6; q++) free(pi[q]);
+    free(phi); free(v0);
+    mesh_free(&m);
+    *dt_out = dt;
+    return 0;
+}

@@ -1,0 +1,75 @@
+/*
+ * Plain, slow FP64 CPU oracle of one FARGO3D hydrodynamic time step
+ * (Benitez-Llambay & Masset 2016, Sec. 3 and Appendices A-B).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package smoke check
+ * and the CPU-baseline leg of the benchmark may load this library.  It shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * Every field is a full array of shape (nz_t + 1, ny_t + 1, nx), X fastest,
+ * ny_t = ny + 2g (ny > 1) else 1, nz_t likewise.  Scalars are cell centred;
+ * v_x, v_y, v_z live on the lower X, Y, Z face of their cell (Sec. 2.3).
+ */
+#ifndef FARGO_ORACLE_H
+#define FARGO_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_CART = 0, OR_CYL = 1, OR_SPH = 2 };
+enum { OR_BC_REFLECT = 0, OR_BC_FROZEN = 1, OR_BC_ZEROGRAD = 2 };
+
+typedef struct {
+    int geom, nx, ny, nz, g;
+    double xmin, xmax;
+    const double *yf, *zf;      /* face coordinates, ny_t+1 and nz_t+1 entries */
+    double gamma;
+    int iso;                    /* 1: P = cs^2 rho (Eq. eos1); 0: P = (gamma-1) e (Eq. eos2) */
+    const double *cs;           /* isothermal sound speed per ring [nz_t][ny_t] */
+    const double *nu;           /* kinematic viscosity per ring [nz_t][ny_t], NULL = inviscid */
+    double cfl, cq;
+    int av_dt_literal;          /* 1: Delta t_3 = 4 sqrt2 |Delta/Delta v| as printed in Sec. 3.4 */
+    double omega_f;             /* constant frame rotation rate */
+    int fargo;                  /* 0: STANDARD transport */
+    int bc_ylo, bc_yhi, bc_zlo, bc_zhi;
+    double star_mass, planet_q, planet_a, planet_eps;
+    int indirect;
+} or_params;
+
+typedef struct { double *rho, *e, *vx, *vy, *vz; } or_state;
+
+/* Full step: cells 2..12 of the flow chart (Fig. 2).  dt_fixed > 0 skips the
+ * Courant reduction and uses the given step.  Returns 0 or a negative code. */
+int  or_step(const or_params *p, or_state *s, double t, double t_end, double dt_fixed, double *dt_out);
+
+/* Individual sub-steps (each cites its section inside the source). */
+void or_bc_fill(const or_params *p, or_state *s);
+void or_v0(const or_params *p, const or_state *s, double *v0 /* [nz_t][ny_t] */);
+int  or_cfl(const or_params *p, const or_state *s, const double *v0, double t, double t_end, double *dt);
+void or_potential(const or_params *p, double t, double *phi /* full cell array */);
+void or_substep1(const or_params *p, or_state *s, const double *phi, double dt);
+void or_artificial_viscosity(const or_params *p, or_state *s, double dt);
+void or_compression_heating(const or_params *p, or_state *s, double dt);
+void or_viscosity(const or_params *p, or_state *s, double dt);
+void or_momenta(const or_params *p, const or_state *s, double *pi[6]);
+void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double *v0, double dt);
+void or_transport_y(const or_params *p, or_state *s, double *pi[6], double dt);
+void or_transport_z(const or_params *p, or_state *s, double *pi[6], double dt);
+void or_new_velocities(const or_params *p, or_state *s, double *pi[6]);
+
+/* Geometry of Appendix A, per ring (j,k): face areas, inverse volume,
+ * volume and azimuthal cell length. Arrays [nz_t][ny_t] (sy, sz also use the
+ * extra row / plane: [nz_t+1][ny_t+1]). */
+void or_geometry(const or_params *p, double *sx, double *sy, double *sz, double *vinv, double *vol, double *dxr);
+
+/* 1D building blocks, exposed for the special-case tests. */
+double or_vanleer_slope(double qm, double q0, double qp, double dxm, double dxp);
+void or_ppa_faces(int n, const double *q, double xi_signed, double *qstar /* face i = between i-1 and i */);
+void or_shift_ring(int n, double *q, long long nshift);
+long long or_nearest_int(double x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

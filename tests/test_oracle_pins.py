@@ -1,0 +1,635 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the exact
+Riemann solution, exact conservation laws, exact symmetries, closed forms and
+convergence rates of continuum solutions.  None needs a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests import riemann
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(HERE, "golden", name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+# --------------------------------------------------------------------------
+# Whole step: Sod shock tube (Sec. 5.1.1) against the exact Riemann solution
+# --------------------------------------------------------------------------
+def run_sod(n=512):
+    w = W.sod(ny=n)
+    o = oracle.Oracle(w)
+    t, nsteps = o.run(w.state, 0.0, w.t_end)
+    assert t == w.t_end
+    y = W.centres(w.yf)[w.gy:w.gy + w.ny]
+    return w, y, nsteps
+
+
+def test_sod_matches_exact_riemann_solution():
+    w, y, nsteps = run_sod()
+    gam = w.gamma
+    ex = riemann.sample(y, 0.2, 0.5, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), gam)
+    rho = w.active(w.state["rho"])[0, :, 0]
+    e = w.active(w.state["e"])[0, :, 0]
+    p = (gam - 1.0) * e
+    l1 = np.mean(np.abs(rho - ex[0])) / np.mean(ex[0])
+    assert l1 < 2e-2, l1
+    # plateau between contact and shock: the paper reports an offset ~1e-2
+    ps, us = riemann.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, gam)
+    xs = 0.5 + 0.2 * riemann.shock_speed(0.125, 0.0, 0.1, ps, gam)
+    xc = 0.5 + 0.2 * us
+    plateau = (y > xc + 0.04) & (y < xs - 0.03)
+    rstar = ex[0][plateau][0]
+    assert np.max(np.abs(rho[plateau] / rstar - 1.0)) < 2e-2
+    assert np.max(np.abs(p[plateau] / ps - 1.0)) < 1e-2
+    # shock position: density crosses the mid value within 2 cells of exact
+    mid = 0.5 * (rstar + 0.125)
+    jshock = np.where((rho[:-1] > mid) & (rho[1:] <= mid))[0][-1]
+    assert abs(y[jshock] + 0.5 / w.ny - xs) < 2.0 / w.ny
+
+
+def test_sod_agrees_with_paper_printed_figures():
+    g = read_golden("sod_paper.txt")
+    w, y, _ = run_sod(n=300)   # the paper's resolution, on [0,1] at t = 0.2
+    rho = w.active(w.state["rho"])[0, :, 0]
+    dy = 1.0 / w.ny
+    ps, us = riemann.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
+    rstar = riemann.sample([0.8], 0.2, 0.5, (1, 0, 1), (0.125, 0, 0.1))[0][0]
+    # shock and contact locations printed in the caption (scaled by 1/10)
+    mid = 0.5 * (rstar + 0.125)
+    js = np.where((rho[:-1] > mid) & (rho[1:] <= mid))[0][-1]
+    assert abs((y[js] + 0.5 * dy) - g["shock_position"] / 10.0) < 0.01
+    rl = riemann.sample([0.6], 0.2, 0.5, (1, 0, 1), (0.125, 0, 0.1))[0][0]
+    midc = 0.5 * (rl + rstar)
+    jc = np.where((rho[:-1] > midc) & (rho[1:] <= midc))[0]
+    jc = jc[(y[jc] > 0.6) & (y[jc] < 0.75)][0]
+    assert abs((y[jc] + 0.5 * dy) - g["contact_position"] / 10.0) < 0.01
+    # shock spread over 2-3 zones: cells strictly between 10% and 90% of the jump
+    lo, hi = 0.125 + 0.1 * (rstar - 0.125), 0.125 + 0.9 * (rstar - 0.125)
+    inside = np.sum((rho > lo) & (rho < hi) & (y > 0.8))
+    assert inside <= g["shock_width_zones_max"]
+    lo, hi = rstar + 0.1 * (rl - rstar), rstar + 0.9 * (rl - rstar)
+    inside = np.sum((rho > lo) & (rho < hi) & (y > 0.6) & (y < 0.8))
+    assert inside <= g["contact_width_zones_max"] + 2
+
+
+# --------------------------------------------------------------------------
+# Conservation (Secs. 3.2.1-3.2.2 and the end of 3.4.1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("geom,dims,iso,nu", [
+    (W.CART, (16, 12, 1), False, 1e-3),
+    (W.CART, (12, 10, 8), False, 1e-3),
+    (W.CYL, (16, 12, 1), True, 1e-3),
+    (W.CYL, (12, 10, 6), False, 0.0),
+    (W.SPH, (12, 10, 8), False, 1e-3),
+])
+def test_mass_conserved_in_closed_box(geom, dims, iso, nu):
+    nx, ny, nz = dims
+    w = W.random_box(geom, nx, ny, nz, g=3, seed=11, iso=iso, nu=nu, planet=True,
+                     bc=W.BC_REFLECT)
+    o = oracle.Oracle(w)
+    st = w.state
+    o.bc_fill(st)
+    m0, _, _ = o.sums(st)
+    t = 0.0
+    for _ in range(6):
+        t += o.step(st, t)
+    m1, _, _ = o.sums(st)
+    assert abs(m1 - m0) / m0 < 2e-14
+
+
+@pytest.mark.parametrize("geom,dims,nu", [
+    (W.CART, (16, 12, 1), 1e-3),     # viscous: no wall shear with reflecting walls
+    (W.CART, (10, 8, 6), 1e-3),
+    (W.CYL, (16, 12, 1), 0.0),
+    (W.SPH, (12, 8, 6), 0.0),
+])
+def test_azimuthal_momentum_conserved_without_external_torque(geom, dims, nu):
+    nx, ny, nz = dims
+    w = W.random_box(geom, nx, ny, nz, g=3, seed=5, iso=False, nu=nu, planet=False,
+                     bc=W.BC_REFLECT)
+    o = oracle.Oracle(w)
+    st = w.state
+    o.bc_fill(st)
+    _, _, l0 = o.sums(st)
+    scale = o.sums({k: np.abs(v) for k, v in st.items()})[2]
+    t = 0.0
+    for _ in range(5):
+        t += o.step(st, t)
+    _, _, l1 = o.sums(st)
+    assert abs(l1 - l0) / scale < 1e-13
+
+
+def test_pressure_source_conserves_ring_momentum():
+    """Eqs. 20-25: with the two-point face density the pressure source step
+    changes the ring's zone-centred momentum only by round-off."""
+    rng = np.random.default_rng(3)
+    w = W.random_box(W.CYL, 64, 1, 1, g=3, seed=2, iso=False, nu=0.0, planet=False)
+    st = w.state
+    st["rho"][:] = rng.uniform(0.5, 2.0, size=st["rho"].shape)
+    st["e"][:] = rng.uniform(0.5, 2.0, size=st["e"].shape)
+    o = oracle.Oracle(w)
+    rho = st["rho"][0, 0]
+    before = np.sum(rho * 0.5 * (st["vx"][0, 0] + np.roll(st["vx"][0, 0], -1)))
+    v_old = st["vx"][0, 0].copy()
+    o.substep1(st, None, 0.01)
+    after = np.sum(rho * 0.5 * (st["vx"][0, 0] + np.roll(st["vx"][0, 0], -1)))
+    change = np.sum(np.abs(rho * (st["vx"][0, 0] - v_old)))
+    assert change > 1e-4                       # the step does move the gas
+    assert abs(after - before) < 1e-14 * change * 64
+    # a one-sided face density breaks it: check the test would notice
+    P = 0.4 * st["e"][0, 0]
+    acc_bad = -(P - np.roll(P, 1)) / (2 * math.pi / 64 * 1.0 * rho)
+    assert abs(np.sum(rho * 0.5 * (acc_bad + np.roll(acc_bad, -1)))) * 0.01 > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Orbital advection (Sec. 3.4.1)
+# --------------------------------------------------------------------------
+def test_shift_is_exact_permutation():
+    rng = np.random.default_rng(1)
+    q = rng.normal(size=37)
+    for n in (0, 1, 5, -3, 37, 100, -81):
+        s = oracle.shift_ring(q, n)
+        assert np.array_equal(s, np.roll(q, n))
+        assert np.array_equal(oracle.shift_ring(s, -n), q)
+
+
+def test_nearest_integer_rounding():
+    assert oracle.nearest_int(2.5) == 3
+    assert oracle.nearest_int(-2.5) == -3
+    assert oracle.nearest_int(0.49999999999999994) == 0
+    assert oracle.nearest_int(-0.5) == -1
+    assert oracle.nearest_int(7.4999) == 7
+
+
+def _axisym_disk(geom, nx, ny, nz, seed, iso=True):
+    w = W.random_box(geom, nx, ny, nz, g=3, seed=seed, iso=iso, nu=1e-4, planet=False)
+    for k in W.FIELDS:
+        a = w.state[k]
+        a[:] = a[:, :, :1]          # every cell of a ring identical
+    if iso:
+        w.state["e"][:] = 0.0
+    return w
+
+
+@pytest.mark.parametrize("geom,dims", [(W.CYL, (48, 16, 1)), (W.SPH, (32, 10, 6))])
+def test_fargo_sweep_is_identity_on_axisymmetric_state(geom, dims):
+    w = _axisym_disk(geom, *dims, seed=4, iso=(geom == W.CYL))
+    o = oracle.Oracle(w)
+    st = w.state
+    v0 = o.v0(st)
+    pis = o.momenta(st)
+    before = [st["rho"].copy(), st["e"].copy()] + [p.copy() for p in pis]
+    dt = 0.1371
+    X = v0[w.gz, w.gy] * dt / (W.centres(w.yf)[w.gy] * 2 * math.pi / w.nx)
+    assert abs(X) > 1.5                          # a real multi-cell shift
+    o.transport_x(st, pis, v0, dt)
+    after = [st["rho"], st["e"]] + pis
+    for b, a in zip(before, after):
+        assert np.array_equal(b, a)
+
+
+def test_axisymmetric_disk_stays_exactly_axisymmetric():
+    w = _axisym_disk(W.CYL, 40, 16, 1, seed=8)
+    o = oracle.Oracle(w)
+    st = w.state
+    t = 0.0
+    for _ in range(8):
+        t += o.step(st, t)
+    for k in ("rho", "vx", "vy"):
+        a = w.active(st[k])
+        assert np.all(a.max(axis=2) == a.min(axis=2)), k
+
+
+def _ring_case(nx, v, dt, fargo, rho):
+    w = W.random_box(W.CART, nx, 1, 1, g=2, seed=0, iso=True, nu=0.0, planet=False, fargo=fargo)
+    w.cs = np.ones((1, 1))
+    st = w.state
+    st["rho"][:] = rho[None, None, :]
+    st["vx"][:] = v
+    o = oracle.Oracle(w)
+    v0 = o.v0(st)
+    pis = o.momenta(st)
+    o.transport_x(st, pis, v0, dt)
+    return st, pis
+
+
+def test_courant_one_upwind_step_is_exact_shift():
+    """Eq. 15 with v dt = dX: the interface value is the donor cell value and the
+    update moves every cell by one zone exactly (power-of-two mesh)."""
+    nx = 64
+    rng = np.random.default_rng(9)
+    rho = rng.uniform(1.0, 2.0, size=nx)
+    st, _ = _ring_case(nx, 0.5, 2.0 / nx, False, rho)
+    assert np.array_equal(st["rho"][0, 0], np.roll(rho, 1))
+
+
+def test_uniform_orbital_shift_is_exact():
+    """v uniform with v dt / dX an integer: the residual and fractional steps
+    vanish and the update is the circular permutation of Eq. 32."""
+    nx = 64
+    rng = np.random.default_rng(10)
+    rho = rng.uniform(0.5, 3.0, size=nx)
+    st, pis = _ring_case(nx, 1.25, 5 * (1.0 / nx) / 1.25, True, rho)
+    assert np.array_equal(st["rho"][0, 0], np.roll(rho, 5))
+
+
+def test_vanleer_slope_special_cases():
+    # linear data: the harmonic mean of equal slopes is the slope
+    assert oracle.vanleer_slope(1.0, 3.0, 5.0, 2.0, 2.0) == 1.0
+    # non-uniform spacing: exact for a linear profile
+    assert abs(oracle.vanleer_slope(0.0, 0.3, 0.8, 0.3, 0.5) - 1.0) < 1e-15
+    # extremum and flat data: zero
+    assert oracle.vanleer_slope(1.0, 2.0, 1.0, 1.0, 1.0) == 0.0
+    assert oracle.vanleer_slope(2.0, 2.0, 3.0, 1.0, 1.0) == 0.0
+    # harmonic mean value
+    assert abs(oracle.vanleer_slope(0.0, 1.0, 4.0, 1.0, 1.0) - 2 * 3 * 1 / 4) < 1e-15
+
+
+def test_ppa_exact_for_monotone_parabola():
+    """Eqs. 34-36 reconstruct a parabola exactly away from extrema, so the
+    interface value is the exact mean of the parabola over the donor region."""
+    n = 40
+    x = np.arange(n + 1) / n            # faces on [0,1]
+    F = lambda s: s ** 3 / 3 + 0.7 * s ** 2 / 2 + 0.2 * s   # primitive of s^2 + 0.7 s + 0.2
+    q = (F(x[1:]) - F(x[:-1])) * n      # cell averages of a monotone parabola
+    for xi in (0.37, 0.9, -0.61, 1.0):
+        qs = oracle.ppa_faces(q, xi)
+        for f in range(4, n - 4):
+            if xi >= 0:
+                a, b = x[f] - xi / n, x[f]
+            else:
+                a, b = x[f], x[f] - xi / n
+            exact = (F(b) - F(a)) / (b - a)
+            assert abs(qs[f] - exact) < 1e-13, (xi, f)
+
+
+def test_ppa_limits_and_monotonicity():
+    rng = np.random.default_rng(2)
+    q = np.where(np.arange(50) < 25, 1.0, 0.1) + 0.0
+    for xi in (0.0, 0.3, 0.8, -0.4):
+        qs = oracle.ppa_faces(q, xi)
+        assert qs.min() >= 0.1 - 1e-15 and qs.max() <= 1.0 + 1e-15
+    q = rng.uniform(size=30)
+    qs = oracle.ppa_faces(q, 1.0)
+    assert np.allclose(qs, np.roll(q, 1), rtol=0, atol=1e-15)   # whole donor cell
+    qs = oracle.ppa_faces(q, -1.0)
+    assert np.allclose(qs, q, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Geometry (Appendix A): "we leave as an exercise to the reader..."
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("geom", [W.CART, W.CYL, W.SPH])
+def test_areas_and_volumes_satisfy_gauss_theorem(geom):
+    """For the position vector, div r = 3, so sum over faces of r.S = 3 V."""
+    w = W.random_box(geom, 8, 6, 5, g=2, seed=1)
+    o = oracle.Oracle(w)
+    sx, sy, sz, vinv, vol, dxr = o.geometry()
+    yf, zf = w.yf, w.zf
+    for k in range(w.nz_t):
+        for j in range(w.ny_t):
+            if geom == W.CART:
+                flux = (1.0 / w.nx) * sx[k, j] + yf[j + 1] * sy[k, j + 1] - yf[j] * sy[k, j] \
+                    + zf[k + 1] * sz[k + 1, j] - zf[k] * sz[k, j]
+                # X faces at x and x + dx contribute dx * S_x
+            elif geom == W.CYL:
+                flux = yf[j + 1] * sy[k, j + 1] - yf[j] * sy[k, j] + zf[k + 1] * sz[k + 1, j] - zf[k] * sz[k, j]
+                flux += 0.0
+                # div(r e_r + z e_z) = 3 in cylindrical coordinates
+            else:
+                flux = yf[j + 1] * sy[k, j + 1] - yf[j] * sy[k, j]
+            assert abs(flux - 3.0 * vol[k, j]) < 1e-13 * abs(vol[k, j]) * 100
+            assert abs(vol[k, j] * vinv[k, j] - 1.0) < 1e-15
+
+
+def test_volume_matches_quadrature():
+    from scipy import integrate
+    w = W.random_box(W.SPH, 8, 6, 5, g=2, seed=1)
+    o = oracle.Oracle(w)
+    _, _, _, _, vol, _ = o.geometry()
+    dphi = (w.xmax - w.xmin) / w.nx
+    for (k, j) in [(0, 0), (3, 4), (8, 9)]:
+        v, _ = integrate.tplquad(lambda r, th, ph: r * r * math.sin(th), 0, dphi,
+                                 w.zf[k], w.zf[k + 1], w.yf[j], w.yf[j + 1])
+        assert abs(v - vol[k, j]) < 1e-12 * v
+
+
+# --------------------------------------------------------------------------
+# Sources (Sec. 3.3 and Appendix B) against continuum solutions
+# --------------------------------------------------------------------------
+def _equilibrium_residual(make, comp):
+    w = make()
+    o = oracle.Oracle(w)
+    st = w.state
+    before = st[comp].copy()
+    phi = o.potential(0.0)
+    dt = 1e-3
+    o.substep1(st, phi, dt)
+    acc = (w.active(st[comp]) - w.active(before)) / dt
+    if comp == "vy":
+        acc = acc[:, 1:, :]
+    if comp == "vz":
+        acc = acc[1:, :, :]
+    return np.max(np.abs(acc))
+
+
+def test_keplerian_disk_balance_converges_second_order():
+    """Gravity, pressure and centrifugal terms of sub-step 1 (Eq. 12) balance
+    the analytic equilibrium up to O(dr^2)."""
+    r1 = _equilibrium_residual(lambda: W.disk2d(nx=8, ny=64, q=0.0, nu=0.0), "vy")
+    r2 = _equilibrium_residual(lambda: W.disk2d(nx=8, ny=128, q=0.0, nu=0.0), "vy")
+    assert r2 < 1e-3
+    assert 3.3 < r1 / r2 < 4.7, (r1, r2)
+
+
+@pytest.mark.parametrize("comp", ["vy", "vz"])
+def test_spherical_hydrostatic_disk_balance_converges_second_order(comp):
+    # rho ~ sin^97.5(theta) is steep: the asymptotic rate needs n_theta >= 64
+    mk = lambda n: (lambda: W.disk3d(nx=4, ny=n, nz=n, q=0.0, alpha=0.0, h=0.1))
+    r1 = _equilibrium_residual(mk(64), comp)
+    r2 = _equilibrium_residual(mk(128), comp)
+    assert 3.2 < r1 / r2 < 4.7, (r1, r2)
+
+
+def _viscous_case(geom, nx, ny, nz, vfun, nu=1e-3):
+    w = W.random_box(geom, nx, ny, nz, g=3, seed=0, iso=True, nu=nu, planet=False)
+    w.nu = np.full((w.nz_t, w.ny_t), nu)
+    st = w.state
+    st["rho"][:] = 1.0
+    for k in ("vx", "vy", "vz"):
+        st[k][:] = 0.0
+    vfun(w, st)
+    return w, st
+
+
+def test_cartesian_shear_wave_decays_at_discrete_rate():
+    """For v_x = sin(k y) the stress divergence is exactly the 3-point
+    Laplacian, -4 sin^2(k dy/2)/dy^2 nu v_x (Eq. 72, 75)."""
+    ny = 32
+    nu, dt = 1e-3, 0.1
+
+    def vf(w, st):
+        ym = W.centres(w.yf)
+        st["vx"][:, :w.ny_t, :] = np.sin(2 * math.pi * ym)[None, :, None]
+    w, st = _viscous_case(W.CART, 4, ny, 1, vf, nu)
+    before = st["vx"].copy()
+    oracle.Oracle(w).viscosity(st, dt)
+    dy = 1.0 / ny
+    rate = -4.0 * math.sin(math.pi * dy) ** 2 / dy ** 2 * nu
+    got = (w.active(st["vx"]) - w.active(before)) / dt
+    want = rate * w.active(before)
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_cartesian_compressive_wave_has_four_thirds_factor():
+    """v_y = sin(k y): tau_yy = -(4/3) rho nu dv/dy, so dv/dt = (4/3) nu Lap v."""
+    ny = 32
+    nu, dt = 1e-3, 0.1
+
+    def vf(w, st):
+        st["vy"][:, :w.ny_t + 1, :] = np.sin(2 * math.pi * w.yf)[None, :, None]
+    w, st = _viscous_case(W.CART, 4, ny, 1, vf, nu)
+    before = st["vy"].copy()
+    oracle.Oracle(w).viscosity(st, dt)
+    dy = 1.0 / ny
+    rate = -4.0 / 3.0 * 4.0 * math.sin(math.pi * dy) ** 2 / dy ** 2 * nu
+    got = ((w.active(st["vy"]) - w.active(before)) / dt)[:, 1:, :]
+    want = (rate * w.active(before))[:, 1:, :]
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+def _kepler_torque_error(geom, n):
+    """Viscous acceleration of v_phi = R^-1/2 (R cylindrical radius), constant
+    rho and nu: continuum value -3/4 nu R^-5/2 (incompressible, nu Lap v)."""
+    nu, dt = 1e-3, 1e-3
+    if geom == W.CYL:
+        def vf(w, st):
+            ym = W.centres(w.yf)
+            st["vx"][:, :w.ny_t, :] = (ym ** -0.5)[None, :, None]
+        w, st = _viscous_case(W.CYL, 4, n, 1, vf, nu)
+        R = W.centres(w.yf)[None, :, None]
+    else:
+        def vf(w, st):
+            ym = W.centres(w.yf)[None, :]
+            zm = W.centres(w.zf)[:, None]
+            st["vx"][:w.nz_t, :w.ny_t, :] = ((ym * np.sin(zm)) ** -0.5)[:, :, None]
+        w, st = _viscous_case(W.SPH, 4, n, n, vf, nu)
+        R = (W.centres(w.yf)[None, :] * np.sin(W.centres(w.zf))[:, None])[:, :, None]
+    before = st["vx"].copy()
+    oracle.Oracle(w).viscosity(st, dt)
+    got = (w.active(st["vx"]) - w.active(before)) / dt
+    want = w.active(np.broadcast_to(-0.75 * nu * R ** -2.5, st["vx"][:w.nz_t, :w.ny_t].shape))
+    others = 0.0
+    for k in ("vy", "vz"):
+        others = max(others, np.max(np.abs(w.active(st[k]))))
+    return np.max(np.abs(got - want)), others
+
+
+@pytest.mark.parametrize("geom", [W.CYL, W.SPH])
+def test_keplerian_viscous_torque_converges_second_order(geom):
+    n1, n2 = (32, 64)
+    e1, o1 = _kepler_torque_error(geom, n1)
+    e2, o2 = _kepler_torque_error(geom, n2)
+    assert 3.0 < e1 / e2 < 5.0, (e1, e2)
+    assert o1 * 1e-3 < 1e-6 and o2 * 1e-3 < 1e-6      # no spurious r/theta forcing
+
+
+def test_compression_heating_follows_adiabat_to_third_order():
+    """Sub-step 3 for a homologous expansion v_r = a r in spherical geometry:
+    div v = 3a exactly (Gauss, Appendix A) and e follows exp(-(gamma-1) 3a t)
+    with an O(dt^3) local error."""
+    def err(dt):
+        w = W.random_box(W.SPH, 4, 8, 6, g=2, seed=0, iso=False, nu=0.0, planet=False)
+        st = w.state
+        a = 0.3
+        st["vy"][:, :, :] = (a * w.yf)[None, :, None]
+        st["vx"][:] = 0.0
+        st["vz"][:] = 0.0
+        e0 = st["e"].copy()
+        oracle.Oracle(w).compression_heating(st, dt)
+        ratio = w.active(st["e"]) / w.active(e0)
+        return np.max(np.abs(ratio - math.exp(-(w.gamma - 1.0) * 3 * a * dt)))
+    e1, e2 = err(0.2), err(0.1)
+    assert e1 < 1e-4
+    assert 6.0 < e1 / e2 < 10.0, (e1, e2)
+
+
+def test_artificial_viscosity_conserves_ring_momentum_and_heats():
+    w = W.random_box(W.CART, 64, 1, 1, g=2, seed=7, iso=False, nu=0.0, planet=False)
+    rng = np.random.default_rng(4)
+    st = w.state
+    st["vx"][:] = rng.normal(size=st["vx"].shape)
+    rho = st["rho"][0, 0]
+    mom = lambda: np.sum(rho * 0.5 * (st["vx"][0, 0] + np.roll(st["vx"][0, 0], -1)))
+    m0, e0 = mom(), st["e"].sum()
+    oracle.Oracle(w).artificial_viscosity(st, 0.01)
+    assert abs(mom() - m0) < 1e-13
+    assert st["e"].sum() > e0       # compressions only ever heat
+
+
+# --------------------------------------------------------------------------
+# Courant condition (Sec. 3.4, Eq. cfl2, and Sec. 3.4.2)
+# --------------------------------------------------------------------------
+def test_sod_initial_step_is_sound_crossing_time():
+    w = W.sod()
+    o = oracle.Oracle(w)
+    st = w.state
+    o.bc_fill(st)
+    rc, dt = o.cfl(st, o.v0(st))
+    assert rc == 0
+    cs = math.sqrt(1.4 * 1.0 / 1.0)
+    assert abs(dt - 0.5 * (1.0 / 512) / cs) < 1e-15 * dt * 4
+
+
+def test_fargo_removes_bulk_rotation_from_courant_condition():
+    w = _axisym_disk(W.CYL, 32, 12, 1, seed=3)
+    w.nu = None
+    w.cq = 0.0
+    st = w.state
+    rng = np.random.default_rng(0)
+    st["vx"] += 1e-3 * rng.normal(size=st["vx"].shape)
+    o = oracle.Oracle(w)
+    _, dt_a = o.cfl(st, o.v0(st))
+    bulk = np.zeros((w.nz_t + 1, w.ny_t + 1, 1))
+    bulk[:, :w.ny_t, 0] = 3.0 * W.centres(w.yf) ** -0.5     # smooth Keplerian-like bulk
+    st2 = {k: v.copy() for k, v in st.items()}
+    st2["vx"] += bulk
+    _, dt_b = o.cfl(st2, o.v0(st2))
+    # with FARGO only the residual enters (Sec. 3.4.2), STANDARD sees the full v
+    w2 = w.copy(); w2.fargo = False
+    o2 = oracle.Oracle(w2)
+    _, dt_c = o2.cfl(st2, o2.v0(st2))
+    assert dt_c < 0.2 * dt_b
+    # without bulk motion and with tiny shear the fargo dt is unchanged by it
+    w3 = _axisym_disk(W.CYL, 32, 12, 1, seed=3)
+    w3.nu = None
+    w3.cq = 0.0
+    st3 = w3.state
+    st3["vx"][:] = 0.0
+    st3["vx"] += 1e-3 * rng.normal(size=st3["vx"].shape)
+    o3 = oracle.Oracle(w3)
+    _, d1 = o3.cfl(st3, o3.v0(st3))
+    # solid-body rotation: v0/dX equal on every ring, so no shear either
+    st3["vx"][:, :w3.ny_t, :] += (7.0 * W.centres(w3.yf))[None, :, None]
+    _, d2 = o3.cfl(st3, o3.v0(st3))
+    assert abs(d1 - d2) < 1e-12 * d1
+
+
+def test_shear_limit_of_eq38_binds_when_sound_speed_vanishes():
+    w = _axisym_disk(W.CYL, 32, 8, 1, seed=3)
+    w.nu = None
+    w.cq = 0.0
+    w.cs = np.full_like(w.cs, 1e-12)
+    st = w.state
+    st["vy"][:] = 0.0
+    ym = W.centres(w.yf)
+    om = 2.0
+    st["vx"][:, :w.ny_t, :] = (om * ym ** 2)[None, :, None]    # v/dX = om r / dphi
+    o = oracle.Oracle(w)
+    _, dt = o.cfl(st, o.v0(st))
+    dphi = 2 * math.pi / w.nx
+    rates = om * ym / dphi
+    worst = np.max(np.abs(np.diff(rates[w.gy:w.gy + w.ny])))
+    assert abs(dt - w.cfl / worst) < 1e-12 * dt
+
+
+def test_nonfinite_state_is_reported():
+    w = W.sod(ny=32)
+    st = w.state
+    st["rho"][0, 5, 0] = float("nan")
+    o = oracle.Oracle(w)
+    rc, _ = o.cfl(st, o.v0(st))
+    assert rc == -4
+
+
+def test_new_velocities_recover_old_velocities_from_old_momenta():
+    """Below Eq. 18: applying Eq. 18 to the momenta of Eqs. 16-17 built from a
+    state returns that state's velocities (geometric factors of Tab. momenta)."""
+    for geom, dims in ((W.CART, (8, 6, 5)), (W.CYL, (8, 6, 5)), (W.SPH, (8, 6, 5))):
+        w = W.random_box(geom, *dims, g=2, seed=3, omega_f=0.7 if geom != W.CART else 0.0)
+        o = oracle.Oracle(w)
+        st = w.state
+        before = {k: v.copy() for k, v in st.items()}
+        pis = o.momenta(st)
+        o.new_velocities(st, pis)
+        for k in ("vx", "vy", "vz"):
+            a, b = w.active(st[k]), w.active(before[k])
+            assert np.max(np.abs(a - b)) < 1e-13 * max(1.0, np.max(np.abs(b))), (geom, k)
+
+
+@pytest.mark.parametrize("axis", ["y", "z"])
+def test_courant_one_sweep_along_y_and_z_is_exact_shift(axis):
+    n = 32
+    w = W.random_box(W.CART, 1, n if axis == "y" else 1, n if axis == "z" else 1, g=2, seed=0,
+                     iso=True, nu=0.0, planet=False, fargo=False)
+    w.cs = np.ones((w.nz_t, w.ny_t))
+    st = w.state
+    rng = np.random.default_rng(5)
+    st["rho"][:] = rng.uniform(1.0, 2.0, size=st["rho"].shape)
+    for k in ("vx", "vy", "vz"):
+        st[k][:] = 0.0
+    comp = "vy" if axis == "y" else "vz"
+    st[comp][:] = 0.25
+    o = oracle.Oracle(w)
+    pis = o.momenta(st)
+    rho0 = st["rho"].copy()
+    dt = (1.0 / n) / 0.25
+    (o.transport_y if axis == "y" else o.transport_z)(st, pis, dt)
+    a = w.active(st["rho"]).ravel()
+    b = (rho0[:, :, 0].ravel() if axis == "z" else rho0[0, :, 0])
+    g = w.g
+    b = b[g - 1:g - 1 + n] if axis == "y" else rho0[g - 1:g - 1 + n, 0, 0]
+    assert np.array_equal(a, b)
+
+
+def test_planet_potential_by_law_of_cosines():
+    """Star + Plummer-smoothed planet + indirect term at the planet phase
+    Omega_p t, Omega_p = sqrt((M+q)/a^3), computed by another route."""
+    w = W.disk2d(nx=16, ny=8, q=1e-3)
+    w.planet_a = 1.1
+    o = oracle.Oracle(w)
+    t = 0.77
+    phi = o.potential(t)
+    M, q, a, eps = 1.0, 1e-3, 1.1, w.planet_eps
+    php = math.sqrt((M + q) / a ** 3) * t
+    r = W.centres(w.yf)[None, :w.ny_t, None]
+    x = (w.xmin + (np.arange(w.nx) + 0.5) * (w.xmax - w.xmin) / w.nx)[None, None, :]
+    d2 = r * r + a * a - 2 * r * a * np.cos(x - php)
+    want = -M / r - q / np.sqrt(d2 + eps * eps) + q * r * np.cos(x - php) / (a * a)
+    assert np.max(np.abs(phi[:1, :w.ny_t] - want)) < 1e-13
+
+
+def test_zero_gradient_and_reflecting_ghosts():
+    w = W.random_box(W.CART, 4, 6, 5, g=2, seed=1, bc=W.BC_ZEROGRAD)
+    o = oracle.Oracle(w)
+    st = w.state
+    o.bc_fill(st)
+    g = w.g
+    assert np.array_equal(st["rho"][g:g + 5, 0], st["rho"][g:g + 5, g])
+    assert np.array_equal(st["rho"][g:g + 5, g + 6 + 1], st["rho"][g:g + 5, g + 5])
+    assert np.array_equal(st["vy"][g:g + 5, g], st["vy"][g:g + 5, g + 1])
+    w = W.random_box(W.CART, 4, 6, 5, g=2, seed=1, bc=W.BC_REFLECT)
+    st = w.state
+    oracle.Oracle(w).bc_fill(st)
+    nzt = w.nz_t     # plane nz_t is storage for v_z only
+    assert np.all(st["vy"][:nzt, g] == 0) and np.all(st["vy"][:nzt, g + 6] == 0)
+    assert np.array_equal(st["vy"][:nzt, g - 1], -st["vy"][:nzt, g + 1])
+    assert np.array_equal(st["rho"][:nzt, g - 2], st["rho"][:nzt, g + 1])
+    assert np.all(st["vz"][g, :w.ny_t] == 0) and np.all(st["vz"][g + 5, :w.ny_t] == 0)

@@ -1,0 +1,312 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module holds no arithmetic of the time step itself: it only builds mesh
+face coordinates and initial conditions (ICs) as plain FP64 NumPy arrays, plus
+the parameter records that describe each workload.  Both the CPU oracle and the
+CUDA library receive these arrays as *inputs*.
+
+Array layout (identical for every field, ghost cells included):
+    shape (nz_t + 1, ny_t + 1, nx), X fastest, where
+    ny_t = ny + 2*g if ny > 1 else 1   (ghost layers in Y only when Y is active)
+    nz_t = nz + 2*g if nz > 1 else 1
+The extra row (j = ny_t) and plane (k = nz_t) exist so that the face-centred
+v_y / v_z of the last ghost cell's upper face has storage (staggered mesh,
+Sec. 2.3: a vector component is stored on the lower face of its cell).
+
+Geometries follow the paper's axis naming (Tab. "corresp"): X = azimuth,
+Y = radius, Z = z (cylindrical) or colatitude (spherical).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+CART, CYL, SPH = 0, 1, 2
+BC_REFLECT, BC_FROZEN, BC_ZEROGRAD = 0, 1, 2
+FIELDS = ("rho", "e", "vx", "vy", "vz")
+
+
+@dataclasses.dataclass
+class Workload:
+    """Everything a run needs: mesh, physics switches, tables and ICs."""
+    name: str
+    geom: int
+    nx: int
+    ny: int
+    nz: int
+    g: int
+    xmin: float
+    xmax: float
+    yf: np.ndarray            # Y face coordinates, length ny_t + 1
+    zf: np.ndarray            # Z face coordinates, length nz_t + 1
+    gamma: float              # ratio of specific heats (adiabatic runs)
+    iso: bool                 # locally isothermal EOS, Eq. eos1
+    cs: Optional[np.ndarray]  # isothermal sound speed per ring, (nz_t, ny_t)
+    nu: Optional[np.ndarray]  # kinematic viscosity per ring, (nz_t, ny_t)
+    cfl: float
+    cq: float                 # artificial-viscosity coefficient C_q
+    fargo: bool
+    omega_f: float
+    bc_y: tuple
+    bc_z: tuple
+    star_mass: float
+    planet_q: float           # 0 = no planet
+    planet_a: float
+    planet_eps: float
+    indirect: bool
+    t0: float
+    t_end: float
+    state: dict               # field name -> (nz_t+1, ny_t+1, nx) float64
+    av_dt_literal: bool = False
+
+    @property
+    def ny_t(self):
+        return self.ny + 2 * self.g if self.ny > 1 else 1
+
+    @property
+    def nz_t(self):
+        return self.nz + 2 * self.g if self.nz > 1 else 1
+
+    @property
+    def shape(self):
+        return (self.nz_t + 1, self.ny_t + 1, self.nx)
+
+    @property
+    def gy(self):
+        return self.g if self.ny > 1 else 0
+
+    @property
+    def gz(self):
+        return self.g if self.nz > 1 else 0
+
+    def active(self, a):
+        """Active-cell view (nz, ny, nx) of a full field array."""
+        return a[self.gz:self.gz + self.nz, self.gy:self.gy + self.ny, :]
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz
+
+    def copy(self):
+        w = dataclasses.replace(self)
+        w.state = {k: v.copy() for k, v in self.state.items()}
+        return w
+
+
+def faces(n, g, lo, hi, log=False):
+    """Face coordinates of a 1D axis with n active cells and g ghosts per side."""
+    if n == 1:
+        return np.array([lo, hi], dtype=np.float64)
+    j = np.arange(-g, n + g + 1, dtype=np.float64)
+    if log:
+        return lo * np.exp(j * (math.log(hi / lo) / n))
+    return lo + j * ((hi - lo) / n)
+
+
+def centres(f):
+    return 0.5 * (f[:-1] + f[1:])
+
+
+def _empty(shape):
+    return {k: np.zeros(shape, dtype=np.float64) for k in FIELDS}
+
+
+def sod(ny=512, g=2, axis="y"):
+    """1D Sod shock tube (Sec. 5.1.1; parameters scaled to [0, 1], t = 0.2).
+
+    Left state rho = P = 1, right rho = 0.125, P = 0.1, gamma = 1.4, v = 0.
+    Run along Y with X and Z absent (one cell each); reflecting walls.
+    With axis="x" the tube lies along the periodic X axis instead (nx = ny).
+    """
+    gamma = 1.4
+    if axis == "y":
+        nx, nyy = 1, ny
+        yf = faces(ny, g, 0.0, 1.0)
+    else:
+        nx, nyy = ny, 1
+        yf = faces(1, g, 0.0, 1.0)
+    zf = faces(1, g, 0.0, 1.0)
+    w = Workload("sod", CART, nx, nyy, 1, g, 0.0, 1.0, yf, zf, gamma, False,
+                 None, None, 0.5, 1.41, False, 0.0,
+                 (BC_REFLECT, BC_REFLECT), (BC_REFLECT, BC_REFLECT),
+                 0.0, 0.0, 1.0, 0.0, False, 0.0, 0.2, {})
+    st = _empty(w.shape)
+    if axis == "y":
+        ym = centres(yf)[None, :, None]
+        left = np.broadcast_to(ym < 0.5, (w.nz_t, w.ny_t, 1))
+    else:
+        xc = (np.arange(nx) + 0.5) / nx
+        left = np.broadcast_to((xc < 0.5)[None, None, :], (w.nz_t, w.ny_t, nx))
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    st["rho"][:w.nz_t, :w.ny_t, :] = rho
+    st["e"][:w.nz_t, :w.ny_t, :] = p / (gamma - 1.0)
+    w.state = st
+    return w
+
+
+def disk2d(nx=768, ny=256, h=0.05, nu=1e-5, q=1e-3, g=3, sigma0=1e-3,
+           rmin=0.4, rmax=2.5, orbits=10.0, fargo=True, cq=1.41):
+    """2D cylindrical locally isothermal Keplerian disk with one planet.
+
+    Sigma = sigma0 r^-1/2, c_s = h r^-1/2, v_phi = sqrt((1 - 1.5 h^2)/r) (radial
+    balance of gravity, pressure and centrifugal force), v_r = 0.  Non-rotating
+    frame; planet on a circular orbit at a = 1, smoothing 0.6 H = 0.6 h a.
+    Radial ghosts are frozen to the initial equilibrium.
+    """
+    yf = faces(ny, g, rmin, rmax, log=True)
+    zf = faces(1, g, -0.5, 0.5)
+    w = Workload("disk2d", CYL, nx, ny, 1, g, -math.pi, math.pi, yf, zf, 1.4, True,
+                 None, None, 0.44, cq, fargo, 0.0,
+                 (BC_FROZEN, BC_FROZEN), (BC_FROZEN, BC_FROZEN),
+                 1.0, q, 1.0, 0.6 * h * 1.0, True, 0.0, orbits * 2.0 * math.pi, {})
+    ym = centres(yf)
+    cs = np.zeros((w.nz_t, w.ny_t))
+    cs[:, :] = h * ym ** -0.5
+    w.cs = cs
+    w.nu = np.full((w.nz_t, w.ny_t), nu) if nu > 0 else None
+    st = _empty(w.shape)
+    st["rho"][:w.nz_t, :w.ny_t, :] = (sigma0 * ym ** -0.5)[None, :, None]
+    st["vx"][:w.nz_t, :w.ny_t, :] = np.sqrt((1.0 - 1.5 * h * h) / ym)[None, :, None]
+    w.state = st
+    return w
+
+
+def disk3d(nx=1536, ny=512, nz=96, h=0.05, alpha=1e-3, q=3e-4, g=3, rho0=1e-3,
+           rmin=0.4, rmax=2.5, gamma=1.4, nsteps=200, fargo=True, cq=1.41):
+    """3D spherical adiabatic disk with one planet, vertically hydrostatic.
+
+    Isothermal on spheres at t = 0: c_s^2 = h^2/r, rho = rho0 r^-1.5
+    sin(theta)^(1/h^2 - 2.5), v_phi = sqrt((1 - 2.5 h^2)/r) (exact continuum
+    equilibrium of the r and theta balances), e = c_s^2 rho/(gamma - 1).
+    alpha viscosity nu = alpha c_s H = alpha h^2 r^(1/2), fixed in time.
+    Colatitude spans pi/2 +- 3.5 h.  Ghosts frozen in r and theta.
+    """
+    yf = faces(ny, g, rmin, rmax, log=True)
+    zf = faces(nz, g, 0.5 * math.pi - 3.5 * h, 0.5 * math.pi + 3.5 * h)
+    w = Workload("disk3d", SPH, nx, ny, nz, g, -math.pi, math.pi, yf, zf, gamma, False,
+                 None, None, 0.44, cq, fargo, 0.0,
+                 (BC_FROZEN, BC_FROZEN), (BC_FROZEN, BC_FROZEN),
+                 1.0, q, 1.0, 0.6 * h * 1.0, True, 0.0, 1e30, {})
+    w.nsteps = nsteps
+    ym = centres(yf)[None, :]
+    zm = centres(zf)[:, None]
+    w.nu = np.broadcast_to(alpha * h * h * np.sqrt(ym), (w.nz_t, w.ny_t)).copy() if alpha > 0 else None
+    st = _empty(w.shape)
+    rho = rho0 * ym ** -1.5 * np.sin(zm) ** (1.0 / (h * h) - 2.5)
+    st["rho"][:w.nz_t, :w.ny_t, :] = rho[:, :, None]
+    st["e"][:w.nz_t, :w.ny_t, :] = ((h * h / ym) * rho / (gamma - 1.0))[:, :, None]
+    st["vx"][:w.nz_t, :w.ny_t, :] = np.broadcast_to(np.sqrt((1.0 - 2.5 * h * h) / ym), (w.nz_t, w.ny_t))[:, :, None]
+    w.state = st
+    return w
+
+
+def batch_params(n=256, seed=1602):
+    """Parameter draws of the batched disk sweep (numpy PCG64, fixed seed).
+
+    Nr ~ U{128..512}, Nphi = 3 Nr, q log-uniform [1e-5, 1e-3], h uniform
+    [0.03, 0.07], nu log-uniform [1e-6, 1e-5].
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nr = rng.integers(128, 513, size=n)
+    q = 10.0 ** rng.uniform(-5.0, -3.0, size=n)
+    h = rng.uniform(0.03, 0.07, size=n)
+    nu = 10.0 ** rng.uniform(-6.0, -5.0, size=n)
+    return [dict(nx=int(3 * r), ny=int(r), q=float(a), h=float(b), nu=float(c))
+            for r, a, b, c in zip(nr, q, h, nu)]
+
+
+def batch_instance(p, orbits=500.0):
+    return disk2d(nx=p["nx"], ny=p["ny"], h=p["h"], nu=p["nu"], q=p["q"], orbits=orbits)
+
+
+def perturb(w, seed, amp=1e-2, fields=FIELDS):
+    """Add seeded multiplicative/additive noise to every cell (ghosts included).
+
+    Used to build generic, non-symmetric states for parity tests.  Density and
+    energy stay positive; velocities get an additive perturbation scaled by the
+    local sound-speed-like magnitude.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    st = w.state
+    for f in fields:
+        a = st[f]
+        if f in ("rho", "e"):
+            if np.any(a):
+                a *= 1.0 + amp * rng.uniform(-1.0, 1.0, size=a.shape)
+        else:
+            if w.nx == 1 and f == "vx" and w.geom == CART:
+                continue
+            if w.ny == 1 and f == "vy":
+                continue
+            if w.nz == 1 and f == "vz":
+                continue
+            scale = max(np.abs(a).max(), 1.0) if f != "vx" else 1.0
+            a += amp * scale * rng.uniform(-1.0, 1.0, size=a.shape) * (0.1 if f == "vx" else 1.0)
+    return w
+
+
+def random_box(geom, nx, ny, nz, g=3, seed=0, iso=False, nu=1e-3, planet=True,
+               fargo=True, bc=BC_FROZEN, cq=1.41, omega_f=0.0):
+    """A small generic mesh with a smooth random state, for sub-step parity.
+
+    Densities/energies ~ 1 with O(10%) structure; velocities O(0.1-1) with a
+    rotation-like v_x so that FARGO shifts are non-trivial.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if geom == CART:
+        yf = faces(ny, g, 0.0, 1.0)
+        zf = faces(nz, g, 0.0, 1.0)
+        xmin, xmax = 0.0, 1.0
+        star, pq = 0.0, 0.0
+    elif geom == CYL:
+        yf = faces(ny, g, 0.5, 1.5, log=True)
+        zf = faces(nz, g, -0.1, 0.1)
+        xmin, xmax = -math.pi, math.pi
+        star, pq = 1.0, (1e-3 if planet else 0.0)
+    else:
+        yf = faces(ny, g, 0.5, 1.5, log=True)
+        zf = faces(nz, g, 0.5 * math.pi - 0.2, 0.5 * math.pi + 0.2)
+        xmin, xmax = -math.pi, math.pi
+        star, pq = 1.0, (1e-3 if planet else 0.0)
+    w = Workload("box", geom, nx, ny, nz, g, xmin, xmax, yf, zf, 1.4, iso,
+                 None, None, 0.44, cq, fargo, omega_f, (bc, bc), (bc, bc),
+                 star, pq, 1.0, 0.05, True, 0.3, 1e30, {})
+    shp = w.shape
+    nzt, nyt = w.nz_t, w.ny_t
+    ym = centres(yf)
+    if iso:
+        w.cs = 0.05 + 0.05 * rng.uniform(size=(nzt, nyt))
+    if nu > 0:
+        w.nu = nu * (1.0 + 0.5 * rng.uniform(size=(nzt, nyt)))
+    st = _empty(shp)
+    x = 2 * math.pi * (np.arange(nx) + 0.5) / nx
+
+    def smooth(amp):
+        a = np.zeros(shp)
+        for _ in range(3):
+            kx = rng.integers(0, 3)
+            ph = rng.uniform(0, 2 * math.pi)
+            a += amp * rng.uniform(0.2, 1.0) * np.cos(kx * x + ph)[None, None, :] * \
+                rng.uniform(0.5, 1.0, size=(shp[0], shp[1], 1))
+        return a + amp * 0.3 * rng.uniform(-1, 1, size=shp)
+
+    st["rho"] = 1.0 + smooth(0.1)
+    st["rho"] = np.abs(st["rho"]) + 0.2
+    st["e"] = 2.0 + smooth(0.2)
+    st["e"] = np.abs(st["e"]) + 0.2
+    if geom == CART:
+        st["vx"] = 0.5 + smooth(0.2) if nx > 1 else np.zeros(shp)
+    else:
+        vk = np.zeros(shp)
+        vk[:, :nyt, :] = (ym[:nyt] ** -0.5)[None, :, None]
+        st["vx"] = vk + smooth(0.05)
+    st["vy"] = smooth(0.1) if ny > 1 else np.zeros(shp)
+    st["vz"] = smooth(0.1) if nz > 1 else np.zeros(shp)
+    if iso:
+        st["e"][:] = 0.0
+    w.state = st
+    return w
