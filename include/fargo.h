@@ -1,0 +1,168 @@
+/*
+ * fargo.h — C ABI of a B300 (sm_103a) implementation of one explicit
+ * hydrodynamic time step of the FARGO3D method (Benitez-Llambay & Masset
+ * 2016): Courant reduction, source sub-steps, dimensionally split van Leer
+ * transport with left/right momenta, and FARGO orbital advection.
+ *
+ * Conventions
+ *  - Every call returns FARGO_OK (0) or a negative FARGO_ERR_* code; no C++
+ *    exception crosses the ABI.  fargo_strerror() names a code.
+ *  - A context owns all device memory it allocates (state, scratch, tables).
+ *    Caller buffers are borrowed for the duration of a call only.
+ *  - Fields are stored in the context precision (FARGO_F64 -> double,
+ *    FARGO_F32 -> float).  Field arrays exchanged with the caller are dense,
+ *    X fastest, in the context precision:
+ *      region FARGO_ACTIVE: nz * ny * nx values (active cells only);
+ *      region FARGO_FULL  : (nz_t+1) * (ny_t+1) * nx values, ghosts included,
+ *        with ny_t = ny + 2*ghost when ny > 1 else 1 (nz_t likewise).  The
+ *        extra row / plane holds the face velocity v_y / v_z on the upper
+ *        face of the last ghost cell (staggered mesh, Sec. 2.3).
+ *    Scalars (density, energy) are cell centred; velocity component v_d sits
+ *    on the lower d-face of its cell.
+ *  - A context is thread-compatible, not thread-safe.  Work is queued on the
+ *    stream given at creation (NULL = the legacy default stream).
+ *  - Errors found on the device (non-finite state, Courant step not
+ *    positive) are latched in a device flag; the step that meets one leaves
+ *    the state unchanged and later calls that synchronise report the code.
+ */
+#ifndef FARGO_H
+#define FARGO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fargo_ctx fargo_ctx;
+
+/* Mesh geometries (Sec. 2.2, Tab. "corresp"): X = azimuth, Y = radius,
+ * Z = z (cylindrical) or colatitude (spherical). */
+enum { FARGO_CART = 0, FARGO_CYL = 1, FARGO_SPH = 2 };
+enum { FARGO_F64 = 0, FARGO_F32 = 1 };
+/* Y/Z boundary conditions (X is periodic, Sec. 3.4.1): reflecting wall,
+ * frozen ghosts (keep the values given), zero gradient. */
+enum { FARGO_BC_REFLECT = 0, FARGO_BC_FROZEN = 1, FARGO_BC_ZEROGRAD = 2 };
+enum { FARGO_RHO = 0, FARGO_ENERGY = 1, FARGO_VX = 2, FARGO_VY = 3, FARGO_VZ = 4 };
+enum { FARGO_ACTIVE = 0, FARGO_FULL = 1 };
+
+enum {
+    FARGO_OK = 0,
+    FARGO_ERR_BADARG = -1,        /* invalid argument or parameter */
+    FARGO_ERR_OOM = -2,           /* device or host allocation failed */
+    FARGO_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    FARGO_ERR_NONFINITE = -4,     /* NaN/Inf, rho <= 0 or e < 0 met by the Courant reduction */
+    FARGO_ERR_DT = -5,            /* Courant step not positive and finite */
+    FARGO_ERR_SIZE = -6,          /* buffer size mismatch or mesh beyond a kernel limit */
+    FARGO_ERR_BARRIER_TIMEOUT = -7,
+    FARGO_ERR_NOTBUILT = -8       /* CUDA device absent or kernel image missing */
+};
+
+/* Planet on a fixed circular orbit (Sec. 3.7, with the orbit fixed): mass
+ * ratio q, orbital radius a, Plummer smoothing length eps, indirect term on
+ * or off.  The planet phase is (Omega_p - Omega_f) t, Omega_p = sqrt((M+q)/a^3). */
+typedef struct {
+    double q, a, eps;
+    int indirect;
+} fargo_planet;
+
+/* Run parameters.  Host pointers are copied at creation. */
+typedef struct {
+    double xmin, xmax;          /* X extent; the azimuth spans 2 pi in cyl/sph */
+    const double *yfaces;       /* ny_t + 1 Y face coordinates (ghost faces included) */
+    const double *zfaces;       /* nz_t + 1 Z face coordinates */
+    const double *cs;           /* isothermal sound speed per ring, nz_t*ny_t (j fastest), Eq. eos1 */
+    const double *nu;           /* kinematic viscosity per ring, nz_t*ny_t, or NULL (App. B) */
+    double cfl;                 /* Courant number C of Eq. cfl2 (paper default 0.44) */
+    double cq;                  /* artificial-viscosity coefficient C_q (<= 0 disables it) */
+    int av_dt_literal;          /* 1: Courant AV term 4 sqrt2 |Delta/Delta v| as printed */
+    double omega_frame;         /* constant frame rotation Omega_f */
+    int fargo;                  /* 1: orbital advection (Sec. 3.4.1); 0: STANDARD transport */
+    int bc_y[2], bc_z[2];       /* lower / upper boundary condition per axis */
+    double star_mass;           /* central mass M (cyl/sph); 0 = none */
+    int precision;              /* FARGO_F64 or FARGO_F32 */
+    void *stream;               /* cudaStream_t, NULL = legacy default stream */
+} fargo_params;
+
+/* Create a context for an nx * ny * nz active mesh with `ghost` ghost layers
+ * in each active Y/Z direction (Sec. 4.1; >= 2).  gamma > 0 selects the
+ * adiabatic EOS P = (gamma-1) e (Eq. eos2); gamma <= 0 the locally isothermal
+ * P = cs^2 rho (Eq. eos1), which needs prm->cs.  planet may be NULL.
+ * Allocates every device buffer and uploads the 1D/2D geometry tables of
+ * Appendix A.  Fields start at zero.  Errors: BADARG, OOM, CUDA, NOTBUILT,
+ * SIZE (a ring does not fit the orbital-advection kernel's shared memory). */
+int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, int ghost,
+                 double gamma, const fargo_planet *planet, const fargo_params *prm);
+void fargo_destroy(fargo_ctx *ctx);
+
+/* Copy one field in or out (region FARGO_ACTIVE or FARGO_FULL, see above).
+ * `bytes` must equal the region's element count times the element size.
+ * on_device = 1: src/dst is a device pointer on the context's device.
+ * Synchronises the context stream.  Errors: BADARG, SIZE, CUDA. */
+int fargo_set_field(fargo_ctx *ctx, int field, int region, const void *src, size_t bytes, int on_device);
+int fargo_get_field(fargo_ctx *ctx, int field, int region, void *dst, size_t bytes, int on_device);
+
+/* Simulation time t (FP64, kept on the device) and the end time that clips
+ * the last Courant step (Sec. 3.4).  Setting t also clears the step counter
+ * and the latched error flag. */
+int fargo_set_time(fargo_ctx *ctx, double t, double t_end);
+
+/* One full update (flow chart Fig. 2, cells 2-12): queued on the context
+ * stream as one CUDA graph launch, no host synchronisation.  dt_out (may be
+ * NULL) receives the step taken, which synchronises.  A step after t has
+ * reached t_end does nothing.  Errors: CUDA, and when dt_out is given the
+ * latched NONFINITE / DT. */
+int fargo_step(fargo_ctx *ctx, double *dt_out);
+
+/* Steps with dt fixed by the caller (no Courant reduction; v0 is still
+ * computed).  Used to compare sub-domains at one common step. */
+int fargo_step_fixed(fargo_ctx *ctx, double dt);
+
+/* Advance until t = t_end (the last step lands on it) or max_steps steps,
+ * polling the device time every `poll` graph launches (>= 1).
+ * steps_done may be NULL.  Errors: CUDA, NONFINITE, DT. */
+int fargo_run_to(fargo_ctx *ctx, double t_end, long long max_steps, int poll, long long *steps_done);
+
+/* t, last dt, steps taken, latched error code (0 or FARGO_ERR_*). Synchronises. */
+int fargo_get_scalars(fargo_ctx *ctx, double *t, double *dt_last, long long *nsteps, int *err);
+
+/* Conserved totals over active cells with compensated FP64 sums:
+ * out[0] = sum rho V, out[1] = sum e V, out[2] = sum (Pi-_x + Pi+_x)/2 V
+ * (X momentum, angular momentum in cyl/sph; Eqs. 16-17, Tab. momenta).
+ * Synchronises. */
+int fargo_sums(fargo_ctx *ctx, double out[3]);
+
+/* Kernel-level access, for parity tests of single sub-steps.
+ * phase: 0 ghost fill, 1 v0 + Courant reduction (the caller's dt is
+ * ignored), 2 sub-step 1, 3 artificial viscosity + compression heating,
+ * 4 viscosity, 5 momenta + residual X sweep, 6 Y sweep, 7 Z sweep,
+ * 8 new velocities, 9 uniform orbital step (integer shift + PPA).
+ * Phases 2-9 use the given dt.  Results land in the state fields; phases
+ * 5-9 read and write the momenta, accessible with fargo_get_aux/set_aux;
+ * phases 5 and 9 read v0 (fargo_set_aux(6) or phase 1). */
+int fargo_debug_phase(fargo_ctx *ctx, int phase, double dt);
+
+/* Auxiliary arrays: which = 0..5 momenta Pi-_x, Pi+_x, Pi-_y, Pi+_y, Pi-_z,
+ * Pi+_z (FULL region, context precision); 6 = v0 per ring (nz_t*ny_t FP64).
+ * Host buffers.  Errors: BADARG, SIZE, CUDA. */
+int fargo_get_aux(fargo_ctx *ctx, int which, void *dst, size_t bytes);
+int fargo_set_aux(fargo_ctx *ctx, int which, const void *src, size_t bytes);
+
+/* One full update launched kernel by kernel with a CUDA event between
+ * launches on the context stream; ms[i] receives the device time of launch
+ * i and names[i] (may be NULL) a static string naming its kernel.  At most
+ * max_kernels entries; *n_out receives the count.  Synchronises. */
+int fargo_profile_step(fargo_ctx *ctx, int max_kernels, float *ms, int *n_out, const char **names);
+
+/* Use (1) or bypass (0) the CUDA graph for fargo_step (default 1). */
+int fargo_use_graph(fargo_ctx *ctx, int enable);
+
+/* Number of kernel launches one fargo_step queues (for accounting). */
+int fargo_launches_per_step(fargo_ctx *ctx);
+
+const char *fargo_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FARGO_H */

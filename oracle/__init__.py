@@ -73,6 +73,7 @@ def lib():
         PP6 = P * 6
         L.or_momenta.argtypes = [pp, ps, PP6]
         L.or_transport_x.argtypes = [pp, ps, PP6, P, C.c_double]
+        L.or_orbital_shift.argtypes = [pp, ps, PP6, P, C.c_double]
         L.or_transport_y.argtypes = [pp, ps, PP6, C.c_double]
         L.or_transport_z.argtypes = [pp, ps, PP6, C.c_double]
         L.or_new_velocities.argtypes = [pp, ps, PP6]
@@ -178,6 +179,10 @@ class Oracle:
     def transport_x(self, st, pis, v0, dt):
         v0 = np.ascontiguousarray(v0, dtype=np.float64)
         lib().or_transport_x(C.byref(self.p), C.byref(self._state(st)), self._pis(pis), _ptr(v0), dt)
+
+    def orbital_shift(self, st, pis, v0, dt):
+        v0 = np.ascontiguousarray(v0, dtype=np.float64)
+        lib().or_orbital_shift(C.byref(self.p), C.byref(self._state(st)), self._pis(pis), _ptr(v0), dt)
 
     def transport_y(self, st, pis, dt):
         lib().or_transport_y(C.byref(self.p), C.byref(self._state(st)), self._pis(pis), dt)

@@ -990,11 +990,11 @@ static int gather_quantities(const mesh *m, or_state *s, double *pi[6], double *
 }
 
 /* ------------------------------------------------------------------------ */
-/* Cells 12b-c along X with orbital advection (Sec. 3.4.1): residual         */
-/* transport at delta v = v - v0 (Eq. fargo1) with van Leer interface values,*/
-/* then the integer shift by N = E(v0 dt / dX) (Eqs. 29-32), then the        */
-/* uniform fractional step at v_shift^R (Eqs. 31, 33) with PPA interface     */
-/* values.  The X length of ring (j,k) is R dx.  Active rings only.          */
+/* ------------------------------------------------------------------------ */
+/* Cells 12b-c along X, residual part (Sec. 3.4.1, Eq. fargo1): upwind       */
+/* transport at delta v = v - v0 with van Leer interface values (Eq. 15).    */
+/* With FARGO off, v0 = 0 and this is the whole STANDARD X transport.        */
+/* The X length of ring (j,k) is R dx.  Active rings only.                   */
 /* ------------------------------------------------------------------------ */
 void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double *v0, double dt)
 {
@@ -1007,13 +1007,12 @@ void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double
     double **lq = malloc(sizeof(double *) * nq);
     for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
     double *cen = zalloc(n), *wid = zalloc(n), *vel = zalloc(n), *area = zalloc(n), *vinv = zalloc(n);
-    double *ring = zalloc(nx), *fs = zalloc(nx);
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++) {
             double dX = len_x(&m, j, k);
             double vr0 = p->fargo ? v0[(size_t)k * m.nyt + j] : 0.0;
             double S = area_x(&m, j, k), Vi = inv_vol(&m, j, k);
-            /* (i) residual velocity sweep on a ring padded by periodic images */
+            /* the ring padded by two periodic images on each side */
             for (int c = 0; c < n; c++) {
                 int i = ((c - 2) % nx + nx) % nx;
                 cen[c] = c * dX; wid[c] = dX; area[c] = S; vinv[c] = Vi;
@@ -1024,8 +1023,35 @@ void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double
             sweep_line(&L, 2, nx + 2, dt);
             for (int q = 0; q < nq; q++)
                 for (int i = 0; i < nx; i++) fld[q][IDX(&m, i, j, k)] = lq[q][i + 2];
-            if (!p->fargo) continue;
-            /* (ii) integer shift */
+        }
+    for (int q = 0; q < nq; q++) free(lq[q]);
+    free(lq); free(cen); free(wid); free(vel); free(area); free(vinv);
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uniform orbital step of each ring (Sec. 3.4.1, Eqs. fargo2, 28-33): the   */
+/* integer shift by N = E(v0 dt / dX) (Eq. 32), then the fractional step at  */
+/* xi = v0 dt/dX - N with PPA interface values (Eqs. 34-36).  Reading: this  */
+/* uniform step is split off and applied after the Y and Z sweeps, so that   */
+/* the radial and vertical fluxes move each cell's content with the face     */
+/* velocities of the same azimuth; applied before them, the multi-cell shift */
+/* decorrelates the two and the scheme is unstable at C = 0.44.              */
+/* ------------------------------------------------------------------------ */
+void or_orbital_shift(const or_params *p, or_state *s, double *pi[6], const double *v0, double dt)
+{
+    mesh m;
+    mesh_init(&m, p);
+    if (!m.hasX || !p->fargo) { mesh_free(&m); return; }
+    double *fld[8];
+    int nq = gather_quantities(&m, s, pi, fld);
+    int nx = m.nx;
+    double *ring = zalloc(nx), *fs = zalloc(nx);
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++) {
+            double dX = len_x(&m, j, k);
+            double vr0 = v0[(size_t)k * m.nyt + j];
+            double S = area_x(&m, j, k), Vi = inv_vol(&m, j, k);
             double X = vr0 * dt / dX;
             long long N = or_nearest_int(X);
             double xs = X - (double)N;
@@ -1034,7 +1060,6 @@ void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double
                 or_shift_ring(nx, ring, N);
                 for (int i = 0; i < nx; i++) fld[q][IDX(&m, i, j, k)] = ring[i];
             }
-            /* (iii) uniform fractional step with PPA interface values */
             if (xs == 0.0) continue;
             double vR = xs * dX / dt;
             double *flux0 = zalloc(nx + 1), **fl = malloc(sizeof(double *) * nq);
@@ -1055,8 +1080,7 @@ void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double
             }
             free(fl); free(flux0);
         }
-    for (int q = 0; q < nq; q++) free(lq[q]);
-    free(lq); free(cen); free(wid); free(vel); free(area); free(vinv); free(ring); free(fs);
+    free(ring); free(fs);
     mesh_free(&m);
 }
 
@@ -1196,6 +1220,7 @@ int or_step(const or_params *p, or_state *s, double t, double t_end, double dt_f
     or_transport_x(p, s, pi, v0, dt);                     /* cells 12b-c */
     or_transport_y(p, s, pi, dt);
     or_transport_z(p, s, pi, dt);
+    or_orbital_shift(p, s, pi, v0, dt);
     or_new_velocities(p, s, pi);                          /* cell 12d */
     for (int q = 0; q < 6; q++) free(pi[q]);
     free(phi); free(v0);

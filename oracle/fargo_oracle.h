@@ -54,6 +54,7 @@ void or_compression_heating(const or_params *p, or_state *s, double dt);
 void or_viscosity(const or_params *p, or_state *s, double dt);
 void or_momenta(const or_params *p, const or_state *s, double *pi[6]);
 void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double *v0, double dt);
+void or_orbital_shift(const or_params *p, or_state *s, double *pi[6], const double *v0, double dt);
 void or_transport_y(const or_params *p, or_state *s, double *pi[6], double dt);
 void or_transport_z(const or_params *p, or_state *s, double *pi[6], double dt);
 void or_new_velocities(const or_params *p, or_state *s, double *pi[6]);

@@ -1,0 +1,235 @@
+"""Python binding of the B300 FARGO3D hydro step (C ABI in include/fargo.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of libfargo_b300.so.  There is no CPU fallback; a missing library or device
+raises.  PyTorch, when used, only provides device buffers and the stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libfargo_b300.so")
+
+CART, CYL, SPH = 0, 1, 2
+F64, F32 = 0, 1
+RHO, ENERGY, VX, VY, VZ = range(5)
+ACTIVE, FULL = 0, 1
+FIELD_IDS = {"rho": RHO, "e": ENERGY, "vx": VX, "vy": VY, "vz": VZ}
+
+ERRORS = {0: "ok", -1: "BADARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "DT", -6: "SIZE",
+          -7: "BARRIER_TIMEOUT", -8: "NOTBUILT"}
+
+EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field", "fargo_set_time",
+            "fargo_step", "fargo_step_fixed", "fargo_run_to", "fargo_get_scalars", "fargo_sums",
+            "fargo_debug_phase", "fargo_get_aux", "fargo_set_aux", "fargo_use_graph",
+            "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step")
+
+PD = C.POINTER(C.c_double)
+
+
+class FargoError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({code})")
+
+
+class Planet(C.Structure):
+    _fields_ = [("q", C.c_double), ("a", C.c_double), ("eps", C.c_double), ("indirect", C.c_int)]
+
+
+class Params(C.Structure):
+    _fields_ = [("xmin", C.c_double), ("xmax", C.c_double), ("yfaces", PD), ("zfaces", PD),
+                ("cs", PD), ("nu", PD), ("cfl", C.c_double), ("cq", C.c_double),
+                ("av_dt_literal", C.c_int), ("omega_frame", C.c_double), ("fargo", C.c_int),
+                ("bc_y", C.c_int * 2), ("bc_z", C.c_int * 2), ("star_mass", C.c_double),
+                ("precision", C.c_int), ("stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libfargo_b300.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"{LIBPATH} is missing: run `python -m paper_1602_02359_b300.build`")
+        L = C.CDLL(LIBPATH)
+        vp = C.c_void_p
+        L.fargo_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                   C.POINTER(Planet), C.POINTER(Params)]
+        L.fargo_destroy.argtypes = [vp]
+        L.fargo_destroy.restype = None
+        L.fargo_set_field.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+        L.fargo_get_field.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+        L.fargo_set_time.argtypes = [vp, C.c_double, C.c_double]
+        L.fargo_step.argtypes = [vp, PD]
+        L.fargo_step_fixed.argtypes = [vp, C.c_double]
+        L.fargo_run_to.argtypes = [vp, C.c_double, C.c_longlong, C.c_int, C.POINTER(C.c_longlong)]
+        L.fargo_get_scalars.argtypes = [vp, PD, PD, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+        L.fargo_sums.argtypes = [vp, PD]
+        L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
+        L.fargo_get_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
+        L.fargo_set_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
+        L.fargo_use_graph.argtypes = [vp, C.c_int]
+        L.fargo_launches_per_step.argtypes = [vp]
+        L.fargo_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_char_p)]
+        L.fargo_strerror.argtypes = [C.c_int]
+        L.fargo_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise FargoError(rc, where)
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(PD)
+
+
+class Fargo:
+    """One simulation context on the current CUDA device.
+
+    `w` carries the mesh and physics parameters (see workloads.Workload:
+    geom, nx, ny, nz, g, xmin, xmax, yf, zf, gamma, iso, cs, nu, cfl, cq,
+    fargo, omega_f, bc_y, bc_z, star_mass, planet_*).
+    """
+
+    def __init__(self, w, precision=F64, stream=None):
+        L = lib()
+        self.w = w
+        self.prec = precision
+        self.dtype = np.float64 if precision == F64 else np.float32
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None
+                      for a in (w.yf, w.zf, w.cs, w.nu)]
+        yf, zf, cs, nu = self._keep
+        p = Params()
+        p.xmin, p.xmax = w.xmin, w.xmax
+        p.yfaces, p.zfaces = _dptr(yf), _dptr(zf)
+        p.cs = _dptr(cs) if (w.iso and cs is not None) else None
+        p.nu = _dptr(nu) if nu is not None else None
+        p.cfl, p.cq = w.cfl, w.cq
+        p.av_dt_literal = int(getattr(w, "av_dt_literal", False))
+        p.omega_frame = w.omega_f
+        p.fargo = int(w.fargo)
+        p.bc_y[0], p.bc_y[1] = w.bc_y
+        p.bc_z[0], p.bc_z[1] = w.bc_z
+        p.star_mass = w.star_mass
+        p.precision = precision
+        p.stream = stream
+        pl = Planet(w.planet_q, w.planet_a, w.planet_eps, int(w.indirect))
+        h = C.c_void_p()
+        gamma = -1.0 if w.iso else w.gamma
+        _check(L.fargo_create(C.byref(h), w.geom, w.nx, w.ny, w.nz, w.g, gamma,
+                              C.byref(pl) if w.planet_q > 0 else None, C.byref(p)), "fargo_create")
+        self.h = h
+        self.shape = w.shape
+        self.active_shape = (w.nz, w.ny, w.nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fargo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- fields
+    def set_field(self, name, a, region=FULL):
+        if hasattr(a, "data_ptr"):      # torch tensor on the device
+            _check(lib().fargo_set_field(self.h, FIELD_IDS[name], region, C.c_void_p(a.data_ptr()),
+                                         a.numel() * a.element_size(), 1), "fargo_set_field")
+            return
+        a = np.ascontiguousarray(a, dtype=self.dtype)
+        _check(lib().fargo_set_field(self.h, FIELD_IDS[name], region, a.ctypes.data, a.nbytes, 0),
+               "fargo_set_field")
+
+    def get_field(self, name, region=FULL, out=None):
+        if out is not None and hasattr(out, "data_ptr"):
+            _check(lib().fargo_get_field(self.h, FIELD_IDS[name], region, C.c_void_p(out.data_ptr()),
+                                         out.numel() * out.element_size(), 1), "fargo_get_field")
+            return out
+        shp = self.shape if region == FULL else self.active_shape
+        a = np.empty(shp, dtype=self.dtype) if out is None else out
+        _check(lib().fargo_get_field(self.h, FIELD_IDS[name], region, a.ctypes.data, a.nbytes, 0),
+               "fargo_get_field")
+        return a
+
+    def set_state(self, st, region=FULL):
+        for k in ("rho", "e", "vx", "vy", "vz"):
+            self.set_field(k, st[k], region)
+
+    def get_state(self, region=FULL):
+        return {k: self.get_field(k, region) for k in ("rho", "e", "vx", "vy", "vz")}
+
+    # ---- time stepping
+    def set_time(self, t, t_end=1e300):
+        _check(lib().fargo_set_time(self.h, t, t_end), "fargo_set_time")
+
+    def step(self, want_dt=True):
+        if want_dt:
+            dt = C.c_double()
+            _check(lib().fargo_step(self.h, C.byref(dt)), "fargo_step")
+            return dt.value
+        _check(lib().fargo_step(self.h, None), "fargo_step")
+        return None
+
+    def step_fixed(self, dt):
+        _check(lib().fargo_step_fixed(self.h, dt), "fargo_step_fixed")
+
+    def run_to(self, t_end, max_steps=10 ** 12, poll=64):
+        n = C.c_longlong()
+        _check(lib().fargo_run_to(self.h, t_end, max_steps, poll, C.byref(n)), "fargo_run_to")
+        return n.value
+
+    def scalars(self):
+        t, dt, n, e = C.c_double(), C.c_double(), C.c_longlong(), C.c_int()
+        _check(lib().fargo_get_scalars(self.h, C.byref(t), C.byref(dt), C.byref(n), C.byref(e)),
+               "fargo_get_scalars")
+        return t.value, dt.value, n.value, e.value
+
+    def sums(self):
+        out = (C.c_double * 3)()
+        _check(lib().fargo_sums(self.h, out), "fargo_sums")
+        return tuple(out)
+
+    def debug_phase(self, phase, dt=0.0):
+        _check(lib().fargo_debug_phase(self.h, phase, dt), f"fargo_debug_phase({phase})")
+
+    def get_aux(self, which):
+        if which == 6:
+            a = np.empty((self.w.nz_t, self.w.ny_t), dtype=np.float64)
+        else:
+            a = np.empty(self.shape, dtype=self.dtype)
+        _check(lib().fargo_get_aux(self.h, which, a.ctypes.data, a.nbytes), "fargo_get_aux")
+        return a
+
+    def set_aux(self, which, a):
+        a = np.ascontiguousarray(a, dtype=np.float64 if which == 6 else self.dtype)
+        _check(lib().fargo_set_aux(self.h, which, a.ctypes.data, a.nbytes), "fargo_set_aux")
+
+    def profile_step(self):
+        """One step launched kernel by kernel; returns [(kernel, ms), ...]."""
+        ms = (C.c_float * 32)()
+        names = (C.c_char_p * 32)()
+        n = C.c_int()
+        _check(lib().fargo_profile_step(self.h, 32, ms, C.byref(n), names), "fargo_profile_step")
+        return [(names[i].decode(), ms[i]) for i in range(n.value)]
+
+    def use_graph(self, on=True):
+        _check(lib().fargo_use_graph(self.h, int(on)), "fargo_use_graph")
+
+    def launches_per_step(self):
+        return lib().fargo_launches_per_step(self.h)

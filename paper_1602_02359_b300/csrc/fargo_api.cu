@@ -1,0 +1,916 @@
+// C ABI of the B300 hydro step: context, geometry tables, step driver and
+// CUDA-graph capture.  See include/fargo.h for the contract of each call.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/fargo.h"
+#include "fargo_internal.cuh"
+#include "kernels_bc_cfl.cuh"
+#include "kernels_source.cuh"
+#include "kernels_transport.cuh"
+
+using namespace fk;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+};
+
+template <typename T>
+struct Buffers {
+    Fld<T> A{};                 // state: rho, e, vx, vy, vz
+    T *vB[3] = {nullptr, nullptr, nullptr};
+    T *piA[6] = {}, *piB[6] = {};
+    T *rhoB = nullptr, *eB = nullptr;
+    Tab<T> tab{};
+};
+
+struct HostGeom {
+    // FP64 tables, computed with the same expressions as a plain evaluation
+    std::vector<double> ym, dy, zm, dz, dyc, lx, ly, lz, dmin, R, zc, vol, fz, dzc;
+    std::vector<double> sx, vinv, sy, sz, lenz, gphy, gphz, cosx, sinx, cs, nu;
+    std::vector<double> rma, fra, z2, qar;
+};
+
+}  // namespace
+
+struct fargo_ctx {
+    int prec;  // FARGO_F64 / FARGO_F32
+    MeshD m{};
+    int nx, ny, nz, g, geom;
+    int nyt, nzt, pitch;
+    size_t esz;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Scal *sc = nullptr;
+    double *v0 = nullptr, *part = nullptr, *part2 = nullptr, *sums = nullptr, *vol = nullptr;
+    float *ringmax = nullptr;
+    int nrings_active = 0, cfl_blocks = 0, sum_blocks = 0;
+    Buffers<double> b64;
+    Buffers<float> b32;
+    std::vector<void *> allocs;
+    HostGeom hg;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    int launches = 0;
+    size_t tx_smem = 0;
+    int tx_threads = 256;
+    std::vector<double> yfaces_store, zfaces_store;
+};
+
+static const char *g_errstr[] = {"ok", "bad argument", "out of memory", "CUDA error", "non-finite state",
+                                 "Courant step not positive", "size mismatch or kernel limit", "barrier timeout",
+                                 "CUDA device or kernel image unavailable"};
+
+extern "C" const char *fargo_strerror(int code)
+{
+    if (code > 0 || code < -8) return "unknown error";
+    return g_errstr[-code];
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            fprintf(stderr, "fargo: %s failed: %s\n", #call, cudaGetErrorString(e_));           \
+            return e_ == cudaErrorMemoryAllocation ? FARGO_ERR_OOM : FARGO_ERR_CUDA;              \
+        }                                                                                        \
+    } while (0)
+
+static int dalloc(fargo_ctx *c, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? FARGO_ERR_OOM : FARGO_ERR_CUDA;
+    }
+    c->allocs.push_back(*p);
+    e = cudaMemsetAsync(*p, 0, bytes < 16 ? 16 : bytes, c->stream);
+    return e == cudaSuccess ? FARGO_OK : FARGO_ERR_CUDA;
+}
+
+template <typename T>
+static int upload(fargo_ctx *c, const T **dst, const std::vector<double> &src)
+{
+    std::vector<T> h(src.size() ? src.size() : 1);
+    for (size_t i = 0; i < src.size(); i++) h[i] = (T)src[i];
+    void *p;
+    int rc = dalloc(c, &p, h.size() * sizeof(T));
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *dst = (const T *)p;
+    return FARGO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of Appendix A (Tab. "geom", Eqs. 70-71), built in FP64 on the host.
+// ---------------------------------------------------------------------------
+static void build_geometry(fargo_ctx *c, const fargo_params *p, double gamma, const fargo_planet *pl)
+{
+    HostGeom &h = c->hg;
+    const int nx = c->nx, nyt = c->nyt, nzt = c->nzt, geom = c->geom;
+    const double *yf = p->yfaces, *zf = p->zfaces;
+    const double dx = (p->xmax - p->xmin) / nx;
+    const bool hasX = nx > 1, hasY = c->ny > 1, hasZ = c->nz > 1;
+    h.ym.assign(nyt + 1, 0.0); h.dy.assign(nyt + 1, 0.0); h.dyc.assign(nyt + 1, 0.0);
+    h.zm.assign(nzt + 1, 0.0); h.dz.assign(nzt + 1, 0.0);
+    for (int j = 0; j < nyt; j++) {
+        h.ym[j] = 0.5 * (yf[j] + yf[j + 1]);
+        h.dy[j] = yf[j + 1] - yf[j];
+    }
+    for (int j = 1; j < nyt; j++) h.dyc[j] = h.ym[j] - h.ym[j - 1];
+    for (int k = 0; k < nzt; k++) {
+        h.zm[k] = 0.5 * (zf[k] + zf[k + 1]);
+        h.dz[k] = zf[k + 1] - zf[k];
+    }
+    const size_t nr = (size_t)nzt * nyt, nf = (size_t)(nzt + 1) * (nyt + 1);
+    h.lx.assign(nr, 0); h.ly.assign(nr, 0); h.lz.assign(nr, 0); h.dmin.assign(nr, 0); h.R.assign(nr, 0);
+    h.zc.assign(nr, 0); h.vol.assign(nr, 0); h.fz.assign(nr, 0); h.dzc.assign(nr, 0); h.sx.assign(nr, 0);
+    h.vinv.assign(nr, 0); h.lenz.assign(nr, 0); h.gphy.assign(nr, 0); h.gphz.assign(nr, 0);
+    h.cs.assign(nr, 0); h.nu.assign(nr, 0);
+    h.rma.assign(nr, 0); h.fra.assign(nr, 0); h.z2.assign(nr, 0); h.qar.assign(nr, 0);
+    h.sy.assign(nf, 0); h.sz.assign(nf, 0);
+    auto syk = [&](int k) {
+        if (geom == FARGO_CYL) return zf[k + 1] - zf[k];
+        if (geom == FARGO_SPH) return cos(zf[k]) - cos(zf[k + 1]);
+        return dx * (zf[k + 1] - zf[k]);
+    };
+    auto syj = [&](int j) {
+        if (geom == FARGO_CYL) return yf[j] * dx;
+        if (geom == FARGO_SPH) return yf[j] * yf[j] * dx;
+        return 1.0;
+    };
+    auto szj = [&](int j) {
+        if (geom == FARGO_CART) return dx * (yf[j + 1] - yf[j]);
+        return 0.5 * dx * (yf[j + 1] * yf[j + 1] - yf[j] * yf[j]);
+    };
+    auto szk = [&](int k) { return geom == FARGO_SPH ? sin(zf[k]) : 1.0; };
+    auto sxj = [&](int j) {
+        if (geom == FARGO_SPH) return 0.5 * (yf[j + 1] * yf[j + 1] - yf[j] * yf[j]);
+        return yf[j + 1] - yf[j];
+    };
+    auto vjinv = [&](int j) {
+        if (geom == FARGO_CYL) return 2.0 / ((yf[j + 1] * yf[j + 1] - yf[j] * yf[j]) * dx);
+        if (geom == FARGO_SPH) return 3.0 / ((yf[j + 1] * yf[j + 1] * yf[j + 1] - yf[j] * yf[j] * yf[j]) * dx);
+        return 1.0 / (yf[j + 1] - yf[j]);
+    };
+    const double M = p->star_mass;
+    auto phis = [&](int j, int k) {
+        if (M <= 0.0 || geom == FARGO_CART) return 0.0;
+        if (geom == FARGO_CYL) return -M / sqrt(h.ym[j] * h.ym[j] + h.zm[k] * h.zm[k]);
+        return -M / h.ym[j];
+    };
+    for (int k = 0; k < nzt; k++)
+        for (int j = 0; j < nyt; j++) {
+            const size_t r = (size_t)k * nyt + j;
+            double R = 1.0;
+            if (geom == FARGO_CYL) R = h.ym[j];
+            else if (geom == FARGO_SPH) R = h.ym[j] * sin(h.zm[k]);
+            h.R[r] = R;
+            h.lx[r] = R * dx;
+            h.ly[r] = h.dy[j];
+            h.lz[r] = geom == FARGO_SPH ? h.ym[j] * h.dz[k] : h.dz[k];
+            double dmin = INFINITY;
+            if (hasX && h.lx[r] < dmin) dmin = h.lx[r];
+            if (hasY && h.ly[r] < dmin) dmin = h.ly[r];
+            if (hasZ && h.lz[r] < dmin) dmin = h.lz[r];
+            h.dmin[r] = dmin;
+            h.lenz[r] = h.lz[r];
+            h.zc[r] = geom == FARGO_SPH ? h.ym[j] * cos(h.zm[k]) : h.zm[k];
+            h.fz[r] = geom == FARGO_SPH ? h.ym[j] : 1.0;
+            if (k > 0) h.dzc[r] = geom == FARGO_SPH ? h.ym[j] * (h.zm[k] - h.zm[k - 1]) : h.zm[k] - h.zm[k - 1];
+            h.sx[r] = sxj(j) * (zf[k + 1] - zf[k]);
+            h.vinv[r] = vjinv(j) / syk(k);
+            h.vol[r] = 1.0 / h.vinv[r];
+            if (j > 0) h.gphy[r] = (phis(j, k) - phis(j - 1, k)) / h.dyc[j];
+            if (k > 0) h.gphz[r] = (phis(j, k) - phis(j, k - 1)) / h.dzc[r];
+            if (p->cs) h.cs[r] = p->cs[r];
+            if (p->nu) h.nu[r] = p->nu[r];
+            if (pl && pl->q > 0.0) {
+                h.rma[r] = R - pl->a;
+                h.fra[r] = 4.0 * R * pl->a;
+                h.z2[r] = h.zc[r] * h.zc[r];
+                h.qar[r] = pl->q / (pl->a * pl->a) * R;
+            }
+        }
+    for (int k = 0; k <= nzt; k++)
+        for (int j = 0; j <= nyt; j++) {
+            const size_t f = (size_t)k * (nyt + 1) + j;
+            if (k < nzt) h.sy[f] = syj(j) * syk(k);
+            if (j < nyt) h.sz[f] = szj(j) * szk(k);
+        }
+    h.cosx.assign(nx, 0);
+    h.sinx.assign(nx, 0);
+    for (int i = 0; i < nx; i++) {
+        const double x = p->xmin + (i + 0.5) * dx;
+        h.cosx[i] = cos(x);
+        h.sinx[i] = sin(x);
+    }
+    MeshD &m = c->m;
+    m.dx = dx;
+    m.xmin = p->xmin;
+    (void)gamma;
+}
+
+template <typename T>
+static int build_tables(fargo_ctx *c, Tab<T> &t)
+{
+    HostGeom &h = c->hg;
+    const int nyt = c->nyt, nzt = c->nzt;
+    int rc;
+#define UP(dst, src) \
+    if ((rc = upload<T>(c, &t.dst, src))) return rc
+#define UPD(dst, src) \
+    if ((rc = upload<double>(c, &t.dst, src))) return rc
+    std::vector<double> szm(nzt + 1, 0), szf(nzt + 1, 0), cotzm(nzt + 1, 0), cotzf(nzt + 1, 0), zf(nzt + 1, 0),
+        yf(nyt + 1, 0);
+    for (int k = 0; k <= nzt; k++) {
+        zf[k] = c->zfaces_store[k];
+        szf[k] = sin(zf[k]);
+        cotzf[k] = cos(zf[k]) / sin(zf[k]);
+        if (k < nzt) {
+            szm[k] = sin(h.zm[k]);
+            cotzm[k] = cos(h.zm[k]) / sin(h.zm[k]);
+        }
+    }
+    for (int j = 0; j <= nyt; j++) yf[j] = c->yfaces_store[j];
+    UP(ym, h.ym); UP(dy, h.dy); UP(yf, yf); UP(dyc, h.dyc);
+    UP(zm, h.zm); UP(dz, h.dz); UP(zf, zf); UP(szm, szm); UP(szf, szf); UP(cotzm, cotzm); UP(cotzf, cotzf);
+    UP(R, h.R); UP(lenx, h.lx); UP(lenz, h.lenz); UP(dzc, h.dzc); UP(sx, h.sx); UP(vinv, h.vinv);
+    UP(cs, h.cs); UP(nu, h.nu); UP(gphy, h.gphy); UP(gphz, h.gphz); UP(fz, h.fz);
+    UP(sy, h.sy); UP(sz, h.sz);
+    UPD(lx, h.lx); UPD(ly, h.ly); UPD(lz, h.lz); UPD(dmin, h.dmin); UPD(csd, h.cs); UPD(nud, h.nu);
+    UPD(Rd, h.R); UPD(zcd, h.zc); UPD(cosx, h.cosx); UPD(sinx, h.sinx);
+    UP(rma, h.rma); UP(fra, h.fra); UP(z2, h.z2); UP(qar, h.qar);
+    {
+        void *q;
+        if ((rc = dalloc(c, &q, sizeof(T) * c->nx))) return rc;
+        t.ps = (T *)q;
+        if ((rc = dalloc(c, &q, sizeof(T) * c->nx))) return rc;
+        t.pc = (T *)q;
+    }
+#undef UP
+#undef UPD
+    return FARGO_OK;
+}
+
+template <typename T>
+static int alloc_fields(fargo_ctx *c, Buffers<T> &b)
+{
+    const size_t n = (size_t)c->m.ntot * sizeof(T);
+    void *p;
+    int rc;
+    T **slots[] = {&b.A.rho, &b.A.e, &b.A.vx, &b.A.vy, &b.A.vz, &b.vB[0], &b.vB[1], &b.vB[2], &b.rhoB, &b.eB};
+    for (T **s : slots) {
+        if ((rc = dalloc(c, &p, n))) return rc;
+        *s = (T *)p;
+    }
+    for (int q = 0; q < 6; q++) {
+        if ((rc = dalloc(c, &p, n))) return rc;
+        b.piA[q] = (T *)p;
+        if ((rc = dalloc(c, &p, n))) return rc;
+        b.piB[q] = (T *)p;
+    }
+    return build_tables<T>(c, b.tab);
+}
+
+// Quantity sets (Sec. 3.2): rho, e (adiabatic), Pi-/+ of each active direction.
+template <typename T>
+static QSet<T> qset(const fargo_ctx *c, T *rho, T *e, T *const *pi)
+{
+    QSet<T> s{};
+    int n = 0;
+    s.q[n++] = rho;
+    if (!c->m.iso) s.q[n++] = e;
+    s.q[n++] = pi[0];
+    s.q[n++] = pi[1];
+    if (c->m.hasY) {
+        s.q[n++] = pi[2];
+        s.q[n++] = pi[3];
+    }
+    if (c->m.hasZ) {
+        s.q[n++] = pi[4];
+        s.q[n++] = pi[5];
+    }
+    s.nq = n;
+    return s;
+}
+
+static unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ---------------------------------------------------------------------------
+// The launch sequence of one full update (flow chart cells 2-12).
+// Velocity buffers ping-pong A -> B -> A (-> B); the Y and Z sweeps are
+// out of place, and the X sweep is in place or not so that the last sweep
+// lands in the state buffers.
+// ---------------------------------------------------------------------------
+// Optional per-launch event marks (fargo_profile_step).
+struct Prof {
+    cudaEvent_t ev[32];
+    const char *name[32];
+    int n;
+};
+
+template <typename T>
+static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
+{
+    const MeshD &m = c->m;
+    cudaStream_t s = c->stream;
+    const int bs = 256;
+    const long long ncell = (long long)m.nx * (m.nyt + 1) * (m.nzt + 1);
+    int nl = 0;
+#define MARK(nm)                                                    \
+    do {                                                            \
+        if (prof) {                                                 \
+            prof->name[nl] = nm;                                    \
+            cudaEventRecord(prof->ev[nl + 1], s);                   \
+        }                                                           \
+        nl++;                                                       \
+    } while (0)
+    Fld<T> A = b.A;
+    Fld<T> VB = {A.rho, A.e, b.vB[0], b.vB[1], b.vB[2]};
+    // cell 2
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 0); MARK("bc_y"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 0); MARK("bc_z"); }
+    // cells 3-6
+    k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
+                                                  c->nrings_active);
+    MARK("cfl_screen");
+    k_cfl_exact<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc, c->nrings_active);
+    MARK("cfl_exact");
+    // cell 7
+    k_substep1<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc); MARK("substep1");
+    k_artvisc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, VB, A, c->sc); MARK("artvisc");
+    Fld<T> vsrc = A;
+    if (m.has_nu) {
+        k_visc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc); MARK("visc");
+        vsrc = VB;
+    }
+    // cell 9
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, vsrc, c->sc, 1); MARK("bc_y9"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, vsrc, c->sc, 1); MARK("bc_z9"); }
+    // cell 12
+    QSet<T> qa = qset<T>(c, A.rho, A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);
+    const int nyz = m.hasY + m.hasZ;
+    const bool x_out = (nyz % 2) == 1;
+    Fld<T> tx_in = {A.rho, A.e, vsrc.vx, vsrc.vy, vsrc.vz};
+    k_transport_x<T><<<m.nyt * m.nzt, c->tx_threads, c->tx_smem, s>>>(m, b.tab, tx_in, x_out ? qb : qa, c->v0, c->sc);
+    MARK("transport_x");
+    QSet<T> cur = x_out ? qb : qa, oth = x_out ? qa : qb;
+    const long long nc = (long long)m.nx * m.nyt * m.nzt;
+    if (m.hasY) {
+        k_transport_yz<T, 1><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, cur, oth, vsrc.vy, c->sc, m.hasZ ? 1 : 0);
+        MARK("transport_y");
+        QSet<T> t = cur; cur = oth; oth = t;
+    }
+    if (m.hasZ) {
+        k_transport_yz<T, 2><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, cur, oth, vsrc.vz, c->sc, 0);
+        MARK("transport_z");
+        QSet<T> t = cur; cur = oth; oth = t;
+    }
+    // cur is the state quantity set again (qa); the uniform orbital step comes last
+    if (m.fargo && m.hasX) {
+        k_orbital<T><<<c->nrings_active, c->tx_threads, c->tx_smem, s>>>(m, b.tab, cur, c->v0, c->sc);
+        MARK("orbital");
+    }
+    k_newvel<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, cur, vsrc, A, c->sc, 0); MARK("newvel");
+#undef MARK
+    c->launches = nl;
+    if (prof) prof->n = nl;
+    CK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+static int enqueue(fargo_ctx *c)
+{
+    return c->prec == FARGO_F64 ? enqueue_step<double>(c, c->b64) : enqueue_step<float>(c, c->b32);
+}
+
+static int launch_step(fargo_ctx *c)
+{
+    if (!c->use_graph) return enqueue(c);
+    if (!c->gexec) {
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue(c);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc) return rc;
+        if (e != cudaSuccess) return FARGO_ERR_CUDA;
+        c->graph = g;
+        CK(cudaGraphInstantiate(&c->gexec, g, 0));
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    return FARGO_OK;
+}
+
+template <typename T>
+static int set_kernel_attrs(fargo_ctx *c)
+{
+    int dev;
+    CK(cudaGetDevice(&dev));
+    int maxsm = 0;
+    CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
+    nq -= 0;
+    size_t smem = (size_t)(nq + 5) * c->nx * sizeof(T);
+    if (smem > (size_t)maxsm) return FARGO_ERR_SIZE;
+    c->tx_smem = smem;
+    c->tx_threads = c->nx >= 1024 ? 512 : 256;
+    CK(cudaFuncSetAttribute(k_transport_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(k_orbital<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, int ghost, double gamma,
+                            const fargo_planet *planet, const fargo_params *prm)
+{
+    if (!out || !prm) return FARGO_ERR_BADARG;
+    *out = nullptr;
+    if (geom < 0 || geom > 2 || nx < 1 || ny < 1 || nz < 1) return FARGO_ERR_BADARG;
+    if ((ny > 1 || nz > 1) && ghost < 2) return FARGO_ERR_BADARG;
+    if (!prm->yfaces || !prm->zfaces || !(prm->xmax > prm->xmin)) return FARGO_ERR_BADARG;
+    if (prm->precision != FARGO_F64 && prm->precision != FARGO_F32) return FARGO_ERR_BADARG;
+    if (gamma <= 0.0 && !prm->cs) return FARGO_ERR_BADARG;
+    if (!(prm->cfl > 0.0)) return FARGO_ERR_BADARG;
+    for (int s = 0; s < 2; s++)
+        if (prm->bc_y[s] < 0 || prm->bc_y[s] > 2 || prm->bc_z[s] < 0 || prm->bc_z[s] > 2) return FARGO_ERR_BADARG;
+    if (planet && planet->q > 0.0 && !(planet->a > 0.0)) return FARGO_ERR_BADARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return FARGO_ERR_NOTBUILT;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_cfl_exact<double>) != cudaSuccess) return FARGO_ERR_NOTBUILT;
+
+    fargo_ctx *c = new fargo_ctx();
+    c->prec = prm->precision;
+    c->nx = nx; c->ny = ny; c->nz = nz; c->g = ghost; c->geom = geom;
+    c->nyt = ny > 1 ? ny + 2 * ghost : 1;
+    c->nzt = nz > 1 ? nz + 2 * ghost : 1;
+    c->pitch = (nx + 31) / 32 * 32;
+    c->esz = c->prec == FARGO_F64 ? 8 : 4;
+    c->yfaces_store.assign(prm->yfaces, prm->yfaces + c->nyt + 1);
+    c->zfaces_store.assign(prm->zfaces, prm->zfaces + c->nzt + 1);
+    if (prm->stream) {
+        c->stream = (cudaStream_t)prm->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return FARGO_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    MeshD &m = c->m;
+    m.nx = nx; m.nyt = c->nyt; m.nzt = c->nzt;
+    m.gy = ny > 1 ? ghost : 0; m.gz = nz > 1 ? ghost : 0; m.g = ghost;
+    m.j0 = m.gy; m.j1 = m.gy + ny; m.k0 = m.gz; m.k1 = m.gz + nz;
+    m.hasX = nx > 1; m.hasY = ny > 1; m.hasZ = nz > 1;
+    m.geom = geom;
+    m.iso = gamma <= 0.0;
+    m.fargo = prm->fargo ? 1 : 0;
+    m.av_lit = prm->av_dt_literal ? 1 : 0;
+    m.has_nu = prm->nu ? 1 : 0;
+    m.has_planet = planet && planet->q > 0.0;
+    m.indirect = m.has_planet && planet->indirect;
+    m.has_star = prm->star_mass > 0.0 && geom != FARGO_CART;
+    for (int s = 0; s < 2; s++) { m.bcy[s] = prm->bc_y[s]; m.bcz[s] = prm->bc_z[s]; }
+    m.sj = c->pitch;
+    m.sk = (long long)(c->nyt + 1) * c->pitch;
+    m.ntot = (long long)(c->nzt + 1) * m.sk;
+    m.gamma = gamma > 0.0 ? gamma : 1.0;
+    m.g1 = m.gamma * (m.gamma - 1.0);
+    m.cq = prm->cq;
+    m.cfl = prm->cfl;
+    m.omega = prm->omega_frame;
+    m.av_c2 = 4.0 * sqrt(2.0);
+    if (m.has_planet) {
+        m.pq = planet->q; m.pa = planet->a; m.pa3 = planet->a * planet->a * planet->a;
+        m.peps = planet->eps; m.peps2 = planet->eps * planet->eps;
+        const double om = sqrt((prm->star_mass + planet->q) / (planet->a * planet->a * planet->a));
+        m.om_rel = om - prm->omega_frame;
+    }
+    fargo_params p2 = *prm;
+    p2.yfaces = c->yfaces_store.data();
+    p2.zfaces = c->zfaces_store.data();
+    build_geometry(c, &p2, gamma, planet);
+    int rc = FARGO_OK;
+    void *p;
+    if ((rc = dalloc(c, &p, sizeof(Scal)))) goto fail;
+    c->sc = (Scal *)p;
+    c->nrings_active = ny * nz;
+    c->cfl_blocks = (c->nrings_active + 7) / 8;
+    if ((rc = dalloc(c, &p, sizeof(double) * (size_t)c->nyt * c->nzt))) goto fail;
+    c->v0 = (double *)p;
+    if ((rc = dalloc(c, &p, sizeof(double) * c->cfl_blocks))) goto fail;
+    c->part = (double *)p;
+    if ((rc = dalloc(c, &p, sizeof(float) * c->nrings_active))) goto fail;
+    c->ringmax = (float *)p;
+    c->sum_blocks = 4 * 148;
+    if ((rc = dalloc(c, &p, sizeof(double) * 6 * c->sum_blocks))) goto fail;
+    c->part2 = (double *)p;
+    if ((rc = dalloc(c, &p, sizeof(double) * 4))) goto fail;
+    c->sums = (double *)p;
+    if ((rc = upload<double>(c, (const double **)&c->vol, c->hg.vol))) goto fail;
+    if (c->prec == FARGO_F64) {
+        if ((rc = alloc_fields<double>(c, c->b64))) goto fail;
+        if ((rc = set_kernel_attrs<double>(c))) goto fail;
+    } else {
+        if ((rc = alloc_fields<float>(c, c->b32))) goto fail;
+        if ((rc = set_kernel_attrs<float>(c))) goto fail;
+    }
+    {
+        Scal s0{};
+        s0.t = 0.0;
+        s0.t_end = 1e300;
+        if (cudaMemcpyAsync(c->sc, &s0, sizeof(Scal), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            rc = FARGO_ERR_CUDA;
+            goto fail;
+        }
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) { rc = FARGO_ERR_CUDA; goto fail; }
+    *out = c;
+    return FARGO_OK;
+fail:
+    fargo_destroy(c);
+    return rc;
+}
+
+extern "C" void fargo_destroy(fargo_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// pointer of a state field
+static void *field_ptr(fargo_ctx *c, int field)
+{
+    if (c->prec == FARGO_F64) {
+        Fld<double> &A = c->b64.A;
+        void *p[5] = {A.rho, A.e, A.vx, A.vy, A.vz};
+        return p[field];
+    }
+    Fld<float> &A = c->b32.A;
+    void *p[5] = {A.rho, A.e, A.vx, A.vy, A.vz};
+    return p[field];
+}
+
+static int copy_region(fargo_ctx *c, void *dev, void *host, int region, size_t bytes, int to_dev)
+{
+    const size_t es = c->esz;
+    const size_t pitchb = (size_t)c->pitch * es, rowb = (size_t)c->nx * es;
+    cudaMemcpyKind kind = cudaMemcpyDefault;
+    if (region == FARGO_FULL) {
+        const size_t rows = (size_t)(c->nzt + 1) * (c->nyt + 1);
+        if (bytes != rows * rowb) return FARGO_ERR_SIZE;
+        if (to_dev) CK(cudaMemcpy2DAsync(dev, pitchb, host, rowb, rowb, rows, kind, c->stream));
+        else CK(cudaMemcpy2DAsync(host, rowb, dev, pitchb, rowb, rows, kind, c->stream));
+    } else if (region == FARGO_ACTIVE) {
+        if (bytes != (size_t)c->nx * c->ny * c->nz * es) return FARGO_ERR_SIZE;
+        const int gy = c->m.gy, gz = c->m.gz;
+        for (int k = 0; k < c->nz; k++) {
+            char *d = (char *)dev + ((size_t)(k + gz) * c->m.sk + (size_t)gy * c->pitch) * es;
+            char *h = (char *)host + (size_t)k * c->ny * rowb;
+            if (to_dev) CK(cudaMemcpy2DAsync(d, pitchb, h, rowb, rowb, c->ny, kind, c->stream));
+            else CK(cudaMemcpy2DAsync(h, rowb, d, pitchb, rowb, c->ny, kind, c->stream));
+        }
+    } else {
+        return FARGO_ERR_BADARG;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_set_field(fargo_ctx *c, int field, int region, const void *src, size_t bytes, int on_device)
+{
+    (void)on_device;
+    if (!c || !src || field < 0 || field > 4) return FARGO_ERR_BADARG;
+    return copy_region(c, field_ptr(c, field), (void *)src, region, bytes, 1);
+}
+
+extern "C" int fargo_get_field(fargo_ctx *c, int field, int region, void *dst, size_t bytes, int on_device)
+{
+    (void)on_device;
+    if (!c || !dst || field < 0 || field > 4) return FARGO_ERR_BADARG;
+    return copy_region(c, field_ptr(c, field), dst, region, bytes, 0);
+}
+
+static int read_scal(fargo_ctx *c, Scal *s)
+{
+    CK(cudaMemcpyAsync(s, c->sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+static int err_code(int flags)
+{
+    if (flags & 1) return FARGO_ERR_NONFINITE;
+    if (flags & 2) return FARGO_ERR_DT;
+    return FARGO_OK;
+}
+
+extern "C" int fargo_set_time(fargo_ctx *c, double t, double t_end)
+{
+    if (!c || !(t_end >= t)) return FARGO_ERR_BADARG;
+    Scal s;
+    int rc = read_scal(c, &s);
+    if (rc) return rc;
+    s.t = t;
+    s.t_end = t_end;
+    s.nstep = 0;
+    s.err = 0;
+    s.fixed = 0;
+    s.counter = 0;
+    s.counter2 = 0;
+    CK(cudaMemcpyAsync(c->sc, &s, sizeof(Scal), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_get_scalars(fargo_ctx *c, double *t, double *dt_last, long long *nsteps, int *err)
+{
+    if (!c) return FARGO_ERR_BADARG;
+    Scal s;
+    int rc = read_scal(c, &s);
+    if (rc) return rc;
+    if (t) *t = s.t;
+    if (dt_last) *dt_last = s.dt;
+    if (nsteps) *nsteps = s.nstep;
+    if (err) *err = err_code(s.err);
+    return FARGO_OK;
+}
+
+extern "C" int fargo_step(fargo_ctx *c, double *dt_out)
+{
+    if (!c) return FARGO_ERR_BADARG;
+    int rc = launch_step(c);
+    if (rc) return rc;
+    if (dt_out) {
+        Scal s;
+        if ((rc = read_scal(c, &s))) return rc;
+        *dt_out = s.dt;
+        return err_code(s.err);
+    }
+    return FARGO_OK;
+}
+
+static int set_fixed(fargo_ctx *c, int fixed, double dt)
+{
+    // fixed and dt_fixed are adjacent ints/doubles of Scal; write the fields one by one
+    CK(cudaMemcpyAsync(&c->sc->fixed, &fixed, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&c->sc->dt_fixed, &dt, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_step_fixed(fargo_ctx *c, double dt)
+{
+    if (!c || !(dt > 0.0)) return FARGO_ERR_BADARG;
+    int rc = set_fixed(c, 1, dt);
+    if (rc) return rc;
+    rc = launch_step(c);
+    int rc2 = set_fixed(c, 0, 0.0);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    Scal s;
+    if ((rc = read_scal(c, &s))) return rc;
+    return err_code(s.err);
+}
+
+extern "C" int fargo_run_to(fargo_ctx *c, double t_end, long long max_steps, int poll, long long *steps_done)
+{
+    if (!c || poll < 1) return FARGO_ERR_BADARG;
+    Scal s;
+    int rc = read_scal(c, &s);
+    if (rc) return rc;
+    s.t_end = t_end;
+    CK(cudaMemcpyAsync(&c->sc->t_end, &s.t_end, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const long long n0 = s.nstep;
+    long long launched = 0;
+    while (launched < max_steps) {
+        const long long k = max_steps - launched < poll ? max_steps - launched : poll;
+        for (long long q = 0; q < k; q++)
+            if ((rc = launch_step(c))) return rc;
+        launched += k;
+        if ((rc = read_scal(c, &s))) return rc;
+        if (s.err || s.t >= t_end) break;
+    }
+    if (steps_done) *steps_done = s.nstep - n0;
+    return err_code(s.err);
+}
+
+template <typename T>
+static int sums_impl(fargo_ctx *c, Buffers<T> &b, double out[3])
+{
+    k_sums<T><<<c->sum_blocks, 256, 0, c->stream>>>(c->m, b.tab, b.A, c->vol, c->part2, c->sc, c->sums);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, c->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_sums(fargo_ctx *c, double out[3])
+{
+    if (!c || !out) return FARGO_ERR_BADARG;
+    return c->prec == FARGO_F64 ? sums_impl<double>(c, c->b64, out) : sums_impl<float>(c, c->b32, out);
+}
+
+// ---------------------------------------------------------------------------
+// Single sub-steps for kernel-level parity tests.
+// ---------------------------------------------------------------------------
+template <typename T>
+static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
+{
+    const MeshD &m = c->m;
+    cudaStream_t s = c->stream;
+    const int bs = 256;
+    const long long ncell = (long long)m.nx * (m.nyt + 1) * (m.nzt + 1);
+    const long long nc = (long long)m.nx * m.nyt * m.nzt;
+    const size_t nbytes = (size_t)m.ntot * sizeof(T);
+    Fld<T> A = b.A;
+    Fld<T> VB = {A.rho, A.e, b.vB[0], b.vB[1], b.vB[2]};
+    QSet<T> qa = qset<T>(c, A.rho, A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);
+    Scal sh;
+    int rc = read_scal(c, &sh);
+    if (rc) return rc;
+    sh.dt = dt;
+    sh.err = 0;
+    sh.fixed = phase == 1 ? 0 : 1;
+    sh.dt_fixed = dt;
+    sh.counter = 0;
+    if (m.has_planet) {
+        const double ph = m.om_rel * sh.t;
+        sh.xp = m.pa * cos(ph);
+        sh.yp = m.pa * sin(ph);
+    }
+    CK(cudaMemcpyAsync(c->sc, &sh, sizeof(Scal), cudaMemcpyHostToDevice, s));
+    auto copyv = [&](T *const *dst, T *const *src) -> int {
+        for (int q = 0; q < 3; q++) CK(cudaMemcpyAsync(dst[q], src[q], nbytes, cudaMemcpyDeviceToDevice, s));
+        return FARGO_OK;
+    };
+    T *va[3] = {A.vx, A.vy, A.vz};
+    switch (phase) {
+    case 0:
+        if (m.hasY) k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1);
+        if (m.hasZ) k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1);
+        break;
+    case 1:
+        k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
+                                                      c->nrings_active);
+        k_cfl_exact<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
+                                                     c->nrings_active);
+        break;
+    case 2:
+        k_substep1<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc);
+        if ((rc = copyv(va, b.vB))) return rc;
+        break;
+    case 3:
+        if ((rc = copyv(b.vB, va))) return rc;
+        k_artvisc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, VB, A, c->sc);
+        break;
+    case 4:
+        if (!m.has_nu) break;
+        k_visc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc);
+        if ((rc = copyv(va, b.vB))) return rc;
+        break;
+    case 5:
+        k_transport_x<T><<<m.nyt * m.nzt, c->tx_threads, c->tx_smem, s>>>(m, b.tab, A, qa, c->v0, c->sc);
+        break;
+    case 6:
+    case 7: {
+        if ((phase == 6 && !m.hasY) || (phase == 7 && !m.hasZ)) break;
+        if (phase == 6) k_transport_yz<T, 1><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, qa, qb, A.vy, c->sc, 1);
+        else k_transport_yz<T, 2><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, qa, qb, A.vz, c->sc, 1);
+        for (int q = 0; q < qa.nq; q++) CK(cudaMemcpyAsync(qa.q[q], qb.q[q], nbytes, cudaMemcpyDeviceToDevice, s));
+        break;
+    }
+    case 8:
+        k_newvel<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
+        break;
+    case 9:
+        if (m.fargo && m.hasX)
+            k_orbital<T><<<c->nrings_active, c->tx_threads, c->tx_smem, s>>>(m, b.tab, qa, c->v0, c->sc);
+        break;
+    default:
+        return FARGO_ERR_BADARG;
+    }
+    CK(cudaGetLastError());
+    // restore time and flags (phase 8 advances t)
+    Scal s2;
+    if ((rc = read_scal(c, &s2))) return rc;
+    if (phase != 1) {
+        s2.t = sh.t;
+        s2.nstep = sh.nstep;
+    }
+    s2.fixed = 0;
+    CK(cudaMemcpyAsync(c->sc, &s2, sizeof(Scal), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return err_code(s2.err);
+}
+
+extern "C" int fargo_debug_phase(fargo_ctx *c, int phase, double dt)
+{
+    if (!c) return FARGO_ERR_BADARG;
+    if (phase != 0 && phase != 1 && !(dt > 0.0)) return FARGO_ERR_BADARG;
+    if (phase == 0 || phase == 1) dt = dt > 0.0 ? dt : 1.0;
+    return c->prec == FARGO_F64 ? debug_impl<double>(c, c->b64, phase, dt) : debug_impl<float>(c, c->b32, phase, dt);
+}
+
+static int aux_ptr(fargo_ctx *c, int which, void **p, size_t *bytes, int *pitched)
+{
+    if (which >= 0 && which < 6) {
+        *p = c->prec == FARGO_F64 ? (void *)c->b64.piA[which] : (void *)c->b32.piA[which];
+        *bytes = (size_t)(c->nzt + 1) * (c->nyt + 1) * c->nx * c->esz;
+        *pitched = 1;
+        return FARGO_OK;
+    }
+    if (which == 6) {
+        *p = c->v0;
+        *bytes = (size_t)c->nzt * c->nyt * sizeof(double);
+        *pitched = 0;
+        return FARGO_OK;
+    }
+    return FARGO_ERR_BADARG;
+}
+
+extern "C" int fargo_get_aux(fargo_ctx *c, int which, void *dst, size_t bytes)
+{
+    if (!c || !dst) return FARGO_ERR_BADARG;
+    void *p;
+    size_t want;
+    int pitched;
+    int rc = aux_ptr(c, which, &p, &want, &pitched);
+    if (rc) return rc;
+    if (bytes != want) return FARGO_ERR_SIZE;
+    if (pitched) return copy_region(c, p, dst, FARGO_FULL, bytes, 0);
+    CK(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_set_aux(fargo_ctx *c, int which, const void *src, size_t bytes)
+{
+    if (!c || !src) return FARGO_ERR_BADARG;
+    void *p;
+    size_t want;
+    int pitched;
+    int rc = aux_ptr(c, which, &p, &want, &pitched);
+    if (rc) return rc;
+    if (bytes != want) return FARGO_ERR_SIZE;
+    if (pitched) return copy_region(c, p, (void *)src, FARGO_FULL, bytes, 1);
+    CK(cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_profile_step(fargo_ctx *c, int max_kernels, float *ms, int *n_out, const char **names)
+{
+    if (!c || !ms || !n_out || max_kernels < 1) return FARGO_ERR_BADARG;
+    Prof prof{};
+    for (int i = 0; i < 32; i++) CK(cudaEventCreate(&prof.ev[i]));
+    CK(cudaEventRecord(prof.ev[0], c->stream));
+    int rc = c->prec == FARGO_F64 ? enqueue_step<double>(c, c->b64, &prof) : enqueue_step<float>(c, c->b32, &prof);
+    if (rc == FARGO_OK) {
+        CK(cudaStreamSynchronize(c->stream));
+        const int n = prof.n < max_kernels ? prof.n : max_kernels;
+        for (int i = 0; i < n; i++) {
+            CK(cudaEventElapsedTime(&ms[i], prof.ev[i], prof.ev[i + 1]));
+            if (names) names[i] = prof.name[i];
+        }
+        *n_out = n;
+    }
+    for (int i = 0; i < 32; i++) cudaEventDestroy(prof.ev[i]);
+    return rc;
+}
+
+extern "C" int fargo_use_graph(fargo_ctx *c, int enable)
+{
+    if (!c) return FARGO_ERR_BADARG;
+    c->use_graph = enable != 0;
+    return FARGO_OK;
+}
+
+extern "C" int fargo_launches_per_step(fargo_ctx *c)
+{
+    if (!c) return FARGO_ERR_BADARG;
+    int n = 0;
+    const MeshD &m = c->m;
+    n += m.hasY + m.hasZ;        // cell 2
+    n += 2;                      // Courant (screen + exact)
+    n += 2 + (m.has_nu ? 1 : 0); // sources
+    n += m.hasY + m.hasZ;        // cell 9
+    n += 1 + m.hasY + m.hasZ;    // sweeps
+    n += (m.fargo && m.hasX) ? 1 : 0;  // orbital step
+    n += 1;                      // new velocities
+    return n;
+}

@@ -1,0 +1,68 @@
+// Device-side data structures shared by the kernels of the hydro step.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fk {
+
+enum { CART = 0, CYL = 1, SPH = 2 };
+enum { BC_REFLECT = 0, BC_FROZEN = 1, BC_ZEROGRAD = 2 };
+
+// Mesh description and run constants, passed by value to every kernel.
+struct MeshD {
+    int nx, nyt, nzt, gy, gz, j0, j1, k0, k1, g;
+    int hasX, hasY, hasZ, geom, iso, fargo, av_lit, has_nu, has_planet, indirect, has_star;
+    int bcy[2], bcz[2];
+    long long sj, sk, ntot;      // row pitch, plane stride, elements per field
+    double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
+};
+
+// Geometry tables (Appendix A) in the field precision T, plus the FP64
+// tables that the Courant reduction and the orbital advection need bit for bit.
+template <typename T>
+struct Tab {
+    // per Y index j (nyt + 1 entries)
+    const T *ym, *dy, *yf, *dyc;
+    // per Z index k (nzt + 1 entries)
+    const T *zm, *dz, *zf, *szm, *szf, *cotzm, *cotzf;
+    // per ring (j,k): index k * nyt + j
+    const T *R, *lenx, *lenz, *dzc, *sx, *vinv, *cs, *nu, *gphy, *gphz, *fz;
+    // per face (j,k): index k * (nyt + 1) + j
+    const T *sy, *sz;
+    // FP64 per ring
+    const double *lx, *ly, *lz, *dmin, *csd, *nud, *Rd, *zcd;
+    // FP64 per azimuthal index i: cos and sin of the cell-centre azimuth
+    const double *cosx, *sinx;
+    // planet: per ring R - a, 4 R a, Z^2 and (q/a^2) R (the indirect term's
+    // coefficient); per azimuth, rewritten every step, sin^2(dphi/2) and
+    // cos(dphi) of the offset to the planet
+    const T *rma, *fra, *z2, *qar;
+    T *ps, *pc;
+};
+
+template <typename T>
+struct Fld {
+    T *rho, *e, *vx, *vy, *vz;
+};
+
+// Up to eight transported quantities: rho, e, Pi-x, Pi+x, Pi-y, Pi+y, Pi-z, Pi+z.
+template <typename T>
+struct QSet {
+    T *q[8];
+    int nq;
+};
+
+// Device scalars of the run.  `counter` serves the last-block reductions.
+struct Scal {
+    double t, t_end, dt, xp, yp, dt_fixed, m32, wsh;
+    long long nstep;
+    int err, fixed;
+    unsigned int counter, counter2;
+};
+
+__device__ __forceinline__ long long IX(const MeshD &m, int i, int j, int k)
+{
+    return (long long)k * m.sk + (long long)j * m.sj + i;
+}
+
+}  // namespace fk

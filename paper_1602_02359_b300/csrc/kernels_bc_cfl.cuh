@@ -1,0 +1,374 @@
+// Ghost fill (flow-chart cells 2 and 9) and the Courant reduction (cells 3-6).
+#pragma once
+#include "fargo_internal.cuh"
+
+namespace fk {
+
+// ---------------------------------------------------------------------------
+// Ghost fill.  Reflecting walls mirror scalars and tangential velocities and
+// set the wall-normal face velocity to zero with odd mirroring beyond; frozen
+// ghosts keep their values; zero gradient copies the last active cell (and
+// the first interior normal face).  One thread per (i, transverse index,
+// side).  mode 0 = cell 2 (skipped once the run is done or failed),
+// mode 1 = cell 9 (skipped when the current step is void).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void fill_line(T *a, long long base, long long stride, int lo, int hi, int g, int normal, int side,
+                          int bc)
+{
+    if (bc == BC_FROZEN) return;
+    if (!normal) {
+        for (int mm = 0; mm < g; mm++) {
+            int dst = side == 0 ? lo - 1 - mm : hi + mm;
+            int src = bc == BC_REFLECT ? (side == 0 ? lo + mm : hi - 1 - mm) : (side == 0 ? lo : hi - 1);
+            a[base + dst * stride] = a[base + src * stride];
+        }
+    } else if (bc == BC_REFLECT) {
+        int w = side == 0 ? lo : hi;
+        a[base + w * stride] = T(0);
+        for (int mm = 1; mm <= g; mm++) {
+            if (side == 0) a[base + (w - mm) * stride] = -a[base + (w + mm) * stride];
+            else a[base + (w + mm) * stride] = -a[base + (w - mm) * stride];
+        }
+    } else {
+        if (side == 0) {
+            T v = a[base + (lo + 1) * stride];
+            for (int mm = 0; mm <= g; mm++) a[base + (lo - mm) * stride] = v;
+        } else {
+            T v = a[base + (hi - 1) * stride];
+            for (int mm = 0; mm <= g; mm++) a[base + (hi + mm) * stride] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ bool bc_skip(const Scal *sc, int mode)
+{
+    if (mode == 0) return sc->err != 0 || (!sc->fixed && sc->t >= sc->t_end);
+    return !(sc->dt > 0.0);
+}
+
+template <typename T>
+__global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)m.nx * (m.nzt + 1) * 2;
+    if (tid >= n || bc_skip(sc, mode)) return;
+    int i = (int)(tid % m.nx);
+    long long r = tid / m.nx;
+    int k = (int)(r % (m.nzt + 1));
+    int side = (int)(r / (m.nzt + 1));
+    int bc = m.bcy[side];
+    T *fl[5] = {f.rho, m.iso ? nullptr : f.e, f.vx, f.vy, f.vz};
+    for (int q = 0; q < 5; q++) {
+        if (!fl[q]) continue;
+        if (q == 4 && !m.hasZ) continue;
+        int kmax = q == 4 ? m.nzt + 1 : m.nzt;
+        if (k >= kmax) continue;
+        fill_line(fl[q], (long long)k * m.sk + i, m.sj, m.j0, m.j1, m.g, q == 3, side, bc);
+    }
+}
+
+template <typename T>
+__global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)m.nx * (m.nyt + 1) * 2;
+    if (tid >= n || bc_skip(sc, mode)) return;
+    int i = (int)(tid % m.nx);
+    long long r = tid / m.nx;
+    int j = (int)(r % (m.nyt + 1));
+    int side = (int)(r / (m.nyt + 1));
+    int bc = m.bcz[side];
+    T *fl[5] = {f.rho, m.iso ? nullptr : f.e, f.vx, f.vy, f.vz};
+    for (int q = 0; q < 5; q++) {
+        if (!fl[q]) continue;
+        if (q == 3 && !m.hasY) continue;
+        int jmax = q == 3 ? m.nyt + 1 : m.nyt;
+        if (j >= jmax) continue;
+        fill_line(fl[q], (long long)j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Courant reduction, Eq. cfl2 with the items of Sec. 3.4 and the FARGO
+// amendments of Sec. 3.4.2, in two launches.
+//
+// Per active cell s = sum_i (Delta t_i)^-2 (four rates, summed in the order
+// 1..4); the step is C / sqrt(max s), which equals C min(1/sqrt(s)) exactly
+// because sqrt and division are correctly rounded and monotone.  The FP64
+// value of s must be bit-identical to a plain IEEE evaluation, and FP64
+// division and square root are slow on this part, so:
+//  k_cfl_screen: one warp per active ring computes v0 = (max + min)/2 of the
+//    ring exactly (Eq. 37) and an FP32 estimate of s per cell (relative error
+//    below 2e-6), keeps the ring maximum of the estimate, and the last block
+//    reduces the global estimate M and the FP64 shear limit of Eq. 38.
+//  k_cfl_exact: every ring whose estimate reaches M (1 - 2^-12) is evaluated
+//    exactly in FP64 with round-to-nearest intrinsics (no fused multiply-add);
+//    the ring holding the true maximum always qualifies.  The last block
+//    publishes dt, clipped to t_end.
+// The screening launch also fills the per-step planet angle tables (sin^2 of
+// half the azimuth offset to the planet and its cosine) used by sub-step 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double av_rate(const MeshD &m, double dv, double len)
+{
+    if (m.av_lit) return __ddiv_rn(fabs(dv), __dmul_rn(m.av_c2, len));
+    if (dv < 0.0) return __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0, m.cq), m.cq), -dv), len);
+    return 0.0;
+}
+__device__ __forceinline__ float av_ratef(const MeshD &m, float dv, float len)
+{
+    if (m.av_lit) return fabsf(dv) / ((float)m.av_c2 * len);
+    if (dv < 0.0f) return (float)(4.0 * m.cq * m.cq) * (-dv) / len;
+    return 0.0f;
+}
+
+__device__ __forceinline__ bool cfl_skip(const Scal *sc)
+{
+    return sc->err != 0 || (!sc->fixed && sc->t >= sc->t_end);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f, double *v0, float *ringmax,
+                                                    double *part, Scal *sc, int nrings)
+{
+    __shared__ float s_red[8];
+    __shared__ double s_w[8], s_m[8];
+    __shared__ int s_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + warp;
+    const bool skip = cfl_skip(sc);
+    // planet angle tables for this step (time t^n)
+    if (m.has_planet) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.nx; i += gridDim.x * blockDim.x) {
+            const double dphi = (m.xmin + (i + 0.5) * m.dx) - m.om_rel * sc->t;
+            const double sh = sin(0.5 * dphi);
+            tb.ps[i] = (T)(sh * sh);
+            tb.pc[i] = (T)cos(dphi);
+        }
+    }
+    float smax = 0.0f;
+    int bad = 0;
+    if (!skip && r < nrings) {
+        const int ny = m.j1 - m.j0;
+        const int j = m.j0 + r % ny, k = m.k0 + r / ny;
+        const int ring = k * m.nyt + j;
+        const long long base = IX(m, 0, j, k);
+        double v0r = 0.0;
+        if (m.fargo) {
+            double mx = -INFINITY, mn = INFINITY;
+            for (int i = lane; i < m.nx; i += 32) {
+                const double v = (double)f.vx[base + i];
+                mx = fmax(mx, v);
+                mn = fmin(mn, v);
+            }
+            mx = warp_max(mx);
+            mn = warp_min(mn);
+            v0r = __dmul_rn(0.5, __dadd_rn(mx, mn));
+            if (lane == 0) v0[ring] = v0r;
+        }
+        const float lx = (float)tb.lx[ring], ly = (float)tb.ly[ring], lz = (float)tb.lz[ring];
+        const float dmin = (float)tb.dmin[ring];
+        const double nu = m.has_nu ? tb.nud[ring] : 0.0;
+        const float r4 = nu > 0.0 ? (float)(4.0 * nu / (tb.dmin[ring] * tb.dmin[ring])) : 0.0f;
+        const float csr = m.iso ? (float)tb.csd[ring] : 0.0f;
+        const float g1 = (float)m.g1;
+        for (int i = lane; i < m.nx; i += 32) {
+            const long long c = base + i;
+            const int ip = i + 1 == m.nx ? 0 : i + 1;
+            const T rho = f.rho[c];
+            float cs;
+            if (m.iso) {
+                cs = csr;
+            } else {
+                const T e = f.e[c];
+                if (!isfinite((double)e) || e < T(0)) bad = 1;
+                cs = sqrtf(g1 * (float)e / (float)rho);
+            }
+            if (!isfinite((double)rho) || rho <= T(0)) bad = 1;
+            const float r1 = cs / dmin;
+            float r2 = 0.0f, r3 = 0.0f;
+            if (m.hasX) {
+                const T vc = f.vx[c], vp = f.vx[base + ip];
+                const float a = fabsf((float)((double)vc - v0r)), b = fabsf((float)((double)vp - v0r));
+                r2 = fmaxf(r2, fmaxf(a, b) / lx);
+                r3 = fmaxf(r3, av_ratef(m, (float)(vp - vc), lx));
+                if (!isfinite((double)vc)) bad = 1;
+            }
+            if (m.hasY) {
+                const T vc = f.vy[c], vp = f.vy[c + m.sj];
+                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) / ly);
+                r3 = fmaxf(r3, av_ratef(m, (float)(vp - vc), ly));
+                if (!isfinite((double)vc)) bad = 1;
+            }
+            if (m.hasZ) {
+                const T vc = f.vz[c], vp = f.vz[c + m.sk];
+                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) / lz);
+                r3 = fmaxf(r3, av_ratef(m, (float)(vp - vc), lz));
+                if (!isfinite((double)vc)) bad = 1;
+            }
+            if (m.cq <= 0.0) r3 = 0.0f;
+            const float s = r1 * r1 + r2 * r2 + r3 * r3 + r4 * r4;
+            smax = fmaxf(smax, s);
+        }
+        smax = warp_maxf(smax);
+        if (lane == 0) ringmax[r] = smax;
+    }
+    smax = warp_maxf(smax);
+    if (lane == 0) s_red[warp] = smax;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&sc->err, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = s_red[0];
+        for (int w = 1; w < 8; w++) b = fmaxf(b, s_red[w]);
+        part[blockIdx.x] = (double)b;
+        __threadfence();
+        s_last = atomicAdd(&sc->counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double mx = 0.0, wsh = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
+    if (m.fargo && m.hasY && !skip) {
+        const int ny = m.j1 - m.j0, nz = m.k1 - m.k0;
+        const int npairs = (ny - 1) * nz;
+        for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+            const int j = m.j0 + p % (ny - 1), k = m.k0 + p / (ny - 1);
+            const int ring = k * m.nyt + j;
+            const double a = __ddiv_rn(__ldcg(&v0[ring]), tb.lx[ring]);
+            const double b = __ddiv_rn(__ldcg(&v0[ring + 1]), tb.lx[ring + 1]);
+            wsh = fmax(wsh, fabs(__dsub_rn(a, b)));
+        }
+    }
+    mx = warp_max(mx);
+    wsh = warp_max(wsh);
+    if (lane == 0) {
+        s_w[warp] = wsh;
+        s_m[warp] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) {
+            mx = fmax(mx, s_m[w]);
+            wsh = fmax(wsh, s_w[w]);
+        }
+        sc->m32 = mx;
+        sc->wsh = wsh;
+        sc->counter = 0u;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cfl_exact(MeshD m, Tab<T> tb, Fld<T> f, const double *v0,
+                                                   const float *ringmax, double *part, Scal *sc, int nrings)
+{
+    __shared__ double s_red[8];
+    __shared__ int s_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + warp;
+    const bool skip = cfl_skip(sc);
+    const double M = sc->m32;
+    const double thr = M < 1e-30 ? -1.0 : M * (1.0 - 1.0 / 4096.0);
+    double smax = 0.0;
+    if (!skip && r < nrings && (double)ringmax[r] >= thr) {
+        const int ny = m.j1 - m.j0;
+        const int j = m.j0 + r % ny, k = m.k0 + r / ny;
+        const int ring = k * m.nyt + j;
+        const long long base = IX(m, 0, j, k);
+        const double v0r = m.fargo ? v0[ring] : 0.0;
+        const double lx = tb.lx[ring], ly = tb.ly[ring], lz = tb.lz[ring], dmin = tb.dmin[ring];
+        const double nu = m.has_nu ? tb.nud[ring] : 0.0;
+        const double r4 = nu > 0.0 ? __ddiv_rn(__dmul_rn(4.0, nu), __dmul_rn(dmin, dmin)) : 0.0;
+        const double csr = m.iso ? tb.csd[ring] : 0.0;
+        for (int i = lane; i < m.nx; i += 32) {
+            const long long c = base + i;
+            const int ip = i + 1 == m.nx ? 0 : i + 1;
+            const double rho = (double)f.rho[c];
+            const double cs = m.iso ? csr : __dsqrt_rn(__ddiv_rn(__dmul_rn(m.g1, (double)f.e[c]), rho));
+            const double r1 = __ddiv_rn(cs, dmin);
+            double r2 = 0.0, r3 = 0.0;
+            if (m.hasX) {
+                const double vc = (double)f.vx[c], vp = (double)f.vx[base + ip];
+                const double a = fabs(__dsub_rn(vc, v0r)), b = fabs(__dsub_rn(vp, v0r));
+                r2 = fmax(r2, __ddiv_rn(a > b ? a : b, lx));
+                r3 = fmax(r3, av_rate(m, __dsub_rn(vp, vc), lx));
+            }
+            if (m.hasY) {
+                const double vc = (double)f.vy[c], vp = (double)f.vy[c + m.sj];
+                const double a = fabs(vc), b = fabs(vp);
+                r2 = fmax(r2, __ddiv_rn(a > b ? a : b, ly));
+                r3 = fmax(r3, av_rate(m, __dsub_rn(vp, vc), ly));
+            }
+            if (m.hasZ) {
+                const double vc = (double)f.vz[c], vp = (double)f.vz[c + m.sk];
+                const double a = fabs(vc), b = fabs(vp);
+                r2 = fmax(r2, __ddiv_rn(a > b ? a : b, lz));
+                r3 = fmax(r3, av_rate(m, __dsub_rn(vp, vc), lz));
+            }
+            if (m.cq <= 0.0) r3 = 0.0;
+            const double s = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(r1, r1), __dmul_rn(r2, r2)),
+                                                 __dmul_rn(r3, r3)),
+                                       __dmul_rn(r4, r4));
+            smax = fmax(smax, s);
+        }
+    }
+    smax = warp_max(smax);
+    if (lane == 0) s_red[warp] = smax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = s_red[0];
+        for (int w = 1; w < 8; w++) b = fmax(b, s_red[w]);
+        part[blockIdx.x] = b;
+        __threadfence();
+        s_last = atomicAdd(&sc->counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double mx = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
+    mx = warp_max(mx);
+    if (lane == 0) s_red[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) mx = fmax(mx, s_red[w]);
+        int err = atomicOr(&sc->err, 0);
+        const double t = sc->t, te = sc->t_end, wsh = sc->wsh;
+        double dt = 0.0;
+        if (!skip) {
+            if (sc->fixed) {
+                dt = sc->dt_fixed;
+            } else {
+                dt = __dmul_rn(m.cfl, __ddiv_rn(1.0, __dsqrt_rn(mx)));
+                if (wsh > 0.0) {
+                    const double ds = __ddiv_rn(m.cfl, wsh);
+                    if (ds < dt) dt = ds;
+                }
+                if (__dadd_rn(t, dt) > te) dt = __dsub_rn(te, t);
+                if (!(dt > 0.0) || !isfinite(dt)) err |= 2;
+            }
+        }
+        if (err) dt = 0.0;
+        sc->err = err;
+        sc->dt = dt;
+        sc->counter = 0u;
+    }
+}
+
+}  // namespace fk

@@ -1,0 +1,499 @@
+// Source step (flow-chart cell 7): sub-step 1, artificial viscosity with
+// compression heating, and the viscous stress tensor.
+//
+// Every kernel runs one thread per cell of the augmented mesh (ghosts and the
+// extra face row / plane included) and writes its output velocity buffer
+// completely: interior faces get the update, every other face is copied, so
+// the buffers can ping-pong without stale values.
+#pragma once
+#include "fargo_internal.cuh"
+
+namespace fk {
+
+struct CellIdx {
+    int i, j, k;
+};
+
+__device__ __forceinline__ bool decode(const MeshD &m, CellIdx &c)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)m.nx * (m.nyt + 1) * (m.nzt + 1);
+    if (tid >= n) return false;
+    c.i = (int)(tid % m.nx);
+    long long r = tid / m.nx;
+    c.j = (int)(r % (m.nyt + 1));
+    c.k = (int)(r / (m.nyt + 1));
+    return true;
+}
+
+// Pressure from the equation of state (Eqs. eos1, eos2).
+template <typename T>
+__device__ __forceinline__ T pressure(const MeshD &m, const Tab<T> &tb, const Fld<T> &f, long long c, int ring)
+{
+    if (m.iso) {
+        T cs = tb.cs[ring];
+        return cs * cs * f.rho[c];
+    }
+    return T(m.gamma - 1.0) * f.e[c];
+}
+
+// Planet part of the potential at the centre of cell (i, ring): Plummer
+// potential of the planet and the indirect term.  The squared distance is
+// written without cancellation, d^2 = (R - a)^2 + 4 R a sin^2(dphi/2) + Z^2,
+// from per-ring tables (R - a formed in FP64) and the per-step azimuth
+// tables, so the hot loop needs no FP64 arithmetic.  The star term, which has
+// no azimuthal dependence, enters through precomputed FP64 face gradients.
+template <typename T>
+__device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i, int ring)
+{
+    const T rm = tb.rma[ring];
+    const T d2 = rm * rm + tb.fra[ring] * tb.ps[i] + tb.z2[ring] + T(m.peps2);
+    T v;
+    if (sizeof(T) == 8) v = -T(m.pq) / sqrt(d2);
+    else v = -T(m.pq) * rsqrtf((float)d2);
+    if (m.indirect) v += tb.qar[ring] * tb.pc[i];
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Sub-step 1 (Sec. 3.3): pressure gradient with the two-point face density
+// (Eq. 20), potential gradient, centrifugal and geometric terms with the
+// four-face average of Eq. 12.  Jacobi: reads `in`, writes `out`.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+{
+    const double dtd = sc->dt;
+    if (!(dtd > 0.0)) return;
+    CellIdx ci;
+    if (!decode(m, ci)) return;
+    const T dt = (T)dtd;
+    const int i = ci.i, j = ci.j, k = ci.k;
+    const long long c = IX(m, i, j, k);
+    const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
+    const int ring = k * m.nyt + j;
+    const T om = (T)m.omega;
+    const int im = i == 0 ? m.nx - 1 : i - 1;
+    const int ip = i + 1 == m.nx ? 0 : i + 1;
+    if (j < m.nyt && k < m.nzt) {
+        T v = in.vx[c];
+        if (m.hasX && jact && kact) {
+            const long long cm = c - i + im;
+            const T d = tb.lenx[ring];
+            const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring);
+            T acc = T(-2) * (P0 - Pm) / (d * (in.rho[c] + in.rho[cm]));
+            if (m.has_planet)
+                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, im, ring)) / d;
+            v = v + dt * acc;
+        }
+        out.vx[c] = v;
+    }
+    if (k < m.nzt) {
+        T v = in.vy[c];
+        if (m.hasY && j > m.j0 && j < m.j1 && kact) {
+            const long long cm = c - m.sj;
+            const T d = tb.dyc[j];
+            const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring - 1);
+            T acc = T(-2) * (P0 - Pm) / (d * (in.rho[c] + in.rho[cm]));
+            if (m.has_planet)
+                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, ring - 1)) / d;
+            if (m.has_star) acc -= tb.gphy[ring];
+            if (m.geom != CART) {
+                const T Rj = tb.R[ring], Rm = tb.R[ring - 1];
+                const long long cp = c - i + ip, cmp = cm - i + ip;
+                const T vt = T(0.25) * ((in.vx[c] + Rj * om) + (in.vx[cp] + Rj * om) + (in.vx[cm] + Rm * om) +
+                                        (in.vx[cmp] + Rm * om));
+                T cen = vt * vt;
+                if (m.geom == SPH && m.hasZ) {
+                    const T vth = T(0.25) * (in.vz[c] + in.vz[c + m.sk] + in.vz[cm] + in.vz[cm + m.sk]);
+                    cen += vth * vth;
+                }
+                acc += cen / tb.yf[j];
+            }
+            v = v + dt * acc;
+        }
+        out.vy[c] = v;
+    }
+    if (j < m.nyt) {
+        T v = in.vz[c];
+        if (m.hasZ && k > m.k0 && k < m.k1 && jact) {
+            const long long cm = c - m.sk;
+            const int rm = ring - m.nyt;
+            const T d = tb.dzc[ring];
+            const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, rm);
+            T acc = T(-2) * (P0 - Pm) / (d * (in.rho[c] + in.rho[cm]));
+            if (m.has_planet)
+                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, rm)) / d;
+            if (m.has_star) acc -= tb.gphz[ring];
+            if (m.geom == SPH) {
+                const T Rk = tb.R[ring], Rm = tb.R[rm];
+                const long long cp = c - i + ip, cmp = cm - i + ip;
+                const T vt = T(0.25) * ((in.vx[c] + Rk * om) + (in.vx[cp] + Rk * om) + (in.vx[cm] + Rm * om) +
+                                        (in.vx[cmp] + Rm * om));
+                acc += vt * vt * tb.cotzf[k] / tb.ym[j];
+            }
+            v = v + dt * acc;
+        }
+        out.vz[c] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sub-steps 2 and 3: von Neumann-Richtmyer artificial viscosity applied
+// component-wise, q_d = C_q^2 rho (Delta v_d)^2 for compressions, its
+// gradient on interior faces (two-point density), the heating -q Delta v /
+// Delta, then the compression heating e (1 - theta)/(1 + theta),
+// theta = dt (gamma-1) div v / 2, with div v from the post-viscosity
+// velocities.  q of a neighbour is recomputed locally instead of stored, so
+// the two passes of the paper become one kernel without races.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T qvisc(T c2, T rho, T dv)
+{
+    return dv < T(0) ? c2 * rho * dv * dv : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+{
+    const double dtd = sc->dt;
+    if (!(dtd > 0.0)) return;
+    CellIdx ci;
+    if (!decode(m, ci)) return;
+    const T dt = (T)dtd;
+    const T c2 = (T)(m.cq * m.cq);
+    const bool av = m.cq > 0.0;
+    const int i = ci.i, j = ci.j, k = ci.k;
+    const long long c = IX(m, i, j, k);
+    const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
+    const int ring = k * m.nyt + j;
+    const int im = i == 0 ? m.nx - 1 : i - 1;
+    const int ip = i + 1 == m.nx ? 0 : i + 1;
+    const int ipp = ip + 1 == m.nx ? 0 : ip + 1;
+    const T *vx = in.vx, *vy = in.vy, *vz = in.vz, *rho = in.rho;
+    const long long sj = m.sj, sk = m.sk;
+    // own lower faces
+    T vxl = 0, vyl = 0, vzl = 0;
+    if (j < m.nyt && k < m.nzt) {
+        T v = vx[c];
+        if (av && m.hasX && jact && kact) {
+            const long long cm = c - i + im, cp = c - i + ip;
+            const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
+            const T qm = qvisc(c2, rho[cm], vx[c] - vx[cm]);
+            v -= dt * T(2) * (q0 - qm) / (tb.lenx[ring] * (rho[c] + rho[cm]));
+        }
+        out.vx[c] = v;
+        vxl = v;
+    }
+    if (k < m.nzt) {
+        T v = vy[c];
+        if (av && m.hasY && j > m.j0 && j < m.j1 && kact) {
+            const long long cm = c - sj;
+            const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
+            const T qm = qvisc(c2, rho[cm], vy[c] - vy[cm]);
+            v -= dt * T(2) * (q0 - qm) / (tb.dyc[j] * (rho[c] + rho[cm]));
+        }
+        out.vy[c] = v;
+        vyl = v;
+    }
+    if (j < m.nyt) {
+        T v = vz[c];
+        if (av && m.hasZ && k > m.k0 && k < m.k1 && jact) {
+            const long long cm = c - sk;
+            const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
+            const T qm = qvisc(c2, rho[cm], vz[c] - vz[cm]);
+            v -= dt * T(2) * (q0 - qm) / (tb.dzc[ring] * (rho[c] + rho[cm]));
+        }
+        out.vz[c] = v;
+        vzl = v;
+    }
+    if (m.iso || !(jact && kact)) return;
+    // heating by the artificial viscosity of the cell itself
+    T e = in.e[c];
+    T h = 0;
+    if (av) {
+        if (m.hasX) {
+            const T dv = vx[c - i + ip] - vx[c];
+            h += qvisc(c2, rho[c], dv) * dv / tb.lenx[ring];
+        }
+        if (m.hasY) {
+            const T dv = vy[c + sj] - vy[c];
+            h += qvisc(c2, rho[c], dv) * dv / tb.dy[j];
+        }
+        if (m.hasZ) {
+            const T dv = vz[c + sk] - vz[c];
+            h += qvisc(c2, rho[c], dv) * dv / tb.lenz[ring];
+        }
+    }
+    e -= dt * h;
+    // post-viscosity velocities on the upper faces (owned by the neighbours)
+    T div = 0;
+    if (m.hasX) {
+        const long long cp = c - i + ip, cpp = c - i + ipp;
+        T vxu = vx[cp];
+        if (av) {
+            const T qp = qvisc(c2, rho[cp], vx[cpp] - vx[cp]);
+            const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
+            vxu -= dt * T(2) * (qp - q0) / (tb.lenx[ring] * (rho[cp] + rho[c]));
+        }
+        div += tb.sx[ring] * (vxu - vxl);
+    }
+    const int fr = k * (m.nyt + 1) + j;
+    if (m.hasY) {
+        T vyu = vy[c + sj];
+        if (av && j + 1 < m.j1) {
+            const T qp = qvisc(c2, rho[c + sj], vy[c + 2 * sj] - vy[c + sj]);
+            const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
+            vyu -= dt * T(2) * (qp - q0) / (tb.dyc[j + 1] * (rho[c + sj] + rho[c]));
+        }
+        div += tb.sy[fr + 1] * vyu - tb.sy[fr] * vyl;
+    }
+    if (m.hasZ) {
+        T vzu = vz[c + sk];
+        if (av && k + 1 < m.k1) {
+            const T qp = qvisc(c2, rho[c + sk], vz[c + 2 * sk] - vz[c + sk]);
+            const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
+            vzu -= dt * T(2) * (qp - q0) / (tb.dzc[ring + m.nyt] * (rho[c + sk] + rho[c]));
+        }
+        div += tb.sz[fr + (m.nyt + 1)] * vzu - tb.sz[fr] * vzl;
+    }
+    div *= tb.vinv[ring];
+    const T th = T(0.5) * dt * T(m.gamma - 1.0) * div;
+    out.e[c] = e * (T(1) - th) / (T(1) + th);
+}
+
+// ---------------------------------------------------------------------------
+// Viscous stress tensor and velocity update (Appendix B, Eqs. 72-77).
+// Diagonal stresses at cell centres, off-diagonal ones on the lowest edges;
+// edge density and viscosity are the means over the cells sharing the edge.
+// Each thread recomputes the stresses its faces need from the velocities at
+// sub-step entry (Jacobi), so no stress array is stored.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ViscCtx {
+    const MeshD &m;
+    const Tab<T> &tb;
+    const T *rho, *vx, *vy, *vz;
+    __device__ ViscCtx(const MeshD &m_, const Tab<T> &tb_, const Fld<T> &f)
+        : m(m_), tb(tb_), rho(f.rho), vx(f.vx), vy(f.vy), vz(f.vz) {}
+    __device__ int wrap(int i) const { return i < 0 ? i + m.nx : (i >= m.nx ? i - m.nx : i); }
+    __device__ long long at(int i, int j, int k) const { return IX(m, wrap(i), j, k); }
+    __device__ T nu(int j, int k) const { return tb.nu[k * m.nyt + j]; }
+
+    __device__ T divv(int i, int j, int k) const
+    {
+        const long long c = at(i, j, k);
+        const int ring = k * m.nyt + j, fr = k * (m.nyt + 1) + j;
+        T f = 0;
+        if (m.hasX) f += tb.sx[ring] * (vx[at(i + 1, j, k)] - vx[c]);
+        if (m.hasY) f += tb.sy[fr + 1] * vy[c + m.sj] - tb.sy[fr] * vy[c];
+        if (m.hasZ) f += tb.sz[fr + m.nyt + 1] * vz[c + m.sk] - tb.sz[fr] * vz[c];
+        return f * tb.vinv[ring];
+    }
+    // diagonal components at the centre of cell (i,j,k)
+    __device__ void diag(int i, int j, int k, T &txx, T &tyy, T &tzz) const
+    {
+        const long long c = at(i, j, k);
+        const int ring = k * m.nyt + j;
+        const T dv = divv(i, j, k);
+        const T rn = rho[c] * nu(j, k);
+        const T dxx = (vx[at(i + 1, j, k)] - vx[c]) / tb.lenx[ring];
+        const T dyy = m.hasY ? (vy[c + m.sj] - vy[c]) / tb.dy[j] : T(0);
+        const T dzz = m.hasZ ? (vz[c + m.sk] - vz[c]) / tb.lenz[ring] : T(0);
+        const T tw = T(2.0 / 3.0) * dv;
+        if (m.geom == CART) {
+            txx = -rn * (T(2) * dxx - tw);
+            tyy = -rn * (T(2) * dyy - tw);
+            tzz = -rn * (T(2) * dzz - tw);
+        } else if (m.geom == CYL) {
+            const T r = tb.ym[j];
+            const T vr = T(0.5) * (vy[c] + vy[c + m.sj]);
+            txx = -rn * (T(2) * (dxx + vr / r) - tw);
+            tyy = -rn * (T(2) * dyy - tw);
+            tzz = -rn * (T(2) * dzz - tw);
+        } else {
+            const T r = tb.ym[j], ct = tb.cotzm[k];
+            const T vr = T(0.5) * (vy[c] + vy[c + m.sj]);
+            const T vt = T(0.5) * (vz[c] + vz[c + m.sk]);
+            txx = -rn * (T(2) * (dxx + vr / r + vt * ct / r) - tw);
+            tyy = -rn * (T(2) * dyy - tw);
+            tzz = -rn * (T(2) * (dzz + vr / r) - tw);
+        }
+    }
+    // tau_xy on the edge (i-1/2, j-1/2, k)
+    __device__ T txy(int i, int j, int k) const
+    {
+        const long long c = at(i, j, k), cm = at(i - 1, j, k);
+        const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sj] + rho[cm - m.sj]);
+        const T nb = T(0.5) * (nu(j, k) + nu(j - 1, k));
+        const T dvx_dy = (vx[c] - vx[c - m.sj]) / tb.dyc[j];
+        T t;
+        if (m.geom == CART) {
+            t = (vy[c] - vy[cm]) / T(m.dx) + dvx_dy;
+        } else if (m.geom == CYL) {
+            const T rf = tb.yf[j];
+            t = dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf + (vy[c] - vy[cm]) / (rf * T(m.dx));
+        } else {
+            const T rf = tb.yf[j], sn = tb.szm[k];
+            t = (vy[c] - vy[cm]) / (rf * sn * T(m.dx)) + dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf;
+        }
+        return -rb * nb * t;
+    }
+    // tau_xz on the edge (i-1/2, j, k-1/2)
+    __device__ T txz(int i, int j, int k) const
+    {
+        const long long c = at(i, j, k), cm = at(i - 1, j, k);
+        const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sk] + rho[cm - m.sk]);
+        const T nb = T(0.5) * (nu(j, k) + nu(j, k - 1));
+        const T dzc = tb.zm[k] - tb.zm[k - 1];
+        T t;
+        if (m.geom == CART) {
+            t = (vz[c] - vz[cm]) / T(m.dx) + (vx[c] - vx[c - m.sk]) / dzc;
+        } else if (m.geom == CYL) {
+            t = (vx[c] - vx[c - m.sk]) / dzc + (vz[c] - vz[cm]) / (tb.ym[j] * T(m.dx));
+        } else {
+            const T r = tb.ym[j], sf = tb.szf[k];
+            t = sf / r * (vx[c] / tb.szm[k] - vx[c - m.sk] / tb.szm[k - 1]) / dzc + (vz[c] - vz[cm]) / (r * sf * T(m.dx));
+        }
+        return -rb * nb * t;
+    }
+    // tau_yz on the edge (i, j-1/2, k-1/2)
+    __device__ T tyz(int i, int j, int k) const
+    {
+        const long long c = at(i, j, k);
+        const T rb = T(0.25) * (rho[c] + rho[c - m.sj] + rho[c - m.sk] + rho[c - m.sj - m.sk]);
+        const T nb = T(0.25) * (nu(j, k) + nu(j - 1, k) + nu(j, k - 1) + nu(j - 1, k - 1));
+        const T dzc = tb.zm[k] - tb.zm[k - 1];
+        T t;
+        if (m.geom == SPH) {
+            const T rf = tb.yf[j];
+            t = (vz[c] - vz[c - m.sj]) / tb.dyc[j] - T(0.5) * (vz[c] + vz[c - m.sj]) / rf +
+                (vy[c] - vy[c - m.sk]) / (rf * dzc);
+        } else {
+            t = (vz[c] - vz[c - m.sj]) / tb.dyc[j] + (vy[c] - vy[c - m.sk]) / dzc;
+        }
+        return -rb * nb * t;
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_visc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+{
+    const double dtd = sc->dt;
+    if (!(dtd > 0.0)) return;
+    CellIdx ci;
+    if (!decode(m, ci)) return;
+    const T dt = (T)dtd;
+    const int i = ci.i, j = ci.j, k = ci.k;
+    const long long c = IX(m, i, j, k);
+    const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
+    const ViscCtx<T> V(m, tb, in);
+    const T dx = (T)m.dx;
+    const T *rho = in.rho;
+    if (j < m.nyt && k < m.nzt) {
+        T v = in.vx[c];
+        if (jact && kact) {
+            const long long cm = V.at(i - 1, j, k);
+            T a0, a1, a2, b0, b1, b2;
+            V.diag(i, j, k, a0, a1, a2);
+            V.diag(i - 1, j, k, b0, b1, b2);
+            const T rf = T(0.5) * (rho[c] + rho[cm]);
+            T f = 0;
+            if (m.geom == CART) {
+                f += (a0 - b0) / dx;
+                if (m.hasY) f += (V.txy(i, j + 1, k) - V.txy(i, j, k)) / tb.dy[j];
+                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) / tb.dz[k];
+            } else if (m.geom == CYL) {
+                const T r = tb.ym[j];
+                if (m.hasY)
+                    f += (tb.yf[j + 1] * tb.yf[j + 1] * V.txy(i, j + 1, k) - tb.yf[j] * tb.yf[j] * V.txy(i, j, k)) /
+                         (r * r * tb.dy[j]);
+                f += (a0 - b0) / (r * dx);
+                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) / tb.dz[k];
+            } else {
+                const T r = tb.ym[j], sn = tb.szm[k], ct = tb.cotzm[k];
+                T ty0 = 0, ty1 = 0, tz0 = 0, tz1 = 0;
+                if (m.hasY) {
+                    ty0 = V.txy(i, j, k);
+                    ty1 = V.txy(i, j + 1, k);
+                    f += (tb.yf[j + 1] * tb.yf[j + 1] * ty1 - tb.yf[j] * tb.yf[j] * ty0) / (r * r * tb.dy[j]);
+                }
+                if (m.hasZ) {
+                    tz0 = V.txz(i, j, k);
+                    tz1 = V.txz(i, j, k + 1);
+                    f += (tz1 - tz0) / (r * tb.dz[k]);
+                }
+                f += (a0 - b0) / (r * sn * dx);
+                if (m.hasY) f += T(0.5) * (ty0 + ty1) / r;
+                if (m.hasZ) f += T(2) * T(0.5) * (tz0 + tz1) * ct / r;
+            }
+            v = v - dt * f / rf;
+        }
+        out.vx[c] = v;
+    }
+    if (k < m.nzt) {
+        T v = in.vy[c];
+        if (m.hasY && j > m.j0 && j < m.j1 && kact) {
+            const long long cjm = c - m.sj;
+            T a0, a1, a2, b0, b1, b2;
+            V.diag(i, j, k, a0, a1, a2);
+            V.diag(i, j - 1, k, b0, b1, b2);
+            const T rf = T(0.5) * (rho[c] + rho[cjm]);
+            T f = 0;
+            if (m.geom == CART) {
+                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) / dx;
+                f += (a1 - b1) / tb.dyc[j];
+                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) / tb.dz[k];
+            } else if (m.geom == CYL) {
+                const T r = tb.yf[j];
+                f += (tb.ym[j] * a1 - tb.ym[j - 1] * b1) / (r * tb.dyc[j]);
+                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) / (r * dx);
+                f -= T(0.5) * (a0 + b0) / r;
+                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) / tb.dz[k];
+            } else {
+                const T r = tb.yf[j], sn = tb.szm[k];
+                f += (tb.ym[j] * tb.ym[j] * a1 - tb.ym[j - 1] * tb.ym[j - 1] * b1) / (r * r * tb.dyc[j]);
+                if (m.hasZ) f += (V.tyz(i, j, k + 1) * tb.szf[k + 1] - V.tyz(i, j, k) * tb.szf[k]) / (r * sn * tb.dz[k]);
+                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) / (r * sn * dx);
+                f -= T(0.5) * (a2 + b2 + a0 + b0) / r;
+            }
+            v = v - dt * f / rf;
+        }
+        out.vy[c] = v;
+    }
+    if (j < m.nyt) {
+        T v = in.vz[c];
+        if (m.hasZ && k > m.k0 && k < m.k1 && jact) {
+            const long long ckm = c - m.sk;
+            T a0, a1, a2, b0, b1, b2;
+            V.diag(i, j, k, a0, a1, a2);
+            V.diag(i, j, k - 1, b0, b1, b2);
+            const T rf = T(0.5) * (rho[c] + rho[ckm]);
+            const T dzc = tb.zm[k] - tb.zm[k - 1];
+            T f = 0;
+            if (m.geom == CART) {
+                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) / dx;
+                if (m.hasY) f += (V.tyz(i, j + 1, k) - V.tyz(i, j, k)) / tb.dy[j];
+                f += (a2 - b2) / dzc;
+            } else if (m.geom == CYL) {
+                const T r = tb.ym[j];
+                if (m.hasY) f += (tb.yf[j + 1] * V.tyz(i, j + 1, k) - tb.yf[j] * V.tyz(i, j, k)) / (r * tb.dy[j]);
+                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) / (r * dx);
+                f += (a2 - b2) / dzc;
+            } else {
+                const T r = tb.ym[j], sf = tb.szf[k], ctf = tb.cotzf[k];
+                if (m.hasY) {
+                    const T y1 = tb.yf[j + 1], y0 = tb.yf[j];
+                    f += (y1 * y1 * y1 * V.tyz(i, j + 1, k) - y0 * y0 * y0 * V.tyz(i, j, k)) / (r * r * r * tb.dy[j]);
+                }
+                f += (a2 * tb.szm[k] - b2 * tb.szm[k - 1]) / (r * sf * dzc);
+                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) / (r * sf * dx);
+                f -= T(0.5) * (a0 + b0) * ctf / r;
+            }
+            v = v - dt * f / rf;
+        }
+        out.vz[c] = v;
+    }
+}
+
+}  // namespace fk

@@ -1,0 +1,68 @@
+"""Helpers shared by the GPU parity tests."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+def have_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def make_ctx(w, prec=None, t=0.0, t_end=1e300):
+    import paper_1602_02359_b300 as fb
+    prec = fb.F64 if prec is None else prec
+    c = fb.Fargo(w, prec)
+    c.set_state(w.state)
+    c.set_time(t, t_end)
+    return c
+
+
+def rel_linf(a, b):
+    """max |a - b| / max |b| (norm-wise relative L-infinity)."""
+    d = np.max(np.abs(np.asarray(a, dtype=np.float64) - b))
+    s = np.max(np.abs(b))
+    return d / s if s > 0 else d
+
+
+def rel_l1(a, b):
+    s = np.sum(np.abs(b))
+    d = np.sum(np.abs(np.asarray(a, dtype=np.float64) - b))
+    return d / s if s > 0 else d
+
+
+def active_faces(w, name, a):
+    """Active region plus the upper boundary face of the staggered component."""
+    gz, gy = w.gz, w.gy
+    if name == "vy" and w.ny > 1:
+        return a[gz:gz + w.nz, gy:gy + w.ny + 1, :]
+    if name == "vz" and w.nz > 1:
+        return a[gz:gz + w.nz + 1, gy:gy + w.ny, :]
+    return w.active(a)
+
+
+def fields_of(w):
+    f = ["rho", "vx"]
+    if not w.iso:
+        f.append("e")
+    if w.ny > 1:
+        f.append("vy")
+    if w.nz > 1:
+        f.append("vz")
+    return f
+
+
+def compare_state(w, gpu_state, ora_state, tol, norm=rel_linf):
+    worst = {}
+    for k in fields_of(w):
+        a = active_faces(w, k, gpu_state[k].astype(np.float64))
+        b = active_faces(w, k, ora_state[k])
+        worst[k] = norm(a, b)
+    bad = {k: v for k, v in worst.items() if not v <= tol}
+    assert not bad, f"parity beyond {tol}: {worst}"
+    return worst

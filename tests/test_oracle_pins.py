@@ -200,6 +200,7 @@ def test_fargo_sweep_is_identity_on_axisymmetric_state(geom, dims):
     X = v0[w.gz, w.gy] * dt / (W.centres(w.yf)[w.gy] * 2 * math.pi / w.nx)
     assert abs(X) > 1.5                          # a real multi-cell shift
     o.transport_x(st, pis, v0, dt)
+    o.orbital_shift(st, pis, v0, dt)
     after = [st["rho"], st["e"]] + pis
     for b, a in zip(before, after):
         assert np.array_equal(b, a)
@@ -227,6 +228,7 @@ def _ring_case(nx, v, dt, fargo, rho):
     v0 = o.v0(st)
     pis = o.momenta(st)
     o.transport_x(st, pis, v0, dt)
+    o.orbital_shift(st, pis, v0, dt)
     return st, pis
 
 
@@ -633,3 +635,22 @@ def test_zero_gradient_and_reflecting_ghosts():
     assert np.array_equal(st["vy"][:nzt, g - 1], -st["vy"][:nzt, g + 1])
     assert np.array_equal(st["rho"][:nzt, g - 2], st["rho"][:nzt, g + 1])
     assert np.all(st["vz"][g, :w.ny_t] == 0) and np.all(st["vz"][g + 5, :w.ny_t] == 0)
+
+
+def test_orbital_step_after_radial_sweep_is_stable():
+    """The uniform orbital step (Eq. fargo2) is applied after the Y and Z
+    sweeps: a 1e-7 density perturbation of a planet-free Keplerian disk at
+    C = 0.44 stays at round-off level over 40 steps (applying the multi-cell
+    shift before the radial sweep amplifies it by orders of magnitude)."""
+    w = W.disk2d(nx=192, ny=64, q=0.0)
+    o = oracle.Oracle(w)
+    a = w.copy().state
+    b = w.copy().state
+    rng = np.random.default_rng(0)
+    b["rho"] *= 1 + 1e-7 * rng.uniform(-1, 1, size=b["rho"].shape)
+    ta = tb = 0.0
+    for _ in range(40):
+        ta += o.step(a, ta)
+        tb += o.step(b, tb)
+    ra, rb = w.active(a["rho"]), w.active(b["rho"])
+    assert np.max(np.abs(ra - rb) / ra) < 1e-6

@@ -176,7 +176,7 @@ def disk2d(nx=768, ny=256, h=0.05, nu=1e-5, q=1e-3, g=3, sigma0=1e-3,
 
 
 def disk3d(nx=1536, ny=512, nz=96, h=0.05, alpha=1e-3, q=3e-4, g=3, rho0=1e-3,
-           rmin=0.4, rmax=2.5, gamma=1.4, nsteps=200, fargo=True, cq=1.41):
+           rmin=0.4, rmax=2.5, gamma=1.4, nsteps=200, fargo=True, cq=1.41, slab=None):
     """3D spherical adiabatic disk with one planet, vertically hydrostatic.
 
     Isothermal on spheres at t = 0: c_s^2 = h^2/r, rho = rho0 r^-1.5
@@ -184,9 +184,16 @@ def disk3d(nx=1536, ny=512, nz=96, h=0.05, alpha=1e-3, q=3e-4, g=3, rho0=1e-3,
     equilibrium of the r and theta balances), e = c_s^2 rho/(gamma - 1).
     alpha viscosity nu = alpha c_s H = alpha h^2 r^(1/2), fixed in time.
     Colatitude spans pi/2 +- 3.5 h.  Ghosts frozen in r and theta.
+    slab = (j0, nj, k0, nk) keeps only active rows j0..j0+nj-1 and planes
+    k0..k0+nk-1 of the full mesh (same faces and ICs there): a bounded sample.
     """
     yf = faces(ny, g, rmin, rmax, log=True)
     zf = faces(nz, g, 0.5 * math.pi - 3.5 * h, 0.5 * math.pi + 3.5 * h)
+    if slab is not None:
+        j0, nj, k0, nk = slab
+        yf = yf[j0:j0 + nj + 2 * g + 1]
+        zf = zf[k0:k0 + nk + 2 * g + 1]
+        ny, nz = nj, nk
     w = Workload("disk3d", SPH, nx, ny, nz, g, -math.pi, math.pi, yf, zf, gamma, False,
                  None, None, 0.44, cq, fargo, 0.0,
                  (BC_FROZEN, BC_FROZEN), (BC_FROZEN, BC_FROZEN),
