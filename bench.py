@@ -127,6 +127,10 @@ def make_workload(name):
     if name == "disk2d":
         w = W.disk2d()
         return w, "disk2d-cyl-isothermal-planet-768x256", False
+    if name == "disk3d-small":
+        # profiling case: the same disk on 1536 x 128 x 48 cells (state still far above L2)
+        w = W.disk3d(ny=128, nz=48)
+        return w, "disk3d-sph-adiabatic-planet-1536x128x48", True
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -230,7 +234,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="disk3d", choices=["disk3d", "disk2d"])
+    ap.add_argument("--workload", default="disk3d", choices=["disk3d", "disk2d", "disk3d-small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -350,7 +354,7 @@ def main():
             fp64 = fp64_plain_disk2d(torch, fb)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload != "disk3d-small":
         cpu = cpu_baseline(args.workload)
 
     if rank == 0:

@@ -251,6 +251,30 @@ static int build_tables(fargo_ctx *c, Tab<T> &t)
     UPD(Rd, h.R); UPD(zcd, h.zc); UPD(cosx, h.cosx); UPD(sinx, h.sinx);
     UP(rma, h.rma); UP(fra, h.fra); UP(z2, h.z2); UP(qar, h.qar);
     {
+        const MeshD &m = c->m;
+        t.gm1 = (T)(m.gamma - 1.0);
+        t.half_gm1 = (T)(0.5 * (m.gamma - 1.0));
+        t.cq2 = (T)(m.cq * m.cq);
+        t.omega = (T)m.omega;
+        t.pq = (T)m.pq;
+        t.peps2 = (T)m.peps2;
+        t.dx = (T)m.dx;
+        t.g1 = (T)m.g1;
+        t.k4 = (T)(m.av_lit ? 1.0 / m.av_c2 : 4.0 * m.cq * m.cq);
+    }
+    {
+        std::vector<double> r4(h.dmin.size(), 0.0);
+        for (size_t r = 0; r < r4.size(); r++)
+            if (h.nu[r] > 0.0) r4[r] = 4.0 * h.nu[r] / (h.dmin[r] * h.dmin[r]);
+        UP(r4, r4);
+        UP(dminT, h.dmin);
+        std::vector<double> idyc(h.dyc.size(), 0.0), idzc(h.dzc.size(), 0.0);
+        for (size_t q = 0; q < idyc.size(); q++) idyc[q] = h.dyc[q] > 0.0 ? 1.0 / h.dyc[q] : 0.0;
+        for (size_t q = 0; q < idzc.size(); q++) idzc[q] = h.dzc[q] > 0.0 ? 1.0 / h.dzc[q] : 0.0;
+        UP(idyc, idyc);
+        UP(idzc, idzc);
+    }
+    {
         void *q;
         if ((rc = dalloc(c, &q, sizeof(T) * c->nx))) return rc;
         t.ps = (T *)q;
@@ -306,6 +330,18 @@ static QSet<T> qset(const fargo_ctx *c, T *rho, T *e, T *const *pi)
 
 static unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// 3D launch shape of the per-cell kernels: x = azimuth, y = rows, z = planes.
+static dim3 cell_block(const MeshD &m)
+{
+    int bx = (m.nx + 31) / 32 * 32;
+    return dim3(bx < 256 ? bx : 256, 1, 1);
+}
+static dim3 cell_grid(const MeshD &m, int ny, int nz)
+{
+    const dim3 b = cell_block(m);
+    return dim3((m.nx + b.x - 1) / b.x, ny, nz);
+}
+
 // ---------------------------------------------------------------------------
 // The launch sequence of one full update (flow chart cells 2-12).
 // Velocity buffers ping-pong A -> B -> A (-> B); the Y and Z sweeps are
@@ -325,7 +361,6 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     const MeshD &m = c->m;
     cudaStream_t s = c->stream;
     const int bs = 256;
-    const long long ncell = (long long)m.nx * (m.nyt + 1) * (m.nzt + 1);
     int nl = 0;
 #define MARK(nm)                                                    \
     do {                                                            \
@@ -347,11 +382,16 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     k_cfl_exact<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc, c->nrings_active);
     MARK("cfl_exact");
     // cell 7
-    k_substep1<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc); MARK("substep1");
-    k_artvisc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, VB, A, c->sc); MARK("artvisc");
+    k_substep1<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, c->sc); MARK("substep1");
+    k_artvisc<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, VB, A, c->sc); MARK("artvisc");
     Fld<T> vsrc = A;
     if (m.has_nu) {
-        k_visc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc); MARK("visc");
+        // stresses once into the scratch momenta of set B (unused until the transport step)
+        QSet<T> tau{};
+        for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
+        tau.nq = 6;
+        k_visc_tau<T><<<cell_grid(m, m.j1 - m.j0 + 1, m.k1 - m.k0 + 1), cell_block(m), 0, s>>>(m, b.tab, A, tau, c->sc); MARK("visc_tau");
+        k_visc_apply<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, tau, c->sc); MARK("visc_apply");
         vsrc = VB;
     }
     // cell 9
@@ -362,26 +402,25 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     const int nyz = m.hasY + m.hasZ;
     const bool x_out = (nyz % 2) == 1;
     Fld<T> tx_in = {A.rho, A.e, vsrc.vx, vsrc.vy, vsrc.vz};
-    k_transport_x<T><<<m.nyt * m.nzt, c->tx_threads, c->tx_smem, s>>>(m, b.tab, tx_in, x_out ? qb : qa, c->v0, c->sc);
+    launch_tx<T>(m, b.tab, tx_in, x_out ? qb : qa, c->v0, c->sc, c->tx_smem, s);
     MARK("transport_x");
     QSet<T> cur = x_out ? qb : qa, oth = x_out ? qa : qb;
-    const long long nc = (long long)m.nx * m.nyt * m.nzt;
     if (m.hasY) {
-        k_transport_yz<T, 1><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, cur, oth, vsrc.vy, c->sc, m.hasZ ? 1 : 0);
+        launch_sweep<T, 1>(m, b.tab, cur, oth, vsrc.vy, c->sc, m.hasZ ? 1 : 0, s);
         MARK("transport_y");
         QSet<T> t = cur; cur = oth; oth = t;
     }
     if (m.hasZ) {
-        k_transport_yz<T, 2><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, cur, oth, vsrc.vz, c->sc, 0);
+        launch_sweep<T, 2>(m, b.tab, cur, oth, vsrc.vz, c->sc, 0, s);
         MARK("transport_z");
         QSet<T> t = cur; cur = oth; oth = t;
     }
     // cur is the state quantity set again (qa); the uniform orbital step comes last
     if (m.fargo && m.hasX) {
-        k_orbital<T><<<c->nrings_active, c->tx_threads, c->tx_smem, s>>>(m, b.tab, cur, c->v0, c->sc);
+        launch_orb<T>(m, b.tab, cur, c->v0, c->sc, c->nrings_active, c->tx_smem, s);
         MARK("orbital");
     }
-    k_newvel<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, cur, vsrc, A, c->sc, 0); MARK("newvel");
+    k_newvel<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, cur, vsrc, A, c->sc, 0); MARK("newvel");
 #undef MARK
     c->launches = nl;
     if (prof) prof->n = nl;
@@ -420,12 +459,20 @@ static int set_kernel_attrs(fargo_ctx *c)
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
     nq -= 0;
-    size_t smem = (size_t)(nq + 5) * c->nx * sizeof(T);
-    if (smem > (size_t)maxsm) return FARGO_ERR_SIZE;
+    size_t smem = (size_t)(nq + 2) * c->nx * sizeof(T);
+    if (smem > (size_t)maxsm - 1024 || ring_chunk(c->nx) == 0) return FARGO_ERR_SIZE;
     c->tx_smem = smem;
-    c->tx_threads = c->nx >= 1024 ? 512 : 256;
-    CK(cudaFuncSetAttribute(k_transport_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CK(cudaFuncSetAttribute(k_orbital<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    CK(cudaFuncSetAttribute(k_transport_x<T, 1>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_transport_x<T, 2>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_transport_x<T, 3>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_transport_x<T, 4>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_transport_x<T, 8>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_orbital<T, 1>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_orbital<T, 2>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_orbital<T, 3>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_orbital<T, 4>, (cudaFuncAttribute)a, (int)smem));
+    CK(cudaFuncSetAttribute(k_orbital<T, 8>, (cudaFuncAttribute)a, (int)smem));
     return FARGO_OK;
 }
 
@@ -476,6 +523,7 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     m.fargo = prm->fargo ? 1 : 0;
     m.av_lit = prm->av_dt_literal ? 1 : 0;
     m.has_nu = prm->nu ? 1 : 0;
+    m.has_av = prm->cq > 0.0 ? 1 : 0;
     m.has_planet = planet && planet->q > 0.0;
     m.indirect = m.has_planet && planet->indirect;
     m.has_star = prm->star_mass > 0.0 && geom != FARGO_CART;
@@ -734,8 +782,6 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     const MeshD &m = c->m;
     cudaStream_t s = c->stream;
     const int bs = 256;
-    const long long ncell = (long long)m.nx * (m.nyt + 1) * (m.nzt + 1);
-    const long long nc = (long long)m.nx * m.nyt * m.nzt;
     const size_t nbytes = (size_t)m.ntot * sizeof(T);
     Fld<T> A = b.A;
     Fld<T> VB = {A.rho, A.e, b.vB[0], b.vB[1], b.vB[2]};
@@ -744,6 +790,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     int rc = read_scal(c, &sh);
     if (rc) return rc;
     sh.dt = dt;
+    sh.dtf = (float)dt;
     sh.err = 0;
     sh.fixed = phase == 1 ? 0 : 1;
     sh.dt_fixed = dt;
@@ -771,35 +818,43 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
                                                      c->nrings_active);
         break;
     case 2:
-        k_substep1<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc);
+        // the screening launch fills the per-step planet angle tables
+        k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
+                                                      c->nrings_active);
+        k_substep1<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
     case 3:
         if ((rc = copyv(b.vB, va))) return rc;
-        k_artvisc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, VB, A, c->sc);
+        k_artvisc<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, VB, A, c->sc);
         break;
-    case 4:
+    case 4: {
         if (!m.has_nu) break;
-        k_visc<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, A, VB, c->sc);
+        QSet<T> tau{};
+        for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
+        tau.nq = 6;
+        k_visc_tau<T><<<cell_grid(m, m.j1 - m.j0 + 1, m.k1 - m.k0 + 1), cell_block(m), 0, s>>>(m, b.tab, A, tau, c->sc);
+        k_visc_apply<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, tau, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
+    }
     case 5:
-        k_transport_x<T><<<m.nyt * m.nzt, c->tx_threads, c->tx_smem, s>>>(m, b.tab, A, qa, c->v0, c->sc);
+        launch_tx<T>(m, b.tab, A, qa, c->v0, c->sc, c->tx_smem, s);
         break;
     case 6:
     case 7: {
         if ((phase == 6 && !m.hasY) || (phase == 7 && !m.hasZ)) break;
-        if (phase == 6) k_transport_yz<T, 1><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, qa, qb, A.vy, c->sc, 1);
-        else k_transport_yz<T, 2><<<grid_for(nc, bs), bs, 0, s>>>(m, b.tab, qa, qb, A.vz, c->sc, 1);
+        if (phase == 6) launch_sweep<T, 1>(m, b.tab, qa, qb, A.vy, c->sc, 1, s);
+        else launch_sweep<T, 2>(m, b.tab, qa, qb, A.vz, c->sc, 1, s);
         for (int q = 0; q < qa.nq; q++) CK(cudaMemcpyAsync(qa.q[q], qb.q[q], nbytes, cudaMemcpyDeviceToDevice, s));
         break;
     }
     case 8:
-        k_newvel<T><<<grid_for(ncell, bs), bs, 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
+        k_newvel<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
         break;
     case 9:
         if (m.fargo && m.hasX)
-            k_orbital<T><<<c->nrings_active, c->tx_threads, c->tx_smem, s>>>(m, b.tab, qa, c->v0, c->sc);
+            launch_orb<T>(m, b.tab, qa, c->v0, c->sc, c->nrings_active, c->tx_smem, s);
         break;
     default:
         return FARGO_ERR_BADARG;
@@ -907,7 +962,7 @@ extern "C" int fargo_launches_per_step(fargo_ctx *c)
     const MeshD &m = c->m;
     n += m.hasY + m.hasZ;        // cell 2
     n += 2;                      // Courant (screen + exact)
-    n += 2 + (m.has_nu ? 1 : 0); // sources
+    n += 2 + (m.has_nu ? 2 : 0); // sources (viscosity: stresses + update)
     n += m.hasY + m.hasZ;        // cell 9
     n += 1 + m.hasY + m.hasZ;    // sweeps
     n += (m.fargo && m.hasX) ? 1 : 0;  // orbital step

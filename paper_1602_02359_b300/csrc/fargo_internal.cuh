@@ -11,7 +11,7 @@ enum { BC_REFLECT = 0, BC_FROZEN = 1, BC_ZEROGRAD = 2 };
 // Mesh description and run constants, passed by value to every kernel.
 struct MeshD {
     int nx, nyt, nzt, gy, gz, j0, j1, k0, k1, g;
-    int hasX, hasY, hasZ, geom, iso, fargo, av_lit, has_nu, has_planet, indirect, has_star;
+    int hasX, hasY, hasZ, geom, iso, fargo, av_lit, has_nu, has_planet, indirect, has_star, has_av;
     int bcy[2], bcz[2];
     long long sj, sk, ntot;      // row pitch, plane stride, elements per field
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
@@ -38,6 +38,12 @@ struct Tab {
     // cos(dphi) of the offset to the planet
     const T *rma, *fra, *z2, *qar;
     T *ps, *pc;
+    // run constants in the field precision (no FP64 work in FP32 kernels)
+    T gm1, cq2, omega, pq, peps2, dx, half_gm1, g1, k4;
+    // Courant screening: 4 nu / dmin^2 and dmin per ring
+    const T *r4, *dminT;
+    // inverse centre-to-centre distances across Y faces (per j) and Z faces (per ring)
+    const T *idyc, *idzc;
 };
 
 template <typename T>
@@ -58,7 +64,29 @@ struct Scal {
     long long nstep;
     int err, fixed;
     unsigned int counter, counter2;
+    float dtf;     // dt rounded to FP32, published with dt
 };
+
+// The step in the field precision.
+template <typename T>
+__device__ __forceinline__ T step_dt(const Scal *sc);
+template <>
+__device__ __forceinline__ double step_dt<double>(const Scal *sc) { return sc->dt; }
+template <>
+__device__ __forceinline__ float step_dt<float>(const Scal *sc) { return sc->dtf; }
+
+// v - v0 for a field value v and an FP64 v0 split as v0 = hi + lo (hi, lo in
+// the field precision): (v - hi) is formed exactly with TwoSum, then lo is
+// subtracted, so the result is within about one ulp of the exact difference
+// without FP64 arithmetic.
+__device__ __forceinline__ float sub_split(float v, float hi, float lo)
+{
+    const float s = v - hi;
+    const float bb = s - v;
+    const float err = (v - (s - bb)) + (-hi - bb);
+    return s + (err - lo);
+}
+__device__ __forceinline__ double sub_split(double v, double hi, double lo) { return v - hi - lo; }
 
 __device__ __forceinline__ long long IX(const MeshD &m, int i, int j, int k)
 {

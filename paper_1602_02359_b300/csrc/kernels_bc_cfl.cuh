@@ -131,10 +131,12 @@ __device__ __forceinline__ double av_rate(const MeshD &m, double dv, double len)
     if (dv < 0.0) return __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0, m.cq), m.cq), -dv), len);
     return 0.0;
 }
-__device__ __forceinline__ float av_ratef(const MeshD &m, float dv, float len)
+// FP32 estimate of the artificial-viscosity rate; k4 = 4 C_q^2 (ZEUS form)
+// or 1/(4 sqrt 2) (printed form), both rounded to FP32 on the host side.
+__device__ __forceinline__ float av_ratef(bool lit, float k4, float dv, float len)
 {
-    if (m.av_lit) return fabsf(dv) / ((float)m.av_c2 * len);
-    if (dv < 0.0f) return (float)(4.0 * m.cq * m.cq) * (-dv) / len;
+    if (lit) return fabsf(dv) * k4 / len;
+    if (dv < 0.0f) return k4 * (-dv) / len;
     return 0.0f;
 }
 
@@ -171,58 +173,60 @@ __global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f
         const long long base = IX(m, 0, j, k);
         double v0r = 0.0;
         if (m.fargo) {
-            double mx = -INFINITY, mn = INFINITY;
+            // max and min are exact in the field precision
+            T mx = f.vx[base], mn = mx;
             for (int i = lane; i < m.nx; i += 32) {
-                const double v = (double)f.vx[base + i];
-                mx = fmax(mx, v);
-                mn = fmin(mn, v);
+                const T v = f.vx[base + i];
+                mx = v > mx ? v : mx;
+                mn = v < mn ? v : mn;
             }
-            mx = warp_max(mx);
-            mn = warp_min(mn);
-            v0r = __dmul_rn(0.5, __dadd_rn(mx, mn));
+            v0r = __dmul_rn(0.5, __dadd_rn(warp_max((double)mx), warp_min((double)mn)));
             if (lane == 0) v0[ring] = v0r;
         }
-        const float lx = (float)tb.lx[ring], ly = (float)tb.ly[ring], lz = (float)tb.lz[ring];
-        const float dmin = (float)tb.dmin[ring];
-        const double nu = m.has_nu ? tb.nud[ring] : 0.0;
-        const float r4 = nu > 0.0 ? (float)(4.0 * nu / (tb.dmin[ring] * tb.dmin[ring])) : 0.0f;
-        const float csr = m.iso ? (float)tb.csd[ring] : 0.0f;
-        const float g1 = (float)m.g1;
+        const T v0hi = (T)v0r, v0lo = (T)(v0r - (double)v0hi);
+        const float lx = (float)tb.lenx[ring], ly = (float)tb.dy[j], lz = (float)tb.lenz[ring];
+        const float dmin = (float)tb.dminT[ring];
+        const float r4 = m.has_nu ? (float)tb.r4[ring] : 0.0f;
+        const float csr = m.iso ? (float)tb.cs[ring] : 0.0f;
+        const float g1 = (float)tb.g1;
+        const bool lit = m.av_lit != 0;
+        const float k4 = (float)tb.k4;
+        const bool avon = m.has_av != 0;
         for (int i = lane; i < m.nx; i += 32) {
             const long long c = base + i;
             const int ip = i + 1 == m.nx ? 0 : i + 1;
-            const T rho = f.rho[c];
+            const float rho = (float)f.rho[c];
             float cs;
             if (m.iso) {
                 cs = csr;
             } else {
-                const T e = f.e[c];
-                if (!isfinite((double)e) || e < T(0)) bad = 1;
-                cs = sqrtf(g1 * (float)e / (float)rho);
+                const float e = (float)f.e[c];
+                if (!isfinite(e) || e < 0.0f) bad = 1;
+                cs = sqrtf(g1 * e / rho);
             }
-            if (!isfinite((double)rho) || rho <= T(0)) bad = 1;
+            if (!isfinite(rho) || rho <= 0.0f) bad = 1;
             const float r1 = cs / dmin;
             float r2 = 0.0f, r3 = 0.0f;
             if (m.hasX) {
                 const T vc = f.vx[c], vp = f.vx[base + ip];
-                const float a = fabsf((float)((double)vc - v0r)), b = fabsf((float)((double)vp - v0r));
+                const float a = fabsf((float)sub_split(vc, v0hi, v0lo));
+                const float b = fabsf((float)sub_split(vp, v0hi, v0lo));
                 r2 = fmaxf(r2, fmaxf(a, b) / lx);
-                r3 = fmaxf(r3, av_ratef(m, (float)(vp - vc), lx));
-                if (!isfinite((double)vc)) bad = 1;
+                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), lx));
+                if (!isfinite((float)vc)) bad = 1;
             }
             if (m.hasY) {
                 const T vc = f.vy[c], vp = f.vy[c + m.sj];
                 r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) / ly);
-                r3 = fmaxf(r3, av_ratef(m, (float)(vp - vc), ly));
-                if (!isfinite((double)vc)) bad = 1;
+                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ly));
+                if (!isfinite((float)vc)) bad = 1;
             }
             if (m.hasZ) {
                 const T vc = f.vz[c], vp = f.vz[c + m.sk];
                 r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) / lz);
-                r3 = fmaxf(r3, av_ratef(m, (float)(vp - vc), lz));
-                if (!isfinite((double)vc)) bad = 1;
+                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), lz));
+                if (!isfinite((float)vc)) bad = 1;
             }
-            if (m.cq <= 0.0) r3 = 0.0f;
             const float s = r1 * r1 + r2 * r2 + r3 * r3 + r4 * r4;
             smax = fmaxf(smax, s);
         }
@@ -367,6 +371,7 @@ __global__ void __launch_bounds__(256) k_cfl_exact(MeshD m, Tab<T> tb, Fld<T> f,
         if (err) dt = 0.0;
         sc->err = err;
         sc->dt = dt;
+        sc->dtf = (float)dt;
         sc->counter = 0u;
     }
 }

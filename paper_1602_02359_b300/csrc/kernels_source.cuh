@@ -14,16 +14,14 @@ struct CellIdx {
     int i, j, k;
 };
 
+// Per-cell kernels run on a 3D grid: x covers the azimuth, y the rows and z
+// the planes of the augmented mesh (extra face row / plane included).
 __device__ __forceinline__ bool decode(const MeshD &m, CellIdx &c)
 {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long n = (long long)m.nx * (m.nyt + 1) * (m.nzt + 1);
-    if (tid >= n) return false;
-    c.i = (int)(tid % m.nx);
-    long long r = tid / m.nx;
-    c.j = (int)(r % (m.nyt + 1));
-    c.k = (int)(r / (m.nyt + 1));
-    return true;
+    c.i = blockIdx.x * blockDim.x + threadIdx.x;
+    c.j = blockIdx.y;
+    c.k = blockIdx.z;
+    return c.i < m.nx;
 }
 
 // Pressure from the equation of state (Eqs. eos1, eos2).
@@ -34,7 +32,7 @@ __device__ __forceinline__ T pressure(const MeshD &m, const Tab<T> &tb, const Fl
         T cs = tb.cs[ring];
         return cs * cs * f.rho[c];
     }
-    return T(m.gamma - 1.0) * f.e[c];
+    return tb.gm1 * f.e[c];
 }
 
 // Planet part of the potential at the centre of cell (i, ring): Plummer
@@ -47,10 +45,10 @@ template <typename T>
 __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i, int ring)
 {
     const T rm = tb.rma[ring];
-    const T d2 = rm * rm + tb.fra[ring] * tb.ps[i] + tb.z2[ring] + T(m.peps2);
+    const T d2 = rm * rm + tb.fra[ring] * tb.ps[i] + tb.z2[ring] + tb.peps2;
     T v;
-    if (sizeof(T) == 8) v = -T(m.pq) / sqrt(d2);
-    else v = -T(m.pq) * rsqrtf((float)d2);
+    if (sizeof(T) == 8) v = -tb.pq / sqrt(d2);
+    else v = -tb.pq * rsqrtf((float)d2);
     if (m.indirect) v += tb.qar[ring] * tb.pc[i];
     return v;
 }
@@ -63,16 +61,15 @@ __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i,
 template <typename T>
 __global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
-    const double dtd = sc->dt;
-    if (!(dtd > 0.0)) return;
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
     CellIdx ci;
     if (!decode(m, ci)) return;
-    const T dt = (T)dtd;
     const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
-    const T om = (T)m.omega;
+    const T om = tb.omega;
     const int im = i == 0 ? m.nx - 1 : i - 1;
     const int ip = i + 1 == m.nx ? 0 : i + 1;
     if (j < m.nyt && k < m.nzt) {
@@ -156,13 +153,12 @@ __device__ __forceinline__ T qvisc(T c2, T rho, T dv)
 template <typename T>
 __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
-    const double dtd = sc->dt;
-    if (!(dtd > 0.0)) return;
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
     CellIdx ci;
     if (!decode(m, ci)) return;
-    const T dt = (T)dtd;
-    const T c2 = (T)(m.cq * m.cq);
-    const bool av = m.cq > 0.0;
+    const T c2 = tb.cq2;
+    const bool av = m.has_av != 0;
     const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
@@ -258,7 +254,7 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
         div += tb.sz[fr + (m.nyt + 1)] * vzu - tb.sz[fr] * vzl;
     }
     div *= tb.vinv[ring];
-    const T th = T(0.5) * dt * T(m.gamma - 1.0) * div;
+    const T th = tb.half_gm1 * dt * div;
     out.e[c] = e * (T(1) - th) / (T(1) + th);
 }
 
@@ -329,13 +325,13 @@ struct ViscCtx {
         const T dvx_dy = (vx[c] - vx[c - m.sj]) / tb.dyc[j];
         T t;
         if (m.geom == CART) {
-            t = (vy[c] - vy[cm]) / T(m.dx) + dvx_dy;
+            t = (vy[c] - vy[cm]) / tb.dx + dvx_dy;
         } else if (m.geom == CYL) {
             const T rf = tb.yf[j];
-            t = dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf + (vy[c] - vy[cm]) / (rf * T(m.dx));
+            t = dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf + (vy[c] - vy[cm]) / (rf * tb.dx);
         } else {
             const T rf = tb.yf[j], sn = tb.szm[k];
-            t = (vy[c] - vy[cm]) / (rf * sn * T(m.dx)) + dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf;
+            t = (vy[c] - vy[cm]) / (rf * sn * tb.dx) + dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf;
         }
         return -rb * nb * t;
     }
@@ -348,12 +344,12 @@ struct ViscCtx {
         const T dzc = tb.zm[k] - tb.zm[k - 1];
         T t;
         if (m.geom == CART) {
-            t = (vz[c] - vz[cm]) / T(m.dx) + (vx[c] - vx[c - m.sk]) / dzc;
+            t = (vz[c] - vz[cm]) / tb.dx + (vx[c] - vx[c - m.sk]) / dzc;
         } else if (m.geom == CYL) {
-            t = (vx[c] - vx[c - m.sk]) / dzc + (vz[c] - vz[cm]) / (tb.ym[j] * T(m.dx));
+            t = (vx[c] - vx[c - m.sk]) / dzc + (vz[c] - vz[cm]) / (tb.ym[j] * tb.dx);
         } else {
             const T r = tb.ym[j], sf = tb.szf[k];
-            t = sf / r * (vx[c] / tb.szm[k] - vx[c - m.sk] / tb.szm[k - 1]) / dzc + (vz[c] - vz[cm]) / (r * sf * T(m.dx));
+            t = sf / r * (vx[c] / tb.szm[k] - vx[c - m.sk] / tb.szm[k - 1]) / dzc + (vz[c] - vz[cm]) / (r * sf * tb.dx);
         }
         return -rb * nb * t;
     }
@@ -376,19 +372,13 @@ struct ViscCtx {
     }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_visc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+template <typename T, typename S>
+__device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
+                                           T dt, int i, int j, int k, const S &V)
 {
-    const double dtd = sc->dt;
-    if (!(dtd > 0.0)) return;
-    CellIdx ci;
-    if (!decode(m, ci)) return;
-    const T dt = (T)dtd;
-    const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
-    const ViscCtx<T> V(m, tb, in);
-    const T dx = (T)m.dx;
+    const T dx = tb.dx;
     const T *rho = in.rho;
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
@@ -494,6 +484,79 @@ __global__ void __launch_bounds__(256) k_visc(MeshD m, Tab<T> tb, Fld<T> in, Fld
         }
         out.vz[c] = v;
     }
+}
+
+
+// Stresses read back from the arrays written by k_visc_tau.
+template <typename T>
+struct TauArr {
+    const MeshD &m;
+    const T *xx, *yy, *zz, *xy, *xz, *yz;
+    __device__ long long at(int i, int j, int k) const
+    {
+        return IX(m, i < 0 ? i + m.nx : (i >= m.nx ? i - m.nx : i), j, k);
+    }
+    __device__ void diag(int i, int j, int k, T &a, T &b, T &c) const
+    {
+        const long long o = at(i, j, k);
+        a = xx[o];
+        b = yy[o];
+        c = zz[o];
+    }
+    __device__ T txy(int i, int j, int k) const { return xy[at(i, j, k)]; }
+    __device__ T txz(int i, int j, int k) const { return xz[at(i, j, k)]; }
+    __device__ T tyz(int i, int j, int k) const { return yz[at(i, j, k)]; }
+};
+
+// Pass 1: every stress component once, diagonal ones on active cells and
+// the edge ones on the edges that interior and boundary faces need
+// (rows j0..j1, planes k0..k1).
+template <typename T>
+__global__ void __launch_bounds__(256) k_visc_tau(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> tau, const Scal *sc)
+{
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.nx) return;
+    const int j = m.j0 + blockIdx.y, k = m.k0 + blockIdx.z;   // rows j0..j1, planes k0..k1
+    const ViscCtx<T> V(m, tb, in);
+    const long long c = IX(m, i, j, k);
+    const bool jin = j < m.j1, kin = k < m.k1;
+    if (jin && kin) {
+        T a, b, d;
+        V.diag(i, j, k, a, b, d);
+        tau.q[0][c] = a;
+        tau.q[1][c] = b;
+        tau.q[2][c] = d;
+    }
+    if (m.hasY && kin) tau.q[3][c] = V.txy(i, j, k);
+    if (m.hasZ && jin) tau.q[4][c] = V.txz(i, j, k);
+    if (m.hasY && m.hasZ) tau.q[5][c] = V.tyz(i, j, k);
+}
+
+// Pass 2: the velocity update of Eqs. 75-77 from the stored stresses.
+template <typename T>
+__global__ void __launch_bounds__(256) k_visc_apply(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, QSet<T> tau,
+                                                    const Scal *sc)
+{
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
+    CellIdx ci;
+    if (!decode(m, ci)) return;
+    const TauArr<T> S{m, tau.q[0], tau.q[1], tau.q[2], tau.q[3], tau.q[4], tau.q[5]};
+    visc_apply(m, tb, in, out, dt, ci.i, ci.j, ci.k, S);
+}
+
+// Single-pass variant: every thread recomputes the stresses it needs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_visc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+{
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
+    CellIdx ci;
+    if (!decode(m, ci)) return;
+    const ViscCtx<T> V(m, tb, in);
+    visc_apply(m, tb, in, out, dt, ci.i, ci.j, ci.k, V);
 }
 
 }  // namespace fk

@@ -15,260 +15,461 @@ __device__ __forceinline__ T vl_slope(T qm, T q0, T qp, T dxm, T dxp)
     return dp * dm > T(0) ? T(2) * dp * dm / (dp + dm) : T(0);
 }
 
-// ---------------------------------------------------------------------------
-// X sweep, residual part, one CTA per ring (j,k), the ring staged in shared
-// memory:
-//  12a  momenta Pi-/+ of Eqs. 16-17 with the factors of Tab. "momenta";
-//  (i)  van Leer sweep at delta v = v_x - v0 (Eq. fargo1, Eq. 15; v0 = 0 for
-//       STANDARD transport), consistent transport (ratio to the density times
-//       the mass flux), all fluxes from the pre-sweep ring.
-// Ghost rings only get their momenta (the Y/Z sweeps read them).
-// Shared memory: nq ring arrays + 5 work arrays of nx values.
-// ---------------------------------------------------------------------------
+// a / b: IEEE division in FP64, the fast reciprocal-based division in FP32
+// (within 2 ulp; the harmonic mean below keeps its operands away from the
+// range where the fast form degrades).
+__device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+
+// The same slope with the inverse centre distances given.
 template <typename T>
+__device__ __forceinline__ T vl_slope_i(T qm, T q0, T qp, T idm, T idp)
+{
+    const T dp = (qp - q0) * idp, dm = (q0 - qm) * idm;
+    const T pr = dp * dm;
+    return pr > T(0) ? div_fast(T(2) * pr, dp + dm) : T(0);
+}
+
+// PPA (Sec. 3.4.1): monotonised-centred slope of Eq. 34 for cell values
+// (qm, q0, qp).
+template <typename T>
+__device__ __forceinline__ T ppa_dm(T qm, T q0, T qp)
+{
+    if (!((qp - q0) * (q0 - qm) > T(0))) return T(0);
+    const T d = T(0.5) * (qp - qm);
+    T mn = fmin(T(2) * fabs(q0 - qm), T(2) * fabs(qp - q0));
+    mn = fmin(mn, fabs(d));
+    return d > T(0) ? mn : -mn;
+}
+
+// PPA interface value through the face whose donor cell is the centre of
+// a[0..4] (cells d-2..d+2): parabolic interface values (Eq. 35), the
+// monotonisation of Eq. 36, then the xi-weighted average over the donor
+// region (pos: the face above the donor; otherwise the face below).
+template <typename T>
+__device__ __forceinline__ T ppa_face(const T a[5], T xi, bool pos)
+{
+    const T sixth = T(1.0 / 6.0);
+    const T dmm = ppa_dm(a[0], a[1], a[2]), dm0 = ppa_dm(a[1], a[2], a[3]), dmp = ppa_dm(a[2], a[3], a[4]);
+    const T q0 = a[2];
+    T l = a[1] + T(0.5) * (a[2] - a[1]) - (dm0 - dmm) * sixth;
+    T r = a[2] + T(0.5) * (a[3] - a[2]) - (dmp - dm0) * sixth;
+    if ((a[3] - q0) * (q0 - a[1]) <= T(0)) {
+        l = q0;
+        r = q0;
+    } else {
+        const T D = r - l, C = q0 - T(0.5) * (l + r);
+        if (D * C > D * D * sixth) l = T(3) * q0 - T(2) * r;
+        else if (-D * D * sixth > D * C) r = T(3) * q0 - T(2) * l;
+    }
+    const T w = xi * (T(1) - xi) * (T(2) * q0 - r - l);
+    return pos ? r + xi * (q0 - r) + w : l + xi * (q0 - l) + w;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ---------------------------------------------------------------------------
+// Ring kernels.  One CTA per ring (j,k); the ring's quantities are staged in
+// shared memory and every thread owns C consecutive cells.  For each
+// quantity a thread rebuilds, in registers, the ratios to the density of its
+// cells and their stencil halo, the slopes, the interface values and the
+// fluxes through its C+1 faces, and writes its C updated cells straight to
+// global memory; the only barriers are after the staging.  Consistent
+// transport: quantity q > 0 moves with the mass flux times the interface
+// ratio, all fluxes from the pre-sweep ring.
+// ---------------------------------------------------------------------------
+
+// X sweep, residual part (Sec. 3.4.1, Eq. fargo1; Eq. 15 with van Leer
+// slopes): the momenta of Eqs. 16-17 (Tab. "momenta") are built while the
+// ring is staged; the face velocity is delta v = v_x - v0 (v0 = 0 for
+// STANDARD transport).  Ghost rings only get their momenta written (the Y/Z
+// sweeps read them).  Shared memory: nq ring arrays, 1/rho, face velocity.
+template <typename T, int C>
 __global__ void __launch_bounds__(512) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
                                                      const Scal *sc)
 {
     extern __shared__ unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    const double dtd = sc->dt;
-    if (!(dtd > 0.0)) return;
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
     const int nx = m.nx, nq = out.nq;
     const int ring = blockIdx.x;
     const int j = ring % m.nyt, k = ring / m.nyt;
     const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
-    T *Q = sm;                       // nq * nx
-    T *Fr = sm + (size_t)nq * nx;    // mass flux on faces
-    T *Ft = Fr + nx;                 // flux of the current quantity
-    T *A = Ft + nx, *Cw = A + 2 * nx;
+    T *Q = sm;
+    T *RI = sm + (size_t)nq * nx;
+    T *V = RI + nx;
     const long long base = IX(m, 0, j, k);
-    const T R = tb.R[ring], w = R * R * T(m.omega), fz = tb.fz[ring];
+    const T R = tb.R[ring], w = R * R * tb.omega, fz = tb.fz[ring];
     const bool adi = !m.iso;
+    const bool sweep = active && m.hasX;
+    __shared__ T s_v0[2];
+    if (threadIdx.x == 0) {
+        const double v0r = m.fargo && sweep ? v0[ring] : 0.0;
+        s_v0[0] = (T)v0r;
+        s_v0[1] = (T)(v0r - (double)s_v0[0]);
+    }
+    __syncthreads();
+    const T v0hi = s_v0[0], v0lo = s_v0[1];
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const long long c = base + i;
         const int ip = i + 1 == nx ? 0 : i + 1;
         const T rho = in.rho[c];
+        const T vx = in.vx[c];
         int q = 0;
-        Q[(q++) * nx + i] = rho;
-        if (adi) Q[(q++) * nx + i] = in.e[c];
-        Q[(q++) * nx + i] = rho * (R * in.vx[c] + w);
-        Q[(q++) * nx + i] = rho * (R * in.vx[base + ip] + w);
+        T val[8];
+        val[q++] = rho;
+        if (adi) val[q++] = in.e[c];
+        val[q++] = rho * (R * vx + w);
+        val[q++] = rho * (R * in.vx[base + ip] + w);
         if (m.hasY) {
-            Q[(q++) * nx + i] = rho * in.vy[c];
-            Q[(q++) * nx + i] = rho * in.vy[c + m.sj];
+            val[q++] = rho * in.vy[c];
+            val[q++] = rho * in.vy[c + m.sj];
         }
         if (m.hasZ) {
-            Q[(q++) * nx + i] = rho * (fz * in.vz[c]);
-            Q[(q++) * nx + i] = rho * (fz * in.vz[c + m.sk]);
+            val[q++] = rho * (fz * in.vz[c]);
+            val[q++] = rho * (fz * in.vz[c + m.sk]);
+        }
+        if (sweep) {
+#pragma unroll
+            for (int s = 0; s < 8; s++)
+                if (s < q) Q[s * nx + i] = val[s];
+            RI[i] = T(1) / rho;
+            V[i] = sub_split(vx, v0hi, v0lo);
+        } else {
+#pragma unroll
+            for (int s = 0; s < 8; s++)
+                if (s < q) out.q[s][c] = val[s];
         }
     }
+    if (!sweep) return;
     __syncthreads();
-    if (active && m.hasX) {
-        const double v0r = m.fargo ? v0[ring] : 0.0;
-        const T dt = (T)dtd;
-        const T dX = tb.lenx[ring], S = tb.sx[ring], Vi = tb.vinv[ring];
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) Cw[i] = (T)((double)in.vx[base + i] - v0r);
-        __syncthreads();
-        for (int q = 0; q < nq; q++) {
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) A[i] = q == 0 ? Q[i] : Q[q * nx + i] / Q[i];
-            __syncthreads();
-            T *F = q == 0 ? Fr : Ft;
-            for (int f = threadIdx.x; f < nx; f += blockDim.x) {
-                const T v = Cw[f];
-                const int d = v >= T(0) ? (f == 0 ? nx - 1 : f - 1) : f;
-                const int dm = d == 0 ? nx - 1 : d - 1, dp = d + 1 == nx ? 0 : d + 1;
-                const T a = vl_slope(A[dm], A[d], A[dp], dX, dX);
-                const T st = v >= T(0) ? A[d] + a * (dX - v * dt) / T(2) : A[d] - a * (dX + v * dt) / T(2);
-                F[f] = q == 0 ? v * st * S : Fr[f] * st;
-            }
-            __syncthreads();
-            if (q > 0) {
-                for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-                    const int ip = i + 1 == nx ? 0 : i + 1;
-                    Q[q * nx + i] -= dt * Vi * (Ft[ip] - Ft[i]);
-                }
-                __syncthreads();
-            }
+    const T dX = tb.lenx[ring], S = tb.sx[ring];
+    const T idX = T(1) / dX;
+    const T dtVi = dt * tb.vinv[ring];
+    const int i0 = threadIdx.x * C;
+    if (i0 >= nx) return;
+    const int cnt = min(C, nx - i0);
+    T vf[C + 1], F0[C + 1];
+#pragma unroll
+    for (int u = 0; u <= C; u++) vf[u] = V[wrapi(i0 + u, nx)];
+    for (int q = 0; q < nq; q++) {
+        const T *Qq = Q + (size_t)q * nx;
+        T a[C + 4];   // ratios of cells i0-2 .. i0+C+1
+#pragma unroll
+        for (int s = 0; s < C + 4; s++) {
+            const int ii = wrapi(i0 - 2 + s, nx);
+            a[s] = q == 0 ? Qq[ii] : Qq[ii] * RI[ii];
         }
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            const int ip = i + 1 == nx ? 0 : i + 1;
-            Q[i] -= dt * Vi * (Fr[ip] - Fr[i]);
+        T sl[C + 2];  // van Leer slopes of cells i0-1 .. i0+C
+#pragma unroll
+        for (int s = 0; s < C + 2; s++) sl[s] = vl_slope_i(a[s], a[s + 1], a[s + 2], idX, idX);
+        T F[C + 1];
+#pragma unroll
+        for (int u = 0; u <= C; u++) {
+            const T v = vf[u];
+            // donor cell i0+u-1 (v >= 0) or i0+u: index s in a[] = donor - (i0 - 2)
+            const T stv = v >= T(0) ? a[u + 1] + sl[u] * (dX - v * dt) * T(0.5)
+                                    : a[u + 2] - sl[u + 1] * (dX + v * dt) * T(0.5);
+            if (q == 0) F0[u] = v * stv * S;
+            F[u] = q == 0 ? F0[u] : F0[u] * stv;
         }
-        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < C; u++)
+            if (u < cnt) out.q[q][base + i0 + u] = Qq[i0 + u] - dtVi * (F[u + 1] - F[u]);
     }
-    for (int q = 0; q < nq; q++)
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) out.q[q][base + i] = Q[q * nx + i];
 }
 
-// ---------------------------------------------------------------------------
 // Uniform orbital step of each active ring (Sec. 3.4.1, Eqs. fargo2, 28-33),
-// applied after the Y and Z sweeps, in place, one CTA per ring:
+// applied after the Y and Z sweeps, in place:
 //  (ii)  circular shift by N = E(v0 dt / dX) (Eq. 32): the ring is rotated
-//        while it is copied into shared memory;
+//        while it is staged in shared memory;
 //  (iii) fractional step at xi = v0 dt/dX - N with PPA interface values
 //        (Eqs. 34-36 and the xi-weighted value of Sec. 3.4.1), consistent
 //        transport, in the same pass.
-// N and xi are FP64, evaluated with round-to-nearest intrinsics.
-// ---------------------------------------------------------------------------
-template <typename T>
+// N and xi are FP64 (round-to-nearest intrinsics), once per CTA.
+template <typename T, int C>
 __global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, const Scal *sc)
 {
     extern __shared__ unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    const double dtd = sc->dt;
-    if (!(dtd > 0.0)) return;
+    const T dtT = step_dt<T>(sc);
+    if (!(dtT > T(0))) return;
     const int nx = m.nx, nq = qs.nq;
     const int r = blockIdx.x;
     const int ny = m.j1 - m.j0;
     const int j = m.j0 + r % ny, k = m.k0 + r / ny;
     const int ring = k * m.nyt + j;
     const long long base = IX(m, 0, j, k);
-    const double v0r = v0[ring];
-    const double X = __ddiv_rn(__dmul_rn(v0r, dtd), tb.lx[ring]);
-    const long long N = llround(X);
-    const double xs = __dsub_rn(X, (double)N);
-    const int Nm = (int)(((N % nx) + nx) % nx);
-    if (Nm == 0 && xs == 0.0) return;
+    __shared__ int s_N;
+    __shared__ T s_x[2];
+    if (threadIdx.x == 0) {
+        const double dtd = sc->dt;
+        const double X = __ddiv_rn(__dmul_rn(v0[ring], dtd), tb.lx[ring]);
+        const long long N = llround(X);
+        const double xs = __dsub_rn(X, (double)N);
+        s_N = (int)(((N % nx) + nx) % nx);
+        s_x[0] = (T)xs;
+        s_x[1] = (T)(xs * tb.lx[ring] / dtd);
+    }
+    __syncthreads();
+    const int Nm = s_N;
+    const T xsT = s_x[0];
+    if (Nm == 0 && xsT == T(0)) return;
     T *Q = sm;
-    T *Fr = sm + (size_t)nq * nx;
-    T *Ft = Fr + nx;
-    T *A = Ft + nx, *B = A + nx, *Cw = B + nx;
+    T *RI = sm + (size_t)nq * nx;
     for (int q = 0; q < nq; q++)
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             int s = i - Nm;
             if (s < 0) s += nx;
-            Q[q * nx + i] = qs.q[q][base + s];
+            const T v = qs.q[q][base + s];
+            Q[q * nx + i] = v;
+            if (q == 0) RI[i] = T(1) / v;
         }
     __syncthreads();
-    if (xs != 0.0) {
-        const T dt = (T)dtd;
-        const T S = tb.sx[ring], Vi = tb.vinv[ring];
-        const T vR = (T)(xs * tb.lx[ring] / dtd);
-        const T xi = (T)fabs(xs);
-        const bool pos = xs >= 0.0;
-        for (int q = 0; q < nq; q++) {
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) A[i] = q == 0 ? Q[i] : Q[q * nx + i] / Q[i];
-            __syncthreads();
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-                const T qm = A[i == 0 ? nx - 1 : i - 1], q0 = A[i], qp = A[i + 1 == nx ? 0 : i + 1];
-                T dmv = T(0);
-                if ((qp - q0) * (q0 - qm) > T(0)) {
-                    const T d = T(0.5) * (qp - qm);
-                    T mn = fmin(T(2) * fabs(q0 - qm), T(2) * fabs(qp - q0));
-                    mn = fmin(mn, fabs(d));
-                    dmv = d > T(0) ? mn : -mn;
-                }
-                B[i] = dmv;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-                const int ip = i + 1 == nx ? 0 : i + 1;
-                Cw[i] = A[i] + T(0.5) * (A[ip] - A[i]) - (B[ip] - B[i]) / T(6);
-            }
-            __syncthreads();
-            T *F = q == 0 ? Fr : Ft;
-            for (int f = threadIdx.x; f < nx; f += blockDim.x) {
-                const int d = pos ? (f == 0 ? nx - 1 : f - 1) : f;
-                const int dm = d == 0 ? nx - 1 : d - 1, dp = d + 1 == nx ? 0 : d + 1;
-                const T qm = A[dm], q0 = A[d], qp = A[dp];
-                T l = Cw[dm], rr = Cw[d];
-                if ((qp - q0) * (q0 - qm) <= T(0)) {
-                    l = q0;
-                    rr = q0;
-                } else {
-                    const T D = rr - l, C = q0 - T(0.5) * (l + rr);
-                    if (D * C > D * D / T(6)) l = T(3) * q0 - T(2) * rr;
-                    else if (-D * D / T(6) > D * C) rr = T(3) * q0 - T(2) * l;
-                }
-                const T st = pos ? rr + xi * (q0 - rr) + xi * (T(1) - xi) * (T(2) * q0 - rr - l)
-                                 : l + xi * (q0 - l) + xi * (T(1) - xi) * (T(2) * q0 - rr - l);
-                F[f] = q == 0 ? vR * st * S : Fr[f] * st;
-            }
-            __syncthreads();
-            if (q > 0) {
-                for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-                    const int ip = i + 1 == nx ? 0 : i + 1;
-                    Q[q * nx + i] -= dt * Vi * (Ft[ip] - Ft[i]);
-                }
-                __syncthreads();
-            }
-        }
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            const int ip = i + 1 == nx ? 0 : i + 1;
-            Q[i] -= dt * Vi * (Fr[ip] - Fr[i]);
-        }
-        __syncthreads();
+    const int i0 = threadIdx.x * C;
+    if (xsT == T(0)) {   // a pure shift
+        for (int q = 0; q < nq; q++)
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) qs.q[q][base + i] = Q[q * nx + i];
+        return;
     }
-    for (int q = 0; q < nq; q++)
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) qs.q[q][base + i] = Q[q * nx + i];
+    if (i0 >= nx) return;
+    const int cnt = min(C, nx - i0);
+    const T S = tb.sx[ring];
+    const T dtVi = dtT * tb.vinv[ring];
+    const T vR = s_x[1];
+    const bool pos = xsT >= T(0);
+    const T xi = pos ? xsT : -xsT;
+    const T sixth = T(1.0 / 6.0);
+    T F0[C + 1];
+    for (int q = 0; q < nq; q++) {
+        const T *Qq = Q + (size_t)q * nx;
+        T a[C + 6];   // ratios of cells i0-3 .. i0+C+2
+#pragma unroll
+        for (int s = 0; s < C + 6; s++) {
+            const int ii = wrapi(i0 - 3 + s, nx);
+            a[s] = q == 0 ? Qq[ii] : Qq[ii] * RI[ii];
+        }
+        T dm[C + 4];  // Eq. 34 slopes of cells i0-2 .. i0+C+1
+#pragma unroll
+        for (int s = 0; s < C + 4; s++) dm[s] = ppa_dm(a[s], a[s + 1], a[s + 2]);
+        T qr[C + 3];  // Eq. 35 right interface value of cells i0-2 .. i0+C
+#pragma unroll
+        for (int s = 0; s < C + 3; s++) qr[s] = a[s + 1] + T(0.5) * (a[s + 2] - a[s + 1]) - (dm[s + 1] - dm[s]) * sixth;
+        T F[C + 1];
+#pragma unroll
+        for (int u = 0; u <= C; u++) {
+            // donor cell d = i0+u-1 (xi >= 0) or i0+u; its value a[d-(i0-3)],
+            // its left value qr[d-1-(i0-2)], its right value qr[d-(i0-2)]
+            const int dd = pos ? u - 1 : u;
+            const T q0 = a[dd + 3], qm = a[dd + 2], qp = a[dd + 4];
+            T l = qr[dd + 1], rr = qr[dd + 2];
+            if ((qp - q0) * (q0 - qm) <= T(0)) {
+                l = q0;
+                rr = q0;
+            } else {
+                const T D = rr - l, Cc = q0 - T(0.5) * (l + rr);
+                if (D * Cc > D * D * sixth) l = T(3) * q0 - T(2) * rr;
+                else if (-D * D * sixth > D * Cc) rr = T(3) * q0 - T(2) * l;
+            }
+            const T wgt = xi * (T(1) - xi) * (T(2) * q0 - rr - l);
+            const T stv = pos ? rr + xi * (q0 - rr) + wgt : l + xi * (q0 - l) + wgt;
+            if (q == 0) F0[u] = vR * stv * S;
+            F[u] = q == 0 ? F0[u] : F0[u] * stv;
+        }
+#pragma unroll
+        for (int u = 0; u < C; u++)
+            if (u < cnt) qs.q[q][base + i0 + u] = Qq[i0 + u] - dtVi * (F[u + 1] - F[u]);
+    }
+}
+
+template <typename T, int C>
+static void launch_tx_c(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
+                        const Scal *sc, size_t smem, cudaStream_t s)
+{
+    const int threads = ((m.nx + C - 1) / C + 31) / 32 * 32;
+    k_transport_x<T, C><<<m.nyt * m.nzt, threads, smem, s>>>(m, tb, in, out, v0, sc);
+}
+template <typename T, int C>
+static void launch_orb_c(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, const Scal *sc,
+                         int nrings, size_t smem, cudaStream_t s)
+{
+    const int threads = ((m.nx + C - 1) / C + 31) / 32 * 32;
+    k_orbital<T, C><<<nrings, threads, smem, s>>>(m, tb, qs, v0, sc);
+}
+
+// Cells per thread of the ring kernels: the smallest of 1, 2, 3, 4, 8 that
+// keeps a ring within 512 threads.
+static inline int ring_chunk(int nx)
+{
+    const int cs[5] = {1, 2, 3, 4, 8};
+    for (int c : cs)
+        if ((nx + c - 1) / c <= 512) return c;
+    return 0;
+}
+
+template <typename T>
+static void launch_tx(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
+                      const Scal *sc, size_t smem, cudaStream_t s)
+{
+    switch (ring_chunk(m.nx)) {
+    case 1: launch_tx_c<T, 1>(m, tb, in, out, v0, sc, smem, s); break;
+    case 2: launch_tx_c<T, 2>(m, tb, in, out, v0, sc, smem, s); break;
+    case 3: launch_tx_c<T, 3>(m, tb, in, out, v0, sc, smem, s); break;
+    case 4: launch_tx_c<T, 4>(m, tb, in, out, v0, sc, smem, s); break;
+    default: launch_tx_c<T, 8>(m, tb, in, out, v0, sc, smem, s); break;
+    }
+}
+template <typename T>
+static void launch_orb(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, const Scal *sc,
+                       int nrings, size_t smem, cudaStream_t s)
+{
+    switch (ring_chunk(m.nx)) {
+    case 1: launch_orb_c<T, 1>(m, tb, qs, v0, sc, nrings, smem, s); break;
+    case 2: launch_orb_c<T, 2>(m, tb, qs, v0, sc, nrings, smem, s); break;
+    case 3: launch_orb_c<T, 3>(m, tb, qs, v0, sc, nrings, smem, s); break;
+    case 4: launch_orb_c<T, 4>(m, tb, qs, v0, sc, nrings, smem, s); break;
+    default: launch_orb_c<T, 8>(m, tb, qs, v0, sc, nrings, smem, s); break;
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Y and Z sweeps (Eqs. 1D-advection-Y/Z): one thread per cell, fluxes through
-// its lower and upper face recomputed from the five cells around it.  Reads
-// `in` (the values of the previous sweep, ghosts included) and writes `out`;
-// with copy_ghosts set, cells outside the active box are copied so that the
-// next sweep finds every ghost it needs.
+// Y and Z sweeps (Eqs. 1D-advection-Y/Z) as marching pencils.  One thread
+// owns a segment of one column along the sweep axis (fixed i and transverse
+// index) and walks it with a five-row register window: at cell p it holds
+// the ratios Q/rho of rows p-2..p+2, the van Leer slope of cell p from the
+// previous row, and the flux through face p (lower), computes the slope of
+// cell p+1, the interface values and fluxes through face p+1 (upper), updates
+// cell p and slides the window.  Each face flux and slope is computed once
+// and each value is loaded once; a warp reads 32 consecutive azimuths of a
+// row, so every load is coalesced.  Consistent transport (ratio to density
+// times the mass flux), all fluxes from the pre-sweep values.  With
+// copy_ghosts set, cells outside the active box are copied to `out` so that
+// the next sweep finds every ghost it needs.
 // ---------------------------------------------------------------------------
-template <typename T, int AXIS>
-__global__ void __launch_bounds__(256) k_transport_yz(MeshD m, Tab<T> tb, QSet<T> in, QSet<T> out, const T *vel,
-                                                      const Scal *sc, int copy_ghosts)
+template <typename T, int AXIS, int NQ>
+__global__ void __launch_bounds__(128, 6) k_sweep(MeshD m, Tab<T> tb, QSet<T> in, QSet<T> out, const T *vel,
+                                               const Scal *sc, int copy_ghosts, int seglen)
 {
-    const double dtd = sc->dt;
-    if (!(dtd > 0.0)) return;
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long n = (long long)m.nx * m.nyt * m.nzt;
-    if (tid >= n) return;
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
+    const int n2t = AXIS == 1 ? m.nzt : m.nyt;           // transverse extent (ghosts included)
+    const int p0 = AXIS == 1 ? m.j0 : m.k0, pN = AXIS == 1 ? m.j1 : m.k1;
+    const int nalong = AXIS == 1 ? m.nyt : m.nzt;
+    const int nseg = (pN - p0 + seglen - 1) / seglen;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)m.nx * n2t * nseg) return;
     const int i = (int)(tid % m.nx);
-    const long long rr = tid / m.nx;
-    const int j = (int)(rr % m.nyt), k = (int)(rr / m.nyt);
-    const long long c = IX(m, i, j, k);
-    const int nq = in.nq;
-    const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
-    if (!active) {
-        if (copy_ghosts)
-            for (int q = 0; q < nq; q++) out.q[q][c] = in.q[q][c];
+    const long long r = tid / m.nx;
+    const int c2 = (int)(r % n2t), seg = (int)(r / n2t);
+    const bool tact = AXIS == 1 ? (c2 >= m.k0 && c2 < m.k1) : (c2 >= m.j0 && c2 < m.j1);
+    const long long st = AXIS == 1 ? m.sj : m.sk;
+    const long long base = AXIS == 1 ? IX(m, i, 0, c2) : IX(m, i, c2, 0);
+    if (!tact) {
+        if (copy_ghosts && seg == 0)
+            for (int p = 0; p < nalong; p++)
+                for (int q = 0; q < NQ; q++) out.q[q][base + p * st] = in.q[q][base + p * st];
         return;
     }
-    const T dt = (T)dtd;
-    const int ring = k * m.nyt + j;
-    const long long st = AXIS == 1 ? m.sj : m.sk;
-    const int p = AXIS == 1 ? j : k;      // index along the sweep
-    // centre distance across face f and width of cell d along the sweep
-    auto cdist = [&](int f) -> T {
-        if (AXIS == 1) return tb.dyc[f];
-        return tb.dzc[f * m.nyt + j];
+    if (copy_ghosts) {
+        if (seg == 0)
+            for (int p = 0; p < p0; p++)
+                for (int q = 0; q < NQ; q++) out.q[q][base + p * st] = in.q[q][base + p * st];
+        if (seg == nseg - 1)
+            for (int p = pN; p < nalong; p++)
+                for (int q = 0; q < NQ; q++) out.q[q][base + p * st] = in.q[q][base + p * st];
+    }
+    const int ps = p0 + seg * seglen, pe = min(ps + seglen, pN);
+    auto ring_of = [&](int p) { return AXIS == 1 ? c2 * m.nyt + p : p * m.nyt + c2; };
+    auto icd = [&](int f) -> T { return AXIS == 1 ? tb.idyc[f] : tb.idzc[f * m.nyt + c2]; };
+    auto width = [&](int d) -> T { return AXIS == 1 ? tb.dy[d] : tb.lenz[d * m.nyt + c2]; };
+    auto area = [&](int f) -> T { return AXIS == 1 ? tb.sy[c2 * (m.nyt + 1) + f] : tb.sz[f * (m.nyt + 1) + c2]; };
+    auto ratios = [&](const T *raw, T *out_r) {
+        const T ri = T(1) / raw[0];
+        out_r[0] = raw[0];
+#pragma unroll
+        for (int q = 1; q < NQ; q++) out_r[q] = raw[q] * ri;
     };
-    auto width = [&](int d) -> T {
-        if (AXIS == 1) return tb.dy[d];
-        return tb.lenz[d * m.nyt + j];
+    auto load_raw = [&](int row, T *raw) {
+        const long long c = base + (long long)row * st;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) raw[q] = in.q[q][c];
     };
-    const int fr = k * (m.nyt + 1) + j;
-    const T Slo = AXIS == 1 ? tb.sy[fr] : tb.sz[fr];
-    const T Sup = AXIS == 1 ? tb.sy[fr + 1] : tb.sz[fr + m.nyt + 1];
-    const T vlo = vel[c], vup = vel[c + st];
-    const T Vi = tb.vinv[ring];
-    // stencil cells p-2 .. p+2 -> s = 0..4
-    T r5[5];
-    for (int s = 0; s < 5; s++) r5[s] = in.q[0][c + (s - 2) * st];
-    // donor index (0..4) for each face, and its slope/width
-    const int dlo = vlo >= T(0) ? 1 : 2, dup = vup >= T(0) ? 2 : 3;
-    const T cdlo_m = cdist(p - 2 + dlo), cdlo_p = cdist(p - 1 + dlo);
-    const T cdup_m = cdist(p - 2 + dup), cdup_p = cdist(p - 1 + dup);
-    const T wlo = width(p - 2 + dlo), wup = width(p - 2 + dup);
-    auto face = [&](const T *f5, int d, T v, T cdm, T cdp, T wd) -> T {
-        const T a = vl_slope(f5[d - 1], f5[d], f5[d + 1], cdm, cdp);
-        return v >= T(0) ? f5[d] + a * (wd - v * dt) / T(2) : f5[d] - a * (wd + v * dt) / T(2);
-    };
-    const T F0lo = vlo * face(r5, dlo, vlo, cdlo_m, cdlo_p, wlo) * Slo;
-    const T F0up = vup * face(r5, dup, vup, cdup_m, cdup_p, wup) * Sup;
-    out.q[0][c] = r5[2] - dt * Vi * (F0up - F0lo);
-    for (int q = 1; q < nq; q++) {
-        T f5[5];
-        for (int s = 0; s < 5; s++) f5[s] = in.q[q][c + (s - 2) * st] / r5[s];
-        const T Flo = F0lo * face(f5, dlo, vlo, cdlo_m, cdlo_p, wlo);
-        const T Fup = F0up * face(f5, dup, vup, cdup_m, cdup_p, wup);
-        out.q[q][c] = in.q[q][c] - dt * Vi * (Fup - Flo);
+    // window: ratios (q = 0: the density) of rows p, p+1, p+2
+    T R0[NQ], R1[NQ], R2[NQ], aP[NQ], Flo[NQ];
+    {
+        T raw[NQ], Rm2[NQ], Rm1[NQ];
+        load_raw(ps - 2, raw); ratios(raw, Rm2);
+        load_raw(ps - 1, raw); ratios(raw, Rm1);
+        load_raw(ps, raw); ratios(raw, R0);
+        load_raw(ps + 1, raw); ratios(raw, R1);
+        load_raw(ps + 2, raw); ratios(raw, R2);
+        const T d0 = icd(ps - 1), d1 = icd(ps), d2 = icd(ps + 1);
+        const T v = vel[base + (long long)ps * st];
+        const T wl = width(ps - 1), wr = width(ps);
+        const T S = area(ps);
+        T F0 = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const T am = vl_slope_i(Rm2[q], Rm1[q], R0[q], d0, d1);
+            const T a0 = vl_slope_i(Rm1[q], R0[q], R1[q], d1, d2);
+            aP[q] = a0;
+            const T stv = v >= T(0) ? Rm1[q] + am * (wl - v * dt) * T(0.5) : R0[q] - a0 * (wr + v * dt) * T(0.5);
+            if (q == 0) F0 = v * stv * S;
+            Flo[q] = q == 0 ? F0 : F0 * stv;
+        }
+    }
+    for (int p = ps; p < pe; p++) {
+        T pre[NQ];
+        const bool more = p + 1 < pe;
+        if (more) load_raw(p + 3, pre);       // issued before the arithmetic of this row
+        const long long c = base + (long long)p * st;
+        const T v = vel[c + st];
+        const T dn = icd(p + 1), dnn = icd(p + 2);
+        const T wp = width(p), wn = width(p + 1);
+        const T S = area(p + 1);
+        const T dtVi = dt * tb.vinv[ring_of(p)];
+        const T rho = R0[0];
+        T F0 = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const T aN = vl_slope_i(R0[q], R1[q], R2[q], dn, dnn);
+            const T stv = v >= T(0) ? R0[q] + aP[q] * (wp - v * dt) * T(0.5) : R1[q] - aN * (wn + v * dt) * T(0.5);
+            if (q == 0) F0 = v * stv * S;
+            const T Fup = q == 0 ? F0 : F0 * stv;
+            const T Q = q == 0 ? rho : R0[q] * rho;
+            out.q[q][c] = Q - dtVi * (Fup - Flo[q]);
+            Flo[q] = Fup;
+            aP[q] = aN;
+        }
+        if (more) {
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                R0[q] = R1[q];
+                R1[q] = R2[q];
+            }
+            ratios(pre, R2);
+        }
+    }
+}
+
+template <typename T, int AXIS>
+static void launch_sweep(const MeshD &m, const Tab<T> &tb, const QSet<T> &in, const QSet<T> &out, const T *vel,
+                         const Scal *sc, int copy_ghosts, cudaStream_t s)
+{
+    const int np = AXIS == 1 ? m.j1 - m.j0 : m.k1 - m.k0;
+    const int n2t = AXIS == 1 ? m.nzt : m.nyt;
+    const int seglen = np > 48 ? 32 : np;
+    const int nseg = (np + seglen - 1) / seglen;
+    const long long n = (long long)m.nx * n2t * nseg;
+    const unsigned g = (unsigned)((n + 127) / 128);
+    switch (in.nq) {
+    case 3: k_sweep<T, AXIS, 3><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
+    case 4: k_sweep<T, AXIS, 4><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
+    case 5: k_sweep<T, AXIS, 5><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
+    case 6: k_sweep<T, AXIS, 6><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
+    case 7: k_sweep<T, AXIS, 7><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
+    default: k_sweep<T, AXIS, 8><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
     }
 }
 
@@ -283,13 +484,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin, Fld<T> vsrc, Fld<T> state,
                                                 Scal *sc, int copy_scalars)
 {
-    const double dtd = sc->dt;
-    if (!(dtd > 0.0)) return;
+    const T dtT = step_dt<T>(sc);
+    if (!(dtT > T(0))) return;
     CellIdx ci;
     if (!decode(m, ci)) return;
     const int i = ci.i, j = ci.j, k = ci.k;
     if (i == 0 && j == 0 && k == 0) {
-        sc->t = sc->t + dtd;
+        sc->t = sc->t + sc->dt;
         sc->nstep += 1;
     }
     const long long c = IX(m, i, j, k);
@@ -301,7 +502,7 @@ __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin,
         T v = vsrc.vx[c];
         if (jact && kact) {
             const long long cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
-            const T R = tb.R[ring], w = R * R * T(m.omega);
+            const T R = tb.R[ring], w = R * R * tb.omega;
             v = ((fin.q[o + 1][cm] + fin.q[o][c]) / (rho[cm] + rho[c]) - w) / R;
         }
         state.vx[c] = v;

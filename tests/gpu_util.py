@@ -66,3 +66,19 @@ def compare_state(w, gpu_state, ora_state, tol, norm=rel_linf):
     bad = {k: v for k, v in worst.items() if not v <= tol}
     assert not bad, f"parity beyond {tol}: {worst}"
     return worst
+
+
+def momentum_density(w, st):
+    """Cell-centred momentum density rho (v_{-1/2} + v_{+1/2})/2 of every
+    active direction, stacked (the zone-centred momentum of Eq. 19)."""
+    rho = w.active(st["rho"]).astype(np.float64)
+    out = []
+    vx = w.active(st["vx"]).astype(np.float64)
+    out.append(rho * 0.5 * (vx + np.roll(vx, -1, axis=2)))
+    if w.ny > 1:
+        vy = st["vy"][w.gz:w.gz + w.nz, w.gy:w.gy + w.ny + 1].astype(np.float64)
+        out.append(rho * 0.5 * (vy[:, :-1] + vy[:, 1:]))
+    if w.nz > 1:
+        vz = st["vz"][w.gz:w.gz + w.nz + 1, w.gy:w.gy + w.ny].astype(np.float64)
+        out.append(rho * 0.5 * (vz[:-1] + vz[1:]))
+    return np.stack(out)
