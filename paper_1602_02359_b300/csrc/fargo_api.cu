@@ -63,7 +63,56 @@ struct fargo_ctx {
     size_t tx_smem = 0;
     int tx_threads = 256;
     std::vector<double> yfaces_store, zfaces_store;
+    SweepMaps mapsY{}, mapsZ{};   // tensor maps of the Y and Z sweeps of the step
 };
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 3D map of one field array (nx, ny_t+1, nz_t+1; row pitch in bytes), box =
+// one row segment of 512 bytes.  Out-of-range azimuths read as zero.
+template <typename T>
+static int encode_field_map(const fargo_ctx *c, CUtensorMap *map, const T *ptr)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return FARGO_ERR_CUDA;
+    const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->nyt + 1, (cuuint64_t)c->nzt + 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(T), (cuuint64_t)c->m.sk * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)TmaTile<T>::TW, 1, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                    (void *)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FARGO_OK : FARGO_ERR_CUDA;
+}
+
+template <typename T>
+static int encode_sweep_maps(const fargo_ctx *c, SweepMaps *mp, const QSet<T> &in, const QSet<T> &ghost,
+                             const T *vel)
+{
+    int rc;
+    for (int q = 0; q < in.nq; q++) {
+        if ((rc = encode_field_map<T>(c, &mp->qin[q], in.q[q]))) return rc;
+        if ((rc = encode_field_map<T>(c, &mp->qg[q], ghost.q[q]))) return rc;
+    }
+    return encode_field_map<T>(c, &mp->vel, vel);
+}
 
 static const char *g_errstr[] = {"ok", "bad argument", "out of memory", "CUDA error", "non-finite state",
                                  "Courant step not positive", "size mismatch or kernel limit", "barrier timeout",
@@ -406,12 +455,12 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     MARK("transport_x");
     QSet<T> cur = x_out ? qb : qa, oth = x_out ? qa : qb;
     if (m.hasY) {
-        launch_sweep<T, 1>(m, b.tab, cur, oth, vsrc.vy, c->sc, m.hasZ ? 1 : 0, s);
+        launch_sweep_tma<T, 1>(m, b.tab, c->mapsY, oth, c->sc, cur.nq, s);
         MARK("transport_y");
         QSet<T> t = cur; cur = oth; oth = t;
     }
     if (m.hasZ) {
-        launch_sweep<T, 2>(m, b.tab, cur, oth, vsrc.vz, c->sc, 0, s);
+        launch_sweep_tma<T, 2>(m, b.tab, c->mapsZ, oth, c->sc, cur.nq, s);
         MARK("transport_z");
         QSet<T> t = cur; cur = oth; oth = t;
     }
@@ -447,6 +496,34 @@ static int launch_step(fargo_ctx *c)
         CK(cudaGraphInstantiate(&c->gexec, g, 0));
     }
     CK(cudaGraphLaunch(c->gexec, c->stream));
+    return FARGO_OK;
+}
+
+// Tensor maps of the step's Y and Z sweeps, following the buffer routing of
+// enqueue_step: the X sweep is in place when an even number of Y/Z sweeps
+// follows it; the Z sweep after a Y sweep reads its ghost planes from the
+// Y sweep's input (the Y sweep writes active cells only).
+template <typename T>
+static int build_sweep_maps(fargo_ctx *c, Buffers<T> &b)
+{
+    const MeshD &m = c->m;
+    QSet<T> qa = qset<T>(c, b.A.rho, b.A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);
+    const T *vy = m.has_nu ? b.vB[1] : b.A.vy;
+    const T *vz = m.has_nu ? b.vB[2] : b.A.vz;
+    const bool x_out = ((m.hasY + m.hasZ) % 2) == 1;
+    QSet<T> cur = x_out ? qb : qa, oth = x_out ? qa : qb;
+    int rc;
+    QSet<T> before_y = cur;
+    if (m.hasY) {
+        if ((rc = encode_sweep_maps<T>(c, &c->mapsY, cur, cur, vy))) return rc;
+        QSet<T> t = cur; cur = oth; oth = t;
+    }
+    if (m.hasZ) {
+        if ((rc = encode_sweep_maps<T>(c, &c->mapsZ, cur, m.hasY ? before_y : cur, vz))) return rc;
+    }
+    const int nq = cur.nq;
+    CK((sweep_tma_attrs<T, 1>(nq)));
+    CK((sweep_tma_attrs<T, 2>(nq)));
     return FARGO_OK;
 }
 
@@ -568,9 +645,11 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     if (c->prec == FARGO_F64) {
         if ((rc = alloc_fields<double>(c, c->b64))) goto fail;
         if ((rc = set_kernel_attrs<double>(c))) goto fail;
+        if ((rc = build_sweep_maps<double>(c, c->b64))) goto fail;
     } else {
         if ((rc = alloc_fields<float>(c, c->b32))) goto fail;
         if ((rc = set_kernel_attrs<float>(c))) goto fail;
+        if ((rc = build_sweep_maps<float>(c, c->b32))) goto fail;
     }
     {
         Scal s0{};
@@ -664,6 +743,7 @@ static int err_code(int flags)
 {
     if (flags & 1) return FARGO_ERR_NONFINITE;
     if (flags & 2) return FARGO_ERR_DT;
+    if (flags & kErrTimeout) return FARGO_ERR_BARRIER_TIMEOUT;
     return FARGO_OK;
 }
 
@@ -844,8 +924,11 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     case 6:
     case 7: {
         if ((phase == 6 && !m.hasY) || (phase == 7 && !m.hasZ)) break;
-        if (phase == 6) launch_sweep<T, 1>(m, b.tab, qa, qb, A.vy, c->sc, 1, s);
-        else launch_sweep<T, 2>(m, b.tab, qa, qb, A.vz, c->sc, 1, s);
+        for (int q = 0; q < qa.nq; q++) CK(cudaMemcpyAsync(qb.q[q], qa.q[q], nbytes, cudaMemcpyDeviceToDevice, s));
+        SweepMaps mp{};
+        if ((rc = encode_sweep_maps<T>(c, &mp, qa, qa, phase == 6 ? A.vy : A.vz))) return rc;
+        if (phase == 6) launch_sweep_tma<T, 1>(m, b.tab, mp, qb, c->sc, qa.nq, s);
+        else launch_sweep_tma<T, 2>(m, b.tab, mp, qb, c->sc, qa.nq, s);
         for (int q = 0; q < qa.nq; q++) CK(cudaMemcpyAsync(qa.q[q], qb.q[q], nbytes, cudaMemcpyDeviceToDevice, s));
         break;
     }

@@ -3,6 +3,7 @@
 #pragma once
 #include "fargo_internal.cuh"
 #include "kernels_source.cuh"
+#include "tma.cuh"
 
 namespace fk {
 
@@ -334,80 +335,144 @@ static void launch_orb(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, cons
 }
 
 // ---------------------------------------------------------------------------
-// Y and Z sweeps (Eqs. 1D-advection-Y/Z) as marching pencils.  One thread
-// owns a segment of one column along the sweep axis (fixed i and transverse
-// index) and walks it with a five-row register window: at cell p it holds
-// the ratios Q/rho of rows p-2..p+2, the van Leer slope of cell p from the
-// previous row, and the flux through face p (lower), computes the slope of
-// cell p+1, the interface values and fluxes through face p+1 (upper), updates
-// cell p and slides the window.  Each face flux and slope is computed once
-// and each value is loaded once; a warp reads 32 consecutive azimuths of a
-// row, so every load is coalesced.  Consistent transport (ratio to density
-// times the mass flux), all fluxes from the pre-sweep values.  With
-// copy_ghosts set, cells outside the active box are copied to `out` so that
-// the next sweep finds every ghost it needs.
+// Y and Z sweeps (Eqs. 1D-advection-Y/Z) as marching pencils.  A thread owns
+// one column (fixed azimuth and transverse index) over a segment of the
+// sweep axis and walks it with a register window: at cell p it holds the
+// ratios Q/rho of rows p..p+2, the van Leer slope of cell p and the flux
+// through face p (lower); it computes the slope of cell p+1, the interface
+// values and fluxes through face p+1 (upper), updates cell p and slides the
+// window.  Each face flux and slope is computed once; consistent transport
+// (ratio to density times the mass flux), all fluxes from the pre-sweep
+// values.
 // ---------------------------------------------------------------------------
+// The Y and Z sweeps with TMA staging.  A CTA owns a tile of TW consecutive
+// azimuths (one 512-byte row segment per quantity) of one transverse index
+// and a segment of the sweep axis.  A producer thread streams the rows of
+// the segment and its 2+2 halo rows, every quantity plus the face velocity,
+// into an S-stage ring of shared memory with 3D tensor-map loads completed
+// on an mbarrier; the TW consumer threads (one column each) march the
+// segment exactly like the register version above, reading each row from
+// shared memory and releasing its stage through a second mbarrier.  Rows
+// outside the active range come from `maps.qg` (the ghost source).
+// Every wait is bounded: on timeout the CTA records kErrTimeout and returns
+// after its copies in flight have landed.
+// ---------------------------------------------------------------------------
+struct SweepMaps {
+    CUtensorMap qin[8];
+    CUtensorMap qg[8];
+    CUtensorMap vel;
+};
+
+template <typename T>
+struct TmaTile {
+    static constexpr int TW = 512 / (int)sizeof(T);   // 128 floats or 64 doubles per row segment
+    static constexpr int S = 8;                       // pipeline stages
+};
+
 template <typename T, int AXIS, int NQ>
-__global__ void __launch_bounds__(128, 6) k_sweep(MeshD m, Tab<T> tb, QSet<T> in, QSet<T> out, const T *vel,
-                                               const Scal *sc, int copy_ghosts, int seglen)
+__global__ void __launch_bounds__(TmaTile<T>::TW + 32) k_sweep_tma(MeshD m, Tab<T> tb,
+                                                                    const __grid_constant__ SweepMaps maps,
+                                                                    QSet<T> out, Scal *sc, int seglen)
 {
+    constexpr int TW = TmaTile<T>::TW, S = TmaTile<T>::S, NW = TW / 32;
+    constexpr int ROW = (NQ + 1) * TW;                // values per stage
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *stage = reinterpret_cast<T *>(smem_raw);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    const int n2t = AXIS == 1 ? m.nzt : m.nyt;           // transverse extent (ghosts included)
     const int p0 = AXIS == 1 ? m.j0 : m.k0, pN = AXIS == 1 ? m.j1 : m.k1;
-    const int nalong = AXIS == 1 ? m.nyt : m.nzt;
-    const int nseg = (pN - p0 + seglen - 1) / seglen;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long long)m.nx * n2t * nseg) return;
-    const int i = (int)(tid % m.nx);
-    const long long r = tid / m.nx;
-    const int c2 = (int)(r % n2t), seg = (int)(r / n2t);
-    const bool tact = AXIS == 1 ? (c2 >= m.k0 && c2 < m.k1) : (c2 >= m.j0 && c2 < m.j1);
-    const long long st = AXIS == 1 ? m.sj : m.sk;
-    const long long base = AXIS == 1 ? IX(m, i, 0, c2) : IX(m, i, c2, 0);
-    if (!tact) {
-        if (copy_ghosts && seg == 0)
-            for (int p = 0; p < nalong; p++)
-                for (int q = 0; q < NQ; q++) out.q[q][base + p * st] = in.q[q][base + p * st];
+    const int n2 = AXIS == 1 ? m.k1 - m.k0 : m.j1 - m.j0;
+    const int ntx = (m.nx + TW - 1) / TW;
+    const int bx = blockIdx.x % ntx;
+    const int rest = blockIdx.x / ntx;
+    const int c2 = (AXIS == 1 ? m.k0 : m.j0) + rest % n2;
+    const int seg = rest / n2;
+    const int ps = p0 + seg * seglen, pe = min(ps + seglen, pN);
+    const int nrows = pe - ps + 4;                    // rows ps-2 .. pe+1
+    const int x0 = bx * TW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (warp == NW) {
+        // ---------------- producer ----------------
+        if (lane != 0) return;
+        for (int q = 0; q < NQ; q++) prefetch_tensormap(&maps.qin[q]);
+        prefetch_tensormap(&maps.vel);
+        bool ok = true;
+        int issued = 0;
+        for (int r = 0; r < nrows && ok; r++) {
+            const int slot = r % S;
+            if (r >= S && !mbar_wait(&empty[slot], ((r / S) - 1) & 1)) {
+                ok = false;
+                break;
+            }
+            const int p = ps - 2 + r;
+            const bool ghost = p < p0 || p >= pN;
+            mbar_expect_tx(&full[slot], (unsigned)(ROW * sizeof(T)));
+            T *dst = stage + (size_t)slot * ROW;
+            const int y = AXIS == 1 ? p : c2, z = AXIS == 1 ? c2 : p;
+#pragma unroll
+            for (int q = 0; q < NQ; q++) tma_load_3d(dst + q * TW, ghost ? &maps.qg[q] : &maps.qin[q], x0, y, z, &full[slot]);
+            tma_load_3d(dst + NQ * TW, &maps.vel, x0, y, z, &full[slot]);
+            issued = r + 1;
+        }
+        if (!ok) atomicOr(&sc->err, kErrTimeout);
+        // let every copy in flight land before the CTA can exit
+        for (int r = issued > S ? issued - S : 0; r < issued; r++) mbar_wait(&full[r % S], (r / S) & 1);
         return;
     }
-    if (copy_ghosts) {
-        if (seg == 0)
-            for (int p = 0; p < p0; p++)
-                for (int q = 0; q < NQ; q++) out.q[q][base + p * st] = in.q[q][base + p * st];
-        if (seg == nseg - 1)
-            for (int p = pN; p < nalong; p++)
-                for (int q = 0; q < NQ; q++) out.q[q][base + p * st] = in.q[q][base + p * st];
-    }
-    const int ps = p0 + seg * seglen, pe = min(ps + seglen, pN);
+    // ---------------- consumers: one column each ----------------
+    const int i = x0 + threadIdx.x;
+    const bool col = i < m.nx;
+    const long long st = AXIS == 1 ? m.sj : m.sk;
+    const long long base = AXIS == 1 ? IX(m, col ? i : 0, 0, c2) : IX(m, col ? i : 0, c2, 0);
     auto ring_of = [&](int p) { return AXIS == 1 ? c2 * m.nyt + p : p * m.nyt + c2; };
     auto icd = [&](int f) -> T { return AXIS == 1 ? tb.idyc[f] : tb.idzc[f * m.nyt + c2]; };
     auto width = [&](int d) -> T { return AXIS == 1 ? tb.dy[d] : tb.lenz[d * m.nyt + c2]; };
     auto area = [&](int f) -> T { return AXIS == 1 ? tb.sy[c2 * (m.nyt + 1) + f] : tb.sz[f * (m.nyt + 1) + c2]; };
-    auto ratios = [&](const T *raw, T *out_r) {
-        const T ri = T(1) / raw[0];
-        out_r[0] = raw[0];
+    bool ok = true;
+    // fetch row r into ratios + face velocity, then release the stage
+    auto fetch = [&](int r, T *rat, T &vface) {
+        const int slot = r % S;
+        if (!mbar_wait(&full[slot], (r / S) & 1)) {
+            ok = false;
+            return;
+        }
+        const T *src = stage + (size_t)slot * ROW + threadIdx.x;
+        const T rho = src[0];
+        const T ri = T(1) / rho;
+        rat[0] = rho;
 #pragma unroll
-        for (int q = 1; q < NQ; q++) out_r[q] = raw[q] * ri;
+        for (int q = 1; q < NQ; q++) rat[q] = src[q * TW] * ri;
+        vface = src[NQ * TW];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
     };
-    auto load_raw = [&](int row, T *raw) {
-        const long long c = base + (long long)row * st;
-#pragma unroll
-        for (int q = 0; q < NQ; q++) raw[q] = in.q[q][c];
-    };
-    // window: ratios (q = 0: the density) of rows p, p+1, p+2
-    T R0[NQ], R1[NQ], R2[NQ], aP[NQ], Flo[NQ];
+    T Rm2[NQ], Rm1[NQ], R0[NQ], R1[NQ], R2[NQ], aP[NQ], Flo[NQ];
+    T vm2, vm1, v0f, v1f, v2f;
+    fetch(0, Rm2, vm2);
+    fetch(1, Rm1, vm1);
+    fetch(2, R0, v0f);
+    fetch(3, R1, v1f);
+    fetch(4, R2, v2f);
+    if (!ok) {
+        atomicOr(&sc->err, kErrTimeout);
+        return;
+    }
+    (void)vm2;
+    (void)vm1;
     {
-        T raw[NQ], Rm2[NQ], Rm1[NQ];
-        load_raw(ps - 2, raw); ratios(raw, Rm2);
-        load_raw(ps - 1, raw); ratios(raw, Rm1);
-        load_raw(ps, raw); ratios(raw, R0);
-        load_raw(ps + 1, raw); ratios(raw, R1);
-        load_raw(ps + 2, raw); ratios(raw, R2);
         const T d0 = icd(ps - 1), d1 = icd(ps), d2 = icd(ps + 1);
-        const T v = vel[base + (long long)ps * st];
+        const T v = v0f;   // face ps
         const T wl = width(ps - 1), wr = width(ps);
-        const T S = area(ps);
+        const T Sa = area(ps);
         T F0 = 0;
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
@@ -415,61 +480,87 @@ __global__ void __launch_bounds__(128, 6) k_sweep(MeshD m, Tab<T> tb, QSet<T> in
             const T a0 = vl_slope_i(Rm1[q], R0[q], R1[q], d1, d2);
             aP[q] = a0;
             const T stv = v >= T(0) ? Rm1[q] + am * (wl - v * dt) * T(0.5) : R0[q] - a0 * (wr + v * dt) * T(0.5);
-            if (q == 0) F0 = v * stv * S;
+            if (q == 0) F0 = v * stv * Sa;
             Flo[q] = q == 0 ? F0 : F0 * stv;
         }
     }
     for (int p = ps; p < pe; p++) {
-        T pre[NQ];
-        const bool more = p + 1 < pe;
-        if (more) load_raw(p + 3, pre);       // issued before the arithmetic of this row
-        const long long c = base + (long long)p * st;
-        const T v = vel[c + st];
+        const T v = v1f;   // face p+1
         const T dn = icd(p + 1), dnn = icd(p + 2);
         const T wp = width(p), wn = width(p + 1);
-        const T S = area(p + 1);
+        const T Sa = area(p + 1);
         const T dtVi = dt * tb.vinv[ring_of(p)];
         const T rho = R0[0];
+        const long long c = base + (long long)p * st;
         T F0 = 0;
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
             const T aN = vl_slope_i(R0[q], R1[q], R2[q], dn, dnn);
             const T stv = v >= T(0) ? R0[q] + aP[q] * (wp - v * dt) * T(0.5) : R1[q] - aN * (wn + v * dt) * T(0.5);
-            if (q == 0) F0 = v * stv * S;
+            if (q == 0) F0 = v * stv * Sa;
             const T Fup = q == 0 ? F0 : F0 * stv;
             const T Q = q == 0 ? rho : R0[q] * rho;
-            out.q[q][c] = Q - dtVi * (Fup - Flo[q]);
+            if (col) out.q[q][c] = Q - dtVi * (Fup - Flo[q]);
             Flo[q] = Fup;
             aP[q] = aN;
         }
-        if (more) {
+        if (p + 1 < pe) {
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
                 R0[q] = R1[q];
                 R1[q] = R2[q];
             }
-            ratios(pre, R2);
+            v0f = v1f;
+            v1f = v2f;
+            fetch(p - ps + 5, R2, v2f);   // row p+3
+            if (!ok) {
+                atomicOr(&sc->err, kErrTimeout);
+                return;
+            }
         }
     }
 }
 
 template <typename T, int AXIS>
-static void launch_sweep(const MeshD &m, const Tab<T> &tb, const QSet<T> &in, const QSet<T> &out, const T *vel,
-                         const Scal *sc, int copy_ghosts, cudaStream_t s)
+static size_t sweep_tma_smem(int nq)
 {
+    return (size_t)TmaTile<T>::S * (nq + 1) * TmaTile<T>::TW * sizeof(T);
+}
+
+template <typename T, int AXIS>
+static void launch_sweep_tma(const MeshD &m, const Tab<T> &tb, const SweepMaps &maps, const QSet<T> &out,
+                             Scal *sc, int nq, cudaStream_t s)
+{
+    constexpr int TW = TmaTile<T>::TW;
     const int np = AXIS == 1 ? m.j1 - m.j0 : m.k1 - m.k0;
-    const int n2t = AXIS == 1 ? m.nzt : m.nyt;
-    const int seglen = np > 48 ? 32 : np;
+    const int n2 = AXIS == 1 ? m.k1 - m.k0 : m.j1 - m.j0;
+    const int seglen = np > 96 ? 64 : np;
     const int nseg = (np + seglen - 1) / seglen;
-    const long long n = (long long)m.nx * n2t * nseg;
-    const unsigned g = (unsigned)((n + 127) / 128);
-    switch (in.nq) {
-    case 3: k_sweep<T, AXIS, 3><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
-    case 4: k_sweep<T, AXIS, 4><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
-    case 5: k_sweep<T, AXIS, 5><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
-    case 6: k_sweep<T, AXIS, 6><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
-    case 7: k_sweep<T, AXIS, 7><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
-    default: k_sweep<T, AXIS, 8><<<g, 128, 0, s>>>(m, tb, in, out, vel, sc, copy_ghosts, seglen); break;
+    const int ntx = (m.nx + TW - 1) / TW;
+    const unsigned g = (unsigned)ntx * n2 * nseg;
+    const size_t sm = sweep_tma_smem<T, AXIS>(nq);
+    switch (nq) {
+    case 3: k_sweep_tma<T, AXIS, 3><<<g, TW + 32, sm, s>>>(m, tb, maps, out, sc, seglen); break;
+    case 4: k_sweep_tma<T, AXIS, 4><<<g, TW + 32, sm, s>>>(m, tb, maps, out, sc, seglen); break;
+    case 5: k_sweep_tma<T, AXIS, 5><<<g, TW + 32, sm, s>>>(m, tb, maps, out, sc, seglen); break;
+    case 6: k_sweep_tma<T, AXIS, 6><<<g, TW + 32, sm, s>>>(m, tb, maps, out, sc, seglen); break;
+    case 7: k_sweep_tma<T, AXIS, 7><<<g, TW + 32, sm, s>>>(m, tb, maps, out, sc, seglen); break;
+    default: k_sweep_tma<T, AXIS, 8><<<g, TW + 32, sm, s>>>(m, tb, maps, out, sc, seglen); break;
+    }
+}
+
+template <typename T, int AXIS>
+static cudaError_t sweep_tma_attrs(int nq)
+{
+    const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int sm = (int)sweep_tma_smem<T, AXIS>(nq);
+    switch (nq) {
+    case 3: return cudaFuncSetAttribute(k_sweep_tma<T, AXIS, 3>, (cudaFuncAttribute)a, sm);
+    case 4: return cudaFuncSetAttribute(k_sweep_tma<T, AXIS, 4>, (cudaFuncAttribute)a, sm);
+    case 5: return cudaFuncSetAttribute(k_sweep_tma<T, AXIS, 5>, (cudaFuncAttribute)a, sm);
+    case 6: return cudaFuncSetAttribute(k_sweep_tma<T, AXIS, 6>, (cudaFuncAttribute)a, sm);
+    case 7: return cudaFuncSetAttribute(k_sweep_tma<T, AXIS, 7>, (cudaFuncAttribute)a, sm);
+    default: return cudaFuncSetAttribute(k_sweep_tma<T, AXIS, 8>, (cudaFuncAttribute)a, sm);
     }
 }
 
