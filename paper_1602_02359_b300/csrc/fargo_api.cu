@@ -322,6 +322,23 @@ static int build_tables(fargo_ctx *c, Tab<T> &t)
         for (size_t q = 0; q < idzc.size(); q++) idzc[q] = h.dzc[q] > 0.0 ? 1.0 / h.dzc[q] : 0.0;
         UP(idyc, idyc);
         UP(idzc, idzc);
+        auto inv = [](const std::vector<double> &a) {
+            std::vector<double> r(a.size(), 0.0);
+            for (size_t q = 0; q < a.size(); q++) r[q] = a[q] != 0.0 ? 1.0 / a[q] : 0.0;
+            return r;
+        };
+        UP(ilenx, inv(h.lx));
+        UP(ilenz, inv(h.lenz));
+        UP(iR, inv(h.R));
+        UP(idy, inv(h.dy));
+        UP(iyf, inv(yf));
+        UP(iym, inv(h.ym));
+        UP(idz, inv(h.dz));
+        UP(iszm, inv(szm));
+        std::vector<double> dzm(nzt + 1, 0.0);
+        for (int k = 1; k < nzt; k++) dzm[k] = h.zm[k] - h.zm[k - 1];
+        UP(idzm, inv(dzm));
+        t.idx = (T)(1.0 / c->m.dx);
     }
     {
         void *q;
@@ -536,7 +553,8 @@ static int set_kernel_attrs(fargo_ctx *c)
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
     nq -= 0;
-    size_t smem = (size_t)(nq + 2) * c->nx * sizeof(T);
+    // ring kernels stage at most max(nq, 7) rows of one pitch each
+    size_t smem = (size_t)(nq > 7 ? nq : 7) * c->pitch * sizeof(T);
     if (smem > (size_t)maxsm - 1024 || ring_chunk(c->nx) == 0) return FARGO_ERR_SIZE;
     c->tx_smem = smem;
     const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;

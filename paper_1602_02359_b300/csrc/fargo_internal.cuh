@@ -44,6 +44,10 @@ struct Tab {
     const T *r4, *dminT;
     // inverse centre-to-centre distances across Y faces (per j) and Z faces (per ring)
     const T *idyc, *idzc;
+    // reciprocals of mesh lengths: per ring 1/lenx, 1/lenz, 1/R; per j 1/dy,
+    // 1/yf, 1/ym; per k 1/dz, 1/sin(zm), 1/(zm[k] - zm[k-1]); scalar 1/dx
+    const T *ilenx, *ilenz, *iR, *idy, *iyf, *iym, *idz, *iszm, *idzm;
+    T idx;
 };
 
 template <typename T>

@@ -76,11 +76,11 @@ __global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in,
         T v = in.vx[c];
         if (m.hasX && jact && kact) {
             const long long cm = c - i + im;
-            const T d = tb.lenx[ring];
+            const T id = tb.ilenx[ring];
             const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring);
-            T acc = T(-2) * (P0 - Pm) / (d * (in.rho[c] + in.rho[cm]));
+            T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
             if (m.has_planet)
-                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, im, ring)) / d;
+                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, im, ring)) * id;
             v = v + dt * acc;
         }
         out.vx[c] = v;
@@ -89,11 +89,11 @@ __global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in,
         T v = in.vy[c];
         if (m.hasY && j > m.j0 && j < m.j1 && kact) {
             const long long cm = c - m.sj;
-            const T d = tb.dyc[j];
+            const T id = tb.idyc[j];
             const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring - 1);
-            T acc = T(-2) * (P0 - Pm) / (d * (in.rho[c] + in.rho[cm]));
+            T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
             if (m.has_planet)
-                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, ring - 1)) / d;
+                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, ring - 1)) * id;
             if (m.has_star) acc -= tb.gphy[ring];
             if (m.geom != CART) {
                 const T Rj = tb.R[ring], Rm = tb.R[ring - 1];
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in,
                     const T vth = T(0.25) * (in.vz[c] + in.vz[c + m.sk] + in.vz[cm] + in.vz[cm + m.sk]);
                     cen += vth * vth;
                 }
-                acc += cen / tb.yf[j];
+                acc += cen * tb.iyf[j];
             }
             v = v + dt * acc;
         }
@@ -116,18 +116,18 @@ __global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in,
         if (m.hasZ && k > m.k0 && k < m.k1 && jact) {
             const long long cm = c - m.sk;
             const int rm = ring - m.nyt;
-            const T d = tb.dzc[ring];
+            const T id = tb.idzc[ring];
             const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, rm);
-            T acc = T(-2) * (P0 - Pm) / (d * (in.rho[c] + in.rho[cm]));
+            T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
             if (m.has_planet)
-                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, rm)) / d;
+                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, rm)) * id;
             if (m.has_star) acc -= tb.gphz[ring];
             if (m.geom == SPH) {
                 const T Rk = tb.R[ring], Rm = tb.R[rm];
                 const long long cp = c - i + ip, cmp = cm - i + ip;
                 const T vt = T(0.25) * ((in.vx[c] + Rk * om) + (in.vx[cp] + Rk * om) + (in.vx[cm] + Rm * om) +
                                         (in.vx[cmp] + Rm * om));
-                acc += vt * vt * tb.cotzf[k] / tb.ym[j];
+                acc += vt * vt * tb.cotzf[k] * tb.iym[j];
             }
             v = v + dt * acc;
         }
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
             const long long cm = c - i + im, cp = c - i + ip;
             const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
             const T qm = qvisc(c2, rho[cm], vx[c] - vx[cm]);
-            v -= dt * T(2) * (q0 - qm) / (tb.lenx[ring] * (rho[c] + rho[cm]));
+            v -= dt * T(2) * (q0 - qm) * tb.ilenx[ring] / (rho[c] + rho[cm]);
         }
         out.vx[c] = v;
         vxl = v;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
             const long long cm = c - sj;
             const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
             const T qm = qvisc(c2, rho[cm], vy[c] - vy[cm]);
-            v -= dt * T(2) * (q0 - qm) / (tb.dyc[j] * (rho[c] + rho[cm]));
+            v -= dt * T(2) * (q0 - qm) * tb.idyc[j] / (rho[c] + rho[cm]);
         }
         out.vy[c] = v;
         vyl = v;
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
             const long long cm = c - sk;
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
             const T qm = qvisc(c2, rho[cm], vz[c] - vz[cm]);
-            v -= dt * T(2) * (q0 - qm) / (tb.dzc[ring] * (rho[c] + rho[cm]));
+            v -= dt * T(2) * (q0 - qm) * tb.idzc[ring] / (rho[c] + rho[cm]);
         }
         out.vz[c] = v;
         vzl = v;
@@ -210,15 +210,15 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
     if (av) {
         if (m.hasX) {
             const T dv = vx[c - i + ip] - vx[c];
-            h += qvisc(c2, rho[c], dv) * dv / tb.lenx[ring];
+            h += qvisc(c2, rho[c], dv) * dv * tb.ilenx[ring];
         }
         if (m.hasY) {
             const T dv = vy[c + sj] - vy[c];
-            h += qvisc(c2, rho[c], dv) * dv / tb.dy[j];
+            h += qvisc(c2, rho[c], dv) * dv * tb.idy[j];
         }
         if (m.hasZ) {
             const T dv = vz[c + sk] - vz[c];
-            h += qvisc(c2, rho[c], dv) * dv / tb.lenz[ring];
+            h += qvisc(c2, rho[c], dv) * dv * tb.ilenz[ring];
         }
     }
     e -= dt * h;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
         if (av) {
             const T qp = qvisc(c2, rho[cp], vx[cpp] - vx[cp]);
             const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
-            vxu -= dt * T(2) * (qp - q0) / (tb.lenx[ring] * (rho[cp] + rho[c]));
+            vxu -= dt * T(2) * (qp - q0) * tb.ilenx[ring] / (rho[cp] + rho[c]);
         }
         div += tb.sx[ring] * (vxu - vxl);
     }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
         if (av && j + 1 < m.j1) {
             const T qp = qvisc(c2, rho[c + sj], vy[c + 2 * sj] - vy[c + sj]);
             const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
-            vyu -= dt * T(2) * (qp - q0) / (tb.dyc[j + 1] * (rho[c + sj] + rho[c]));
+            vyu -= dt * T(2) * (qp - q0) * tb.idyc[j + 1] / (rho[c + sj] + rho[c]);
         }
         div += tb.sy[fr + 1] * vyu - tb.sy[fr] * vyl;
     }
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, 
         if (av && k + 1 < m.k1) {
             const T qp = qvisc(c2, rho[c + sk], vz[c + 2 * sk] - vz[c + sk]);
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
-            vzu -= dt * T(2) * (qp - q0) / (tb.dzc[ring + m.nyt] * (rho[c + sk] + rho[c]));
+            vzu -= dt * T(2) * (qp - q0) * tb.idzc[ring + m.nyt] / (rho[c + sk] + rho[c]);
         }
         div += tb.sz[fr + (m.nyt + 1)] * vzu - tb.sz[fr] * vzl;
     }
@@ -293,27 +293,27 @@ struct ViscCtx {
         const int ring = k * m.nyt + j;
         const T dv = divv(i, j, k);
         const T rn = rho[c] * nu(j, k);
-        const T dxx = (vx[at(i + 1, j, k)] - vx[c]) / tb.lenx[ring];
-        const T dyy = m.hasY ? (vy[c + m.sj] - vy[c]) / tb.dy[j] : T(0);
-        const T dzz = m.hasZ ? (vz[c + m.sk] - vz[c]) / tb.lenz[ring] : T(0);
+        const T dxx = (vx[at(i + 1, j, k)] - vx[c]) * tb.ilenx[ring];
+        const T dyy = m.hasY ? (vy[c + m.sj] - vy[c]) * tb.idy[j] : T(0);
+        const T dzz = m.hasZ ? (vz[c + m.sk] - vz[c]) * tb.ilenz[ring] : T(0);
         const T tw = T(2.0 / 3.0) * dv;
         if (m.geom == CART) {
             txx = -rn * (T(2) * dxx - tw);
             tyy = -rn * (T(2) * dyy - tw);
             tzz = -rn * (T(2) * dzz - tw);
         } else if (m.geom == CYL) {
-            const T r = tb.ym[j];
+            const T ir = tb.iym[j];
             const T vr = T(0.5) * (vy[c] + vy[c + m.sj]);
-            txx = -rn * (T(2) * (dxx + vr / r) - tw);
+            txx = -rn * (T(2) * (dxx + vr * ir) - tw);
             tyy = -rn * (T(2) * dyy - tw);
             tzz = -rn * (T(2) * dzz - tw);
         } else {
-            const T r = tb.ym[j], ct = tb.cotzm[k];
+            const T ir = tb.iym[j], ct = tb.cotzm[k];
             const T vr = T(0.5) * (vy[c] + vy[c + m.sj]);
             const T vt = T(0.5) * (vz[c] + vz[c + m.sk]);
-            txx = -rn * (T(2) * (dxx + vr / r + vt * ct / r) - tw);
+            txx = -rn * (T(2) * (dxx + vr * ir + vt * ct * ir) - tw);
             tyy = -rn * (T(2) * dyy - tw);
-            tzz = -rn * (T(2) * (dzz + vr / r) - tw);
+            tzz = -rn * (T(2) * (dzz + vr * ir) - tw);
         }
     }
     // tau_xy on the edge (i-1/2, j-1/2, k)
@@ -322,16 +322,16 @@ struct ViscCtx {
         const long long c = at(i, j, k), cm = at(i - 1, j, k);
         const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sj] + rho[cm - m.sj]);
         const T nb = T(0.5) * (nu(j, k) + nu(j - 1, k));
-        const T dvx_dy = (vx[c] - vx[c - m.sj]) / tb.dyc[j];
+        const T dvx_dy = (vx[c] - vx[c - m.sj]) * tb.idyc[j];
         T t;
         if (m.geom == CART) {
-            t = (vy[c] - vy[cm]) / tb.dx + dvx_dy;
+            t = (vy[c] - vy[cm]) * tb.idx + dvx_dy;
         } else if (m.geom == CYL) {
-            const T rf = tb.yf[j];
-            t = dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf + (vy[c] - vy[cm]) / (rf * tb.dx);
+            const T irf = tb.iyf[j];
+            t = dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) * irf + (vy[c] - vy[cm]) * (irf * tb.idx);
         } else {
-            const T rf = tb.yf[j], sn = tb.szm[k];
-            t = (vy[c] - vy[cm]) / (rf * sn * tb.dx) + dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) / rf;
+            const T irf = tb.iyf[j], isn = tb.iszm[k];
+            t = (vy[c] - vy[cm]) * (irf * isn * tb.idx) + dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) * irf;
         }
         return -rb * nb * t;
     }
@@ -341,15 +341,16 @@ struct ViscCtx {
         const long long c = at(i, j, k), cm = at(i - 1, j, k);
         const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sk] + rho[cm - m.sk]);
         const T nb = T(0.5) * (nu(j, k) + nu(j, k - 1));
-        const T dzc = tb.zm[k] - tb.zm[k - 1];
+        const T idzm = tb.idzm[k];
         T t;
         if (m.geom == CART) {
-            t = (vz[c] - vz[cm]) / tb.dx + (vx[c] - vx[c - m.sk]) / dzc;
+            t = (vz[c] - vz[cm]) * tb.idx + (vx[c] - vx[c - m.sk]) * idzm;
         } else if (m.geom == CYL) {
-            t = (vx[c] - vx[c - m.sk]) / dzc + (vz[c] - vz[cm]) / (tb.ym[j] * tb.dx);
+            t = (vx[c] - vx[c - m.sk]) * idzm + (vz[c] - vz[cm]) * (tb.iym[j] * tb.idx);
         } else {
-            const T r = tb.ym[j], sf = tb.szf[k];
-            t = sf / r * (vx[c] / tb.szm[k] - vx[c - m.sk] / tb.szm[k - 1]) / dzc + (vz[c] - vz[cm]) / (r * sf * tb.dx);
+            const T ir = tb.iym[j], sf = tb.szf[k];
+            t = sf * ir * (vx[c] * tb.iszm[k] - vx[c - m.sk] * tb.iszm[k - 1]) * idzm +
+                (vz[c] - vz[cm]) * (ir * tb.idx) / sf;
         }
         return -rb * nb * t;
     }
@@ -359,14 +360,14 @@ struct ViscCtx {
         const long long c = at(i, j, k);
         const T rb = T(0.25) * (rho[c] + rho[c - m.sj] + rho[c - m.sk] + rho[c - m.sj - m.sk]);
         const T nb = T(0.25) * (nu(j, k) + nu(j - 1, k) + nu(j, k - 1) + nu(j - 1, k - 1));
-        const T dzc = tb.zm[k] - tb.zm[k - 1];
+        const T idzm = tb.idzm[k];
         T t;
         if (m.geom == SPH) {
-            const T rf = tb.yf[j];
-            t = (vz[c] - vz[c - m.sj]) / tb.dyc[j] - T(0.5) * (vz[c] + vz[c - m.sj]) / rf +
-                (vy[c] - vy[c - m.sk]) / (rf * dzc);
+            const T irf = tb.iyf[j];
+            t = (vz[c] - vz[c - m.sj]) * tb.idyc[j] - T(0.5) * (vz[c] + vz[c - m.sj]) * irf +
+                (vy[c] - vy[c - m.sk]) * (irf * idzm);
         } else {
-            t = (vz[c] - vz[c - m.sj]) / tb.dyc[j] + (vy[c] - vy[c - m.sk]) / dzc;
+            t = (vz[c] - vz[c - m.sj]) * tb.idyc[j] + (vy[c] - vy[c - m.sk]) * idzm;
         }
         return -rb * nb * t;
     }
@@ -378,7 +379,7 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
 {
     const long long c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
-    const T dx = tb.dx;
+    const T idx = tb.idx;
     const T *rho = in.rho;
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
@@ -387,37 +388,36 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i - 1, j, k, b0, b1, b2);
-            const T rf = T(0.5) * (rho[c] + rho[cm]);
             T f = 0;
             if (m.geom == CART) {
-                f += (a0 - b0) / dx;
-                if (m.hasY) f += (V.txy(i, j + 1, k) - V.txy(i, j, k)) / tb.dy[j];
-                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) / tb.dz[k];
+                f += (a0 - b0) * idx;
+                if (m.hasY) f += (V.txy(i, j + 1, k) - V.txy(i, j, k)) * tb.idy[j];
+                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) * tb.idz[k];
             } else if (m.geom == CYL) {
-                const T r = tb.ym[j];
+                const T ir = tb.iym[j];
                 if (m.hasY)
-                    f += (tb.yf[j + 1] * tb.yf[j + 1] * V.txy(i, j + 1, k) - tb.yf[j] * tb.yf[j] * V.txy(i, j, k)) /
-                         (r * r * tb.dy[j]);
-                f += (a0 - b0) / (r * dx);
-                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) / tb.dz[k];
+                    f += (tb.yf[j + 1] * tb.yf[j + 1] * V.txy(i, j + 1, k) - tb.yf[j] * tb.yf[j] * V.txy(i, j, k)) *
+                         (ir * ir * tb.idy[j]);
+                f += (a0 - b0) * (ir * idx);
+                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) * tb.idz[k];
             } else {
-                const T r = tb.ym[j], sn = tb.szm[k], ct = tb.cotzm[k];
+                const T ir = tb.iym[j], isn = tb.iszm[k], ct = tb.cotzm[k];
                 T ty0 = 0, ty1 = 0, tz0 = 0, tz1 = 0;
                 if (m.hasY) {
                     ty0 = V.txy(i, j, k);
                     ty1 = V.txy(i, j + 1, k);
-                    f += (tb.yf[j + 1] * tb.yf[j + 1] * ty1 - tb.yf[j] * tb.yf[j] * ty0) / (r * r * tb.dy[j]);
+                    f += (tb.yf[j + 1] * tb.yf[j + 1] * ty1 - tb.yf[j] * tb.yf[j] * ty0) * (ir * ir * tb.idy[j]);
                 }
                 if (m.hasZ) {
                     tz0 = V.txz(i, j, k);
                     tz1 = V.txz(i, j, k + 1);
-                    f += (tz1 - tz0) / (r * tb.dz[k]);
+                    f += (tz1 - tz0) * (ir * tb.idz[k]);
                 }
-                f += (a0 - b0) / (r * sn * dx);
-                if (m.hasY) f += T(0.5) * (ty0 + ty1) / r;
-                if (m.hasZ) f += T(2) * T(0.5) * (tz0 + tz1) * ct / r;
+                f += (a0 - b0) * (ir * isn * idx);
+                if (m.hasY) f += T(0.5) * (ty0 + ty1) * ir;
+                if (m.hasZ) f += T(2) * T(0.5) * (tz0 + tz1) * ct * ir;
             }
-            v = v - dt * f / rf;
+            v = v - T(2) * dt * f / (rho[c] + rho[cm]);
         }
         out.vx[c] = v;
     }
@@ -428,26 +428,26 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i, j - 1, k, b0, b1, b2);
-            const T rf = T(0.5) * (rho[c] + rho[cjm]);
             T f = 0;
             if (m.geom == CART) {
-                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) / dx;
-                f += (a1 - b1) / tb.dyc[j];
-                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) / tb.dz[k];
+                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) * idx;
+                f += (a1 - b1) * tb.idyc[j];
+                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) * tb.idz[k];
             } else if (m.geom == CYL) {
-                const T r = tb.yf[j];
-                f += (tb.ym[j] * a1 - tb.ym[j - 1] * b1) / (r * tb.dyc[j]);
-                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) / (r * dx);
-                f -= T(0.5) * (a0 + b0) / r;
-                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) / tb.dz[k];
+                const T irf = tb.iyf[j];
+                f += (tb.ym[j] * a1 - tb.ym[j - 1] * b1) * (irf * tb.idyc[j]);
+                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) * (irf * idx);
+                f -= T(0.5) * (a0 + b0) * irf;
+                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) * tb.idz[k];
             } else {
-                const T r = tb.yf[j], sn = tb.szm[k];
-                f += (tb.ym[j] * tb.ym[j] * a1 - tb.ym[j - 1] * tb.ym[j - 1] * b1) / (r * r * tb.dyc[j]);
-                if (m.hasZ) f += (V.tyz(i, j, k + 1) * tb.szf[k + 1] - V.tyz(i, j, k) * tb.szf[k]) / (r * sn * tb.dz[k]);
-                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) / (r * sn * dx);
-                f -= T(0.5) * (a2 + b2 + a0 + b0) / r;
+                const T irf = tb.iyf[j], isn = tb.iszm[k];
+                f += (tb.ym[j] * tb.ym[j] * a1 - tb.ym[j - 1] * tb.ym[j - 1] * b1) * (irf * irf * tb.idyc[j]);
+                if (m.hasZ)
+                    f += (V.tyz(i, j, k + 1) * tb.szf[k + 1] - V.tyz(i, j, k) * tb.szf[k]) * (irf * isn * tb.idz[k]);
+                f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) * (irf * isn * idx);
+                f -= T(0.5) * (a2 + b2 + a0 + b0) * irf;
             }
-            v = v - dt * f / rf;
+            v = v - T(2) * dt * f / (rho[c] + rho[cjm]);
         }
         out.vy[c] = v;
     }
@@ -458,34 +458,32 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i, j, k - 1, b0, b1, b2);
-            const T rf = T(0.5) * (rho[c] + rho[ckm]);
-            const T dzc = tb.zm[k] - tb.zm[k - 1];
+            const T idzm = tb.idzm[k];
             T f = 0;
             if (m.geom == CART) {
-                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) / dx;
-                if (m.hasY) f += (V.tyz(i, j + 1, k) - V.tyz(i, j, k)) / tb.dy[j];
-                f += (a2 - b2) / dzc;
+                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) * idx;
+                if (m.hasY) f += (V.tyz(i, j + 1, k) - V.tyz(i, j, k)) * tb.idy[j];
+                f += (a2 - b2) * idzm;
             } else if (m.geom == CYL) {
-                const T r = tb.ym[j];
-                if (m.hasY) f += (tb.yf[j + 1] * V.tyz(i, j + 1, k) - tb.yf[j] * V.tyz(i, j, k)) / (r * tb.dy[j]);
-                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) / (r * dx);
-                f += (a2 - b2) / dzc;
+                const T ir = tb.iym[j];
+                if (m.hasY) f += (tb.yf[j + 1] * V.tyz(i, j + 1, k) - tb.yf[j] * V.tyz(i, j, k)) * (ir * tb.idy[j]);
+                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) * (ir * idx);
+                f += (a2 - b2) * idzm;
             } else {
-                const T r = tb.ym[j], sf = tb.szf[k], ctf = tb.cotzf[k];
+                const T ir = tb.iym[j], sf = tb.szf[k], isf = T(1) / sf, ctf = tb.cotzf[k];
                 if (m.hasY) {
                     const T y1 = tb.yf[j + 1], y0 = tb.yf[j];
-                    f += (y1 * y1 * y1 * V.tyz(i, j + 1, k) - y0 * y0 * y0 * V.tyz(i, j, k)) / (r * r * r * tb.dy[j]);
+                    f += (y1 * y1 * y1 * V.tyz(i, j + 1, k) - y0 * y0 * y0 * V.tyz(i, j, k)) * (ir * ir * ir * tb.idy[j]);
                 }
-                f += (a2 * tb.szm[k] - b2 * tb.szm[k - 1]) / (r * sf * dzc);
-                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) / (r * sf * dx);
-                f -= T(0.5) * (a0 + b0) * ctf / r;
+                f += (a2 * tb.szm[k] - b2 * tb.szm[k - 1]) * (ir * isf * idzm);
+                f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) * (ir * isf * idx);
+                f -= T(0.5) * (a0 + b0) * ctf * ir;
             }
-            v = v - dt * f / rf;
+            v = v - T(2) * dt * f / (rho[c] + rho[ckm]);
         }
         out.vz[c] = v;
     }
 }
-
 
 // Stresses read back from the arrays written by k_visc_tau.
 template <typename T>

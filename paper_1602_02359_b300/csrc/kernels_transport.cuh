@@ -80,71 +80,107 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 // ratio, all fluxes from the pre-sweep ring.
 // ---------------------------------------------------------------------------
 
-// X sweep, residual part (Sec. 3.4.1, Eq. fargo1; Eq. 15 with van Leer
-// slopes): the momenta of Eqs. 16-17 (Tab. "momenta") are built while the
-// ring is staged; the face velocity is delta v = v_x - v0 (v0 = 0 for
-// STANDARD transport).  Ghost rings only get their momenta written (the Y/Z
-// sweeps read them).  Shared memory: nq ring arrays, 1/rho, face velocity.
-template <typename T, int C>
-__global__ void __launch_bounds__(512) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
-                                                     const Scal *sc)
+// Stage rows of one ring into shared memory with 1D bulk copies issued by
+// thread 0 and completed on `bar` (rows are pitch-aligned: 128-byte
+// boundaries, sizes rounded up to 16 bytes within the row padding).  All
+// threads then wait, bounded; returns false on timeout.
+template <typename T>
+__device__ __forceinline__ bool stage_rows(T *dst, int rowlen, const T *const *src, int nrow, int nx,
+                                           uint64_t *bar)
 {
-    extern __shared__ unsigned char smem_raw[];
+    const unsigned bytes = (unsigned)(((size_t)nx * sizeof(T) + 15) / 16 * 16);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+        mbar_expect_tx(bar, bytes * (unsigned)nrow);
+        for (int r = 0; r < nrow; r++) bulk_load(dst + (size_t)r * rowlen, src[r], bytes, bar);
+    }
+    __syncthreads();
+    return mbar_wait(bar, 0);
+}
+
+// X sweep, residual part (Sec. 3.4.1, Eq. fargo1; Eq. 15 with van Leer
+// slopes).  The rows rho, e, v_x and the v_y / v_z rows of the cell's lower
+// and upper faces are staged; the momenta of Eqs. 16-17 (Tab. "momenta")
+// are formed from them, and so are their consistent-transport ratios, which
+// are just the face velocities times the geometric factors (Pi-_x / rho =
+// R v_x + R^2 Omega_f, Pi+_y / rho = v_y of the upper face, ...).  The face
+// velocity is delta v = v_x - v0 (v0 = 0 for STANDARD transport).  Ghost
+// rings only get their momenta written (the Y/Z sweeps read them).
+template <typename T, int C>
+__global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
+                                                     Scal *sc)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ T s_v0[2];
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    const int nx = m.nx, nq = out.nq;
+    const int nx = m.nx, nq = out.nq, pitch = (int)m.sj;
     const int ring = blockIdx.x;
     const int j = ring % m.nyt, k = ring / m.nyt;
     const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
-    T *Q = sm;
-    T *RI = sm + (size_t)nq * nx;
-    T *V = RI + nx;
     const long long base = IX(m, 0, j, k);
-    const T R = tb.R[ring], w = R * R * tb.omega, fz = tb.fz[ring];
     const bool adi = !m.iso;
     const bool sweep = active && m.hasX;
-    __shared__ T s_v0[2];
+    // staged rows: 0 rho, 1 e, 2 vx, 3 vy(j), 4 vy(j+1), 5 vz(k), 6 vz(k+1)
+    const T *src[7];
+    int nrow = 0;
+    int rE = -1, rVY = -1, rVZ = -1;
+    src[nrow++] = in.rho + base;
+    if (adi) { rE = nrow; src[nrow++] = in.e + base; }
+    const int rVX = nrow;
+    src[nrow++] = in.vx + base;
+    if (m.hasY) { rVY = nrow; src[nrow++] = in.vy + base; src[nrow++] = in.vy + base + m.sj; }
+    if (m.hasZ) { rVZ = nrow; src[nrow++] = in.vz + base; src[nrow++] = in.vz + base + m.sk; }
     if (threadIdx.x == 0) {
         const double v0r = m.fargo && sweep ? v0[ring] : 0.0;
         s_v0[0] = (T)v0r;
         s_v0[1] = (T)(v0r - (double)s_v0[0]);
     }
-    __syncthreads();
-    const T v0hi = s_v0[0], v0lo = s_v0[1];
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const long long c = base + i;
-        const int ip = i + 1 == nx ? 0 : i + 1;
-        const T rho = in.rho[c];
-        const T vx = in.vx[c];
-        int q = 0;
-        T val[8];
-        val[q++] = rho;
-        if (adi) val[q++] = in.e[c];
-        val[q++] = rho * (R * vx + w);
-        val[q++] = rho * (R * in.vx[base + ip] + w);
-        if (m.hasY) {
-            val[q++] = rho * in.vy[c];
-            val[q++] = rho * in.vy[c + m.sj];
-        }
-        if (m.hasZ) {
-            val[q++] = rho * (fz * in.vz[c]);
-            val[q++] = rho * (fz * in.vz[c + m.sk]);
-        }
-        if (sweep) {
-#pragma unroll
-            for (int s = 0; s < 8; s++)
-                if (s < q) Q[s * nx + i] = val[s];
-            RI[i] = T(1) / rho;
-            V[i] = sub_split(vx, v0hi, v0lo);
-        } else {
-#pragma unroll
-            for (int s = 0; s < 8; s++)
-                if (s < q) out.q[s][c] = val[s];
-        }
+    if (!stage_rows(sm, pitch, src, nrow, nx, &bar)) {
+        if (threadIdx.x == 0) atomicOr(&sc->err, kErrTimeout);
+        return;
     }
-    if (!sweep) return;
-    __syncthreads();
+    const T R = tb.R[ring], w = R * R * tb.omega, fz = tb.fz[ring];
+    const T *Rho = sm, *Vx = sm + (size_t)rVX * pitch;
+    // ratio of quantity q to the density at cell i, as scale * row[i + off] +
+    // shift (or e / rho), for the order rho, e, Pi-x, Pi+x, Pi-y, Pi+y,
+    // Pi-z, Pi+z of the present components
+    struct RatioSpec {
+        const T *row;
+        int off, div;
+        T a, b;
+    };
+    auto spec = [&](int q) -> RatioSpec {
+        if (q == 0) return {Rho, 0, 0, T(1), T(0)};
+        int o = q - 1;
+        if (adi) {
+            if (o == 0) return {sm + (size_t)rE * pitch, 0, 1, T(1), T(0)};
+            o -= 1;
+        }
+        if (o == 0) return {Vx, 0, 0, R, w};
+        if (o == 1) return {Vx, 1, 0, R, w};
+        if (m.hasY) {
+            if (o == 2) return {sm + (size_t)rVY * pitch, 0, 0, T(1), T(0)};
+            if (o == 3) return {sm + (size_t)(rVY + 1) * pitch, 0, 0, T(1), T(0)};
+            o -= 2;
+        }
+        if (o == 2) return {sm + (size_t)rVZ * pitch, 0, 0, fz, T(0)};
+        return {sm + (size_t)(rVZ + 1) * pitch, 0, 0, fz, T(0)};
+    };
+    if (!sweep) {
+        for (int q = 0; q < nq; q++) {
+            const RatioSpec sp = spec(q);
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+                const T v = sp.row[wrapi(i + sp.off, nx)];
+                out.q[q][base + i] = q == 0 ? v : (sp.div ? v : Rho[i] * (sp.a * v + sp.b));
+            }
+        }
+        return;
+    }
+    const T v0hi = s_v0[0], v0lo = s_v0[1];
     const T dX = tb.lenx[ring], S = tb.sx[ring];
     const T idX = T(1) / dX;
     const T dtVi = dt * tb.vinv[ring];
@@ -153,14 +189,17 @@ __global__ void __launch_bounds__(512) k_transport_x(MeshD m, Tab<T> tb, Fld<T> 
     const int cnt = min(C, nx - i0);
     T vf[C + 1], F0[C + 1];
 #pragma unroll
-    for (int u = 0; u <= C; u++) vf[u] = V[wrapi(i0 + u, nx)];
+    for (int u = 0; u <= C; u++) vf[u] = sub_split(Vx[wrapi(i0 + u, nx)], v0hi, v0lo);
+    T rho[C + 4];
+#pragma unroll
+    for (int s = 0; s < C + 4; s++) rho[s] = Rho[wrapi(i0 - 2 + s, nx)];
     for (int q = 0; q < nq; q++) {
-        const T *Qq = Q + (size_t)q * nx;
+        const RatioSpec sp = spec(q);
         T a[C + 4];   // ratios of cells i0-2 .. i0+C+1
 #pragma unroll
         for (int s = 0; s < C + 4; s++) {
-            const int ii = wrapi(i0 - 2 + s, nx);
-            a[s] = q == 0 ? Qq[ii] : Qq[ii] * RI[ii];
+            const T v = sp.row[wrapi(i0 - 2 + s + sp.off, nx)];
+            a[s] = sp.div ? v / rho[s] : sp.a * v + sp.b;
         }
         T sl[C + 2];  // van Leer slopes of cells i0-1 .. i0+C
 #pragma unroll
@@ -169,7 +208,6 @@ __global__ void __launch_bounds__(512) k_transport_x(MeshD m, Tab<T> tb, Fld<T> 
 #pragma unroll
         for (int u = 0; u <= C; u++) {
             const T v = vf[u];
-            // donor cell i0+u-1 (v >= 0) or i0+u: index s in a[] = donor - (i0 - 2)
             const T stv = v >= T(0) ? a[u + 1] + sl[u] * (dX - v * dt) * T(0.5)
                                     : a[u + 2] - sl[u + 1] * (dX + v * dt) * T(0.5);
             if (q == 0) F0[u] = v * stv * S;
@@ -177,33 +215,37 @@ __global__ void __launch_bounds__(512) k_transport_x(MeshD m, Tab<T> tb, Fld<T> 
         }
 #pragma unroll
         for (int u = 0; u < C; u++)
-            if (u < cnt) out.q[q][base + i0 + u] = Qq[i0 + u] - dtVi * (F[u + 1] - F[u]);
+            if (u < cnt) {
+                const T old = q == 0 ? a[u + 2] : rho[u + 2] * a[u + 2];
+                out.q[q][base + i0 + u] = old - dtVi * (F[u + 1] - F[u]);
+            }
     }
 }
 
 // Uniform orbital step of each active ring (Sec. 3.4.1, Eqs. fargo2, 28-33),
 // applied after the Y and Z sweeps, in place:
-//  (ii)  circular shift by N = E(v0 dt / dX) (Eq. 32): the ring is rotated
-//        while it is staged in shared memory;
+//  (ii)  circular shift by N = E(v0 dt / dX) (Eq. 32): the ring is staged
+//        unrotated and read at the shifted index;
 //  (iii) fractional step at xi = v0 dt/dX - N with PPA interface values
 //        (Eqs. 34-36 and the xi-weighted value of Sec. 3.4.1), consistent
 //        transport, in the same pass.
 // N and xi are FP64 (round-to-nearest intrinsics), once per CTA.
 template <typename T, int C>
-__global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, const Scal *sc)
+__global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, Scal *sc)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_N;
+    __shared__ T s_x[2];
     const T dtT = step_dt<T>(sc);
     if (!(dtT > T(0))) return;
-    const int nx = m.nx, nq = qs.nq;
+    const int nx = m.nx, nq = qs.nq, pitch = (int)m.sj;
     const int r = blockIdx.x;
     const int ny = m.j1 - m.j0;
     const int j = m.j0 + r % ny, k = m.k0 + r / ny;
     const int ring = k * m.nyt + j;
     const long long base = IX(m, 0, j, k);
-    __shared__ int s_N;
-    __shared__ T s_x[2];
     if (threadIdx.x == 0) {
         const double dtd = sc->dt;
         const double X = __ddiv_rn(__dmul_rn(v0[ring], dtd), tb.lx[ring]);
@@ -217,23 +259,20 @@ __global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs,
     const int Nm = s_N;
     const T xsT = s_x[0];
     if (Nm == 0 && xsT == T(0)) return;
-    T *Q = sm;
-    T *RI = sm + (size_t)nq * nx;
-    for (int q = 0; q < nq; q++)
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            int s = i - Nm;
-            if (s < 0) s += nx;
-            const T v = qs.q[q][base + s];
-            Q[q * nx + i] = v;
-            if (q == 0) RI[i] = T(1) / v;
-        }
-    __syncthreads();
-    const int i0 = threadIdx.x * C;
-    if (xsT == T(0)) {   // a pure shift
-        for (int q = 0; q < nq; q++)
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) qs.q[q][base + i] = Q[q * nx + i];
+    const T *src[8];
+    for (int q = 0; q < nq; q++) src[q] = qs.q[q] + base;
+    if (!stage_rows(sm, pitch, src, nq, nx, &bar)) {
+        if (threadIdx.x == 0) atomicOr(&sc->err, kErrTimeout);
         return;
     }
+    // cell i after the shift holds the staged cell i - N
+    auto at = [&](int q, int i) -> T { return sm[(size_t)q * pitch + wrapi(i - Nm, nx)]; };
+    if (xsT == T(0)) {   // a pure shift
+        for (int q = 0; q < nq; q++)
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) qs.q[q][base + i] = at(q, i);
+        return;
+    }
+    const int i0 = threadIdx.x * C;
     if (i0 >= nx) return;
     const int cnt = min(C, nx - i0);
     const T S = tb.sx[ring];
@@ -242,15 +281,17 @@ __global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs,
     const bool pos = xsT >= T(0);
     const T xi = pos ? xsT : -xsT;
     const T sixth = T(1.0 / 6.0);
+    T rinv[C + 6], rho[C + 6];
+#pragma unroll
+    for (int s = 0; s < C + 6; s++) {
+        rho[s] = at(0, wrapi(i0 - 3 + s, nx));
+        rinv[s] = T(1) / rho[s];
+    }
     T F0[C + 1];
     for (int q = 0; q < nq; q++) {
-        const T *Qq = Q + (size_t)q * nx;
         T a[C + 6];   // ratios of cells i0-3 .. i0+C+2
 #pragma unroll
-        for (int s = 0; s < C + 6; s++) {
-            const int ii = wrapi(i0 - 3 + s, nx);
-            a[s] = q == 0 ? Qq[ii] : Qq[ii] * RI[ii];
-        }
+        for (int s = 0; s < C + 6; s++) a[s] = q == 0 ? rho[s] : at(q, wrapi(i0 - 3 + s, nx)) * rinv[s];
         T dm[C + 4];  // Eq. 34 slopes of cells i0-2 .. i0+C+1
 #pragma unroll
         for (int s = 0; s < C + 4; s++) dm[s] = ppa_dm(a[s], a[s + 1], a[s + 2]);
@@ -280,19 +321,19 @@ __global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs,
         }
 #pragma unroll
         for (int u = 0; u < C; u++)
-            if (u < cnt) qs.q[q][base + i0 + u] = Qq[i0 + u] - dtVi * (F[u + 1] - F[u]);
+            if (u < cnt) qs.q[q][base + i0 + u] = at(q, i0 + u) - dtVi * (F[u + 1] - F[u]);
     }
 }
 
 template <typename T, int C>
 static void launch_tx_c(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
-                        const Scal *sc, size_t smem, cudaStream_t s)
+                        Scal *sc, size_t smem, cudaStream_t s)
 {
     const int threads = ((m.nx + C - 1) / C + 31) / 32 * 32;
     k_transport_x<T, C><<<m.nyt * m.nzt, threads, smem, s>>>(m, tb, in, out, v0, sc);
 }
 template <typename T, int C>
-static void launch_orb_c(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, const Scal *sc,
+static void launch_orb_c(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, Scal *sc,
                          int nrings, size_t smem, cudaStream_t s)
 {
     const int threads = ((m.nx + C - 1) / C + 31) / 32 * 32;
@@ -311,7 +352,7 @@ static inline int ring_chunk(int nx)
 
 template <typename T>
 static void launch_tx(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
-                      const Scal *sc, size_t smem, cudaStream_t s)
+                      Scal *sc, size_t smem, cudaStream_t s)
 {
     switch (ring_chunk(m.nx)) {
     case 1: launch_tx_c<T, 1>(m, tb, in, out, v0, sc, smem, s); break;
@@ -322,7 +363,7 @@ static void launch_tx(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const 
     }
 }
 template <typename T>
-static void launch_orb(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, const Scal *sc,
+static void launch_orb(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, Scal *sc,
                        int nrings, size_t smem, cudaStream_t s)
 {
     switch (ring_chunk(m.nx)) {
@@ -564,6 +605,23 @@ static cudaError_t sweep_tma_attrs(int nq)
     }
 }
 
+// Pointer n of a quantity set through constant indices (a runtime index into
+// the parameter array would copy it to local memory).
+template <typename T>
+__device__ __forceinline__ T *qsel(const QSet<T> &s, int n)
+{
+    switch (n) {
+    case 0: return s.q[0];
+    case 1: return s.q[1];
+    case 2: return s.q[2];
+    case 3: return s.q[3];
+    case 4: return s.q[4];
+    case 5: return s.q[5];
+    case 6: return s.q[6];
+    default: return s.q[7];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // New face velocities from the new momenta and densities (Eq. 18), undoing
 // the geometric factors of Tab. "momenta", on interior faces; every other
@@ -589,12 +647,16 @@ __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin,
     const int ring = k * m.nyt + j;
     const T *rho = fin.q[0];
     const int o = m.iso ? 1 : 2;   // index of Pi-x in the quantity set
+    const T *pmx = m.iso ? fin.q[1] : fin.q[2], *ppx = m.iso ? fin.q[2] : fin.q[3];
+    const int oy = o + 2, oz = o + (m.hasY ? 4 : 2);
+    const T *pmy = qsel(fin, oy), *ppy = qsel(fin, oy + 1);
+    const T *pmz = qsel(fin, oz), *ppz = qsel(fin, oz + 1);
     if (j < m.nyt && k < m.nzt) {
         T v = vsrc.vx[c];
         if (jact && kact) {
             const long long cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
             const T R = tb.R[ring], w = R * R * tb.omega;
-            v = ((fin.q[o + 1][cm] + fin.q[o][c]) / (rho[cm] + rho[c]) - w) / R;
+            v = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
         }
         state.vx[c] = v;
         if (copy_scalars) {
@@ -602,12 +664,11 @@ __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin,
             if (!m.iso) state.e[c] = fin.q[1][c];
         }
     }
-    const int oy = o + 2, oz = o + (m.hasY ? 4 : 2);
     if (k < m.nzt) {
         T v = vsrc.vy[c];
         if (m.hasY && j > m.j0 && j < m.j1 && kact) {
             const long long cm = c - m.sj;
-            v = (fin.q[oy + 1][cm] + fin.q[oy][c]) / (rho[cm] + rho[c]);
+            v = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
         }
         state.vy[c] = v;
     }
@@ -615,7 +676,7 @@ __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin,
         T v = vsrc.vz[c];
         if (m.hasZ && k > m.k0 && k < m.k1 && jact) {
             const long long cm = c - m.sk;
-            v = (fin.q[oz + 1][cm] + fin.q[oz][c]) / (rho[cm] + rho[c]) / tb.fz[ring];
+            v = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
         }
         state.vz[c] = v;
     }

@@ -82,3 +82,14 @@ def momentum_density(w, st):
         vz = st["vz"][w.gz:w.gz + w.nz + 1, w.gy:w.gy + w.ny].astype(np.float64)
         out.append(rho * 0.5 * (vz[:-1] + vz[1:]))
     return np.stack(out)
+
+
+def record(name, **vals):
+    """Append measured parity figures to gpurun_out/parity_record.jsonl when
+    that folder exists (kept for the write-up; never read by a test)."""
+    import json
+    import os
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(d):
+        with open(os.path.join(d, "parity_record.jsonl"), "a") as f:
+            f.write(json.dumps({"case": name, **{k: float(v) for k, v in vals.items()}}) + "\n")

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import workloads as W
-from tests.gpu_util import active_faces, compare_state, fields_of, make_ctx, momentum_density, rel_l1, rel_linf
+from tests.gpu_util import active_faces, compare_state, fields_of, make_ctx, momentum_density, record, rel_l1, rel_linf
 
 pytestmark = pytest.mark.gpu
 
@@ -263,8 +263,11 @@ def test_fp32_disk_within_stated_tolerance():
         t += o.step(st, t, w.t_end)
         c.step(want_dt=False)
     g = c.get_state()
-    assert rel_l1(w.active(g["rho"]), w.active(st["rho"])) < 2e-5
-    assert rel_l1(momentum_density(w, g), momentum_density(w, st)) < 1e-4
+    e_rho = rel_l1(w.active(g["rho"]), w.active(st["rho"]))
+    e_mom = rel_l1(momentum_density(w, g), momentum_density(w, st))
+    record("fp32_disk_192x64_100steps", rel_l1_rho=e_rho, rel_l1_momentum=e_mom)
+    assert e_rho < 2e-5
+    assert e_mom < 1e-4
 
 
 def test_fp32_courant_step_bit_exact_on_promoted_state():
