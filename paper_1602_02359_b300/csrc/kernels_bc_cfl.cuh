@@ -192,7 +192,6 @@ __global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f
         const bool lit = m.av_lit != 0;
         const float k4 = (float)tb.k4;
         const bool avon = m.has_av != 0;
-#pragma unroll 2
         for (int i = lane; i < m.nx; i += 32) {
             const long long c = base + i;
             const int ip = i + 1 == m.nx ? 0 : i + 1;
