@@ -132,6 +132,39 @@ int fargo_get_scalars(fargo_ctx *ctx, double *t, double *dt_last, long long *nst
  * Synchronises. */
 int fargo_sums(fargo_ctx *ctx, double out[3]);
 
+/* Conserved totals of fargo_sums for a state held in caller buffers, with no
+ * device memory allocated by the call.  The paper has no counterpart; this
+ * exists for callers that cannot allocate device memory themselves: an
+ * application whose device memory belongs to another allocator (a framework
+ * pool or a fixed arena with a preset budget), or a latency-critical loop
+ * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree.
+ * Such a caller hands over its own buffers and needs no fargo_ctx.
+ *
+ * Inputs (device pointers, precision FARGO_F64 or FARGO_F32): rho, e (NULL
+ * when isothermal: out[1] = 0) and v_x in the FULL layout with a dense row
+ * pitch of nx values, i.e. shape (nz_t+1, ny_t+1, nx) for the mesh
+ * nx*ny*nz with `ghost` ghost layers; vol and R, the cell volume and the
+ * azimuthal lever arm (1 Cartesian, r cylindrical, r sin(theta) spherical)
+ * per ring, nz_t*ny_t FP64 values (j fastest); omega_frame as for the
+ * context.  Output: out, a device pointer to 3 FP64 values, written on
+ * `stream` (NULL = legacy default stream) in the order of fargo_sums.
+ * The call returns once the work is queued; synchronise the stream before
+ * reading out.
+ *
+ * Scratch: a library-wide device array of 1184 * 6 + 2 doubles (about
+ * 57 KB), allocated when the library is loaded and held by every GPU that
+ * loads it until the process exits.  nblocks (0 = four per SM) is the
+ * number of thread blocks, at most 1184; a larger value returns
+ * FARGO_ERR_SIZE.  The first call on each device (with that device
+ * current) looks up the array's device address; make that first call
+ * before any stream capture.  Every call shares the one array and the call
+ * clears its counter itself, so calls that overlap on the GPU (for example
+ * on two streams at once) race and must be serialised by the caller.
+ * Errors: BADARG, SIZE, CUDA. */
+int fargo_sums_noalloc(const void *rho, const void *e, const void *vx, int precision, int nx, int ny, int nz,
+                       int ghost, const double *vol, const double *R, double omega_frame, int nblocks,
+                       double *out, void *stream);
+
 /* Kernel-level access, for parity tests of single sub-steps.
  * phase: 0 ghost fill, 1 v0 + Courant reduction (the caller's dt is
  * ignored), 2 sub-step 1, 3 artificial viscosity + compression heating,

@@ -26,7 +26,7 @@ ERRORS = {0: "ok", -1: "BADARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "DT
 EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field", "fargo_set_time",
             "fargo_step", "fargo_step_fixed", "fargo_run_to", "fargo_get_scalars", "fargo_sums",
             "fargo_debug_phase", "fargo_get_aux", "fargo_set_aux", "fargo_use_graph",
-            "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step")
+            "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc")
 
 PD = C.POINTER(C.c_double)
 
@@ -79,6 +79,8 @@ def lib():
         L.fargo_launches_per_step.argtypes = [vp]
         L.fargo_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_char_p)]
+        L.fargo_sums_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
+                                         C.c_double, C.c_int, vp, vp]
         L.fargo_strerror.argtypes = [C.c_int]
         L.fargo_strerror.restype = C.c_char_p
         _lib = L
@@ -233,3 +235,16 @@ class Fargo:
 
     def launches_per_step(self):
         return lib().fargo_launches_per_step(self.h)
+
+
+def sums_noalloc(rho, e, vx, precision, nx, ny, nz, ghost, vol, R, omega_frame, out, nblocks=0, stream=None):
+    """Conserved totals of caller-owned device buffers without any device
+    allocation by the library (see fargo_sums_noalloc in include/fargo.h).
+    Buffers are torch CUDA tensors (or raw device addresses); `out` receives
+    3 FP64 values on `stream` (a raw cudaStream_t, None = legacy default)."""
+    def addr(t):
+        if t is None:
+            return None
+        return C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+    _check(lib().fargo_sums_noalloc(addr(rho), addr(e), addr(vx), precision, nx, ny, nz, ghost, addr(vol),
+                                    addr(R), omega_frame, nblocks, addr(out), stream), "fargo_sums_noalloc")

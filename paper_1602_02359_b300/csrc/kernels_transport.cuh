@@ -703,28 +703,41 @@ __device__ __forceinline__ void kb_merge(KB &a, const KB &b)
     a.c += b.c;
 }
 
+// What the sums need of a state: density, internal energy (NULL when
+// isothermal), azimuthal velocity, and per ring the volume and lever arm.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sums(MeshD m, Tab<T> tb, Fld<T> f, const double *vol, double *part,
-                                              Scal *sc, double *result)
+struct SumInput {
+    const T *rho, *e, *vx;
+    const double *vol, *R;
+    double omega;
+    int nx, j0, j1, k0, k1, nyt;
+    long long sj, sk;
+};
+
+// Per-block compensated partials of the three totals, then the last block to
+// finish (ticket counter) folds the partials in block order.  `part` holds
+// 6 doubles per block; `counter` starts at zero and is left at zero.
+template <typename T>
+__device__ void sums_reduce(const SumInput<T> &in, double *part, unsigned *counter, double *result)
 {
     __shared__ KB sh[3][256];
     __shared__ int s_last;
     KB acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    const int ny = m.j1 - m.j0, nz = m.k1 - m.k0;
-    const long long n = (long long)m.nx * ny * nz;
+    const int ny = in.j1 - in.j0, nz = in.k1 - in.k0;
+    const long long n = (long long)in.nx * ny * nz;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % m.nx);
-        const long long r = t / m.nx;
-        const int j = m.j0 + (int)(r % ny), k = m.k0 + (int)(r / ny);
-        const int ring = k * m.nyt + j;
-        const long long c = IX(m, i, j, k);
-        const double V = vol[ring];
-        const double rho = (double)f.rho[c];
+        const int i = (int)(t % in.nx);
+        const long long r = t / in.nx;
+        const int j = in.j0 + (int)(r % ny), k = in.k0 + (int)(r / ny);
+        const int ring = k * in.nyt + j;
+        const long long c = (long long)k * in.sk + (long long)j * in.sj + i;
+        const double V = in.vol[ring];
+        const double rho = (double)in.rho[c];
         kb_add(acc[0], rho * V);
-        if (!m.iso) kb_add(acc[1], (double)f.e[c] * V);
-        const double R = tb.Rd[ring], w = R * R * m.omega;
-        const int ip = i + 1 == m.nx ? 0 : i + 1;
-        const double pm = rho * (R * (double)f.vx[c] + w), pp = rho * (R * (double)f.vx[c - i + ip] + w);
+        if (in.e) kb_add(acc[1], (double)in.e[c] * V);
+        const double R = in.R[ring], w = R * R * in.omega;
+        const int ip = i + 1 == in.nx ? 0 : i + 1;
+        const double pm = rho * (R * (double)in.vx[c] + w), pp = rho * (R * (double)in.vx[c - i + ip] + w);
         kb_add(acc[2], 0.5 * (pm + pp) * V);
     }
     for (int q = 0; q < 3; q++) sh[q][threadIdx.x] = acc[q];
@@ -740,7 +753,7 @@ __global__ void __launch_bounds__(256) k_sums(MeshD m, Tab<T> tb, Fld<T> f, cons
             part[(blockIdx.x * 3 + q) * 2 + 1] = sh[q][0].c;
         }
         __threadfence();
-        s_last = atomicAdd(&sc->counter2, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!s_last || threadIdx.x != 0) return;
@@ -753,7 +766,13 @@ __global__ void __launch_bounds__(256) k_sums(MeshD m, Tab<T> tb, Fld<T> f, cons
         }
         result[q] = a.s + a.c;
     }
-    sc->counter2 = 0u;
+    *counter = 0u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sums(SumInput<T> in, double *part, unsigned *counter, double *result)
+{
+    sums_reduce<T>(in, part, counter, result);
 }
 
 }  // namespace fk
