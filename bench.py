@@ -19,6 +19,7 @@ rank advances its own replica and `value` is the total over ranks.
 workload on the host cores (rank 0 only).
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -34,23 +35,46 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-# Algorithmic bytes per active cell of each kernel: each field the kernel
-# must read or write, once (FP32 fields; FP64 doubles them).  3D adiabatic:
-# 5 state fields, 6 momenta.
+# Algorithmic bytes per active cell of each kernel (FP32; FP64 doubles them):
+# every field the kernel must read or write, once.  3D adiabatic step: state
+# rho, e, vx, vy, vz; six momenta; six viscous stresses.
 ALG_FIELDS_3D = {
-    "cfl": 5,            # rho, e, vx, vy, vz read
-    "substep1": 5 + 3,   # read state, write 3 velocities
-    "artvisc": 5 + 4,    # read rho, e, 3 v; write 3 v, e
-    "visc": 4 + 3,       # read rho, 3 v; write 3 v
-    "transport_x": 5 + 8,  # read rho, e, 3 v; write rho, e, 6 Pi
-    "transport_y": 9 + 8,  # read rho, e, 6 Pi, vy; write 8
+    "cfl_screen": 5,        # read rho, e, vx, vy, vz
+    "cfl_exact": 0,         # re-reads only the candidate rings (a few)
+    "substep1": 5 + 3,      # read the state, write 3 velocities
+    "artvisc": 5 + 4,       # read rho, e, 3 v; write 3 v, e
+    "visc_tau": 4 + 6,      # read rho, 3 v; write 6 stresses
+    "visc_apply": 10 + 3,   # read 6 stresses, rho, 3 v; write 3 v
+    "transport_x": 5 + 8,   # read rho, e, 3 v; write rho, e, 6 momenta
+    "transport_y": 9 + 8,   # read 8 quantities + v_y; write 8
     "transport_z": 9 + 8,
-    "newvel": 7 + 3,     # read rho, 6 Pi; write 3 v
+    "orbital": 8 + 8,       # read and write 8 quantities
+    "newvel": 7 + 3,        # read rho, 6 momenta; write 3 v
 }
+# 2D isothermal step: state rho, vx, vy; four momenta; three stresses.
 ALG_FIELDS_2D_ISO = {
-    "cfl": 3, "substep1": 3 + 2, "artvisc": 3 + 2, "visc": 3 + 2,
-    "transport_x": 3 + 5, "transport_y": 6 + 5, "newvel": 5 + 2,
+    "cfl_screen": 3, "cfl_exact": 0, "substep1": 3 + 2, "artvisc": 3 + 2, "visc_tau": 3 + 3,
+    "visc_apply": 6 + 2, "transport_x": 3 + 5, "transport_y": 6 + 5, "orbital": 5 + 5, "newvel": 5 + 2,
 }
+
+# DRAM bytes per active cell and launch measured by ncu (dram__bytes_read.sum
+# + dram__bytes_write.sum) on the 1536 x 128 x 48 case of the 3D disk, FP32,
+# with the kernel sources whose SHA-256 prefix is KERNEL_SRC_HASH (see
+# profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
+# cells, so a full launch is this figure times the cells; once the sources
+# change the figures no longer apply and the bench reports null.
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.25, "substep1": 33.35, "artvisc": 36.51, "visc_tau": 36.62, "visc_apply": 54.64, "transport_x": 60.58, "transport_y": 64.64, "transport_z": 65.79, "orbital": 70.83, "newvel": 54.01}
+KERNEL_SRC_HASH = "a7f09bbf09ba8ed5"
+
+
+def kernel_source_hash():
+    d = os.path.join(ROOT, "paper_1602_02359_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -312,10 +336,16 @@ def main():
     alg_bytes = table.get(top, 0) * esz * w.cells
     achieved = alg_bytes / (avg[top] * 1e-3) / 1e9
     share = {k: round(v / sum(avg.values()), 4) for k, v in sorted(avg.items(), key=lambda x: -x[1])}
+    per_kernel = {k: {"ms": round(v, 4), "alg_GBps": round(table.get(k, 0) * esz * w.cells / (v * 1e-3) / 1e9, 1)}
+                  for k, v in sorted(avg.items(), key=lambda x: -x[1]) if k in table}
+    traffic = None
+    if (fp32 and w.nz > 1 and not w.iso and top in TRAFFIC_PER_CELL_3D
+            and kernel_source_hash() == KERNEL_SRC_HASH):
+        traffic = int(TRAFFIC_PER_CELL_3D[top] * w.cells)
     roofline = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_kind": f"{peak_kind} copy bandwidth",
-                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(avg[top], 4), "traffic": None,
-                "kernel_share": share}
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(avg[top], 4), "traffic": traffic,
+                "kernel_share": share, "per_kernel": per_kernel}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
