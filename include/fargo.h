@@ -195,6 +195,58 @@ int fargo_launches_per_step(fargo_ctx *ctx);
 
 const char *fargo_strerror(int code);
 
+/* ------------------------------------------------------------------------
+ * Batched engine: n independent contexts (uneven meshes, parameters,
+ * geometries and boundary conditions; one precision) advanced together.
+ * Each member takes the step of Fig. 2 (cells 2-12) with its OWN Courant
+ * step (Sec. 3.4, Eq. 38) and time, exactly as fargo_step would take it:
+ * the batched kernels run the single-instance kernels' per-cell and
+ * per-ring code on every member, one launch per phase covering all
+ * members' blocks, and the step is captured once as a CUDA graph.  A member
+ * whose t reached its t_end (fargo_set_time) or whose error flag is set
+ * takes void steps.  The paper runs one problem at a time; the batch has
+ * no counterpart there.
+ *
+ * The batch borrows the members: it holds pointers to their device state,
+ * tables and tensor maps.  Destroy the batch before any member, and do not
+ * step a member on its own while batch work is in flight (call
+ * fargo_batch_status first, which synchronises).  Field and time accessors
+ * of a member (fargo_set_field, fargo_get_field, fargo_set_time,
+ * fargo_get_scalars) are valid between batch calls once
+ * fargo_batch_status has returned.
+ * ------------------------------------------------------------------------ */
+typedef struct fargo_batch fargo_batch;
+
+/* members: n distinct contexts of one precision.  stream: cudaStream_t of the
+ * batch (NULL = a stream the batch creates and owns).  Synchronises the
+ * members' streams.  Errors: BADARG (NULL, duplicate or mixed precision),
+ * OOM, CUDA. */
+int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, int n, void *stream);
+void fargo_batch_destroy(fargo_batch *b);
+
+/* Queue one step of every member (one graph launch); no host sync. */
+int fargo_batch_step(fargo_batch *b);
+
+/* Synchronise; n_running (may be NULL) = members with no error and t < t_end;
+ * first_failed (may be NULL) = lowest index of a member with an error, or -1.
+ * Returns that member's latched error (NONFINITE, DT, BARRIER_TIMEOUT) or OK. */
+int fargo_batch_status(fargo_batch *b, int *n_running, int *first_failed);
+
+/* Step until no member is running or max_steps batch steps were queued,
+ * checking fargo_batch_status every `poll` steps (>= 1).  steps_done and
+ * n_running may be NULL.  Errors as fargo_batch_status, BADARG. */
+int fargo_batch_run(fargo_batch *b, long long max_steps, int poll, long long *steps_done, int *n_running);
+
+/* Use (1) or bypass (0) the CUDA graph of the batched step (default 1). */
+int fargo_batch_use_graph(fargo_batch *b, int enable);
+
+/* Number of kernel launches one batched step queues. */
+int fargo_batch_launches_per_step(const fargo_batch *b);
+
+/* One batched step launched kernel by kernel with CUDA events between
+ * launches; as fargo_profile_step.  Synchronises. */
+int fargo_batch_profile_step(fargo_batch *b, int max_kernels, float *ms, int *n_out, const char **names);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,10 @@ ERRORS = {0: "ok", -1: "BADARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "DT
 EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field", "fargo_set_time",
             "fargo_step", "fargo_step_fixed", "fargo_run_to", "fargo_get_scalars", "fargo_sums",
             "fargo_debug_phase", "fargo_get_aux", "fargo_set_aux", "fargo_use_graph",
-            "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc")
+            "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
+            "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
+            "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
+            "fargo_batch_profile_step")
 
 PD = C.POINTER(C.c_double)
 
@@ -81,6 +84,16 @@ def lib():
                                          C.POINTER(C.c_char_p)]
         L.fargo_sums_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
                                          C.c_double, C.c_int, vp, vp]
+        L.fargo_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
+        L.fargo_batch_destroy.argtypes = [vp]
+        L.fargo_batch_destroy.restype = None
+        L.fargo_batch_step.argtypes = [vp]
+        L.fargo_batch_status.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.fargo_batch_run.argtypes = [vp, C.c_longlong, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+        L.fargo_batch_use_graph.argtypes = [vp, C.c_int]
+        L.fargo_batch_launches_per_step.argtypes = [vp]
+        L.fargo_batch_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int),
+                                               C.POINTER(C.c_char_p)]
         L.fargo_strerror.argtypes = [C.c_int]
         L.fargo_strerror.restype = C.c_char_p
         _lib = L
@@ -248,3 +261,64 @@ def sums_noalloc(rho, e, vx, precision, nx, ny, nz, ghost, vol, R, omega_frame, 
         return C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
     _check(lib().fargo_sums_noalloc(addr(rho), addr(e), addr(vx), precision, nx, ny, nz, ghost, addr(vol),
                                     addr(R), omega_frame, nblocks, addr(out), stream), "fargo_sums_noalloc")
+
+
+class FargoBatch:
+    """Independent contexts (one precision) stepped together by the batched
+    engine (fargo_batch_* in include/fargo.h), each with its own Courant step
+    and time.  The batch keeps its members alive and must be closed before
+    them; member accessors are valid after status()/run()."""
+
+    def __init__(self, members, stream=None):
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m.h for m in self.members])
+        h = C.c_void_p()
+        _check(lib().fargo_batch_create(C.byref(h), arr, len(self.members), stream), "fargo_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fargo_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, sync=True):
+        """Queue one step of every member; with sync, wait and raise on a
+        member's latched error."""
+        _check(lib().fargo_batch_step(self.h), "fargo_batch_step")
+        if sync:
+            return self.status()
+        return None
+
+    def status(self):
+        """(members still running, lowest failed member or -1); raises on error."""
+        run, first = C.c_int(), C.c_int()
+        rc = lib().fargo_batch_status(self.h, C.byref(run), C.byref(first))
+        if rc != 0:
+            raise FargoError(rc, f"fargo_batch_status (member {first.value})")
+        return run.value, first.value
+
+    def run(self, max_steps=10 ** 12, poll=64):
+        """Step until every member reached its end time; returns (steps, running)."""
+        n, run = C.c_longlong(), C.c_int()
+        _check(lib().fargo_batch_run(self.h, max_steps, poll, C.byref(n), C.byref(run)), "fargo_batch_run")
+        return n.value, run.value
+
+    def use_graph(self, on=True):
+        _check(lib().fargo_batch_use_graph(self.h, int(on)), "fargo_batch_use_graph")
+
+    def launches_per_step(self):
+        return lib().fargo_batch_launches_per_step(self.h)
+
+    def profile_step(self):
+        """One batched step launched kernel by kernel; returns [(kernel, ms), ...]."""
+        ms = (C.c_float * 64)()
+        names = (C.c_char_p * 64)()
+        n = C.c_int()
+        _check(lib().fargo_batch_profile_step(self.h, 64, ms, C.byref(n), names), "fargo_batch_profile_step")
+        return [(names[i].decode(), ms[i]) for i in range(n.value)]

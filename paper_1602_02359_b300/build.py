@@ -2,14 +2,16 @@
 
     python -m paper_1602_02359_b300.build
 
-Compiles csrc/fargo_api.cu (which includes every kernel) into
-libfargo_b300.so next to this file with nvcc.  Host code is compiled without
-floating-point contraction so that the FP64 geometry tables match a plain
-IEEE evaluation.
+Compiles the translation units csrc/fargo_api.cu (single-instance entry
+points) and csrc/fargo_batch.cu (batched engine) in parallel with nvcc, then
+links them into libfargo_b300.so next to this file.  Host code is compiled
+without floating-point contraction so that the FP64 geometry tables match a
+plain IEEE evaluation.
 """
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC_DIR = os.path.join(HERE, "csrc")
@@ -26,9 +28,14 @@ def sources():
     return out
 
 
-def nvcc_cmd(out=LIB, extra=()):
-    return ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC,-ffp-contract=off",
-            "-o", out, os.path.join(SRC_DIR, "fargo_api.cu"), *extra]
+UNITS = ("fargo_api.cu", "fargo_batch.cu")
+OBJ_DIR = os.path.join(HERE, "_build")
+FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
+
+
+def nvcc_cmd(unit, out, extra=()):
+    """Compile command of one translation unit into an object file."""
+    return ["nvcc", *FLAGS, "-c", "-o", out, os.path.join(SRC_DIR, unit), *extra]
 
 
 def build(force=False, verbose=False):
@@ -36,9 +43,16 @@ def build(force=False, verbose=False):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(s) <= t for s in sources()):
             return LIB
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    objs = [os.path.join(OBJ_DIR, u.replace(".cu", ".o")) for u in UNITS]
+    extra = ("-Xptxas", "-v") if verbose else ()
+    with ThreadPoolExecutor(len(UNITS)) as ex:
+        procs = list(ex.map(lambda a: subprocess.run(nvcc_cmd(*a, extra)), zip(UNITS, objs)))
+    for u, p in zip(UNITS, procs):
+        if p.returncode != 0:
+            raise subprocess.CalledProcessError(p.returncode, f"nvcc {u}")
     tmp = LIB + ".tmp"
-    cmd = nvcc_cmd(tmp, ("-Xptxas", "-v") if verbose else ())
-    subprocess.check_call(cmd)
+    subprocess.check_call(["nvcc", ARCH, "--shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)
     return LIB
 

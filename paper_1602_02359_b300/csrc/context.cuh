@@ -1,0 +1,188 @@
+// Host-side state of one hydro instance (the opaque fargo_ctx of the C ABI)
+// and the buffer routing of its step, shared by the single-instance entry
+// points (fargo_api.cu) and the batched engine (fargo_batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "../../include/fargo.h"
+#include "fargo_internal.cuh"
+#include "kernels_bc_cfl.cuh"
+#include "kernels_source.cuh"
+#include "kernels_transport.cuh"
+
+namespace fk {
+
+template <typename T>
+struct Buffers {
+    Fld<T> A{};                 // state: rho, e, vx, vy, vz
+    T *vB[3] = {nullptr, nullptr, nullptr};
+    T *piA[6] = {}, *piB[6] = {};
+    T *rhoB = nullptr, *eB = nullptr;
+    Tab<T> tab{};
+};
+
+struct HostGeom {
+    // FP64 tables, computed with the same expressions as a plain evaluation
+    std::vector<double> ym, dy, zm, dz, dyc, lx, ly, lz, dmin, R, zc, vol, fz, dzc;
+    std::vector<double> sx, vinv, sy, sz, lenz, gphy, gphz, cosx, sinx, cs, nu;
+    std::vector<double> rma, fra, z2, qar;
+};
+
+// Everything one step of one instance needs on the device: the mesh, its
+// tables, and the routing of the step, i.e. which buffers each phase reads
+// and writes.  Velocity buffers go A -> B -> A (-> B); the Y and Z sweeps are
+// out of place, and the X sweep is in place or not so that the last sweep
+// lands in the state buffers.
+template <typename T>
+struct StepPlan {
+    MeshD m;
+    Tab<T> tb;
+    Fld<T> A, VB;      // state and the scratch velocities of the source step
+    Fld<T> vsrc;       // post-source velocities (VB with viscosity, else A)
+    Fld<T> txin;       // input of the X sweep: state scalars, post-source velocities
+    QSet<T> qx, qy, qz;   // outputs of the X, Y and Z sweeps
+    QSet<T> qfin;      // quantity set after the sweeps (orbital step in place, new velocities)
+    QSet<T> tau;       // viscous stresses (the scratch momenta of set B)
+    Scal *sc;
+    double *v0, *part;
+    float *ringmax;
+    int nrings_active, cfl_blocks, seg_y, seg_z;
+};
+
+}  // namespace fk
+
+struct fargo_ctx {
+    int prec;  // FARGO_F64 / FARGO_F32
+    fk::MeshD m{};
+    int nx, ny, nz, g, geom;
+    int nyt, nzt, pitch;
+    size_t esz;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    fk::Scal *sc = nullptr;
+    double *v0 = nullptr, *part = nullptr, *part2 = nullptr, *sums = nullptr, *vol = nullptr;
+    float *ringmax = nullptr;
+    int nrings_active = 0, cfl_blocks = 0, sum_blocks = 0;
+    fk::Buffers<double> b64;
+    fk::Buffers<float> b32;
+    std::vector<void *> allocs;
+    fk::HostGeom hg;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    int launches = 0;
+    size_t tx_smem = 0;
+    int tx_threads = 256;
+    std::vector<double> yfaces_store, zfaces_store;
+    fk::SweepMaps mapsY{}, mapsZ{};   // tensor maps of the Y and Z sweeps of the step
+};
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            fprintf(stderr, "fargo: %s failed: %s\n", #call, cudaGetErrorString(e_));           \
+            return e_ == cudaErrorMemoryAllocation ? FARGO_ERR_OOM : FARGO_ERR_CUDA;              \
+        }                                                                                        \
+    } while (0)
+
+namespace fk {
+
+// Quantity sets (Sec. 3.2): rho, e (adiabatic), Pi-/+ of each active direction.
+template <typename T>
+static QSet<T> qset(const fargo_ctx *c, T *rho, T *e, T *const *pi)
+{
+    QSet<T> s{};
+    int n = 0;
+    s.q[n++] = rho;
+    if (!c->m.iso) s.q[n++] = e;
+    s.q[n++] = pi[0];
+    s.q[n++] = pi[1];
+    if (c->m.hasY) {
+        s.q[n++] = pi[2];
+        s.q[n++] = pi[3];
+    }
+    if (c->m.hasZ) {
+        s.q[n++] = pi[4];
+        s.q[n++] = pi[5];
+    }
+    s.nq = n;
+    return s;
+}
+
+template <typename T>
+static StepPlan<T> make_plan(const fargo_ctx *c, const Buffers<T> &b)
+{
+    StepPlan<T> p{};
+    const MeshD &m = c->m;
+    p.m = m;
+    p.tb = b.tab;
+    p.A = b.A;
+    p.VB = {b.A.rho, b.A.e, b.vB[0], b.vB[1], b.vB[2]};
+    p.vsrc = m.has_nu ? p.VB : p.A;
+    p.txin = {b.A.rho, b.A.e, p.vsrc.vx, p.vsrc.vy, p.vsrc.vz};
+    for (int q = 0; q < 6; q++) p.tau.q[q] = b.piB[q];
+    p.tau.nq = 6;
+    QSet<T> qa = qset<T>(c, b.A.rho, b.A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);
+    const bool x_out = ((m.hasY + m.hasZ) % 2) == 1;
+    p.qx = x_out ? qb : qa;
+    QSet<T> cur = p.qx, oth = x_out ? qa : qb;
+    if (m.hasY) {
+        p.qy = oth;
+        QSet<T> t = cur; cur = oth; oth = t;
+    }
+    if (m.hasZ) {
+        p.qz = oth;
+        QSet<T> t = cur; cur = oth; oth = t;
+    }
+    p.qfin = cur;   // the state set qa again
+    p.sc = c->sc;
+    p.v0 = c->v0;
+    p.part = c->part;
+    p.ringmax = c->ringmax;
+    p.nrings_active = c->nrings_active;
+    p.cfl_blocks = c->cfl_blocks;
+    p.seg_y = sweep_seglen(m.j1 - m.j0);
+    p.seg_z = sweep_seglen(m.k1 - m.k0);
+    return p;
+}
+
+static inline int err_code(int flags)
+{
+    if (flags & 1) return FARGO_ERR_NONFINITE;
+    if (flags & 2) return FARGO_ERR_DT;
+    if (flags & kErrTimeout) return FARGO_ERR_BARRIER_TIMEOUT;
+    return FARGO_OK;
+}
+
+// 3D launch shape of the per-cell kernels: x = azimuth, y = rows, z = planes.
+static inline dim3 cell_block(const MeshD &m)
+{
+    int bx = (m.nx + 31) / 32 * 32;
+    return dim3(bx < 256 ? bx : 256, 1, 1);
+}
+static inline dim3 cell_grid(const MeshD &m, int ny, int nz)
+{
+    const dim3 b = cell_block(m);
+    return dim3((m.nx + b.x - 1) / b.x, ny, nz);
+}
+
+static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Raise (never lower) a kernel's dynamic shared-memory cap: the cap is per
+// function and process-wide, so lowering it for one context would break
+// another context's launches.
+template <typename F>
+static cudaError_t raise_smem_cap(F *func, size_t bytes)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace fk

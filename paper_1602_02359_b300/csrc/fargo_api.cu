@@ -8,63 +8,9 @@
 #include <cstring>
 #include <vector>
 
-#include "../../include/fargo.h"
-#include "fargo_internal.cuh"
-#include "kernels_bc_cfl.cuh"
-#include "kernels_source.cuh"
-#include "kernels_transport.cuh"
+#include "context.cuh"
 
 using namespace fk;
-
-namespace {
-
-struct DevBuf {
-    void *p = nullptr;
-};
-
-template <typename T>
-struct Buffers {
-    Fld<T> A{};                 // state: rho, e, vx, vy, vz
-    T *vB[3] = {nullptr, nullptr, nullptr};
-    T *piA[6] = {}, *piB[6] = {};
-    T *rhoB = nullptr, *eB = nullptr;
-    Tab<T> tab{};
-};
-
-struct HostGeom {
-    // FP64 tables, computed with the same expressions as a plain evaluation
-    std::vector<double> ym, dy, zm, dz, dyc, lx, ly, lz, dmin, R, zc, vol, fz, dzc;
-    std::vector<double> sx, vinv, sy, sz, lenz, gphy, gphz, cosx, sinx, cs, nu;
-    std::vector<double> rma, fra, z2, qar;
-};
-
-}  // namespace
-
-struct fargo_ctx {
-    int prec;  // FARGO_F64 / FARGO_F32
-    MeshD m{};
-    int nx, ny, nz, g, geom;
-    int nyt, nzt, pitch;
-    size_t esz;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    Scal *sc = nullptr;
-    double *v0 = nullptr, *part = nullptr, *part2 = nullptr, *sums = nullptr, *vol = nullptr;
-    float *ringmax = nullptr;
-    int nrings_active = 0, cfl_blocks = 0, sum_blocks = 0;
-    Buffers<double> b64;
-    Buffers<float> b32;
-    std::vector<void *> allocs;
-    HostGeom hg;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    bool use_graph = true;
-    int launches = 0;
-    size_t tx_smem = 0;
-    int tx_threads = 256;
-    std::vector<double> yfaces_store, zfaces_store;
-    SweepMaps mapsY{}, mapsZ{};   // tensor maps of the Y and Z sweeps of the step
-};
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -123,15 +69,6 @@ extern "C" const char *fargo_strerror(int code)
     if (code > 0 || code < -8) return "unknown error";
     return g_errstr[-code];
 }
-
-#define CK(call)                                                                                 \
-    do {                                                                                         \
-        cudaError_t e_ = (call);                                                                 \
-        if (e_ != cudaSuccess) {                                                                 \
-            fprintf(stderr, "fargo: %s failed: %s\n", #call, cudaGetErrorString(e_));           \
-            return e_ == cudaErrorMemoryAllocation ? FARGO_ERR_OOM : FARGO_ERR_CUDA;              \
-        }                                                                                        \
-    } while (0)
 
 static int dalloc(fargo_ctx *c, void **p, size_t bytes)
 {
@@ -372,42 +309,6 @@ static int alloc_fields(fargo_ctx *c, Buffers<T> &b)
     return build_tables<T>(c, b.tab);
 }
 
-// Quantity sets (Sec. 3.2): rho, e (adiabatic), Pi-/+ of each active direction.
-template <typename T>
-static QSet<T> qset(const fargo_ctx *c, T *rho, T *e, T *const *pi)
-{
-    QSet<T> s{};
-    int n = 0;
-    s.q[n++] = rho;
-    if (!c->m.iso) s.q[n++] = e;
-    s.q[n++] = pi[0];
-    s.q[n++] = pi[1];
-    if (c->m.hasY) {
-        s.q[n++] = pi[2];
-        s.q[n++] = pi[3];
-    }
-    if (c->m.hasZ) {
-        s.q[n++] = pi[4];
-        s.q[n++] = pi[5];
-    }
-    s.nq = n;
-    return s;
-}
-
-static unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
-
-// 3D launch shape of the per-cell kernels: x = azimuth, y = rows, z = planes.
-static dim3 cell_block(const MeshD &m)
-{
-    int bx = (m.nx + 31) / 32 * 32;
-    return dim3(bx < 256 ? bx : 256, 1, 1);
-}
-static dim3 cell_grid(const MeshD &m, int ny, int nz)
-{
-    const dim3 b = cell_block(m);
-    return dim3((m.nx + b.x - 1) / b.x, ny, nz);
-}
-
 // ---------------------------------------------------------------------------
 // The launch sequence of one full update (flow chart cells 2-12).
 // Velocity buffers ping-pong A -> B -> A (-> B); the Y and Z sweeps are
@@ -424,7 +325,8 @@ struct Prof {
 template <typename T>
 static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
 {
-    const MeshD &m = c->m;
+    const StepPlan<T> P = make_plan<T>(c, b);
+    const MeshD &m = P.m;
     cudaStream_t s = c->stream;
     const int bs = 256;
     int nl = 0;
@@ -436,57 +338,43 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         }                                                           \
         nl++;                                                       \
     } while (0)
-    Fld<T> A = b.A;
-    Fld<T> VB = {A.rho, A.e, b.vB[0], b.vB[1], b.vB[2]};
+    const dim3 cb = cell_block(m), cg = cell_grid(m, m.nyt + 1, m.nzt + 1);
     // cell 2
-    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 0); MARK("bc_y"); }
-    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 0); MARK("bc_z"); }
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_y"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_z"); }
     // cells 3-6
-    k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
-                                                  c->nrings_active);
+    k_cfl_screen<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_screen");
-    k_cfl_exact<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc, c->nrings_active);
+    k_cfl_exact<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_exact");
     // cell 7
-    k_substep1<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, c->sc); MARK("substep1");
-    k_artvisc<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, VB, A, c->sc); MARK("artvisc");
-    Fld<T> vsrc = A;
+    k_substep1<T><<<cg, cb, 0, s>>>(m, P.tb, P.A, P.VB, P.sc); MARK("substep1");
+    k_artvisc<T><<<cg, cb, 0, s>>>(m, P.tb, P.VB, P.A, P.sc); MARK("artvisc");
     if (m.has_nu) {
         // stresses once into the scratch momenta of set B (unused until the transport step)
-        QSet<T> tau{};
-        for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
-        tau.nq = 6;
-        k_visc_tau<T><<<cell_grid(m, m.j1 - m.j0 + 1, m.k1 - m.k0 + 1), cell_block(m), 0, s>>>(m, b.tab, A, tau, c->sc); MARK("visc_tau");
-        k_visc_apply<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, tau, c->sc); MARK("visc_apply");
-        vsrc = VB;
+        k_visc_tau<T><<<cell_grid(m, m.j1 - m.j0 + 1, m.k1 - m.k0 + 1), cb, 0, s>>>(m, P.tb, P.A, P.tau, P.sc); MARK("visc_tau");
+        k_visc_apply<T><<<cg, cb, 0, s>>>(m, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
     }
     // cell 9
-    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, vsrc, c->sc, 1); MARK("bc_y9"); }
-    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, vsrc, c->sc, 1); MARK("bc_z9"); }
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_y9"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_z9"); }
     // cell 12
-    QSet<T> qa = qset<T>(c, A.rho, A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);
-    const int nyz = m.hasY + m.hasZ;
-    const bool x_out = (nyz % 2) == 1;
-    Fld<T> tx_in = {A.rho, A.e, vsrc.vx, vsrc.vy, vsrc.vz};
-    launch_tx<T>(m, b.tab, tx_in, x_out ? qb : qa, c->v0, c->sc, c->tx_smem, s);
+    launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_smem, s);
     MARK("transport_x");
-    QSet<T> cur = x_out ? qb : qa, oth = x_out ? qa : qb;
     if (m.hasY) {
-        launch_sweep_tma<T, 1>(m, b.tab, c->mapsY, oth, c->sc, cur.nq, s);
+        launch_sweep_tma<T, 1>(m, P.tb, c->mapsY, P.qy, P.sc, P.qx.nq, s);
         MARK("transport_y");
-        QSet<T> t = cur; cur = oth; oth = t;
     }
     if (m.hasZ) {
-        launch_sweep_tma<T, 2>(m, b.tab, c->mapsZ, oth, c->sc, cur.nq, s);
+        launch_sweep_tma<T, 2>(m, P.tb, c->mapsZ, P.qz, P.sc, P.qx.nq, s);
         MARK("transport_z");
-        QSet<T> t = cur; cur = oth; oth = t;
     }
-    // cur is the state quantity set again (qa); the uniform orbital step comes last
+    // the uniform orbital step comes last, in place on the state set
     if (m.fargo && m.hasX) {
-        launch_orb<T>(m, b.tab, cur, c->v0, c->sc, c->nrings_active, c->tx_smem, s);
+        launch_orb<T>(m, P.tb, P.qfin, P.v0, P.sc, P.nrings_active, c->tx_smem, s);
         MARK("orbital");
     }
-    k_newvel<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, cur, vsrc, A, c->sc, 0); MARK("newvel");
+    k_newvel<T><<<cg, cb, 0, s>>>(m, P.tb, P.qfin, P.vsrc, P.A, P.sc, 0); MARK("newvel");
 #undef MARK
     c->launches = nl;
     if (prof) prof->n = nl;
@@ -520,25 +408,21 @@ static int launch_step(fargo_ctx *c)
 // enqueue_step: the X sweep is in place when an even number of Y/Z sweeps
 // follows it; the Z sweep after a Y sweep reads its ghost planes from the
 // Y sweep's input (the Y sweep writes active cells only).
+// Tensor maps of the step's Y and Z sweeps, following the plan's buffer
+// routing; the Z sweep after a Y sweep reads its ghost planes from the Y
+// sweep's input (the Y sweep writes active cells only).
 template <typename T>
 static int build_sweep_maps(fargo_ctx *c, Buffers<T> &b)
 {
-    const MeshD &m = c->m;
-    QSet<T> qa = qset<T>(c, b.A.rho, b.A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);
-    const T *vy = m.has_nu ? b.vB[1] : b.A.vy;
-    const T *vz = m.has_nu ? b.vB[2] : b.A.vz;
-    const bool x_out = ((m.hasY + m.hasZ) % 2) == 1;
-    QSet<T> cur = x_out ? qb : qa, oth = x_out ? qa : qb;
+    const StepPlan<T> P = make_plan<T>(c, b);
+    const MeshD &m = P.m;
     int rc;
-    QSet<T> before_y = cur;
-    if (m.hasY) {
-        if ((rc = encode_sweep_maps<T>(c, &c->mapsY, cur, cur, vy))) return rc;
-        QSet<T> t = cur; cur = oth; oth = t;
-    }
+    if (m.hasY && (rc = encode_sweep_maps<T>(c, &c->mapsY, P.qx, P.qx, P.vsrc.vy))) return rc;
     if (m.hasZ) {
-        if ((rc = encode_sweep_maps<T>(c, &c->mapsZ, cur, m.hasY ? before_y : cur, vz))) return rc;
+        const QSet<T> &zin = m.hasY ? P.qy : P.qx;
+        if ((rc = encode_sweep_maps<T>(c, &c->mapsZ, zin, P.qx, P.vsrc.vz))) return rc;
     }
-    const int nq = cur.nq;
+    const int nq = P.qx.nq;
     CK((sweep_tma_attrs<T, 1>(nq)));
     CK((sweep_tma_attrs<T, 2>(nq)));
     return FARGO_OK;
@@ -551,23 +435,21 @@ static int set_kernel_attrs(fargo_ctx *c)
     CK(cudaGetDevice(&dev));
     int maxsm = 0;
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
-    nq -= 0;
+    const int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
     // ring kernels stage at most max(nq, 7) rows of one pitch each
     size_t smem = (size_t)(nq > 7 ? nq : 7) * c->pitch * sizeof(T);
     if (smem > (size_t)maxsm - 1024 || ring_chunk(c->nx) == 0) return FARGO_ERR_SIZE;
     c->tx_smem = smem;
-    const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    CK(cudaFuncSetAttribute(k_transport_x<T, 1>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_transport_x<T, 2>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_transport_x<T, 3>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_transport_x<T, 4>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_transport_x<T, 8>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_orbital<T, 1>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_orbital<T, 2>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_orbital<T, 3>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_orbital<T, 4>, (cudaFuncAttribute)a, (int)smem));
-    CK(cudaFuncSetAttribute(k_orbital<T, 8>, (cudaFuncAttribute)a, (int)smem));
+    CK(raise_smem_cap(k_transport_x<T, 1>, smem));
+    CK(raise_smem_cap(k_transport_x<T, 2>, smem));
+    CK(raise_smem_cap(k_transport_x<T, 3>, smem));
+    CK(raise_smem_cap(k_transport_x<T, 4>, smem));
+    CK(raise_smem_cap(k_transport_x<T, 8>, smem));
+    CK(raise_smem_cap(k_orbital<T, 1>, smem));
+    CK(raise_smem_cap(k_orbital<T, 2>, smem));
+    CK(raise_smem_cap(k_orbital<T, 3>, smem));
+    CK(raise_smem_cap(k_orbital<T, 4>, smem));
+    CK(raise_smem_cap(k_orbital<T, 8>, smem));
     return FARGO_OK;
 }
 
@@ -754,14 +636,6 @@ static int read_scal(fargo_ctx *c, Scal *s)
 {
     CK(cudaMemcpyAsync(s, c->sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    return FARGO_OK;
-}
-
-static int err_code(int flags)
-{
-    if (flags & 1) return FARGO_ERR_NONFINITE;
-    if (flags & 2) return FARGO_ERR_DT;
-    if (flags & kErrTimeout) return FARGO_ERR_BARRIER_TIMEOUT;
     return FARGO_OK;
 }
 

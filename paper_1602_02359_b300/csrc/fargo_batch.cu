@@ -1,0 +1,605 @@
+// Batched engine: many independent hydro instances (uneven meshes and
+// parameters) advanced together.  Each phase of the step is ONE launch
+// whose blocks cover every member's work for that phase; a block finds its
+// member by a binary search over the launch's block offsets and runs the
+// same device body as the single-instance kernel on that member's mesh,
+// tables and buffers.  Every member keeps its own Courant step and time
+// (its own two-stage reduction and device scalars), so members that reached
+// their end time or failed drop out on the device without host involvement.
+// The sequence of launches is captured once as a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "context.cuh"
+
+using namespace fk;
+
+namespace fk {
+
+// The members that share one launch of a phase kernel.
+struct Group {
+    const int *ids;   // member index of each entry
+    const int *off;   // first block of each entry; off[n] = blocks of the launch
+    int n;
+};
+
+// Member of block b and the block's index within that member's work.
+__device__ __forceinline__ int group_member(const Group &g, int b, int &local)
+{
+    int lo = 0, hi = g.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&g.off[mid]) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    local = b - __ldg(&g.off[lo]);
+    return __ldg(&g.ids[lo]);
+}
+
+enum { PH_SUB1, PH_AV, PH_TAU, PH_VAPPLY, PH_NEWVEL };
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_bc(const StepPlan<T> *__restrict__ P, Group g, int axis, int mode)
+{
+    int local;
+    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    const long long tid = (long long)local * blockDim.x + threadIdx.x;
+    if (axis == 1) bc_y_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid);
+    else bc_z_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_cfl_screen(const StepPlan<T> *__restrict__ P, Group g)
+{
+    int local;
+    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    cfl_screen_body(p.m, p.tb, p.A, p.v0, p.ringmax, p.part, p.sc, p.nrings_active, local, p.cfl_blocks);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_cfl_exact(const StepPlan<T> *__restrict__ P, Group g)
+{
+    int local;
+    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    cfl_exact_body(p.m, p.tb, p.A, p.v0, p.ringmax, p.part, p.sc, p.nrings_active, local, p.cfl_blocks);
+}
+
+// Per-cell phases: a member's blocks tile (azimuth, row, plane) as the
+// single-instance grid does, with blockDim.x azimuths per block.
+template <typename T, int PH>
+__global__ void __launch_bounds__(256) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
+{
+    int local;
+    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    const MeshD &m = p.m;
+    const int nbx = (m.nx + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int nyr = PH == PH_TAU ? m.j1 - m.j0 + 1 : m.nyt + 1;
+    const int bx = local % nbx, r = local / nbx;
+    int by = r % nyr, bz = r / nyr;
+    if constexpr (PH == PH_TAU) {
+        by += m.j0;
+        bz += m.k0;
+    }
+    if constexpr (PH == PH_SUB1) substep1_body(m, p.tb, p.A, p.VB, p.sc, bx, by, bz);
+    else if constexpr (PH == PH_AV) artvisc_body(m, p.tb, p.VB, p.A, p.sc, bx, by, bz);
+    else if constexpr (PH == PH_TAU) visc_tau_body(m, p.tb, p.A, p.tau, p.sc, bx, by, bz);
+    else if constexpr (PH == PH_VAPPLY) visc_apply_body(m, p.tb, p.A, p.VB, p.tau, p.sc, bx, by, bz);
+    else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, bx, by, bz);
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(512, 2) kb_tx(const StepPlan<T> *__restrict__ P, Group g)
+{
+    int local;
+    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    transport_x_body<T, C>(p.m, p.tb, p.txin, p.qx, p.v0, p.sc, local);
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(512) kb_orb(const StepPlan<T> *__restrict__ P, Group g)
+{
+    int local;
+    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    orbital_body<T, C>(p.m, p.tb, p.qfin, p.v0, p.sc, local);
+}
+
+// Tensor maps of every member live in global memory (64-byte aligned).
+template <typename T, int AXIS, int NQ>
+__global__ void __launch_bounds__(TmaTile<T>::TW + 32) kb_sweep(const StepPlan<T> *__restrict__ P,
+                                                                 const SweepMaps *__restrict__ maps, Group g)
+{
+    int local;
+    const int id = group_member(g, blockIdx.x, local);
+    const StepPlan<T> &p = P[id];
+    sweep_body<T, AXIS, NQ>(p.m, p.tb, maps[id], AXIS == 1 ? p.qy : p.qz, p.sc, AXIS == 1 ? p.seg_y : p.seg_z,
+                            local);
+}
+
+// out[0] = members still running, out[1] = OR of their error flags,
+// out[2] = lowest index of a failed member (n if none).
+__global__ void __launch_bounds__(256) kb_status(Scal *const *sc, int n, int *out)
+{
+    __shared__ int s_run, s_err, s_first;
+    if (threadIdx.x == 0) {
+        s_run = 0;
+        s_err = 0;
+        s_first = n;
+    }
+    __syncthreads();
+    int run = 0, err = 0, first = n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Scal *s = sc[i];
+        const int e = s->err;
+        err |= e;
+        if (e && i < first) first = i;
+        if (!e && (s->fixed || s->t < s->t_end)) run++;
+    }
+    atomicAdd(&s_run, run);
+    atomicOr(&s_err, err);
+    atomicMin(&s_first, first);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = s_run;
+        out[1] = s_err;
+        out[2] = s_first;
+    }
+}
+
+}  // namespace fk
+
+namespace {
+
+enum LaunchKind { L_BC, L_SCREEN, L_EXACT, L_CELL, L_TX, L_SWEEP, L_ORB };
+
+// One launch of the batched step: a phase over a group of members.
+struct BLaunch {
+    LaunchKind kind;
+    int arg = 0;       // BC: axis; CELL: phase; SWEEP: axis
+    int mode = 0;      // BC: 0 = cell 2, 1 = cell 9
+    int key = 0;       // ring kernels: cells per thread; sweeps: quantities
+    std::vector<int> ids, off;
+    int *d = nullptr;  // device copy: ids, then off
+    int threads = 256;
+    size_t smem = 0;
+    const char *name = "";
+    Group dev() const { return Group{d, d + ids.size(), (int)ids.size()}; }
+    int blocks() const { return off.empty() ? 0 : off.back(); }
+};
+
+}  // namespace
+
+struct fargo_batch {
+    int n = 0, prec = FARGO_F32;
+    std::vector<fargo_ctx *> mem;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *plans = nullptr;                    // StepPlan<T>[n]
+    SweepMaps *mapsY = nullptr, *mapsZ = nullptr;
+    Scal **scs = nullptr;
+    int *status = nullptr;                    // device: run, err, first failed
+    int *hstatus = nullptr;                   // pinned host copy
+    std::vector<void *> allocs;
+    std::vector<BLaunch> seq;                 // the launches of one step, in order
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    long long steps = 0;
+};
+
+static int balloc(fargo_batch *b, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? FARGO_ERR_OOM : FARGO_ERR_CUDA;
+    }
+    b->allocs.push_back(*p);
+    return FARGO_OK;
+}
+
+// Group the eligible members of a phase by `key` (one launch per key value)
+// with `blocks(member)` blocks each.
+template <typename Elig, typename Key, typename Blocks>
+static void add_phase(fargo_batch *b, BLaunch proto, Elig elig, Key key, Blocks blocks)
+{
+    std::map<int, BLaunch> by;
+    for (int i = 0; i < b->n; i++) {
+        if (!elig(b->mem[i])) continue;
+        const int k = key(b->mem[i]);
+        auto it = by.find(k);
+        if (it == by.end()) {
+            BLaunch L = proto;
+            L.key = k;
+            L.off.push_back(0);
+            it = by.emplace(k, L).first;
+        }
+        BLaunch &L = it->second;
+        L.ids.push_back(i);
+        L.off.push_back(L.off.back() + blocks(b->mem[i]));
+    }
+    for (auto &kv : by) b->seq.push_back(kv.second);
+}
+
+template <typename T>
+static const Buffers<T> &bufs(const fargo_ctx *c);
+template <>
+const Buffers<double> &bufs<double>(const fargo_ctx *c) { return c->b64; }
+template <>
+const Buffers<float> &bufs<float>(const fargo_ctx *c) { return c->b32; }
+
+template <typename T, int C>
+static cudaError_t ring_attrs(size_t smem)
+{
+    cudaError_t e = raise_smem_cap(kb_tx<T, C>, smem);
+    if (e == cudaSuccess) e = raise_smem_cap(kb_orb<T, C>, smem);
+    return e;
+}
+
+template <typename T, int AXIS>
+static cudaError_t sweep_attrs(int nq)
+{
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int sm = (int)sweep_tma_smem<T, AXIS>(nq);
+    switch (nq) {
+    case 3: return cudaFuncSetAttribute(kb_sweep<T, AXIS, 3>, a, sm);
+    case 4: return cudaFuncSetAttribute(kb_sweep<T, AXIS, 4>, a, sm);
+    case 5: return cudaFuncSetAttribute(kb_sweep<T, AXIS, 5>, a, sm);
+    case 6: return cudaFuncSetAttribute(kb_sweep<T, AXIS, 6>, a, sm);
+    case 7: return cudaFuncSetAttribute(kb_sweep<T, AXIS, 7>, a, sm);
+    default: return cudaFuncSetAttribute(kb_sweep<T, AXIS, 8>, a, sm);
+    }
+}
+
+// Build the launch sequence (the same phase order as the single-instance
+// step) and upload the plans, tensor maps and groups.
+template <typename T>
+static int batch_setup(fargo_batch *b)
+{
+    const int n = b->n;
+    std::vector<StepPlan<T>> plans(n);
+    std::vector<SweepMaps> my(n), mz(n);
+    std::vector<Scal *> scs(n);
+    for (int i = 0; i < n; i++) {
+        plans[i] = make_plan<T>(b->mem[i], bufs<T>(b->mem[i]));
+        my[i] = b->mem[i]->mapsY;
+        mz[i] = b->mem[i]->mapsZ;
+        scs[i] = b->mem[i]->sc;
+    }
+    auto all = [](const fargo_ctx *) { return true; };
+    auto one = [](const fargo_ctx *) { return 0; };
+    auto cells = [](const fargo_ctx *c) { return ((c->nx + 255) / 256) * (c->nyt + 1) * (c->nzt + 1); };
+    auto tau_cells = [](const fargo_ctx *c) {
+        return ((c->nx + 255) / 256) * (c->m.j1 - c->m.j0 + 1) * (c->m.k1 - c->m.k0 + 1);
+    };
+    auto hasY = [](const fargo_ctx *c) { return c->m.hasY != 0; };
+    auto hasZ = [](const fargo_ctx *c) { return c->m.hasZ != 0; };
+    auto hasNu = [](const fargo_ctx *c) { return c->m.has_nu != 0; };
+    auto bcy = [](const fargo_ctx *c) { return (int)grid_for((long long)c->nx * (c->nzt + 1) * 2, 256); };
+    auto bcz = [](const fargo_ctx *c) { return (int)grid_for((long long)c->nx * (c->nyt + 1) * 2, 256); };
+    auto chunk = [](const fargo_ctx *c) { return ring_chunk(c->nx); };
+    auto nqk = [](const fargo_ctx *c) { return 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0); };
+    auto sweep_blocks = [](int axis) {
+        return [axis](const fargo_ctx *c) {
+            const MeshD &m = c->m;
+            const int np = axis == 1 ? m.j1 - m.j0 : m.k1 - m.k0;
+            const int n2 = axis == 1 ? m.k1 - m.k0 : m.j1 - m.j0;
+            const int sl = sweep_seglen(np);
+            const int ntx = (m.nx + TmaTile<T>::TW - 1) / TmaTile<T>::TW;
+            return ntx * n2 * ((np + sl - 1) / sl);
+        };
+    };
+    BLaunch L;
+    b->seq.clear();
+    L = BLaunch{L_BC}; L.arg = 1; L.mode = 0; L.name = "bc_y";
+    add_phase(b, L, hasY, one, bcy);
+    L = BLaunch{L_BC}; L.arg = 2; L.mode = 0; L.name = "bc_z";
+    add_phase(b, L, hasZ, one, bcz);
+    L = BLaunch{L_SCREEN}; L.name = "cfl_screen";
+    add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
+    L = BLaunch{L_EXACT}; L.name = "cfl_exact";
+    add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
+    L = BLaunch{L_CELL}; L.arg = PH_SUB1; L.name = "substep1";
+    add_phase(b, L, all, one, cells);
+    L = BLaunch{L_CELL}; L.arg = PH_AV; L.name = "artvisc";
+    add_phase(b, L, all, one, cells);
+    L = BLaunch{L_CELL}; L.arg = PH_TAU; L.name = "visc_tau";
+    add_phase(b, L, hasNu, one, tau_cells);
+    L = BLaunch{L_CELL}; L.arg = PH_VAPPLY; L.name = "visc_apply";
+    add_phase(b, L, hasNu, one, cells);
+    L = BLaunch{L_BC}; L.arg = 1; L.mode = 1; L.name = "bc_y9";
+    add_phase(b, L, hasY, one, bcy);
+    L = BLaunch{L_BC}; L.arg = 2; L.mode = 1; L.name = "bc_z9";
+    add_phase(b, L, hasZ, one, bcz);
+    L = BLaunch{L_TX}; L.name = "transport_x";
+    add_phase(b, L, all, chunk, [](const fargo_ctx *c) { return c->nyt * c->nzt; });
+    L = BLaunch{L_SWEEP}; L.arg = 1; L.name = "transport_y";
+    add_phase(b, L, hasY, nqk, sweep_blocks(1));
+    L = BLaunch{L_SWEEP}; L.arg = 2; L.name = "transport_z";
+    add_phase(b, L, hasZ, nqk, sweep_blocks(2));
+    L = BLaunch{L_ORB}; L.name = "orbital";
+    add_phase(b, L, [](const fargo_ctx *c) { return c->m.fargo && c->m.hasX; }, chunk,
+              [](const fargo_ctx *c) { return c->nrings_active; });
+    L = BLaunch{L_CELL}; L.arg = PH_NEWVEL; L.name = "newvel";
+    add_phase(b, L, all, one, cells);
+
+    // launch shapes of the ring and sweep groups
+    int rc;
+    for (BLaunch &x : b->seq) {
+        if (x.kind == L_TX || x.kind == L_ORB) {
+            int maxnx = 0;
+            size_t smem = 0;
+            for (int id : x.ids) {
+                maxnx = std::max(maxnx, b->mem[id]->nx);
+                smem = std::max(smem, b->mem[id]->tx_smem);
+            }
+            x.threads = ((maxnx + x.key - 1) / x.key + 31) / 32 * 32;
+            x.smem = smem;
+        } else if (x.kind == L_SWEEP) {
+            x.threads = TmaTile<T>::TW + 32;
+            x.smem = x.arg == 1 ? sweep_tma_smem<T, 1>(x.key) : sweep_tma_smem<T, 2>(x.key);
+        }
+        const size_t nb = (x.ids.size() + x.off.size()) * sizeof(int);
+        if ((rc = balloc(b, (void **)&x.d, nb))) return rc;
+        CK(cudaMemcpyAsync(x.d, x.ids.data(), x.ids.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(x.d + x.ids.size(), x.off.data(), x.off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           b->stream));
+    }
+    // ring kernels: one dynamic shared-memory limit per variant (the largest member)
+    size_t ring_smem[9] = {};
+    for (const BLaunch &x : b->seq)
+        if (x.kind == L_TX || x.kind == L_ORB) ring_smem[x.key] = std::max(ring_smem[x.key], x.smem);
+    if (ring_smem[1]) CK((ring_attrs<T, 1>(ring_smem[1])));
+    if (ring_smem[2]) CK((ring_attrs<T, 2>(ring_smem[2])));
+    if (ring_smem[3]) CK((ring_attrs<T, 3>(ring_smem[3])));
+    if (ring_smem[4]) CK((ring_attrs<T, 4>(ring_smem[4])));
+    if (ring_smem[8]) CK((ring_attrs<T, 8>(ring_smem[8])));
+    for (const BLaunch &x : b->seq)
+        if (x.kind == L_SWEEP) CK(x.arg == 1 ? (sweep_attrs<T, 1>(x.key)) : (sweep_attrs<T, 2>(x.key)));
+
+    if ((rc = balloc(b, &b->plans, sizeof(StepPlan<T>) * n))) return rc;
+    if ((rc = balloc(b, (void **)&b->mapsY, sizeof(SweepMaps) * n))) return rc;
+    if ((rc = balloc(b, (void **)&b->mapsZ, sizeof(SweepMaps) * n))) return rc;
+    if ((rc = balloc(b, (void **)&b->scs, sizeof(Scal *) * n))) return rc;
+    if ((rc = balloc(b, (void **)&b->status, sizeof(int) * 4))) return rc;
+    CK(cudaMemcpyAsync(b->plans, plans.data(), sizeof(StepPlan<T>) * n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->mapsY, my.data(), sizeof(SweepMaps) * n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->mapsZ, mz.data(), sizeof(SweepMaps) * n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->scs, scs.data(), sizeof(Scal *) * n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return FARGO_OK;
+}
+
+template <typename T>
+static void launch_ring(const BLaunch &x, const StepPlan<T> *P, cudaStream_t s)
+{
+    const Group g = x.dev();
+    const unsigned nb = (unsigned)x.blocks();
+    if (x.kind == L_TX) {
+        switch (x.key) {
+        case 1: kb_tx<T, 1><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 2: kb_tx<T, 2><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 3: kb_tx<T, 3><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 4: kb_tx<T, 4><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        default: kb_tx<T, 8><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        }
+    } else {
+        switch (x.key) {
+        case 1: kb_orb<T, 1><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 2: kb_orb<T, 2><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 3: kb_orb<T, 3><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 4: kb_orb<T, 4><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        default: kb_orb<T, 8><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        }
+    }
+}
+
+template <typename T, int AXIS>
+static void launch_bsweep(const BLaunch &x, const StepPlan<T> *P, const SweepMaps *maps, cudaStream_t s)
+{
+    const Group g = x.dev();
+    const unsigned nb = (unsigned)x.blocks();
+    switch (x.key) {
+    case 3: kb_sweep<T, AXIS, 3><<<nb, x.threads, x.smem, s>>>(P, maps, g); break;
+    case 4: kb_sweep<T, AXIS, 4><<<nb, x.threads, x.smem, s>>>(P, maps, g); break;
+    case 5: kb_sweep<T, AXIS, 5><<<nb, x.threads, x.smem, s>>>(P, maps, g); break;
+    case 6: kb_sweep<T, AXIS, 6><<<nb, x.threads, x.smem, s>>>(P, maps, g); break;
+    case 7: kb_sweep<T, AXIS, 7><<<nb, x.threads, x.smem, s>>>(P, maps, g); break;
+    default: kb_sweep<T, AXIS, 8><<<nb, x.threads, x.smem, s>>>(P, maps, g); break;
+    }
+}
+
+template <typename T>
+static int batch_enqueue(fargo_batch *b, cudaEvent_t *marks = nullptr)
+{
+    const StepPlan<T> *P = (const StepPlan<T> *)b->plans;
+    cudaStream_t s = b->stream;
+    int nl = 0;
+    for (const BLaunch &x : b->seq) {
+        const unsigned nb = (unsigned)x.blocks();
+        if (nb == 0) continue;
+        const Group g = x.dev();
+        switch (x.kind) {
+        case L_BC: kb_bc<T><<<nb, 256, 0, s>>>(P, g, x.arg, x.mode); break;
+        case L_SCREEN: kb_cfl_screen<T><<<nb, 256, 0, s>>>(P, g); break;
+        case L_EXACT: kb_cfl_exact<T><<<nb, 256, 0, s>>>(P, g); break;
+        case L_CELL:
+            switch (x.arg) {
+            case PH_SUB1: kb_cell<T, PH_SUB1><<<nb, 256, 0, s>>>(P, g); break;
+            case PH_AV: kb_cell<T, PH_AV><<<nb, 256, 0, s>>>(P, g); break;
+            case PH_TAU: kb_cell<T, PH_TAU><<<nb, 256, 0, s>>>(P, g); break;
+            case PH_VAPPLY: kb_cell<T, PH_VAPPLY><<<nb, 256, 0, s>>>(P, g); break;
+            default: kb_cell<T, PH_NEWVEL><<<nb, 256, 0, s>>>(P, g); break;
+            }
+            break;
+        case L_TX:
+        case L_ORB: launch_ring<T>(x, P, s); break;
+        case L_SWEEP:
+            if (x.arg == 1) launch_bsweep<T, 1>(x, P, b->mapsY, s);
+            else launch_bsweep<T, 2>(x, P, b->mapsZ, s);
+            break;
+        }
+        if (marks) cudaEventRecord(marks[nl + 1], s);
+        nl++;
+    }
+    CK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+static int benqueue(fargo_batch *b)
+{
+    return b->prec == FARGO_F64 ? batch_enqueue<double>(b) : batch_enqueue<float>(b);
+}
+
+static int batch_launch(fargo_batch *b)
+{
+    if (!b->use_graph) return benqueue(b);
+    if (!b->gexec) {
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = benqueue(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (rc) return rc;
+        if (e != cudaSuccess) return FARGO_ERR_CUDA;
+        b->graph = g;
+        CK(cudaGraphInstantiate(&b->gexec, g, 0));
+    }
+    CK(cudaGraphLaunch(b->gexec, b->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, int n, void *stream)
+{
+    if (!out || !members || n < 1) return FARGO_ERR_BADARG;
+    *out = nullptr;
+    const int prec = members[0] ? members[0]->prec : -1;
+    for (int i = 0; i < n; i++) {
+        if (!members[i] || members[i]->prec != prec) return FARGO_ERR_BADARG;
+        for (int k = 0; k < i; k++)
+            if (members[k] == members[i]) return FARGO_ERR_BADARG;
+    }
+    fargo_batch *b = new fargo_batch();
+    b->n = n;
+    b->prec = prec;
+    b->mem.assign(members, members + n);
+    int rc = FARGO_OK;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        b->stream = nullptr;
+        fargo_batch_destroy(b);
+        return FARGO_ERR_CUDA;
+    } else {
+        b->own_stream = true;
+    }
+    // the members' own streams may still hold work (uploads of their state)
+    for (int i = 0; i < n; i++)
+        if (cudaStreamSynchronize(members[i]->stream) != cudaSuccess) rc = FARGO_ERR_CUDA;
+    if (!rc && cudaMallocHost((void **)&b->hstatus, sizeof(int) * 4) != cudaSuccess) rc = FARGO_ERR_OOM;
+    if (!rc) rc = prec == FARGO_F64 ? batch_setup<double>(b) : batch_setup<float>(b);
+    if (rc) {
+        fargo_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return FARGO_OK;
+}
+
+extern "C" void fargo_batch_destroy(fargo_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->hstatus) cudaFreeHost(b->hstatus);
+    // a stream handed in by the caller stays theirs; the member contexts too
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+extern "C" int fargo_batch_step(fargo_batch *b)
+{
+    if (!b) return FARGO_ERR_BADARG;
+    int rc = batch_launch(b);
+    if (!rc) b->steps++;
+    return rc;
+}
+
+extern "C" int fargo_batch_status(fargo_batch *b, int *n_running, int *first_failed)
+{
+    if (!b) return FARGO_ERR_BADARG;
+    kb_status<<<1, 256, 0, b->stream>>>(b->scs, b->n, b->status);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(b->hstatus, b->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (n_running) *n_running = b->hstatus[0];
+    if (first_failed) *first_failed = b->hstatus[2] < b->n ? b->hstatus[2] : -1;
+    return err_code(b->hstatus[1]);
+}
+
+extern "C" int fargo_batch_run(fargo_batch *b, long long max_steps, int poll, long long *steps_done,
+                               int *n_running)
+{
+    if (!b || poll < 1 || max_steps < 0) return FARGO_ERR_BADARG;
+    long long launched = 0;
+    int run = 0, first = -1;
+    int rc = fargo_batch_status(b, &run, &first);
+    while (rc == FARGO_OK && run > 0 && launched < max_steps) {
+        const long long k = max_steps - launched < poll ? max_steps - launched : poll;
+        for (long long q = 0; q < k; q++) {
+            int r2 = fargo_batch_step(b);
+            if (r2) return r2;
+        }
+        launched += k;
+        rc = fargo_batch_status(b, &run, &first);
+    }
+    if (steps_done) *steps_done = launched;
+    if (n_running) *n_running = run;
+    return rc;
+}
+
+extern "C" int fargo_batch_use_graph(fargo_batch *b, int enable)
+{
+    if (!b) return FARGO_ERR_BADARG;
+    b->use_graph = enable != 0;
+    return FARGO_OK;
+}
+
+extern "C" int fargo_batch_launches_per_step(const fargo_batch *b)
+{
+    if (!b) return FARGO_ERR_BADARG;
+    int n = 0;
+    for (const BLaunch &x : b->seq) n += x.blocks() > 0;
+    return n;
+}
+
+extern "C" int fargo_batch_profile_step(fargo_batch *b, int max_kernels, float *ms, int *n_out, const char **names)
+{
+    if (!b || !ms || !n_out || max_kernels < 1) return FARGO_ERR_BADARG;
+    const int nseq = (int)b->seq.size();
+    std::vector<cudaEvent_t> ev(nseq + 1);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(ev[0], b->stream));
+    int rc = b->prec == FARGO_F64 ? batch_enqueue<double>(b, ev.data()) : batch_enqueue<float>(b, ev.data());
+    if (rc == FARGO_OK) {
+        CK(cudaStreamSynchronize(b->stream));
+        int n = 0;
+        for (const BLaunch &x : b->seq) {
+            if (x.blocks() == 0) continue;
+            if (n < max_kernels) {
+                CK(cudaEventElapsedTime(&ms[n], ev[n], ev[n + 1]));
+                if (names) names[n] = x.name;
+            }
+            n++;
+        }
+        *n_out = n < max_kernels ? n : max_kernels;
+        b->steps++;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}

@@ -48,9 +48,8 @@ __device__ __forceinline__ bool bc_skip(const Scal *sc, int mode)
 }
 
 template <typename T>
-__global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode)
+__device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid)
 {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long n = (long long)m.nx * (m.nzt + 1) * 2;
     if (tid >= n || bc_skip(sc, mode)) return;
     int i = (int)(tid % m.nx);
@@ -69,9 +68,8 @@ __global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode)
 }
 
 template <typename T>
-__global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode)
+__device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid)
 {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long n = (long long)m.nx * (m.nyt + 1) * 2;
     if (tid >= n || bc_skip(sc, mode)) return;
     int i = (int)(tid % m.nx);
@@ -87,6 +85,17 @@ __global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode)
         if (j >= jmax) continue;
         fill_line(fl[q], (long long)j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc);
     }
+}
+
+template <typename T>
+__global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode)
+{
+    bc_y_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <typename T>
+__global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode)
+{
+    bc_z_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -146,18 +155,19 @@ __device__ __forceinline__ bool cfl_skip(const Scal *sc)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f, double *v0, float *ringmax,
-                                                    double *part, Scal *sc, int nrings)
+__device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &f, double *v0,
+                                                float *ringmax, double *part, Scal *sc, int nrings, int bid,
+                                                int nblk)
 {
     __shared__ float s_red[8];
     __shared__ double s_w[8], s_m[8];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * 8 + warp;
+    const int r = bid * 8 + warp;
     const bool skip = cfl_skip(sc);
     // planet angle tables for this step (time t^n)
     if (m.has_planet) {
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.nx; i += gridDim.x * blockDim.x) {
+        for (int i = bid * blockDim.x + threadIdx.x; i < m.nx; i += nblk * blockDim.x) {
             const double dphi = (m.xmin + (i + 0.5) * m.dx) - m.om_rel * sc->t;
             const double sh = sin(0.5 * dphi);
             tb.ps[i] = (T)(sh * sh);
@@ -240,15 +250,15 @@ __global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f
     if (threadIdx.x == 0) {
         float b = s_red[0];
         for (int w = 1; w < 8; w++) b = fmaxf(b, s_red[w]);
-        part[blockIdx.x] = (double)b;
+        part[bid] = (double)b;
         __threadfence();
-        s_last = atomicAdd(&sc->counter, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(&sc->counter, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     double mx = 0.0, wsh = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
+    for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
     if (m.fargo && m.hasY && !skip) {
         const int ny = m.j1 - m.j0, nz = m.k1 - m.k0;
         const int npairs = (ny - 1) * nz;
@@ -279,13 +289,14 @@ __global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_cfl_exact(MeshD m, Tab<T> tb, Fld<T> f, const double *v0,
-                                                   const float *ringmax, double *part, Scal *sc, int nrings)
+__device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &f, const double *v0,
+                                               const float *ringmax, double *part, Scal *sc, int nrings, int bid,
+                                               int nblk)
 {
     __shared__ double s_red[8];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * 8 + warp;
+    const int r = bid * 8 + warp;
     const bool skip = cfl_skip(sc);
     const double M = sc->m32;
     const double thr = M < 1e-30 ? -1.0 : M * (1.0 - 1.0 / 4096.0);
@@ -338,15 +349,15 @@ __global__ void __launch_bounds__(256) k_cfl_exact(MeshD m, Tab<T> tb, Fld<T> f,
     if (threadIdx.x == 0) {
         double b = s_red[0];
         for (int w = 1; w < 8; w++) b = fmax(b, s_red[w]);
-        part[blockIdx.x] = b;
+        part[bid] = b;
         __threadfence();
-        s_last = atomicAdd(&sc->counter, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(&sc->counter, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     double mx = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
+    for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
     mx = warp_max(mx);
     if (lane == 0) s_red[warp] = mx;
     __syncthreads();
@@ -374,6 +385,19 @@ __global__ void __launch_bounds__(256) k_cfl_exact(MeshD m, Tab<T> tb, Fld<T> f,
         sc->dtf = (float)dt;
         sc->counter = 0u;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f, double *v0, float *ringmax,
+                                                    double *part, Scal *sc, int nrings)
+{
+    cfl_screen_body(m, tb, f, v0, ringmax, part, sc, nrings, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_cfl_exact(MeshD m, Tab<T> tb, Fld<T> f, const double *v0,
+                                                   const float *ringmax, double *part, Scal *sc, int nrings)
+{
+    cfl_exact_body(m, tb, f, v0, ringmax, part, sc, nrings, blockIdx.x, gridDim.x);
 }
 
 }  // namespace fk

@@ -16,11 +16,11 @@ struct CellIdx {
 
 // Per-cell kernels run on a 3D grid: x covers the azimuth, y the rows and z
 // the planes of the augmented mesh (extra face row / plane included).
-__device__ __forceinline__ bool decode(const MeshD &m, CellIdx &c)
+__device__ __forceinline__ bool decode(const MeshD &m, CellIdx &c, int bx, int by, int bz)
 {
-    c.i = blockIdx.x * blockDim.x + threadIdx.x;
-    c.j = blockIdx.y;
-    c.k = blockIdx.z;
+    c.i = bx * blockDim.x + threadIdx.x;
+    c.j = by;
+    c.k = bz;
     return c.i < m.nx;
 }
 
@@ -59,12 +59,13 @@ __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i,
 // four-face average of Eq. 12.  Jacobi: reads `in`, writes `out`.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+__device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
+                                              const Scal *sc, int bx, int by, int bz)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     CellIdx ci;
-    if (!decode(m, ci)) return;
+    if (!decode(m, ci, bx, by, bz)) return;
     const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
@@ -151,12 +152,13 @@ __device__ __forceinline__ T qvisc(T c2, T rho, T dv)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+__device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
+                                             const Scal *sc, int bx, int by, int bz)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     CellIdx ci;
-    if (!decode(m, ci)) return;
+    if (!decode(m, ci, bx, by, bz)) return;
     const T c2 = tb.cq2;
     const bool av = m.has_av != 0;
     const int i = ci.i, j = ci.j, k = ci.k;
@@ -510,13 +512,15 @@ struct TauArr {
 // the edge ones on the edges that interior and boundary faces need
 // (rows j0..j1, planes k0..k1).
 template <typename T>
-__global__ void __launch_bounds__(256) k_visc_tau(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> tau, const Scal *sc)
+__device__ __forceinline__ void visc_tau_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &tau,
+                                              const Scal *sc, int bx, int by, int bz)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.nx) return;
-    const int j = m.j0 + blockIdx.y, k = m.k0 + blockIdx.z;   // rows j0..j1, planes k0..k1
+    const int i = bx * blockDim.x + threadIdx.x;
+    // rows j0..j1 and planes k0..k1 (by, bz index the augmented mesh)
+    const int j = by, k = bz;
+    if (i >= m.nx || j < m.j0 || j > m.j1 || k < m.k0 || k > m.k1) return;
     const ViscCtx<T> V(m, tb, in);
     const long long c = IX(m, i, j, k);
     const bool jin = j < m.j1, kin = k < m.k1;
@@ -534,27 +538,38 @@ __global__ void __launch_bounds__(256) k_visc_tau(MeshD m, Tab<T> tb, Fld<T> in,
 
 // Pass 2: the velocity update of Eqs. 75-77 from the stored stresses.
 template <typename T>
-__global__ void __launch_bounds__(256) k_visc_apply(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, QSet<T> tau,
-                                                    const Scal *sc)
+__device__ __forceinline__ void visc_apply_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in,
+                                                const Fld<T> &out, const QSet<T> &tau, const Scal *sc, int bx,
+                                                int by, int bz)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     CellIdx ci;
-    if (!decode(m, ci)) return;
+    if (!decode(m, ci, bx, by, bz)) return;
     const TauArr<T> S{m, tau.q[0], tau.q[1], tau.q[2], tau.q[3], tau.q[4], tau.q[5]};
     visc_apply(m, tb, in, out, dt, ci.i, ci.j, ci.k, S);
 }
 
-// Single-pass variant: every thread recomputes the stresses it needs.
 template <typename T>
-__global__ void __launch_bounds__(256) k_visc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+__global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
-    const T dt = step_dt<T>(sc);
-    if (!(dt > T(0))) return;
-    CellIdx ci;
-    if (!decode(m, ci)) return;
-    const ViscCtx<T> V(m, tb, in);
-    visc_apply(m, tb, in, out, dt, ci.i, ci.j, ci.k, V);
+    substep1_body(m, tb, in, out, sc, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+{
+    artvisc_body(m, tb, in, out, sc, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_visc_tau(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> tau, const Scal *sc)
+{
+    visc_tau_body(m, tb, in, tau, sc, blockIdx.x, m.j0 + blockIdx.y, m.k0 + blockIdx.z);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_visc_apply(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, QSet<T> tau,
+                                                    const Scal *sc)
+{
+    visc_apply_body(m, tb, in, out, tau, sc, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace fk

@@ -108,8 +108,8 @@ __device__ __forceinline__ bool stage_rows(T *dst, int rowlen, const T *const *s
 // velocity is delta v = v_x - v0 (v0 = 0 for STANDARD transport).  Ghost
 // rings only get their momenta written (the Y/Z sweeps read them).
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
-                                                     Scal *sc)
+__device__ __forceinline__ void transport_x_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in,
+                                                 const QSet<T> &out, const double *v0, Scal *sc, int ring)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -118,7 +118,6 @@ __global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     const int nx = m.nx, nq = out.nq, pitch = (int)m.sj;
-    const int ring = blockIdx.x;
     const int j = ring % m.nyt, k = ring / m.nyt;
     const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
     const long long base = IX(m, 0, j, k);
@@ -231,7 +230,8 @@ __global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<
 //        transport, in the same pass.
 // N and xi are FP64 (round-to-nearest intrinsics), once per CTA.
 template <typename T, int C>
-__global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, Scal *sc)
+__device__ __forceinline__ void orbital_body(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0,
+                                             Scal *sc, int r)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -241,7 +241,6 @@ __global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs,
     const T dtT = step_dt<T>(sc);
     if (!(dtT > T(0))) return;
     const int nx = m.nx, nq = qs.nq, pitch = (int)m.sj;
-    const int r = blockIdx.x;
     const int ny = m.j1 - m.j0;
     const int j = m.j0 + r % ny, k = m.k0 + r / ny;
     const int ring = k * m.nyt + j;
@@ -326,6 +325,18 @@ __global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs,
 }
 
 template <typename T, int C>
+__global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
+                                                     Scal *sc)
+{
+    transport_x_body<T, C>(m, tb, in, out, v0, sc, blockIdx.x);
+}
+template <typename T, int C>
+__global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, Scal *sc)
+{
+    orbital_body<T, C>(m, tb, qs, v0, sc, blockIdx.x);
+}
+
+template <typename T, int C>
 static void launch_tx_c(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
                         Scal *sc, size_t smem, cudaStream_t s)
 {
@@ -376,27 +387,21 @@ static void launch_orb(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, cons
 }
 
 // ---------------------------------------------------------------------------
-// Y and Z sweeps (Eqs. 1D-advection-Y/Z) as marching pencils.  A thread owns
-// one column (fixed azimuth and transverse index) over a segment of the
-// sweep axis and walks it with a register window: at cell p it holds the
-// ratios Q/rho of rows p..p+2, the van Leer slope of cell p and the flux
-// through face p (lower); it computes the slope of cell p+1, the interface
-// values and fluxes through face p+1 (upper), updates cell p and slides the
-// window.  Each face flux and slope is computed once; consistent transport
-// (ratio to density times the mass flux), all fluxes from the pre-sweep
-// values.
-// ---------------------------------------------------------------------------
-// The Y and Z sweeps with TMA staging.  A CTA owns a tile of TW consecutive
-// azimuths (one 512-byte row segment per quantity) of one transverse index
-// and a segment of the sweep axis.  A producer thread streams the rows of
-// the segment and its 2+2 halo rows, every quantity plus the face velocity,
-// into an S-stage ring of shared memory with 3D tensor-map loads completed
-// on an mbarrier; the TW consumer threads (one column each) march the
-// segment exactly like the register version above, reading each row from
-// shared memory and releasing its stage through a second mbarrier.  Rows
-// outside the active range come from `maps.qg` (the ghost source).
-// Every wait is bounded: on timeout the CTA records kErrTimeout and returns
-// after its copies in flight have landed.
+// Y and Z sweeps (Eqs. 1D-advection-Y/Z) with TMA staging.  A CTA owns a tile
+// of TW consecutive azimuths (one 512-byte row segment per quantity) of one
+// transverse index and a segment of the sweep axis.  A producer thread
+// streams the rows of the segment and its 2+2 halo rows, every quantity plus
+// the face velocity, into an S-stage ring of shared memory with 3D
+// tensor-map loads completed on an mbarrier.  The TW consumer threads own one
+// column each and march it with a register window: at cell p a thread holds
+// the ratios Q/rho of rows p..p+2, the van Leer slope of cell p and the flux
+// through its lower face; it forms the slope of cell p+1 and the flux through
+// the upper face, updates cell p, slides the window and releases the row's
+// stage through a second mbarrier.  Each face flux and slope is computed
+// once; consistent transport (ratio to density times the mass flux), all
+// fluxes from the pre-sweep values.  Rows outside the active range come from
+// `maps.qg` (the ghost source).  Every wait is bounded: on timeout the CTA
+// records kErrTimeout and returns after its copies in flight have landed.
 // ---------------------------------------------------------------------------
 struct SweepMaps {
     CUtensorMap qin[8];
@@ -411,9 +416,8 @@ struct TmaTile {
 };
 
 template <typename T, int AXIS, int NQ>
-__global__ void __launch_bounds__(TmaTile<T>::TW + 32) k_sweep_tma(MeshD m, Tab<T> tb,
-                                                                    const __grid_constant__ SweepMaps maps,
-                                                                    QSet<T> out, Scal *sc, int seglen)
+__device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, const SweepMaps &maps,
+                                           const QSet<T> &out, Scal *sc, int seglen, int bid)
 {
     constexpr int TW = TmaTile<T>::TW, S = TmaTile<T>::S, NW = TW / 32;
     constexpr int ROW = (NQ + 1) * TW;                // values per stage
@@ -425,8 +429,8 @@ __global__ void __launch_bounds__(TmaTile<T>::TW + 32) k_sweep_tma(MeshD m, Tab<
     const int p0 = AXIS == 1 ? m.j0 : m.k0, pN = AXIS == 1 ? m.j1 : m.k1;
     const int n2 = AXIS == 1 ? m.k1 - m.k0 : m.j1 - m.j0;
     const int ntx = (m.nx + TW - 1) / TW;
-    const int bx = blockIdx.x % ntx;
-    const int rest = blockIdx.x / ntx;
+    const int bx = bid % ntx;
+    const int rest = bid / ntx;
     const int c2 = (AXIS == 1 ? m.k0 : m.j0) + rest % n2;
     const int seg = rest / n2;
     const int ps = p0 + seg * seglen, pe = min(ps + seglen, pN);
@@ -562,6 +566,17 @@ __global__ void __launch_bounds__(TmaTile<T>::TW + 32) k_sweep_tma(MeshD m, Tab<
     }
 }
 
+template <typename T, int AXIS, int NQ>
+__global__ void __launch_bounds__(TmaTile<T>::TW + 32) k_sweep_tma(MeshD m, Tab<T> tb,
+                                                                    const __grid_constant__ SweepMaps maps,
+                                                                    QSet<T> out, Scal *sc, int seglen)
+{
+    sweep_body<T, AXIS, NQ>(m, tb, maps, out, sc, seglen, blockIdx.x);
+}
+
+// Segment length of a sweep over np active rows.
+static inline int sweep_seglen(int np) { return np > 96 ? 64 : np; }
+
 template <typename T, int AXIS>
 static size_t sweep_tma_smem(int nq)
 {
@@ -575,7 +590,7 @@ static void launch_sweep_tma(const MeshD &m, const Tab<T> &tb, const SweepMaps &
     constexpr int TW = TmaTile<T>::TW;
     const int np = AXIS == 1 ? m.j1 - m.j0 : m.k1 - m.k0;
     const int n2 = AXIS == 1 ? m.k1 - m.k0 : m.j1 - m.j0;
-    const int seglen = np > 96 ? 64 : np;
+    const int seglen = sweep_seglen(np);
     const int nseg = (np + seglen - 1) / seglen;
     const int ntx = (m.nx + TW - 1) / TW;
     const unsigned g = (unsigned)ntx * n2 * nseg;
@@ -630,13 +645,13 @@ __device__ __forceinline__ T *qsel(const QSet<T> &s, int n)
 // advances the device time.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin, Fld<T> vsrc, Fld<T> state,
-                                                Scal *sc, int copy_scalars)
+__device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, const QSet<T> &fin, const Fld<T> &vsrc,
+                                            const Fld<T> &state, Scal *sc, int copy_scalars, int bx, int by, int bz)
 {
     const T dtT = step_dt<T>(sc);
     if (!(dtT > T(0))) return;
     CellIdx ci;
-    if (!decode(m, ci)) return;
+    if (!decode(m, ci, bx, by, bz)) return;
     const int i = ci.i, j = ci.j, k = ci.k;
     if (i == 0 && j == 0 && k == 0) {
         sc->t = sc->t + sc->dt;
@@ -680,6 +695,13 @@ __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin,
         }
         state.vz[c] = v;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin, Fld<T> vsrc, Fld<T> state,
+                                                Scal *sc, int copy_scalars)
+{
+    newvel_body(m, tb, fin, vsrc, state, sc, copy_scalars, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
