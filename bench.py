@@ -1,22 +1,32 @@
 """Benchmark of the B300 FARGO3D hydro step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                    [--workload disk3d|disk2d] [--no-cpu-baseline] [--no-e2e]
+                    [--workload batch256|disk3d|disk2d|disk3d-small|batch-small]
+                    [--no-cpu-baseline] [--no-e2e] [--no-fp64] [--no-single]
 
-Default workload: the 3D spherical adiabatic planet disk, 1536 x 512 x 96
-active cells, FP32 fields with FP64 islands (Courant step, v0, shift, planet
-offset, sums).  A step is one full update of every active cell (flow chart
-cells 2-12); the metric is cell-updates per second.  The state (about 2.6 GB
-of fields plus 5 GB of scratch) is far larger than the 126 MB L2, so no L2
-flush is needed between steps.  A secondary measurement runs the 2D
-cylindrical planet disk (256 x 768) in FP64, flushing L2 before every timed
-step (its 30 MB state would otherwise stay L2-resident).
+Default workload (batch256): the batched parameter sweep of 256 independent
+2D cylindrical isothermal planet disks, Nr ~ U{128..512}, Nphi = 3 Nr,
+q log-uniform [1e-5, 1e-3], h U[0.03, 0.07], nu log-uniform [1e-6, 1e-5]
+(seed 1602), about 88 M active cells in total, FP32 fields with FP64 islands
+(Courant step, v0, shift, planet offset), advanced by the batched engine:
+one launch per phase over every disk, each disk with its own Courant step,
+the step captured as a CUDA graph.  A step is one full update of every
+active cell of every disk (flow chart cells 2-12); the metric is
+cell-updates per second.  The sweep's run length (500 orbits, ~1e5 steps
+per disk) only multiplies the step count: the cost of a step does not depend
+on the state, so the bench times K steps from the initial state.  The state
+(about 16 GB) is far larger than the 126 MB L2; no flush is needed.
+
+Reported beside it: the same metric for the plain FP64 single-instance
+step (the 768 x 256 disk, L2 flushed before every timed step) and their
+ratio, and the single-instance FP32 step of the 3D spherical adiabatic
+planet disk (1536 x 512 x 96) with its own roofline.
 
 Multi-GPU: the hot path does not shard; with N > 1 ranks (torchrun) every
 rank advances its own replica and `value` is the total over ranks.
 
---impl reference times the plain FP64 CPU oracle on a bounded slab of the same
-workload on the host cores (rank 0 only).
+--impl reference times the plain FP64 CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
 """
 import argparse
 import hashlib
@@ -144,6 +154,9 @@ def dist_env():
     return ws, rank, local
 
 
+BATCH_WORKLOADS = {"batch256": 256, "batch-small": 16}
+
+
 def make_workload(name):
     if name == "disk3d":
         w = W.disk3d()
@@ -158,28 +171,86 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-def cpu_baseline(wname, budget_s=20.0):
-    """The plain FP64 oracle on a bounded slab of the workload, host cores."""
+def batch_label(n):
+    return f"batch{n}-disk2d-cyl-isothermal-planet-Nr128..512-Nphi3Nr-seed1602"
+
+
+def batch_params(wname):
+    """Parameters of the sweep (batch-small: the first 16 draws at a quarter
+    of the radial resolution, a profiling case still far above L2)."""
+    n = BATCH_WORKLOADS[wname]
+    ps = W.batch_params(n=n, seed=1602)
+    if wname == "batch-small":
+        ps = [dict(p, ny=max(32, p["ny"] // 4), nx=3 * max(32, p["ny"] // 4)) for p in ps]
+    return ps
+
+
+def make_batch(fb, ps, stream):
+    """One FP32 context per disk (state uploaded, host copy dropped), then
+    the batch over all of them."""
+    mem, cells = [], 0
+    for p in ps:
+        w = W.batch_instance(p)
+        c = fb.Fargo(w, fb.F32)
+        c.set_state(w.state)
+        c.set_time(0.0, 1e30)
+        w.state = None
+        cells += w.cells
+        mem.append(c)
+    return mem, fb.FargoBatch(mem, stream=stream), cells
+
+
+def oracle_steps(make, budget_s, max_steps=50):
+    """Step oracle instances from make() (at most max_steps steps each)
+    until budget_s seconds of stepping have passed; instance set-up is not
+    timed.  Returns (cell-updates, seconds, steps, instances)."""
     import oracle
-    if wname == "disk3d":
-        w = W.disk3d(slab=(200, 24, 36, 24))
-        sample = "oracle on a 1536x24x24 slab of the 1536x512x96 disk (rows 200-223, planes 36-59), frozen ghosts"
-    else:
-        w = W.disk2d()
-        sample = "oracle on the full 768x256 disk"
-    o = oracle.Oracle(w)
-    st = w.copy().state
-    t = 0.0
+    cells = 0
     n = 0
-    t0 = time.perf_counter()
+    k = 0
+    el = 0.0
     while True:
-        t += o.step(st, t, w.t_end)
-        n += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or n >= 50:
-            break
-    return {"value": w.cells * n / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample}; {n} steps in {el:.1f} s"}
+        w = make(k)
+        k += 1
+        o = oracle.Oracle(w)
+        st = w.copy().state
+        t = 0.0
+        for _ in range(max_steps):
+            t0 = time.perf_counter()
+            t += o.step(st, t, w.t_end)
+            el += time.perf_counter() - t0
+            cells += w.cells
+            n += 1
+            if el > budget_s:
+                return cells, el, n, k
+
+
+def cpu_sample(wname):
+    """(instance maker, description) of the bounded oracle sample of a workload."""
+    if wname in BATCH_WORKLOADS:
+        ps = batch_params(wname)
+        return (lambda k: W.batch_instance(ps[k % len(ps)]),
+                "oracle stepping disks of the sweep in order (member 0 first), full meshes")
+    if wname in ("disk3d", "disk3d-small"):
+        return (lambda k: W.disk3d(slab=(200, 24, 36, 24)),
+                "oracle on a 1536x24x24 slab of the 1536x512x96 disk (rows 200-223, planes 36-59), frozen ghosts")
+    return (lambda k: W.disk2d(), "oracle on the full 768x256 disk")
+
+
+def cpu_baseline(wname, budget_s=20.0):
+    """The plain FP64 oracle on a bounded sample of the workload, host cores."""
+    make, sample = cpu_sample(wname)
+    cells, el, n, k = oracle_steps(make, budget_s)
+    return {"value": cells / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample}; {n} steps of {k} instance(s) in {el:.1f} s"}
+
+
+def workload_label(wname):
+    if wname in BATCH_WORKLOADS:
+        return batch_label(BATCH_WORKLOADS[wname])
+    return {"disk3d": "disk3d-sph-adiabatic-planet-1536x512x96",
+            "disk3d-small": "disk3d-sph-adiabatic-planet-1536x128x48"}.get(
+        wname, "disk2d-cyl-isothermal-planet-768x256")
 
 
 def run_reference(args):
@@ -187,39 +258,21 @@ def run_reference(args):
     if rank != 0:
         return
     wname = args.workload
-    _, label, _ = make_workload_meta(wname)
-    import oracle
-    if wname == "disk3d":
-        w = W.disk3d(slab=(200, 24, 36, 24))
-        sample = "1536x24x24 slab of the 1536x512x96 disk per step"
-    else:
-        w = W.disk2d()
-        sample = "full 768x256 disk per step"
-    o = oracle.Oracle(w)
-    st = w.copy().state
-    t = 0.0
-    for _ in range(args.warmup):
-        t += o.step(st, t, w.t_end)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        t += o.step(st, t, w.t_end)
-    el = time.perf_counter() - t0
-    val = w.cells * args.steps / el
+    make, sample = cpu_sample(wname)
+    # each step: about one second of oracle work on the sample
+    oracle_steps(make, 0.5 * args.warmup, max_steps=args.warmup)
+    cells, el, n, k = oracle_steps(make, 1.0 * args.steps)
+    val = cells / el
     line = {"metric": "cell-updates/s", "value": val, "unit": "cell-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": label, "sample": sample},
+            "config": {"workload": workload_label(wname), "sample": sample,
+                       "step": "about 1 s of oracle work on the sample per step"},
             "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": f"{sample}; {n} oracle steps of {k} instance(s) in {el:.1f} s"},
             "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def make_workload_meta(wname):
-    if wname == "disk3d":
-        return None, "disk3d-sph-adiabatic-planet-1536x512x96", True
-    return None, "disk2d-cyl-isothermal-planet-768x256", False
 
 
 def fp64_plain_disk2d(torch, fb, steps=50, warmup=5):
@@ -252,16 +305,177 @@ def fp64_plain_disk2d(torch, fb, steps=50, warmup=5):
             "l2": "flushed (512 MB write) before every timed step", "err": err}
 
 
+def roofline_of(per, cells, table, esz, traffic_tab=None):
+    """Roofline of the dominant kernel from per-launch device times (ms)."""
+    hbm, peak_kind = peaks()
+    avg = {k: sum(v) / len(v) for k, v in per.items()}
+    top = max(avg, key=avg.get)
+    alg_bytes = table.get(top, 0) * esz * cells
+    achieved = alg_bytes / (avg[top] * 1e-3) / 1e9
+    tot = sum(avg.values())
+    share = {k: round(v / tot, 4) for k, v in sorted(avg.items(), key=lambda x: -x[1])}
+    per_kernel = {k: {"ms": round(v, 4), "alg_GBps": round(table.get(k, 0) * esz * cells / (v * 1e-3) / 1e9, 1)}
+                  for k, v in sorted(avg.items(), key=lambda x: -x[1]) if k in table}
+    traffic = None
+    if traffic_tab is not None and top in traffic_tab:
+        traffic = int(traffic_tab[top] * cells)
+    step_alg = sum(table.get(k, 0) for k in avg) * esz * cells
+    return {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(avg[top], 4), "traffic": traffic,
+            "step_alg_GBps": round(step_alg / (tot * 1e-3) / 1e9, 1),
+            "step_frac": round(step_alg / (tot * 1e-3) / 1e9 / hbm, 4),
+            "kernel_share": share, "per_kernel": per_kernel}
+
+
+def timed_steps(torch, stream, step, n, dev, barrier):
+    """Device time per step (ms) of n steps on `stream` with CUDA events,
+    clocks sampled during the region."""
+    clk = Clocks(dev)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / n, clk.stop()
+
+
+def bench_single(args, torch, fb, wname, dev, barrier, e2e_on=True, steps=None):
+    steps = steps or args.steps
+    w, label, fp32 = make_workload(wname)
+    prec = fb.F32 if fp32 else fb.F64
+    esz = 4 if fp32 else 8
+    stream = torch.cuda.Stream()
+    c = fb.Fargo(w, prec, stream=stream.cuda_stream)
+    c.set_state(w.state)
+    c.set_time(0.0, 1e30)
+    nl = c.launches_per_step()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            c.step(want_dt=False)
+        torch.cuda.synchronize()
+        ms, clocks = timed_steps(torch, stream, lambda: c.step(want_dt=False), steps, dev, barrier)
+        per = {}
+        for _ in range(steps):
+            for name, t in c.profile_step():
+                per.setdefault(name, []).append(t)
+    _, _, nsteps, err = c.scalars()
+    if err:
+        raise SystemExit(f"device error {err} during the benchmark")
+    table = ALG_FIELDS_3D if (w.nz > 1 and not w.iso) else ALG_FIELDS_2D_ISO
+    traffic_tab = (TRAFFIC_PER_CELL_3D if (fp32 and w.nz > 1 and not w.iso
+                                           and kernel_source_hash() == KERNEL_SRC_HASH) else None)
+    roof = roofline_of(per, w.cells, table, esz, traffic_tab)
+    e2e = None
+    if e2e_on:
+        names = ["rho", "e", "vx", "vy", "vz"] if not w.iso else ["rho", "vx", "vy", "vz"]
+        if w.nz == 1:
+            names = [n for n in names if n != "vz"]
+        hdt = torch.float32 if fp32 else torch.float64
+        host = {n: torch.empty(w.shape, dtype=hdt, pin_memory=True) for n in names}
+        for n in names:
+            host[n].numpy()[...] = w.state[n]
+        bytes_io = sum(h.numel() * h.element_size() for h in host.values())
+        ksteps = max(3, min(steps, 10))
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(ksteps):
+                for n in names:
+                    c.set_field(n, host[n].numpy())
+                c.step(want_dt=False)
+                for n in names:
+                    c.get_field(n, out=host[n].numpy())
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            barrier()
+        e2e = {"value": w.cells * ksteps / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": ksteps,
+               "note": "every step uploads the full state from pinned host memory and reads it back"}
+    c.close()
+    return {"workload": label, "cells": w.cells, "fp32": fp32, "ms": ms, "clocks": clocks, "roofline": roof,
+            "e2e": e2e, "launches": nl, "steps_advanced": int(nsteps),
+            "state_gb": w.cells * 21 * esz / 1e9}
+
+
+def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
+    ps = batch_params(wname)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    mem, b, cells = make_batch(fb, ps, stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    nl = b.launches_per_step()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            b.step(sync=False)
+        b.status()
+        ms, clocks = timed_steps(torch, stream, lambda: b.step(sync=False), args.steps, dev, barrier)
+        per = {}
+        for _ in range(args.steps):
+            for name, t in b.profile_step():
+                per.setdefault(name, []).append(t)
+    running, _ = b.status()
+    nsteps = [m.scalars()[2] for m in mem]
+    roof = roofline_of(per, cells, ALG_FIELDS_2D_ISO, 4)
+    e2e = None
+    if e2e_on:
+        # public API end to end: every step uploads each disk's active state
+        # (rho, v_x, v_y) from pinned host memory and reads it back
+        names = ["rho", "vx", "vy"]
+        host = []
+        for m in mem:
+            host.append({n: torch.empty(m.active_shape, dtype=torch.float32, pin_memory=True) for n in names})
+            for n in names:
+                m.get_field(n, region=fb.ACTIVE, out=host[-1][n].numpy())
+        bytes_io = sum(h.numel() * h.element_size() for d in host for h in d.values())
+        ksteps = max(3, min(args.steps, 6))
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            barrier()
+            t1 = time.perf_counter()
+            for _ in range(ksteps):
+                for m, d in zip(mem, host):
+                    for n in names:
+                        m.set_field(n, d[n].numpy(), region=fb.ACTIVE)
+                b.step(sync=True)
+                for m, d in zip(mem, host):
+                    for n in names:
+                        m.get_field(n, region=fb.ACTIVE, out=d[n].numpy())
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t1
+            barrier()
+        e2e = {"value": cells * ksteps / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": ksteps,
+               "note": "every step uploads every disk's active rho, v_x, v_y from pinned host memory "
+                       "through fargo_set_field and reads them back through fargo_get_field"}
+    b.close()
+    for m in mem:
+        m.close()
+    return {"workload": batch_label(len(ps)), "cells": cells, "members": len(ps), "ms": ms, "clocks": clocks,
+            "roofline": roof, "e2e": e2e, "launches": nl, "setup_s": round(setup_s, 1),
+            "steps_advanced_min": int(min(nsteps)), "running": running,
+            "state_gb": cells * 2 * 22 * 4 / 1e9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="disk3d", choices=["disk3d", "disk2d", "disk3d-small"])
+    ap.add_argument("--workload", default="batch256",
+                    choices=["batch256", "batch-small", "disk3d", "disk2d", "disk3d-small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-single", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -285,127 +499,69 @@ def main():
         if ws > 1:
             torch.distributed.barrier()
 
-    w, label, fp32 = make_workload(args.workload)
-    prec = fb.F32 if fp32 else fb.F64
-    stream = torch.cuda.Stream()
-    c = fb.Fargo(w, prec, stream=stream.cuda_stream)
-    c.set_state(w.state)
-    c.set_time(0.0, 1e30)
-    nl = c.launches_per_step()
-    esz = 4 if fp32 else 8
+    def max_over_ranks(x):
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        if ws > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
 
-    # ---- warm-up, then the timed region (CUDA graph replays on `stream`)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            c.step(want_dt=False)
-        torch.cuda.synchronize()
-        clk = Clocks(dev)
-        clk.start()
-        barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            c.step(want_dt=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms = e0.elapsed_time(e1) / args.steps
-        clocks = clk.stop()
-        # ---- per-kernel device time over the same number of steps (live roofline)
-        per = {}
-        for _ in range(args.steps):
-            for name, t in c.profile_step():
-                per.setdefault(name, []).append(t)
-    t_dev, dt_last, nsteps, err = c.scalars()
-    if err:
-        raise SystemExit(f"device error {err} during the benchmark")
+    batched = args.workload in BATCH_WORKLOADS
+    if batched:
+        r = bench_batch(args, torch, fb, args.workload, dev, barrier, e2e_on=not args.no_e2e)
+    else:
+        r = bench_single(args, torch, fb, args.workload, dev, barrier, e2e_on=not args.no_e2e)
+    ms_max = max_over_ranks(r["ms"])
+    value = r["cells"] * ws / (ms_max * 1e-3)
+    if r["e2e"] is not None:
+        # whole-job end-to-end rate: the slowest rank's rate times the ranks
+        r["e2e"]["value"] = ws / max_over_ranks(1.0 / r["e2e"]["value"])
 
-    ms_t = torch.tensor([ms], device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = w.cells * ws / (ms_max * 1e-3)
-
-    # roofline of the dominant kernel
-    hbm, peak_kind = peaks()
-    avg = {k: sum(v) / len(v) for k, v in per.items()}
-    top = max(avg, key=avg.get)
-    table = ALG_FIELDS_3D if (w.nz > 1 and not w.iso) else ALG_FIELDS_2D_ISO
-    alg_bytes = table.get(top, 0) * esz * w.cells
-    achieved = alg_bytes / (avg[top] * 1e-3) / 1e9
-    share = {k: round(v / sum(avg.values()), 4) for k, v in sorted(avg.items(), key=lambda x: -x[1])}
-    per_kernel = {k: {"ms": round(v, 4), "alg_GBps": round(table.get(k, 0) * esz * w.cells / (v * 1e-3) / 1e9, 1)}
-                  for k, v in sorted(avg.items(), key=lambda x: -x[1]) if k in table}
-    traffic = None
-    if (fp32 and w.nz > 1 and not w.iso and top in TRAFFIC_PER_CELL_3D
-            and kernel_source_hash() == KERNEL_SRC_HASH):
-        traffic = int(TRAFFIC_PER_CELL_3D[top] * w.cells)
-    roofline = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "peak_kind": f"{peak_kind} copy bandwidth",
-                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(avg[top], 4), "traffic": traffic,
-                "kernel_share": share, "per_kernel": per_kernel}
-
-    # ---- end to end through the C ABI with pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        names = ["rho", "e", "vx", "vy", "vz"] if not w.iso else ["rho", "vx", "vy", "vz"]
-        if w.nz == 1:
-            names = [n for n in names if n != "vz"]
-        hdt = torch.float32 if fp32 else torch.float64
-        host = {n: torch.empty(w.shape, dtype=hdt, pin_memory=True) for n in names}
-        for n in names:
-            host[n].numpy()[...] = w.state[n]
-        bytes_io = sum(h.numel() * h.element_size() for h in host.values())
-        ksteps = max(3, min(args.steps, 10))
-        with torch.cuda.stream(stream):
-            torch.cuda.synchronize()
-            barrier()
-            t0 = time.perf_counter()
-            for _ in range(ksteps):
-                for n in names:
-                    c.set_field(n, host[n].numpy())
-                c.step(want_dt=False)
-                for n in names:
-                    c.get_field(n, out=host[n].numpy())
-            torch.cuda.synchronize()
-            el = time.perf_counter() - t0
-            barrier()
-        e2e = {"value": w.cells * ws * ksteps / el, "unit": "cell-updates/s",
-               "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": ksteps,
-               "note": "every step uploads the full state from pinned host memory and reads it back"}
-    c.close()
-    del c
+    single = None
+    if rank == 0 and batched and not args.no_single:
+        s = bench_single(args, torch, fb, "disk3d", dev, lambda: None, e2e_on=False, steps=min(args.steps, 20))
+        single = {"workload": s["workload"], "dtype": "f32", "value": s["cells"] / (s["ms"] * 1e-3),
+                  "unit": "cell-updates/s", "ms_per_step": s["ms"],
+                  "roofline": {k: s["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac",
+                                                             "step_alg_GBps", "step_frac", "traffic")},
+                  "per_kernel": s["roofline"]["per_kernel"], "clocks": s["clocks"]}
 
     fp64 = None
-    if rank == 0 and not args.no_fp64 and args.workload == "disk3d":
-        with torch.cuda.device(dev):
-            fp64 = fp64_plain_disk2d(torch, fb)
+    if rank == 0 and not args.no_fp64 and args.workload in ("disk3d",) + tuple(BATCH_WORKLOADS):
+        fp64 = fp64_plain_disk2d(torch, fb)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload != "disk3d-small":
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload not in ("disk3d-small", "batch-small"):
         cpu = cpu_baseline(args.workload)
 
     if rank == 0:
+        cfg = {"workload": r["workload"], "cells": r["cells"],
+               "precision": "FP32 fields, FP64 dt/v0/shift/planet offset" if (batched or r["fp32"]) else "FP64",
+               "parallelism": "replicas" if ws > 1 else "single GPU",
+               "l2": "inputs larger than L2 (state %.1f GB)" % r["state_gb"], "graph": True}
+        if batched:
+            cfg.update({"members": r["members"], "engine": "batched, one launch per phase over all members, "
+                                                            "per-member Courant step",
+                        "steps_advanced_min": r["steps_advanced_min"], "setup_s": r["setup_s"],
+                        "run_length": "500 orbits per disk in the sweep; the bench times per-step throughput"})
+        else:
+            cfg["steps_advanced"] = r["steps_advanced"]
         line = {
             "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
-            "config": {"workload": label, "cells": w.cells, "steps_advanced": int(nsteps),
-                       "precision": "FP32 fields, FP64 dt/v0/shift/planet offset/sums" if fp32 else "FP64",
-                       "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (state %.1f GB)" % (w.cells * 21 * esz / 1e9),
-                       "graph": True},
-            "roofline": roofline,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if (batched or r["fp32"]) else "f64",
+            "data": "synthetic", "config": cfg,
+            "roofline": r["roofline"],
             "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": nl * args.steps,
-            "clocks": clocks,
+            "e2e": r["e2e"],
+            "gpu_launches": r["launches"] * args.steps,
+            "clocks": r["clocks"],
         }
         if fp64 is not None:
             line["fp64_plain"] = fp64
-            line["fp32_vs_fp64_plain"] = value / fp64["value"]
+            key = "fp32_batched_vs_fp64_plain" if batched else "fp32_vs_fp64_plain"
+            line[key] = value / ws / fp64["value"]
+        if single is not None:
+            line["single_instance_fp32"] = single
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -169,6 +169,9 @@ static inline dim3 cell_grid(const MeshD &m, int ny, int nz)
     const dim3 b = cell_block(m);
     return dim3((m.nx + b.x - 1) / b.x, ny, nz);
 }
+// every row (extra face row included) and the planes of cell_planes()
+static inline dim3 cell_grid_all(const MeshD &m) { return cell_grid(m, m.nyt + 1, cell_planes(m)); }
+static inline dim3 tau_grid(const MeshD &m) { return cell_grid(m, tau_rows(m), tau_planes(m)); }
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 

@@ -338,7 +338,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         }                                                           \
         nl++;                                                       \
     } while (0)
-    const dim3 cb = cell_block(m), cg = cell_grid(m, m.nyt + 1, m.nzt + 1);
+    const dim3 cb = cell_block(m), cg = cell_grid_all(m);
     // cell 2
     if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_y"); }
     if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_z"); }
@@ -352,7 +352,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     k_artvisc<T><<<cg, cb, 0, s>>>(m, P.tb, P.VB, P.A, P.sc); MARK("artvisc");
     if (m.has_nu) {
         // stresses once into the scratch momenta of set B (unused until the transport step)
-        k_visc_tau<T><<<cell_grid(m, m.j1 - m.j0 + 1, m.k1 - m.k0 + 1), cb, 0, s>>>(m, P.tb, P.A, P.tau, P.sc); MARK("visc_tau");
+        k_visc_tau<T><<<tau_grid(m), cb, 0, s>>>(m, P.tb, P.A, P.tau, P.sc); MARK("visc_tau");
         k_visc_apply<T><<<cg, cb, 0, s>>>(m, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
     }
     // cell 9
@@ -837,7 +837,9 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     }
     CK(cudaMemcpyAsync(c->sc, &sh, sizeof(Scal), cudaMemcpyHostToDevice, s));
     auto copyv = [&](T *const *dst, T *const *src) -> int {
-        for (int q = 0; q < 3; q++) CK(cudaMemcpyAsync(dst[q], src[q], nbytes, cudaMemcpyDeviceToDevice, s));
+        // v_z only exists with a Z direction
+        for (int q = 0; q < (m.hasZ ? 3 : 2); q++)
+            CK(cudaMemcpyAsync(dst[q], src[q], nbytes, cudaMemcpyDeviceToDevice, s));
         return FARGO_OK;
     };
     T *va[3] = {A.vx, A.vy, A.vz};
@@ -856,20 +858,20 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         // the screening launch fills the per-step planet angle tables
         k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
                                                       c->nrings_active);
-        k_substep1<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, c->sc);
+        k_substep1<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, A, VB, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
     case 3:
         if ((rc = copyv(b.vB, va))) return rc;
-        k_artvisc<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, VB, A, c->sc);
+        k_artvisc<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, VB, A, c->sc);
         break;
     case 4: {
         if (!m.has_nu) break;
         QSet<T> tau{};
         for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
         tau.nq = 6;
-        k_visc_tau<T><<<cell_grid(m, m.j1 - m.j0 + 1, m.k1 - m.k0 + 1), cell_block(m), 0, s>>>(m, b.tab, A, tau, c->sc);
-        k_visc_apply<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, A, VB, tau, c->sc);
+        k_visc_tau<T><<<tau_grid(m), cell_block(m), 0, s>>>(m, b.tab, A, tau, c->sc);
+        k_visc_apply<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, A, VB, tau, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
     }
@@ -888,7 +890,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         break;
     }
     case 8:
-        k_newvel<T><<<cell_grid(m, m.nyt + 1, m.nzt + 1), cell_block(m), 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
+        k_newvel<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
         break;
     case 9:
         if (m.fargo && m.hasX)

@@ -69,27 +69,32 @@ __global__ void __launch_bounds__(256) kb_cfl_exact(const StepPlan<T> *__restric
     cfl_exact_body(p.m, p.tb, p.A, p.v0, p.ringmax, p.part, p.sc, p.nrings_active, local, p.cfl_blocks);
 }
 
-// Per-cell phases: a member's blocks tile (azimuth, row, plane) as the
-// single-instance grid does, with blockDim.x azimuths per block.
+// Per-cell phases: a member's cells of the augmented mesh (rows, planes as
+// in the single-instance grid) are numbered row by row, blockDim.x
+// consecutive cells per block, so no block is padded to a row's end.
 template <typename T, int PH>
 __global__ void __launch_bounds__(256) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
     const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
     const MeshD &m = p.m;
-    const int nbx = (m.nx + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int nyr = PH == PH_TAU ? m.j1 - m.j0 + 1 : m.nyt + 1;
-    const int bx = local % nbx, r = local / nbx;
-    int by = r % nyr, bz = r / nyr;
+    const unsigned nyr = PH == PH_TAU ? tau_rows(m) : m.nyt + 1;
+    const unsigned npl = PH == PH_TAU ? tau_planes(m) : cell_planes(m);
+    const unsigned nx = (unsigned)m.nx;
+    const unsigned lin = (unsigned)local * blockDim.x + threadIdx.x;
+    const unsigned row = lin / nx;
+    if (row >= nyr * npl) return;
+    const int i = (int)(lin - row * nx);
+    int j = (int)(row % nyr), k = (int)(row / nyr);
     if constexpr (PH == PH_TAU) {
-        by += m.j0;
-        bz += m.k0;
+        j += m.j0;
+        k += m.k0;
     }
-    if constexpr (PH == PH_SUB1) substep1_body(m, p.tb, p.A, p.VB, p.sc, bx, by, bz);
-    else if constexpr (PH == PH_AV) artvisc_body(m, p.tb, p.VB, p.A, p.sc, bx, by, bz);
-    else if constexpr (PH == PH_TAU) visc_tau_body(m, p.tb, p.A, p.tau, p.sc, bx, by, bz);
-    else if constexpr (PH == PH_VAPPLY) visc_apply_body(m, p.tb, p.A, p.VB, p.tau, p.sc, bx, by, bz);
-    else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, bx, by, bz);
+    if constexpr (PH == PH_SUB1) substep1_body(m, p.tb, p.A, p.VB, p.sc, i, j, k);
+    else if constexpr (PH == PH_AV) artvisc_body(m, p.tb, p.VB, p.A, p.sc, i, j, k);
+    else if constexpr (PH == PH_TAU) visc_tau_body(m, p.tb, p.A, p.tau, p.sc, i, j, k);
+    else if constexpr (PH == PH_VAPPLY) visc_apply_body(m, p.tb, p.A, p.VB, p.tau, p.sc, i, j, k);
+    else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, i, j, k);
 }
 
 template <typename T, int C>
@@ -272,9 +277,11 @@ static int batch_setup(fargo_batch *b)
     }
     auto all = [](const fargo_ctx *) { return true; };
     auto one = [](const fargo_ctx *) { return 0; };
-    auto cells = [](const fargo_ctx *c) { return ((c->nx + 255) / 256) * (c->nyt + 1) * (c->nzt + 1); };
+    auto cells = [](const fargo_ctx *c) {
+        return (int)grid_for((long long)c->nx * (c->nyt + 1) * cell_planes(c->m), 256);
+    };
     auto tau_cells = [](const fargo_ctx *c) {
-        return ((c->nx + 255) / 256) * (c->m.j1 - c->m.j0 + 1) * (c->m.k1 - c->m.k0 + 1);
+        return (int)grid_for((long long)c->nx * tau_rows(c->m) * tau_planes(c->m), 256);
     };
     auto hasY = [](const fargo_ctx *c) { return c->m.hasY != 0; };
     auto hasZ = [](const fargo_ctx *c) { return c->m.hasZ != 0; };

@@ -2,27 +2,24 @@
 // compression heating, and the viscous stress tensor.
 //
 // Every kernel runs one thread per cell of the augmented mesh (ghosts and the
-// extra face row / plane included) and writes its output velocity buffer
-// completely: interior faces get the update, every other face is copied, so
-// the buffers can ping-pong without stale values.
+// extra face row, plus the extra face plane when Z is active) and writes its
+// output velocity buffer completely: interior faces get the update, every
+// other face is copied, so the buffers can ping-pong without stale values.
+// Without a Z direction v_z is not a variable of the method: it is neither
+// read nor written.  The bodies take the cell (i, j, k) with 0 <= i < nx; the
+// kernel wrappers map their launch shape onto cells.
 #pragma once
 #include "fargo_internal.cuh"
 
 namespace fk {
 
-struct CellIdx {
-    int i, j, k;
-};
-
-// Per-cell kernels run on a 3D grid: x covers the azimuth, y the rows and z
-// the planes of the augmented mesh (extra face row / plane included).
-__device__ __forceinline__ bool decode(const MeshD &m, CellIdx &c, int bx, int by, int bz)
-{
-    c.i = bx * blockDim.x + threadIdx.x;
-    c.j = by;
-    c.k = bz;
-    return c.i < m.nx;
-}
+// Planes of the augmented mesh the per-cell kernels visit: the extra face
+// plane only holds v_z of the last ghost's upper face.
+__device__ __host__ __forceinline__ int cell_planes(const MeshD &m) { return m.nzt + (m.hasZ ? 1 : 0); }
+// Rows j0..j1 and planes k0..k1 of the stress pass (the upper ones only with
+// that direction).
+__device__ __host__ __forceinline__ int tau_rows(const MeshD &m) { return m.j1 - m.j0 + (m.hasY ? 1 : 0); }
+__device__ __host__ __forceinline__ int tau_planes(const MeshD &m) { return m.k1 - m.k0 + (m.hasZ ? 1 : 0); }
 
 // Pressure from the equation of state (Eqs. eos1, eos2).
 template <typename T>
@@ -60,13 +57,10 @@ __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i,
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
-                                              const Scal *sc, int bx, int by, int bz)
+                                              const Scal *sc, int i, int j, int k)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    CellIdx ci;
-    if (!decode(m, ci, bx, by, bz)) return;
-    const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
@@ -112,9 +106,9 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
         }
         out.vy[c] = v;
     }
-    if (j < m.nyt) {
+    if (m.hasZ && j < m.nyt) {
         T v = in.vz[c];
-        if (m.hasZ && k > m.k0 && k < m.k1 && jact) {
+        if (k > m.k0 && k < m.k1 && jact) {
             const long long cm = c - m.sk;
             const int rm = ring - m.nyt;
             const T id = tb.idzc[ring];
@@ -153,15 +147,12 @@ __device__ __forceinline__ T qvisc(T c2, T rho, T dv)
 
 template <typename T>
 __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
-                                             const Scal *sc, int bx, int by, int bz)
+                                             const Scal *sc, int i, int j, int k)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    CellIdx ci;
-    if (!decode(m, ci, bx, by, bz)) return;
     const T c2 = tb.cq2;
     const bool av = m.has_av != 0;
-    const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
@@ -194,9 +185,9 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
         out.vy[c] = v;
         vyl = v;
     }
-    if (j < m.nyt) {
+    if (m.hasZ && j < m.nyt) {
         T v = vz[c];
-        if (av && m.hasZ && k > m.k0 && k < m.k1 && jact) {
+        if (av && k > m.k0 && k < m.k1 && jact) {
             const long long cm = c - sk;
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
             const T qm = qvisc(c2, rho[cm], vz[c] - vz[cm]);
@@ -453,9 +444,9 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
         }
         out.vy[c] = v;
     }
-    if (j < m.nyt) {
+    if (m.hasZ && j < m.nyt) {
         T v = in.vz[c];
-        if (m.hasZ && k > m.k0 && k < m.k1 && jact) {
+        if (k > m.k0 && k < m.k1 && jact) {
             const long long ckm = c - m.sk;
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
@@ -501,7 +492,7 @@ struct TauArr {
         const long long o = at(i, j, k);
         a = xx[o];
         b = yy[o];
-        c = zz[o];
+        c = m.hasZ ? zz[o] : T(0);
     }
     __device__ T txy(int i, int j, int k) const { return xy[at(i, j, k)]; }
     __device__ T txz(int i, int j, int k) const { return xz[at(i, j, k)]; }
@@ -513,14 +504,12 @@ struct TauArr {
 // (rows j0..j1, planes k0..k1).
 template <typename T>
 __device__ __forceinline__ void visc_tau_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &tau,
-                                              const Scal *sc, int bx, int by, int bz)
+                                              const Scal *sc, int i, int j, int k)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    const int i = bx * blockDim.x + threadIdx.x;
-    // rows j0..j1 and planes k0..k1 (by, bz index the augmented mesh)
-    const int j = by, k = bz;
-    if (i >= m.nx || j < m.j0 || j > m.j1 || k < m.k0 || k > m.k1) return;
+    // rows j0..j1, planes k0..k1 (the upper one only with that direction)
+    if (j < m.j0 || j > m.j1 - (m.hasY ? 0 : 1) || k < m.k0 || k > m.k1 - (m.hasZ ? 0 : 1)) return;
     const ViscCtx<T> V(m, tb, in);
     const long long c = IX(m, i, j, k);
     const bool jin = j < m.j1, kin = k < m.k1;
@@ -529,7 +518,7 @@ __device__ __forceinline__ void visc_tau_body(const MeshD &m, const Tab<T> &tb, 
         V.diag(i, j, k, a, b, d);
         tau.q[0][c] = a;
         tau.q[1][c] = b;
-        tau.q[2][c] = d;
+        if (m.hasZ) tau.q[2][c] = d;
     }
     if (m.hasY && kin) tau.q[3][c] = V.txy(i, j, k);
     if (m.hasZ && jin) tau.q[4][c] = V.txz(i, j, k);
@@ -539,37 +528,42 @@ __device__ __forceinline__ void visc_tau_body(const MeshD &m, const Tab<T> &tb, 
 // Pass 2: the velocity update of Eqs. 75-77 from the stored stresses.
 template <typename T>
 __device__ __forceinline__ void visc_apply_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in,
-                                                const Fld<T> &out, const QSet<T> &tau, const Scal *sc, int bx,
-                                                int by, int bz)
+                                                const Fld<T> &out, const QSet<T> &tau, const Scal *sc, int i,
+                                                int j, int k)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    CellIdx ci;
-    if (!decode(m, ci, bx, by, bz)) return;
     const TauArr<T> S{m, tau.q[0], tau.q[1], tau.q[2], tau.q[3], tau.q[4], tau.q[5]};
-    visc_apply(m, tb, in, out, dt, ci.i, ci.j, ci.k, S);
+    visc_apply(m, tb, in, out, dt, i, j, k, S);
 }
 
+// Single-instance wrappers: a 3D grid, x over the azimuth (blockDim.x
+// cells per block), y over the rows, z over the planes.
 template <typename T>
 __global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
-    substep1_body(m, tb, in, out, sc, blockIdx.x, blockIdx.y, blockIdx.z);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.nx) substep1_body(m, tb, in, out, sc, i, blockIdx.y, blockIdx.z);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
-    artvisc_body(m, tb, in, out, sc, blockIdx.x, blockIdx.y, blockIdx.z);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.nx) artvisc_body(m, tb, in, out, sc, i, blockIdx.y, blockIdx.z);
 }
+// grid rows and planes start at j0 and k0
 template <typename T>
 __global__ void __launch_bounds__(256) k_visc_tau(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> tau, const Scal *sc)
 {
-    visc_tau_body(m, tb, in, tau, sc, blockIdx.x, m.j0 + blockIdx.y, m.k0 + blockIdx.z);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.nx) visc_tau_body(m, tb, in, tau, sc, i, m.j0 + blockIdx.y, m.k0 + blockIdx.z);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_visc_apply(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, QSet<T> tau,
                                                     const Scal *sc)
 {
-    visc_apply_body(m, tb, in, out, tau, sc, blockIdx.x, blockIdx.y, blockIdx.z);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.nx) visc_apply_body(m, tb, in, out, tau, sc, i, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace fk

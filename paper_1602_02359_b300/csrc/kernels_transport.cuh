@@ -646,13 +646,10 @@ __device__ __forceinline__ T *qsel(const QSet<T> &s, int n)
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, const QSet<T> &fin, const Fld<T> &vsrc,
-                                            const Fld<T> &state, Scal *sc, int copy_scalars, int bx, int by, int bz)
+                                            const Fld<T> &state, Scal *sc, int copy_scalars, int i, int j, int k)
 {
     const T dtT = step_dt<T>(sc);
     if (!(dtT > T(0))) return;
-    CellIdx ci;
-    if (!decode(m, ci, bx, by, bz)) return;
-    const int i = ci.i, j = ci.j, k = ci.k;
     if (i == 0 && j == 0 && k == 0) {
         sc->t = sc->t + sc->dt;
         sc->nstep += 1;
@@ -687,9 +684,9 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
         }
         state.vy[c] = v;
     }
-    if (j < m.nyt) {
+    if (m.hasZ && j < m.nyt) {
         T v = vsrc.vz[c];
-        if (m.hasZ && k > m.k0 && k < m.k1 && jact) {
+        if (k > m.k0 && k < m.k1 && jact) {
             const long long cm = c - m.sk;
             v = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
         }
@@ -701,7 +698,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin, Fld<T> vsrc, Fld<T> state,
                                                 Scal *sc, int copy_scalars)
 {
-    newvel_body(m, tb, fin, vsrc, state, sc, copy_scalars, blockIdx.x, blockIdx.y, blockIdx.z);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.nx) newvel_body(m, tb, fin, vsrc, state, sc, copy_scalars, i, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
