@@ -317,3 +317,58 @@ def random_box(geom, nx, ny, nz, g=3, seed=0, iso=False, nu=1e-3, planet=True,
         st["e"][:] = 0.0
     w.state = st
     return w
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate of the batched disk sweep (no counterpart in the paper):
+# seeded inputs only.  The network maps (log10 q, h, log10 nu) and the
+# initial surface density on SURR_BINS radial bins to the azimuthally
+# averaged Sigma / Sigma_0 after a fixed number of orbits on the same bins.
+# ---------------------------------------------------------------------------
+SURR_BINS = 256
+
+
+def mlp_dims(n_in=3 + SURR_BINS, width=256, hidden=4, n_out=SURR_BINS):
+    """Layer widths: input, `hidden` hidden layers, output."""
+    return [n_in] + [width] * hidden + [n_out]
+
+
+def mlp_init(dims, seed):
+    """Seeded initial parameters: He-uniform weights W_l of shape
+    (dims[l+1], dims[l]) drawn from U(-sqrt(6/fan_in), +sqrt(6/fan_in)),
+    zero biases.  Returns [(W_0, b_0), (W_1, b_1), ...] in FP64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for a, b in zip(dims[:-1], dims[1:]):
+        lim = math.sqrt(6.0 / a)
+        out.append((rng.uniform(-lim, lim, size=(b, a)), np.zeros(b)))
+    return out
+
+
+def surrogate_bins(n=SURR_BINS, rmin=0.4, rmax=2.5):
+    """Bin centres, logarithmically spaced on [rmin, rmax]."""
+    e = np.linspace(math.log(rmin), math.log(rmax), n + 1)
+    return np.exp(0.5 * (e[:-1] + e[1:]))
+
+
+def surrogate_params(n=4096, seed=1602, nr=(48, 96)):
+    """Parameter draws of the surrogate's training sweep: the batched sweep's
+    distributions of q, h and nu (seeded PCG64) on reduced meshes,
+    Nr ~ U{nr[0]..nr[1]}, Nphi = 3 Nr."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = rng.integers(nr[0], nr[1] + 1, size=n)
+    q = 10.0 ** rng.uniform(-5.0, -3.0, size=n)
+    h = rng.uniform(0.03, 0.07, size=n)
+    nu = 10.0 ** rng.uniform(-6.0, -5.0, size=n)
+    return [dict(nx=int(3 * a), ny=int(a), q=float(b), h=float(c), nu=float(d))
+            for a, b, c, d in zip(r, q, h, nu)]
+
+
+def regression_set(n, n_in, n_out, seed):
+    """A smooth synthetic regression task (inputs U(-1, 1), targets a fixed
+    random two-layer tanh map) for training tests of the network kernels."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.uniform(-1.0, 1.0, size=(n, n_in))
+    a = rng.normal(size=(n_in, 64)) / math.sqrt(n_in)
+    b = rng.normal(size=(64, n_out)) / 8.0
+    return x, np.tanh(x @ a) @ b
