@@ -3,8 +3,9 @@
     python -m paper_1602_02359_b300.build
 
 Compiles the translation units csrc/fargo_api.cu (single-instance entry
-points) and csrc/fargo_batch.cu (batched engine) in parallel with nvcc, then
-links them into libfargo_b300.so next to this file.  Host code is compiled
+points), csrc/fargo_batch.cu (batched engine) and csrc/mlp.cu (surrogate
+network) in parallel with nvcc, then links them into libfargo_b300.so next
+to this file.  Host code is compiled
 without floating-point contraction so that the FP64 geometry tables match a
 plain IEEE evaluation.
 """
@@ -28,7 +29,7 @@ def sources():
     return out
 
 
-UNITS = ("fargo_api.cu", "fargo_batch.cu")
+UNITS = ("fargo_api.cu", "fargo_batch.cu", "mlp.cu")
 OBJ_DIR = os.path.join(HERE, "_build")
 FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
 

@@ -1,0 +1,602 @@
+// Surrogate network of the batched disk sweep: bfloat16 tensor-core products
+// with FP32 accumulation for the forward pass, back-propagation and Adam.
+// The contract of each entry point is in include/fargo_mlp.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/fargo.h"
+#include "../../include/fargo_mlp.h"
+
+namespace mlp {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------------------
+// Tiled product C[m][n] = sum_k A^[m][k] B^[n][k] on the bfloat16 tensor
+// cores (mma m16n8k16, FP32 accumulators).  A^[m][k] is A[m*lda + k], or
+// A[k*lda + m] when TA; B^[n][k] likewise with TB.  A 64 x 64 block tile,
+// 32-deep K slices staged in shared memory K-contiguous (rows padded to 40
+// values so the 8 row addresses of an ldmatrix fall in distinct banks); four
+// warps of 32 x 32.  Out-of-range elements load as zero, so any M, N, K work.
+// ---------------------------------------------------------------------------
+constexpr int BM = 64, BN = 64, BK = 32, SROW = BK + 8, NT = 128;
+
+enum { EPI_HIDDEN, EPI_OUT, EPI_STORE, EPI_DA };
+
+struct GemmArgs {
+    const bf16 *A, *B;
+    int lda, ldb, M, N, K;
+    // EPI_HIDDEN: Z = acc + bias (FP32), Ab = bf16(relu(Z))
+    // EPI_OUT:    C = acc + bias (FP32)
+    // EPI_STORE:  C = acc (FP32)
+    // EPI_DA:     acc masked by Zmask > 0 -> C (FP32) and Ab (bf16)
+    float *C;
+    bf16 *Ab;
+    const float *bias, *Zmask;
+    int ldc;
+};
+
+__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float *d, const unsigned *a, unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Stage rows r0.. of a K slice k0.. of X^ (TX: X^[r][k] = X[k*ld + r]).
+template <bool TX, int ROWS>
+__device__ __forceinline__ void load_tile(bf16 (*s)[SROW], const bf16 *X, int ld, int R, int Kd, int r0, int k0)
+{
+    const bf16 zero = __float2bfloat16(0.0f);
+    for (int idx = threadIdx.x; idx < ROWS * BK; idx += NT) {
+        int r, k;
+        if (TX) {
+            r = idx % ROWS;
+            k = idx / ROWS;
+        } else {
+            r = idx / BK;
+            k = idx % BK;
+        }
+        const int gr = r0 + r, gk = k0 + k;
+        bf16 v = zero;
+        if (gr < R && gk < Kd) v = TX ? X[(size_t)gk * ld + gr] : X[(size_t)gr * ld + gk];
+        s[r][k] = v;
+    }
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(NT) k_gemm(GemmArgs g)
+{
+    __shared__ __align__(16) bf16 sA[BM][SROW];
+    __shared__ __align__(16) bf16 sB[BN][SROW];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[a][b][c] = 0.0f;
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+        load_tile<TA, BM>(sA, g.A, g.lda, g.M, g.K, m0, k0);
+        load_tile<TB, BN>(sB, g.B, g.ldb, g.N, g.K, n0, k0);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
+                ldsm_x4(su32(&sA[wm + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]), af[mt][0], af[mt][1],
+                        af[mt][2], af[mt][3]);
+#pragma unroll
+            for (int np = 0; np < 2; np++)
+                ldsm_x4(su32(&sB[wn + np * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]),
+                        bfr[2 * np][0], bfr[2 * np][1], bfr[2 * np + 1][0], bfr[2 * np + 1][1]);
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
+        }
+        __syncthreads();
+    }
+    // accumulator element (row g, cols 2t, 2t+1) and (row g+8, same cols)
+    const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const int row = m0 + wm + mt * 16 + gq + (h >> 1) * 8;
+                const int col = n0 + wn + nt * 8 + tq * 2 + (h & 1);
+                if (row >= g.M || col >= g.N) continue;
+                const size_t o = (size_t)row * g.ldc + col;
+                float v = acc[mt][nt][h];
+                if (EPI == EPI_HIDDEN) {
+                    v += g.bias[col];
+                    g.C[o] = v;
+                    g.Ab[o] = __float2bfloat16_rn(v > 0.0f ? v : 0.0f);
+                } else if (EPI == EPI_OUT) {
+                    g.C[o] = v + g.bias[col];
+                } else if (EPI == EPI_STORE) {
+                    g.C[o] = v;
+                } else {
+                    v = g.Zmask[o] > 0.0f ? v : 0.0f;
+                    g.C[o] = v;
+                    g.Ab[o] = __float2bfloat16_rn(v);
+                }
+            }
+}
+
+template <bool TA, bool TB, int EPI>
+static void gemm(const GemmArgs &g, cudaStream_t s)
+{
+    const dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    k_gemm<TA, TB, EPI><<<grid, NT, 0, s>>>(g);
+}
+
+// x' = bf16((x - shift) * scale)
+__global__ void k_input(const float *x, int n, int cols, const float *shift, const float *scale, bf16 *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = i % cols;
+        out[i] = __float2bfloat16_rn((x[i] - shift[c]) * scale[c]);
+    }
+}
+
+// Mean-squared error and its gradient 2 (y - t) / count, one block with a
+// fixed-shape reduction (deterministic).
+__global__ void __launch_bounds__(1024) k_mse(const float *y, const float *t, int count, float *dz, bf16 *dzb,
+                                              float *loss)
+{
+    __shared__ float red[32];
+    const float s2 = 2.0f / (float)count;
+    float acc = 0.0f;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const float d = y[i] - t[i];
+        acc += d * d;
+        const float gz = s2 * d;
+        dz[i] = gz;
+        dzb[i] = __float2bfloat16_rn(gz);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0 && loss) *loss = v / (float)count;
+    }
+}
+
+// Bias gradients: column sums of dz [rows][cols], one thread per column.
+__global__ void k_colsum(const float *dz, int rows, int cols, float *db)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; r++) s += dz[(size_t)r * cols + c];
+    db[c] = s;
+}
+
+struct AdamHyper {
+    float lr, b1, b2, eps;
+    int t;
+};
+
+__global__ void k_adam_tick(AdamHyper *h) { h->t += 1; }
+
+// Adam on the flat parameter vector; bfloat16 copies re-rounded.
+__global__ void k_adam(float *w, float *m, float *v, const float *g, bf16 *wb, size_t n, const AdamHyper *h)
+{
+    const float lr = h->lr, b1 = h->b1, b2 = h->b2, eps = h->eps;
+    const float t = (float)h->t;
+    const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        wb[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+__global__ void k_round(const float *w, bf16 *wb, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// One block per sample: ensemble mean and relative spread.
+__global__ void __launch_bounds__(256) k_ensemble(const float *ys, int k, int batch, int n, float *mean,
+                                                   float *spread)
+{
+    __shared__ float r1[8], r2[8];
+    const int b = blockIdx.x;
+    float sv = 0.0f, sm = 0.0f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        float mu = 0.0f;
+        for (int e = 0; e < k; e++) mu += ys[((size_t)e * batch + b) * n + j];
+        mu /= (float)k;
+        float var = 0.0f;
+        for (int e = 0; e < k; e++) {
+            const float d = ys[((size_t)e * batch + b) * n + j] - mu;
+            var += d * d;
+        }
+        var /= (float)(k - 1);
+        mean[(size_t)b * n + j] = mu;
+        sv += var;
+        sm += mu * mu;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        r1[threadIdx.x >> 5] = sv;
+        r2[threadIdx.x >> 5] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.0f, c = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            a += r1[w];
+            c += r2[w];
+        }
+        spread[b] = c > 0.0f ? sqrtf(a / c) : 0.0f;
+    }
+}
+
+}  // namespace mlp
+
+using namespace mlp;
+
+struct fargo_mlp {
+    std::vector<int> dims;
+    int L = 0, max_batch = 0;
+    size_t np = 0;
+    std::vector<size_t> woff, boff;   // offsets of W_l and b_l in the parameter vector
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;   // FP32 master, moments, gradients
+    bf16 *wb = nullptr;                                            // bfloat16 copy (same layout)
+    float *shift = nullptr, *scale = nullptr;
+    bf16 *xb = nullptr;                                            // bfloat16 input
+    std::vector<float *> Z;                                        // hidden pre-activations (FP32)
+    std::vector<bf16 *> Ab;                                        // hidden activations (bf16)
+    float *y = nullptr;                                            // output of the last forward
+    float *dz[2] = {nullptr, nullptr};
+    bf16 *dzb[2] = {nullptr, nullptr};
+    AdamHyper *hyper = nullptr;
+    std::vector<void *> allocs;
+    cudaGraphExec_t gexec = nullptr;
+    const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+    int gbatch = 0;
+};
+
+#define MK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            fprintf(stderr, "fargo_mlp: %s failed: %s\n", #call, cudaGetErrorString(e_));     \
+            return e_ == cudaErrorMemoryAllocation ? FARGO_ERR_OOM : FARGO_ERR_CUDA;           \
+        }                                                                                     \
+    } while (0)
+
+template <typename P>
+static int nalloc(fargo_mlp *n, P **p, size_t count)
+{
+    void *q = nullptr;
+    MK(cudaMalloc(&q, (count ? count : 1) * sizeof(P)));
+    n->allocs.push_back(q);
+    MK(cudaMemsetAsync(q, 0, (count ? count : 1) * sizeof(P), n->stream));
+    *p = (P *)q;
+    return FARGO_OK;
+}
+
+static unsigned blocks_for(size_t n, int bs)
+{
+    size_t b = (n + bs - 1) / bs;
+    return (unsigned)(b > 4096 ? 4096 : (b ? b : 1));
+}
+
+extern "C" int fargo_mlp_create(fargo_mlp **out, const int *dims, int nlayers, int max_batch, void *stream)
+{
+    if (!out || !dims || nlayers < 1 || nlayers > 16 || max_batch < 1) return FARGO_ERR_BADARG;
+    *out = nullptr;
+    for (int l = 0; l <= nlayers; l++)
+        if (dims[l] < 1 || dims[l] > 4096) return FARGO_ERR_BADARG;
+    fargo_mlp *n = new fargo_mlp();
+    n->dims.assign(dims, dims + nlayers + 1);
+    n->L = nlayers;
+    n->max_batch = max_batch;
+    for (int l = 0; l < nlayers; l++) {
+        n->woff.push_back(n->np);
+        n->np += (size_t)dims[l] * dims[l + 1];
+        n->boff.push_back(n->np);
+        n->np += dims[l + 1];
+    }
+    int rc = FARGO_OK;
+    if (stream) {
+        n->stream = (cudaStream_t)stream;
+    } else if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        n->own_stream = true;
+    } else {
+        delete n;
+        return FARGO_ERR_CUDA;
+    }
+    const size_t B = (size_t)max_batch;
+    int wmax = 0;
+    for (int d : n->dims) wmax = d > wmax ? d : wmax;
+    if (!rc) rc = nalloc(n, &n->w, n->np);
+    if (!rc) rc = nalloc(n, &n->m, n->np);
+    if (!rc) rc = nalloc(n, &n->v, n->np);
+    if (!rc) rc = nalloc(n, &n->g, n->np);
+    if (!rc) rc = nalloc(n, &n->wb, n->np);
+    if (!rc) rc = nalloc(n, &n->shift, dims[0]);
+    if (!rc) rc = nalloc(n, &n->scale, dims[0]);
+    if (!rc) rc = nalloc(n, &n->xb, B * dims[0]);
+    for (int l = 0; l < nlayers - 1 && !rc; l++) {
+        float *z = nullptr;
+        bf16 *a = nullptr;
+        rc = nalloc(n, &z, B * dims[l + 1]);
+        if (!rc) rc = nalloc(n, &a, B * dims[l + 1]);
+        n->Z.push_back(z);
+        n->Ab.push_back(a);
+    }
+    if (!rc) rc = nalloc(n, &n->y, B * dims[nlayers]);
+    for (int q = 0; q < 2 && !rc; q++) {
+        rc = nalloc(n, &n->dz[q], B * wmax);
+        if (!rc) rc = nalloc(n, &n->dzb[q], B * wmax);
+    }
+    if (!rc) rc = nalloc(n, &n->hyper, 1);
+    if (!rc) {
+        std::vector<float> ones(dims[0], 1.0f);
+        AdamHyper h{1e-3f, 0.9f, 0.999f, 1e-8f, 0};
+        if (cudaMemcpyAsync(n->scale, ones.data(), sizeof(float) * dims[0], cudaMemcpyHostToDevice, n->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(n->hyper, &h, sizeof(h), cudaMemcpyHostToDevice, n->stream) != cudaSuccess ||
+            cudaStreamSynchronize(n->stream) != cudaSuccess)
+            rc = FARGO_ERR_CUDA;
+    }
+    if (rc) {
+        fargo_mlp_destroy(n);
+        return rc;
+    }
+    *out = n;
+    return FARGO_OK;
+}
+
+extern "C" void fargo_mlp_destroy(fargo_mlp *n)
+{
+    if (!n) return;
+    if (n->stream) cudaStreamSynchronize(n->stream);
+    if (n->gexec) cudaGraphExecDestroy(n->gexec);
+    for (void *p : n->allocs) cudaFree(p);
+    if (n->own_stream) cudaStreamDestroy(n->stream);
+    delete n;
+}
+
+extern "C" size_t fargo_mlp_num_params(const fargo_mlp *n) { return n ? n->np : 0; }
+
+extern "C" int fargo_mlp_set_params(fargo_mlp *n, const float *host, size_t count)
+{
+    if (!n || !host) return FARGO_ERR_BADARG;
+    if (count != n->np) return FARGO_ERR_SIZE;
+    MK(cudaMemcpyAsync(n->w, host, n->np * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+    MK(cudaMemsetAsync(n->m, 0, n->np * sizeof(float), n->stream));
+    MK(cudaMemsetAsync(n->v, 0, n->np * sizeof(float), n->stream));
+    k_round<<<blocks_for(n->np, 256), 256, 0, n->stream>>>(n->w, n->wb, n->np);
+    MK(cudaGetLastError());
+    const int zero = 0;
+    MK(cudaMemcpyAsync(&n->hyper->t, &zero, sizeof(int), cudaMemcpyHostToDevice, n->stream));
+    MK(cudaStreamSynchronize(n->stream));
+    return FARGO_OK;
+}
+
+static int copy_out(fargo_mlp *n, const float *src, float *host, size_t count)
+{
+    if (!n || !host) return FARGO_ERR_BADARG;
+    if (count != n->np) return FARGO_ERR_SIZE;
+    MK(cudaMemcpyAsync(host, src, n->np * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    MK(cudaStreamSynchronize(n->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_mlp_get_params(fargo_mlp *n, float *host, size_t count)
+{
+    return n ? copy_out(n, n->w, host, count) : FARGO_ERR_BADARG;
+}
+
+extern "C" int fargo_mlp_get_grads(fargo_mlp *n, float *host, size_t count)
+{
+    return n ? copy_out(n, n->g, host, count) : FARGO_ERR_BADARG;
+}
+
+extern "C" int fargo_mlp_set_input_map(fargo_mlp *n, const float *shift, const float *scale)
+{
+    if (!n || !shift || !scale) return FARGO_ERR_BADARG;
+    MK(cudaMemcpyAsync(n->shift, shift, sizeof(float) * n->dims[0], cudaMemcpyHostToDevice, n->stream));
+    MK(cudaMemcpyAsync(n->scale, scale, sizeof(float) * n->dims[0], cudaMemcpyHostToDevice, n->stream));
+    MK(cudaStreamSynchronize(n->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_mlp_set_optimizer(fargo_mlp *n, float lr, float b1, float b2, float eps)
+{
+    if (!n || !(lr > 0.0f) || !(b1 >= 0.0f && b1 < 1.0f) || !(b2 >= 0.0f && b2 < 1.0f) || !(eps >= 0.0f))
+        return FARGO_ERR_BADARG;
+    AdamHyper h;
+    MK(cudaMemcpyAsync(&h, n->hyper, sizeof(h), cudaMemcpyDeviceToHost, n->stream));
+    MK(cudaStreamSynchronize(n->stream));
+    h.lr = lr;
+    h.b1 = b1;
+    h.b2 = b2;
+    h.eps = eps;
+    MK(cudaMemcpyAsync(n->hyper, &h, sizeof(h), cudaMemcpyHostToDevice, n->stream));
+    MK(cudaStreamSynchronize(n->stream));
+    return FARGO_OK;
+}
+
+// Forward pass into n->y (hidden pre-activations and activations kept).
+static int forward(fargo_mlp *n, const float *x, int batch)
+{
+    cudaStream_t s = n->stream;
+    const int K0 = n->dims[0];
+    k_input<<<blocks_for((size_t)batch * K0, 256), 256, 0, s>>>(x, batch * K0, K0, n->shift, n->scale, n->xb);
+    const bf16 *A = n->xb;
+    for (int l = 0; l < n->L; l++) {
+        GemmArgs g{};
+        g.A = A;
+        g.lda = n->dims[l];
+        g.B = n->wb + n->woff[l];
+        g.ldb = n->dims[l];
+        g.M = batch;
+        g.N = n->dims[l + 1];
+        g.K = n->dims[l];
+        g.bias = n->w + n->boff[l];
+        g.ldc = g.N;
+        if (l < n->L - 1) {
+            g.C = n->Z[l];
+            g.Ab = n->Ab[l];
+            gemm<false, false, EPI_HIDDEN>(g, s);
+            A = n->Ab[l];
+        } else {
+            g.C = n->y;
+            gemm<false, false, EPI_OUT>(g, s);
+        }
+    }
+    MK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+extern "C" int fargo_mlp_forward(fargo_mlp *n, const float *x, int batch, float *y)
+{
+    if (!n || !x || !y || batch < 1) return FARGO_ERR_BADARG;
+    if (batch > n->max_batch) return FARGO_ERR_SIZE;
+    int rc = forward(n, x, batch);
+    if (rc) return rc;
+    MK(cudaMemcpyAsync(y, n->y, sizeof(float) * batch * n->dims[n->L], cudaMemcpyDeviceToDevice, n->stream));
+    return FARGO_OK;
+}
+
+static int backward(fargo_mlp *n, const float *x, const float *t, int batch, float *loss)
+{
+    int rc = forward(n, x, batch);
+    if (rc) return rc;
+    cudaStream_t s = n->stream;
+    const int L = n->L;
+    int cur = 0;
+    k_mse<<<1, 1024, 0, s>>>(n->y, t, batch * n->dims[L], n->dz[cur], n->dzb[cur], loss);
+    for (int l = L - 1; l >= 0; l--) {
+        const int No = n->dims[l + 1], Ki = n->dims[l];
+        const bf16 *Ain = l == 0 ? n->xb : n->Ab[l - 1];
+        // dW_l[o][i] = sum_b dZ[b][o] A[b][i]
+        GemmArgs gw{};
+        gw.A = n->dzb[cur];
+        gw.lda = No;
+        gw.B = Ain;
+        gw.ldb = Ki;
+        gw.M = No;
+        gw.N = Ki;
+        gw.K = batch;
+        gw.C = n->g + n->woff[l];
+        gw.ldc = Ki;
+        gemm<true, true, EPI_STORE>(gw, s);
+        k_colsum<<<(No + 255) / 256, 256, 0, s>>>(n->dz[cur], batch, No, n->g + n->boff[l]);
+        if (l > 0) {
+            // dZ_{l-1}[b][i] = (Z_{l-1}[b][i] > 0) sum_o dZ[b][o] W_l[o][i]
+            GemmArgs ga{};
+            ga.A = n->dzb[cur];
+            ga.lda = No;
+            ga.B = n->wb + n->woff[l];
+            ga.ldb = Ki;
+            ga.M = batch;
+            ga.N = Ki;
+            ga.K = No;
+            ga.C = n->dz[1 - cur];
+            ga.Ab = n->dzb[1 - cur];
+            ga.Zmask = n->Z[l - 1];
+            ga.ldc = Ki;
+            gemm<false, true, EPI_DA>(ga, s);
+            cur = 1 - cur;
+        }
+    }
+    MK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+extern "C" int fargo_mlp_backward(fargo_mlp *n, const float *x, const float *t, int batch, float *loss)
+{
+    if (!n || !x || !t || batch < 1) return FARGO_ERR_BADARG;
+    if (batch > n->max_batch) return FARGO_ERR_SIZE;
+    return backward(n, x, t, batch, loss);
+}
+
+static int adam(fargo_mlp *n)
+{
+    k_adam_tick<<<1, 1, 0, n->stream>>>(n->hyper);
+    k_adam<<<blocks_for(n->np, 256), 256, 0, n->stream>>>(n->w, n->m, n->v, n->g, n->wb, n->np, n->hyper);
+    MK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+extern "C" int fargo_mlp_adam(fargo_mlp *n) { return n ? adam(n) : FARGO_ERR_BADARG; }
+
+extern "C" int fargo_mlp_train_step(fargo_mlp *n, const float *x, const float *t, int batch, float *loss)
+{
+    if (!n || !x || !t || batch < 1) return FARGO_ERR_BADARG;
+    if (batch > n->max_batch) return FARGO_ERR_SIZE;
+    const void *key[4] = {x, t, loss, nullptr};
+    if (!n->gexec || memcmp(key, n->gkey, sizeof(key)) != 0 || n->gbatch != batch) {
+        if (n->gexec) {
+            cudaGraphExecDestroy(n->gexec);
+            n->gexec = nullptr;
+        }
+        MK(cudaStreamBeginCapture(n->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = backward(n, x, t, batch, loss);
+        if (!rc) rc = adam(n);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(n->stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return FARGO_ERR_CUDA;
+        e = cudaGraphInstantiate(&n->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return FARGO_ERR_CUDA;
+        memcpy(n->gkey, key, sizeof(key));
+        n->gbatch = batch;
+    }
+    MK(cudaGraphLaunch(n->gexec, n->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_mlp_ensemble(const float *ys, int k, int batch, int n, float *mean, float *spread, void *stream)
+{
+    if (!ys || !mean || !spread || k < 2 || batch < 1 || n < 1) return FARGO_ERR_BADARG;
+    k_ensemble<<<batch, 256, 0, (cudaStream_t)stream>>>(ys, k, batch, n, mean, spread);
+    MK(cudaGetLastError());
+    return FARGO_OK;
+}
