@@ -7,7 +7,8 @@ It shares no code with the CUDA library.
 
 Definitions (the network has no counterpart in the paper):
   Z_l = A_{l-1} W_l^T + b_l,  A_l = max(Z_l, 0) for hidden layers,
-  Y = Z_L (linear output), A_0 = X (rows = samples);
+  Y = Z_L * s + c (linear output with an optional per-output map (c, s)),
+  A_0 = X (rows = samples);
   loss = mean over samples and outputs of (Y - T)^2;
   Adam (Kingma & Ba 2015, Algorithm 1): m <- b1 m + (1-b1) g,
   v <- b2 v + (1-b2) g^2, w <- w - lr mhat / (sqrt(vhat) + eps) with
@@ -38,8 +39,9 @@ def _q(a, on):
     return bf16_round(a) if on else np.asarray(a, dtype=np.float64)
 
 
-def forward(params, X, emulate_bf16=False):
-    """Returns (Y, cache) with cache = (A_0 .. A_{L-1}, Z_1 .. Z_L)."""
+def forward(params, X, emulate_bf16=False, out_map=None):
+    """Returns (Y, cache) with cache = (A_0 .. A_{L-1}, Z_1 .. Z_L);
+    out_map = (shift, scale) per output, or None for the identity."""
     A = _q(X, emulate_bf16)
     As, Zs = [A], []
     L = len(params)
@@ -49,18 +51,21 @@ def forward(params, X, emulate_bf16=False):
         if l < L - 1:
             A = _q(np.maximum(Z, 0.0), emulate_bf16)
             As.append(A)
-    return Zs[-1], (As, Zs)
+    Y = Zs[-1] if out_map is None else Zs[-1] * out_map[1] + out_map[0]
+    return Y, (As, Zs)
 
 
 def loss(Y, T):
     return float(np.mean((Y - T) ** 2))
 
 
-def grads(params, X, T, emulate_bf16=False):
+def grads(params, X, T, emulate_bf16=False, out_map=None):
     """(loss, [(dW_l, db_l)]) of the mean-squared error by back-propagation."""
-    Y, (As, Zs) = forward(params, X, emulate_bf16)
+    Y, (As, Zs) = forward(params, X, emulate_bf16, out_map)
     B, m = Y.shape
     dZ = 2.0 * (Y - T) / (B * m)
+    if out_map is not None:
+        dZ = dZ * out_map[1]
     out = [None] * len(params)
     for l in range(len(params) - 1, -1, -1):
         W = _q(params[l][0], emulate_bf16)

@@ -31,8 +31,8 @@ def test_loss_is_the_library_mean_squared_error():
     assert M.loss(Y, T) == pytest.approx(mean_squared_error(T, Y), rel=1e-15)
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_gradients_match_central_differences(seed):
+@pytest.mark.parametrize("seed,mapped", [(0, False), (1, False), (2, True)])
+def test_gradients_match_central_differences(seed, mapped):
     """Every weight and bias gradient of a 3-layer ReLU network against
     central differences of the FP64 loss (h = 1e-6), with random biases so
     that no pre-activation sits on the ReLU kink (checked)."""
@@ -40,9 +40,10 @@ def test_gradients_match_central_differences(seed):
     params = [(Wl, rng.normal(size=bl.size) * 0.5) for Wl, bl in small_net(seed)]
     X = rng.normal(size=(11, 7))
     T = rng.normal(size=(11, 4))
+    om = (rng.normal(size=4), rng.uniform(0.1, 3.0, size=4)) if mapped else None
     _, (_, Zs) = M.forward(params, X)
     assert min(np.abs(z).min() for z in Zs[:-1]) > 1e-4
-    _, g = M.grads(params, X, T)
+    _, g = M.grads(params, X, T, out_map=om)
     dims = [7, 6, 5, 4]
     vec = M.flatten(params)
     gvec = M.flatten(g)
@@ -52,8 +53,8 @@ def test_gradients_match_central_differences(seed):
         vp, vm = vec.copy(), vec.copy()
         vp[idx] += h
         vm[idx] -= h
-        fp = M.loss(M.forward(M.unflatten(vp, dims), X)[0], T)
-        fm = M.loss(M.forward(M.unflatten(vm, dims), X)[0], T)
+        fp = M.loss(M.forward(M.unflatten(vp, dims), X, out_map=om)[0], T)
+        fm = M.loss(M.forward(M.unflatten(vm, dims), X, out_map=om)[0], T)
         fd = (fp - fm) / (2 * h)
         worst = max(worst, abs(fd - gvec[idx]) / (abs(gvec[idx]) + 1e-6))
     assert worst < 1e-5, worst
@@ -77,6 +78,16 @@ def test_single_linear_layer_gradient_closed_form():
     sol = np.linalg.lstsq(Xa, T, rcond=None)[0]
     _, g2 = M.grads([(sol[:5].T, sol[5])], X, T)
     assert np.abs(g2[0][0]).max() < 1e-13 and np.abs(g2[0][1]).max() < 1e-13
+
+
+def test_identity_output_map_changes_nothing():
+    params = small_net(4)
+    rng = np.random.Generator(np.random.PCG64(12))
+    X, T = rng.normal(size=(6, 7)), rng.normal(size=(6, 4))
+    idm = (np.zeros(4), np.ones(4))
+    assert np.array_equal(M.forward(params, X)[0], M.forward(params, X, out_map=idm)[0])
+    a, b = M.grads(params, X, T), M.grads(params, X, T, out_map=idm)
+    assert a[0] == b[0] and all(np.array_equal(x[0], y[0]) for x, y in zip(a[1], b[1]))
 
 
 def test_relu_special_cases():
