@@ -53,6 +53,12 @@ int fargo_mlp_get_grads(fargo_mlp *net, float *host, size_t n);
  * Synchronises. */
 int fargo_mlp_set_input_map(fargo_mlp *net, const float *shift, const float *scale);
 
+/* Output map applied after the last layer: y = z * scale + shift per output
+ * (host arrays of dims[L] values; default 0 and 1).  The loss compares y
+ * with the targets, so its gradient with respect to z carries the scale.
+ * Synchronises. */
+int fargo_mlp_set_output_map(fargo_mlp *net, const float *shift, const float *scale);
+
 /* Adam hyper-parameters read by every later fargo_mlp_adam (default
  * lr 1e-3, b1 0.9, b2 0.999, eps 1e-8).  Synchronises. */
 int fargo_mlp_set_optimizer(fargo_mlp *net, float lr, float b1, float b2, float eps);

@@ -31,12 +31,12 @@ struct GemmArgs {
     const bf16 *A, *B;
     int lda, ldb, M, N, K;
     // EPI_HIDDEN: Z = acc + bias (FP32), Ab = bf16(relu(Z))
-    // EPI_OUT:    C = acc + bias (FP32)
+    // EPI_OUT:    C = (acc + bias) * oscale + oshift (FP32)
     // EPI_STORE:  C = acc (FP32)
     // EPI_DA:     acc masked by Zmask > 0 -> C (FP32) and Ab (bf16)
     float *C;
     bf16 *Ab;
-    const float *bias, *Zmask;
+    const float *bias, *Zmask, *oshift, *oscale;
     int ldc;
 };
 
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmArgs g)
                     g.C[o] = v;
                     g.Ab[o] = __float2bfloat16_rn(v > 0.0f ? v : 0.0f);
                 } else if (EPI == EPI_OUT) {
-                    g.C[o] = v + g.bias[col];
+                    g.C[o] = (v + g.bias[col]) * g.oscale[col] + g.oshift[col];
                 } else if (EPI == EPI_STORE) {
                     g.C[o] = v;
                 } else {
@@ -161,10 +161,11 @@ __global__ void k_input(const float *x, int n, int cols, const float *shift, con
     }
 }
 
-// Mean-squared error and its gradient 2 (y - t) / count, one block with a
-// fixed-shape reduction (deterministic).
-__global__ void __launch_bounds__(1024) k_mse(const float *y, const float *t, int count, float *dz, bf16 *dzb,
-                                              float *loss)
+// Mean-squared error of y = z * oscale + oshift and its gradient with respect
+// to z, 2 (y - t) oscale / count; one block with a fixed-shape reduction
+// (deterministic).
+__global__ void __launch_bounds__(1024) k_mse(const float *y, const float *t, int count, int cols,
+                                              const float *oscale, float *dz, bf16 *dzb, float *loss)
 {
     __shared__ float red[32];
     const float s2 = 2.0f / (float)count;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(1024) k_mse(const float *y, const float *t, in
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         const float d = y[i] - t[i];
         acc += d * d;
-        const float gz = s2 * d;
+        const float gz = s2 * d * oscale[i % cols];
         dz[i] = gz;
         dzb[i] = __float2bfloat16_rn(gz);
     }
@@ -280,7 +281,8 @@ struct fargo_mlp {
     bool own_stream = false;
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;   // FP32 master, moments, gradients
     bf16 *wb = nullptr;                                            // bfloat16 copy (same layout)
-    float *shift = nullptr, *scale = nullptr;
+    float *shift = nullptr, *scale = nullptr;      // input map
+    float *oshift = nullptr, *oscale = nullptr;    // output map
     bf16 *xb = nullptr;                                            // bfloat16 input
     std::vector<float *> Z;                                        // hidden pre-activations (FP32)
     std::vector<bf16 *> Ab;                                        // hidden activations (bf16)
@@ -355,6 +357,8 @@ extern "C" int fargo_mlp_create(fargo_mlp **out, const int *dims, int nlayers, i
     if (!rc) rc = nalloc(n, &n->wb, n->np);
     if (!rc) rc = nalloc(n, &n->shift, dims[0]);
     if (!rc) rc = nalloc(n, &n->scale, dims[0]);
+    if (!rc) rc = nalloc(n, &n->oshift, dims[nlayers]);
+    if (!rc) rc = nalloc(n, &n->oscale, dims[nlayers]);
     if (!rc) rc = nalloc(n, &n->xb, B * dims[0]);
     for (int l = 0; l < nlayers - 1 && !rc; l++) {
         float *z = nullptr;
@@ -371,10 +375,12 @@ extern "C" int fargo_mlp_create(fargo_mlp **out, const int *dims, int nlayers, i
     }
     if (!rc) rc = nalloc(n, &n->hyper, 1);
     if (!rc) {
-        std::vector<float> ones(dims[0], 1.0f);
+        std::vector<float> ones(wmax, 1.0f);
         AdamHyper h{1e-3f, 0.9f, 0.999f, 1e-8f, 0};
         if (cudaMemcpyAsync(n->scale, ones.data(), sizeof(float) * dims[0], cudaMemcpyHostToDevice, n->stream) !=
                 cudaSuccess ||
+            cudaMemcpyAsync(n->oscale, ones.data(), sizeof(float) * dims[nlayers], cudaMemcpyHostToDevice,
+                            n->stream) != cudaSuccess ||
             cudaMemcpyAsync(n->hyper, &h, sizeof(h), cudaMemcpyHostToDevice, n->stream) != cudaSuccess ||
             cudaStreamSynchronize(n->stream) != cudaSuccess)
             rc = FARGO_ERR_CUDA;
@@ -442,6 +448,16 @@ extern "C" int fargo_mlp_set_input_map(fargo_mlp *n, const float *shift, const f
     return FARGO_OK;
 }
 
+extern "C" int fargo_mlp_set_output_map(fargo_mlp *n, const float *shift, const float *scale)
+{
+    if (!n || !shift || !scale) return FARGO_ERR_BADARG;
+    const int m = n->dims[n->L];
+    MK(cudaMemcpyAsync(n->oshift, shift, sizeof(float) * m, cudaMemcpyHostToDevice, n->stream));
+    MK(cudaMemcpyAsync(n->oscale, scale, sizeof(float) * m, cudaMemcpyHostToDevice, n->stream));
+    MK(cudaStreamSynchronize(n->stream));
+    return FARGO_OK;
+}
+
 extern "C" int fargo_mlp_set_optimizer(fargo_mlp *n, float lr, float b1, float b2, float eps)
 {
     if (!n || !(lr > 0.0f) || !(b1 >= 0.0f && b1 < 1.0f) || !(b2 >= 0.0f && b2 < 1.0f) || !(eps >= 0.0f))
@@ -483,6 +499,8 @@ static int forward(fargo_mlp *n, const float *x, int batch)
             A = n->Ab[l];
         } else {
             g.C = n->y;
+            g.oshift = n->oshift;
+            g.oscale = n->oscale;
             gemm<false, false, EPI_OUT>(g, s);
         }
     }
@@ -507,7 +525,7 @@ static int backward(fargo_mlp *n, const float *x, const float *t, int batch, flo
     cudaStream_t s = n->stream;
     const int L = n->L;
     int cur = 0;
-    k_mse<<<1, 1024, 0, s>>>(n->y, t, batch * n->dims[L], n->dz[cur], n->dzb[cur], loss);
+    k_mse<<<1, 1024, 0, s>>>(n->y, t, batch * n->dims[L], n->dims[L], n->oscale, n->dz[cur], n->dzb[cur], loss);
     for (int l = L - 1; l >= 0; l--) {
         const int No = n->dims[l + 1], Ki = n->dims[l];
         const bf16 *Ain = l == 0 ? n->xb : n->Ab[l - 1];

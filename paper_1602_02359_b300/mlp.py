@@ -28,6 +28,7 @@ def _lib():
         for f in ("fargo_mlp_set_params", "fargo_mlp_get_params", "fargo_mlp_get_grads"):
             getattr(L, f).argtypes = [vp, vp, C.c_size_t]
         L.fargo_mlp_set_input_map.argtypes = [vp, vp, vp]
+        L.fargo_mlp_set_output_map.argtypes = [vp, vp, vp]
         L.fargo_mlp_set_optimizer.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
         L.fargo_mlp_forward.argtypes = [vp, vp, C.c_int, vp]
         L.fargo_mlp_backward.argtypes = [vp, vp, vp, C.c_int, vp]
@@ -88,6 +89,11 @@ class Mlp:
         s = np.ascontiguousarray(shift, dtype=np.float32)
         c = np.ascontiguousarray(scale, dtype=np.float32)
         _check(_lib().fargo_mlp_set_input_map(self.h, s.ctypes.data, c.ctypes.data), "fargo_mlp_set_input_map")
+
+    def set_output_map(self, shift, scale):
+        s = np.ascontiguousarray(shift, dtype=np.float32)
+        c = np.ascontiguousarray(scale, dtype=np.float32)
+        _check(_lib().fargo_mlp_set_output_map(self.h, s.ctypes.data, c.ctypes.data), "fargo_mlp_set_output_map")
 
     def set_optimizer(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         _check(_lib().fargo_mlp_set_optimizer(self.h, lr, b1, b2, eps), "fargo_mlp_set_optimizer")

@@ -128,6 +128,31 @@ def test_train_step_graph_equals_backward_plus_adam_and_learns():
     b.close()
 
 
+def test_output_map_forward_and_gradients():
+    import torch
+    dims = [33, 70, 65, 9]
+    net, vec, p = net_and_params(dims, 12)
+    rng = np.random.Generator(np.random.PCG64(13))
+    sh = rng.normal(size=9).astype(np.float32)
+    sc = rng.uniform(0.01, 2, size=9).astype(np.float32)
+    net.set_output_map(sh, sc)
+    om = (sh.astype(np.float64), sc.astype(np.float64))
+    X = rng.uniform(-1, 1, size=(50, 33)).astype(np.float32)
+    T = rng.normal(size=(50, 9)).astype(np.float32)
+    y = torch.empty(50, 9, device="cuda")
+    net.forward(dev(X), y)
+    Yo, _ = M.forward(p, X.astype(np.float64), emulate_bf16=True, out_map=om)
+    assert rel_l2(y.cpu().numpy(), Yo) < 2e-3
+    loss = torch.zeros(1, device="cuda")
+    net.backward(dev(X), dev(T), loss)
+    lo, go = M.grads(p, X.astype(np.float64), T.astype(np.float64), emulate_bf16=True, out_map=om)
+    assert abs(loss.item() - lo) <= 1e-4 * lo
+    gl = M.unflatten(net.get_grads().astype(np.float64), dims)
+    for (dW, db), (oW, ob) in zip(gl, go):
+        assert rel_l2(dW, oW) < 1e-2 and rel_l2(db, ob) < 1e-2
+    net.close()
+
+
 def test_input_map_is_applied_before_the_first_layer():
     import torch
     dims = [12, 32, 5]
