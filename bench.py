@@ -305,7 +305,12 @@ def fp64_plain_disk2d(torch, fb, steps=50, warmup=5):
             "l2": "flushed (512 MB write) before every timed step", "err": err}
 
 
-def roofline_of(per, cells, table, esz, traffic_tab=None):
+# The method's minimum traffic per cell-update: read the state once for the
+# Courant step, then read and write it once for the update (3 F b).
+METHOD_FIELDS_3D_ADI, METHOD_FIELDS_2D_ISO = 5, 3
+
+
+def roofline_of(per, cells, table, esz, traffic_tab=None, method_fields=None):
     """Roofline of the dominant kernel from per-launch device times (ms)."""
     hbm, peak_kind = peaks()
     avg = {k: sum(v) / len(v) for k, v in per.items()}
@@ -320,7 +325,13 @@ def roofline_of(per, cells, table, esz, traffic_tab=None):
     if traffic_tab is not None and top in traffic_tab:
         traffic = int(traffic_tab[top] * cells)
     step_alg = sum(table.get(k, 0) for k in avg) * esz * cells
-    return {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+    extra = {}
+    if method_fields:
+        mb = 3 * method_fields * esz * cells
+        extra = {"method_bytes_per_cell": 3 * method_fields * esz,
+                 "method_GBps": round(mb / (tot * 1e-3) / 1e9, 1),
+                 "method_frac": round(mb / (tot * 1e-3) / 1e9 / hbm, 4)}
+    return {**extra, "bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "peak_kind": f"{peak_kind} copy bandwidth (burst)",
             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(avg[top], 4), "traffic": traffic,
             "step_alg_GBps": round(step_alg / (tot * 1e-3) / 1e9, 1),
@@ -371,7 +382,8 @@ def bench_single(args, torch, fb, wname, dev, barrier, e2e_on=True, steps=None):
     table = ALG_FIELDS_3D if (w.nz > 1 and not w.iso) else ALG_FIELDS_2D_ISO
     traffic_tab = (TRAFFIC_PER_CELL_3D if (fp32 and w.nz > 1 and not w.iso
                                            and kernel_source_hash() == KERNEL_SRC_HASH) else None)
-    roof = roofline_of(per, w.cells, table, esz, traffic_tab)
+    roof = roofline_of(per, w.cells, table, esz, traffic_tab,
+                       METHOD_FIELDS_3D_ADI if (w.nz > 1 and not w.iso) else METHOD_FIELDS_2D_ISO)
     e2e = None
     if e2e_on:
         names = ["rho", "e", "vx", "vy", "vz"] if not w.iso else ["rho", "vx", "vy", "vz"]
@@ -423,7 +435,7 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
                 per.setdefault(name, []).append(t)
     running, _ = b.status()
     nsteps = [m.scalars()[2] for m in mem]
-    roof = roofline_of(per, cells, ALG_FIELDS_2D_ISO, 4)
+    roof = roofline_of(per, cells, ALG_FIELDS_2D_ISO, 4, method_fields=METHOD_FIELDS_2D_ISO)
     e2e = None
     if e2e_on:
         # public API end to end: every step uploads each disk's active state
@@ -521,8 +533,9 @@ def main():
         s = bench_single(args, torch, fb, "disk3d", dev, lambda: None, e2e_on=False, steps=min(args.steps, 20))
         single = {"workload": s["workload"], "dtype": "f32", "value": s["cells"] / (s["ms"] * 1e-3),
                   "unit": "cell-updates/s", "ms_per_step": s["ms"],
-                  "roofline": {k: s["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac",
-                                                             "step_alg_GBps", "step_frac", "traffic")},
+                  "roofline": {k: s["roofline"].get(k) for k in ("kernel", "achieved", "peak", "unit", "frac",
+                                                                 "step_alg_GBps", "step_frac", "method_GBps",
+                                                                 "method_frac", "traffic")},
                   "per_kernel": s["roofline"]["per_kernel"], "clocks": s["clocks"]}
 
     fp64 = None
