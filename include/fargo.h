@@ -187,6 +187,30 @@ int fargo_set_aux(fargo_ctx *ctx, int which, const void *src, size_t bytes);
  * max_kernels entries; *n_out receives the count.  Synchronises. */
 int fargo_profile_step(fargo_ctx *ctx, int max_kernels, float *ms, int *n_out, const char **names);
 
+/* Autotuner of the launch shapes that leave every result unchanged: the
+ * azimuths per block of the per-cell source kernels (128, 256, 512) and the
+ * segment lengths of the Y and Z sweeps (16 .. 256 rows).  Each candidate is
+ * timed with CUDA events on `reps` (>= 2, the first one warming up) full
+ * steps, coordinate by coordinate; the state and time are restored from a
+ * device snapshot before every trial step and at the end, so the run is
+ * unchanged.  cfg (may be NULL) receives {cell block, Y segment, Z segment}.
+ * Allocates a temporary snapshot of the state; synchronises.  The paper's
+ * own code searches block sizes per kernel in a similar way (Sec. 4.2).  Errors:
+ * BADARG, OOM, CUDA. */
+int fargo_autotune(fargo_ctx *ctx, int reps, int *cfg);
+
+/* Set those launch shapes directly: cell_bs in {128, 256, 512}; seg_y, seg_z
+ * rows per sweep segment (0 = the default: the whole axis up to 96 rows,
+ * else 64). */
+int fargo_set_launch_shape(fargo_ctx *ctx, int cell_bs, int seg_y, int seg_z);
+
+/* Failure-detection check of the kernels' bounded waits: one block waits on
+ * an mbarrier whose arrival never comes, for at most spin_limit polls
+ * (1 .. 2^22; the kernels use 2^22), and records the timeout as the step
+ * kernels do.  Returns FARGO_ERR_BARRIER_TIMEOUT, the expected outcome:
+ * no hang and no fault.  Synchronises the legacy default stream. */
+int fargo_debug_wait_timeout(unsigned spin_limit);
+
 /* Use (1) or bypass (0) the CUDA graph for fargo_step (default 1). */
 int fargo_use_graph(fargo_ctx *ctx, int enable);
 

@@ -29,7 +29,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
             "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step",
+            "fargo_batch_profile_step", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -99,6 +99,9 @@ def lib():
         L.fargo_batch_launches_per_step.argtypes = [vp]
         L.fargo_batch_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int),
                                                C.POINTER(C.c_char_p)]
+        L.fargo_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.fargo_set_launch_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.fargo_debug_wait_timeout.argtypes = [C.c_uint]
         L.fargo_strerror.argtypes = [C.c_int]
         L.fargo_strerror.restype = C.c_char_p
         _lib = L
@@ -251,8 +254,24 @@ class Fargo:
     def use_graph(self, on=True):
         _check(lib().fargo_use_graph(self.h, int(on)), "fargo_use_graph")
 
+    def autotune(self, reps=3):
+        """Pick the per-cell block width and the sweep segment lengths by
+        timing; the state is left unchanged.  Returns (block, seg_y, seg_z)."""
+        cfg = (C.c_int * 3)()
+        _check(lib().fargo_autotune(self.h, reps, cfg), "fargo_autotune")
+        return tuple(cfg)
+
+    def set_launch_shape(self, cell_bs=256, seg_y=0, seg_z=0):
+        _check(lib().fargo_set_launch_shape(self.h, cell_bs, seg_y, seg_z), "fargo_set_launch_shape")
+
     def launches_per_step(self):
         return lib().fargo_launches_per_step(self.h)
+
+
+def debug_wait_timeout(spin_limit=1000):
+    """Run the bounded-wait failure check; returns the library's code
+    (FARGO_ERR_BARRIER_TIMEOUT = -7 when the wait ran out, as expected)."""
+    return lib().fargo_debug_wait_timeout(spin_limit)
 
 
 def sums_noalloc(rho, e, vx, precision, nx, ny, nz, ghost, vol, R, omega_frame, out, nblocks=0, stream=None):

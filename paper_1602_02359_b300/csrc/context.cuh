@@ -78,6 +78,9 @@ struct fargo_ctx {
     int tx_threads = 256;
     std::vector<double> yfaces_store, zfaces_store;
     fk::SweepMaps mapsY{}, mapsZ{};   // tensor maps of the Y and Z sweeps of the step
+    // launch shapes (fargo_autotune): azimuths per block of the per-cell
+    // kernels, and segment lengths of the Y / Z sweeps (0 = the default rule)
+    int cell_bs = 256, seg_y = 0, seg_z = 0;
 };
 
 #define CK(call)                                                                                 \
@@ -145,8 +148,8 @@ static StepPlan<T> make_plan(const fargo_ctx *c, const Buffers<T> &b)
     p.ringmax = c->ringmax;
     p.nrings_active = c->nrings_active;
     p.cfl_blocks = c->cfl_blocks;
-    p.seg_y = sweep_seglen(m.j1 - m.j0);
-    p.seg_z = sweep_seglen(m.k1 - m.k0);
+    p.seg_y = c->seg_y > 0 ? c->seg_y : sweep_seglen(m.j1 - m.j0);
+    p.seg_z = c->seg_z > 0 ? c->seg_z : sweep_seglen(m.k1 - m.k0);
     return p;
 }
 
@@ -158,20 +161,21 @@ static inline int err_code(int flags)
     return FARGO_OK;
 }
 
-// 3D launch shape of the per-cell kernels: x = azimuth, y = rows, z = planes.
-static inline dim3 cell_block(const MeshD &m)
+// 3D launch shape of the per-cell kernels: x = azimuth (at most bs per
+// block), y = rows, z = planes.
+static inline dim3 cell_block(const MeshD &m, int bs)
 {
     int bx = (m.nx + 31) / 32 * 32;
-    return dim3(bx < 256 ? bx : 256, 1, 1);
+    return dim3(bx < bs ? bx : bs, 1, 1);
 }
-static inline dim3 cell_grid(const MeshD &m, int ny, int nz)
+static inline dim3 cell_grid(const MeshD &m, int ny, int nz, int bs)
 {
-    const dim3 b = cell_block(m);
+    const dim3 b = cell_block(m, bs);
     return dim3((m.nx + b.x - 1) / b.x, ny, nz);
 }
 // every row (extra face row included) and the planes of cell_planes()
-static inline dim3 cell_grid_all(const MeshD &m) { return cell_grid(m, m.nyt + 1, cell_planes(m)); }
-static inline dim3 tau_grid(const MeshD &m) { return cell_grid(m, tau_rows(m), tau_planes(m)); }
+static inline dim3 cell_grid_all(const MeshD &m, int bs) { return cell_grid(m, m.nyt + 1, cell_planes(m), bs); }
+static inline dim3 tau_grid(const MeshD &m, int bs) { return cell_grid(m, tau_rows(m), tau_planes(m), bs); }
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 

@@ -338,7 +338,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         }                                                           \
         nl++;                                                       \
     } while (0)
-    const dim3 cb = cell_block(m), cg = cell_grid_all(m);
+    const dim3 cb = cell_block(m, c->cell_bs), cg = cell_grid_all(m, c->cell_bs);
     // cell 2
     if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_y"); }
     if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_z"); }
@@ -352,7 +352,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     k_artvisc<T><<<cg, cb, 0, s>>>(m, P.tb, P.VB, P.A, P.sc); MARK("artvisc");
     if (m.has_nu) {
         // stresses once into the scratch momenta of set B (unused until the transport step)
-        k_visc_tau<T><<<tau_grid(m), cb, 0, s>>>(m, P.tb, P.A, P.tau, P.sc); MARK("visc_tau");
+        k_visc_tau<T><<<tau_grid(m, c->cell_bs), cb, 0, s>>>(m, P.tb, P.A, P.tau, P.sc); MARK("visc_tau");
         k_visc_apply<T><<<cg, cb, 0, s>>>(m, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
     }
     // cell 9
@@ -362,11 +362,11 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_smem, s);
     MARK("transport_x");
     if (m.hasY) {
-        launch_sweep_tma<T, 1>(m, P.tb, c->mapsY, P.qy, P.sc, P.qx.nq, s);
+        launch_sweep_tma<T, 1>(m, P.tb, c->mapsY, P.qy, P.sc, P.qx.nq, s, P.seg_y);
         MARK("transport_y");
     }
     if (m.hasZ) {
-        launch_sweep_tma<T, 2>(m, P.tb, c->mapsZ, P.qz, P.sc, P.qx.nq, s);
+        launch_sweep_tma<T, 2>(m, P.tb, c->mapsZ, P.qz, P.sc, P.qx.nq, s, P.seg_z);
         MARK("transport_z");
     }
     // the uniform orbital step comes last, in place on the state set
@@ -858,20 +858,20 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         // the screening launch fills the per-step planet angle tables
         k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
                                                       c->nrings_active);
-        k_substep1<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, A, VB, c->sc);
+        k_substep1<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, A, VB, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
     case 3:
         if ((rc = copyv(b.vB, va))) return rc;
-        k_artvisc<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, VB, A, c->sc);
+        k_artvisc<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, VB, A, c->sc);
         break;
     case 4: {
         if (!m.has_nu) break;
         QSet<T> tau{};
         for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
         tau.nq = 6;
-        k_visc_tau<T><<<tau_grid(m), cell_block(m), 0, s>>>(m, b.tab, A, tau, c->sc);
-        k_visc_apply<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, A, VB, tau, c->sc);
+        k_visc_tau<T><<<tau_grid(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, A, tau, c->sc);
+        k_visc_apply<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, A, VB, tau, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
     }
@@ -890,7 +890,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         break;
     }
     case 8:
-        k_newvel<T><<<cell_grid_all(m), cell_block(m), 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
+        k_newvel<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
         break;
     case 9:
         if (m.fargo && m.hasX)
@@ -986,6 +986,196 @@ extern "C" int fargo_profile_step(fargo_ctx *c, int max_kernels, float *ms, int 
     }
     for (int i = 0; i < 32; i++) cudaEventDestroy(prof.ev[i]);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the launch shapes that do not change results: the azimuths
+// per block of the per-cell kernels (the same compiled kernel on any block
+// width) and the segment lengths of the Y / Z sweeps (each column marches
+// the same arithmetic whatever the segmentation).  Coordinate search with
+// per-launch CUDA events on `reps` steps per candidate, the state restored
+// from a snapshot before every trial step and at the end.
+// ---------------------------------------------------------------------------
+namespace {
+struct Snapshot {
+    std::vector<void *> bufs;
+    ~Snapshot()
+    {
+        for (void *p : bufs) cudaFree(p);
+    }
+};
+}  // namespace
+
+template <typename T>
+static int snapshot_copy(fargo_ctx *c, Buffers<T> &b, Snapshot &sn, bool save)
+{
+    const size_t nbytes = (size_t)c->m.ntot * sizeof(T);
+    T *f[5] = {b.A.rho, b.A.e, b.A.vx, b.A.vy, b.A.vz};
+    void *aux[2] = {c->sc, c->v0};
+    const size_t auxb[2] = {sizeof(Scal), sizeof(double) * (size_t)c->nyt * c->nzt};
+    if (save && sn.bufs.empty()) {
+        for (int q = 0; q < 7; q++) {
+            void *p = nullptr;
+            CK(cudaMalloc(&p, q < 5 ? nbytes : auxb[q - 5]));
+            sn.bufs.push_back(p);
+        }
+    }
+    for (int q = 0; q < 7; q++) {
+        void *live = q < 5 ? (void *)f[q] : aux[q - 5];
+        const size_t n = q < 5 ? nbytes : auxb[q - 5];
+        if (save) CK(cudaMemcpyAsync(sn.bufs[q], live, n, cudaMemcpyDeviceToDevice, c->stream));
+        else CK(cudaMemcpyAsync(live, sn.bufs[q], n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return FARGO_OK;
+}
+
+// Summed device time (ms) of the launches named in `names` over `reps`
+// steps of the current configuration, the state restored before each.
+template <typename T>
+static int time_step_kernels(fargo_ctx *c, Buffers<T> &b, Snapshot &sn, int reps, const char *const *names,
+                             int nnames, double *ms_out)
+{
+    double tot = 0.0;
+    for (int r = 0; r < reps; r++) {
+        int rc = snapshot_copy<T>(c, b, sn, false);
+        if (rc) return rc;
+        Prof prof{};
+        for (int i = 0; i < 32; i++) CK(cudaEventCreate(&prof.ev[i]));
+        CK(cudaEventRecord(prof.ev[0], c->stream));
+        rc = enqueue_step<T>(c, b, &prof);
+        if (rc == FARGO_OK) {
+            CK(cudaStreamSynchronize(c->stream));
+            for (int i = 0; i < prof.n; i++)
+                for (int q = 0; q < nnames; q++)
+                    if (!strcmp(prof.name[i], names[q])) {
+                        float ms = 0.0f;
+                        CK(cudaEventElapsedTime(&ms, prof.ev[i], prof.ev[i + 1]));
+                        if (r > 0) tot += ms;   // the first repetition warms up
+                    }
+        }
+        for (int i = 0; i < 32; i++) cudaEventDestroy(prof.ev[i]);
+        if (rc) return rc;
+    }
+    *ms_out = tot;
+    return FARGO_OK;
+}
+
+template <typename T>
+static int autotune_impl(fargo_ctx *c, Buffers<T> &b, int reps, int *cfg)
+{
+    Snapshot sn;
+    int rc = snapshot_copy<T>(c, b, sn, true);
+    if (rc) return rc;
+    const MeshD &m = c->m;
+    const char *cell_names[] = {"substep1", "artvisc", "visc_tau", "visc_apply", "newvel"};
+    const int cand_bs[] = {128, 256, 512};
+    double best = 1e300;
+    int best_bs = c->cell_bs;
+    for (int bs : cand_bs) {
+        if (bs > 32 && (m.nx + 31) / 32 * 32 < bs && bs != 128) continue;   // wider than a row
+        c->cell_bs = bs;
+        double t;
+        if ((rc = time_step_kernels<T>(c, b, sn, reps, cell_names, 5, &t))) return rc;
+        if (t < best) {
+            best = t;
+            best_bs = bs;
+        }
+    }
+    c->cell_bs = best_bs;
+    const int cand_seg[] = {16, 32, 64, 128, 256};
+    for (int axis = 1; axis <= 2; axis++) {
+        if ((axis == 1 && !m.hasY) || (axis == 2 && !m.hasZ)) continue;
+        const int np = axis == 1 ? m.j1 - m.j0 : m.k1 - m.k0;
+        int &seg = axis == 1 ? c->seg_y : c->seg_z;
+        const char *nm[] = {axis == 1 ? "transport_y" : "transport_z"};
+        best = 1e300;
+        int best_seg = seg;
+        for (int sl : cand_seg) {
+            if (sl > np && sl != cand_seg[0]) continue;
+            seg = sl < np ? sl : np;
+            double t;
+            if ((rc = time_step_kernels<T>(c, b, sn, reps, nm, 1, &t))) return rc;
+            if (t < best) {
+                best = t;
+                best_seg = seg;
+            }
+        }
+        seg = best_seg;
+    }
+    if ((rc = snapshot_copy<T>(c, b, sn, false))) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    // the captured step used the old shapes
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (cfg) {
+        cfg[0] = c->cell_bs;
+        cfg[1] = c->seg_y;
+        cfg[2] = c->seg_z;
+    }
+    return FARGO_OK;
+}
+
+extern "C" int fargo_autotune(fargo_ctx *c, int reps, int *cfg)
+{
+    if (!c || reps < 2) return FARGO_ERR_BADARG;
+    return c->prec == FARGO_F64 ? autotune_impl<double>(c, c->b64, reps, cfg)
+                                : autotune_impl<float>(c, c->b32, reps, cfg);
+}
+
+extern "C" int fargo_set_launch_shape(fargo_ctx *c, int cell_bs, int seg_y, int seg_z)
+{
+    if (!c || (cell_bs != 128 && cell_bs != 256 && cell_bs != 512) || seg_y < 0 || seg_z < 0)
+        return FARGO_ERR_BADARG;
+    c->cell_bs = cell_bs;
+    c->seg_y = seg_y;
+    c->seg_z = seg_z;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return FARGO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Failure-detection check of the bounded waits: an mbarrier that expects one
+// arrival which never comes, waited on with a given poll budget.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_probe(unsigned limit, int *flag)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool done = mbar_wait(&bar, 0, limit);
+    if (!done && threadIdx.x == 0) atomicOr(flag, kErrTimeout);
+}
+
+extern "C" int fargo_debug_wait_timeout(unsigned spin_limit)
+{
+    if (spin_limit < 1 || spin_limit > (1u << 22)) return FARGO_ERR_BADARG;
+    int *d = nullptr, h = 0;
+    CK(cudaMalloc(&d, sizeof(int)));
+    int rc = FARGO_OK;
+    if (cudaMemset(d, 0, sizeof(int)) != cudaSuccess) rc = FARGO_ERR_CUDA;
+    if (!rc) {
+        k_wait_probe<<<1, 64>>>(spin_limit, d);
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = FARGO_ERR_CUDA;
+    }
+    cudaFree(d);
+    return rc ? rc : err_code(h);
 }
 
 extern "C" int fargo_use_graph(fargo_ctx *c, int enable)

@@ -585,12 +585,12 @@ static size_t sweep_tma_smem(int nq)
 
 template <typename T, int AXIS>
 static void launch_sweep_tma(const MeshD &m, const Tab<T> &tb, const SweepMaps &maps, const QSet<T> &out,
-                             Scal *sc, int nq, cudaStream_t s)
+                             Scal *sc, int nq, cudaStream_t s, int seglen = 0)
 {
     constexpr int TW = TmaTile<T>::TW;
     const int np = AXIS == 1 ? m.j1 - m.j0 : m.k1 - m.k0;
     const int n2 = AXIS == 1 ? m.k1 - m.k0 : m.j1 - m.j0;
-    const int seglen = sweep_seglen(np);
+    if (seglen <= 0) seglen = sweep_seglen(np);
     const int nseg = (np + seglen - 1) / seglen;
     const int ntx = (m.nx + TW - 1) / TW;
     const unsigned g = (unsigned)ntx * n2 * nseg;

@@ -42,11 +42,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait for the phase of the given parity to complete.  Returns false
-// when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+// when the budget of `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit = kSpinLimit)
 {
     const unsigned a = smem_u32(bar);
-    for (unsigned it = 0; it < kSpinLimit; it++) {
+    for (unsigned it = 0; it < limit; it++) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
