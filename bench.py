@@ -339,6 +339,17 @@ def roofline_of(per, cells, table, esz, traffic_tab=None, method_fields=None):
             "kernel_share": share, "per_kernel": per_kernel}
 
 
+def add_step_times(per, launches):
+    """Accumulate one profiled step: the device times of the launches of one
+    kernel within the step are summed (the batched engine launches a ring
+    kernel once per cell-chunk group), one entry per step and kernel."""
+    step = {}
+    for name, t in launches:
+        step[name] = step.get(name, 0.0) + t
+    for name, t in step.items():
+        per.setdefault(name, []).append(t)
+
+
 def timed_steps(torch, stream, step, n, dev, barrier):
     """Device time per step (ms) of n steps on `stream` with CUDA events,
     clocks sampled during the region."""
@@ -374,8 +385,7 @@ def bench_single(args, torch, fb, wname, dev, barrier, e2e_on=True, steps=None):
         ms, clocks = timed_steps(torch, stream, lambda: c.step(want_dt=False), steps, dev, barrier)
         per = {}
         for _ in range(steps):
-            for name, t in c.profile_step():
-                per.setdefault(name, []).append(t)
+            add_step_times(per, c.profile_step())
     _, _, nsteps, err = c.scalars()
     if err:
         raise SystemExit(f"device error {err} during the benchmark")
@@ -431,8 +441,7 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
         ms, clocks = timed_steps(torch, stream, lambda: b.step(sync=False), args.steps, dev, barrier)
         per = {}
         for _ in range(args.steps):
-            for name, t in b.profile_step():
-                per.setdefault(name, []).append(t)
+            add_step_times(per, b.profile_step())
     running, _ = b.status()
     nsteps = [m.scalars()[2] for m in mem]
     roof = roofline_of(per, cells, ALG_FIELDS_2D_ISO, 4, method_fields=METHOD_FIELDS_2D_ISO)

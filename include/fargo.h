@@ -188,7 +188,7 @@ int fargo_set_aux(fargo_ctx *ctx, int which, const void *src, size_t bytes);
 int fargo_profile_step(fargo_ctx *ctx, int max_kernels, float *ms, int *n_out, const char **names);
 
 /* Autotuner of the launch shapes that leave every result unchanged: the
- * azimuths per block of the per-cell source kernels (128, 256, 512) and the
+ * azimuths per block of the per-cell source kernels (64, 128, 256) and the
  * segment lengths of the Y and Z sweeps (16 .. 256 rows).  Each candidate is
  * timed with CUDA events on `reps` (>= 2, the first one warming up) full
  * steps, coordinate by coordinate; the state and time are restored from a
@@ -199,7 +199,7 @@ int fargo_profile_step(fargo_ctx *ctx, int max_kernels, float *ms, int *n_out, c
  * BADARG, OOM, CUDA. */
 int fargo_autotune(fargo_ctx *ctx, int reps, int *cfg);
 
-/* Set those launch shapes directly: cell_bs in {128, 256, 512}; seg_y, seg_z
+/* Set those launch shapes directly: cell_bs in {64, 128, 256}; seg_y, seg_z
  * rows per sweep segment (0 = the default: the whole axis up to 96 rows,
  * else 64). */
 int fargo_set_launch_shape(fargo_ctx *ctx, int cell_bs, int seg_y, int seg_z);

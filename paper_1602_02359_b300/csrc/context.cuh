@@ -74,8 +74,7 @@ struct fargo_ctx {
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
     int launches = 0;
-    size_t tx_smem = 0;
-    int tx_threads = 256;
+    fk::RingShape tx_rs{}, orb_rs{};   // launch shapes of the two ring kernels
     std::vector<double> yfaces_store, zfaces_store;
     fk::SweepMaps mapsY{}, mapsZ{};   // tensor maps of the Y and Z sweeps of the step
     // launch shapes (fargo_autotune): azimuths per block of the per-cell
@@ -178,18 +177,5 @@ static inline dim3 cell_grid_all(const MeshD &m, int bs) { return cell_grid(m, m
 static inline dim3 tau_grid(const MeshD &m, int bs) { return cell_grid(m, tau_rows(m), tau_planes(m), bs); }
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
-
-// Raise (never lower) a kernel's dynamic shared-memory cap: the cap is per
-// function and process-wide, so lowering it for one context would break
-// another context's launches.
-template <typename F>
-static cudaError_t raise_smem_cap(F *func, size_t bytes)
-{
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, func);
-    if (e != cudaSuccess) return e;
-    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
-    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 }  // namespace fk

@@ -359,7 +359,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_y9"); }
     if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_z9"); }
     // cell 12
-    launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_smem, s);
+    launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_rs, s);
     MARK("transport_x");
     if (m.hasY) {
         launch_sweep_tma<T, 1>(m, P.tb, c->mapsY, P.qy, P.sc, P.qx.nq, s, P.seg_y);
@@ -371,7 +371,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     }
     // the uniform orbital step comes last, in place on the state set
     if (m.fargo && m.hasX) {
-        launch_orb<T>(m, P.tb, P.qfin, P.v0, P.sc, P.nrings_active, c->tx_smem, s);
+        launch_orb<T>(m, P.tb, P.qfin, P.v0, P.sc, P.nrings_active, c->orb_rs, s);
         MARK("orbital");
     }
     k_newvel<T><<<cg, cb, 0, s>>>(m, P.tb, P.qfin, P.vsrc, P.A, P.sc, 0); MARK("newvel");
@@ -428,6 +428,15 @@ static int build_sweep_maps(fargo_ctx *c, Buffers<T> &b)
     return FARGO_OK;
 }
 
+template <typename T, int C>
+static int ring_attrs_c(fargo_ctx *c)
+{
+    if (ring_grid<T>(k_transport_x<T, C>, c->tx_rs, c->nyt * c->nzt) != cudaSuccess ||
+        ring_grid<T>(k_orbital<T, C>, c->orb_rs, c->nrings_active) != cudaSuccess)
+        return FARGO_ERR_SIZE;
+    return FARGO_OK;
+}
+
 template <typename T>
 static int set_kernel_attrs(fargo_ctx *c)
 {
@@ -436,21 +445,19 @@ static int set_kernel_attrs(fargo_ctx *c)
     int maxsm = 0;
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
-    // ring kernels stage at most max(nq, 7) rows of one pitch each
-    size_t smem = (size_t)(nq > 7 ? nq : 7) * c->pitch * sizeof(T);
+    const int txrows = 2 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
+    // two ring buffers per CTA (double buffering)
+    c->tx_rs = ring_shape<T>(c->nx, txrows, c->pitch);
+    c->orb_rs = ring_shape<T>(c->nx, nq, c->pitch);
+    const size_t smem = c->tx_rs.smem > c->orb_rs.smem ? c->tx_rs.smem : c->orb_rs.smem;
     if (smem > (size_t)maxsm - 1024 || ring_chunk(c->nx) == 0) return FARGO_ERR_SIZE;
-    c->tx_smem = smem;
-    CK(raise_smem_cap(k_transport_x<T, 1>, smem));
-    CK(raise_smem_cap(k_transport_x<T, 2>, smem));
-    CK(raise_smem_cap(k_transport_x<T, 3>, smem));
-    CK(raise_smem_cap(k_transport_x<T, 4>, smem));
-    CK(raise_smem_cap(k_transport_x<T, 8>, smem));
-    CK(raise_smem_cap(k_orbital<T, 1>, smem));
-    CK(raise_smem_cap(k_orbital<T, 2>, smem));
-    CK(raise_smem_cap(k_orbital<T, 3>, smem));
-    CK(raise_smem_cap(k_orbital<T, 4>, smem));
-    CK(raise_smem_cap(k_orbital<T, 8>, smem));
-    return FARGO_OK;
+    switch (ring_chunk(c->nx)) {
+    case 1: return ring_attrs_c<T, 1>(c);
+    case 2: return ring_attrs_c<T, 2>(c);
+    case 3: return ring_attrs_c<T, 3>(c);
+    case 4: return ring_attrs_c<T, 4>(c);
+    default: return ring_attrs_c<T, 8>(c);
+    }
 }
 
 extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, int ghost, double gamma,
@@ -505,8 +512,14 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     m.indirect = m.has_planet && planet->indirect;
     m.has_star = prm->star_mass > 0.0 && geom != FARGO_CART;
     for (int s = 0; s < 2; s++) { m.bcy[s] = prm->bc_y[s]; m.bcz[s] = prm->bc_z[s]; }
+    if ((long long)(c->nzt + 1) * (c->nyt + 1) * c->pitch >= (1LL << 31)) {
+        // field indices are 32-bit in the kernels
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return FARGO_ERR_SIZE;
+    }
     m.sj = c->pitch;
-    m.sk = (long long)(c->nyt + 1) * c->pitch;
+    m.sk = (c->nyt + 1) * c->pitch;
     m.ntot = (long long)(c->nzt + 1) * m.sk;
     m.gamma = gamma > 0.0 ? gamma : 1.0;
     m.g1 = m.gamma * (m.gamma - 1.0);
@@ -876,7 +889,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         break;
     }
     case 5:
-        launch_tx<T>(m, b.tab, A, qa, c->v0, c->sc, c->tx_smem, s);
+        launch_tx<T>(m, b.tab, A, qa, c->v0, c->sc, c->tx_rs, s);
         break;
     case 6:
     case 7: {
@@ -894,7 +907,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         break;
     case 9:
         if (m.fargo && m.hasX)
-            launch_orb<T>(m, b.tab, qa, c->v0, c->sc, c->nrings_active, c->tx_smem, s);
+            launch_orb<T>(m, b.tab, qa, c->v0, c->sc, c->nrings_active, c->orb_rs, s);
         break;
     default:
         return FARGO_ERR_BADARG;
@@ -1068,11 +1081,12 @@ static int autotune_impl(fargo_ctx *c, Buffers<T> &b, int reps, int *cfg)
     if (rc) return rc;
     const MeshD &m = c->m;
     const char *cell_names[] = {"substep1", "artvisc", "visc_tau", "visc_apply", "newvel"};
-    const int cand_bs[] = {128, 256, 512};
+    // the per-cell kernels are compiled for at most 256 threads per block
+    const int cand_bs[] = {64, 128, 256};
     double best = 1e300;
     int best_bs = c->cell_bs;
     for (int bs : cand_bs) {
-        if (bs > 32 && (m.nx + 31) / 32 * 32 < bs && bs != 128) continue;   // wider than a row
+        if ((m.nx + 31) / 32 * 32 < bs && bs != cand_bs[0]) continue;   // wider than a row
         c->cell_bs = bs;
         double t;
         if ((rc = time_step_kernels<T>(c, b, sn, reps, cell_names, 5, &t))) return rc;
@@ -1130,7 +1144,7 @@ extern "C" int fargo_autotune(fargo_ctx *c, int reps, int *cfg)
 
 extern "C" int fargo_set_launch_shape(fargo_ctx *c, int cell_bs, int seg_y, int seg_z)
 {
-    if (!c || (cell_bs != 128 && cell_bs != 256 && cell_bs != 512) || seg_y < 0 || seg_z < 0)
+    if (!c || (cell_bs != 64 && cell_bs != 128 && cell_bs != 256) || seg_y < 0 || seg_z < 0)
         return FARGO_ERR_BADARG;
     c->cell_bs = cell_bs;
     c->seg_y = seg_y;

@@ -72,8 +72,10 @@ __global__ void __launch_bounds__(256) kb_cfl_exact(const StepPlan<T> *__restric
 // Per-cell phases: a member's cells of the augmented mesh (rows, planes as
 // in the single-instance grid) are numbered row by row, blockDim.x
 // consecutive cells per block, so no block is padded to a row's end.
+// Register budgets: 40 per thread (six 256-thread blocks per SM) for every
+// phase but the viscous update, which gets 48 (five blocks).
 template <typename T, int PH>
-__global__ void __launch_bounds__(256) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
+__global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
     const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
@@ -97,20 +99,92 @@ __global__ void __launch_bounds__(256) kb_cell(const StepPlan<T> *__restrict__ P
     else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, i, j, k);
 }
 
+// Ring operations over the items (member, ring) of a group: the member and
+// local ring of every iteration are found in parallel before the loop.  A
+// member that takes a void step gets a plain arrive instead of copies.
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) kb_tx(const StepPlan<T> *__restrict__ P, Group g)
+struct BTxOp {
+    const StepPlan<T> *P;
+    Group g;
+    RingMeta<T> *meta;
+    __device__ void prepare(int it, int item)
+    {
+        RingMeta<T> &e = meta[it];
+        e.id = group_member(g, item, e.local);
+        const StepPlan<T> &p = P[e.id];
+        e.N = step_dt<T>(p.sc) > T(0) ? 0 : -1;
+        tx_v0(p.m, p.v0, e.local, e.a, e.b);
+    }
+    __device__ void issue(int it, T *dst, uint64_t *bar)
+    {
+        const RingMeta<T> &e = meta[it];
+        if (e.N < 0) {
+            mbar_arrive(bar);
+            return;
+        }
+        const StepPlan<T> &p = P[e.id];
+        tx_issue(p.m, p.txin, e.local, dst, bar);
+    }
+    __device__ void compute(int it, const T *src)
+    {
+        const RingMeta<T> &e = meta[it];
+        if (e.N < 0) return;
+        const StepPlan<T> &p = P[e.id];
+        tx_compute<T, C>(p.m, p.tb, p.qx, e.local, src, e.a, e.b, step_dt<T>(p.sc));
+    }
+    __device__ void fail(int it) { atomicOr(&P[meta[it].id].sc->err, kErrTimeout); }
+};
+
+template <typename T, int C>
+struct BOrbOp {
+    const StepPlan<T> *P;
+    Group g;
+    RingMeta<T> *meta;
+    __device__ void prepare(int it, int item)
+    {
+        RingMeta<T> &e = meta[it];
+        e.id = group_member(g, item, e.local);
+        const StepPlan<T> &p = P[e.id];
+        if (!(step_dt<T>(p.sc) > T(0))) {
+            e.N = -1;
+            return;
+        }
+        orb_prepare(p.m, p.tb, p.v0, p.sc, e.local, e.N, e.a, e.b);
+    }
+    __device__ void issue(int it, T *dst, uint64_t *bar)
+    {
+        const RingMeta<T> &e = meta[it];
+        const StepPlan<T> &p = P[e.id];
+        orb_issue(p.m, p.qfin, e.local, e.N, dst, bar);
+    }
+    __device__ void compute(int it, const T *src)
+    {
+        const RingMeta<T> &e = meta[it];
+        if (e.N < 0) return;
+        const StepPlan<T> &p = P[e.id];
+        orb_compute<T, C>(p.m, p.tb, p.qfin, e.local, src, e.N, e.a, e.b, step_dt<T>(p.sc));
+    }
+    __device__ void fail(int it) { atomicOr(&P[meta[it].id].sc->err, kErrTimeout); }
+};
+
+template <typename T, int C>
+__global__ void __launch_bounds__(512, 2) kb_tx(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems)
 {
-    int local;
-    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
-    transport_x_body<T, C>(p.m, p.tb, p.txin, p.qx, p.v0, p.sc, local);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    ring_bars_init(bar);
+    BTxOp<T, C> op{P, g, ring_meta<T>(smem_raw, stride)};
+    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nitems);
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(512) kb_orb(const StepPlan<T> *__restrict__ P, Group g)
+__global__ void __launch_bounds__(512, 2) kb_orb(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems)
 {
-    int local;
-    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
-    orbital_body<T, C>(p.m, p.tb, p.qfin, p.v0, p.sc, local);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    ring_bars_init(bar);
+    BOrbOp<T, C> op{P, g, ring_meta<T>(smem_raw, stride)};
+    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nitems);
 }
 
 // Tensor maps of every member live in global memory (64-byte aligned).
@@ -171,6 +245,7 @@ struct BLaunch {
     int *d = nullptr;  // device copy: ids, then off
     int threads = 256;
     size_t smem = 0;
+    RingShape rs{};    // ring kernels: threads, values per ring buffer, shared memory, persistent grid
     const char *name = "";
     Group dev() const { return Group{d, d + ids.size(), (int)ids.size()}; }
     int blocks() const { return off.empty() ? 0 : off.back(); }
@@ -238,10 +313,12 @@ template <>
 const Buffers<float> &bufs<float>(const fargo_ctx *c) { return c->b32; }
 
 template <typename T, int C>
-static cudaError_t ring_attrs(size_t smem)
+static cudaError_t ring_attrs(BLaunch &x)
 {
-    cudaError_t e = raise_smem_cap(kb_tx<T, C>, smem);
-    if (e == cudaSuccess) e = raise_smem_cap(kb_orb<T, C>, smem);
+    cudaError_t e;
+    if (x.kind == L_TX) e = ring_grid<T>(kb_tx<T, C>, x.rs, x.blocks());
+    else e = ring_grid<T>(kb_orb<T, C>, x.rs, x.blocks());
+    x.smem = x.rs.smem;
     return e;
 }
 
@@ -338,14 +415,15 @@ static int batch_setup(fargo_batch *b)
     int rc;
     for (BLaunch &x : b->seq) {
         if (x.kind == L_TX || x.kind == L_ORB) {
-            int maxnx = 0;
-            size_t smem = 0;
+            int threads = 0, stride = 0;
             for (int id : x.ids) {
-                maxnx = std::max(maxnx, b->mem[id]->nx);
-                smem = std::max(smem, b->mem[id]->tx_smem);
+                const RingShape &rs = x.kind == L_TX ? b->mem[id]->tx_rs : b->mem[id]->orb_rs;
+                threads = std::max(threads, rs.threads);
+                stride = std::max(stride, rs.stride);
             }
-            x.threads = ((maxnx + x.key - 1) / x.key + 31) / 32 * 32;
-            x.smem = smem;
+            x.rs.threads = x.threads = threads;
+            x.rs.stride = stride;
+            x.rs.smem = x.smem = 2 * (size_t)stride * sizeof(T);
         } else if (x.kind == L_SWEEP) {
             x.threads = TmaTile<T>::TW + 32;
             x.smem = x.arg == 1 ? sweep_tma_smem<T, 1>(x.key) : sweep_tma_smem<T, 2>(x.key);
@@ -357,14 +435,16 @@ static int batch_setup(fargo_batch *b)
                            b->stream));
     }
     // ring kernels: one dynamic shared-memory limit per variant (the largest member)
-    size_t ring_smem[9] = {};
-    for (const BLaunch &x : b->seq)
-        if (x.kind == L_TX || x.kind == L_ORB) ring_smem[x.key] = std::max(ring_smem[x.key], x.smem);
-    if (ring_smem[1]) CK((ring_attrs<T, 1>(ring_smem[1])));
-    if (ring_smem[2]) CK((ring_attrs<T, 2>(ring_smem[2])));
-    if (ring_smem[3]) CK((ring_attrs<T, 3>(ring_smem[3])));
-    if (ring_smem[4]) CK((ring_attrs<T, 4>(ring_smem[4])));
-    if (ring_smem[8]) CK((ring_attrs<T, 8>(ring_smem[8])));
+    for (BLaunch &x : b->seq) {
+        if (x.kind != L_TX && x.kind != L_ORB) continue;
+        switch (x.key) {
+        case 1: CK((ring_attrs<T, 1>(x))); break;
+        case 2: CK((ring_attrs<T, 2>(x))); break;
+        case 3: CK((ring_attrs<T, 3>(x))); break;
+        case 4: CK((ring_attrs<T, 4>(x))); break;
+        default: CK((ring_attrs<T, 8>(x))); break;
+        }
+    }
     for (const BLaunch &x : b->seq)
         if (x.kind == L_SWEEP) CK(x.arg == 1 ? (sweep_attrs<T, 1>(x.key)) : (sweep_attrs<T, 2>(x.key)));
 
@@ -385,22 +465,23 @@ template <typename T>
 static void launch_ring(const BLaunch &x, const StepPlan<T> *P, cudaStream_t s)
 {
     const Group g = x.dev();
-    const unsigned nb = (unsigned)x.blocks();
+    const int n = x.blocks();
+    const RingShape &r = x.rs;
     if (x.kind == L_TX) {
         switch (x.key) {
-        case 1: kb_tx<T, 1><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        case 2: kb_tx<T, 2><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        case 3: kb_tx<T, 3><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        case 4: kb_tx<T, 4><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        default: kb_tx<T, 8><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 1: kb_tx<T, 1><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 2: kb_tx<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 3: kb_tx<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 4: kb_tx<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        default: kb_tx<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         }
     } else {
         switch (x.key) {
-        case 1: kb_orb<T, 1><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        case 2: kb_orb<T, 2><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        case 3: kb_orb<T, 3><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        case 4: kb_orb<T, 4><<<nb, x.threads, x.smem, s>>>(P, g); break;
-        default: kb_orb<T, 8><<<nb, x.threads, x.smem, s>>>(P, g); break;
+        case 1: kb_orb<T, 1><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 2: kb_orb<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 3: kb_orb<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 4: kb_orb<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        default: kb_orb<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         }
     }
 }

@@ -13,7 +13,8 @@ struct MeshD {
     int nx, nyt, nzt, gy, gz, j0, j1, k0, k1, g;
     int hasX, hasY, hasZ, geom, iso, fargo, av_lit, has_nu, has_planet, indirect, has_star, has_av;
     int bcy[2], bcz[2];
-    long long sj, sk, ntot;      // row pitch, plane stride, elements per field
+    int sj, sk;                  // row pitch, plane stride (elements)
+    long long ntot;              // elements per field (below 2^31, checked at creation)
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
 };
 
@@ -92,9 +93,10 @@ __device__ __forceinline__ float sub_split(float v, float hi, float lo)
 }
 __device__ __forceinline__ double sub_split(double v, double hi, double lo) { return v - hi - lo; }
 
-__device__ __forceinline__ long long IX(const MeshD &m, int i, int j, int k)
-{
-    return (long long)k * m.sk + (long long)j * m.sj + i;
-}
+// Element index of cell (i, j, k) in a field array.  32-bit: a context's
+// fields hold fewer than 2^31 elements, so no index overflows and each
+// neighbour address costs one integer multiply-add.
+typedef int idx_t;
+__device__ __forceinline__ idx_t IX(const MeshD &m, int i, int j, int k) { return k * m.sk + j * m.sj + i; }
 
 }  // namespace fk

@@ -13,7 +13,7 @@ namespace fk {
 // mode 1 = cell 9 (skipped when the current step is void).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void fill_line(T *a, long long base, long long stride, int lo, int hi, int g, int normal, int side,
+__device__ void fill_line(T *a, idx_t base, idx_t stride, int lo, int hi, int g, int normal, int side,
                           int bc)
 {
     if (bc == BC_FROZEN) return;
@@ -63,7 +63,7 @@ __device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const
         if (q == 4 && !m.hasZ) continue;
         int kmax = q == 4 ? m.nzt + 1 : m.nzt;
         if (k >= kmax) continue;
-        fill_line(fl[q], (long long)k * m.sk + i, m.sj, m.j0, m.j1, m.g, q == 3, side, bc);
+        fill_line(fl[q], k * m.sk + i, m.sj, m.j0, m.j1, m.g, q == 3, side, bc);
     }
 }
 
@@ -83,7 +83,7 @@ __device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const
         if (q == 3 && !m.hasY) continue;
         int jmax = q == 3 ? m.nyt + 1 : m.nyt;
         if (j >= jmax) continue;
-        fill_line(fl[q], (long long)j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc);
+        fill_line(fl[q], j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc);
     }
 }
 
@@ -180,7 +180,7 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
         const int ny = m.j1 - m.j0;
         const int j = m.j0 + r % ny, k = m.k0 + r / ny;
         const int ring = k * m.nyt + j;
-        const long long base = IX(m, 0, j, k);
+        const idx_t base = IX(m, 0, j, k);
         double v0r = 0.0;
         if (m.fargo) {
             // max and min are exact in the field precision
@@ -203,7 +203,7 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
         const float k4 = (float)tb.k4;
         const bool avon = m.has_av != 0;
         for (int i = lane; i < m.nx; i += 32) {
-            const long long c = base + i;
+            const idx_t c = base + i;
             const int ip = i + 1 == m.nx ? 0 : i + 1;
             const float rho = (float)f.rho[c];
             float cs;
@@ -305,14 +305,14 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
         const int ny = m.j1 - m.j0;
         const int j = m.j0 + r % ny, k = m.k0 + r / ny;
         const int ring = k * m.nyt + j;
-        const long long base = IX(m, 0, j, k);
+        const idx_t base = IX(m, 0, j, k);
         const double v0r = m.fargo ? v0[ring] : 0.0;
         const double lx = tb.lx[ring], ly = tb.ly[ring], lz = tb.lz[ring], dmin = tb.dmin[ring];
         const double nu = m.has_nu ? tb.nud[ring] : 0.0;
         const double r4 = nu > 0.0 ? __ddiv_rn(__dmul_rn(4.0, nu), __dmul_rn(dmin, dmin)) : 0.0;
         const double csr = m.iso ? tb.csd[ring] : 0.0;
         for (int i = lane; i < m.nx; i += 32) {
-            const long long c = base + i;
+            const idx_t c = base + i;
             const int ip = i + 1 == m.nx ? 0 : i + 1;
             const double rho = (double)f.rho[c];
             const double cs = m.iso ? csr : __dsqrt_rn(__ddiv_rn(__dmul_rn(m.g1, (double)f.e[c]), rho));

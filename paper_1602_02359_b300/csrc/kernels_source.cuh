@@ -23,7 +23,7 @@ __device__ __host__ __forceinline__ int tau_planes(const MeshD &m) { return m.k1
 
 // Pressure from the equation of state (Eqs. eos1, eos2).
 template <typename T>
-__device__ __forceinline__ T pressure(const MeshD &m, const Tab<T> &tb, const Fld<T> &f, long long c, int ring)
+__device__ __forceinline__ T pressure(const MeshD &m, const Tab<T> &tb, const Fld<T> &f, idx_t c, int ring)
 {
     if (m.iso) {
         T cs = tb.cs[ring];
@@ -61,7 +61,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    const long long c = IX(m, i, j, k);
+    const idx_t c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
     const T om = tb.omega;
@@ -70,7 +70,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
         if (m.hasX && jact && kact) {
-            const long long cm = c - i + im;
+            const idx_t cm = c - i + im;
             const T id = tb.ilenx[ring];
             const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring);
             T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
@@ -83,7 +83,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     if (k < m.nzt) {
         T v = in.vy[c];
         if (m.hasY && j > m.j0 && j < m.j1 && kact) {
-            const long long cm = c - m.sj;
+            const idx_t cm = c - m.sj;
             const T id = tb.idyc[j];
             const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring - 1);
             T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
@@ -92,7 +92,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
             if (m.has_star) acc -= tb.gphy[ring];
             if (m.geom != CART) {
                 const T Rj = tb.R[ring], Rm = tb.R[ring - 1];
-                const long long cp = c - i + ip, cmp = cm - i + ip;
+                const idx_t cp = c - i + ip, cmp = cm - i + ip;
                 const T vt = T(0.25) * ((in.vx[c] + Rj * om) + (in.vx[cp] + Rj * om) + (in.vx[cm] + Rm * om) +
                                         (in.vx[cmp] + Rm * om));
                 T cen = vt * vt;
@@ -109,7 +109,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     if (m.hasZ && j < m.nyt) {
         T v = in.vz[c];
         if (k > m.k0 && k < m.k1 && jact) {
-            const long long cm = c - m.sk;
+            const idx_t cm = c - m.sk;
             const int rm = ring - m.nyt;
             const T id = tb.idzc[ring];
             const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, rm);
@@ -119,7 +119,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
             if (m.has_star) acc -= tb.gphz[ring];
             if (m.geom == SPH) {
                 const T Rk = tb.R[ring], Rm = tb.R[rm];
-                const long long cp = c - i + ip, cmp = cm - i + ip;
+                const idx_t cp = c - i + ip, cmp = cm - i + ip;
                 const T vt = T(0.25) * ((in.vx[c] + Rk * om) + (in.vx[cp] + Rk * om) + (in.vx[cm] + Rm * om) +
                                         (in.vx[cmp] + Rm * om));
                 acc += vt * vt * tb.cotzf[k] * tb.iym[j];
@@ -153,20 +153,20 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     if (!(dt > T(0))) return;
     const T c2 = tb.cq2;
     const bool av = m.has_av != 0;
-    const long long c = IX(m, i, j, k);
+    const idx_t c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
     const int im = i == 0 ? m.nx - 1 : i - 1;
     const int ip = i + 1 == m.nx ? 0 : i + 1;
     const int ipp = ip + 1 == m.nx ? 0 : ip + 1;
     const T *vx = in.vx, *vy = in.vy, *vz = in.vz, *rho = in.rho;
-    const long long sj = m.sj, sk = m.sk;
+    const idx_t sj = m.sj, sk = m.sk;
     // own lower faces
     T vxl = 0, vyl = 0, vzl = 0;
     if (j < m.nyt && k < m.nzt) {
         T v = vx[c];
         if (av && m.hasX && jact && kact) {
-            const long long cm = c - i + im, cp = c - i + ip;
+            const idx_t cm = c - i + im, cp = c - i + ip;
             const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
             const T qm = qvisc(c2, rho[cm], vx[c] - vx[cm]);
             v -= dt * T(2) * (q0 - qm) * tb.ilenx[ring] / (rho[c] + rho[cm]);
@@ -177,7 +177,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     if (k < m.nzt) {
         T v = vy[c];
         if (av && m.hasY && j > m.j0 && j < m.j1 && kact) {
-            const long long cm = c - sj;
+            const idx_t cm = c - sj;
             const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
             const T qm = qvisc(c2, rho[cm], vy[c] - vy[cm]);
             v -= dt * T(2) * (q0 - qm) * tb.idyc[j] / (rho[c] + rho[cm]);
@@ -188,7 +188,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     if (m.hasZ && j < m.nyt) {
         T v = vz[c];
         if (av && k > m.k0 && k < m.k1 && jact) {
-            const long long cm = c - sk;
+            const idx_t cm = c - sk;
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
             const T qm = qvisc(c2, rho[cm], vz[c] - vz[cm]);
             v -= dt * T(2) * (q0 - qm) * tb.idzc[ring] / (rho[c] + rho[cm]);
@@ -218,7 +218,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     // post-viscosity velocities on the upper faces (owned by the neighbours)
     T div = 0;
     if (m.hasX) {
-        const long long cp = c - i + ip, cpp = c - i + ipp;
+        const idx_t cp = c - i + ip, cpp = c - i + ipp;
         T vxu = vx[cp];
         if (av) {
             const T qp = qvisc(c2, rho[cp], vx[cpp] - vx[cp]);
@@ -266,12 +266,12 @@ struct ViscCtx {
     __device__ ViscCtx(const MeshD &m_, const Tab<T> &tb_, const Fld<T> &f)
         : m(m_), tb(tb_), rho(f.rho), vx(f.vx), vy(f.vy), vz(f.vz) {}
     __device__ int wrap(int i) const { return i < 0 ? i + m.nx : (i >= m.nx ? i - m.nx : i); }
-    __device__ long long at(int i, int j, int k) const { return IX(m, wrap(i), j, k); }
+    __device__ idx_t at(int i, int j, int k) const { return IX(m, wrap(i), j, k); }
     __device__ T nu(int j, int k) const { return tb.nu[k * m.nyt + j]; }
 
     __device__ T divv(int i, int j, int k) const
     {
-        const long long c = at(i, j, k);
+        const idx_t c = at(i, j, k);
         const int ring = k * m.nyt + j, fr = k * (m.nyt + 1) + j;
         T f = 0;
         if (m.hasX) f += tb.sx[ring] * (vx[at(i + 1, j, k)] - vx[c]);
@@ -282,7 +282,7 @@ struct ViscCtx {
     // diagonal components at the centre of cell (i,j,k)
     __device__ void diag(int i, int j, int k, T &txx, T &tyy, T &tzz) const
     {
-        const long long c = at(i, j, k);
+        const idx_t c = at(i, j, k);
         const int ring = k * m.nyt + j;
         const T dv = divv(i, j, k);
         const T rn = rho[c] * nu(j, k);
@@ -312,7 +312,7 @@ struct ViscCtx {
     // tau_xy on the edge (i-1/2, j-1/2, k)
     __device__ T txy(int i, int j, int k) const
     {
-        const long long c = at(i, j, k), cm = at(i - 1, j, k);
+        const idx_t c = at(i, j, k), cm = at(i - 1, j, k);
         const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sj] + rho[cm - m.sj]);
         const T nb = T(0.5) * (nu(j, k) + nu(j - 1, k));
         const T dvx_dy = (vx[c] - vx[c - m.sj]) * tb.idyc[j];
@@ -331,7 +331,7 @@ struct ViscCtx {
     // tau_xz on the edge (i-1/2, j, k-1/2)
     __device__ T txz(int i, int j, int k) const
     {
-        const long long c = at(i, j, k), cm = at(i - 1, j, k);
+        const idx_t c = at(i, j, k), cm = at(i - 1, j, k);
         const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sk] + rho[cm - m.sk]);
         const T nb = T(0.5) * (nu(j, k) + nu(j, k - 1));
         const T idzm = tb.idzm[k];
@@ -350,7 +350,7 @@ struct ViscCtx {
     // tau_yz on the edge (i, j-1/2, k-1/2)
     __device__ T tyz(int i, int j, int k) const
     {
-        const long long c = at(i, j, k);
+        const idx_t c = at(i, j, k);
         const T rb = T(0.25) * (rho[c] + rho[c - m.sj] + rho[c - m.sk] + rho[c - m.sj - m.sk]);
         const T nb = T(0.25) * (nu(j, k) + nu(j - 1, k) + nu(j, k - 1) + nu(j - 1, k - 1));
         const T idzm = tb.idzm[k];
@@ -370,14 +370,14 @@ template <typename T, typename S>
 __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
                                            T dt, int i, int j, int k, const S &V)
 {
-    const long long c = IX(m, i, j, k);
+    const idx_t c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const T idx = tb.idx;
     const T *rho = in.rho;
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
         if (jact && kact) {
-            const long long cm = V.at(i - 1, j, k);
+            const idx_t cm = V.at(i - 1, j, k);
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i - 1, j, k, b0, b1, b2);
@@ -417,7 +417,7 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
     if (k < m.nzt) {
         T v = in.vy[c];
         if (m.hasY && j > m.j0 && j < m.j1 && kact) {
-            const long long cjm = c - m.sj;
+            const idx_t cjm = c - m.sj;
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i, j - 1, k, b0, b1, b2);
@@ -447,7 +447,7 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
     if (m.hasZ && j < m.nyt) {
         T v = in.vz[c];
         if (k > m.k0 && k < m.k1 && jact) {
-            const long long ckm = c - m.sk;
+            const idx_t ckm = c - m.sk;
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i, j, k - 1, b0, b1, b2);
@@ -483,13 +483,13 @@ template <typename T>
 struct TauArr {
     const MeshD &m;
     const T *xx, *yy, *zz, *xy, *xz, *yz;
-    __device__ long long at(int i, int j, int k) const
+    __device__ idx_t at(int i, int j, int k) const
     {
         return IX(m, i < 0 ? i + m.nx : (i >= m.nx ? i - m.nx : i), j, k);
     }
     __device__ void diag(int i, int j, int k, T &a, T &b, T &c) const
     {
-        const long long o = at(i, j, k);
+        const idx_t o = at(i, j, k);
         a = xx[o];
         b = yy[o];
         c = m.hasZ ? zz[o] : T(0);
@@ -511,7 +511,7 @@ __device__ __forceinline__ void visc_tau_body(const MeshD &m, const Tab<T> &tb, 
     // rows j0..j1, planes k0..k1 (the upper one only with that direction)
     if (j < m.j0 || j > m.j1 - (m.hasY ? 0 : 1) || k < m.k0 || k > m.k1 - (m.hasZ ? 0 : 1)) return;
     const ViscCtx<T> V(m, tb, in);
-    const long long c = IX(m, i, j, k);
+    const idx_t c = IX(m, i, j, k);
     const bool jin = j < m.j1, kin = k < m.k1;
     if (jin && kin) {
         T a, b, d;

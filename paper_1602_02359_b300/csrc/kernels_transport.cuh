@@ -70,33 +70,85 @@ __device__ __forceinline__ T ppa_face(const T a[5], T xi, bool pos)
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // ---------------------------------------------------------------------------
-// Ring kernels.  One CTA per ring (j,k); the ring's quantities are staged in
-// shared memory and every thread owns C consecutive cells.  For each
-// quantity a thread rebuilds, in registers, the ratios to the density of its
-// cells and their stencil halo, the slopes, the interface values and the
-// fluxes through its C+1 faces, and writes its C updated cells straight to
-// global memory; the only barriers are after the staging.  Consistent
-// transport: quantity q > 0 moves with the mass flux times the interface
-// ratio, all fluxes from the pre-sweep ring.
+// Ring kernels.  Persistent CTAs walk the rings (j,k) with a stride of the
+// grid and keep two ring buffers in shared memory: while the threads
+// compute ring r from one buffer, thread 0 has already issued the 1D bulk
+// copies (cp.async.bulk, completed on that buffer's mbarrier) of the CTA's
+// next ring into the other, so the staging latency hides behind compute.
+// Every thread owns C consecutive cells of a ring.  For each quantity it
+// rebuilds, in registers, the ratios to the density of its cells and their
+// stencil halo, the slopes, the interface values and the fluxes through its
+// C+1 faces, and writes its C updated cells straight to global memory.
+// Consistent transport: quantity q > 0 moves with the mass flux times the
+// interface ratio, all fluxes from the pre-sweep ring.
 // ---------------------------------------------------------------------------
 
-// Stage rows of one ring into shared memory with 1D bulk copies issued by
-// thread 0 and completed on `bar` (rows are pitch-aligned: 128-byte
-// boundaries, sizes rounded up to 16 bytes within the row padding).  All
-// threads then wait, bounded; returns false on timeout.
+// Bytes of one staged row: nx values rounded up to 16 bytes (rows are
+// pitch-aligned, 128-byte boundaries, so the rounding stays in the padding).
 template <typename T>
-__device__ __forceinline__ bool stage_rows(T *dst, int rowlen, const T *const *src, int nrow, int nx,
-                                           uint64_t *bar)
+__device__ __forceinline__ unsigned row_bytes(int nx)
 {
-    const unsigned bytes = (unsigned)(((size_t)nx * sizeof(T) + 15) / 16 * 16);
+    return (unsigned)(((size_t)nx * sizeof(T) + 15) / 16 * 16);
+}
+
+// Per-iteration facts of a ring, computed by all threads in parallel before
+// the loop (so no FP64 division or member search sits on the loop's
+// critical path): the member and local ring (batched launches), the integer
+// shift (orbital step, -1: nothing to do) and two values in the field
+// precision (v0 split hi/lo for the X sweep; xi and the fractional
+// velocity for the orbital step).
+template <typename T>
+struct RingMeta {
+    int id, local, N;
+    T a, b;
+};
+
+// Persistent double-buffered loop over items first, first+step, ... < n.
+// Op provides prepare(it, item) (any thread: fill meta[it]), issue(it, dst,
+// bar) (thread 0 only: start the copies of iteration it into dst completed
+// on bar, or a plain arrive when it needs no data), compute(it, src) (all
+// threads) and fail(it).  bar[0..1] are initialised by the caller with an
+// arrival count of one.  Every wait is bounded and the decision to stop is
+// block-uniform; on timeout the error is recorded and the copies still in
+// flight land before the CTA exits.
+template <typename T, class Op>
+__device__ __forceinline__ void ring_pipeline(Op &op, T *buf, size_t stride, uint64_t *bar, int first, int step,
+                                              int n)
+{
+    if (first >= n) return;
+    const int K = (n - first + step - 1) / step;
+    for (int it = threadIdx.x; it < K; it += blockDim.x) op.prepare(it, first + it * step);
+    __syncthreads();
+    if (threadIdx.x == 0) op.issue(0, buf, &bar[0]);
+    unsigned uses[2] = {0u, 0u};
+    for (int it = 0; it < K; it++) {
+        const int b = it & 1;
+        if (threadIdx.x == 0 && it + 1 < K) op.issue(it + 1, buf + (size_t)(1 - b) * stride, &bar[1 - b]);
+        const bool ok = __syncthreads_and(mbar_wait(&bar[b], uses[b] & 1u));
+        uses[b]++;
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                op.fail(it);
+                if (it + 1 < K) mbar_wait(&bar[1 - b], uses[1 - b] & 1u);
+            }
+            return;
+        }
+        op.compute(it, buf + (size_t)b * stride);
+        __syncthreads();
+    }
+}
+
+// Iterations of one persistent CTA (the metadata entries it needs).
+__host__ __device__ __forceinline__ int ring_iters(int n, int grid) { return (n + grid - 1) / grid; }
+
+__device__ __forceinline__ void ring_bars_init(uint64_t *bar)
+{
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_barrier_init();
-        mbar_expect_tx(bar, bytes * (unsigned)nrow);
-        for (int r = 0; r < nrow; r++) bulk_load(dst + (size_t)r * rowlen, src[r], bytes, bar);
     }
     __syncthreads();
-    return mbar_wait(bar, 0);
 }
 
 // X sweep, residual part (Sec. 3.4.1, Eq. fargo1; Eq. 15 with van Leer
@@ -107,43 +159,74 @@ __device__ __forceinline__ bool stage_rows(T *dst, int rowlen, const T *const *s
 // R v_x + R^2 Omega_f, Pi+_y / rho = v_y of the upper face, ...).  The face
 // velocity is delta v = v_x - v0 (v0 = 0 for STANDARD transport).  Ghost
 // rings only get their momenta written (the Y/Z sweeps read them).
-template <typename T, int C>
-__device__ __forceinline__ void transport_x_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in,
-                                                 const QSet<T> &out, const double *v0, Scal *sc, int ring)
+struct TxRows {
+    int n, rE, rVX, rVY, rVZ;   // staged rows: rho, e, vx, vy(j), vy(j+1), vz(k), vz(k+1)
+};
+__device__ __forceinline__ TxRows tx_rows(const MeshD &m)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ T s_v0[2];
-    const T dt = step_dt<T>(sc);
-    if (!(dt > T(0))) return;
+    TxRows r{0, -1, -1, -1, -1};
+    r.n = 1;
+    if (!m.iso) r.rE = r.n++;
+    r.rVX = r.n++;
+    if (m.hasY) {
+        r.rVY = r.n;
+        r.n += 2;
+    }
+    if (m.hasZ) {
+        r.rVZ = r.n;
+        r.n += 2;
+    }
+    return r;
+}
+
+// v0 of ring `ring` split as hi + lo in the field precision (0 off the
+// active rings and for STANDARD transport).
+template <typename T>
+__device__ __forceinline__ void tx_v0(const MeshD &m, const double *v0, int ring, T &hi, T &lo)
+{
+    const int j = ring % m.nyt, k = ring / m.nyt;
+    const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
+    const double v0r = m.fargo && active && m.hasX ? v0[ring] : 0.0;
+    hi = (T)v0r;
+    lo = (T)(v0r - (double)hi);
+}
+
+// Thread 0: copies of ring `ring` of the X sweep's input into dst.
+template <typename T>
+__device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int ring, T *dst, uint64_t *bar)
+{
+    const TxRows r = tx_rows(m);
+    const int j = ring % m.nyt, k = ring / m.nyt;
+    const idx_t base = IX(m, 0, j, k);
+    const size_t pitch = (size_t)m.sj;
+    const unsigned bytes = row_bytes<T>(m.nx);
+    mbar_expect_tx(bar, bytes * (unsigned)r.n);
+    bulk_load(dst, in.rho + base, bytes, bar);
+    if (r.rE >= 0) bulk_load(dst + r.rE * pitch, in.e + base, bytes, bar);
+    bulk_load(dst + r.rVX * pitch, in.vx + base, bytes, bar);
+    if (r.rVY >= 0) {
+        bulk_load(dst + r.rVY * pitch, in.vy + base, bytes, bar);
+        bulk_load(dst + (r.rVY + 1) * pitch, in.vy + base + m.sj, bytes, bar);
+    }
+    if (r.rVZ >= 0) {
+        bulk_load(dst + r.rVZ * pitch, in.vz + base, bytes, bar);
+        bulk_load(dst + (r.rVZ + 1) * pitch, in.vz + base + m.sk, bytes, bar);
+    }
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &out, int ring,
+                                           const T *sm, T v0hi, T v0lo, T dt)
+{
     const int nx = m.nx, nq = out.nq, pitch = (int)m.sj;
     const int j = ring % m.nyt, k = ring / m.nyt;
     const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
-    const long long base = IX(m, 0, j, k);
+    const idx_t base = IX(m, 0, j, k);
     const bool adi = !m.iso;
     const bool sweep = active && m.hasX;
-    // staged rows: 0 rho, 1 e, 2 vx, 3 vy(j), 4 vy(j+1), 5 vz(k), 6 vz(k+1)
-    const T *src[7];
-    int nrow = 0;
-    int rE = -1, rVY = -1, rVZ = -1;
-    src[nrow++] = in.rho + base;
-    if (adi) { rE = nrow; src[nrow++] = in.e + base; }
-    const int rVX = nrow;
-    src[nrow++] = in.vx + base;
-    if (m.hasY) { rVY = nrow; src[nrow++] = in.vy + base; src[nrow++] = in.vy + base + m.sj; }
-    if (m.hasZ) { rVZ = nrow; src[nrow++] = in.vz + base; src[nrow++] = in.vz + base + m.sk; }
-    if (threadIdx.x == 0) {
-        const double v0r = m.fargo && sweep ? v0[ring] : 0.0;
-        s_v0[0] = (T)v0r;
-        s_v0[1] = (T)(v0r - (double)s_v0[0]);
-    }
-    if (!stage_rows(sm, pitch, src, nrow, nx, &bar)) {
-        if (threadIdx.x == 0) atomicOr(&sc->err, kErrTimeout);
-        return;
-    }
+    const TxRows rw = tx_rows(m);
     const T R = tb.R[ring], w = R * R * tb.omega, fz = tb.fz[ring];
-    const T *Rho = sm, *Vx = sm + (size_t)rVX * pitch;
+    const T *Rho = sm, *Vx = sm + (size_t)rw.rVX * pitch;
     // ratio of quantity q to the density at cell i, as scale * row[i + off] +
     // shift (or e / rho), for the order rho, e, Pi-x, Pi+x, Pi-y, Pi+y,
     // Pi-z, Pi+z of the present components
@@ -156,18 +239,18 @@ __device__ __forceinline__ void transport_x_body(const MeshD &m, const Tab<T> &t
         if (q == 0) return {Rho, 0, 0, T(1), T(0)};
         int o = q - 1;
         if (adi) {
-            if (o == 0) return {sm + (size_t)rE * pitch, 0, 1, T(1), T(0)};
+            if (o == 0) return {sm + (size_t)rw.rE * pitch, 0, 1, T(1), T(0)};
             o -= 1;
         }
         if (o == 0) return {Vx, 0, 0, R, w};
         if (o == 1) return {Vx, 1, 0, R, w};
         if (m.hasY) {
-            if (o == 2) return {sm + (size_t)rVY * pitch, 0, 0, T(1), T(0)};
-            if (o == 3) return {sm + (size_t)(rVY + 1) * pitch, 0, 0, T(1), T(0)};
+            if (o == 2) return {sm + (size_t)rw.rVY * pitch, 0, 0, T(1), T(0)};
+            if (o == 3) return {sm + (size_t)(rw.rVY + 1) * pitch, 0, 0, T(1), T(0)};
             o -= 2;
         }
-        if (o == 2) return {sm + (size_t)rVZ * pitch, 0, 0, fz, T(0)};
-        return {sm + (size_t)(rVZ + 1) * pitch, 0, 0, fz, T(0)};
+        if (o == 2) return {sm + (size_t)rw.rVZ * pitch, 0, 0, fz, T(0)};
+        return {sm + (size_t)(rw.rVZ + 1) * pitch, 0, 0, fz, T(0)};
     };
     if (!sweep) {
         for (int q = 0; q < nq; q++) {
@@ -179,7 +262,6 @@ __device__ __forceinline__ void transport_x_body(const MeshD &m, const Tab<T> &t
         }
         return;
     }
-    const T v0hi = s_v0[0], v0lo = s_v0[1];
     const T dX = tb.lenx[ring], S = tb.sx[ring];
     const T idX = T(1) / dX;
     const T dtVi = dt * tb.vinv[ring];
@@ -228,42 +310,85 @@ __device__ __forceinline__ void transport_x_body(const MeshD &m, const Tab<T> &t
 //  (iii) fractional step at xi = v0 dt/dX - N with PPA interface values
 //        (Eqs. 34-36 and the xi-weighted value of Sec. 3.4.1), consistent
 //        transport, in the same pass.
-// N and xi are FP64 (round-to-nearest intrinsics), once per CTA.
-template <typename T, int C>
-__device__ __forceinline__ void orbital_body(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0,
-                                             Scal *sc, int r)
+// N and xi are FP64 (round-to-nearest intrinsics), once per ring by thread 0
+// when it issues the ring's copies; a ring with N = 0 and xi = 0 is skipped.
+// Shift N (modulo nx; -1 when the ring needs no work), xi in the field
+// precision and the fractional velocity xi dX / dt of active ring r.
+template <typename T>
+__device__ __forceinline__ void orb_prepare(const MeshD &m, const Tab<T> &tb, const double *v0, const Scal *sc,
+                                            int r, int &Nm, T &xs, T &vR)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_N;
-    __shared__ T s_x[2];
-    const T dtT = step_dt<T>(sc);
-    if (!(dtT > T(0))) return;
+    const int nx = m.nx, ny = m.j1 - m.j0;
+    const int j = m.j0 + r % ny, k = m.k0 + r / ny;
+    const int ring = k * m.nyt + j;
+    const double dtd = sc->dt;
+    const double X = __ddiv_rn(__dmul_rn(v0[ring], dtd), tb.lx[ring]);
+    const long long N = llround(X);
+    const double x = __dsub_rn(X, (double)N);
+    Nm = (int)(((N % nx) + nx) % nx);
+    xs = (T)x;
+    vR = (T)(x * tb.lx[ring] / dtd);
+    if (Nm == 0 && xs == T(0)) Nm = -1;
+}
+
+// Thread 0: copies of the nq rows of active ring r into dst, or a plain
+// arrive when the ring needs no work (Nm < 0).
+template <typename T>
+__device__ __forceinline__ void orb_issue(const MeshD &m, const QSet<T> &qs, int r, int Nm, T *dst, uint64_t *bar)
+{
+    if (Nm < 0) {
+        mbar_arrive(bar);
+        return;
+    }
+    const int ny = m.j1 - m.j0;
+    const int j = m.j0 + r % ny, k = m.k0 + r / ny;
+    const idx_t base = IX(m, 0, j, k);
+    const unsigned bytes = row_bytes<T>(m.nx);
+    mbar_expect_tx(bar, bytes * (unsigned)qs.nq);
+    for (int q = 0; q < qs.nq; q++) bulk_load(dst + (size_t)q * m.sj, qs.q[q] + base, bytes, bar);
+}
+
+// Upwind PPA value through each of a thread's C+1 faces (Sec. 3.4.1, Eqs.
+// 34-36 and the xi-weighted value): for xi >= 0 (POS) the donor of face u
+// is the cell left of it, else the cell right of it.  a holds the ratios of
+// cells i0-3 .. i0+C+2, qr the right interface values of cells i0-2 ..
+// i0+C.  The donor offset is a template constant, so every array index is a
+// compile-time constant and the arrays stay in registers.
+template <typename T, int C, bool POS>
+__device__ __forceinline__ void ppa_face_values(const T *a, const T *qr, T xi, T *stv)
+{
+    const T sixth = T(1.0 / 6.0);
+#pragma unroll
+    for (int u = 0; u <= C; u++) {
+        // donor cell d = i0+u-1 (POS) or i0+u; its value a[d-(i0-3)], its
+        // left value qr[d-1-(i0-2)], its right value qr[d-(i0-2)]
+        constexpr int sh = POS ? -1 : 0;
+        const int dd = u + sh;
+        const T q0 = a[dd + 3], qm = a[dd + 2], qp = a[dd + 4];
+        T l = qr[dd + 1], rr = qr[dd + 2];
+        if ((qp - q0) * (q0 - qm) <= T(0)) {
+            l = q0;
+            rr = q0;
+        } else {
+            const T D = rr - l, Cc = q0 - T(0.5) * (l + rr);
+            if (D * Cc > D * D * sixth) l = T(3) * q0 - T(2) * rr;
+            else if (-D * D * sixth > D * Cc) rr = T(3) * q0 - T(2) * l;
+        }
+        const T wgt = xi * (T(1) - xi) * (T(2) * q0 - rr - l);
+        stv[u] = POS ? rr + xi * (q0 - rr) + wgt : l + xi * (q0 - l) + wgt;
+    }
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, int r,
+                                            const T *sm, int Nm, T xsT, T vR, T dtT)
+{
+    if (Nm < 0) return;
     const int nx = m.nx, nq = qs.nq, pitch = (int)m.sj;
     const int ny = m.j1 - m.j0;
     const int j = m.j0 + r % ny, k = m.k0 + r / ny;
     const int ring = k * m.nyt + j;
-    const long long base = IX(m, 0, j, k);
-    if (threadIdx.x == 0) {
-        const double dtd = sc->dt;
-        const double X = __ddiv_rn(__dmul_rn(v0[ring], dtd), tb.lx[ring]);
-        const long long N = llround(X);
-        const double xs = __dsub_rn(X, (double)N);
-        s_N = (int)(((N % nx) + nx) % nx);
-        s_x[0] = (T)xs;
-        s_x[1] = (T)(xs * tb.lx[ring] / dtd);
-    }
-    __syncthreads();
-    const int Nm = s_N;
-    const T xsT = s_x[0];
-    if (Nm == 0 && xsT == T(0)) return;
-    const T *src[8];
-    for (int q = 0; q < nq; q++) src[q] = qs.q[q] + base;
-    if (!stage_rows(sm, pitch, src, nq, nx, &bar)) {
-        if (threadIdx.x == 0) atomicOr(&sc->err, kErrTimeout);
-        return;
-    }
+    const idx_t base = IX(m, 0, j, k);
     // cell i after the shift holds the staged cell i - N
     auto at = [&](int q, int i) -> T { return sm[(size_t)q * pitch + wrapi(i - Nm, nx)]; };
     if (xsT == T(0)) {   // a pure shift
@@ -276,7 +401,6 @@ __device__ __forceinline__ void orbital_body(const MeshD &m, const Tab<T> &tb, c
     const int cnt = min(C, nx - i0);
     const T S = tb.sx[ring];
     const T dtVi = dtT * tb.vinv[ring];
-    const T vR = s_x[1];
     const bool pos = xsT >= T(0);
     const T xi = pos ? xsT : -xsT;
     const T sixth = T(1.0 / 6.0);
@@ -297,26 +421,14 @@ __device__ __forceinline__ void orbital_body(const MeshD &m, const Tab<T> &tb, c
         T qr[C + 3];  // Eq. 35 right interface value of cells i0-2 .. i0+C
 #pragma unroll
         for (int s = 0; s < C + 3; s++) qr[s] = a[s + 1] + T(0.5) * (a[s + 2] - a[s + 1]) - (dm[s + 1] - dm[s]) * sixth;
+        T stv[C + 1];
+        if (pos) ppa_face_values<T, C, true>(a, qr, xi, stv);
+        else ppa_face_values<T, C, false>(a, qr, xi, stv);
         T F[C + 1];
 #pragma unroll
         for (int u = 0; u <= C; u++) {
-            // donor cell d = i0+u-1 (xi >= 0) or i0+u; its value a[d-(i0-3)],
-            // its left value qr[d-1-(i0-2)], its right value qr[d-(i0-2)]
-            const int dd = pos ? u - 1 : u;
-            const T q0 = a[dd + 3], qm = a[dd + 2], qp = a[dd + 4];
-            T l = qr[dd + 1], rr = qr[dd + 2];
-            if ((qp - q0) * (q0 - qm) <= T(0)) {
-                l = q0;
-                rr = q0;
-            } else {
-                const T D = rr - l, Cc = q0 - T(0.5) * (l + rr);
-                if (D * Cc > D * D * sixth) l = T(3) * q0 - T(2) * rr;
-                else if (-D * D * sixth > D * Cc) rr = T(3) * q0 - T(2) * l;
-            }
-            const T wgt = xi * (T(1) - xi) * (T(2) * q0 - rr - l);
-            const T stv = pos ? rr + xi * (q0 - rr) + wgt : l + xi * (q0 - l) + wgt;
-            if (q == 0) F0[u] = vR * stv * S;
-            F[u] = q == 0 ? F0[u] : F0[u] * stv;
+            if (q == 0) F0[u] = vR * stv[u] * S;
+            F[u] = q == 0 ? F0[u] : F0[u] * stv[u];
         }
 #pragma unroll
         for (int u = 0; u < C; u++)
@@ -324,31 +436,88 @@ __device__ __forceinline__ void orbital_body(const MeshD &m, const Tab<T> &tb, c
     }
 }
 
+// Single-instance ring operations for ring_pipeline (meta: the per-iteration
+// table in shared memory).
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
-                                                     Scal *sc)
-{
-    transport_x_body<T, C>(m, tb, in, out, v0, sc, blockIdx.x);
-}
+struct TxOp {
+    const MeshD &m;
+    const Tab<T> &tb;
+    const Fld<T> &in;
+    const QSet<T> &out;
+    const double *v0;
+    Scal *sc;
+    T dt;
+    RingMeta<T> *meta;
+    __device__ void prepare(int it, int ring)
+    {
+        meta[it].local = ring;
+        tx_v0(m, v0, ring, meta[it].a, meta[it].b);
+    }
+    __device__ void issue(int it, T *dst, uint64_t *bar) { tx_issue(m, in, meta[it].local, dst, bar); }
+    __device__ void compute(int it, const T *src)
+    {
+        tx_compute<T, C>(m, tb, out, meta[it].local, src, meta[it].a, meta[it].b, dt);
+    }
+    __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
+};
+
 template <typename T, int C>
-__global__ void __launch_bounds__(512) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, Scal *sc)
+struct OrbOp {
+    const MeshD &m;
+    const Tab<T> &tb;
+    const QSet<T> &qs;
+    const double *v0;
+    Scal *sc;
+    T dt;
+    RingMeta<T> *meta;
+    __device__ void prepare(int it, int r)
+    {
+        meta[it].local = r;
+        orb_prepare(m, tb, v0, sc, r, meta[it].N, meta[it].a, meta[it].b);
+    }
+    __device__ void issue(int it, T *dst, uint64_t *bar) { orb_issue(m, qs, meta[it].local, meta[it].N, dst, bar); }
+    __device__ void compute(int it, const T *src)
+    {
+        const RingMeta<T> &e = meta[it];
+        orb_compute<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
+    }
+    __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
+};
+
+// stride: values per ring buffer (two buffers in the dynamic shared memory)
+// Dynamic shared memory of a ring kernel: two ring buffers of `stride`
+// values, then the per-iteration table.
+template <typename T>
+__device__ __forceinline__ RingMeta<T> *ring_meta(unsigned char *smem, int stride)
 {
-    orbital_body<T, C>(m, tb, qs, v0, sc, blockIdx.x);
+    return reinterpret_cast<RingMeta<T> *>(smem + 2 * (size_t)stride * sizeof(T));
 }
 
 template <typename T, int C>
-static void launch_tx_c(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
-                        Scal *sc, size_t smem, cudaStream_t s)
+__global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
+                                                     Scal *sc, int stride)
 {
-    const int threads = ((m.nx + C - 1) / C + 31) / 32 * 32;
-    k_transport_x<T, C><<<m.nyt * m.nzt, threads, smem, s>>>(m, tb, in, out, v0, sc);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
+    ring_bars_init(bar);
+    TxOp<T, C> op{m, tb, in, out, v0, sc, dt, ring_meta<T>(smem_raw, stride)};
+    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x,
+                     m.nyt * m.nzt);
 }
+
 template <typename T, int C>
-static void launch_orb_c(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, Scal *sc,
-                         int nrings, size_t smem, cudaStream_t s)
+__global__ void __launch_bounds__(512, 2) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, Scal *sc,
+                                                 int nrings, int stride)
 {
-    const int threads = ((m.nx + C - 1) / C + 31) / 32 * 32;
-    k_orbital<T, C><<<nrings, threads, smem, s>>>(m, tb, qs, v0, sc);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const T dt = step_dt<T>(sc);
+    if (!(dt > T(0))) return;
+    ring_bars_init(bar);
+    OrbOp<T, C> op{m, tb, qs, v0, sc, dt, ring_meta<T>(smem_raw, stride)};
+    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nrings);
 }
 
 // Cells per thread of the ring kernels: the smallest of 1, 2, 3, 4, 8 that
@@ -361,28 +530,108 @@ static inline int ring_chunk(int nx)
     return 0;
 }
 
+// Launch shape of a ring kernel: threads per CTA, values per ring buffer,
+// dynamic shared memory (two buffers) and the persistent grid.
+struct RingShape {
+    int threads, stride, grid;
+    size_t smem;
+};
+
+template <typename T, int C>
+static void launch_tx_c(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
+                        Scal *sc, const RingShape &rs, cudaStream_t s)
+{
+    k_transport_x<T, C><<<rs.grid, rs.threads, rs.smem, s>>>(m, tb, in, out, v0, sc, rs.stride);
+}
+template <typename T, int C>
+static void launch_orb_c(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, Scal *sc,
+                         int nrings, const RingShape &rs, cudaStream_t s)
+{
+    k_orbital<T, C><<<rs.grid, rs.threads, rs.smem, s>>>(m, tb, qs, v0, sc, nrings, rs.stride);
+}
+
 template <typename T>
 static void launch_tx(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
-                      Scal *sc, size_t smem, cudaStream_t s)
+                      Scal *sc, const RingShape &rs, cudaStream_t s)
 {
     switch (ring_chunk(m.nx)) {
-    case 1: launch_tx_c<T, 1>(m, tb, in, out, v0, sc, smem, s); break;
-    case 2: launch_tx_c<T, 2>(m, tb, in, out, v0, sc, smem, s); break;
-    case 3: launch_tx_c<T, 3>(m, tb, in, out, v0, sc, smem, s); break;
-    case 4: launch_tx_c<T, 4>(m, tb, in, out, v0, sc, smem, s); break;
-    default: launch_tx_c<T, 8>(m, tb, in, out, v0, sc, smem, s); break;
+    case 1: launch_tx_c<T, 1>(m, tb, in, out, v0, sc, rs, s); break;
+    case 2: launch_tx_c<T, 2>(m, tb, in, out, v0, sc, rs, s); break;
+    case 3: launch_tx_c<T, 3>(m, tb, in, out, v0, sc, rs, s); break;
+    case 4: launch_tx_c<T, 4>(m, tb, in, out, v0, sc, rs, s); break;
+    default: launch_tx_c<T, 8>(m, tb, in, out, v0, sc, rs, s); break;
     }
 }
+// Threads, buffer stride and shared memory of a ring kernel for rings of up
+// to nx cells staged as `rows` rows of `pitch` values; the persistent grid is
+// filled in by ring_grid.
+template <typename T>
+static RingShape ring_shape(int nx, int rows, int pitch)
+{
+    RingShape rs{};
+    const int C = ring_chunk(nx);
+    rs.threads = C ? ((nx + C - 1) / C + 31) / 32 * 32 : 0;
+    rs.stride = rows * pitch;
+    rs.smem = 2 * (size_t)rs.stride * sizeof(T);
+    return rs;
+}
+
+// Raise (never lower) a kernel's dynamic shared-memory cap: the cap is per
+// function and process-wide, so lowering it for one context would break
+// another context's launches.
+template <typename F>
+static cudaError_t raise_smem_cap(F *func, size_t bytes)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Persistent grid of a ring kernel: the CTAs resident on the whole GPU, at
+// most one per item.  The dynamic shared memory is the two ring buffers
+// plus the per-iteration table, whose length depends on the grid, so the
+// grid and the memory are settled together (the memory only grows as the
+// grid shrinks).  The kernel's shared-memory cap is raised accordingly.
+template <typename T, typename K>
+static cudaError_t ring_grid(K *kernel, RingShape &rs, int nitems)
+{
+    int dev = 0, sms = 0, maxsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const size_t bufs = 2 * (size_t)rs.stride * sizeof(T);
+    const int n = nitems > 0 ? nitems : 1;
+    int grid = n;
+    for (int pass = 0; pass < 4; pass++) {
+        const size_t smem = bufs + (size_t)ring_iters(n, grid) * sizeof(RingMeta<T>);
+        if (smem > (size_t)maxsm) return cudaErrorInvalidValue;
+        if ((e = raise_smem_cap(kernel, smem)) != cudaSuccess) return e;
+        int per = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, rs.threads, smem)) != cudaSuccess)
+            return e;
+        const long long g = (long long)(per > 0 ? per : 1) * sms;
+        if (g >= grid) break;
+        grid = (int)g;
+    }
+    rs.grid = grid;
+    rs.smem = bufs + (size_t)ring_iters(n, grid) * sizeof(RingMeta<T>);
+    if (rs.smem > (size_t)maxsm) return cudaErrorInvalidValue;
+    return raise_smem_cap(kernel, rs.smem);
+}
+
 template <typename T>
 static void launch_orb(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, Scal *sc,
-                       int nrings, size_t smem, cudaStream_t s)
+                       int nrings, const RingShape &rs, cudaStream_t s)
 {
     switch (ring_chunk(m.nx)) {
-    case 1: launch_orb_c<T, 1>(m, tb, qs, v0, sc, nrings, smem, s); break;
-    case 2: launch_orb_c<T, 2>(m, tb, qs, v0, sc, nrings, smem, s); break;
-    case 3: launch_orb_c<T, 3>(m, tb, qs, v0, sc, nrings, smem, s); break;
-    case 4: launch_orb_c<T, 4>(m, tb, qs, v0, sc, nrings, smem, s); break;
-    default: launch_orb_c<T, 8>(m, tb, qs, v0, sc, nrings, smem, s); break;
+    case 1: launch_orb_c<T, 1>(m, tb, qs, v0, sc, nrings, rs, s); break;
+    case 2: launch_orb_c<T, 2>(m, tb, qs, v0, sc, nrings, rs, s); break;
+    case 3: launch_orb_c<T, 3>(m, tb, qs, v0, sc, nrings, rs, s); break;
+    case 4: launch_orb_c<T, 4>(m, tb, qs, v0, sc, nrings, rs, s); break;
+    default: launch_orb_c<T, 8>(m, tb, qs, v0, sc, nrings, rs, s); break;
     }
 }
 
@@ -476,8 +725,8 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
     // ---------------- consumers: one column each ----------------
     const int i = x0 + threadIdx.x;
     const bool col = i < m.nx;
-    const long long st = AXIS == 1 ? m.sj : m.sk;
-    const long long base = AXIS == 1 ? IX(m, col ? i : 0, 0, c2) : IX(m, col ? i : 0, c2, 0);
+    const idx_t st = AXIS == 1 ? m.sj : m.sk;
+    const idx_t base = AXIS == 1 ? IX(m, col ? i : 0, 0, c2) : IX(m, col ? i : 0, c2, 0);
     auto ring_of = [&](int p) { return AXIS == 1 ? c2 * m.nyt + p : p * m.nyt + c2; };
     auto icd = [&](int f) -> T { return AXIS == 1 ? tb.idyc[f] : tb.idzc[f * m.nyt + c2]; };
     auto width = [&](int d) -> T { return AXIS == 1 ? tb.dy[d] : tb.lenz[d * m.nyt + c2]; };
@@ -536,7 +785,7 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
         const T Sa = area(p + 1);
         const T dtVi = dt * tb.vinv[ring_of(p)];
         const T rho = R0[0];
-        const long long c = base + (long long)p * st;
+        const idx_t c = base + p * st;
         T F0 = 0;
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
@@ -654,7 +903,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
         sc->t = sc->t + sc->dt;
         sc->nstep += 1;
     }
-    const long long c = IX(m, i, j, k);
+    const idx_t c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
     const T *rho = fin.q[0];
@@ -666,7 +915,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     if (j < m.nyt && k < m.nzt) {
         T v = vsrc.vx[c];
         if (jact && kact) {
-            const long long cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
+            const idx_t cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
             const T R = tb.R[ring], w = R * R * tb.omega;
             v = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
         }
@@ -679,7 +928,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     if (k < m.nzt) {
         T v = vsrc.vy[c];
         if (m.hasY && j > m.j0 && j < m.j1 && kact) {
-            const long long cm = c - m.sj;
+            const idx_t cm = c - m.sj;
             v = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
         }
         state.vy[c] = v;
@@ -687,7 +936,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     if (m.hasZ && j < m.nyt) {
         T v = vsrc.vz[c];
         if (k > m.k0 && k < m.k1 && jact) {
-            const long long cm = c - m.sk;
+            const idx_t cm = c - m.sk;
             v = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
         }
         state.vz[c] = v;

@@ -191,3 +191,45 @@ def test_batch_rejects_bad_members():
     with pytest.raises(fb.FargoError) as e:
         fb.FargoBatch([a, a])                    # duplicate member
     assert e.value.code == -1
+
+
+def test_full_size_sweep_sampled_members():
+    """The 256-disk sweep at full size, as the benchmark runs it (FP32,
+    batched, CUDA graph): after two batched steps, the smallest and the
+    largest disk against the oracle stepping the same disk alone (2e-5
+    relative L1 on density, 1e-4 on the momentum density); the first
+    step's dt of both is bit-exact."""
+    import paper_1602_02359_b300 as fb
+    ps = W.batch_params(n=256, seed=1602)
+    sizes = [p["ny"] for p in ps]
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes))]
+    mem, ws = [], {}
+    for i, p in enumerate(ps):
+        w = W.batch_instance(p)
+        mem.append(make_ctx(w, fb.F32, t=0.0, t_end=w.t_end))
+        if i in pick:
+            ws[i] = w
+        else:
+            w.state = None
+    b = fb.FargoBatch(mem)
+    for n in range(2):
+        b.step()
+        for i in pick:
+            w = ws[i]
+            if n == 0:
+                o = oracle.Oracle(w)
+                st = {k: v.astype(np.float32).astype(np.float64) for k, v in w.state.items()}
+                ws[i] = (w, o, st, [0.0])
+            w, o, st, t = ws[i]
+            dt_o = o.step(st, t[0], w.t_end)
+            t[0] += dt_o
+            if n == 0:
+                assert mem[i].scalars()[1] == dt_o, i
+    for i in pick:
+        w, o, st, _ = ws[i]
+        g = mem[i].get_state()
+        assert rel_l1(w.active(g["rho"]), w.active(st["rho"])) < 2e-5, i
+        assert rel_l1(momentum_density(w, g), momentum_density(w, st)) < 1e-4, i
+    b.close()
+    for m in mem:
+        m.close()

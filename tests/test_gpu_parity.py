@@ -334,3 +334,40 @@ def test_run_to_lands_on_end_time_and_stops():
     assert t == 0.05 and err == 0
     c.run_to(0.05, max_steps=5)        # nothing left to do
     assert c.scalars()[2] == n
+
+
+def test_disk3d_full_size_sampled_slab():
+    """The 1536 x 512 x 96 disk in FP32, in the benchmark's launch
+    configuration (CUDA graph), one step at a fixed dt from a perturbed
+    state, sampled against the oracle run on a 1536 x 40 x 40 slab cut from
+    the same state.  The slab's ghosts are frozen while the full mesh updates
+    those cells, and every sub-step carries that difference at most a few
+    cells inward, so only cells 10 or more rows and planes inside the slab
+    are compared.  v0 of the sampled rings is bit-exact."""
+    import paper_1602_02359_b300 as fb
+    w = W.perturb(W.disk3d(), seed=31, amp=1e-2)
+    c = make_ctx(w, fb.F32)
+    st32 = {k: v.astype(np.float32).astype(np.float64) for k, v in w.state.items()}
+    w.state = None
+    j0, nj, k0, nk, edge = 200, 40, 28, 40, 10
+    ws = W.disk3d(slab=(j0, nj, k0, nk))
+    g = ws.g
+    sub = {k: v[k0:k0 + nk + 2 * g + 1, j0:j0 + nj + 2 * g + 1, :].copy() for k, v in st32.items()}
+    dt = 2e-3
+    c.step_fixed(dt)
+    o = oracle.Oracle(ws)
+    o.step(sub, 0.0, dt_fixed=dt)
+    full = c.get_state()
+    v0 = c.get_aux(6)
+    vo = o.v0({k: v[k0:k0 + nk + 2 * g + 1, j0:j0 + nj + 2 * g + 1, :].copy() for k, v in st32.items()})
+    zs, ys = slice(g + edge, g + nk - edge), slice(g + edge, g + nj - edge)
+    assert np.array_equal(v0[k0 + g + edge:k0 + g + nk - edge, j0 + g + edge:j0 + g + nj - edge], vo[zs, ys])
+    cut = lambda a: a[k0 + g + edge:k0 + g + nk - edge, j0 + g + edge:j0 + g + nj - edge, :]  # noqa: E731
+    e_rho = rel_l1(cut(full["rho"]), sub["rho"][zs, ys])
+    e_e = rel_l1(cut(full["e"]), sub["e"][zs, ys])
+    mg = np.stack([cut(full[k]) * cut(full["rho"]) for k in ("vx", "vy", "vz")])
+    mo = np.stack([sub[k][zs, ys] * sub["rho"][zs, ys] for k in ("vx", "vy", "vz")])
+    e_mom = rel_l1(mg, mo)
+    record("disk3d_full_size_slab_fp32_1step", rel_l1_rho=e_rho, rel_l1_e=e_e, rel_l1_momentum=e_mom)
+    assert e_rho < 2e-5 and e_e < 2e-5 and e_mom < 1e-4, (e_rho, e_e, e_mom)
+    c.close()
