@@ -274,7 +274,11 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     T rho[C + 4];
 #pragma unroll
     for (int s = 0; s < C + 4; s++) rho[s] = Rho[wrapi(i0 - 2 + s, nx)];
-    for (int q = 0; q < nq; q++) {
+    // unrolled over the largest quantity count: every row and output pointer
+    // index is then a compile-time constant
+    #pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if (q >= nq) break;
         const RatioSpec sp = spec(q);
         T a[C + 4];   // ratios of cells i0-2 .. i0+C+1
 #pragma unroll
@@ -411,7 +415,11 @@ __device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, co
         rinv[s] = T(1) / rho[s];
     }
     T F0[C + 1];
-    for (int q = 0; q < nq; q++) {
+    // unrolled over the largest quantity count: every row and output pointer
+    // index is then a compile-time constant
+    #pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if (q >= nq) break;
         T a[C + 6];   // ratios of cells i0-3 .. i0+C+2
 #pragma unroll
         for (int s = 0; s < C + 6; s++) a[s] = q == 0 ? rho[s] : at(q, wrapi(i0 - 3 + s, nx)) * rinv[s];
