@@ -70,10 +70,15 @@ __global__ void __launch_bounds__(256) kb_cfl_exact(const StepPlan<T> *__restric
 }
 
 // Per-cell phases: a member's cells of the augmented mesh (rows, planes as
-// in the single-instance grid) are numbered row by row, blockDim.x
-// consecutive cells per block, so no block is padded to a row's end.
+// in the single-instance grid) are numbered row by row; a block takes
+// kCellsPerThread * blockDim.x consecutive cells, each thread every
+// blockDim.x-th of them, so the member lookup is paid once per block for
+// several cells and no block is padded to a row's end.
+constexpr int kCellsPerThread = 16;
+
 // Register budgets: 40 per thread (six 256-thread blocks per SM) for every
-// phase but the viscous update, which gets 48 (five blocks).
+// phase but the viscous update, which gets 48 (five blocks); the few
+// spills this costs are cheaper than the occupancy larger budgets lose.
 template <typename T, int PH>
 __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
 {
@@ -81,22 +86,28 @@ __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const St
     const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
     const MeshD &m = p.m;
     const unsigned nyr = PH == PH_TAU ? tau_rows(m) : m.nyt + 1;
-    const unsigned npl = PH == PH_TAU ? tau_planes(m) : cell_planes(m);
+    const unsigned rows = nyr * (PH == PH_TAU ? tau_planes(m) : cell_planes(m));
     const unsigned nx = (unsigned)m.nx;
-    const unsigned lin = (unsigned)local * blockDim.x + threadIdx.x;
-    const unsigned row = lin / nx;
-    if (row >= nyr * npl) return;
-    const int i = (int)(lin - row * nx);
-    int j = (int)(row % nyr), k = (int)(row / nyr);
-    if constexpr (PH == PH_TAU) {
-        j += m.j0;
-        k += m.k0;
+    const unsigned lin = (unsigned)local * (kCellsPerThread * blockDim.x) + threadIdx.x;
+    unsigned row = lin / nx;
+    unsigned i = lin - row * nx;
+    for (int u = 0; u < kCellsPerThread && row < rows; u++) {
+        int j = (int)(row % nyr), k = (int)(row / nyr);
+        if constexpr (PH == PH_TAU) {
+            j += m.j0;
+            k += m.k0;
+        }
+        if constexpr (PH == PH_SUB1) substep1_body(m, p.tb, p.A, p.VB, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_AV) artvisc_body(m, p.tb, p.VB, p.A, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_TAU) visc_tau_body(m, p.tb, p.A, p.tau, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_VAPPLY) visc_apply_body(m, p.tb, p.A, p.VB, p.tau, p.sc, (int)i, j, k);
+        else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, (int)i, j, k);
+        i += blockDim.x;
+        while (i >= nx) {
+            i -= nx;
+            row++;
+        }
     }
-    if constexpr (PH == PH_SUB1) substep1_body(m, p.tb, p.A, p.VB, p.sc, i, j, k);
-    else if constexpr (PH == PH_AV) artvisc_body(m, p.tb, p.VB, p.A, p.sc, i, j, k);
-    else if constexpr (PH == PH_TAU) visc_tau_body(m, p.tb, p.A, p.tau, p.sc, i, j, k);
-    else if constexpr (PH == PH_VAPPLY) visc_apply_body(m, p.tb, p.A, p.VB, p.tau, p.sc, i, j, k);
-    else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, i, j, k);
 }
 
 // Ring operations over the items (member, ring) of a group: the member and
@@ -355,10 +366,10 @@ static int batch_setup(fargo_batch *b)
     auto all = [](const fargo_ctx *) { return true; };
     auto one = [](const fargo_ctx *) { return 0; };
     auto cells = [](const fargo_ctx *c) {
-        return (int)grid_for((long long)c->nx * (c->nyt + 1) * cell_planes(c->m), 256);
+        return (int)grid_for((long long)c->nx * (c->nyt + 1) * cell_planes(c->m), 256 * kCellsPerThread);
     };
     auto tau_cells = [](const fargo_ctx *c) {
-        return (int)grid_for((long long)c->nx * tau_rows(c->m) * tau_planes(c->m), 256);
+        return (int)grid_for((long long)c->nx * tau_rows(c->m) * tau_planes(c->m), 256 * kCellsPerThread);
     };
     auto hasY = [](const fargo_ctx *c) { return c->m.hasY != 0; };
     auto hasZ = [](const fargo_ctx *c) { return c->m.hasZ != 0; };
