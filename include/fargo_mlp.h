@@ -8,7 +8,8 @@
  *
  * Arithmetic: weights, the network input, hidden activations and the
  * back-propagated gradients that feed the products are bfloat16 (round to
- * nearest even); every product accumulates in FP32 on the tensor cores;
+ * nearest even); every product runs on the fifth-generation tensor cores
+ * (tcgen05, accumulator in tensor memory) and accumulates in FP32;
  * biases, pre-activations, the output, the loss, the gradients and the
  * Adam state (master weights, first and second moments) are FP32.
  *
@@ -79,6 +80,10 @@ int fargo_mlp_adam(fargo_mlp *net);
 /* fargo_mlp_backward then fargo_mlp_adam, replayed from a CUDA graph that is
  * captured on the first call with a given (x, t, batch, loss). */
 int fargo_mlp_train_step(fargo_mlp *net, const float *x, const float *t, int batch, float *loss);
+
+/* Synchronise and report a product that gave up waiting for its tensor-core
+ * work (FARGO_ERR_BARRIER_TIMEOUT), else OK.  The flag stays set. */
+int fargo_mlp_status(fargo_mlp *net);
 
 /* Deep-ensemble statistics of k outputs stacked as ys[k][batch][n] (device):
  * mean[batch][n] and, per sample, the relative spread

@@ -33,7 +33,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
-            "fargo_mlp_forward", "fargo_mlp_backward", "fargo_mlp_adam", "fargo_mlp_train_step",
+            "fargo_mlp_forward", "fargo_mlp_backward", "fargo_mlp_adam", "fargo_mlp_train_step", "fargo_mlp_status",
             "fargo_mlp_ensemble")
 
 PD = C.POINTER(C.c_double)

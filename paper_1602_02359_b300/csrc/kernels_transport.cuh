@@ -920,34 +920,38 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     const int oy = o + 2, oz = o + (m.hasY ? 4 : 2);
     const T *pmy = qsel(fin, oy), *ppy = qsel(fin, oy + 1);
     const T *pmz = qsel(fin, oz), *ppz = qsel(fin, oz + 1);
+    // interior faces from the momenta; every other face from the post-source
+    // velocities, read only there (and not at all when they are the state)
     if (j < m.nyt && k < m.nzt) {
-        T v = vsrc.vx[c];
         if (jact && kact) {
             const idx_t cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
             const T R = tb.R[ring], w = R * R * tb.omega;
-            v = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
+            state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) * tb.iR[ring];
+        } else if (vsrc.vx != state.vx) {
+            state.vx[c] = vsrc.vx[c];
         }
-        state.vx[c] = v;
         if (copy_scalars) {
             state.rho[c] = rho[c];
             if (!m.iso) state.e[c] = fin.q[1][c];
         }
     }
     if (k < m.nzt) {
-        T v = vsrc.vy[c];
         if (m.hasY && j > m.j0 && j < m.j1 && kact) {
             const idx_t cm = c - m.sj;
-            v = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
+            state.vy[c] = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
+        } else if (vsrc.vy != state.vy) {
+            state.vy[c] = vsrc.vy[c];
         }
-        state.vy[c] = v;
     }
     if (m.hasZ && j < m.nyt) {
-        T v = vsrc.vz[c];
         if (k > m.k0 && k < m.k1 && jact) {
             const idx_t cm = c - m.sk;
-            v = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
+            T v = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]);
+            if (m.geom == SPH) v *= tb.iym[j];   // Pi_z = rho r v_theta in spherical geometry
+            state.vz[c] = v;
+        } else if (vsrc.vz != state.vz) {
+            state.vz[c] = vsrc.vz[c];
         }
-        state.vz[c] = v;
     }
 }
 

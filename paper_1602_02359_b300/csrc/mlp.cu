@@ -3,6 +3,7 @@
 // The contract of each entry point is in include/fargo_mlp.h.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <cstdio>
 #include <cstring>
@@ -16,15 +17,9 @@ namespace mlp {
 typedef __nv_bfloat16 bf16;
 
 // ---------------------------------------------------------------------------
-// Tiled product C[m][n] = sum_k A^[m][k] B^[n][k] on the bfloat16 tensor
-// cores (mma m16n8k16, FP32 accumulators).  A^[m][k] is A[m*lda + k], or
-// A[k*lda + m] when TA; B^[n][k] likewise with TB.  A 64 x 64 block tile,
-// 32-deep K slices staged in shared memory K-contiguous (rows padded to 40
-// values so the 8 row addresses of an ldmatrix fall in distinct banks); four
-// warps of 32 x 32.  Out-of-range elements load as zero, so any M, N, K work.
+// Products C[m][n] = sum_k A^[m][k] B^[n][k] with fused epilogues.  A^[m][k]
+// is A[m*lda + k], or A[k*lda + m] when TA; B^[n][k] likewise with TB.
 // ---------------------------------------------------------------------------
-constexpr int BM = 64, BN = 64, BK = 32, SROW = BK + 8, NT = 128;
-
 enum { EPI_HIDDEN, EPI_OUT, EPI_STORE, EPI_DA };
 
 struct GemmArgs {
@@ -38,97 +33,182 @@ struct GemmArgs {
     bf16 *Ab;
     const float *bias, *Zmask, *oshift, *oscale;
     int ldc;
+    int *err;   // timeout flag (tcgen05 kernel)
 };
 
 __device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+// ---------------------------------------------------------------------------
+// The products run on the fifth-generation tensor cores (tcgen05).  One CTA
+// of four warps computes a 128 x 256 tile of C with its FP32 accumulator in
+// tensor memory (TMEM: 128 lanes = rows, 256 columns).  K advances in
+// 64-deep chunks through two shared-memory stages holding A^ (128 x 64) and
+// B^ (256 x 64) in the canonical K-major layout without swizzle: 8 x 8
+// "core matrices" of 128 contiguous bytes (8 rows of 16 bytes), K-adjacent
+// core matrices 128 bytes apart (leading offset) and 8-row groups 1024
+// bytes apart (stride offset).  All threads stage a chunk with plain loads
+// (transposing when TA / TB), then one thread issues four
+// tcgen05.mma.kind::f16 (K = 16 each, bfloat16 operands, FP32 accumulate)
+// and commits them to the stage's mbarrier, which releases the stage two
+// chunks later.  The epilogue reads the accumulator row by row with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31) and applies the fused
+// epilogue.  Every wait is bounded; on expiry
+// the CTA records the timeout, skips the epilogue and still frees its TMEM.
+// ---------------------------------------------------------------------------
+namespace tc {
+
+constexpr int TM = 128, TN = 256, TK = 64, NTH = 128;
+constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = 2 * STAGE_BYTES;   // 96 KB: at most two CTAs (512 TMEM columns) per SM
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(float *d, const unsigned *a, unsigned b0, unsigned b1)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    const unsigned a = su32(bar);
+    for (unsigned it = 0; it < kWaitLimit; it++) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
-// Stage rows r0.. of a K slice k0.. of X^ (TX: X^[r][k] = X[k*ld + r]).
-template <bool TX, int ROWS>
-__device__ __forceinline__ void load_tile(bf16 (*s)[SROW], const bf16 *X, int ld, int R, int Kd, int r0, int k0)
+// Shared-memory matrix descriptor: K-major, no swizzle (layout type 0),
+// descriptor version 1, leading offset 128 bytes (K direction), stride
+// offset 1024 bytes (8-row groups).
+__device__ __forceinline__ uint64_t smem_desc(unsigned saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bfloat16 A and B,
+// both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+// byte offset of element (r, k) of a staged chunk
+__device__ __forceinline__ unsigned core_off(int r, int k)
+{
+    return (unsigned)((((r >> 3) * (TK / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+template <bool TX>
+__device__ __forceinline__ void stage(unsigned char *dst, int rows, const bf16 *X, int ld, int R, int Kd, int r0,
+                                      int k0)
 {
     const bf16 zero = __float2bfloat16(0.0f);
-    for (int idx = threadIdx.x; idx < ROWS * BK; idx += NT) {
+    for (int idx = threadIdx.x; idx < rows * TK; idx += NTH) {
         int r, k;
         if (TX) {
-            r = idx % ROWS;
-            k = idx / ROWS;
+            r = idx % rows;
+            k = idx / rows;
         } else {
-            r = idx / BK;
-            k = idx % BK;
+            r = idx / TK;
+            k = idx % TK;
         }
         const int gr = r0 + r, gk = k0 + k;
         bf16 v = zero;
         if (gr < R && gk < Kd) v = TX ? X[(size_t)gk * ld + gr] : X[(size_t)gr * ld + gk];
-        s[r][k] = v;
+        *reinterpret_cast<bf16 *>(dst + core_off(r, k)) = v;
     }
 }
 
 template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(NT) k_gemm(GemmArgs g)
+__global__ void __launch_bounds__(NTH, 1) k_gemm_tc(GemmArgs g)
 {
-    __shared__ __align__(16) bf16 sA[BM][SROW];
-    __shared__ __align__(16) bf16 sB[BN][SROW];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_ok;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int b = 0; b < 4; b++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) acc[a][b][c] = 0.0f;
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
-        load_tile<TA, BM>(sA, g.A, g.lda, g.M, g.K, m0, k0);
-        load_tile<TB, BN>(sB, g.B, g.ldb, g.N, g.K, n0, k0);
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            unsigned af[2][4], bfr[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-                ldsm_x4(su32(&sA[wm + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]), af[mt][0], af[mt][1],
-                        af[mt][2], af[mt][3]);
-#pragma unroll
-            for (int np = 0; np < 2; np++)
-                ldsm_x4(su32(&sB[wn + np * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]),
-                        bfr[2 * np][0], bfr[2 * np][1], bfr[2 * np + 1][0], bfr[2 * np + 1][1]);
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
-        }
-        __syncthreads();
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                     "r"((unsigned)TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // accumulator element (row g, cols 2t, 2t+1) and (row g+8, same cols)
-    const int gq = lane >> 2, tq = lane & 3;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const int nk = (g.K + TK - 1) / TK;
+    bool ok = true;
+    for (int kc = 0; kc < nk && ok; kc++) {
+        const int st = kc & 1;
+        unsigned char *sa = smem + st * STAGE_BYTES, *sb = sa + A_BYTES;
+        // the MMAs of chunk kc-2 read this stage: wait for their commit
+        if (kc >= 2) ok = mbar_wait(&bar[st], ((kc - 2) >> 1) & 1);
+        if (!__syncthreads_and(ok)) break;
+        stage<TA>(sa, TM, g.A, g.lda, g.M, g.K, m0, kc * TK);
+        stage<TB>(sb, TN, g.B, g.ldb, g.N, g.K, n0, kc * TK);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = su32(sa), b0 = su32(sb);
 #pragma unroll
-    for (int mt = 0; mt < 2; mt++)
+            for (int kk = 0; kk < TK / 16; kk++) {
+                const uint64_t ad = smem_desc(a0 + kk * 256), bd = smem_desc(b0 + kk * 256);
+                const unsigned acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&bar[st]))
+                         : "memory");
+        }
+    }
+    // the last commit covers every MMA issued before it
+    if (ok && nk > 0) ok = mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row >= g.M) continue;
 #pragma unroll
-        for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-            for (int h = 0; h < 4; h++) {
-                const int row = m0 + wm + mt * 16 + gq + (h >> 1) * 8;
-                const int col = n0 + wn + nt * 8 + tq * 2 + (h & 1);
-                if (row >= g.M || col >= g.N) continue;
+            for (int u = 0; u < 16; u++) {
+                const int col = n0 + c0 + u;
+                if (col >= g.N) continue;
                 const size_t o = (size_t)row * g.ldc + col;
-                float v = acc[mt][nt][h];
+                float v = __uint_as_float(r[u]);
                 if (EPI == EPI_HIDDEN) {
                     v += g.bias[col];
                     g.C[o] = v;
@@ -143,13 +223,33 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmArgs g)
                     g.Ab[o] = __float2bfloat16_rn(v);
                 }
             }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(g.err, 4);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)TN)
+                     : "memory");
+    }
 }
+
+}  // namespace tc
 
 template <bool TA, bool TB, int EPI>
 static void gemm(const GemmArgs &g, cudaStream_t s)
 {
-    const dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-    k_gemm<TA, TB, EPI><<<grid, NT, 0, s>>>(g);
+    const dim3 grid((g.N + tc::TN - 1) / tc::TN, (g.M + tc::TM - 1) / tc::TM);
+    tc::k_gemm_tc<TA, TB, EPI><<<grid, tc::NTH, tc::SMEM_BYTES, s>>>(g);
+}
+
+template <bool TA, bool TB, int EPI>
+static cudaError_t gemm_attr()
+{
+    return cudaFuncSetAttribute(tc::k_gemm_tc<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES);
 }
 
 // x' = bf16((x - shift) * scale)
@@ -290,6 +390,7 @@ struct fargo_mlp {
     float *dz[2] = {nullptr, nullptr};
     bf16 *dzb[2] = {nullptr, nullptr};
     AdamHyper *hyper = nullptr;
+    int *err = nullptr;                                            // timeout flag of the products
     std::vector<void *> allocs;
     cudaGraphExec_t gexec = nullptr;
     const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -374,6 +475,10 @@ extern "C" int fargo_mlp_create(fargo_mlp **out, const int *dims, int nlayers, i
         if (!rc) rc = nalloc(n, &n->dzb[q], B * wmax);
     }
     if (!rc) rc = nalloc(n, &n->hyper, 1);
+    if (!rc) rc = nalloc(n, &n->err, 1);
+    if (!rc && (gemm_attr<false, false, EPI_HIDDEN>() != cudaSuccess || gemm_attr<false, false, EPI_OUT>() != cudaSuccess ||
+                gemm_attr<true, true, EPI_STORE>() != cudaSuccess || gemm_attr<false, true, EPI_DA>() != cudaSuccess))
+        rc = FARGO_ERR_CUDA;
     if (!rc) {
         std::vector<float> ones(wmax, 1.0f);
         AdamHyper h{1e-3f, 0.9f, 0.999f, 1e-8f, 0};
@@ -483,6 +588,7 @@ static int forward(fargo_mlp *n, const float *x, int batch)
     const bf16 *A = n->xb;
     for (int l = 0; l < n->L; l++) {
         GemmArgs g{};
+        g.err = n->err;
         g.A = A;
         g.lda = n->dims[l];
         g.B = n->wb + n->woff[l];
@@ -531,6 +637,7 @@ static int backward(fargo_mlp *n, const float *x, const float *t, int batch, flo
         const bf16 *Ain = l == 0 ? n->xb : n->Ab[l - 1];
         // dW_l[o][i] = sum_b dZ[b][o] A[b][i]
         GemmArgs gw{};
+        gw.err = n->err;
         gw.A = n->dzb[cur];
         gw.lda = No;
         gw.B = Ain;
@@ -545,6 +652,7 @@ static int backward(fargo_mlp *n, const float *x, const float *t, int batch, flo
         if (l > 0) {
             // dZ_{l-1}[b][i] = (Z_{l-1}[b][i] > 0) sum_o dZ[b][o] W_l[o][i]
             GemmArgs ga{};
+            ga.err = n->err;
             ga.A = n->dzb[cur];
             ga.lda = No;
             ga.B = n->wb + n->woff[l];
@@ -609,6 +717,15 @@ extern "C" int fargo_mlp_train_step(fargo_mlp *n, const float *x, const float *t
     }
     MK(cudaGraphLaunch(n->gexec, n->stream));
     return FARGO_OK;
+}
+
+extern "C" int fargo_mlp_status(fargo_mlp *n)
+{
+    if (!n) return FARGO_ERR_BADARG;
+    int h = 0;
+    MK(cudaMemcpyAsync(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    MK(cudaStreamSynchronize(n->stream));
+    return h ? FARGO_ERR_BARRIER_TIMEOUT : FARGO_OK;
 }
 
 extern "C" int fargo_mlp_ensemble(const float *ys, int k, int batch, int n, float *mean, float *spread, void *stream)

@@ -35,6 +35,7 @@ def _lib():
         L.fargo_mlp_adam.argtypes = [vp]
         L.fargo_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp]
         L.fargo_mlp_ensemble.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+        L.fargo_mlp_status.argtypes = [vp]
         _ready = True
     return L
 
@@ -107,6 +108,10 @@ class Mlp:
 
     def adam(self):
         _check(_lib().fargo_mlp_adam(self.h), "fargo_mlp_adam")
+
+    def status(self):
+        """Synchronise; raises if a tensor-core product gave up waiting."""
+        _check(_lib().fargo_mlp_status(self.h), "fargo_mlp_status")
 
     def train_step(self, x, t, loss=None):
         _check(_lib().fargo_mlp_train_step(self.h, _p(x), _p(t), x.shape[0], _p(loss)), "fargo_mlp_train_step")

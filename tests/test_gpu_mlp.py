@@ -51,6 +51,7 @@ def test_forward_matches_oracle(dims, batch):
     y = torch.empty(batch, dims[-1], device="cuda")
     net.forward(dev(X), y)
     Yo, _ = M.forward(p, X.astype(np.float64), emulate_bf16=True)
+    net.status()
     e = rel_l2(y.cpu().numpy(), Yo)
     record(f"mlp_forward_{'x'.join(map(str, dims))}_b{batch}", rel_l2=e)
     assert e < 2e-3
