@@ -926,7 +926,9 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
         if (jact && kact) {
             const idx_t cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
             const T R = tb.R[ring], w = R * R * tb.omega;
-            state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) * tb.iR[ring];
+            // divisions, not reciprocal products: v_x is rebuilt from R v_x every
+            // step, and a rounded 1/R would bias it by R (1/R) - 1 each time
+            state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
         } else if (vsrc.vx != state.vx) {
             state.vx[c] = vsrc.vx[c];
         }
@@ -946,9 +948,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     if (m.hasZ && j < m.nyt) {
         if (k > m.k0 && k < m.k1 && jact) {
             const idx_t cm = c - m.sk;
-            T v = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]);
-            if (m.geom == SPH) v *= tb.iym[j];   // Pi_z = rho r v_theta in spherical geometry
-            state.vz[c] = v;
+            state.vz[c] = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
         } else if (vsrc.vz != state.vz) {
             state.vz[c] = vsrc.vz[c];
         }
