@@ -140,12 +140,13 @@ __device__ __forceinline__ double av_rate(const MeshD &m, double dv, double len)
     if (dv < 0.0) return __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0, m.cq), m.cq), -dv), len);
     return 0.0;
 }
-// FP32 estimate of the artificial-viscosity rate; k4 = 4 C_q^2 (ZEUS form)
-// or 1/(4 sqrt 2) (printed form), both rounded to FP32 on the host side.
-__device__ __forceinline__ float av_ratef(bool lit, float k4, float dv, float len)
+// FP32 estimate of the artificial-viscosity rate from the reciprocal of the
+// cell length; k4 = 4 C_q^2 (ZEUS form) or 1/(4 sqrt 2) (printed form), both
+// rounded to FP32 on the host side.
+__device__ __forceinline__ float av_ratef(bool lit, float k4, float dv, float ilen)
 {
-    if (lit) return fabsf(dv) * k4 / len;
-    if (dv < 0.0f) return k4 * (-dv) / len;
+    if (lit) return fabsf(dv) * k4 * ilen;
+    if (dv < 0.0f) return k4 * (-dv) * ilen;
     return 0.0f;
 }
 
@@ -194,11 +195,15 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
             if (lane == 0) v0[ring] = v0r;
         }
         const T v0hi = (T)v0r, v0lo = (T)(v0r - (double)v0hi);
-        const float lx = (float)tb.lenx[ring], ly = (float)tb.dy[j], lz = (float)tb.lenz[ring];
+        // per-ring reciprocals: the estimate needs no division per cell and no
+        // square root (the sound-speed rate enters squared)
+        const float ilx = 1.0f / (float)tb.lenx[ring], ily = 1.0f / (float)tb.dy[j];
+        const float ilz = 1.0f / (float)tb.lenz[ring];
         const float dmin = (float)tb.dminT[ring];
+        const float idm2 = 1.0f / (dmin * dmin);
         const float r4 = m.has_nu ? (float)tb.r4[ring] : 0.0f;
         const float csr = m.iso ? (float)tb.cs[ring] : 0.0f;
-        const float g1 = (float)tb.g1;
+        const float c1 = m.iso ? csr * csr * idm2 : (float)tb.g1 * idm2;
         const bool lit = m.av_lit != 0;
         const float k4 = (float)tb.k4;
         const bool avon = m.has_av != 0;
@@ -206,38 +211,37 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
             const idx_t c = base + i;
             const int ip = i + 1 == m.nx ? 0 : i + 1;
             const float rho = (float)f.rho[c];
-            float cs;
+            float r1s;   // (c_s / dmin)^2
             if (m.iso) {
-                cs = csr;
+                r1s = c1;
             } else {
                 const float e = (float)f.e[c];
                 if (!isfinite(e) || e < 0.0f) bad = 1;
-                cs = sqrtf(g1 * e / rho);
+                r1s = c1 * __fdividef(e, rho);
             }
             if (!isfinite(rho) || rho <= 0.0f) bad = 1;
-            const float r1 = cs / dmin;
             float r2 = 0.0f, r3 = 0.0f;
             if (m.hasX) {
                 const T vc = f.vx[c], vp = f.vx[base + ip];
                 const float a = fabsf((float)sub_split(vc, v0hi, v0lo));
                 const float b = fabsf((float)sub_split(vp, v0hi, v0lo));
-                r2 = fmaxf(r2, fmaxf(a, b) / lx);
-                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), lx));
+                r2 = fmaxf(r2, fmaxf(a, b) * ilx);
+                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ilx));
                 if (!isfinite((float)vc)) bad = 1;
             }
             if (m.hasY) {
                 const T vc = f.vy[c], vp = f.vy[c + m.sj];
-                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) / ly);
-                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ly));
+                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ily);
+                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ily));
                 if (!isfinite((float)vc)) bad = 1;
             }
             if (m.hasZ) {
                 const T vc = f.vz[c], vp = f.vz[c + m.sk];
-                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) / lz);
-                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), lz));
+                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ilz);
+                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ilz));
                 if (!isfinite((float)vc)) bad = 1;
             }
-            const float s = r1 * r1 + r2 * r2 + r3 * r3 + r4 * r4;
+            const float s = r1s + r2 * r2 + r3 * r3 + r4 * r4;
             smax = fmaxf(smax, s);
         }
         smax = warp_maxf(smax);
