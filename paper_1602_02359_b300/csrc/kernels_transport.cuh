@@ -501,9 +501,12 @@ __device__ __forceinline__ RingMeta<T> *ring_meta(unsigned char *smem, int strid
     return reinterpret_cast<RingMeta<T> *>(smem + 2 * (size_t)stride * sizeof(T));
 }
 
+// The parameters are __grid_constant__: the ring operations hold references
+// to them, which then point into the parameter bank instead of a local copy.
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> out, const double *v0,
-                                                     Scal *sc, int stride)
+__global__ void __launch_bounds__(512, 2)
+    k_transport_x(const __grid_constant__ MeshD m, const __grid_constant__ Tab<T> tb, const __grid_constant__ Fld<T> in,
+                  const __grid_constant__ QSet<T> out, const double *v0, Scal *sc, int stride)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -516,8 +519,9 @@ __global__ void __launch_bounds__(512, 2) k_transport_x(MeshD m, Tab<T> tb, Fld<
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) k_orbital(MeshD m, Tab<T> tb, QSet<T> qs, const double *v0, Scal *sc,
-                                                 int nrings, int stride)
+__global__ void __launch_bounds__(512, 2)
+    k_orbital(const __grid_constant__ MeshD m, const __grid_constant__ Tab<T> tb, const __grid_constant__ QSet<T> qs,
+              const double *v0, Scal *sc, int nrings, int stride)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
