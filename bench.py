@@ -102,6 +102,65 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def bf16_peak():
+    """Dense bf16 tensor peak (TFLOP/s): the burst figure for a kernel timed alone."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1800.0, "fallback"
+
+
+def bench_surrogate(torch, reps=20):
+    """The surrogate network kernels (tcgen05 products): ensemble inference
+    latency for the 205 evaluation queries of the sweep, one training step
+    (batch 256, 4 members), and forward throughput at a large batch against
+    the bf16 tensor peak.  Seeded random weights and inputs; the timing does
+    not depend on their values."""
+    import paper_1602_02359_b300.mlp as fm
+    from paper_1602_02359_b300.surrogate import Ensemble
+    dims = W.mlp_dims()
+    flop_per_sample = 2 * sum(a * b for a, b in zip(dims[:-1], dims[1:]))
+    ens = Ensemble(k=4, seed=1602, max_batch=65536)
+    g = torch.Generator(device="cpu").manual_seed(1602)
+    xq = torch.rand(205, dims[0], generator=g).cuda()
+    st = ens.stream
+
+    def timed(fn, n):
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(n):
+                fn()
+            e1.record(st)
+            e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ms_query = timed(lambda: ens.predict(xq), reps)
+    xb = torch.rand(256, dims[0], generator=g).cuda()
+    tb = torch.rand(256, dims[-1], generator=g).cuda()
+    ms_train = timed(lambda: [n.train_step(xb, tb) for n in ens.nets], reps)
+    big = 65536
+    xl = torch.rand(big, dims[0], generator=g).cuda()
+    yl = torch.empty(big, dims[-1], device="cuda")
+    ms_big = timed(lambda: ens.nets[0].forward(xl, yl), reps)
+    for n in ens.nets:
+        n.status()
+    ens.close()
+    peak, kind = bf16_peak()
+    tflops = flop_per_sample * big / (ms_big * 1e-3) / 1e12
+    return {"network": "x".join(map(str, dims)), "ensemble": 4,
+            "query_205_ms": round(ms_query, 4), "train_step_4_members_batch256_ms": round(ms_train, 4),
+            "forward_batch65536_ms": round(ms_big, 4),
+            "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tflops / peak, 4), "peak_kind": f"{kind} bf16 dense (burst)",
+                         "flop_per_sample": flop_per_sample}}
+
+
 class Clocks:
     """nvidia-smi sampler (SM clock, max clock, throttle reasons) during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -502,6 +561,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-single", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -552,6 +612,10 @@ def main():
                                                                  "method_frac", "traffic")},
                   "per_kernel": s["roofline"]["per_kernel"], "clocks": s["clocks"]}
 
+    surrogate = None
+    if rank == 0 and batched and not args.no_surrogate:
+        surrogate = bench_surrogate(torch)
+
     fp64 = None
     if rank == 0 and not args.no_fp64 and args.workload in ("disk3d",) + tuple(BATCH_WORKLOADS):
         fp64 = fp64_plain_disk2d(torch, fb)
@@ -589,6 +653,8 @@ def main():
             line[key] = value / ws / fp64["value"]
         if single is not None:
             line["single_instance_fp32"] = single
+        if surrogate is not None:
+            line["surrogate_kernels"] = surrogate
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -1,6 +1,7 @@
 // Surrogate network of the batched disk sweep: bfloat16 tensor-core products
 // with FP32 accumulation for the forward pass, back-propagation and Adam.
 // The contract of each entry point is in include/fargo_mlp.h.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,6 +34,7 @@ struct GemmArgs {
     bf16 *Ab;
     const float *bias, *Zmask, *oshift, *oscale;
     int ldc;
+    int ldab;   // row pitch of Ab (EPI_HIDDEN: the padded activation pitch)
     int *err;   // timeout flag (tcgen05 kernel)
 };
 
@@ -85,15 +87,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 }
 
 // Shared-memory matrix descriptor: K-major, no swizzle (layout type 0),
-// descriptor version 1, leading offset 128 bytes (K direction), stride
-// offset 1024 bytes (8-row groups).
-__device__ __forceinline__ uint64_t smem_desc(unsigned saddr)
+// descriptor version 1; lbo = byte distance of K-adjacent core matrices,
+// sbo = byte distance of adjacent 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(unsigned saddr, unsigned lbo = 128, unsigned sbo = 1024)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Shared-memory matrix descriptor of the K-major 128-byte-swizzle layout:
+// rows of 128 bytes, 8-row atoms 1024 bytes apart (stride offset), leading
+// offset unused (encoded 1), layout type 2 (128-byte swizzle) in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc_sw128(unsigned saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -129,6 +145,73 @@ __device__ __forceinline__ void stage(unsigned char *dst, int rows, const bf16 *
     }
 }
 
+// Epilogue of a 128 x TN accumulator tile.  Warp w owns TMEM lanes
+// 32w..32w+31 (rows m0+32w..); per 32-column slice it reads its 32 x 32
+// block with two tcgen05.ld, parks it in shared memory (row pitch 33 floats:
+// conflict-free both ways) and then writes it row by row, lane = column, so
+// every store instruction covers one contiguous row segment.  `tile` is the
+// warp's 32 x 33 float scratch (the operand stages are free by then).
+// EPI_HIDDEN with C == nullptr stores only the activations (inference).
+template <int EPI>
+__device__ __forceinline__ void epilogue(const GemmArgs &g, uint32_t tmem, int m0, int n0, float *tile)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rbase = m0 + warp * 32;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+        if (n0 + c0 >= g.N || rbase >= g.M) break;   // warp-uniform
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15}, [%16];"
+            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr + 16u));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int u = 0; u < 32; u++) tile[lane * 33 + u] = __uint_as_float(r[u]);
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        const bool cok = col < g.N;
+        float b = 0.0f, sc = 1.0f, sh = 0.0f;
+        if (cok && (EPI == EPI_HIDDEN || EPI == EPI_OUT)) b = g.bias[col];
+        if (cok && EPI == EPI_OUT) {
+            sc = g.oscale[col];
+            sh = g.oshift[col];
+        }
+        const int nr = min(32, g.M - rbase);
+#pragma unroll 4
+        for (int rr = 0; rr < nr; rr++) {
+            float v = tile[rr * 33 + lane];
+            if (!cok) continue;
+            const int row = rbase + rr;
+            const size_t o = (size_t)row * g.ldc + col;
+            if (EPI == EPI_HIDDEN) {
+                v += b;
+                if (g.C) g.C[o] = v;
+                g.Ab[(size_t)row * g.ldab + col] = __float2bfloat16_rn(v > 0.0f ? v : 0.0f);
+            } else if (EPI == EPI_OUT) {
+                g.C[o] = (v + b) * sc + sh;
+            } else if (EPI == EPI_STORE) {
+                g.C[o] = v;
+            } else {
+                v = g.Zmask[o] > 0.0f ? v : 0.0f;
+                g.C[o] = v;
+                g.Ab[o] = __float2bfloat16_rn(v);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(GemmArgs g)
 {
@@ -136,7 +219,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(GemmArgs g)
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_ok;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
@@ -189,41 +272,131 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(GemmArgs g)
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int row = m0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row >= g.M) continue;
-#pragma unroll
-            for (int u = 0; u < 16; u++) {
-                const int col = n0 + c0 + u;
-                if (col >= g.N) continue;
-                const size_t o = (size_t)row * g.ldc + col;
-                float v = __uint_as_float(r[u]);
-                if (EPI == EPI_HIDDEN) {
-                    v += g.bias[col];
-                    g.C[o] = v;
-                    g.Ab[o] = __float2bfloat16_rn(v > 0.0f ? v : 0.0f);
-                } else if (EPI == EPI_OUT) {
-                    g.C[o] = (v + g.bias[col]) * g.oscale[col] + g.oshift[col];
-                } else if (EPI == EPI_STORE) {
-                    g.C[o] = v;
-                } else {
-                    v = g.Zmask[o] > 0.0f ? v : 0.0f;
-                    g.C[o] = v;
-                    g.Ab[o] = __float2bfloat16_rn(v);
-                }
-            }
+        epilogue<EPI>(g, tmem, m0, n0, reinterpret_cast<float *>(smem) + warp * 32 * 33);
+    } else if (threadIdx.x == 0) {
+        atomicOr(g.err, 4);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)TN)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward products with TMA staging.  Both operands are K-contiguous (the
+// activations [rows][K] and the weights [N][K], rows 16-byte aligned), so
+// thread 0 stages a 64-deep chunk with one 2D tensor-map load per operand:
+// box 64 K x 128 rows for A, 64 x 256 for B, 128-byte swizzle.  A row of the
+// box is 128 bytes (the chunk's 64 K values), eight rows form a 1024-byte
+// swizzle atom, so the MMA descriptors use the 128-byte-swizzle K-major
+// layout with a stride offset of 1024 bytes, and the K = 16 step inside the
+// chunk advances the start address by 32 bytes (the swizzle is applied to
+// the absolute shared address, hence the 1024-byte aligned stages).
+// Out-of-range rows and K columns read as zero.  Thread 0 prefetches chunk
+// kc+1 while the tensor cores work on chunk kc; every wait is bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(su32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(NTH, 1) k_gemm_tma(const __grid_constant__ CUtensorMap ma,
+                                                    const __grid_constant__ CUtensorMap mb, GemmArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2], done[2];
+    // swizzled stages start on a 1024-byte boundary (the launch adds 1 KB)
+    unsigned char *sm = smem + ((1024u - (su32(smem) & 1023u)) & 1023u);
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_ok;
+    const int warp = threadIdx.x >> 5;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                     "r"((unsigned)TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 2; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&done[q], 1);
         }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const int nk = (g.K + TK - 1) / TK;
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&ma) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mb) : "memory");
+        auto issue = [&](int kc) {
+            const int st = kc & 1;
+            unsigned char *sa = sm + st * STAGE_BYTES, *sb = sa + A_BYTES;
+            mbar_expect_tx(&full[st], (unsigned)STAGE_BYTES);
+            tma_load_2d(sa, &ma, kc * TK, m0, &full[st]);
+            tma_load_2d(sb, &mb, kc * TK, n0, &full[st]);
+        };
+        bool ok = true;
+        int issued = 0;   // chunks whose copies were issued
+        if (nk > 0) {
+            issue(0);
+            issued = 1;
+        }
+        for (int kc = 0; kc < nk && ok; kc++) {
+            const int st = kc & 1;
+            if (kc + 1 < nk) {
+                // chunk kc-1 used the other stage: its MMAs must be done
+                if (kc >= 1) ok = mbar_wait(&done[(kc + 1) & 1], ((kc - 1) >> 1) & 1);
+                if (!ok) break;
+                issue(kc + 1);
+                issued = kc + 2;
+            }
+            ok = mbar_wait(&full[st], (kc >> 1) & 1);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = su32(sm + st * STAGE_BYTES), b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; kk++) {
+                const uint64_t ad = smem_desc_sw128(a0 + kk * 32);
+                const uint64_t bd = smem_desc_sw128(b0 + kk * 32);
+                const unsigned acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&done[st]))
+                         : "memory");
+        }
+        if (ok && nk > 0) ok = mbar_wait(&done[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+        if (!ok) {
+            // let the copies in flight land before the CTA can leave
+            for (int kc = 0; kc < issued; kc++) mbar_wait(&full[kc & 1], (kc >> 1) & 1);
+        }
+        s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_ok) {
+        epilogue<EPI>(g, tmem, m0, n0, reinterpret_cast<float *>(sm) + warp * 32 * 33);
     } else if (threadIdx.x == 0) {
         atomicOr(g.err, 4);
     }
@@ -252,12 +425,86 @@ static cudaError_t gemm_attr()
                                 tc::SMEM_BYTES);
 }
 
-// x' = bf16((x - shift) * scale)
-__global__ void k_input(const float *x, int n, int cols, const float *shift, const float *scale, bf16 *out)
+template <int EPI>
+static void gemm_tma(const CUtensorMap &ma, const CUtensorMap &mb, const GemmArgs &g, cudaStream_t s)
 {
+    const dim3 grid((g.N + tc::TN - 1) / tc::TN, (g.M + tc::TM - 1) / tc::TM);
+    tc::k_gemm_tma<EPI><<<grid, tc::NTH, tc::SMEM_BYTES + 1024, s>>>(ma, mb, g);
+}
+
+template <int EPI>
+static cudaError_t gemm_tma_attr()
+{
+    return cudaFuncSetAttribute(tc::k_gemm_tma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES + 1024);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2D map of a bfloat16 matrix [rows][cols] with row pitch `ld` values (a
+// multiple of 8), box of 64 columns (128 bytes) by box_rows rows, 128-byte
+// swizzle, zero fill outside.
+static bool encode_bf16(CUtensorMap *map, const bf16 *base, int cols, int rows, int ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::TK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Where each layer's weights sit in the flat parameter vector, and their
+// padded bfloat16 copies (row pitch a multiple of 8) for the tensor maps.
+struct LayerTab {
+    int L;
+    unsigned long long woff[16];
+    int K[16], N[16], ldp[16];
+    bf16 *wpad[16];
+};
+
+__device__ __forceinline__ void pack_weight(const LayerTab &lt, size_t i, bf16 v)
+{
+    for (int l = 0; l < lt.L; l++) {
+        const size_t rel = i - (size_t)lt.woff[l];
+        if (i >= (size_t)lt.woff[l] && rel < (size_t)lt.K[l] * lt.N[l]) {
+            const size_t n = rel / lt.K[l], k = rel - n * lt.K[l];
+            lt.wpad[l][n * lt.ldp[l] + k] = v;
+            return;
+        }
+    }
+}
+
+// x' = bf16((x - shift) * scale), rows of `cols` values written with pitch
+// ld (the padding columns hold zeros)
+__global__ void k_input(const float *x, int rows, int cols, int ld, const float *shift, const float *scale,
+                        bf16 *out)
+{
+    const int n = rows * ld;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = i % cols;
-        out[i] = __float2bfloat16_rn((x[i] - shift[c]) * scale[c]);
+        const int r = i / ld, c = i - r * ld;
+        out[i] = c < cols ? __float2bfloat16_rn((x[(size_t)r * cols + c] - shift[c]) * scale[c])
+                          : __float2bfloat16(0.0f);
     }
 }
 
@@ -304,8 +551,9 @@ struct AdamHyper {
 
 __global__ void k_adam_tick(AdamHyper *h) { h->t += 1; }
 
-// Adam on the flat parameter vector; bfloat16 copies re-rounded.
-__global__ void k_adam(float *w, float *m, float *v, const float *g, bf16 *wb, size_t n, const AdamHyper *h)
+// Adam on the flat parameter vector; bfloat16 copies (flat and padded) re-rounded.
+__global__ void k_adam(float *w, float *m, float *v, const float *g, bf16 *wb, size_t n, const AdamHyper *h,
+                       LayerTab lt)
 {
     const float lr = h->lr, b1 = h->b1, b2 = h->b2, eps = h->eps;
     const float t = (float)h->t;
@@ -318,14 +566,19 @@ __global__ void k_adam(float *w, float *m, float *v, const float *g, bf16 *wb, s
         v[i] = vi;
         const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         w[i] = wi;
-        wb[i] = __float2bfloat16_rn(wi);
+        const bf16 b = __float2bfloat16_rn(wi);
+        wb[i] = b;
+        pack_weight(lt, i, b);
     }
 }
 
-__global__ void k_round(const float *w, bf16 *wb, size_t n)
+__global__ void k_round(const float *w, bf16 *wb, size_t n, LayerTab lt)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        wb[i] = __float2bfloat16_rn(w[i]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const bf16 b = __float2bfloat16_rn(w[i]);
+        wb[i] = b;
+        pack_weight(lt, i, b);
+    }
 }
 
 // One block per sample: ensemble mean and relative spread.
@@ -383,9 +636,13 @@ struct fargo_mlp {
     bf16 *wb = nullptr;                                            // bfloat16 copy (same layout)
     float *shift = nullptr, *scale = nullptr;      // input map
     float *oshift = nullptr, *oscale = nullptr;    // output map
-    bf16 *xb = nullptr;                                            // bfloat16 input
+    bf16 *xb = nullptr;                                            // bfloat16 input, pitch ldp[0]
+    std::vector<int> ldp;                                          // padded widths (multiples of 8)
+    std::vector<bf16 *> wpad;                                      // padded bfloat16 weights per layer
+    std::vector<CUtensorMap> mapA, mapB;                           // forward operands per layer
+    LayerTab lt{};
     std::vector<float *> Z;                                        // hidden pre-activations (FP32)
-    std::vector<bf16 *> Ab;                                        // hidden activations (bf16)
+    std::vector<bf16 *> Ab;                                        // hidden activations (bf16, pitch ldp[l+1])
     float *y = nullptr;                                            // output of the last forward
     float *dz[2] = {nullptr, nullptr};
     bf16 *dzb[2] = {nullptr, nullptr};
@@ -460,14 +717,34 @@ extern "C" int fargo_mlp_create(fargo_mlp **out, const int *dims, int nlayers, i
     if (!rc) rc = nalloc(n, &n->scale, dims[0]);
     if (!rc) rc = nalloc(n, &n->oshift, dims[nlayers]);
     if (!rc) rc = nalloc(n, &n->oscale, dims[nlayers]);
-    if (!rc) rc = nalloc(n, &n->xb, B * dims[0]);
+    for (int l = 0; l <= nlayers; l++) n->ldp.push_back((dims[l] + 7) / 8 * 8);
+    if (!rc) rc = nalloc(n, &n->xb, B * n->ldp[0]);
     for (int l = 0; l < nlayers - 1 && !rc; l++) {
         float *z = nullptr;
         bf16 *a = nullptr;
         rc = nalloc(n, &z, B * dims[l + 1]);
-        if (!rc) rc = nalloc(n, &a, B * dims[l + 1]);
+        if (!rc) rc = nalloc(n, &a, B * n->ldp[l + 1]);
         n->Z.push_back(z);
         n->Ab.push_back(a);
+    }
+    n->lt.L = nlayers;
+    for (int l = 0; l < nlayers && !rc; l++) {
+        bf16 *wp = nullptr;
+        rc = nalloc(n, &wp, (size_t)dims[l + 1] * n->ldp[l]);
+        n->wpad.push_back(wp);
+        n->lt.woff[l] = n->woff[l];
+        n->lt.K[l] = dims[l];
+        n->lt.N[l] = dims[l + 1];
+        n->lt.ldp[l] = n->ldp[l];
+        n->lt.wpad[l] = wp;
+    }
+    n->mapA.resize(nlayers);
+    n->mapB.resize(nlayers);
+    for (int l = 0; l < nlayers && !rc; l++) {
+        const bf16 *ain = l == 0 ? n->xb : n->Ab[l - 1];
+        if (!encode_bf16(&n->mapA[l], ain, dims[l], max_batch, n->ldp[l], tc::TM) ||
+            !encode_bf16(&n->mapB[l], n->wpad[l], dims[l], dims[l + 1], n->ldp[l], tc::TN))
+            rc = FARGO_ERR_CUDA;
     }
     if (!rc) rc = nalloc(n, &n->y, B * dims[nlayers]);
     for (int q = 0; q < 2 && !rc; q++) {
@@ -476,7 +753,7 @@ extern "C" int fargo_mlp_create(fargo_mlp **out, const int *dims, int nlayers, i
     }
     if (!rc) rc = nalloc(n, &n->hyper, 1);
     if (!rc) rc = nalloc(n, &n->err, 1);
-    if (!rc && (gemm_attr<false, false, EPI_HIDDEN>() != cudaSuccess || gemm_attr<false, false, EPI_OUT>() != cudaSuccess ||
+    if (!rc && (gemm_tma_attr<EPI_HIDDEN>() != cudaSuccess || gemm_tma_attr<EPI_OUT>() != cudaSuccess ||
                 gemm_attr<true, true, EPI_STORE>() != cudaSuccess || gemm_attr<false, true, EPI_DA>() != cudaSuccess))
         rc = FARGO_ERR_CUDA;
     if (!rc) {
@@ -517,7 +794,7 @@ extern "C" int fargo_mlp_set_params(fargo_mlp *n, const float *host, size_t coun
     MK(cudaMemcpyAsync(n->w, host, n->np * sizeof(float), cudaMemcpyHostToDevice, n->stream));
     MK(cudaMemsetAsync(n->m, 0, n->np * sizeof(float), n->stream));
     MK(cudaMemsetAsync(n->v, 0, n->np * sizeof(float), n->stream));
-    k_round<<<blocks_for(n->np, 256), 256, 0, n->stream>>>(n->w, n->wb, n->np);
+    k_round<<<blocks_for(n->np, 256), 256, 0, n->stream>>>(n->w, n->wb, n->np, n->lt);
     MK(cudaGetLastError());
     const int zero = 0;
     MK(cudaMemcpyAsync(&n->hyper->t, &zero, sizeof(int), cudaMemcpyHostToDevice, n->stream));
@@ -580,34 +857,32 @@ extern "C" int fargo_mlp_set_optimizer(fargo_mlp *n, float lr, float b1, float b
 }
 
 // Forward pass into n->y (hidden pre-activations and activations kept).
-static int forward(fargo_mlp *n, const float *x, int batch)
+// keep_z: store the FP32 pre-activations that back-propagation masks with
+// (inference skips them)
+static int forward(fargo_mlp *n, const float *x, int batch, bool keep_z)
 {
     cudaStream_t s = n->stream;
     const int K0 = n->dims[0];
-    k_input<<<blocks_for((size_t)batch * K0, 256), 256, 0, s>>>(x, batch * K0, K0, n->shift, n->scale, n->xb);
-    const bf16 *A = n->xb;
+    k_input<<<blocks_for((size_t)batch * n->ldp[0], 256), 256, 0, s>>>(x, batch, K0, n->ldp[0], n->shift, n->scale,
+                                                                      n->xb);
     for (int l = 0; l < n->L; l++) {
         GemmArgs g{};
         g.err = n->err;
-        g.A = A;
-        g.lda = n->dims[l];
-        g.B = n->wb + n->woff[l];
-        g.ldb = n->dims[l];
         g.M = batch;
         g.N = n->dims[l + 1];
         g.K = n->dims[l];
         g.bias = n->w + n->boff[l];
         g.ldc = g.N;
         if (l < n->L - 1) {
-            g.C = n->Z[l];
+            g.C = keep_z ? n->Z[l] : nullptr;
             g.Ab = n->Ab[l];
-            gemm<false, false, EPI_HIDDEN>(g, s);
-            A = n->Ab[l];
+            g.ldab = n->ldp[l + 1];
+            gemm_tma<EPI_HIDDEN>(n->mapA[l], n->mapB[l], g, s);
         } else {
             g.C = n->y;
             g.oshift = n->oshift;
             g.oscale = n->oscale;
-            gemm<false, false, EPI_OUT>(g, s);
+            gemm_tma<EPI_OUT>(n->mapA[l], n->mapB[l], g, s);
         }
     }
     MK(cudaGetLastError());
@@ -618,7 +893,7 @@ extern "C" int fargo_mlp_forward(fargo_mlp *n, const float *x, int batch, float 
 {
     if (!n || !x || !y || batch < 1) return FARGO_ERR_BADARG;
     if (batch > n->max_batch) return FARGO_ERR_SIZE;
-    int rc = forward(n, x, batch);
+    int rc = forward(n, x, batch, false);
     if (rc) return rc;
     MK(cudaMemcpyAsync(y, n->y, sizeof(float) * batch * n->dims[n->L], cudaMemcpyDeviceToDevice, n->stream));
     return FARGO_OK;
@@ -626,7 +901,7 @@ extern "C" int fargo_mlp_forward(fargo_mlp *n, const float *x, int batch, float 
 
 static int backward(fargo_mlp *n, const float *x, const float *t, int batch, float *loss)
 {
-    int rc = forward(n, x, batch);
+    int rc = forward(n, x, batch, true);
     if (rc) return rc;
     cudaStream_t s = n->stream;
     const int L = n->L;
@@ -641,7 +916,7 @@ static int backward(fargo_mlp *n, const float *x, const float *t, int batch, flo
         gw.A = n->dzb[cur];
         gw.lda = No;
         gw.B = Ain;
-        gw.ldb = Ki;
+        gw.ldb = n->ldp[l];
         gw.M = No;
         gw.N = Ki;
         gw.K = batch;
@@ -682,7 +957,7 @@ extern "C" int fargo_mlp_backward(fargo_mlp *n, const float *x, const float *t, 
 static int adam(fargo_mlp *n)
 {
     k_adam_tick<<<1, 1, 0, n->stream>>>(n->hyper);
-    k_adam<<<blocks_for(n->np, 256), 256, 0, n->stream>>>(n->w, n->m, n->v, n->g, n->wb, n->np, n->hyper);
+    k_adam<<<blocks_for(n->np, 256), 256, 0, n->stream>>>(n->w, n->m, n->v, n->g, n->wb, n->np, n->hyper, n->lt);
     MK(cudaGetLastError());
     return FARGO_OK;
 }
