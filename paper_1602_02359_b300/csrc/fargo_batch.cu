@@ -136,7 +136,7 @@ struct BTxOp {
         const StepPlan<T> &p = P[e.id];
         tx_issue(p.m, p.txin, e.local, dst, bar);
     }
-    __device__ void compute(int it, const T *src)
+    __device__ void compute(int it, T *src)
     {
         const RingMeta<T> &e = meta[it];
         if (e.N < 0) return;
@@ -168,7 +168,7 @@ struct BOrbOp {
         const StepPlan<T> &p = P[e.id];
         orb_issue(p.m, p.qfin, e.local, e.N, dst, bar);
     }
-    __device__ void compute(int it, const T *src)
+    __device__ void compute(int it, T *src)
     {
         const RingMeta<T> &e = meta[it];
         if (e.N < 0) return;

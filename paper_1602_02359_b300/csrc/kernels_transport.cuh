@@ -91,6 +91,32 @@ __device__ __forceinline__ unsigned row_bytes(int nx)
     return (unsigned)(((size_t)nx * sizeof(T) + 15) / 16 * 16);
 }
 
+// Shared-memory layout of a staged ring row: the nx values start kRingLead
+// values in (16-byte aligned for the bulk copies) and the row takes the
+// field pitch plus kRingPad values.  After a ring lands, ring_frame copies
+// its last kRingLead values in front of it and its first kRingTail values
+// behind it, so every stencil window of a thread (at most kRingLead cells
+// to the left of the ring, kRingTail to the right, or a window of up to
+// nx + kRingTail cells starting anywhere on the ring) is one contiguous run
+// of shared memory addressed at constant offsets from one base.
+constexpr int kRingLead = 4, kRingTail = 16, kRingPad = 32;
+__host__ __device__ __forceinline__ int ring_row(int pitch) { return pitch + kRingPad; }
+
+template <typename T>
+__device__ __forceinline__ void ring_frame(T *buf, int rows, int rp, int nx)
+{
+    constexpr int H = kRingLead + kRingTail;
+    for (int t = threadIdx.x; t < rows * H; t += blockDim.x) {
+        const int r = t / H, h = t - r * H;
+        const int x = h < kRingLead ? h - kRingLead : nx + (h - kRingLead);
+        int src = x % nx;
+        if (src < 0) src += nx;
+        T *row = buf + (size_t)r * rp + kRingLead;
+        row[x] = row[src];
+    }
+    __syncthreads();
+}
+
 // Per-iteration facts of a ring, computed by all threads in parallel before
 // the loop (so no FP64 division or member search sits on the loop's
 // critical path): the member and local ring (batched launches), the integer
@@ -123,7 +149,11 @@ __device__ __forceinline__ void ring_pipeline(Op &op, T *buf, size_t stride, uin
     unsigned uses[2] = {0u, 0u};
     for (int it = 0; it < K; it++) {
         const int b = it & 1;
-        if (threadIdx.x == 0 && it + 1 < K) op.issue(it + 1, buf + (size_t)(1 - b) * stride, &bar[1 - b]);
+        if (threadIdx.x == 0 && it + 1 < K) {
+            // the other buffer was last read and framed through the generic proxy
+            fence_proxy_async_smem();
+            op.issue(it + 1, buf + (size_t)(1 - b) * stride, &bar[1 - b]);
+        }
         const bool ok = __syncthreads_and(mbar_wait(&bar[b], uses[b] & 1u));
         uses[b]++;
         if (!ok) {
@@ -191,42 +221,46 @@ __device__ __forceinline__ void tx_v0(const MeshD &m, const double *v0, int ring
     lo = (T)(v0r - (double)hi);
 }
 
-// Thread 0: copies of ring `ring` of the X sweep's input into dst.
+// Thread 0: copies of ring `ring` of the X sweep's input into dst (row r of
+// the staging at dst + r * ring_row(pitch) + kRingLead).
 template <typename T>
 __device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int ring, T *dst, uint64_t *bar)
 {
     const TxRows r = tx_rows(m);
     const int j = ring % m.nyt, k = ring / m.nyt;
     const idx_t base = IX(m, 0, j, k);
-    const size_t pitch = (size_t)m.sj;
+    const size_t rp = (size_t)ring_row(m.sj);
     const unsigned bytes = row_bytes<T>(m.nx);
+    dst += kRingLead;
     mbar_expect_tx(bar, bytes * (unsigned)r.n);
     bulk_load(dst, in.rho + base, bytes, bar);
-    if (r.rE >= 0) bulk_load(dst + r.rE * pitch, in.e + base, bytes, bar);
-    bulk_load(dst + r.rVX * pitch, in.vx + base, bytes, bar);
+    if (r.rE >= 0) bulk_load(dst + r.rE * rp, in.e + base, bytes, bar);
+    bulk_load(dst + r.rVX * rp, in.vx + base, bytes, bar);
     if (r.rVY >= 0) {
-        bulk_load(dst + r.rVY * pitch, in.vy + base, bytes, bar);
-        bulk_load(dst + (r.rVY + 1) * pitch, in.vy + base + m.sj, bytes, bar);
+        bulk_load(dst + r.rVY * rp, in.vy + base, bytes, bar);
+        bulk_load(dst + (r.rVY + 1) * rp, in.vy + base + m.sj, bytes, bar);
     }
     if (r.rVZ >= 0) {
-        bulk_load(dst + r.rVZ * pitch, in.vz + base, bytes, bar);
-        bulk_load(dst + (r.rVZ + 1) * pitch, in.vz + base + m.sk, bytes, bar);
+        bulk_load(dst + r.rVZ * rp, in.vz + base, bytes, bar);
+        bulk_load(dst + (r.rVZ + 1) * rp, in.vz + base + m.sk, bytes, bar);
     }
 }
 
 template <typename T, int C>
-__device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &out, int ring,
-                                           const T *sm, T v0hi, T v0lo, T dt)
+__device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &out, int ring, T *buf,
+                                           T v0hi, T v0lo, T dt)
 {
-    const int nx = m.nx, nq = out.nq, pitch = (int)m.sj;
+    const int nx = m.nx, nq = out.nq, rp = ring_row(m.sj);
+    const TxRows rw = tx_rows(m);
+    ring_frame(buf, rw.n, rp, nx);
+    const T *sm = buf + kRingLead;   // cell i of staged row r: sm[r * rp + i], -kRingLead <= i < nx + kRingTail
     const int j = ring % m.nyt, k = ring / m.nyt;
     const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
     const idx_t base = IX(m, 0, j, k);
     const bool adi = !m.iso;
     const bool sweep = active && m.hasX;
-    const TxRows rw = tx_rows(m);
     const T R = tb.R[ring], w = R * R * tb.omega, fz = tb.fz[ring];
-    const T *Rho = sm, *Vx = sm + (size_t)rw.rVX * pitch;
+    const T *Rho = sm, *Vx = sm + (size_t)rw.rVX * rp;
     // ratio of quantity q to the density at cell i, as scale * row[i + off] +
     // shift (or e / rho), for the order rho, e, Pi-x, Pi+x, Pi-y, Pi+y,
     // Pi-z, Pi+z of the present components
@@ -239,24 +273,24 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
         if (q == 0) return {Rho, 0, 0, T(1), T(0)};
         int o = q - 1;
         if (adi) {
-            if (o == 0) return {sm + (size_t)rw.rE * pitch, 0, 1, T(1), T(0)};
+            if (o == 0) return {sm + (size_t)rw.rE * rp, 0, 1, T(1), T(0)};
             o -= 1;
         }
         if (o == 0) return {Vx, 0, 0, R, w};
         if (o == 1) return {Vx, 1, 0, R, w};
         if (m.hasY) {
-            if (o == 2) return {sm + (size_t)rw.rVY * pitch, 0, 0, T(1), T(0)};
-            if (o == 3) return {sm + (size_t)(rw.rVY + 1) * pitch, 0, 0, T(1), T(0)};
+            if (o == 2) return {sm + (size_t)rw.rVY * rp, 0, 0, T(1), T(0)};
+            if (o == 3) return {sm + (size_t)(rw.rVY + 1) * rp, 0, 0, T(1), T(0)};
             o -= 2;
         }
-        if (o == 2) return {sm + (size_t)rw.rVZ * pitch, 0, 0, fz, T(0)};
-        return {sm + (size_t)(rw.rVZ + 1) * pitch, 0, 0, fz, T(0)};
+        if (o == 2) return {sm + (size_t)rw.rVZ * rp, 0, 0, fz, T(0)};
+        return {sm + (size_t)(rw.rVZ + 1) * rp, 0, 0, fz, T(0)};
     };
     if (!sweep) {
         for (int q = 0; q < nq; q++) {
             const RatioSpec sp = spec(q);
             for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-                const T v = sp.row[wrapi(i + sp.off, nx)];
+                const T v = sp.row[i + sp.off];
                 out.q[q][base + i] = q == 0 ? v : (sp.div ? v : Rho[i] * (sp.a * v + sp.b));
             }
         }
@@ -270,20 +304,21 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     const int cnt = min(C, nx - i0);
     T vf[C + 1], F0[C + 1];
 #pragma unroll
-    for (int u = 0; u <= C; u++) vf[u] = sub_split(Vx[wrapi(i0 + u, nx)], v0hi, v0lo);
+    for (int u = 0; u <= C; u++) vf[u] = sub_split(Vx[i0 + u], v0hi, v0lo);
     T rho[C + 4];
 #pragma unroll
-    for (int s = 0; s < C + 4; s++) rho[s] = Rho[wrapi(i0 - 2 + s, nx)];
+    for (int s = 0; s < C + 4; s++) rho[s] = Rho[i0 - 2 + s];
     // unrolled over the largest quantity count: every row and output pointer
     // index is then a compile-time constant
     #pragma unroll
     for (int q = 0; q < 8; q++) {
         if (q >= nq) break;
         const RatioSpec sp = spec(q);
+        const T *win = sp.row + (i0 - 2 + sp.off);
         T a[C + 4];   // ratios of cells i0-2 .. i0+C+1
 #pragma unroll
         for (int s = 0; s < C + 4; s++) {
-            const T v = sp.row[wrapi(i0 - 2 + s + sp.off, nx)];
+            const T v = win[s];
             a[s] = sp.div ? v / rho[s] : sp.a * v + sp.b;
         }
         T sl[C + 2];  // van Leer slopes of cells i0-1 .. i0+C
@@ -335,8 +370,9 @@ __device__ __forceinline__ void orb_prepare(const MeshD &m, const Tab<T> &tb, co
     if (Nm == 0 && xs == T(0)) Nm = -1;
 }
 
-// Thread 0: copies of the nq rows of active ring r into dst, or a plain
-// arrive when the ring needs no work (Nm < 0).
+// Thread 0: copies of the nq rows of active ring r into dst (row q at
+// dst + q * ring_row(pitch) + kRingLead), or a plain arrive when the ring
+// needs no work (Nm < 0).
 template <typename T>
 __device__ __forceinline__ void orb_issue(const MeshD &m, const QSet<T> &qs, int r, int Nm, T *dst, uint64_t *bar)
 {
@@ -347,9 +383,10 @@ __device__ __forceinline__ void orb_issue(const MeshD &m, const QSet<T> &qs, int
     const int ny = m.j1 - m.j0;
     const int j = m.j0 + r % ny, k = m.k0 + r / ny;
     const idx_t base = IX(m, 0, j, k);
+    const size_t rp = (size_t)ring_row(m.sj);
     const unsigned bytes = row_bytes<T>(m.nx);
     mbar_expect_tx(bar, bytes * (unsigned)qs.nq);
-    for (int q = 0; q < qs.nq; q++) bulk_load(dst + (size_t)q * m.sj, qs.q[q] + base, bytes, bar);
+    for (int q = 0; q < qs.nq; q++) bulk_load(dst + kRingLead + q * rp, qs.q[q] + base, bytes, bar);
 }
 
 // Upwind PPA value through each of a thread's C+1 faces (Sec. 3.4.1, Eqs.
@@ -384,25 +421,32 @@ __device__ __forceinline__ void ppa_face_values(const T *a, const T *qr, T xi, T
 }
 
 template <typename T, int C>
-__device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, int r,
-                                            const T *sm, int Nm, T xsT, T vR, T dtT)
+__device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, int r, T *buf,
+                                            int Nm, T xsT, T vR, T dtT)
 {
     if (Nm < 0) return;
-    const int nx = m.nx, nq = qs.nq, pitch = (int)m.sj;
+    const int nx = m.nx, nq = qs.nq, rp = ring_row(m.sj);
+    ring_frame(buf, nq, rp, nx);
+    const T *sm = buf + kRingLead;
     const int ny = m.j1 - m.j0;
     const int j = m.j0 + r % ny, k = m.k0 + r / ny;
     const int ring = k * m.nyt + j;
     const idx_t base = IX(m, 0, j, k);
     // cell i after the shift holds the staged cell i - N
-    auto at = [&](int q, int i) -> T { return sm[(size_t)q * pitch + wrapi(i - Nm, nx)]; };
     if (xsT == T(0)) {   // a pure shift
         for (int q = 0; q < nq; q++)
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) qs.q[q][base + i] = at(q, i);
+            for (int i = threadIdx.x; i < nx; i += blockDim.x)
+                qs.q[q][base + i] = sm[(size_t)q * rp + wrapi(i - Nm, nx)];
         return;
     }
     const int i0 = threadIdx.x * C;
     if (i0 >= nx) return;
     const int cnt = min(C, nx - i0);
+    // the thread's window, cells i0-3 .. i0+C+2 after the shift, is the
+    // staged run starting at cell (i0 - 3 - N) mod nx (framed rows: no wrap)
+    int b = (i0 - 3 - Nm) % nx;
+    if (b < 0) b += nx;
+    const T *win = sm + b;
     const T S = tb.sx[ring];
     const T dtVi = dtT * tb.vinv[ring];
     const bool pos = xsT >= T(0);
@@ -411,7 +455,7 @@ __device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, co
     T rinv[C + 6], rho[C + 6];
 #pragma unroll
     for (int s = 0; s < C + 6; s++) {
-        rho[s] = at(0, wrapi(i0 - 3 + s, nx));
+        rho[s] = win[s];
         rinv[s] = T(1) / rho[s];
     }
     T F0[C + 1];
@@ -420,9 +464,10 @@ __device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, co
     #pragma unroll
     for (int q = 0; q < 8; q++) {
         if (q >= nq) break;
+        const T *wq = win + (size_t)q * rp;
         T a[C + 6];   // ratios of cells i0-3 .. i0+C+2
 #pragma unroll
-        for (int s = 0; s < C + 6; s++) a[s] = q == 0 ? rho[s] : at(q, wrapi(i0 - 3 + s, nx)) * rinv[s];
+        for (int s = 0; s < C + 6; s++) a[s] = q == 0 ? rho[s] : wq[s] * rinv[s];
         T dm[C + 4];  // Eq. 34 slopes of cells i0-2 .. i0+C+1
 #pragma unroll
         for (int s = 0; s < C + 4; s++) dm[s] = ppa_dm(a[s], a[s + 1], a[s + 2]);
@@ -440,7 +485,7 @@ __device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, co
         }
 #pragma unroll
         for (int u = 0; u < C; u++)
-            if (u < cnt) qs.q[q][base + i0 + u] = at(q, i0 + u) - dtVi * (F[u + 1] - F[u]);
+            if (u < cnt) qs.q[q][base + i0 + u] = wq[3 + u] - dtVi * (F[u + 1] - F[u]);
     }
 }
 
@@ -462,7 +507,7 @@ struct TxOp {
         tx_v0(m, v0, ring, meta[it].a, meta[it].b);
     }
     __device__ void issue(int it, T *dst, uint64_t *bar) { tx_issue(m, in, meta[it].local, dst, bar); }
-    __device__ void compute(int it, const T *src)
+    __device__ void compute(int it, T *src)
     {
         tx_compute<T, C>(m, tb, out, meta[it].local, src, meta[it].a, meta[it].b, dt);
     }
@@ -484,7 +529,7 @@ struct OrbOp {
         orb_prepare(m, tb, v0, sc, r, meta[it].N, meta[it].a, meta[it].b);
     }
     __device__ void issue(int it, T *dst, uint64_t *bar) { orb_issue(m, qs, meta[it].local, meta[it].N, dst, bar); }
-    __device__ void compute(int it, const T *src)
+    __device__ void compute(int it, T *src)
     {
         const RingMeta<T> &e = meta[it];
         orb_compute<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
@@ -583,7 +628,7 @@ static RingShape ring_shape(int nx, int rows, int pitch)
     RingShape rs{};
     const int C = ring_chunk(nx);
     rs.threads = C ? ((nx + C - 1) / C + 31) / 32 * 32 : 0;
-    rs.stride = rows * pitch;
+    rs.stride = rows * ring_row(pitch);
     rs.smem = 2 * (size_t)rs.stride * sizeof(T);
     return rs;
 }
