@@ -348,12 +348,12 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     k_cfl_exact<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_exact");
     // cell 7
-    k_substep1<T><<<cg, cb, 0, s>>>(m, P.tb, P.A, P.VB, P.sc); MARK("substep1");
-    k_artvisc<T><<<cg, cb, 0, s>>>(m, P.tb, P.VB, P.A, P.sc); MARK("artvisc");
+    launch_source<T>(SRC_SUB1, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("substep1");
+    launch_source<T>(SRC_AV, m, cg, cb, s, P.tb, P.VB, P.A, P.tau, P.sc); MARK("artvisc");
     if (m.has_nu) {
         // stresses once into the scratch momenta of set B (unused until the transport step)
-        k_visc_tau<T><<<tau_grid(m, c->cell_bs), cb, 0, s>>>(m, P.tb, P.A, P.tau, P.sc); MARK("visc_tau");
-        k_visc_apply<T><<<cg, cb, 0, s>>>(m, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
+        launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_tau");
+        launch_source<T>(SRC_VAPPLY, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
     }
     // cell 9
     if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_y9"); }
@@ -871,20 +871,23 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         // the screening launch fills the per-step planet angle tables
         k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
                                                       c->nrings_active);
-        k_substep1<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, A, VB, c->sc);
+        launch_source<T>(SRC_SUB1, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB,
+                         QSet<T>{}, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
     case 3:
         if ((rc = copyv(b.vB, va))) return rc;
-        k_artvisc<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, VB, A, c->sc);
+        launch_source<T>(SRC_AV, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, VB, A,
+                         QSet<T>{}, c->sc);
         break;
     case 4: {
         if (!m.has_nu) break;
         QSet<T> tau{};
         for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
         tau.nq = 6;
-        k_visc_tau<T><<<tau_grid(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, A, tau, c->sc);
-        k_visc_apply<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, A, VB, tau, c->sc);
+        launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB, tau, c->sc);
+        launch_source<T>(SRC_VAPPLY, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB, tau,
+                         c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
         break;
     }

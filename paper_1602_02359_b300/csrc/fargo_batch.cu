@@ -79,7 +79,7 @@ constexpr int kCellsPerThread = 16;
 // Register budgets: 40 per thread (six 256-thread blocks per SM) for every
 // phase but the viscous update, which gets 48 (five blocks); the few
 // spills this costs are cheaper than the occupancy larger budgets lose.
-template <typename T, int PH>
+template <typename T, int PH, class F>
 __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
@@ -97,10 +97,10 @@ __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const St
             j += m.j0;
             k += m.k0;
         }
-        if constexpr (PH == PH_SUB1) substep1_body(m, p.tb, p.A, p.VB, p.sc, (int)i, j, k);
-        else if constexpr (PH == PH_AV) artvisc_body(m, p.tb, p.VB, p.A, p.sc, (int)i, j, k);
-        else if constexpr (PH == PH_TAU) visc_tau_body(m, p.tb, p.A, p.tau, p.sc, (int)i, j, k);
-        else if constexpr (PH == PH_VAPPLY) visc_apply_body(m, p.tb, p.A, p.VB, p.tau, p.sc, (int)i, j, k);
+        if constexpr (PH == PH_SUB1) substep1_body<T, F>(m, p.tb, p.A, p.VB, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_AV) artvisc_body<T, F>(m, p.tb, p.VB, p.A, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_TAU) visc_tau_body<T, F>(m, p.tb, p.A, p.tau, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_VAPPLY) visc_apply_body<T, F>(m, p.tb, p.A, p.VB, p.tau, p.sc, (int)i, j, k);
         else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, (int)i, j, k);
         i += blockDim.x;
         while (i >= nx) {
@@ -398,14 +398,16 @@ static int batch_setup(fargo_batch *b)
     add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
     L = BLaunch{L_EXACT}; L.name = "cfl_exact";
     add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
+    // the source phases launch once per configuration class (cfg_of)
+    auto cfg = [](const fargo_ctx *c) { return cfg_of(c->m); };
     L = BLaunch{L_CELL}; L.arg = PH_SUB1; L.name = "substep1";
-    add_phase(b, L, all, one, cells);
+    add_phase(b, L, all, cfg, cells);
     L = BLaunch{L_CELL}; L.arg = PH_AV; L.name = "artvisc";
-    add_phase(b, L, all, one, cells);
+    add_phase(b, L, all, cfg, cells);
     L = BLaunch{L_CELL}; L.arg = PH_TAU; L.name = "visc_tau";
-    add_phase(b, L, hasNu, one, tau_cells);
+    add_phase(b, L, hasNu, cfg, tau_cells);
     L = BLaunch{L_CELL}; L.arg = PH_VAPPLY; L.name = "visc_apply";
-    add_phase(b, L, hasNu, one, cells);
+    add_phase(b, L, hasNu, cfg, cells);
     L = BLaunch{L_BC}; L.arg = 1; L.mode = 1; L.name = "bc_y9";
     add_phase(b, L, hasY, one, bcy);
     L = BLaunch{L_BC}; L.arg = 2; L.mode = 1; L.name = "bc_z9";
@@ -472,6 +474,17 @@ static int batch_setup(fargo_batch *b)
     return FARGO_OK;
 }
 
+template <typename T, class F>
+static void launch_cell_cfg(int ph, int nb, const StepPlan<T> *P, Group g, cudaStream_t s)
+{
+    switch (ph) {
+    case PH_SUB1: kb_cell<T, PH_SUB1, F><<<nb, 256, 0, s>>>(P, g); break;
+    case PH_AV: kb_cell<T, PH_AV, F><<<nb, 256, 0, s>>>(P, g); break;
+    case PH_TAU: kb_cell<T, PH_TAU, F><<<nb, 256, 0, s>>>(P, g); break;
+    default: kb_cell<T, PH_VAPPLY, F><<<nb, 256, 0, s>>>(P, g); break;
+    }
+}
+
 template <typename T>
 static void launch_ring(const BLaunch &x, const StepPlan<T> *P, cudaStream_t s)
 {
@@ -527,13 +540,10 @@ static int batch_enqueue(fargo_batch *b, cudaEvent_t *marks = nullptr)
         case L_SCREEN: kb_cfl_screen<T><<<nb, 256, 0, s>>>(P, g); break;
         case L_EXACT: kb_cfl_exact<T><<<nb, 256, 0, s>>>(P, g); break;
         case L_CELL:
-            switch (x.arg) {
-            case PH_SUB1: kb_cell<T, PH_SUB1><<<nb, 256, 0, s>>>(P, g); break;
-            case PH_AV: kb_cell<T, PH_AV><<<nb, 256, 0, s>>>(P, g); break;
-            case PH_TAU: kb_cell<T, PH_TAU><<<nb, 256, 0, s>>>(P, g); break;
-            case PH_VAPPLY: kb_cell<T, PH_VAPPLY><<<nb, 256, 0, s>>>(P, g); break;
-            default: kb_cell<T, PH_NEWVEL><<<nb, 256, 0, s>>>(P, g); break;
-            }
+            if (x.arg == PH_NEWVEL) kb_cell<T, PH_NEWVEL, CfgRun><<<nb, 256, 0, s>>>(P, g);
+            else if (x.key == CFG_DISK3D) launch_cell_cfg<T, CfgDisk3D>(x.arg, nb, P, g, s);
+            else if (x.key == CFG_DISK2D) launch_cell_cfg<T, CfgDisk2D>(x.arg, nb, P, g, s);
+            else launch_cell_cfg<T, CfgRun>(x.arg, nb, P, g, s);
             break;
         case L_TX:
         case L_ORB: launch_ring<T>(x, P, s); break;

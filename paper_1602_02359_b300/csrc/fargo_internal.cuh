@@ -72,6 +72,52 @@ struct Scal {
     float dtf;     // dt rounded to FP32, published with dt
 };
 
+// Mesh facts the per-cell source kernels branch on.  CfgRun reads them from
+// the mesh at run time; CfgDisk fixes them at compile time for a disk (the
+// azimuth and the radius present, a planet with the indirect term, the
+// star, artificial viscosity), which turns those uniform branches into
+// straight-line code.  cfg_of picks the class a mesh runs with.
+struct CfgRun {
+    __host__ __device__ static int geom(const MeshD &m) { return m.geom; }
+    __host__ __device__ static bool hasX(const MeshD &m) { return m.hasX; }
+    __host__ __device__ static bool hasY(const MeshD &m) { return m.hasY; }
+    __host__ __device__ static bool hasZ(const MeshD &m) { return m.hasZ; }
+    __host__ __device__ static bool iso(const MeshD &m) { return m.iso; }
+    __host__ __device__ static bool planet(const MeshD &m) { return m.has_planet; }
+    __host__ __device__ static bool indirect(const MeshD &m) { return m.indirect; }
+    __host__ __device__ static bool star(const MeshD &m) { return m.has_star; }
+    __host__ __device__ static bool av(const MeshD &m) { return m.has_av; }
+};
+template <int GEOM, bool Z, bool ISO>
+struct CfgDisk {
+    __host__ __device__ static constexpr int geom(const MeshD &) { return GEOM; }
+    __host__ __device__ static constexpr bool hasX(const MeshD &) { return true; }
+    __host__ __device__ static constexpr bool hasY(const MeshD &) { return true; }
+    __host__ __device__ static constexpr bool hasZ(const MeshD &) { return Z; }
+    __host__ __device__ static constexpr bool iso(const MeshD &) { return ISO; }
+    __host__ __device__ static constexpr bool planet(const MeshD &) { return true; }
+    __host__ __device__ static constexpr bool indirect(const MeshD &) { return true; }
+    __host__ __device__ static constexpr bool star(const MeshD &) { return true; }
+    __host__ __device__ static constexpr bool av(const MeshD &) { return true; }
+};
+typedef CfgDisk<SPH, true, false> CfgDisk3D;   // spherical, adiabatic
+typedef CfgDisk<CYL, false, true> CfgDisk2D;   // cylindrical, isothermal
+enum { CFG_RUN = 0, CFG_DISK3D = 1, CFG_DISK2D = 2 };
+
+template <class F>
+inline bool cfg_matches(const MeshD &m)
+{
+    return F::geom(m) == m.geom && F::hasX(m) == (m.hasX != 0) && F::hasY(m) == (m.hasY != 0) &&
+           F::hasZ(m) == (m.hasZ != 0) && F::iso(m) == (m.iso != 0) && F::planet(m) == (m.has_planet != 0) &&
+           F::indirect(m) == (m.indirect != 0) && F::star(m) == (m.has_star != 0) && F::av(m) == (m.has_av != 0);
+}
+inline int cfg_of(const MeshD &m)
+{
+    if (cfg_matches<CfgDisk3D>(m)) return CFG_DISK3D;
+    if (cfg_matches<CfgDisk2D>(m)) return CFG_DISK2D;
+    return CFG_RUN;
+}
+
 // The step in the field precision.
 template <typename T>
 __device__ __forceinline__ T step_dt(const Scal *sc);
@@ -79,6 +125,14 @@ template <>
 __device__ __forceinline__ double step_dt<double>(const Scal *sc) { return sc->dt; }
 template <>
 __device__ __forceinline__ float step_dt<float>(const Scal *sc) { return sc->dtf; }
+
+// a / b: IEEE division in FP64, the fast reciprocal-based division in FP32
+// (within 2 ulp for |b| below 2^126, and branch-free: the IEEE FP32 division
+// carries a slow-path branch).  Used where the quotient is an increment
+// (an acceleration, a slope), never where a state value is rebuilt every
+// step, since its error is not centred and would accumulate there.
+__device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
 
 // v - v0 for a field value v and an FP64 v0 split as v0 = hi + lo (hi, lo in
 // the field precision): (v - hi) is formed exactly with TwoSum, then lo is

@@ -22,10 +22,10 @@ __device__ __host__ __forceinline__ int tau_rows(const MeshD &m) { return m.j1 -
 __device__ __host__ __forceinline__ int tau_planes(const MeshD &m) { return m.k1 - m.k0 + (m.hasZ ? 1 : 0); }
 
 // Pressure from the equation of state (Eqs. eos1, eos2).
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ T pressure(const MeshD &m, const Tab<T> &tb, const Fld<T> &f, idx_t c, int ring)
 {
-    if (m.iso) {
+    if (F::iso(m)) {
         T cs = tb.cs[ring];
         return cs * cs * f.rho[c];
     }
@@ -38,7 +38,7 @@ __device__ __forceinline__ T pressure(const MeshD &m, const Tab<T> &tb, const Fl
 // from per-ring tables (R - a formed in FP64) and the per-step azimuth
 // tables, so the hot loop needs no FP64 arithmetic.  The star term, which has
 // no azimuthal dependence, enters through precomputed FP64 face gradients.
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i, int ring)
 {
     const T rm = tb.rma[ring];
@@ -46,7 +46,7 @@ __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i,
     T v;
     if (sizeof(T) == 8) v = -tb.pq / sqrt(d2);
     else v = -tb.pq * rsqrtf((float)d2);
-    if (m.indirect) v += tb.qar[ring] * tb.pc[i];
+    if (F::indirect(m)) v += tb.qar[ring] * tb.pc[i];
     return v;
 }
 
@@ -55,7 +55,7 @@ __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i,
 // (Eq. 20), potential gradient, centrifugal and geometric terms with the
 // four-face average of Eq. 12.  Jacobi: reads `in`, writes `out`.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
                                               const Scal *sc, int i, int j, int k)
 {
@@ -69,34 +69,34 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     const int ip = i + 1 == m.nx ? 0 : i + 1;
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
-        if (m.hasX && jact && kact) {
+        if (F::hasX(m) && jact && kact) {
             const idx_t cm = c - i + im;
             const T id = tb.ilenx[ring];
-            const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring);
-            T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
-            if (m.has_planet)
-                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, im, ring)) * id;
+            const T P0 = pressure<T, F>(m, tb, in, c, ring), Pm = pressure<T, F>(m, tb, in, cm, ring);
+            T acc = div_fast(T(-2) * (P0 - Pm) * id, in.rho[c] + in.rho[cm]);
+            if (F::planet(m))
+                acc -= (phi_planet<T, F>(m, tb, i, ring) - phi_planet<T, F>(m, tb, im, ring)) * id;
             v = v + dt * acc;
         }
         out.vx[c] = v;
     }
     if (k < m.nzt) {
         T v = in.vy[c];
-        if (m.hasY && j > m.j0 && j < m.j1 && kact) {
+        if (F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
             const idx_t cm = c - m.sj;
             const T id = tb.idyc[j];
-            const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, ring - 1);
-            T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
-            if (m.has_planet)
-                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, ring - 1)) * id;
-            if (m.has_star) acc -= tb.gphy[ring];
-            if (m.geom != CART) {
+            const T P0 = pressure<T, F>(m, tb, in, c, ring), Pm = pressure<T, F>(m, tb, in, cm, ring - 1);
+            T acc = div_fast(T(-2) * (P0 - Pm) * id, in.rho[c] + in.rho[cm]);
+            if (F::planet(m))
+                acc -= (phi_planet<T, F>(m, tb, i, ring) - phi_planet<T, F>(m, tb, i, ring - 1)) * id;
+            if (F::star(m)) acc -= tb.gphy[ring];
+            if (F::geom(m) != CART) {
                 const T Rj = tb.R[ring], Rm = tb.R[ring - 1];
                 const idx_t cp = c - i + ip, cmp = cm - i + ip;
                 const T vt = T(0.25) * ((in.vx[c] + Rj * om) + (in.vx[cp] + Rj * om) + (in.vx[cm] + Rm * om) +
                                         (in.vx[cmp] + Rm * om));
                 T cen = vt * vt;
-                if (m.geom == SPH && m.hasZ) {
+                if (F::geom(m) == SPH && F::hasZ(m)) {
                     const T vth = T(0.25) * (in.vz[c] + in.vz[c + m.sk] + in.vz[cm] + in.vz[cm + m.sk]);
                     cen += vth * vth;
                 }
@@ -106,18 +106,18 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
         }
         out.vy[c] = v;
     }
-    if (m.hasZ && j < m.nyt) {
+    if (F::hasZ(m) && j < m.nyt) {
         T v = in.vz[c];
         if (k > m.k0 && k < m.k1 && jact) {
             const idx_t cm = c - m.sk;
             const int rm = ring - m.nyt;
             const T id = tb.idzc[ring];
-            const T P0 = pressure(m, tb, in, c, ring), Pm = pressure(m, tb, in, cm, rm);
-            T acc = T(-2) * (P0 - Pm) * id / (in.rho[c] + in.rho[cm]);
-            if (m.has_planet)
-                acc -= (phi_planet(m, tb, i, ring) - phi_planet(m, tb, i, rm)) * id;
-            if (m.has_star) acc -= tb.gphz[ring];
-            if (m.geom == SPH) {
+            const T P0 = pressure<T, F>(m, tb, in, c, ring), Pm = pressure<T, F>(m, tb, in, cm, rm);
+            T acc = div_fast(T(-2) * (P0 - Pm) * id, in.rho[c] + in.rho[cm]);
+            if (F::planet(m))
+                acc -= (phi_planet<T, F>(m, tb, i, ring) - phi_planet<T, F>(m, tb, i, rm)) * id;
+            if (F::star(m)) acc -= tb.gphz[ring];
+            if (F::geom(m) == SPH) {
                 const T Rk = tb.R[ring], Rm = tb.R[rm];
                 const idx_t cp = c - i + ip, cmp = cm - i + ip;
                 const T vt = T(0.25) * ((in.vx[c] + Rk * om) + (in.vx[cp] + Rk * om) + (in.vx[cm] + Rm * om) +
@@ -139,20 +139,20 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
 // velocities.  q of a neighbour is recomputed locally instead of stored, so
 // the two passes of the paper become one kernel without races.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ T qvisc(T c2, T rho, T dv)
 {
     return dv < T(0) ? c2 * rho * dv * dv : T(0);
 }
 
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
                                              const Scal *sc, int i, int j, int k)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     const T c2 = tb.cq2;
-    const bool av = m.has_av != 0;
+    const bool av = F::av(m) != 0;
     const idx_t c = IX(m, i, j, k);
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
@@ -165,51 +165,51 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     T vxl = 0, vyl = 0, vzl = 0;
     if (j < m.nyt && k < m.nzt) {
         T v = vx[c];
-        if (av && m.hasX && jact && kact) {
+        if (av && F::hasX(m) && jact && kact) {
             const idx_t cm = c - i + im, cp = c - i + ip;
             const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
             const T qm = qvisc(c2, rho[cm], vx[c] - vx[cm]);
-            v -= dt * T(2) * (q0 - qm) * tb.ilenx[ring] / (rho[c] + rho[cm]);
+            v -= div_fast(dt * T(2) * (q0 - qm) * tb.ilenx[ring], rho[c] + rho[cm]);
         }
         out.vx[c] = v;
         vxl = v;
     }
     if (k < m.nzt) {
         T v = vy[c];
-        if (av && m.hasY && j > m.j0 && j < m.j1 && kact) {
+        if (av && F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
             const idx_t cm = c - sj;
             const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
             const T qm = qvisc(c2, rho[cm], vy[c] - vy[cm]);
-            v -= dt * T(2) * (q0 - qm) * tb.idyc[j] / (rho[c] + rho[cm]);
+            v -= div_fast(dt * T(2) * (q0 - qm) * tb.idyc[j], rho[c] + rho[cm]);
         }
         out.vy[c] = v;
         vyl = v;
     }
-    if (m.hasZ && j < m.nyt) {
+    if (F::hasZ(m) && j < m.nyt) {
         T v = vz[c];
         if (av && k > m.k0 && k < m.k1 && jact) {
             const idx_t cm = c - sk;
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
             const T qm = qvisc(c2, rho[cm], vz[c] - vz[cm]);
-            v -= dt * T(2) * (q0 - qm) * tb.idzc[ring] / (rho[c] + rho[cm]);
+            v -= div_fast(dt * T(2) * (q0 - qm) * tb.idzc[ring], rho[c] + rho[cm]);
         }
         out.vz[c] = v;
         vzl = v;
     }
-    if (m.iso || !(jact && kact)) return;
+    if (F::iso(m) || !(jact && kact)) return;
     // heating by the artificial viscosity of the cell itself
     T e = in.e[c];
     T h = 0;
     if (av) {
-        if (m.hasX) {
+        if (F::hasX(m)) {
             const T dv = vx[c - i + ip] - vx[c];
             h += qvisc(c2, rho[c], dv) * dv * tb.ilenx[ring];
         }
-        if (m.hasY) {
+        if (F::hasY(m)) {
             const T dv = vy[c + sj] - vy[c];
             h += qvisc(c2, rho[c], dv) * dv * tb.idy[j];
         }
-        if (m.hasZ) {
+        if (F::hasZ(m)) {
             const T dv = vz[c + sk] - vz[c];
             h += qvisc(c2, rho[c], dv) * dv * tb.ilenz[ring];
         }
@@ -217,32 +217,32 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     e -= dt * h;
     // post-viscosity velocities on the upper faces (owned by the neighbours)
     T div = 0;
-    if (m.hasX) {
+    if (F::hasX(m)) {
         const idx_t cp = c - i + ip, cpp = c - i + ipp;
         T vxu = vx[cp];
         if (av) {
             const T qp = qvisc(c2, rho[cp], vx[cpp] - vx[cp]);
             const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
-            vxu -= dt * T(2) * (qp - q0) * tb.ilenx[ring] / (rho[cp] + rho[c]);
+            vxu -= div_fast(dt * T(2) * (qp - q0) * tb.ilenx[ring], rho[cp] + rho[c]);
         }
         div += tb.sx[ring] * (vxu - vxl);
     }
     const int fr = k * (m.nyt + 1) + j;
-    if (m.hasY) {
+    if (F::hasY(m)) {
         T vyu = vy[c + sj];
         if (av && j + 1 < m.j1) {
             const T qp = qvisc(c2, rho[c + sj], vy[c + 2 * sj] - vy[c + sj]);
             const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
-            vyu -= dt * T(2) * (qp - q0) * tb.idyc[j + 1] / (rho[c + sj] + rho[c]);
+            vyu -= div_fast(dt * T(2) * (qp - q0) * tb.idyc[j + 1], rho[c + sj] + rho[c]);
         }
         div += tb.sy[fr + 1] * vyu - tb.sy[fr] * vyl;
     }
-    if (m.hasZ) {
+    if (F::hasZ(m)) {
         T vzu = vz[c + sk];
         if (av && k + 1 < m.k1) {
             const T qp = qvisc(c2, rho[c + sk], vz[c + 2 * sk] - vz[c + sk]);
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
-            vzu -= dt * T(2) * (qp - q0) * tb.idzc[ring + m.nyt] / (rho[c + sk] + rho[c]);
+            vzu -= div_fast(dt * T(2) * (qp - q0) * tb.idzc[ring + m.nyt], rho[c + sk] + rho[c]);
         }
         div += tb.sz[fr + (m.nyt + 1)] * vzu - tb.sz[fr] * vzl;
     }
@@ -258,7 +258,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
 // Each thread recomputes the stresses its faces need from the velocities at
 // sub-step entry (Jacobi), so no stress array is stored.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, class F = CfgRun>
 struct ViscCtx {
     const MeshD &m;
     const Tab<T> &tb;
@@ -274,9 +274,9 @@ struct ViscCtx {
         const idx_t c = at(i, j, k);
         const int ring = k * m.nyt + j, fr = k * (m.nyt + 1) + j;
         T f = 0;
-        if (m.hasX) f += tb.sx[ring] * (vx[at(i + 1, j, k)] - vx[c]);
-        if (m.hasY) f += tb.sy[fr + 1] * vy[c + m.sj] - tb.sy[fr] * vy[c];
-        if (m.hasZ) f += tb.sz[fr + m.nyt + 1] * vz[c + m.sk] - tb.sz[fr] * vz[c];
+        if (F::hasX(m)) f += tb.sx[ring] * (vx[at(i + 1, j, k)] - vx[c]);
+        if (F::hasY(m)) f += tb.sy[fr + 1] * vy[c + m.sj] - tb.sy[fr] * vy[c];
+        if (F::hasZ(m)) f += tb.sz[fr + m.nyt + 1] * vz[c + m.sk] - tb.sz[fr] * vz[c];
         return f * tb.vinv[ring];
     }
     // diagonal components at the centre of cell (i,j,k)
@@ -287,14 +287,14 @@ struct ViscCtx {
         const T dv = divv(i, j, k);
         const T rn = rho[c] * nu(j, k);
         const T dxx = (vx[at(i + 1, j, k)] - vx[c]) * tb.ilenx[ring];
-        const T dyy = m.hasY ? (vy[c + m.sj] - vy[c]) * tb.idy[j] : T(0);
-        const T dzz = m.hasZ ? (vz[c + m.sk] - vz[c]) * tb.ilenz[ring] : T(0);
+        const T dyy = F::hasY(m) ? (vy[c + m.sj] - vy[c]) * tb.idy[j] : T(0);
+        const T dzz = F::hasZ(m) ? (vz[c + m.sk] - vz[c]) * tb.ilenz[ring] : T(0);
         const T tw = T(2.0 / 3.0) * dv;
-        if (m.geom == CART) {
+        if (F::geom(m) == CART) {
             txx = -rn * (T(2) * dxx - tw);
             tyy = -rn * (T(2) * dyy - tw);
             tzz = -rn * (T(2) * dzz - tw);
-        } else if (m.geom == CYL) {
+        } else if (F::geom(m) == CYL) {
             const T ir = tb.iym[j];
             const T vr = T(0.5) * (vy[c] + vy[c + m.sj]);
             txx = -rn * (T(2) * (dxx + vr * ir) - tw);
@@ -317,9 +317,9 @@ struct ViscCtx {
         const T nb = T(0.5) * (nu(j, k) + nu(j - 1, k));
         const T dvx_dy = (vx[c] - vx[c - m.sj]) * tb.idyc[j];
         T t;
-        if (m.geom == CART) {
+        if (F::geom(m) == CART) {
             t = (vy[c] - vy[cm]) * tb.idx + dvx_dy;
-        } else if (m.geom == CYL) {
+        } else if (F::geom(m) == CYL) {
             const T irf = tb.iyf[j];
             t = dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) * irf + (vy[c] - vy[cm]) * (irf * tb.idx);
         } else {
@@ -336,14 +336,14 @@ struct ViscCtx {
         const T nb = T(0.5) * (nu(j, k) + nu(j, k - 1));
         const T idzm = tb.idzm[k];
         T t;
-        if (m.geom == CART) {
+        if (F::geom(m) == CART) {
             t = (vz[c] - vz[cm]) * tb.idx + (vx[c] - vx[c - m.sk]) * idzm;
-        } else if (m.geom == CYL) {
+        } else if (F::geom(m) == CYL) {
             t = (vx[c] - vx[c - m.sk]) * idzm + (vz[c] - vz[cm]) * (tb.iym[j] * tb.idx);
         } else {
             const T ir = tb.iym[j], sf = tb.szf[k];
             t = sf * ir * (vx[c] * tb.iszm[k] - vx[c - m.sk] * tb.iszm[k - 1]) * idzm +
-                (vz[c] - vz[cm]) * (ir * tb.idx) / sf;
+                div_fast((vz[c] - vz[cm]) * (ir * tb.idx), sf);
         }
         return -rb * nb * t;
     }
@@ -355,7 +355,7 @@ struct ViscCtx {
         const T nb = T(0.25) * (nu(j, k) + nu(j - 1, k) + nu(j, k - 1) + nu(j - 1, k - 1));
         const T idzm = tb.idzm[k];
         T t;
-        if (m.geom == SPH) {
+        if (F::geom(m) == SPH) {
             const T irf = tb.iyf[j];
             t = (vz[c] - vz[c - m.sj]) * tb.idyc[j] - T(0.5) * (vz[c] + vz[c - m.sj]) * irf +
                 (vy[c] - vy[c - m.sk]) * (irf * idzm);
@@ -366,7 +366,7 @@ struct ViscCtx {
     }
 };
 
-template <typename T, typename S>
+template <typename T, class F, typename S>
 __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const Fld<T> &out,
                                            T dt, int i, int j, int k, const S &V)
 {
@@ -382,69 +382,69 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i - 1, j, k, b0, b1, b2);
             T f = 0;
-            if (m.geom == CART) {
+            if (F::geom(m) == CART) {
                 f += (a0 - b0) * idx;
-                if (m.hasY) f += (V.txy(i, j + 1, k) - V.txy(i, j, k)) * tb.idy[j];
-                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) * tb.idz[k];
-            } else if (m.geom == CYL) {
+                if (F::hasY(m)) f += (V.txy(i, j + 1, k) - V.txy(i, j, k)) * tb.idy[j];
+                if (F::hasZ(m)) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) * tb.idz[k];
+            } else if (F::geom(m) == CYL) {
                 const T ir = tb.iym[j];
-                if (m.hasY)
+                if (F::hasY(m))
                     f += (tb.yf[j + 1] * tb.yf[j + 1] * V.txy(i, j + 1, k) - tb.yf[j] * tb.yf[j] * V.txy(i, j, k)) *
                          (ir * ir * tb.idy[j]);
                 f += (a0 - b0) * (ir * idx);
-                if (m.hasZ) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) * tb.idz[k];
+                if (F::hasZ(m)) f += (V.txz(i, j, k + 1) - V.txz(i, j, k)) * tb.idz[k];
             } else {
                 const T ir = tb.iym[j], isn = tb.iszm[k], ct = tb.cotzm[k];
                 T ty0 = 0, ty1 = 0, tz0 = 0, tz1 = 0;
-                if (m.hasY) {
+                if (F::hasY(m)) {
                     ty0 = V.txy(i, j, k);
                     ty1 = V.txy(i, j + 1, k);
                     f += (tb.yf[j + 1] * tb.yf[j + 1] * ty1 - tb.yf[j] * tb.yf[j] * ty0) * (ir * ir * tb.idy[j]);
                 }
-                if (m.hasZ) {
+                if (F::hasZ(m)) {
                     tz0 = V.txz(i, j, k);
                     tz1 = V.txz(i, j, k + 1);
                     f += (tz1 - tz0) * (ir * tb.idz[k]);
                 }
                 f += (a0 - b0) * (ir * isn * idx);
-                if (m.hasY) f += T(0.5) * (ty0 + ty1) * ir;
-                if (m.hasZ) f += T(2) * T(0.5) * (tz0 + tz1) * ct * ir;
+                if (F::hasY(m)) f += T(0.5) * (ty0 + ty1) * ir;
+                if (F::hasZ(m)) f += T(2) * T(0.5) * (tz0 + tz1) * ct * ir;
             }
-            v = v - T(2) * dt * f / (rho[c] + rho[cm]);
+            v = v - div_fast(T(2) * dt * f, rho[c] + rho[cm]);
         }
         out.vx[c] = v;
     }
     if (k < m.nzt) {
         T v = in.vy[c];
-        if (m.hasY && j > m.j0 && j < m.j1 && kact) {
+        if (F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
             const idx_t cjm = c - m.sj;
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
             V.diag(i, j - 1, k, b0, b1, b2);
             T f = 0;
-            if (m.geom == CART) {
+            if (F::geom(m) == CART) {
                 f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) * idx;
                 f += (a1 - b1) * tb.idyc[j];
-                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) * tb.idz[k];
-            } else if (m.geom == CYL) {
+                if (F::hasZ(m)) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) * tb.idz[k];
+            } else if (F::geom(m) == CYL) {
                 const T irf = tb.iyf[j];
                 f += (tb.ym[j] * a1 - tb.ym[j - 1] * b1) * (irf * tb.idyc[j]);
                 f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) * (irf * idx);
                 f -= T(0.5) * (a0 + b0) * irf;
-                if (m.hasZ) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) * tb.idz[k];
+                if (F::hasZ(m)) f += (V.tyz(i, j, k + 1) - V.tyz(i, j, k)) * tb.idz[k];
             } else {
                 const T irf = tb.iyf[j], isn = tb.iszm[k];
                 f += (tb.ym[j] * tb.ym[j] * a1 - tb.ym[j - 1] * tb.ym[j - 1] * b1) * (irf * irf * tb.idyc[j]);
-                if (m.hasZ)
+                if (F::hasZ(m))
                     f += (V.tyz(i, j, k + 1) * tb.szf[k + 1] - V.tyz(i, j, k) * tb.szf[k]) * (irf * isn * tb.idz[k]);
                 f += (V.txy(i + 1, j, k) - V.txy(i, j, k)) * (irf * isn * idx);
                 f -= T(0.5) * (a2 + b2 + a0 + b0) * irf;
             }
-            v = v - T(2) * dt * f / (rho[c] + rho[cjm]);
+            v = v - div_fast(T(2) * dt * f, rho[c] + rho[cjm]);
         }
         out.vy[c] = v;
     }
-    if (m.hasZ && j < m.nyt) {
+    if (F::hasZ(m) && j < m.nyt) {
         T v = in.vz[c];
         if (k > m.k0 && k < m.k1 && jact) {
             const idx_t ckm = c - m.sk;
@@ -453,18 +453,18 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
             V.diag(i, j, k - 1, b0, b1, b2);
             const T idzm = tb.idzm[k];
             T f = 0;
-            if (m.geom == CART) {
+            if (F::geom(m) == CART) {
                 f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) * idx;
-                if (m.hasY) f += (V.tyz(i, j + 1, k) - V.tyz(i, j, k)) * tb.idy[j];
+                if (F::hasY(m)) f += (V.tyz(i, j + 1, k) - V.tyz(i, j, k)) * tb.idy[j];
                 f += (a2 - b2) * idzm;
-            } else if (m.geom == CYL) {
+            } else if (F::geom(m) == CYL) {
                 const T ir = tb.iym[j];
-                if (m.hasY) f += (tb.yf[j + 1] * V.tyz(i, j + 1, k) - tb.yf[j] * V.tyz(i, j, k)) * (ir * tb.idy[j]);
+                if (F::hasY(m)) f += (tb.yf[j + 1] * V.tyz(i, j + 1, k) - tb.yf[j] * V.tyz(i, j, k)) * (ir * tb.idy[j]);
                 f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) * (ir * idx);
                 f += (a2 - b2) * idzm;
             } else {
-                const T ir = tb.iym[j], sf = tb.szf[k], isf = T(1) / sf, ctf = tb.cotzf[k];
-                if (m.hasY) {
+                const T ir = tb.iym[j], sf = tb.szf[k], isf = div_fast(T(1), sf), ctf = tb.cotzf[k];
+                if (F::hasY(m)) {
                     const T y1 = tb.yf[j + 1], y0 = tb.yf[j];
                     f += (y1 * y1 * y1 * V.tyz(i, j + 1, k) - y0 * y0 * y0 * V.tyz(i, j, k)) * (ir * ir * ir * tb.idy[j]);
                 }
@@ -472,14 +472,14 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
                 f += (V.txz(i + 1, j, k) - V.txz(i, j, k)) * (ir * isf * idx);
                 f -= T(0.5) * (a0 + b0) * ctf * ir;
             }
-            v = v - T(2) * dt * f / (rho[c] + rho[ckm]);
+            v = v - div_fast(T(2) * dt * f, rho[c] + rho[ckm]);
         }
         out.vz[c] = v;
     }
 }
 
 // Stresses read back from the arrays written by k_visc_tau.
-template <typename T>
+template <typename T, class F = CfgRun>
 struct TauArr {
     const MeshD &m;
     const T *xx, *yy, *zz, *xy, *xz, *yz;
@@ -492,7 +492,7 @@ struct TauArr {
         const idx_t o = at(i, j, k);
         a = xx[o];
         b = yy[o];
-        c = m.hasZ ? zz[o] : T(0);
+        c = F::hasZ(m) ? zz[o] : T(0);
     }
     __device__ T txy(int i, int j, int k) const { return xy[at(i, j, k)]; }
     __device__ T txz(int i, int j, int k) const { return xz[at(i, j, k)]; }
@@ -502,15 +502,15 @@ struct TauArr {
 // Pass 1: every stress component once, diagonal ones on active cells and
 // the edge ones on the edges that interior and boundary faces need
 // (rows j0..j1, planes k0..k1).
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ void visc_tau_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &tau,
                                               const Scal *sc, int i, int j, int k)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     // rows j0..j1, planes k0..k1 (the upper one only with that direction)
-    if (j < m.j0 || j > m.j1 - (m.hasY ? 0 : 1) || k < m.k0 || k > m.k1 - (m.hasZ ? 0 : 1)) return;
-    const ViscCtx<T> V(m, tb, in);
+    if (j < m.j0 || j > m.j1 - (F::hasY(m) ? 0 : 1) || k < m.k0 || k > m.k1 - (F::hasZ(m) ? 0 : 1)) return;
+    const ViscCtx<T, F> V(m, tb, in);
     const idx_t c = IX(m, i, j, k);
     const bool jin = j < m.j1, kin = k < m.k1;
     if (jin && kin) {
@@ -518,52 +518,77 @@ __device__ __forceinline__ void visc_tau_body(const MeshD &m, const Tab<T> &tb, 
         V.diag(i, j, k, a, b, d);
         tau.q[0][c] = a;
         tau.q[1][c] = b;
-        if (m.hasZ) tau.q[2][c] = d;
+        if (F::hasZ(m)) tau.q[2][c] = d;
     }
-    if (m.hasY && kin) tau.q[3][c] = V.txy(i, j, k);
-    if (m.hasZ && jin) tau.q[4][c] = V.txz(i, j, k);
-    if (m.hasY && m.hasZ) tau.q[5][c] = V.tyz(i, j, k);
+    if (F::hasY(m) && kin) tau.q[3][c] = V.txy(i, j, k);
+    if (F::hasZ(m) && jin) tau.q[4][c] = V.txz(i, j, k);
+    if (F::hasY(m) && F::hasZ(m)) tau.q[5][c] = V.tyz(i, j, k);
 }
 
 // Pass 2: the velocity update of Eqs. 75-77 from the stored stresses.
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ void visc_apply_body(const MeshD &m, const Tab<T> &tb, const Fld<T> &in,
                                                 const Fld<T> &out, const QSet<T> &tau, const Scal *sc, int i,
                                                 int j, int k)
 {
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
-    const TauArr<T> S{m, tau.q[0], tau.q[1], tau.q[2], tau.q[3], tau.q[4], tau.q[5]};
-    visc_apply(m, tb, in, out, dt, i, j, k, S);
+    const TauArr<T, F> S{m, tau.q[0], tau.q[1], tau.q[2], tau.q[3], tau.q[4], tau.q[5]};
+    visc_apply<T, F>(m, tb, in, out, dt, i, j, k, S);
 }
 
 // Single-instance wrappers: a 3D grid, x over the azimuth (blockDim.x
 // cells per block), y over the rows, z over the planes.
-template <typename T>
+template <typename T, class F = CfgRun>
 __global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.nx) substep1_body(m, tb, in, out, sc, i, blockIdx.y, blockIdx.z);
+    if (i < m.nx) substep1_body<T, F>(m, tb, in, out, sc, i, blockIdx.y, blockIdx.z);
 }
-template <typename T>
+template <typename T, class F = CfgRun>
 __global__ void __launch_bounds__(256) k_artvisc(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.nx) artvisc_body(m, tb, in, out, sc, i, blockIdx.y, blockIdx.z);
+    if (i < m.nx) artvisc_body<T, F>(m, tb, in, out, sc, i, blockIdx.y, blockIdx.z);
 }
 // grid rows and planes start at j0 and k0
-template <typename T>
+template <typename T, class F = CfgRun>
 __global__ void __launch_bounds__(256) k_visc_tau(MeshD m, Tab<T> tb, Fld<T> in, QSet<T> tau, const Scal *sc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.nx) visc_tau_body(m, tb, in, tau, sc, i, m.j0 + blockIdx.y, m.k0 + blockIdx.z);
+    if (i < m.nx) visc_tau_body<T, F>(m, tb, in, tau, sc, i, m.j0 + blockIdx.y, m.k0 + blockIdx.z);
 }
-template <typename T>
+template <typename T, class F = CfgRun>
 __global__ void __launch_bounds__(256) k_visc_apply(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, QSet<T> tau,
                                                     const Scal *sc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.nx) visc_apply_body(m, tb, in, out, tau, sc, i, blockIdx.y, blockIdx.z);
+    if (i < m.nx) visc_apply_body<T, F>(m, tb, in, out, tau, sc, i, blockIdx.y, blockIdx.z);
+}
+
+// Launches with the configuration class cfg_of(m) selects.
+template <typename T, class F>
+static void launch_source_cfg(int which, const MeshD &m, dim3 g, dim3 b, cudaStream_t s, const Tab<T> &tb,
+                              const Fld<T> &in, const Fld<T> &out, const QSet<T> &tau, const Scal *sc)
+{
+    switch (which) {
+    case 0: k_substep1<T, F><<<g, b, 0, s>>>(m, tb, in, out, sc); break;
+    case 1: k_artvisc<T, F><<<g, b, 0, s>>>(m, tb, in, out, sc); break;
+    case 2: k_visc_tau<T, F><<<g, b, 0, s>>>(m, tb, in, tau, sc); break;
+    default: k_visc_apply<T, F><<<g, b, 0, s>>>(m, tb, in, out, tau, sc); break;
+    }
+}
+enum { SRC_SUB1 = 0, SRC_AV = 1, SRC_TAU = 2, SRC_VAPPLY = 3 };
+// which: SRC_*; out is unused by SRC_TAU, tau by SRC_SUB1 and SRC_AV
+template <typename T>
+static void launch_source(int which, const MeshD &m, dim3 g, dim3 b, cudaStream_t s, const Tab<T> &tb,
+                          const Fld<T> &in, const Fld<T> &out, const QSet<T> &tau, const Scal *sc)
+{
+    switch (cfg_of(m)) {
+    case CFG_DISK3D: launch_source_cfg<T, CfgDisk3D>(which, m, g, b, s, tb, in, out, tau, sc); break;
+    case CFG_DISK2D: launch_source_cfg<T, CfgDisk2D>(which, m, g, b, s, tb, in, out, tau, sc); break;
+    default: launch_source_cfg<T, CfgRun>(which, m, g, b, s, tb, in, out, tau, sc); break;
+    }
 }
 
 }  // namespace fk

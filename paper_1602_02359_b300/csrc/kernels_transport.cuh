@@ -16,11 +16,6 @@ __device__ __forceinline__ T vl_slope(T qm, T q0, T qp, T dxm, T dxp)
     return dp * dm > T(0) ? T(2) * dp * dm / (dp + dm) : T(0);
 }
 
-// a / b: IEEE division in FP64, the fast reciprocal-based division in FP32
-// (within 2 ulp; the harmonic mean below keeps its operands away from the
-// range where the fast form degrades).
-__device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
-__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
 
 // The same slope with the inverse centre distances given.
 template <typename T>
