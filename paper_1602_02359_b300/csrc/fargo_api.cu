@@ -374,7 +374,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         launch_orb<T>(m, P.tb, P.qfin, P.v0, P.sc, P.nrings_active, c->orb_rs, s);
         MARK("orbital");
     }
-    k_newvel<T><<<cg, cb, 0, s>>>(m, P.tb, P.qfin, P.vsrc, P.A, P.sc, 0); MARK("newvel");
+    launch_newvel<T>(m, cg, cb, s, P.tb, P.qfin, P.vsrc, P.A, P.sc, 0); MARK("newvel");
 #undef MARK
     c->launches = nl;
     if (prof) prof->n = nl;
@@ -906,7 +906,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         break;
     }
     case 8:
-        k_newvel<T><<<cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), 0, s>>>(m, b.tab, qa, A, A, c->sc, 0);
+        launch_newvel<T>(m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, qa, A, A, c->sc, 0);
         break;
     case 9:
         if (m.fargo && m.hasX)

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const St
         else if constexpr (PH == PH_AV) artvisc_body<T, F>(m, p.tb, p.VB, p.A, p.sc, (int)i, j, k);
         else if constexpr (PH == PH_TAU) visc_tau_body<T, F>(m, p.tb, p.A, p.tau, p.sc, (int)i, j, k);
         else if constexpr (PH == PH_VAPPLY) visc_apply_body<T, F>(m, p.tb, p.A, p.VB, p.tau, p.sc, (int)i, j, k);
-        else newvel_body(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, (int)i, j, k);
+        else newvel_body<T, F>(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, (int)i, j, k);
         i += blockDim.x;
         while (i >= nx) {
             i -= nx;
@@ -398,7 +398,7 @@ static int batch_setup(fargo_batch *b)
     add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
     L = BLaunch{L_EXACT}; L.name = "cfl_exact";
     add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
-    // the source phases launch once per configuration class (cfg_of)
+    // the per-cell phases launch once per configuration class (cfg_of)
     auto cfg = [](const fargo_ctx *c) { return cfg_of(c->m); };
     L = BLaunch{L_CELL}; L.arg = PH_SUB1; L.name = "substep1";
     add_phase(b, L, all, cfg, cells);
@@ -422,7 +422,7 @@ static int batch_setup(fargo_batch *b)
     add_phase(b, L, [](const fargo_ctx *c) { return c->m.fargo && c->m.hasX; }, chunk,
               [](const fargo_ctx *c) { return c->nrings_active; });
     L = BLaunch{L_CELL}; L.arg = PH_NEWVEL; L.name = "newvel";
-    add_phase(b, L, all, one, cells);
+    add_phase(b, L, all, cfg, cells);
 
     // launch shapes of the ring and sweep groups
     int rc;
@@ -481,7 +481,8 @@ static void launch_cell_cfg(int ph, int nb, const StepPlan<T> *P, Group g, cudaS
     case PH_SUB1: kb_cell<T, PH_SUB1, F><<<nb, 256, 0, s>>>(P, g); break;
     case PH_AV: kb_cell<T, PH_AV, F><<<nb, 256, 0, s>>>(P, g); break;
     case PH_TAU: kb_cell<T, PH_TAU, F><<<nb, 256, 0, s>>>(P, g); break;
-    default: kb_cell<T, PH_VAPPLY, F><<<nb, 256, 0, s>>>(P, g); break;
+    case PH_VAPPLY: kb_cell<T, PH_VAPPLY, F><<<nb, 256, 0, s>>>(P, g); break;
+    default: kb_cell<T, PH_NEWVEL, F><<<nb, 256, 0, s>>>(P, g); break;
     }
 }
 
@@ -540,8 +541,7 @@ static int batch_enqueue(fargo_batch *b, cudaEvent_t *marks = nullptr)
         case L_SCREEN: kb_cfl_screen<T><<<nb, 256, 0, s>>>(P, g); break;
         case L_EXACT: kb_cfl_exact<T><<<nb, 256, 0, s>>>(P, g); break;
         case L_CELL:
-            if (x.arg == PH_NEWVEL) kb_cell<T, PH_NEWVEL, CfgRun><<<nb, 256, 0, s>>>(P, g);
-            else if (x.key == CFG_DISK3D) launch_cell_cfg<T, CfgDisk3D>(x.arg, nb, P, g, s);
+            if (x.key == CFG_DISK3D) launch_cell_cfg<T, CfgDisk3D>(x.arg, nb, P, g, s);
             else if (x.key == CFG_DISK2D) launch_cell_cfg<T, CfgDisk2D>(x.arg, nb, P, g, s);
             else launch_cell_cfg<T, CfgRun>(x.arg, nb, P, g, s);
             break;

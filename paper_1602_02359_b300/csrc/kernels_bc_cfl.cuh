@@ -150,6 +150,19 @@ __device__ __forceinline__ float av_ratef(bool lit, float k4, float dv, float il
     return 0.0f;
 }
 
+// 16 bytes of a field row: 4 FP32 or 2 FP64 values, loaded with one
+// 128-bit access (the address is 16-byte aligned).
+template <typename T>
+struct alignas(16) Pack {
+    static constexpr int W = 16 / sizeof(T);
+    T v[W];
+};
+template <typename T>
+__device__ __forceinline__ Pack<T> ldpack(const T *p)
+{
+    return *reinterpret_cast<const Pack<T> *>(p);
+}
+
 __device__ __forceinline__ bool cfl_skip(const Scal *sc)
 {
     return sc->err != 0 || (!sc->fixed && sc->t >= sc->t_end);
@@ -182,14 +195,23 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
         const int j = m.j0 + r % ny, k = m.k0 + r / ny;
         const int ring = k * m.nyt + j;
         const idx_t base = IX(m, 0, j, k);
+        // 16-byte loads: W cells per lane (rows start on 128-byte boundaries;
+        // the last pack of a ragged row reads into the row padding, and
+        // only cells i < nx count)
+        constexpr int W = Pack<T>::W;
+        const int nx = m.nx;
         double v0r = 0.0;
         if (m.fargo) {
             // max and min are exact in the field precision
             T mx = f.vx[base], mn = mx;
-            for (int i = lane; i < m.nx; i += 32) {
-                const T v = f.vx[base + i];
-                mx = v > mx ? v : mx;
-                mn = v < mn ? v : mn;
+            for (int i0 = lane * W; i0 < nx; i0 += 32 * W) {
+                const Pack<T> pv = ldpack(f.vx + base + i0);
+#pragma unroll
+                for (int u = 0; u < W; u++)
+                    if (i0 + u < nx) {
+                        mx = pv.v[u] > mx ? pv.v[u] : mx;
+                        mn = pv.v[u] < mn ? pv.v[u] : mn;
+                    }
             }
             v0r = __dmul_rn(0.5, __dadd_rn(warp_max((double)mx), warp_min((double)mn)));
             if (lane == 0) v0[ring] = v0r;
@@ -207,42 +229,63 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
         const bool lit = m.av_lit != 0;
         const float k4 = (float)tb.k4;
         const bool avon = m.has_av != 0;
-        for (int i = lane; i < m.nx; i += 32) {
-            const idx_t c = base + i;
-            const int ip = i + 1 == m.nx ? 0 : i + 1;
-            const float rho = (float)f.rho[c];
-            float r1s;   // (c_s / dmin)^2
-            if (m.iso) {
-                r1s = c1;
-            } else {
-                const float e = (float)f.e[c];
-                if (!isfinite(e) || e < 0.0f) bad = 1;
-                r1s = c1 * __fdividef(e, rho);
-            }
-            if (!isfinite(rho) || rho <= 0.0f) bad = 1;
-            float r2 = 0.0f, r3 = 0.0f;
+        const T vx0 = f.vx[base];   // right neighbour of the ring's last cell
+        for (int i0 = lane * W; i0 < nx; i0 += 32 * W) {
+            const idx_t c = base + i0;
+            const Pack<T> prho = ldpack(f.rho + c);
+            Pack<T> pe{}, px{}, py{}, pyu{}, pz{}, pzu{};
+            if (!m.iso) pe = ldpack(f.e + c);
+            T xnext = vx0;
             if (m.hasX) {
-                const T vc = f.vx[c], vp = f.vx[base + ip];
-                const float a = fabsf((float)sub_split(vc, v0hi, v0lo));
-                const float b = fabsf((float)sub_split(vp, v0hi, v0lo));
-                r2 = fmaxf(r2, fmaxf(a, b) * ilx);
-                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ilx));
-                if (!isfinite((float)vc)) bad = 1;
+                px = ldpack(f.vx + c);
+                if (i0 + W < nx) xnext = f.vx[c + W];
             }
             if (m.hasY) {
-                const T vc = f.vy[c], vp = f.vy[c + m.sj];
-                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ily);
-                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ily));
-                if (!isfinite((float)vc)) bad = 1;
+                py = ldpack(f.vy + c);
+                pyu = ldpack(f.vy + c + m.sj);
             }
             if (m.hasZ) {
-                const T vc = f.vz[c], vp = f.vz[c + m.sk];
-                r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ilz);
-                if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ilz));
-                if (!isfinite((float)vc)) bad = 1;
+                pz = ldpack(f.vz + c);
+                pzu = ldpack(f.vz + c + m.sk);
             }
-            const float s = r1s + r2 * r2 + r3 * r3 + r4 * r4;
-            smax = fmaxf(smax, s);
+#pragma unroll
+            for (int u = 0; u < W; u++) {
+                if (i0 + u >= nx) break;
+                const float rho = (float)prho.v[u];
+                float r1s;   // (c_s / dmin)^2
+                if (m.iso) {
+                    r1s = c1;
+                } else {
+                    const float e = (float)pe.v[u];
+                    if (!isfinite(e) || e < 0.0f) bad = 1;
+                    r1s = c1 * __fdividef(e, rho);
+                }
+                if (!isfinite(rho) || rho <= 0.0f) bad = 1;
+                float r2 = 0.0f, r3 = 0.0f;
+                if (m.hasX) {
+                    const T vc = px.v[u];
+                    const T vp = i0 + u + 1 < nx ? (u + 1 < W ? px.v[u + 1 < W ? u + 1 : u] : xnext) : vx0;
+                    const float a = fabsf((float)sub_split(vc, v0hi, v0lo));
+                    const float b = fabsf((float)sub_split(vp, v0hi, v0lo));
+                    r2 = fmaxf(r2, fmaxf(a, b) * ilx);
+                    if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ilx));
+                    if (!isfinite((float)vc)) bad = 1;
+                }
+                if (m.hasY) {
+                    const T vc = py.v[u], vp = pyu.v[u];
+                    r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ily);
+                    if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ily));
+                    if (!isfinite((float)vc)) bad = 1;
+                }
+                if (m.hasZ) {
+                    const T vc = pz.v[u], vp = pzu.v[u];
+                    r2 = fmaxf(r2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ilz);
+                    if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ilz));
+                    if (!isfinite((float)vc)) bad = 1;
+                }
+                const float s = r1s + r2 * r2 + r3 * r3 + r4 * r4;
+                smax = fmaxf(smax, s);
+            }
         }
         smax = warp_maxf(smax);
         if (lane == 0) ringmax[r] = smax;

@@ -945,7 +945,7 @@ __device__ __forceinline__ T *qsel(const QSet<T> &s, int n)
 // density and energy in the scratch set, they are copied back too.  Thread 0
 // advances the device time.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, class F = CfgRun>
 __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, const QSet<T> &fin, const Fld<T> &vsrc,
                                             const Fld<T> &state, Scal *sc, int copy_scalars, int i, int j, int k)
 {
@@ -959,9 +959,9 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     const bool jact = j >= m.j0 && j < m.j1, kact = k >= m.k0 && k < m.k1;
     const int ring = k * m.nyt + j;
     const T *rho = fin.q[0];
-    const int o = m.iso ? 1 : 2;   // index of Pi-x in the quantity set
-    const T *pmx = m.iso ? fin.q[1] : fin.q[2], *ppx = m.iso ? fin.q[2] : fin.q[3];
-    const int oy = o + 2, oz = o + (m.hasY ? 4 : 2);
+    const int o = F::iso(m) ? 1 : 2;   // index of Pi-x in the quantity set
+    const T *pmx = F::iso(m) ? fin.q[1] : fin.q[2], *ppx = F::iso(m) ? fin.q[2] : fin.q[3];
+    const int oy = o + 2, oz = o + (F::hasY(m) ? 4 : 2);
     const T *pmy = qsel(fin, oy), *ppy = qsel(fin, oy + 1);
     const T *pmz = qsel(fin, oz), *ppz = qsel(fin, oz + 1);
     // interior faces from the momenta; every other face from the post-source
@@ -978,18 +978,18 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
         }
         if (copy_scalars) {
             state.rho[c] = rho[c];
-            if (!m.iso) state.e[c] = fin.q[1][c];
+            if (!F::iso(m)) state.e[c] = fin.q[1][c];
         }
     }
     if (k < m.nzt) {
-        if (m.hasY && j > m.j0 && j < m.j1 && kact) {
+        if (F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
             const idx_t cm = c - m.sj;
             state.vy[c] = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
         } else if (vsrc.vy != state.vy) {
             state.vy[c] = vsrc.vy[c];
         }
     }
-    if (m.hasZ && j < m.nyt) {
+    if (F::hasZ(m) && j < m.nyt) {
         if (k > m.k0 && k < m.k1 && jact) {
             const idx_t cm = c - m.sk;
             state.vz[c] = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
@@ -999,12 +999,12 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     }
 }
 
-template <typename T>
+template <typename T, class F = CfgRun>
 __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin, Fld<T> vsrc, Fld<T> state,
                                                 Scal *sc, int copy_scalars)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.nx) newvel_body(m, tb, fin, vsrc, state, sc, copy_scalars, i, blockIdx.y, blockIdx.z);
+    if (i < m.nx) newvel_body<T, F>(m, tb, fin, vsrc, state, sc, copy_scalars, i, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -1098,6 +1098,18 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_sums(SumInput<T> in, double *part, unsigned *counter, double *result)
 {
     sums_reduce<T>(in, part, counter, result);
+}
+
+// k_newvel with the configuration class cfg_of(m) selects.
+template <typename T>
+static void launch_newvel(const MeshD &m, dim3 g, dim3 b, cudaStream_t s, const Tab<T> &tb, const QSet<T> &fin,
+                          const Fld<T> &vsrc, const Fld<T> &state, Scal *sc, int copy_scalars)
+{
+    switch (cfg_of(m)) {
+    case CFG_DISK3D: k_newvel<T, CfgDisk3D><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
+    case CFG_DISK2D: k_newvel<T, CfgDisk2D><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
+    default: k_newvel<T, CfgRun><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
+    }
 }
 
 }  // namespace fk
