@@ -429,12 +429,21 @@ static int build_sweep_maps(fargo_ctx *c, Buffers<T> &b)
 }
 
 template <typename T, int C>
-static int ring_attrs_c(fargo_ctx *c)
+static cudaError_t ring_attrs_c(RingShape &rs, int n, bool orb)
 {
-    if (ring_grid<T>(k_transport_x<T, C>, c->tx_rs, c->nyt * c->nzt) != cudaSuccess ||
-        ring_grid<T>(k_orbital<T, C>, c->orb_rs, c->nrings_active) != cudaSuccess)
-        return FARGO_ERR_SIZE;
-    return FARGO_OK;
+    return orb ? ring_grid<T>(k_orbital<T, C>, rs, n) : ring_grid<T>(k_transport_x<T, C>, rs, n);
+}
+template <typename T>
+static cudaError_t ring_attrs(RingShape &rs, int n, bool orb)
+{
+    switch (rs.chunk) {
+    case 1: return ring_attrs_c<T, 1>(rs, n, orb);
+    case 2: return ring_attrs_c<T, 2>(rs, n, orb);
+    case 3: return ring_attrs_c<T, 3>(rs, n, orb);
+    case 4: return ring_attrs_c<T, 4>(rs, n, orb);
+    case 6: return ring_attrs_c<T, 6>(rs, n, orb);
+    default: return ring_attrs_c<T, 8>(rs, n, orb);
+    }
 }
 
 template <typename T>
@@ -450,14 +459,11 @@ static int set_kernel_attrs(fargo_ctx *c)
     c->tx_rs = ring_shape<T>(c->nx, txrows, c->pitch);
     c->orb_rs = ring_shape<T>(c->nx, nq, c->pitch);
     const size_t smem = c->tx_rs.smem > c->orb_rs.smem ? c->tx_rs.smem : c->orb_rs.smem;
-    if (smem > (size_t)maxsm - 1024 || ring_chunk(c->nx) == 0) return FARGO_ERR_SIZE;
-    switch (ring_chunk(c->nx)) {
-    case 1: return ring_attrs_c<T, 1>(c);
-    case 2: return ring_attrs_c<T, 2>(c);
-    case 3: return ring_attrs_c<T, 3>(c);
-    case 4: return ring_attrs_c<T, 4>(c);
-    default: return ring_attrs_c<T, 8>(c);
-    }
+    if (smem > (size_t)maxsm - 1024 || c->tx_rs.chunk == 0 || c->orb_rs.chunk == 0) return FARGO_ERR_SIZE;
+    if (ring_attrs<T>(c->tx_rs, c->nyt * c->nzt, false) != cudaSuccess ||
+        ring_attrs<T>(c->orb_rs, c->nrings_active, true) != cudaSuccess)
+        return FARGO_ERR_SIZE;
+    return FARGO_OK;
 }
 
 extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, int ghost, double gamma,

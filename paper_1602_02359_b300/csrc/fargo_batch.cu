@@ -376,7 +376,8 @@ static int batch_setup(fargo_batch *b)
     auto hasNu = [](const fargo_ctx *c) { return c->m.has_nu != 0; };
     auto bcy = [](const fargo_ctx *c) { return (int)grid_for((long long)c->nx * (c->nzt + 1) * 2, 256); };
     auto bcz = [](const fargo_ctx *c) { return (int)grid_for((long long)c->nx * (c->nyt + 1) * 2, 256); };
-    auto chunk = [](const fargo_ctx *c) { return ring_chunk(c->nx); };
+    auto tx_chunk = [](const fargo_ctx *c) { return c->tx_rs.chunk; };
+    auto orb_chunk = [](const fargo_ctx *c) { return c->orb_rs.chunk; };
     auto nqk = [](const fargo_ctx *c) { return 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0); };
     auto sweep_blocks = [](int axis) {
         return [axis](const fargo_ctx *c) {
@@ -413,13 +414,13 @@ static int batch_setup(fargo_batch *b)
     L = BLaunch{L_BC}; L.arg = 2; L.mode = 1; L.name = "bc_z9";
     add_phase(b, L, hasZ, one, bcz);
     L = BLaunch{L_TX}; L.name = "transport_x";
-    add_phase(b, L, all, chunk, [](const fargo_ctx *c) { return c->nyt * c->nzt; });
+    add_phase(b, L, all, tx_chunk, [](const fargo_ctx *c) { return c->nyt * c->nzt; });
     L = BLaunch{L_SWEEP}; L.arg = 1; L.name = "transport_y";
     add_phase(b, L, hasY, nqk, sweep_blocks(1));
     L = BLaunch{L_SWEEP}; L.arg = 2; L.name = "transport_z";
     add_phase(b, L, hasZ, nqk, sweep_blocks(2));
     L = BLaunch{L_ORB}; L.name = "orbital";
-    add_phase(b, L, [](const fargo_ctx *c) { return c->m.fargo && c->m.hasX; }, chunk,
+    add_phase(b, L, [](const fargo_ctx *c) { return c->m.fargo && c->m.hasX; }, orb_chunk,
               [](const fargo_ctx *c) { return c->nrings_active; });
     L = BLaunch{L_CELL}; L.arg = PH_NEWVEL; L.name = "newvel";
     add_phase(b, L, all, cfg, cells);
@@ -436,6 +437,7 @@ static int batch_setup(fargo_batch *b)
             }
             x.rs.threads = x.threads = threads;
             x.rs.stride = stride;
+            x.rs.chunk = x.key;
             x.rs.smem = x.smem = 2 * (size_t)stride * sizeof(T);
         } else if (x.kind == L_SWEEP) {
             x.threads = TmaTile<T>::TW + 32;
@@ -455,6 +457,7 @@ static int batch_setup(fargo_batch *b)
         case 2: CK((ring_attrs<T, 2>(x))); break;
         case 3: CK((ring_attrs<T, 3>(x))); break;
         case 4: CK((ring_attrs<T, 4>(x))); break;
+        case 6: CK((ring_attrs<T, 6>(x))); break;
         default: CK((ring_attrs<T, 8>(x))); break;
         }
     }
@@ -498,6 +501,7 @@ static void launch_ring(const BLaunch &x, const StepPlan<T> *P, cudaStream_t s)
         case 2: kb_tx<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         case 3: kb_tx<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         case 4: kb_tx<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 6: kb_tx<T, 6><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         default: kb_tx<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         }
     } else {
@@ -506,6 +510,7 @@ static void launch_ring(const BLaunch &x, const StepPlan<T> *P, cudaStream_t s)
         case 2: kb_orb<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         case 3: kb_orb<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         case 4: kb_orb<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 6: kb_orb<T, 6><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         default: kb_orb<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
         }
     }

@@ -1,6 +1,7 @@
 // Transport step (flow-chart cell 12): left/right momenta, the X sweep with
 // orbital advection, the Y and Z sweeps, and the new face velocities.
 #pragma once
+#include <algorithm>
 #include "fargo_internal.cuh"
 #include "kernels_source.cuh"
 #include "tma.cuh"
@@ -572,14 +573,31 @@ __global__ void __launch_bounds__(512, 2)
     ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nrings);
 }
 
-// Cells per thread of the ring kernels: the smallest of 1, 2, 3, 4, 8 that
-// keeps a ring within 512 threads.
-static inline int ring_chunk(int nx)
+// Cells per thread of a ring kernel whose CTA stages `rows` rows of `pitch`
+// values of esz bytes in two buffers.  Larger chunks recompute less of the
+// stencil halo per cell but leave fewer threads per ring, and the staging
+// decides how many CTAs share an SM: take the largest of 1, 2, 3, 4, 6 that
+// keeps the ring within 512 threads, at 192 threads or more (below that the
+// per-ring staging and barriers dominate), and at least 24 warps resident per
+// SM (228 KB of shared memory, 64 registers a thread), else the smallest
+// that fits; 8 (which spills) only for rings above 3072 cells.
+static inline int ring_chunk(int nx, int rows, int pitch, int esz)
 {
-    const int cs[5] = {1, 2, 3, 4, 8};
-    for (int c : cs)
-        if ((nx + c - 1) / c <= 512) return c;
-    return 0;
+    const int cs[6] = {1, 2, 3, 4, 6, 8};
+    const size_t smem = 2 * (size_t)rows * ring_row(pitch) * esz + 2048;
+    int best = 0;
+    for (int c : cs) {
+        const int th = ((nx + c - 1) / c + 31) / 32 * 32;
+        if (th > 512) continue;
+        if (c == 8 && best) break;
+        if (th < 192 && best) break;
+        int per = (int)(233472 / smem);
+        per = std::min(per, 2048 / th);
+        per = std::min(per, 65536 / (64 * th));
+        per = std::min(per, 32);
+        if (best == 0 || per * th >= 768) best = c;
+    }
+    return best;
 }
 
 // Launch shape of a ring kernel: threads per CTA, values per ring buffer,
@@ -587,6 +605,7 @@ static inline int ring_chunk(int nx)
 struct RingShape {
     int threads, stride, grid;
     size_t smem;
+    int chunk;   // cells per thread (ring_chunk)
 };
 
 template <typename T, int C>
@@ -606,11 +625,12 @@ template <typename T>
 static void launch_tx(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
                       Scal *sc, const RingShape &rs, cudaStream_t s)
 {
-    switch (ring_chunk(m.nx)) {
+    switch (rs.chunk) {
     case 1: launch_tx_c<T, 1>(m, tb, in, out, v0, sc, rs, s); break;
     case 2: launch_tx_c<T, 2>(m, tb, in, out, v0, sc, rs, s); break;
     case 3: launch_tx_c<T, 3>(m, tb, in, out, v0, sc, rs, s); break;
     case 4: launch_tx_c<T, 4>(m, tb, in, out, v0, sc, rs, s); break;
+    case 6: launch_tx_c<T, 6>(m, tb, in, out, v0, sc, rs, s); break;
     default: launch_tx_c<T, 8>(m, tb, in, out, v0, sc, rs, s); break;
     }
 }
@@ -621,7 +641,8 @@ template <typename T>
 static RingShape ring_shape(int nx, int rows, int pitch)
 {
     RingShape rs{};
-    const int C = ring_chunk(nx);
+    const int C = ring_chunk(nx, rows, pitch, (int)sizeof(T));
+    rs.chunk = C;
     rs.threads = C ? ((nx + C - 1) / C + 31) / 32 * 32 : 0;
     rs.stride = rows * ring_row(pitch);
     rs.smem = 2 * (size_t)rs.stride * sizeof(T);
@@ -678,11 +699,12 @@ template <typename T>
 static void launch_orb(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, Scal *sc,
                        int nrings, const RingShape &rs, cudaStream_t s)
 {
-    switch (ring_chunk(m.nx)) {
+    switch (rs.chunk) {
     case 1: launch_orb_c<T, 1>(m, tb, qs, v0, sc, nrings, rs, s); break;
     case 2: launch_orb_c<T, 2>(m, tb, qs, v0, sc, nrings, rs, s); break;
     case 3: launch_orb_c<T, 3>(m, tb, qs, v0, sc, nrings, rs, s); break;
     case 4: launch_orb_c<T, 4>(m, tb, qs, v0, sc, nrings, rs, s); break;
+    case 6: launch_orb_c<T, 6>(m, tb, qs, v0, sc, nrings, rs, s); break;
     default: launch_orb_c<T, 8>(m, tb, qs, v0, sc, nrings, rs, s); break;
     }
 }
