@@ -456,8 +456,8 @@ static int set_kernel_attrs(fargo_ctx *c)
     const int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
     const int txrows = 2 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
     // two ring buffers per CTA (double buffering)
-    c->tx_rs = ring_shape<T>(c->nx, txrows, c->pitch);
-    c->orb_rs = ring_shape<T>(c->nx, nq, c->pitch);
+    c->tx_rs = ring_shape<T>(c->nx, txrows, c->pitch, false);
+    c->orb_rs = ring_shape<T>(c->nx, nq, c->pitch, true);
     const size_t smem = c->tx_rs.smem > c->orb_rs.smem ? c->tx_rs.smem : c->orb_rs.smem;
     if (smem > (size_t)maxsm - 1024 || c->tx_rs.chunk == 0 || c->orb_rs.chunk == 0) return FARGO_ERR_SIZE;
     if (ring_attrs<T>(c->tx_rs, c->nyt * c->nzt, false) != cudaSuccess ||

@@ -485,6 +485,119 @@ __device__ __forceinline__ void orb_compute(const MeshD &m, const Tab<T> &tb, co
     }
 }
 
+// The same step with the stencil halo exchanged between lanes (C >= 3).  A
+// warp covers 30 C consecutive cells: lane l in 1..30 owns C of them and
+// lanes 0 and 31 own the C cells just outside, only so that their
+// neighbours find the halo values in registers.  Every lane evaluates its
+// cells' ratios, Eq. 34 slopes and Eq. 35 interface values once; the two
+// values left of a lane's cells and one right of them arrive by shuffle, and
+// so does the flux through its right face, so no value is computed twice
+// inside a warp.
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <typename T>
+__device__ __forceinline__ T shfl_dn1(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// Quantity loop of orb_compute_w for one upwind direction (POS: xi >= 0,
+// the donor of a face is the cell left of it).
+template <typename T, int C, bool POS>
+__device__ __forceinline__ void orb_lanes(const QSet<T> &qs, int nq, int rp, const T *win, idx_t base, int i0,
+                                          bool owner, int nx, T xi, T vR, T S, T dtVi)
+{
+    const T sixth = T(1.0 / 6.0);
+    T rho[C], rinv[C];
+#pragma unroll
+    for (int s = 0; s < C; s++) {
+        rho[s] = win[s];
+        rinv[s] = T(1) / rho[s];
+    }
+    T F0[C];
+    #pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if (q >= nq) break;
+        const T *wq = win + (size_t)q * rp;
+        // A[x + 2]: ratio of cell x = -2 .. C (own cells 0 .. C-1)
+        T A[C + 3];
+#pragma unroll
+        for (int s = 0; s < C; s++) A[s + 2] = q == 0 ? rho[s] : wq[s] * rinv[s];
+        A[0] = shfl_up1(A[C]);
+        A[1] = shfl_up1(A[C + 1]);
+        A[C + 2] = shfl_dn1(A[2]);
+        T dm[C + 1];   // Eq. 34 slopes of cells 0 .. C
+#pragma unroll
+        for (int s = 0; s < C; s++) dm[s] = ppa_dm(A[s + 1], A[s + 2], A[s + 3]);
+        dm[C] = shfl_dn1(dm[0]);
+        // QR[x + 2]: Eq. 35 right interface value of cell x = -2 .. C-1
+        T QR[C + 2];
+#pragma unroll
+        for (int s = 0; s < C; s++)
+            QR[s + 2] = A[s + 2] + T(0.5) * (A[s + 3] - A[s + 2]) - (dm[s + 1] - dm[s]) * sixth;
+        QR[0] = shfl_up1(QR[C]);
+        QR[1] = shfl_up1(QR[C + 1]);
+        // upwind PPA value through the left face u of each own cell: donor
+        // cell d = u-1 (POS) or u, its value, neighbours and interface values
+        T F[C];
+#pragma unroll
+        for (int u = 0; u < C; u++) {
+            constexpr int sh = POS ? -1 : 0;
+            const int d = u + sh;
+            const T q0 = A[d + 2], qm = A[d + 1], qp = A[d + 3];
+            T l = QR[d + 1], rr = QR[d + 2];
+            if ((qp - q0) * (q0 - qm) <= T(0)) {
+                l = q0;
+                rr = q0;
+            } else {
+                const T D = rr - l, Cc = q0 - T(0.5) * (l + rr);
+                if (D * Cc > D * D * sixth) l = T(3) * q0 - T(2) * rr;
+                else if (-D * D * sixth > D * Cc) rr = T(3) * q0 - T(2) * l;
+            }
+            const T wgt = xi * (T(1) - xi) * (T(2) * q0 - rr - l);
+            const T stv = POS ? rr + xi * (q0 - rr) + wgt : l + xi * (q0 - l) + wgt;
+            if (q == 0) F0[u] = vR * stv * S;
+            F[u] = q == 0 ? F0[u] : F0[u] * stv;
+        }
+        const T Fr = shfl_dn1(F[0]);   // flux through the right face of the last own cell
+#pragma unroll
+        for (int u = 0; u < C; u++) {
+            const T fr = u + 1 < C ? F[u + 1 < C ? u + 1 : u] : Fr;
+            if (owner && i0 + u < nx) qs.q[q][base + i0 + u] = wq[u] - dtVi * (fr - F[u]);
+        }
+    }
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void orb_compute_w(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, int r, T *buf,
+                                              int Nm, T xsT, T vR, T dtT)
+{
+    // the left halo of a lane's interface values reaches three cells back,
+    // and the halo lanes must own those cells
+    static_assert(C >= 3, "the halo lanes need three cells");
+    if (Nm < 0) return;
+    const int nx = m.nx, nq = qs.nq, rp = ring_row(m.sj);
+    ring_frame(buf, nq, rp, nx);
+    const T *sm = buf + kRingLead;
+    const int ny = m.j1 - m.j0;
+    const int j = m.j0 + r % ny, k = m.k0 + r / ny;
+    const int ring = k * m.nyt + j;
+    const idx_t base = IX(m, 0, j, k);
+    if (xsT == T(0)) {   // a pure shift
+        for (int q = 0; q < nq; q++)
+            for (int i = threadIdx.x; i < nx; i += blockDim.x)
+                qs.q[q][base + i] = sm[(size_t)q * rp + wrapi(i - Nm, nx)];
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int i0 = (int)(threadIdx.x >> 5) * (30 * C) + (lane - 1) * C;
+    const bool owner = lane >= 1 && lane <= 30;
+    // cells i0 .. i0+C-1 after the shift: the staged run from (i0 - N) mod nx
+    int b = (i0 - Nm) % nx;
+    if (b < 0) b += nx;
+    const T S = tb.sx[ring];
+    const T dtVi = dtT * tb.vinv[ring];
+    if (xsT >= T(0)) orb_lanes<T, C, true>(qs, nq, rp, sm + b, base, i0, owner, nx, xsT, vR, S, dtVi);
+    else orb_lanes<T, C, false>(qs, nq, rp, sm + b, base, i0, owner, nx, -xsT, vR, S, dtVi);
+}
+
 // Single-instance ring operations for ring_pipeline (meta: the per-iteration
 // table in shared memory).
 template <typename T, int C>
@@ -528,7 +641,8 @@ struct OrbOp {
     __device__ void compute(int it, T *src)
     {
         const RingMeta<T> &e = meta[it];
-        orb_compute<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
+        if constexpr (C >= 3) orb_compute_w<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
+        else orb_compute<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
     }
     __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
 };
@@ -581,13 +695,21 @@ __global__ void __launch_bounds__(512, 2)
 // per-ring staging and barriers dominate), and at least 24 warps resident per
 // SM (228 KB of shared memory, 64 registers a thread), else the smallest
 // that fits; 8 (which spills) only for rings above 3072 cells.
-static inline int ring_chunk(int nx, int rows, int pitch, int esz)
+// Threads of a ring kernel with C cells per thread: C cells per lane, or
+// (halo) warps of 30 C cells, lanes 0 and 31 holding the neighbours' halo
+// (the orbital step; its one-cell-per-lane forms work with either count).
+static inline int ring_threads(int nx, int C, bool halo)
+{
+    return halo ? 32 * ((nx + 30 * C - 1) / (30 * C)) : ((nx + C - 1) / C + 31) / 32 * 32;
+}
+
+static inline int ring_chunk(int nx, int rows, int pitch, int esz, bool halo)
 {
     const int cs[6] = {1, 2, 3, 4, 6, 8};
     const size_t smem = 2 * (size_t)rows * ring_row(pitch) * esz + 2048;
     int best = 0;
     for (int c : cs) {
-        const int th = ((nx + c - 1) / c + 31) / 32 * 32;
+        const int th = ring_threads(nx, c, halo);
         if (th > 512) continue;
         if (c == 8 && best) break;
         if (th < 192 && best) break;
@@ -635,15 +757,15 @@ static void launch_tx(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const 
     }
 }
 // Threads, buffer stride and shared memory of a ring kernel for rings of up
-// to nx cells staged as `rows` rows of `pitch` values; the persistent grid is
-// filled in by ring_grid.
+// to nx cells staged as `rows` rows of `pitch` values (halo: the thread
+// count of ring_threads); the persistent grid is filled in by ring_grid.
 template <typename T>
-static RingShape ring_shape(int nx, int rows, int pitch)
+static RingShape ring_shape(int nx, int rows, int pitch, bool halo)
 {
     RingShape rs{};
-    const int C = ring_chunk(nx, rows, pitch, (int)sizeof(T));
+    const int C = ring_chunk(nx, rows, pitch, (int)sizeof(T), halo);
     rs.chunk = C;
-    rs.threads = C ? ((nx + C - 1) / C + 31) / 32 * 32 : 0;
+    rs.threads = C ? ring_threads(nx, C, halo) : 0;
     rs.stride = rows * ring_row(pitch);
     rs.smem = 2 * (size_t)rs.stride * sizeof(T);
     return rs;

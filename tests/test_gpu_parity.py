@@ -27,6 +27,11 @@ CASES = [
     (W.CYL, 41, 17, 9, False, 1e-3, W.BC_REFLECT),
     (W.SPH, 64, 24, 14, False, 1e-3, W.BC_FROZEN),
     (W.SPH, 33, 19, 10, True, 0.0, W.BC_REFLECT),
+    # rings long enough for several cells per thread in the ring kernels
+    # (in FP64: three per thread, lanes exchanging the orbital step's stencil
+    # halo, at 600 cells; two at 480)
+    (W.CYL, 600, 9, 1, True, 1e-3, W.BC_FROZEN),
+    (W.SPH, 480, 10, 6, False, 1e-3, W.BC_REFLECT),
 ]
 IDS = [f"g{c[0]}-{c[1]}x{c[2]}x{c[3]}-{'iso' if c[4] else 'adi'}-nu{c[5]}-bc{c[6]}" for c in CASES]
 
