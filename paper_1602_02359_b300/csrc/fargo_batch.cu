@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const St
     unsigned row = lin / nx;
     unsigned i = lin - row * nx;
     for (int u = 0; u < kCellsPerThread && row < rows; u++) {
-        int j = (int)(row % nyr), k = (int)(row / nyr);
+        // one plane without a Z direction: the row is the Y index
+        int j = F::hasZ(m) ? (int)(row % nyr) : (int)row, k = F::hasZ(m) ? (int)(row / nyr) : 0;
         if constexpr (PH == PH_TAU) {
             j += m.j0;
             k += m.k0;
