@@ -1,7 +1,7 @@
 """Benchmark of the B300 FARGO3D hydro step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                    [--workload batch256|disk3d|disk2d|disk3d-small|batch-small]
+                    [--workload batch256|disk3d|disk2d|disk3d-small|batch-small|batch-medium]
                     [--no-cpu-baseline] [--no-e2e] [--no-fp64] [--no-single]
 
 Default workload (batch256): the batched parameter sweep of 256 independent
@@ -73,8 +73,15 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 22.93, "substep1": 33.46, "artvisc": 36.54, "visc_tau": 36.61, "visc_apply": 54.68, "transport_x": 61.17, "transport_y": 64.73, "transport_z": 65.87, "orbital": 59.8, "newvel": 41.68}
-KERNEL_SRC_HASH = "0c3bf5b3c7ee5fcf"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 21.89, "substep1": 33.45, "artvisc": 36.6, "visc_tau": 36.6, "visc_apply": 54.67, "transport_x": 55.97, "transport_y": 64.73, "transport_z": 65.84, "orbital": 58.09, "newvel": 41.66}
+KERNEL_SRC_HASH = "c5048398a68a2283"
+
+# The same for the batched step: DRAM bytes per active cell of every batched
+# phase (all its launches of one step summed), measured on batch-medium (the
+# first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
+# whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 12.24, "substep1": 17.55, "artvisc": 17.4, "visc_tau": 20.86, "visc_apply": 31.91, "transport_x": 24.78, "transport_y": 42.68, "orbital": 32.27, "newvel": 26.56}
+BATCH_SRC_HASH = "b8cd9415248608ff"
 
 
 # Sources of the single-instance step's kernels (the traffic table above
@@ -83,10 +90,10 @@ STEP_SOURCES = ("fargo_internal.cuh", "tma.cuh", "kernels_bc_cfl.cuh", "kernels_
                 "kernels_transport.cuh", "context.cuh", "fargo_api.cu")
 
 
-def kernel_source_hash():
+def kernel_source_hash(sources=STEP_SOURCES):
     d = os.path.join(ROOT, "paper_1602_02359_b300", "csrc")
     h = hashlib.sha256()
-    for f in STEP_SOURCES:
+    for f in sources:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
@@ -218,7 +225,7 @@ def dist_env():
     return ws, rank, local
 
 
-BATCH_WORKLOADS = {"batch256": 256, "batch-small": 16}
+BATCH_WORKLOADS = {"batch256": 256, "batch-small": 16, "batch-medium": 32}
 
 
 def make_workload(name):
@@ -241,9 +248,12 @@ def batch_label(n):
 
 def batch_params(wname):
     """Parameters of the sweep (batch-small: the first 16 draws at a quarter
-    of the radial resolution, a profiling case still far above L2)."""
+    of the radial resolution; batch-medium: the first 32 disks of the 256-disk
+    sweep at full resolution; both profiling cases still far above L2)."""
     n = BATCH_WORKLOADS[wname]
     ps = W.batch_params(n=n, seed=1602)
+    if wname == "batch-medium":
+        ps = W.batch_params(n=256, seed=1602)[:n]
     if wname == "batch-small":
         ps = [dict(p, ny=max(32, p["ny"] // 4), nx=3 * max(32, p["ny"] // 4)) for p in ps]
     return ps
@@ -508,7 +518,9 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
             add_step_times(per, b.profile_step())
     running, _ = b.status()
     nsteps = [m.scalars()[2] for m in mem]
-    roof = roofline_of(per, cells, ALG_FIELDS_2D_ISO, 4, method_fields=METHOD_FIELDS_2D_ISO)
+    btraffic = (TRAFFIC_PER_CELL_BATCH if BATCH_SRC_HASH and
+                kernel_source_hash(STEP_SOURCES + ("fargo_batch.cu",)) == BATCH_SRC_HASH else None)
+    roof = roofline_of(per, cells, ALG_FIELDS_2D_ISO, 4, btraffic, method_fields=METHOD_FIELDS_2D_ISO)
     e2e = None
     if e2e_on:
         # public API end to end: every step uploads each disk's active state
@@ -556,7 +568,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="batch256",
-                    choices=["batch256", "batch-small", "disk3d", "disk2d", "disk3d-small"])
+                    choices=["batch256", "batch-small", "batch-medium", "disk3d", "disk2d", "disk3d-small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -621,7 +633,7 @@ def main():
         fp64 = fp64_plain_disk2d(torch, fb)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload not in ("disk3d-small", "batch-small"):
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload not in ("disk3d-small", "batch-small", "batch-medium"):
         cpu = cpu_baseline(args.workload)
 
     if rank == 0:
