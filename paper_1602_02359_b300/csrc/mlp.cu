@@ -409,6 +409,277 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tma(const __grid_constant__ CUt
     }
 }
 
+// ---------------------------------------------------------------------------
+// Whole-network inference in one kernel.  A CTA owns 128 samples and keeps
+// them on chip through every layer: their activations in shared memory
+// (bfloat16, the 128-byte-swizzle K-major layout the MMA reads, up to five
+// 64-deep chunks), the layer's accumulator in tensor memory.  Only the
+// weights stream in, by TMA, in 32 KB chunks (64 K x 256 rows) through four
+// stages that run ahead across layer boundaries, so the next layer's weights
+// arrive while the current layer's epilogue runs.  Per layer:
+//  - thread 0 issues the layer's MMAs chunk by chunk (each chunk as soon as
+//    its weights land; the stage of the previous chunk is refilled once its
+//    MMAs completed) and commits the layer to an mbarrier;
+//  - all eight warps drain the accumulator (warp w: TMEM lanes 32 (w % 4)..,
+//    columns 128 (w / 4)..): bias and ReLU, rounded to bfloat16 and written
+//    back into the activation chunks, or, after the last layer, the output
+//    map and row-coalesced FP32 stores through shared memory;
+//  - a proxy fence and a barrier hand the new activations to the next
+//    layer's MMAs.
+// The input map and the rounding to bfloat16 happen here too, from the FP32
+// input rows.  The arithmetic is that of the layer-by-layer products: the
+// same operands, chunking and MMA shapes.  Networks with an input of at most
+// 320 features, layers of at most 256 and at most 8 layers qualify.
+// ---------------------------------------------------------------------------
+constexpr int F_THREADS = 256, F_MAXL = 8, F_ACT = 5, F_STAGES = 4;
+constexpr int F_CHUNK_A = 128 * 128, F_CHUNK_W = 256 * 128;
+constexpr int F_SMEM = F_ACT * F_CHUNK_A + F_STAGES * F_CHUNK_W + F_MAXL * 256 * 4 + 1024;
+
+struct FusedArgs {
+    const float *x;
+    float *y;
+    const float *shift, *scale, *oshift, *oscale;
+    const float *bias[F_MAXL];
+    int dims[F_MAXL + 1];
+    int L, M;
+    int *err;
+};
+struct FusedMaps {
+    CUtensorMap w[F_MAXL];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+// byte offset of the 16-byte unit u (8 values along K) of row r in a
+// 128-byte-swizzled 128-row chunk
+__device__ __forceinline__ unsigned sw128_off(int r, int u) { return (unsigned)(r * 128 + ((u ^ (r & 7)) << 4)); }
+
+__global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(const __grid_constant__ FusedMaps fm,
+                                                          const __grid_constant__ FusedArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t wfull[F_STAGES], wempty[F_STAGES], accb;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    unsigned char *sm = smem + ((1024u - (su32(smem) & 1023u)) & 1023u);
+    unsigned char *act = sm;
+    unsigned char *wst = sm + F_ACT * F_CHUNK_A;
+    float *sbias = reinterpret_cast<float *>(wst + F_STAGES * F_CHUNK_W);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, L = a.L;
+    int total = 0;
+    for (int l = 0; l < L; l++) total += (a.dims[l] + 63) / 64;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < F_STAGES; q++) {
+            mbar_init(&wfull[q], 1);
+            mbar_init(&wempty[q], 1);
+        }
+        mbar_init(&accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    for (int i = tid; i < L * 256; i += F_THREADS) {
+        const int l = i >> 8, c = i & 255;
+        sbias[i] = c < a.dims[l + 1] ? a.bias[l][c] : 0.0f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    // thread 0: weight chunk gg of the whole network into stage gg % 4
+    int issued = 0;
+    auto issue_w = [&](int gg) {
+        int l = 0, c = gg;
+        while (c >= (a.dims[l] + 63) / 64) {
+            c -= (a.dims[l] + 63) / 64;
+            l++;
+        }
+        const int st = gg & (F_STAGES - 1);
+        mbar_expect_tx(&wfull[st], (unsigned)F_CHUNK_W);
+        tma_load_2d(wst + st * F_CHUNK_W, &fm.w[l], c * 64, 0, &wfull[st]);
+        issued = gg + 1;
+    };
+    if (tid == 0) {
+        for (int l = 0; l < L; l++) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&fm.w[l]) : "memory");
+        for (int gg = 0; gg < F_STAGES && gg < total; gg++) issue_w(gg);
+    }
+    // the input rows: (x - shift) * scale rounded to bfloat16, zero beyond the
+    // batch and the features.  Thread t owns the 8-feature unit t % units of
+    // every (F_THREADS / units)-th row, with that unit's shift and scale in
+    // registers; the loads of eight rows are issued before any is stored.
+    {
+        const int K0 = a.dims[0], units = ((K0 + 63) / 64) * 8;
+        const int rstep = F_THREADS / units, u = tid % units, k0 = u * 8;
+        if (tid < units * rstep) {
+            float sh[8], sc[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int k = k0 + e;
+                sh[e] = k < K0 ? a.shift[k] : 0.0f;
+                sc[e] = k < K0 ? a.scale[k] : 0.0f;
+            }
+            constexpr int RB = 8;
+            for (int rb = tid / units; rb < 128; rb += RB * rstep) {
+                float v[RB][8];
+#pragma unroll
+                for (int j = 0; j < RB; j++) {
+                    const int r = rb + j * rstep, row = m0 + r;
+#pragma unroll
+                    for (int e = 0; e < 8; e++)
+                        v[j][e] = r < 128 && row < a.M && k0 + e < K0 ? a.x[(size_t)row * K0 + k0 + e] : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < RB; j++) {
+                    const int r = rb + j * rstep, row = m0 + r;
+                    if (r >= 128) break;
+                    float f[8];
+#pragma unroll
+                    for (int e = 0; e < 8; e++) f[e] = row < a.M && k0 + e < K0 ? (v[j][e] - sh[e]) * sc[e] : 0.0f;
+                    const unsigned off = (unsigned)((u >> 3) * F_CHUNK_A) + sw128_off(r, u & 7);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(su32(act + off)),
+                                 "r"(pack_bf16(f[0], f[1])), "r"(pack_bf16(f[2], f[3])),
+                                 "r"(pack_bf16(f[4], f[5])), "r"(pack_bf16(f[6], f[7]))
+                                 : "memory");
+                }
+            }
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    int g = 0;
+    const int q4 = warp & 3, h = warp >> 2;
+    const int r = q4 * 32 + lane;   // the thread's accumulator row
+    for (int l = 0; l < L; l++) {
+        const int nk = (a.dims[l] + 63) / 64;
+        if (tid == 0) {
+            bool ok = s_fail == 0;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int kc = 0; kc < nk && ok; kc++, g++) {
+                const int st = g & (F_STAGES - 1);
+                ok = mbar_wait(&wfull[st], (g >> 2) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned a0 = su32(act + kc * F_CHUNK_A), b0 = su32(wst + st * F_CHUNK_W);
+#pragma unroll
+                for (int kk = 0; kk < 4; kk++) {
+                    const uint64_t ad = smem_desc_sw128(a0 + kk * 32), bd = smem_desc_sw128(b0 + kk * 32);
+                    const unsigned acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&wempty[st]))
+                             : "memory");
+                // refill the previous chunk's stage once its MMAs are done
+                if (g >= 1 && g + F_STAGES - 1 < total) {
+                    const int ps = (g - 1) & (F_STAGES - 1);
+                    ok = mbar_wait(&wempty[ps], ((g - 1) >> 2) & 1);
+                    if (!ok) break;
+                    issue_w(g + F_STAGES - 1);
+                }
+            }
+            if (ok)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&accb))
+                             : "memory");
+            else
+                s_fail = 1;
+        }
+        // every thread waits for the layer's accumulator (bounded)
+        const bool got = mbar_wait(&accb, l & 1);
+        if (!got) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float *bl = sbias + l * 256;
+        const bool last = l == L - 1;
+        float *tile = reinterpret_cast<float *>(wst) + warp * 32 * 33;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            const int cb = h * 128 + c0;
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)cb;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+                  "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                  "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr + 16u));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (!last) {
+                // bias, ReLU, bfloat16: four 16-byte units of the next layer's input
+#pragma unroll
+                for (int uu = 0; uu < 4; uu++) {
+                    float f[8];
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const float z = __uint_as_float(v[uu * 8 + e]) + bl[cb + uu * 8 + e];
+                        f[e] = z > 0.0f ? z : 0.0f;
+                    }
+                    const int col = cb + uu * 8;
+                    const unsigned off = (unsigned)((col >> 6) * F_CHUNK_A) + sw128_off(r, (col & 63) >> 3);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(su32(act + off)),
+                                 "r"(pack_bf16(f[0], f[1])), "r"(pack_bf16(f[2], f[3])),
+                                 "r"(pack_bf16(f[4], f[5])), "r"(pack_bf16(f[6], f[7]))
+                                 : "memory");
+                }
+            } else {
+                // output map, stored row by row (lane = column) through the
+                // warp's 32 x 33 scratch in the now idle weight stages
+#pragma unroll
+                for (int e = 0; e < 32; e++) tile[lane * 33 + e] = __uint_as_float(v[e]);
+                __syncwarp();
+                const int col = cb + lane, N = a.dims[L];
+                if (col < N) {
+                    const float b = bl[col], sc = a.oscale[col], sh = a.oshift[col];
+                    for (int rr = 0; rr < 32; rr++) {
+                        const int row = m0 + q4 * 32 + rr;
+                        if (row < a.M) a.y[(size_t)row * N + col] = (tile[rr * 33 + lane] + b) * sc + sh;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) {
+            atomicOr(a.err, 4);
+            // let the weight copies in flight land, and the MMAs finish
+            for (int gg = g; gg < issued; gg++) mbar_wait(&wfull[gg & (F_STAGES - 1)], (gg >> 2) & 1);
+            if (g > 0) mbar_wait(&wempty[(g - 1) & (F_STAGES - 1)], ((g - 1) >> 2) & 1);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+    }
+}
+
 }  // namespace tc
 
 template <bool TA, bool TB, int EPI>
@@ -640,6 +911,8 @@ struct fargo_mlp {
     std::vector<int> ldp;                                          // padded widths (multiples of 8)
     std::vector<bf16 *> wpad;                                      // padded bfloat16 weights per layer
     std::vector<CUtensorMap> mapA, mapB;                           // forward operands per layer
+    bool fused = false;                                            // inference in one kernel (k_mlp_fused)
+    tc::FusedMaps fmaps{};                                         // its weight maps
     LayerTab lt{};
     std::vector<float *> Z;                                        // hidden pre-activations (FP32)
     std::vector<bf16 *> Ab;                                        // hidden activations (bf16, pitch ldp[l+1])
@@ -744,6 +1017,14 @@ extern "C" int fargo_mlp_create(fargo_mlp **out, const int *dims, int nlayers, i
         const bf16 *ain = l == 0 ? n->xb : n->Ab[l - 1];
         if (!encode_bf16(&n->mapA[l], ain, dims[l], max_batch, n->ldp[l], tc::TM) ||
             !encode_bf16(&n->mapB[l], n->wpad[l], dims[l], dims[l + 1], n->ldp[l], tc::TN))
+            rc = FARGO_ERR_CUDA;
+    }
+    n->fused = nlayers <= tc::F_MAXL && dims[0] <= 64 * tc::F_ACT;
+    for (int l = 1; l <= nlayers; l++) n->fused = n->fused && dims[l] <= 256;
+    if (n->fused && !rc) {
+        for (int l = 0; l < nlayers; l++) n->fmaps.w[l] = n->mapB[l];
+        if (cudaFuncSetAttribute(tc::k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::F_SMEM) !=
+            cudaSuccess)
             rc = FARGO_ERR_CUDA;
     }
     if (!rc) rc = nalloc(n, &n->y, B * dims[nlayers]);
@@ -893,6 +1174,23 @@ extern "C" int fargo_mlp_forward(fargo_mlp *n, const float *x, int batch, float 
 {
     if (!n || !x || !y || batch < 1) return FARGO_ERR_BADARG;
     if (batch > n->max_batch) return FARGO_ERR_SIZE;
+    if (n->fused) {
+        tc::FusedArgs fa{};
+        fa.x = x;
+        fa.y = y;
+        fa.shift = n->shift;
+        fa.scale = n->scale;
+        fa.oshift = n->oshift;
+        fa.oscale = n->oscale;
+        for (int l = 0; l < n->L; l++) fa.bias[l] = n->w + n->boff[l];
+        for (int l = 0; l <= n->L; l++) fa.dims[l] = n->dims[l];
+        fa.L = n->L;
+        fa.M = batch;
+        fa.err = n->err;
+        tc::k_mlp_fused<<<(batch + 127) / 128, tc::F_THREADS, tc::F_SMEM, n->stream>>>(n->fmaps, fa);
+        MK(cudaGetLastError());
+        return FARGO_OK;
+    }
     int rc = forward(n, x, batch, false);
     if (rc) return rc;
     MK(cudaMemcpyAsync(y, n->y, sizeof(float) * batch * n->dims[n->L], cudaMemcpyDeviceToDevice, n->stream));
