@@ -41,13 +41,33 @@ __device__ __forceinline__ int group_member(const Group &g, int b, int &local)
     return __ldg(&g.ids[lo]);
 }
 
+// A member's plan copied into shared memory by the whole block: the per-cell
+// kernels read its mesh constants and table pointers many times per cell, and
+// from shared memory these are short-latency loads instead of dependent
+// global ones (the single-instance kernels find them in the constant bank).
+// The ring kernels and the exact Courant pass keep reading the plan from
+// global memory: a copy per ring costs them more than it saves.
+template <typename T>
+struct PlanSmem {
+    long long w[(sizeof(StepPlan<T>) + 7) / 8];
+};
+template <typename T>
+__device__ __forceinline__ const StepPlan<T> &plan_to_smem(const StepPlan<T> *P, int id, PlanSmem<T> &s)
+{
+    const long long *src = reinterpret_cast<const long long *>(&P[id]);
+    for (int t = threadIdx.x; t < (int)(sizeof(s.w) / 8); t += blockDim.x) s.w[t] = src[t];
+    __syncthreads();
+    return *reinterpret_cast<const StepPlan<T> *>(s.w);
+}
+
 enum { PH_SUB1, PH_AV, PH_TAU, PH_VAPPLY, PH_NEWVEL };
 
 template <typename T>
 __global__ void __launch_bounds__(256) kb_bc(const StepPlan<T> *__restrict__ P, Group g, int axis, int mode)
 {
     int local;
-    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    __shared__ PlanSmem<T> sp;
+    const StepPlan<T> &p = plan_to_smem(P, group_member(g, blockIdx.x, local), sp);
     const long long tid = (long long)local * blockDim.x + threadIdx.x;
     if (axis == 1) bc_y_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid);
     else bc_z_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid);
@@ -57,7 +77,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) kb_cfl_screen(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
-    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    __shared__ PlanSmem<T> sp;
+    const StepPlan<T> &p = plan_to_smem(P, group_member(g, blockIdx.x, local), sp);
     cfl_screen_body(p.m, p.tb, p.A, p.v0, p.ringmax, p.part, p.sc, p.nrings_active, local, p.cfl_blocks);
 }
 
@@ -83,7 +104,8 @@ template <typename T, int PH, class F>
 __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
-    const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
+    __shared__ PlanSmem<T> sp;
+    const StepPlan<T> &p = plan_to_smem(P, group_member(g, blockIdx.x, local), sp);
     const MeshD &m = p.m;
     const unsigned nyr = PH == PH_TAU ? tau_rows(m) : m.nyt + 1;
     const unsigned rows = nyr * (PH == PH_TAU ? tau_planes(m) : cell_planes(m));
@@ -207,7 +229,8 @@ __global__ void __launch_bounds__(TmaTile<T>::TW + 32) kb_sweep(const StepPlan<T
 {
     int local;
     const int id = group_member(g, blockIdx.x, local);
-    const StepPlan<T> &p = P[id];
+    __shared__ PlanSmem<T> sp;
+    const StepPlan<T> &p = plan_to_smem(P, id, sp);
     sweep_body<T, AXIS, NQ>(p.m, p.tb, maps[id], AXIS == 1 ? p.qy : p.qz, p.sc, AXIS == 1 ? p.seg_y : p.seg_z,
                             local);
 }
