@@ -112,9 +112,10 @@ __global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode)
 //    below 2e-6), keeps the ring maximum of the estimate, and the last block
 //    reduces the global estimate M and the FP64 shear limit of Eq. 38.
 //  k_cfl_exact: every ring whose estimate reaches M (1 - 2^-12) is evaluated
-//    exactly in FP64 with round-to-nearest intrinsics (no fused multiply-add);
-//    the ring holding the true maximum always qualifies.  The last block
-//    publishes dt, clipped to t_end.
+//    exactly in FP64 with round-to-nearest intrinsics (no fused multiply-add),
+//    by a whole block (all four sub-partitions' FP64 units); the ring holding
+//    the true maximum always qualifies.  The last block publishes dt, clipped
+//    to t_end.
 // The screening launch also fills the per-step planet angle tables (sin^2 of
 // half the azimuth offset to the planet and its cosine) used by sub-step 1.
 // ---------------------------------------------------------------------------
@@ -343,12 +344,15 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
     __shared__ double s_red[8];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = bid * 8 + warp;
     const bool skip = cfl_skip(sc);
     const double M = sc->m32;
     const double thr = M < 1e-30 ? -1.0 : M * (1.0 - 1.0 / 4096.0);
     double smax = 0.0;
-    if (!skip && r < nrings && (double)ringmax[r] >= thr) {
+    // the block's eight rings; each candidate is evaluated by the whole block
+    // (its FP64 divisions then use every sub-partition's FP64 unit)
+    for (int w = 0; w < 8 && !skip; w++) {
+        const int r = bid * 8 + w;
+        if (r >= nrings || !((double)ringmax[r] >= thr)) continue;
         const int ny = m.j1 - m.j0;
         const int j = m.j0 + r % ny, k = m.k0 + r / ny;
         const int ring = k * m.nyt + j;
@@ -358,7 +362,7 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
         const double nu = m.has_nu ? tb.nud[ring] : 0.0;
         const double r4 = nu > 0.0 ? __ddiv_rn(__dmul_rn(4.0, nu), __dmul_rn(dmin, dmin)) : 0.0;
         const double csr = m.iso ? tb.csd[ring] : 0.0;
-        for (int i = lane; i < m.nx; i += 32) {
+        for (int i = threadIdx.x; i < m.nx; i += blockDim.x) {
             const idx_t c = base + i;
             const int ip = i + 1 == m.nx ? 0 : i + 1;
             const double rho = (double)f.rho[c];
