@@ -196,8 +196,10 @@ struct BOrbOp {
         const RingMeta<T> &e = meta[it];
         if (e.N < 0) return;
         const StepPlan<T> &p = P[e.id];
-        if constexpr (C >= 3) orb_compute_w<T, C>(p.m, p.tb, p.qfin, e.local, src, e.N, e.a, e.b, step_dt<T>(p.sc));
-        else orb_compute<T, C>(p.m, p.tb, p.qfin, e.local, src, e.N, e.a, e.b, step_dt<T>(p.sc));
+        if constexpr (orb_uses_lanes<C>())
+            orb_compute_w<T, C>(p.m, p.tb, p.qfin, e.local, src, e.N, e.a, e.b, step_dt<T>(p.sc));
+        else
+            orb_compute<T, C>(p.m, p.tb, p.qfin, e.local, src, e.N, e.a, e.b, step_dt<T>(p.sc));
     }
     __device__ void fail(int it) { atomicOr(&P[meta[it].id].sc->err, kErrTimeout); }
 };

@@ -565,13 +565,23 @@ __device__ __forceinline__ void orb_lanes(const QSet<T> &qs, int nq, int rp, con
     }
 }
 
+// The orbital step's form per cells-per-thread class: the lane-exchange form
+// for C = 3, 4, 6; the per-thread form for C = 1, 2 (too few cells for the
+// halo lanes) and C = 8 (rings beyond 2880 cells, too long for the halo
+// lanes' thread count).
+template <int C>
+__host__ __device__ constexpr bool orb_uses_lanes()
+{
+    return C >= 3 && C <= 6;
+}
+
 template <typename T, int C>
 __device__ __forceinline__ void orb_compute_w(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, int r, T *buf,
                                               int Nm, T xsT, T vR, T dtT)
 {
     // the left halo of a lane's interface values reaches three cells back,
-    // and the halo lanes must own those cells
-    static_assert(C >= 3, "the halo lanes need three cells");
+    // and the halo lanes must own those cells: C >= 3
+    static_assert(orb_uses_lanes<C>(), "the halo lanes need three cells");
     if (Nm < 0) return;
     const int nx = m.nx, nq = qs.nq, rp = ring_row(m.sj);
     ring_frame(buf, nq, rp, nx);
@@ -641,7 +651,7 @@ struct OrbOp {
     __device__ void compute(int it, T *src)
     {
         const RingMeta<T> &e = meta[it];
-        if constexpr (C >= 3) orb_compute_w<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
+        if constexpr (orb_uses_lanes<C>()) orb_compute_w<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
         else orb_compute<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
     }
     __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
@@ -696,11 +706,11 @@ __global__ void __launch_bounds__(512, 2)
 // SM (228 KB of shared memory, 64 registers a thread), else the smallest
 // that fits; 8 (which spills) only for rings above 3072 cells.
 // Threads of a ring kernel with C cells per thread: C cells per lane, or
-// (halo) warps of 30 C cells, lanes 0 and 31 holding the neighbours' halo
-// (the orbital step; its one-cell-per-lane forms work with either count).
+// (halo, C = 3..6) warps of 30 C cells, lanes 0 and 31 holding the
+// neighbours' halo (the orbital step's lane-exchange form).
 static inline int ring_threads(int nx, int C, bool halo)
 {
-    return halo ? 32 * ((nx + 30 * C - 1) / (30 * C)) : ((nx + C - 1) / C + 31) / 32 * 32;
+    return halo && C >= 3 && C <= 6 ? 32 * ((nx + 30 * C - 1) / (30 * C)) : ((nx + C - 1) / C + 31) / 32 * 32;
 }
 
 static inline int ring_chunk(int nx, int rows, int pitch, int esz, bool halo)

@@ -275,6 +275,28 @@ def test_fp32_disk_within_stated_tolerance():
     assert e_mom < 1e-4
 
 
+def test_fp32_longest_ring_within_stated_tolerance():
+    """The longest azimuthal ring a 2D isothermal disk can stage (4000 cells,
+    eight per thread in the ring kernels, the orbital step in its per-thread
+    form), ten steps against the FP64 oracle at the FP32 tolerances; the
+    Courant step stays bit-exact on the promoted state."""
+    w = W.perturb(W.disk2d(nx=4000, ny=6), seed=41, amp=1e-2)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    import paper_1602_02359_b300 as fb
+    c = make_ctx(w, fb.F32, t=0.0, t_end=w.t_end)
+    t = 0.0
+    for n in range(10):
+        t += o.step(st, t, w.t_end)
+        c.step(want_dt=False)
+    g = c.get_state()
+    e_rho = rel_l1(w.active(g["rho"]), w.active(st["rho"]))
+    e_mom = rel_l1(momentum_density(w, g), momentum_density(w, st))
+    record("fp32_longest_ring_4000x6_10steps", rel_l1_rho=e_rho, rel_l1_momentum=e_mom)
+    assert e_rho < 2e-5
+    assert e_mom < 1e-4
+
+
 def test_fp32_courant_step_bit_exact_on_promoted_state():
     """dt and v0 are FP64 islands: from the FP32 fields promoted to FP64 they
     equal the oracle's bit for bit."""
