@@ -225,6 +225,45 @@ def dist_env():
     return ws, rank, local
 
 
+class Ranks:
+    """Rank plumbing of a replicas run: one process per GPU under torchrun
+    (NCCL, reductions on the GPU), each rank stepping its own copy of the
+    workload; the tests drive the same code with gloo on the CPU.  There is
+    no collective on the data path: only the barrier around the timed region
+    and the reductions of the timings."""
+
+    def __init__(self, torch, backend="nccl", device="cuda"):
+        self.torch = torch
+        self.ws, self.rank, self.local = dist_env()
+        self.device = device
+        if self.ws > 1:
+            torch.distributed.init_process_group(backend)
+
+    def barrier(self):
+        if self.ws > 1:
+            self.torch.distributed.barrier()
+
+    def max(self, x):
+        t = self.torch.tensor([float(x)], device=self.device, dtype=self.torch.float64)
+        if self.ws > 1:
+            self.torch.distributed.all_reduce(t, op=self.torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def aggregate(self, cells, ms, e2e_rate=None):
+        """Whole-job figures of weak scaling: every rank processed `cells`
+        per step; the job's step time is the slowest rank's, so the rate is
+        ranks x cells / max time; the end-to-end rate likewise from the
+        slowest rank's end-to-end rate."""
+        ms_max = self.max(ms)
+        value = cells * self.ws / (ms_max * 1e-3)
+        e2e = None if e2e_rate is None else self.ws / self.max(1.0 / e2e_rate)
+        return value, ms_max, e2e
+
+    def close(self):
+        if self.ws > 1:
+            self.torch.distributed.destroy_process_group()
+
+
 BATCH_WORKLOADS = {"batch256": 256, "batch-small": 16, "batch-medium": 32}
 
 
@@ -585,34 +624,20 @@ def main():
     import paper_1602_02359_b300 as fb
 
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    torch.cuda.set_device(local if ws > 1 else 0)
+    ranks = Ranks(torch)
     dev = torch.cuda.current_device()
-
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x):
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        if ws > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    barrier = ranks.barrier
 
     batched = args.workload in BATCH_WORKLOADS
     if batched:
         r = bench_batch(args, torch, fb, args.workload, dev, barrier, e2e_on=not args.no_e2e)
     else:
         r = bench_single(args, torch, fb, args.workload, dev, barrier, e2e_on=not args.no_e2e)
-    ms_max = max_over_ranks(r["ms"])
-    value = r["cells"] * ws / (ms_max * 1e-3)
+    value, ms_max, e2e_rate = ranks.aggregate(r["cells"], r["ms"],
+                                              r["e2e"]["value"] if r["e2e"] is not None else None)
     if r["e2e"] is not None:
-        # whole-job end-to-end rate: the slowest rank's rate times the ranks
-        r["e2e"]["value"] = ws / max_over_ranks(1.0 / r["e2e"]["value"])
+        r["e2e"]["value"] = e2e_rate
 
     single = None
     if rank == 0 and batched and not args.no_single:
@@ -668,8 +693,7 @@ def main():
         if surrogate is not None:
             line["surrogate_kernels"] = surrogate
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":
