@@ -73,15 +73,15 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 21.89, "substep1": 33.45, "artvisc": 36.6, "visc_tau": 36.6, "visc_apply": 54.67, "transport_x": 55.97, "transport_y": 64.73, "transport_z": 65.84, "orbital": 58.09, "newvel": 41.66}
-KERNEL_SRC_HASH = "c5048398a68a2283"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 21.85, "substep1": 33.42, "artvisc": 36.5, "visc_tau": 36.56, "visc_apply": 54.6, "transport_x": 55.76, "transport_y": 64.7, "transport_z": 65.84, "orbital": 58.11, "newvel": 41.66}
+KERNEL_SRC_HASH = "b17975553c9be440"
 
 # The same for the batched step: DRAM bytes per active cell of every batched
 # phase (all its launches of one step summed), measured on batch-medium (the
 # first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
 # whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
-TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 12.24, "substep1": 17.55, "artvisc": 17.4, "visc_tau": 20.86, "visc_apply": 31.91, "transport_x": 24.78, "transport_y": 42.68, "orbital": 32.27, "newvel": 26.56}
-BATCH_SRC_HASH = "b8cd9415248608ff"
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 12.27, "substep1": 17.5, "artvisc": 18.05, "visc_tau": 20.68, "visc_apply": 33.32, "transport_x": 24.77, "transport_y": 42.85, "orbital": 32.27, "newvel": 27.13}
+BATCH_SRC_HASH = "621ea52e7d61ba77"
 
 
 # Sources of the single-instance step's kernels (the traffic table above
