@@ -576,21 +576,22 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
             torch.cuda.synchronize()
             barrier()
             t1 = time.perf_counter()
+            cols = {n: [d[n] for d in host] for n in names}
             for _ in range(ksteps):
-                for m, d in zip(mem, host):
-                    for n in names:
-                        m.set_field(n, d[n].numpy(), region=fb.ACTIVE)
-                b.step(sync=True)
-                for m, d in zip(mem, host):
-                    for n in names:
-                        m.get_field(n, region=fb.ACTIVE, out=d[n].numpy())
+                for n in names:
+                    b.set_field(n, cols[n], region=fb.ACTIVE)   # queued on the batch's stream
+                b.step(sync=False)
+                for n in names:
+                    b.get_field(n, cols[n], region=fb.ACTIVE)   # the last one synchronises
+                b.status()
             torch.cuda.synchronize()
             el = time.perf_counter() - t1
             barrier()
         e2e = {"value": cells * ksteps / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": ksteps,
                "note": "every step uploads every disk's active rho, v_x, v_y from pinned host memory "
-                       "through fargo_set_field and reads them back through fargo_get_field"}
+                       "(fargo_batch_set_field, queued on the batch's stream), steps the batch and reads "
+                       "them back (fargo_batch_get_field); one host synchronisation per field read"}
     b.close()
     for m in mem:
         m.close()

@@ -248,6 +248,22 @@ typedef struct fargo_batch fargo_batch;
 int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, int n, void *stream);
 void fargo_batch_destroy(fargo_batch *b);
 
+/* One field (FARGO_FIELD_*) of every member in or out in one call, region
+ * FARGO_ACTIVE or FARGO_FULL as for fargo_set_field.  src[i] / dst[i] is
+ * member i's buffer (host memory, pinned for asynchronous copies, or device
+ * memory on the batch's device) of bytes[i] bytes, which must equal that
+ * member's region size.  The copies are queued on the batch's stream, so
+ * they are ordered with the batch's steps:
+ *  - fargo_batch_set_field returns without synchronising; the source
+ *    buffers must stay unchanged until the next synchronising batch call
+ *    (fargo_batch_get_field or fargo_batch_status);
+ *  - fargo_batch_get_field synchronises once, after the last copy.
+ * An upload, a step and a download thus cost one host synchronisation per
+ * step instead of one per member and field.  Errors: BADARG, SIZE (a
+ * member's byte count), CUDA. */
+int fargo_batch_set_field(fargo_batch *b, int field, int region, const void *const *src, const size_t *bytes);
+int fargo_batch_get_field(fargo_batch *b, int field, int region, void *const *dst, const size_t *bytes);
+
 /* Queue one step of every member (one graph launch); no host sync. */
 int fargo_batch_step(fargo_batch *b);
 

@@ -29,7 +29,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
             "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_profile_step", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -96,6 +96,8 @@ def lib():
         L.fargo_batch_status.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.fargo_batch_run.argtypes = [vp, C.c_longlong, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
         L.fargo_batch_use_graph.argtypes = [vp, C.c_int]
+        L.fargo_batch_set_field.argtypes = [vp, C.c_int, C.c_int, C.POINTER(vp), C.POINTER(C.c_size_t)]
+        L.fargo_batch_get_field.argtypes = [vp, C.c_int, C.c_int, C.POINTER(vp), C.POINTER(C.c_size_t)]
         L.fargo_batch_launches_per_step.argtypes = [vp]
         L.fargo_batch_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int),
                                                C.POINTER(C.c_char_p)]
@@ -335,6 +337,39 @@ class FargoBatch:
 
     def use_graph(self, on=True):
         _check(lib().fargo_batch_use_graph(self.h, int(on)), "fargo_batch_use_graph")
+
+    @staticmethod
+    def _ptrs(arrays):
+        """Pointers and byte counts of numpy arrays or torch tensors (contiguous)."""
+        ptr, nb = [], []
+        for a in arrays:
+            if hasattr(a, "data_ptr"):
+                ptr.append(a.data_ptr())
+                nb.append(a.numel() * a.element_size())
+            else:
+                if not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("field buffers must be contiguous")
+                ptr.append(a.ctypes.data)
+                nb.append(a.nbytes)
+        n = len(ptr)
+        return (C.c_void_p * n)(*ptr), (C.c_size_t * n)(*nb)
+
+    def set_field(self, name, arrays, region=FULL):
+        """Queue field `name` of every member from arrays[i] (one per member,
+        the member's region shape; host arrays should be pinned).  No host
+        synchronisation: keep the arrays unchanged until get_field/status."""
+        if len(arrays) != len(self.members):
+            raise ValueError("one array per member")
+        ptr, nb = self._ptrs(arrays)
+        _check(lib().fargo_batch_set_field(self.h, FIELD_IDS[name], region, ptr, nb), "fargo_batch_set_field")
+
+    def get_field(self, name, arrays, region=FULL):
+        """Copy field `name` of every member into arrays[i]; synchronises."""
+        if len(arrays) != len(self.members):
+            raise ValueError("one array per member")
+        ptr, nb = self._ptrs(arrays)
+        _check(lib().fargo_batch_get_field(self.h, FIELD_IDS[name], region, ptr, nb), "fargo_batch_get_field")
+        return arrays
 
     def launches_per_step(self):
         return lib().fargo_batch_launches_per_step(self.h)

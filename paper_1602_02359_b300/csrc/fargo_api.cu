@@ -611,7 +611,9 @@ static void *field_ptr(fargo_ctx *c, int field)
     return p[field];
 }
 
-static int copy_region(fargo_ctx *c, void *dev, void *host, int region, size_t bytes, int to_dev)
+// Queue the copies of one field region on `stream` (no synchronisation).
+static int queue_region(fargo_ctx *c, void *dev, void *host, int region, size_t bytes, int to_dev,
+                        cudaStream_t stream)
 {
     const size_t es = c->esz;
     const size_t pitchb = (size_t)c->pitch * es, rowb = (size_t)c->nx * es;
@@ -619,22 +621,37 @@ static int copy_region(fargo_ctx *c, void *dev, void *host, int region, size_t b
     if (region == FARGO_FULL) {
         const size_t rows = (size_t)(c->nzt + 1) * (c->nyt + 1);
         if (bytes != rows * rowb) return FARGO_ERR_SIZE;
-        if (to_dev) CK(cudaMemcpy2DAsync(dev, pitchb, host, rowb, rowb, rows, kind, c->stream));
-        else CK(cudaMemcpy2DAsync(host, rowb, dev, pitchb, rowb, rows, kind, c->stream));
+        if (to_dev) CK(cudaMemcpy2DAsync(dev, pitchb, host, rowb, rowb, rows, kind, stream));
+        else CK(cudaMemcpy2DAsync(host, rowb, dev, pitchb, rowb, rows, kind, stream));
     } else if (region == FARGO_ACTIVE) {
         if (bytes != (size_t)c->nx * c->ny * c->nz * es) return FARGO_ERR_SIZE;
         const int gy = c->m.gy, gz = c->m.gz;
         for (int k = 0; k < c->nz; k++) {
             char *d = (char *)dev + ((size_t)(k + gz) * c->m.sk + (size_t)gy * c->pitch) * es;
             char *h = (char *)host + (size_t)k * c->ny * rowb;
-            if (to_dev) CK(cudaMemcpy2DAsync(d, pitchb, h, rowb, rowb, c->ny, kind, c->stream));
-            else CK(cudaMemcpy2DAsync(h, rowb, d, pitchb, rowb, c->ny, kind, c->stream));
+            if (to_dev) CK(cudaMemcpy2DAsync(d, pitchb, h, rowb, rowb, c->ny, kind, stream));
+            else CK(cudaMemcpy2DAsync(h, rowb, d, pitchb, rowb, c->ny, kind, stream));
         }
     } else {
         return FARGO_ERR_BADARG;
     }
+    return FARGO_OK;
+}
+
+static int copy_region(fargo_ctx *c, void *dev, void *host, int region, size_t bytes, int to_dev)
+{
+    const int rc = queue_region(c, dev, host, region, bytes, to_dev, c->stream);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     return FARGO_OK;
+}
+
+// Batch field transfers (fargo_batch_set_field / fargo_batch_get_field in
+// fargo_batch.cu): one field of member c queued on the batch's stream.
+int fargo_queue_field(fargo_ctx *c, int field, int region, void *buf, size_t bytes, int to_dev, cudaStream_t s)
+{
+    if (!c || !buf || field < 0 || field > 4) return FARGO_ERR_BADARG;
+    return queue_region(c, field_ptr(c, field), buf, region, bytes, to_dev, s);
 }
 
 extern "C" int fargo_set_field(fargo_ctx *c, int field, int region, const void *src, size_t bytes, int on_device)

@@ -663,6 +663,30 @@ extern "C" void fargo_batch_destroy(fargo_batch *b)
     delete b;
 }
 
+int fargo_queue_field(fargo_ctx *c, int field, int region, void *buf, size_t bytes, int to_dev, cudaStream_t s);
+
+extern "C" int fargo_batch_set_field(fargo_batch *b, int field, int region, const void *const *src,
+                                     const size_t *bytes)
+{
+    if (!b || !src || !bytes) return FARGO_ERR_BADARG;
+    for (int i = 0; i < b->n; i++) {
+        const int rc = fargo_queue_field(b->mem[i], field, region, (void *)src[i], bytes[i], 1, b->stream);
+        if (rc) return rc;
+    }
+    return FARGO_OK;
+}
+
+extern "C" int fargo_batch_get_field(fargo_batch *b, int field, int region, void *const *dst, const size_t *bytes)
+{
+    if (!b || !dst || !bytes) return FARGO_ERR_BADARG;
+    for (int i = 0; i < b->n; i++) {
+        const int rc = fargo_queue_field(b->mem[i], field, region, dst[i], bytes[i], 0, b->stream);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    return FARGO_OK;
+}
+
 extern "C" int fargo_batch_step(fargo_batch *b)
 {
     if (!b) return FARGO_ERR_BADARG;
