@@ -97,11 +97,11 @@ __global__ void __launch_bounds__(256) kb_cfl_exact(const StepPlan<T> *__restric
 // several cells and no block is padded to a row's end.
 constexpr int kCellsPerThread = 16;
 
-// Register budgets: 40 per thread (six 256-thread blocks per SM) for every
-// phase but the viscous update, which gets 48 (five blocks); the few
-// spills this costs are cheaper than the occupancy larger budgets lose.
+// Register budgets (measured): 32 per thread for sub-step 1 (eight 256-thread
+// blocks per SM), 48 for the viscous update (five blocks), 40 for the other
+// phases (six blocks).
 template <typename T, int PH, class F>
-__global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : 6) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
+__global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : (PH == PH_SUB1 ? 8 : 6)) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
     __shared__ PlanSmem<T> sp;

@@ -539,8 +539,9 @@ __device__ __forceinline__ void visc_apply_body(const MeshD &m, const Tab<T> &tb
 
 // Single-instance wrappers: a 3D grid, x over the azimuth (blockDim.x
 // cells per block), y over the rows, z over the planes.
+// (eight blocks per SM: a 32-register budget, full occupancy)
 template <typename T, class F = CfgRun>
-__global__ void __launch_bounds__(256) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
+__global__ void __launch_bounds__(256, 8) k_substep1(MeshD m, Tab<T> tb, Fld<T> in, Fld<T> out, const Scal *sc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m.nx) substep1_body<T, F>(m, tb, in, out, sc, i, blockIdx.y, blockIdx.z);
