@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) kb_bc(const StepPlan<T> *__restrict__ P, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) kb_cfl_screen(const StepPlan<T> *__restrict__ P, Group g)
+__global__ void __launch_bounds__(256, 6) kb_cfl_screen(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
     __shared__ PlanSmem<T> sp;

@@ -438,8 +438,10 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
     }
 }
 
+// (six blocks per SM: the screen is latency-bound, and the occupancy a
+// 40-register budget buys outweighs its few spills)
 template <typename T>
-__global__ void __launch_bounds__(256) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f, double *v0, float *ringmax,
+__global__ void __launch_bounds__(256, 6) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f, double *v0, float *ringmax,
                                                     double *part, Scal *sc, int nrings)
 {
     cfl_screen_body(m, tb, f, v0, ringmax, part, sc, nrings, blockIdx.x, gridDim.x);
