@@ -59,6 +59,29 @@ def test_forward_matches_oracle(dims, batch):
 
 
 @pytest.mark.parametrize("dims,batch", CASES)
+def test_inference_kernel_agrees_with_the_training_forward(dims, batch):
+    """Inference runs the whole network in one kernel; back-propagation runs
+    the layer-by-layer products.  The loss back-propagation reports must be
+    the mean squared error of the inference output against the same targets
+    (both FP32 over the same bfloat16 operands)."""
+    import torch
+    net, vec, p = net_and_params(dims, 4)
+    rng = np.random.Generator(np.random.PCG64(5))
+    X = dev(rng.uniform(-1, 1, size=(batch, dims[0])))
+    T = dev(rng.normal(size=(batch, dims[-1])))
+    y = torch.empty(batch, dims[-1], device="cuda")
+    net.forward(X, y)
+    loss = torch.zeros(1, device="cuda")
+    net.backward(X, T, loss)
+    net.status()
+    mse = float(((y.double() - T.double()) ** 2).mean())
+    got = float(loss.item())
+    record(f"mlp_inference_vs_training_forward_{'x'.join(map(str, dims))}_b{batch}", rel=abs(got - mse) / mse)
+    assert abs(got - mse) <= 1e-5 * mse, (got, mse)
+    net.close()
+
+
+@pytest.mark.parametrize("dims,batch", CASES)
 def test_gradients_match_oracle(dims, batch):
     import torch
     net, vec, p = net_and_params(dims, 3)
