@@ -78,6 +78,7 @@ def lib():
         L.or_transport_z.argtypes = [pp, ps, PP6, C.c_double]
         L.or_new_velocities.argtypes = [pp, ps, PP6]
         L.or_geometry.argtypes = [pp, P, P, P, P, P, P]
+        L.or_planet_force.argtypes = [pp, ps, P, C.c_double, C.c_int, P]
         L.or_vanleer_slope.argtypes = [C.c_double] * 5
         L.or_vanleer_slope.restype = C.c_double
         L.or_ppa_faces.argtypes = [C.c_int, P, C.c_double, P]
@@ -198,6 +199,15 @@ class Oracle:
         out = [np.zeros(n) for _ in range(6)]
         lib().or_geometry(C.byref(self.p), *[_ptr(a) for a in out])
         return [a.reshape(self.w.nz_t + 1, self.w.ny_t + 1) for a in out]
+
+    def planet_force(self, st, rp, eps, bm08=False):
+        """Force of the gas on a planet at rp = (x, y, z), per unit planet
+        mass (G = 1), Plummer softening eps; bm08 removes each ring's mean
+        density first.  Returns (a_x, a_y, a_z, specific torque z)."""
+        out = np.zeros(4)
+        r = np.ascontiguousarray(rp, dtype=np.float64)
+        lib().or_planet_force(C.byref(self.p), C.byref(self._state(st)), _ptr(r), float(eps), int(bm08), _ptr(out))
+        return out
 
     def sums(self, st):
         """Conserved totals (mass, internal energy, X momentum), exactly rounded sums.

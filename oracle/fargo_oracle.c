@@ -1228,3 +1228,66 @@ int or_step(const or_params *p, or_state *s, double t, double t_end, double dt_f
     *dt_out = dt;
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Force of the gas on a planet (Sec. 3.7, orbital integrator: the force of  */
+/* the disk on the planets, evaluated once per hydrodynamical step), per     */
+/* unit planet mass, G = 1:                                                   */
+/*   a = sum over active cells of  m_c (r_c - r_p) / (|r_c - r_p|^2 + eps^2)^(3/2) */
+/* with m_c = rho_c V_c and r_c the cell centre in Cartesian coordinates.    */
+/* bm08 = 1 removes the axisymmetric part of the density first: rho_c minus  */
+/* the mean of rho over the cell's ring (the option of the same section, so */
+/* that an axisymmetric disk exerts no force).  out = (a_x, a_y, a_z, the z  */
+/* component of r_p x a, the specific torque).  Compensated (Neumaier) sums. */
+/* ------------------------------------------------------------------------ */
+typedef struct { double s, c; } nsum;
+static void nsum_add(nsum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+void or_planet_force(const or_params *p, const or_state *st, const double rp[3], double eps, int bm08,
+                     double out[4])
+{
+    mesh m;
+    mesh_init(&m, p);
+    nsum ax = {0, 0}, ay = {0, 0}, az = {0, 0};
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++) {
+            double mean = 0.0;
+            if (bm08) {
+                nsum r = {0, 0};
+                for (int i = 0; i < m.nx; i++) nsum_add(&r, st->rho[IDX(&m, i, j, k)]);
+                mean = (r.s + r.c) / m.nx;
+            }
+            double V = 1.0 / inv_vol(&m, j, k);
+            for (int i = 0; i < m.nx; i++) {
+                double x = p->xmin + (i + 0.5) * m.dx;
+                double X, Y, Z;
+                if (p->geom == OR_CYL) {
+                    double r = m.ym[j];
+                    X = r * cos(x); Y = r * sin(x); Z = m.zm[k];
+                } else if (p->geom == OR_SPH) {
+                    double r = m.ym[j], sn = sin(m.zm[k]);
+                    X = r * sn * cos(x); Y = r * sn * sin(x); Z = r * cos(m.zm[k]);
+                } else {
+                    X = x; Y = m.ym[j]; Z = m.zm[k];
+                }
+                double mc = (st->rho[IDX(&m, i, j, k)] - mean) * V;
+                double dx = X - rp[0], dy = Y - rp[1], dz = Z - rp[2];
+                double d2 = dx * dx + dy * dy + dz * dz + eps * eps;
+                double w = mc / (d2 * sqrt(d2));
+                nsum_add(&ax, w * dx);
+                nsum_add(&ay, w * dy);
+                nsum_add(&az, w * dz);
+            }
+        }
+    out[0] = ax.s + ax.c;
+    out[1] = ay.s + ay.c;
+    out[2] = az.s + az.c;
+    out[3] = rp[0] * out[1] - rp[1] * out[0];
+    mesh_free(&m);
+}

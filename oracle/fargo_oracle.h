@@ -64,6 +64,12 @@ void or_new_velocities(const or_params *p, or_state *s, double *pi[6]);
  * extra row / plane: [nz_t+1][ny_t+1]). */
 void or_geometry(const or_params *p, double *sx, double *sy, double *sz, double *vinv, double *vol, double *dxr);
 
+/* Force of the active cells' gas on a planet at rp (per unit planet mass),
+ * Plummer softening eps; bm08 = 1 subtracts each ring's mean density first.
+ * out = (a_x, a_y, a_z, specific torque z). */
+void or_planet_force(const or_params *p, const or_state *st, const double rp[3], double eps, int bm08,
+                     double out[4]);
+
 /* 1D building blocks, exposed for the special-case tests. */
 double or_vanleer_slope(double qm, double q0, double qp, double dxm, double dxp);
 void or_ppa_faces(int n, const double *q, double xi_signed, double *qstar /* face i = between i-1 and i */);

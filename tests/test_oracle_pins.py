@@ -654,3 +654,118 @@ def test_orbital_step_after_radial_sweep_is_stable():
         tb += o.step(b, tb)
     ra, rb = w.active(a["rho"]), w.active(b["rho"])
     assert np.max(np.abs(ra - rb) / ra) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Force of the gas on the planet (Sec. 3.7, orbital integrator)
+# ---------------------------------------------------------------------------
+
+def _lumpy_disk(nx=48, ny=20, seed=3):
+    """A 2D planet disk with a non-axisymmetric density (seeded bumps)."""
+    w = W.disk2d(nx=nx, ny=ny, q=1e-3)
+    st = w.copy().state
+    rng = np.random.default_rng(seed)
+    st["rho"] *= 1.0 + 0.3 * rng.uniform(-1, 1, size=st["rho"].shape)
+    return w, st
+
+
+def _interaction_energy(w, st, t, a):
+    """Gas-planet interaction energy per unit planet mass for the planet of
+    the oracle's potential (unit mass, no star, no indirect term) at time t
+    on its orbit of radius a: sum over active cells of rho V Phi_p."""
+    ww = w.copy()
+    ww.star_mass, ww.planet_q, ww.indirect, ww.planet_a = 0.0, 1.0, False, a
+    o = oracle.Oracle(ww)
+    phi = o.potential(t)
+    _, _, _, _, vol, _ = o.geometry()
+    V = vol[:w.nz_t, :w.ny_t][w.gz:w.gz + w.nz, w.gy:w.gy + w.ny][:, :, None]
+    return math.fsum((w.active(st["rho"]) * V * w.active(phi)).ravel())
+
+
+def test_planet_torque_is_minus_the_azimuthal_derivative_of_the_interaction_energy():
+    """Newton's third law through an independent route: the oracle's potential
+    routine gives the energy E(phi_p) of the gas in the planet's potential;
+    the torque on the planet is -dE/dphi_p and the radial force -dE/da
+    (central differences, O(h^2))."""
+    w, st = _lumpy_disk()
+    o = oracle.Oracle(w)
+    a, eps = 1.0, w.planet_eps
+    om = math.sqrt(1.0 / a ** 3)          # the potential routine's orbital rate for M = 0, q = 1
+    t, h = 0.4, 2e-5
+    php = om * t
+    f = o.planet_force(st, (a * math.cos(php), a * math.sin(php), 0.0), eps)
+
+    def d4(E, x, h):   # fourth-order central difference
+        return (-E(x + 2 * h) + 8 * E(x + h) - 8 * E(x - h) + E(x - 2 * h)) / (12 * h)
+    dE = d4(lambda tt: _interaction_energy(w, st, tt, a), t, h) / om
+    assert abs(f[3] - (-dE)) <= 1e-8 * abs(f[3]), (f[3], -dE)
+    # radial force: move the orbit radius at the same phase
+    dEda = d4(lambda aa: _interaction_energy(w, st, php / math.sqrt(1.0 / aa ** 3), aa), a, 2e-5)
+    fr = f[0] * math.cos(php) + f[1] * math.sin(php)
+    assert abs(fr - (-dEda)) <= 1e-8 * abs(fr), (fr, -dEda)
+
+
+def test_planet_force_far_field_is_inverse_square_toward_the_mass():
+    """A single massive cell seen from far away: |a| d^2 -> the cell's mass
+    (rho V, V from the oracle's geometry), pointing at the cell."""
+    w = W.disk2d(nx=32, ny=16)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    st["rho"][:] = 0.0
+    j, i = w.gy + 7, 5
+    st["rho"][0, j, i] = 2.5
+    _, _, _, _, vol, _ = o.geometry()
+    mass = 2.5 * vol[0, j]
+    r = 0.5 * (w.yf[j] + w.yf[j + 1])
+    x = w.xmin + (i + 0.5) * (w.xmax - w.xmin) / w.nx
+    cell = np.array([r * math.cos(x), r * math.sin(x), 0.0])
+    for D in (1e3, 1e4):
+        rp = cell + np.array([D * 0.6, -D * 0.8, 0.0])
+        f = o.planet_force(st, rp, eps=0.0)
+        d = cell - rp
+        want = mass * d / np.linalg.norm(d) ** 3
+        assert np.allclose(f[:3], want, rtol=1e-12, atol=0), (f, want)
+
+
+def test_axisymmetric_disk_exerts_no_torque_and_bm08_removes_it_entirely():
+    """An axisymmetric disk exerts no torque on a planet in its midplane on a
+    symmetry axis of the azimuthal grid (elsewhere the cells' discreteness
+    gives a torque); with each ring's mean removed (BM08) it exerts no force
+    at all, anywhere.  For a lumpy disk the BM08 option changes the force but
+    not the torque."""
+    w = W.disk2d(nx=64, ny=24)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    dphi = (w.xmax - w.xmin) / w.nx
+    # on a symmetry axis of the azimuthal grid: a cell centre and a cell edge
+    for ph in (w.xmin + 9.5 * dphi, w.xmin + 20 * dphi):
+        rp = (0.98 * math.cos(ph), 0.98 * math.sin(ph), 0.0)
+        f = o.planet_force(st, rp, w.planet_eps)
+        scale = abs(f[0]) + abs(f[1])
+        assert abs(f[3]) <= 1e-12 * scale, (ph, f)
+        assert np.all(o.planet_force(st, rp, w.planet_eps, bm08=True) == 0.0)
+    w, st = _lumpy_disk()
+    o = oracle.Oracle(w)
+    ph = w.xmin + 11.5 * (w.xmax - w.xmin) / w.nx
+    rp = (0.98 * math.cos(ph), 0.98 * math.sin(ph), 0.0)
+    fd = o.planet_force(st, rp, w.planet_eps)
+    fb = o.planet_force(st, rp, w.planet_eps, bm08=True)
+    assert abs(fd[3] - fb[3]) <= 1e-10 * abs(fd[3])
+    assert abs(fd[0] - fb[0]) > 1e-3 * abs(fd[0])
+
+
+def test_planet_force_turns_with_the_disk():
+    """Rotating the density by k azimuthal cells and the planet by k dphi
+    rotates the force by k dphi and leaves the torque unchanged."""
+    w, st = _lumpy_disk(nx=40)
+    o = oracle.Oracle(w)
+    k = 7
+    dphi = 2 * math.pi / w.nx * k
+    rp = np.array([1.02, 0.0, 0.0])
+    f0 = o.planet_force(st, rp, w.planet_eps)
+    st2 = {n: np.roll(v, k, axis=-1) for n, v in st.items()}
+    rp2 = np.array([rp[0] * math.cos(dphi), rp[0] * math.sin(dphi), 0.0])
+    f1 = o.planet_force(st2, rp2, w.planet_eps)
+    c, s = math.cos(dphi), math.sin(dphi)
+    assert np.allclose(f1[:2], [c * f0[0] - s * f0[1], s * f0[0] + c * f0[1]], rtol=1e-11, atol=1e-15)
+    assert abs(f1[3] - f0[3]) <= 1e-11 * (abs(f0[0]) + abs(f0[1]))
