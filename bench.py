@@ -502,6 +502,7 @@ def bench_single(args, torch, fb, wname, dev, barrier, e2e_on=True, steps=None):
     _, _, nsteps, err = c.scalars()
     if err:
         raise SystemExit(f"device error {err} during the benchmark")
+    pforce = planet_force_timing(torch, c, stream, w, esz, dev) if w.geom != W.CART and w.planet_q > 0 else None
     table = ALG_FIELDS_3D if (w.nz > 1 and not w.iso) else ALG_FIELDS_2D_ISO
     traffic_tab = (TRAFFIC_PER_CELL_3D if (fp32 and w.nz > 1 and not w.iso
                                            and kernel_source_hash() == KERNEL_SRC_HASH) else None)
@@ -537,7 +538,46 @@ def bench_single(args, torch, fb, wname, dev, barrier, e2e_on=True, steps=None):
     c.close()
     return {"workload": label, "cells": w.cells, "fp32": fp32, "ms": ms, "clocks": clocks, "roofline": roof,
             "e2e": e2e, "launches": nl, "steps_advanced": int(nsteps),
-            "state_gb": w.cells * 21 * esz / 1e9}
+            "state_gb": w.cells * 21 * esz / 1e9, "planet_force": pforce}
+
+
+def planet_force_timing(torch, c, stream, w, esz, dev, reps=20):
+    """Force of the gas on the planet on the workload's state after the timed
+    steps, direct sum and BM08.  Device time per call from CUDA events on the
+    context's stream around `reps` queued calls (fargo_planet_force_async:
+    the table and the force kernels, results left on the device); and the
+    time of the synchronous call a host integrator makes
+    (fargo_planet_force: the same two launches, the 32-byte copy back and
+    the synchronisation), host clock.  Algorithmic bytes: one read of the
+    density per active cell (the BM08 ring mean re-reads a ring that is
+    still in L1/L2)."""
+    hbm, kind = peaks()
+    rp = (w.planet_a, 0.0, 0.0)
+    res = torch.empty(4, dtype=torch.float64, device=dev)
+    out = {"bound": "hbm", "peak": hbm, "peak_kind": f"{kind} copy bandwidth (burst)", "unit": "GB/s",
+           "alg_bytes_per_call": w.cells * esz, "launches_per_call": 2}
+    for bm08 in (False, True):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                c.planet_force_async(rp, w.planet_eps, res.data_ptr(), bm08)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                c.planet_force_async(rp, w.planet_eps, res.data_ptr(), bm08)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                c.planet_force(rp, w.planet_eps, bm08)
+            sync_ms = (time.perf_counter() - t0) * 1e3 / reps
+        key = "bm08" if bm08 else "direct"
+        gbs = w.cells * esz / (ms * 1e-3) / 1e9
+        out[key] = {"ms": round(ms, 4), "achieved": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                    "sync_call_ms": round(sync_ms, 4)}
+    return out
 
 
 def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
@@ -648,7 +688,8 @@ def main():
                   "roofline": {k: s["roofline"].get(k) for k in ("kernel", "achieved", "peak", "unit", "frac",
                                                                  "step_alg_GBps", "step_frac", "method_GBps",
                                                                  "method_frac", "traffic")},
-                  "per_kernel": s["roofline"]["per_kernel"], "clocks": s["clocks"]}
+                  "per_kernel": s["roofline"]["per_kernel"], "clocks": s["clocks"],
+                  "planet_force": s["planet_force"]}
 
     surrogate = None
     if rank == 0 and batched and not args.no_surrogate:
@@ -691,6 +732,8 @@ def main():
             line[key] = value / ws / fp64["value"]
         if single is not None:
             line["single_instance_fp32"] = single
+        if r.get("planet_force") is not None:
+            line["planet_force"] = r["planet_force"]
         if surrogate is not None:
             line["surrogate_kernels"] = surrogate
         print(json.dumps(line), flush=True)

@@ -126,6 +126,31 @@ int fargo_run_to(fargo_ctx *ctx, double t_end, long long max_steps, int poll, lo
 /* t, last dt, steps taken, latched error code (0 or FARGO_ERR_*). Synchronises. */
 int fargo_get_scalars(fargo_ctx *ctx, double *t, double *dt_last, long long *nsteps, int *err);
 
+/* Force of the gas on a planet at rp (Sec. 3.7, orbital integrator: the
+ * force of the disk on the planets, evaluated once per hydrodynamical step),
+ * per unit planet mass, G = 1:
+ *   a = sum over active cells of rho V (r_c - r_p) / (|r_c - r_p|^2 + eps^2)^(3/2)
+ * with r_c the cell centre (Cartesian coordinates, the star at the origin)
+ * and eps the Plummer softening.  bm08 = 1 removes each ring's mean density
+ * before the sum (the option of the same section: an axisymmetric disk then
+ * exerts no force).  out (host, 4 values) = (a_x, a_y, a_z, the z component
+ * of r_p x a, the specific torque).  Reads the current state; per-cell
+ * arithmetic in the field precision, each lane's per-ring sums in the field
+ * precision added into a compensated total, lanes and blocks summed in
+ * FP64; deterministic.  Cylindrical and spherical meshes.  Synchronises.
+ * Errors: BADARG (NULL, eps < 0 or not finite, non-finite rp, Cartesian
+ * mesh), CUDA. */
+int fargo_planet_force(fargo_ctx *ctx, const double rp[3], double eps, int bm08, double out[4]);
+
+/* fargo_planet_force without the synchronisation: the work is queued on the
+ * context's stream after whatever is queued there (a step, a field upload),
+ * and the 4 FP64 results are written to out, memory the device can write
+ * (device memory, or mapped pinned host memory), 8-byte aligned, owned by
+ * the caller.  Read out after synchronising the stream.  Calls on one
+ * context share its scratch and are ordered by its stream.  Errors: as
+ * fargo_planet_force, plus BADARG for a misaligned out. */
+int fargo_planet_force_async(fargo_ctx *ctx, const double rp[3], double eps, int bm08, double *out);
+
 /* Conserved totals over active cells with compensated FP64 sums:
  * out[0] = sum rho V, out[1] = sum e V, out[2] = sum (Pi-_x + Pi+_x)/2 V
  * (X momentum, angular momentum in cyl/sph; Eqs. 16-17, Tab. momenta).

@@ -206,7 +206,10 @@ class Oracle:
         density first.  Returns (a_x, a_y, a_z, specific torque z)."""
         out = np.zeros(4)
         r = np.ascontiguousarray(rp, dtype=np.float64)
-        lib().or_planet_force(C.byref(self.p), C.byref(self._state(st)), _ptr(r), float(eps), int(bm08), _ptr(out))
+        rho = st["rho"]       # the only field the force reads
+        assert rho.dtype == np.float64 and rho.flags.c_contiguous and rho.shape == self.shape
+        s = OrState(_ptr(rho), None, None, None, None)
+        lib().or_planet_force(C.byref(self.p), C.byref(s), _ptr(r), float(eps), int(bm08), _ptr(out))
         return out
 
     def sums(self, st):

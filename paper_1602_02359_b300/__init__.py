@@ -29,7 +29,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
             "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -80,6 +80,8 @@ def lib():
         L.fargo_run_to.argtypes = [vp, C.c_double, C.c_longlong, C.c_int, C.POINTER(C.c_longlong)]
         L.fargo_get_scalars.argtypes = [vp, PD, PD, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
         L.fargo_sums.argtypes = [vp, PD]
+        L.fargo_planet_force.argtypes = [vp, PD, C.c_double, C.c_int, PD]
+        L.fargo_planet_force_async.argtypes = [vp, PD, C.c_double, C.c_int, vp]
         L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
         L.fargo_get_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
         L.fargo_set_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
@@ -229,6 +231,21 @@ class Fargo:
         out = (C.c_double * 3)()
         _check(lib().fargo_sums(self.h, out), "fargo_sums")
         return tuple(out)
+
+    def planet_force(self, rp, eps, bm08=False):
+        """Force of the gas on a planet at rp = (x, y, z) per unit planet mass
+        (fargo_planet_force): (a_x, a_y, a_z, specific z torque)."""
+        r = (C.c_double * 3)(*[float(v) for v in rp])
+        out = (C.c_double * 4)()
+        _check(lib().fargo_planet_force(self.h, r, float(eps), int(bool(bm08)), out), "fargo_planet_force")
+        return tuple(out)
+
+    def planet_force_async(self, rp, eps, out_ptr, bm08=False):
+        """fargo_planet_force_async: queue the force on the context's stream,
+        its 4 FP64 results written to the device address out_ptr."""
+        r = (C.c_double * 3)(*[float(v) for v in rp])
+        _check(lib().fargo_planet_force_async(self.h, r, float(eps), int(bool(bm08)), C.c_void_p(out_ptr)),
+               "fargo_planet_force_async")
 
     def debug_phase(self, phase, dt=0.0):
         _check(lib().fargo_debug_phase(self.h, phase, dt), f"fargo_debug_phase({phase})")

@@ -12,6 +12,7 @@
 #include "kernels_bc_cfl.cuh"
 #include "kernels_source.cuh"
 #include "kernels_transport.cuh"
+#include "kernels_planet.cuh"
 
 namespace fk {
 
@@ -64,6 +65,7 @@ struct fargo_ctx {
     bool own_stream = false;
     fk::Scal *sc = nullptr;
     double *v0 = nullptr, *part = nullptr, *part2 = nullptr, *sums = nullptr, *vol = nullptr;
+    double *pf = nullptr;   // planet force: result (4), then the azimuth tables (4 nx)
     float *ringmax = nullptr;
     int nrings_active = 0, cfl_blocks = 0, sum_blocks = 0;
     fk::Buffers<double> b64;

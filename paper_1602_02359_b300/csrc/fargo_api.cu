@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -560,6 +561,9 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     c->part2 = (double *)p;
     if ((rc = dalloc(c, &p, sizeof(double) * 4))) goto fail;
     c->sums = (double *)p;
+    // planet force: result, then the azimuth and ring tables of one call
+    if ((rc = dalloc(c, &p, sizeof(double) * (4 + 2 * (size_t)c->pitch + 4 * (size_t)c->nrings_active)))) goto fail;
+    c->pf = (double *)p;
     if ((rc = upload<double>(c, (const double **)&c->vol, c->hg.vol))) goto fail;
     if (c->prec == FARGO_F64) {
         if ((rc = alloc_fields<double>(c, c->b64))) goto fail;
@@ -836,6 +840,75 @@ extern "C" int fargo_sums_noalloc(const void *rho, const void *e, const void *vx
                                          g_noalloc_ptr[dev]);
     return sums_noalloc_impl<float>(rho, e, vx, nx, ny, nz, ghost, vol, R, omega_frame, nblocks, out, st,
                                     g_noalloc_ptr[dev]);
+}
+
+// ---------------------------------------------------------------------------
+// Force of the gas on a planet (kernels_planet.cuh).
+// ---------------------------------------------------------------------------
+template <typename T>
+static int pforce_impl(fargo_ctx *c, Buffers<T> &b, const double rp[3], double eps, int bm08, double *out)
+{
+    const MeshD &m = c->m;
+    cudaStream_t s = c->stream;
+    const double Rp = sqrt(rp[0] * rp[0] + rp[1] * rp[1]);
+    const double php = Rp > 0.0 ? atan2(rp[1], rp[0]) : 0.0;
+    T *tab = reinterpret_cast<T *>(c->pf + 4);
+    const int nt = std::max(m.nx, c->nrings_active);
+    k_pforce_tables<T><<<grid_for(nt, 256), 256, 0, s>>>(tab, m.nx, m.sj, m.xmin, m.dx, php, b.tab.Rd, b.tab.zcd,
+                                                          c->vol, Rp, rp[2], m.j0, m.j1, m.k0, m.k1, m.nyt);
+    PForceArgs<T> a{};
+    a.rho = b.A.rho;
+    a.tab = tab;
+    a.cph = Rp > 0.0 ? rp[0] / Rp : 1.0;
+    a.sph = Rp > 0.0 ? rp[1] / Rp : 0.0;
+    a.Rp = Rp;
+    a.eps2 = (T)(eps * eps);
+    a.nx = m.nx;
+    a.j0 = m.j0;
+    a.j1 = m.j1;
+    a.k0 = m.k0;
+    a.k1 = m.k1;
+    a.nyt = m.nyt;
+    a.sj = m.sj;
+    a.sk = m.sk;
+    // one resident wave; part2 holds 3 partials for up to 2 * sum_blocks blocks
+    const int grid = std::min(148 * pforce_blocks_per_sm<T>(), 2 * c->sum_blocks);
+    if (bm08)
+        k_planet_force<T, true><<<grid, 256, 0, s>>>(a, c->part2, &c->sc->counter2, out);
+    else
+        k_planet_force<T, false><<<grid, 256, 0, s>>>(a, c->part2, &c->sc->counter2, out);
+    CK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+static int pforce_check(fargo_ctx *c, const double rp[3], double eps, const double *out)
+{
+    if (!c || !rp || !out || !(eps >= 0.0) || !isfinite(eps) || !isfinite(rp[0]) || !isfinite(rp[1]) ||
+        !isfinite(rp[2]))
+        return FARGO_ERR_BADARG;
+    if (c->geom == FARGO_CART) return FARGO_ERR_BADARG;
+    if ((reinterpret_cast<uintptr_t>(out) & 7u) != 0) return FARGO_ERR_BADARG;
+    return FARGO_OK;
+}
+
+extern "C" int fargo_planet_force_async(fargo_ctx *c, const double rp[3], double eps, int bm08, double *out)
+{
+    int rc = pforce_check(c, rp, eps, out);
+    if (rc) return rc;
+    return c->prec == FARGO_F64 ? pforce_impl<double>(c, c->b64, rp, eps, bm08, out)
+                                : pforce_impl<float>(c, c->b32, rp, eps, bm08, out);
+}
+
+extern "C" int fargo_planet_force(fargo_ctx *c, const double rp[3], double eps, int bm08, double out[4])
+{
+    int rc = pforce_check(c, rp, eps, out);
+    if (rc) return rc;
+    rc = c->prec == FARGO_F64 ? pforce_impl<double>(c, c->b64, rp, eps, bm08, c->pf)
+                              : pforce_impl<float>(c, c->b32, rp, eps, bm08, c->pf);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, c->pf, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
 }
 
 extern "C" int fargo_sums(fargo_ctx *c, double out[3])

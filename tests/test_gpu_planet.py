@@ -1,0 +1,143 @@
+"""Force of the gas on a planet (fargo_planet_force through the C ABI)
+against the FP64 oracle.
+
+Tolerances, relative to the size |a_x| + |a_y| + |a_z| of the oracle's force
+(the torque relative to R_p times that size, its natural scale):
+FP64 1e-11 (the GPU sums in another order and in the planet's frame);
+FP32 2e-5 against the oracle fed the same FP32-rounded density (per-cell
+FP32 arithmetic, sums in FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests.gpu_util import make_ctx, record
+
+pytestmark = pytest.mark.gpu
+
+
+def lumpy(w, seed):
+    st = w.copy().state
+    rng = np.random.default_rng(seed)
+    st["rho"] = st["rho"] * (1.0 + 0.3 * rng.uniform(-1, 1, size=st["rho"].shape))
+    w.state = st
+    return w
+
+
+CASES = [
+    ("disk2d", lambda: lumpy(W.disk2d(nx=300, ny=70, q=1e-3), 1)),
+    ("sph", lambda: lumpy(W.random_box(W.SPH, 96, 24, 14, seed=2, iso=False, nu=1e-3), 2)),
+]
+PLANETS = [(1.0, 0.0, 0.0), (0.7, 0.75, 0.0), (-0.9, 0.2, 0.05)]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("bm08", [False, True])
+def test_planet_force_fp64_matches_oracle(name, make, bm08):
+    w = make()
+    o = oracle.Oracle(w)
+    c = make_ctx(w)
+    eps = 0.03
+    for ip, rp in enumerate(PLANETS):
+        g = np.array(c.planet_force(rp, eps, bm08))
+        f = o.planet_force(w.state, rp, eps, bm08)
+        scale = np.sum(np.abs(f[:3]))
+        Rp = math.hypot(rp[0], rp[1])
+        e = np.max(np.abs(g[:3] - f[:3])) / scale
+        et = abs(g[3] - f[3]) / (Rp * scale)
+        record(f"planet_force_fp64_{name}_bm08{int(bm08)}", planet=ip, rel_force=e, rel_torque=et)
+        assert e < 1e-11 and et < 1e-11, (rp, g, f)
+    c.close()
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("bm08", [False, True])
+def test_planet_force_fp32_within_tolerance(name, make, bm08):
+    import paper_1602_02359_b300 as fb
+    w = make()
+    c = make_ctx(w, fb.F32)
+    st32 = dict(w.state)
+    st32["rho"] = w.state["rho"].astype(np.float32).astype(np.float64)
+    o = oracle.Oracle(w)
+    eps = 0.03
+    for ip, rp in enumerate(PLANETS):
+        g = np.array(c.planet_force(rp, eps, bm08))
+        f = o.planet_force(st32, rp, eps, bm08)
+        scale = np.sum(np.abs(f[:3]))
+        Rp = math.hypot(rp[0], rp[1])
+        e = np.max(np.abs(g[:3] - f[:3])) / scale
+        et = abs(g[3] - f[3]) / (Rp * scale)
+        record(f"planet_force_fp32_{name}_bm08{int(bm08)}", planet=ip, rel_force=e, rel_torque=et)
+        assert e < 2e-5 and et < 2e-5, (rp, g, f)
+    c.close()
+
+
+def test_planet_force_full_size_3d_disk_fp32():
+    """The 1536 x 512 x 96 disk of the benchmark, FP32, its density made
+    non-axisymmetric (seeded 1 % noise: the initial disk is axisymmetric, on
+    which the BM08 force vanishes identically), the planet of its potential at
+    t = 0 and another off the midplane, against the oracle fed the same
+    FP32-rounded density (only the density is uploaded to either)."""
+    import paper_1602_02359_b300 as fb
+    w = W.disk3d()
+    rho = w.state["rho"]
+    rng = np.random.default_rng(17)
+    for k in range(rho.shape[0]):
+        rho[k] *= 1.0 + 0.01 * rng.uniform(-1, 1, size=rho[k].shape)
+    c = fb.Fargo(w, fb.F32)
+    c.set_field("rho", rho)
+    w.state = None
+    o = oracle.Oracle(w)
+    st = {"rho": rho.astype(np.float32).astype(np.float64), "e": None, "vx": None, "vy": None, "vz": None}
+    for ip, rp in enumerate([(w.planet_a, 0.0, 0.0), (0.8, -0.5, 0.02)]):
+        for bm08 in (False, True):
+            g = np.array(c.planet_force(rp, w.planet_eps, bm08))
+            f = o.planet_force(st, rp, w.planet_eps, bm08)
+            scale = np.sum(np.abs(f[:3]))
+            Rp = math.hypot(rp[0], rp[1])
+            e = np.max(np.abs(g[:3] - f[:3])) / scale
+            et = abs(g[3] - f[3]) / (Rp * scale)
+            record("planet_force_fp32_disk3d_full", planet=ip, bm08=bm08, rel_force=e, rel_torque=et)
+            assert e < 2e-5 and et < 2e-5, (rp, bm08, g, f)
+    c.close()
+
+
+def test_planet_force_rejects_bad_arguments():
+    import paper_1602_02359_b300 as fb
+    w = W.random_box(W.CART, 16, 8, 1, seed=1, planet=False)
+    c = make_ctx(w)
+    with pytest.raises(fb.FargoError):
+        c.planet_force((1.0, 0.0, 0.0), 0.03)
+    c.close()
+    w = W.disk2d(nx=32, ny=8)
+    c = make_ctx(w)
+    with pytest.raises(fb.FargoError):
+        c.planet_force((1.0, 0.0, 0.0), -1.0)
+    with pytest.raises(fb.FargoError):
+        c.planet_force((float("nan"), 0.0, 0.0), 0.03)
+    c.close()
+
+
+def test_planet_force_async_equals_the_synchronous_call():
+    """fargo_planet_force_async, queued twice behind each other on the
+    context's stream into device memory, gives bit for bit the synchronous
+    call's result (the reduction order is fixed); a misaligned result
+    pointer is refused before anything is queued."""
+    import torch
+    import paper_1602_02359_b300 as fb
+    w = lumpy(W.disk2d(nx=300, ny=70, q=1e-3), 5)
+    c = make_ctx(w, fb.F32)
+    res = torch.zeros(8, dtype=torch.float64, device="cuda")
+    for bm08 in (False, True):
+        g = np.array(c.planet_force((0.7, 0.75, 0.0), 0.03, bm08))
+        c.planet_force_async((0.7, 0.75, 0.0), 0.03, res.data_ptr(), bm08)
+        c.planet_force_async((0.7, 0.75, 0.0), 0.03, res.data_ptr() + 32, bm08)
+        c.planet_force((0.7, 0.75, 0.0), 0.03, bm08)   # synchronises the context's stream
+        a = res.cpu().numpy()
+        assert np.array_equal(a[:4], g) and np.array_equal(a[4:], g), (a, g)
+    with pytest.raises(fb.FargoError):
+        c.planet_force_async((0.7, 0.75, 0.0), 0.03, res.data_ptr() + 4)
+    c.close()
