@@ -151,6 +151,57 @@ int fargo_planet_force(fargo_ctx *ctx, const double rp[3], double eps, int bm08,
  * fargo_planet_force, plus BADARG for a misaligned out. */
 int fargo_planet_force_async(fargo_ctx *ctx, const double rp[3], double eps, int bm08, double *out);
 
+/* Planets per call of the planetary entry points below (one lane each). */
+#define FARGO_MAX_PLANETS 32
+
+/* fargo_planet_force_async for n planets whose positions are on the device:
+ * planet i at y + i*stride (x, y, z; stride >= 3 doubles, e.g. 6 for the
+ * state rows of fargo_nbody_rk5_async), its 4 results at out + 4*i.  y and
+ * out are device memory, 8-byte aligned, owned by the caller; nothing is
+ * read on the host, so the call can follow a step with no synchronisation.
+ * Errors: BADARG (NULL, n < 1, stride < 3, eps < 0 or not finite,
+ * misaligned pointer, Cartesian mesh), SIZE (n > FARGO_MAX_PLANETS), CUDA. */
+int fargo_planets_force_async(fargo_ctx *ctx, int n, const double *y, int stride, double eps, int bm08,
+                              double *out);
+
+/* One step of the planetary integrator (Sec. 3.7, orbital integrator for
+ * planets): the fifth-order Cash-Karp Runge-Kutta method with the Butcher
+ * tableau of Tab. rk, fixed step h, for n planets orbiting a star of mass
+ * mstar, G = 1, FP64, in the star's frame:
+ *   d2r_i/dt2 = -(mstar + m_i) r_i/|r_i|^3
+ *               + sum_{j != i} m_j [(r_j - r_i)/|r_j - r_i|^3 - r_j/|r_j|^3]
+ * (with indirect = 0 the frame terms are dropped: the m_i beside mstar and
+ * the bracket's second term).  No softening between planets.  Before the
+ * stages, when kick is given, the gas force updates the velocities:
+ * v_i += h (kick_i - kick_star), kick_i = kick + i*kick_stride (3 values
+ * used; kick_stride >= 3, 4 for the output of fargo_planets_force_async),
+ * kick_star (3 values, may be NULL) the star's gas acceleration.
+ * y: [n][6] = (x, y, z, vx, vy, vz) per planet, updated in place; mass: [n].
+ * h_dev, when not NULL, holds h on the device (the argument h is then
+ * ignored).  All pointers are device memory, 8-byte aligned, owned by the
+ * caller.  Queued on `stream` (NULL = legacy default stream); synchronise
+ * it before reading y.  Errors: BADARG (NULL y or mass, n < 1, mstar < 0,
+ * non-finite mstar or h, kick_stride < 3 with a kick, kick_star without a
+ * kick, misaligned pointer), SIZE (n > FARGO_MAX_PLANETS), CUDA. */
+int fargo_nbody_rk5_async(int n, double *y, const double *mass, double mstar, double h, const double *h_dev,
+                          const double *kick, int kick_stride, const double *kick_star, int indirect,
+                          void *stream);
+
+/* The planets' update after a hydrodynamical step, queued on the context's
+ * stream behind it (Sec. 3.7: the gas force, evaluated once per step,
+ * updates the velocities; then the planets move by the step's dt):
+ *   1. the gas force on each planet at its position in y (softening eps,
+ *      BM08 option as fargo_planet_force);
+ *   2. with indirect = 1, the gas force on the star at the origin
+ *      (unsoftened), subtracted from each planet's (the star's frame);
+ *   3. fargo_nbody_rk5_async with h = the dt of the context's last step,
+ *      read on the device, and the context's star mass.
+ * y ([n][6]) and mass ([n]) are device memory owned by the caller; y is
+ * updated in place.  The force scratch belongs to the context.  Errors: as
+ * fargo_planets_force_async. */
+int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *mass, double eps, int bm08,
+                                int indirect);
+
 /* Conserved totals over active cells with compensated FP64 sums:
  * out[0] = sum rho V, out[1] = sum e V, out[2] = sum (Pi-_x + Pi+_x)/2 V
  * (X momentum, angular momentum in cyl/sph; Eqs. 16-17, Tab. momenta).

@@ -29,7 +29,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
             "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -37,6 +37,16 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_mlp_ensemble")
 
 PD = C.POINTER(C.c_double)
+
+
+def nbody_rk5_async(n, y_ptr, mass_ptr, mstar, h=0.0, h_ptr=None, kick_ptr=None, kick_stride=4,
+                    kick_star_ptr=None, indirect=True, stream=None):
+    """fargo_nbody_rk5_async: one Cash-Karp step of n planets (device arrays
+    y [n][6], mass [n]), queued on `stream` (a CUDA stream handle or None)."""
+    vp = C.c_void_p
+    _check(lib().fargo_nbody_rk5_async(int(n), vp(y_ptr), vp(mass_ptr), float(mstar), float(h), vp(h_ptr),
+                                       vp(kick_ptr), int(kick_stride), vp(kick_star_ptr), int(bool(indirect)),
+                                       vp(stream)), "fargo_nbody_rk5_async")
 
 
 class FargoError(RuntimeError):
@@ -82,6 +92,10 @@ def lib():
         L.fargo_sums.argtypes = [vp, PD]
         L.fargo_planet_force.argtypes = [vp, PD, C.c_double, C.c_int, PD]
         L.fargo_planet_force_async.argtypes = [vp, PD, C.c_double, C.c_int, vp]
+        L.fargo_planets_force_async.argtypes = [vp, C.c_int, vp, C.c_int, C.c_double, C.c_int, vp]
+        L.fargo_nbody_rk5_async.argtypes = [C.c_int, vp, vp, C.c_double, C.c_double, vp, vp, C.c_int, vp, C.c_int,
+                                            vp]
+        L.fargo_planets_advance_async.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int]
         L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
         L.fargo_get_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
         L.fargo_set_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
@@ -246,6 +260,19 @@ class Fargo:
         r = (C.c_double * 3)(*[float(v) for v in rp])
         _check(lib().fargo_planet_force_async(self.h, r, float(eps), int(bool(bm08)), C.c_void_p(out_ptr)),
                "fargo_planet_force_async")
+
+    def planets_force_async(self, n, y_ptr, stride, eps, out_ptr, bm08=False):
+        """fargo_planets_force_async: the gas force on n planets whose
+        positions are on the device (planet i at y_ptr + 8*stride*i)."""
+        _check(lib().fargo_planets_force_async(self.h, int(n), C.c_void_p(y_ptr), int(stride), float(eps),
+                                               int(bool(bm08)), C.c_void_p(out_ptr)), "fargo_planets_force_async")
+
+    def planets_advance_async(self, n, y_ptr, mass_ptr, eps, bm08=False, indirect=True):
+        """fargo_planets_advance_async: gas force, kick and one Cash-Karp step
+        of the planets (device arrays y [n][6], mass [n]) by the last dt."""
+        _check(lib().fargo_planets_advance_async(self.h, int(n), C.c_void_p(y_ptr), C.c_void_p(mass_ptr),
+                                                 float(eps), int(bool(bm08)), int(bool(indirect))),
+               "fargo_planets_advance_async")
 
     def debug_phase(self, phase, dt=0.0):
         _check(lib().fargo_debug_phase(self.h, phase, dt), f"fargo_debug_phase({phase})")

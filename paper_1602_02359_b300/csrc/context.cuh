@@ -13,6 +13,7 @@
 #include "kernels_source.cuh"
 #include "kernels_transport.cuh"
 #include "kernels_planet.cuh"
+#include "kernels_nbody.cuh"
 
 namespace fk {
 
@@ -65,7 +66,9 @@ struct fargo_ctx {
     bool own_stream = false;
     fk::Scal *sc = nullptr;
     double *v0 = nullptr, *part = nullptr, *part2 = nullptr, *sums = nullptr, *vol = nullptr;
-    double *pf = nullptr;   // planet force: result (4), then the azimuth tables (4 nx)
+    double *pf = nullptr;   // planet force: result (4), then the azimuth and ring tables of one call
+    double *pacc = nullptr; // planetary step: gas accelerations of up to kNbMax planets and of the star (4 each)
+    double star_mass = 0.0;
     float *ringmax = nullptr;
     int nrings_active = 0, cfl_blocks = 0, sum_blocks = 0;
     fk::Buffers<double> b64;

@@ -489,6 +489,7 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     fargo_ctx *c = new fargo_ctx();
     c->prec = prm->precision;
     c->nx = nx; c->ny = ny; c->nz = nz; c->g = ghost; c->geom = geom;
+    c->star_mass = prm->star_mass;
     c->nyt = ny > 1 ? ny + 2 * ghost : 1;
     c->nzt = nz > 1 ? nz + 2 * ghost : 1;
     c->pitch = (nx + 31) / 32 * 32;
@@ -564,6 +565,8 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     // planet force: result, then the azimuth and ring tables of one call
     if ((rc = dalloc(c, &p, sizeof(double) * (4 + 2 * (size_t)c->pitch + 4 * (size_t)c->nrings_active)))) goto fail;
     c->pf = (double *)p;
+    if ((rc = dalloc(c, &p, sizeof(double) * 4 * (kNbMax + 1)))) goto fail;
+    c->pacc = (double *)p;
     if ((rc = upload<double>(c, (const double **)&c->vol, c->hg.vol))) goto fail;
     if (c->prec == FARGO_F64) {
         if ((rc = alloc_fields<double>(c, c->b64))) goto fail;
@@ -846,22 +849,18 @@ extern "C" int fargo_sums_noalloc(const void *rho, const void *e, const void *vx
 // Force of the gas on a planet (kernels_planet.cuh).
 // ---------------------------------------------------------------------------
 template <typename T>
-static int pforce_impl(fargo_ctx *c, Buffers<T> &b, const double rp[3], double eps, int bm08, double *out)
+static int pforce_impl(fargo_ctx *c, Buffers<T> &b, PfPlanet pl, double eps, int bm08, double *out)
 {
     const MeshD &m = c->m;
     cudaStream_t s = c->stream;
-    const double Rp = sqrt(rp[0] * rp[0] + rp[1] * rp[1]);
-    const double php = Rp > 0.0 ? atan2(rp[1], rp[0]) : 0.0;
     T *tab = reinterpret_cast<T *>(c->pf + 4);
     const int nt = std::max(m.nx, c->nrings_active);
-    k_pforce_tables<T><<<grid_for(nt, 256), 256, 0, s>>>(tab, m.nx, m.sj, m.xmin, m.dx, php, b.tab.Rd, b.tab.zcd,
-                                                          c->vol, Rp, rp[2], m.j0, m.j1, m.k0, m.k1, m.nyt);
+    k_pforce_tables<T><<<grid_for(nt, 256), 256, 0, s>>>(tab, m.nx, m.sj, m.xmin, m.dx, pl, b.tab.Rd, b.tab.zcd,
+                                                          c->vol, m.j0, m.j1, m.k0, m.k1, m.nyt);
     PForceArgs<T> a{};
     a.rho = b.A.rho;
     a.tab = tab;
-    a.cph = Rp > 0.0 ? rp[0] / Rp : 1.0;
-    a.sph = Rp > 0.0 ? rp[1] / Rp : 0.0;
-    a.Rp = Rp;
+    a.pl = pl;
     a.eps2 = (T)(eps * eps);
     a.nx = m.nx;
     a.j0 = m.j0;
@@ -881,13 +880,21 @@ static int pforce_impl(fargo_ctx *c, Buffers<T> &b, const double rp[3], double e
     return FARGO_OK;
 }
 
+static int pforce_any(fargo_ctx *c, PfPlanet pl, double eps, int bm08, double *out)
+{
+    return c->prec == FARGO_F64 ? pforce_impl<double>(c, c->b64, pl, eps, bm08, out)
+                                : pforce_impl<float>(c, c->b32, pl, eps, bm08, out);
+}
+
+static bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
 static int pforce_check(fargo_ctx *c, const double rp[3], double eps, const double *out)
 {
     if (!c || !rp || !out || !(eps >= 0.0) || !isfinite(eps) || !isfinite(rp[0]) || !isfinite(rp[1]) ||
         !isfinite(rp[2]))
         return FARGO_ERR_BADARG;
     if (c->geom == FARGO_CART) return FARGO_ERR_BADARG;
-    if ((reinterpret_cast<uintptr_t>(out) & 7u) != 0) return FARGO_ERR_BADARG;
+    if (!aligned8(out)) return FARGO_ERR_BADARG;
     return FARGO_OK;
 }
 
@@ -895,20 +902,81 @@ extern "C" int fargo_planet_force_async(fargo_ctx *c, const double rp[3], double
 {
     int rc = pforce_check(c, rp, eps, out);
     if (rc) return rc;
-    return c->prec == FARGO_F64 ? pforce_impl<double>(c, c->b64, rp, eps, bm08, out)
-                                : pforce_impl<float>(c, c->b32, rp, eps, bm08, out);
+    return pforce_any(c, PfPlanet{rp[0], rp[1], rp[2], nullptr}, eps, bm08, out);
 }
 
 extern "C" int fargo_planet_force(fargo_ctx *c, const double rp[3], double eps, int bm08, double out[4])
 {
     int rc = pforce_check(c, rp, eps, out);
     if (rc) return rc;
-    rc = c->prec == FARGO_F64 ? pforce_impl<double>(c, c->b64, rp, eps, bm08, c->pf)
-                              : pforce_impl<float>(c, c->b32, rp, eps, bm08, c->pf);
-    if (rc) return rc;
+    if ((rc = pforce_any(c, PfPlanet{rp[0], rp[1], rp[2], nullptr}, eps, bm08, c->pf))) return rc;
     CK(cudaMemcpyAsync(out, c->pf, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return FARGO_OK;
+}
+
+extern "C" int fargo_planets_force_async(fargo_ctx *c, int n, const double *y, int stride, double eps, int bm08,
+                                         double *out)
+{
+    if (!c || !y || !out || n < 1 || stride < 3 || !(eps >= 0.0) || !isfinite(eps)) return FARGO_ERR_BADARG;
+    if (c->geom == FARGO_CART || !aligned8(y) || !aligned8(out)) return FARGO_ERR_BADARG;
+    if (n > kNbMax) return FARGO_ERR_SIZE;
+    for (int i = 0; i < n; i++) {
+        const int rc = pforce_any(c, PfPlanet{0.0, 0.0, 0.0, y + (size_t)stride * i}, eps, bm08, out + 4 * i);
+        if (rc) return rc;
+    }
+    return FARGO_OK;
+}
+
+static int nbody_launch(int n, double *y, const double *mass, double mstar, double h, const double *h_dev,
+                        const double *kick, int kick_stride, const double *kick_star, int indirect,
+                        cudaStream_t s)
+{
+    NbArgs a{};
+    a.y = y;
+    a.mass = mass;
+    a.kick = kick;
+    a.kick_star = kick_star;
+    a.h_dev = h_dev;
+    a.mstar = mstar;
+    a.h = h;
+    a.n = n;
+    a.kick_stride = kick_stride;
+    a.indirect = indirect ? 1 : 0;
+    k_nbody_rk5<<<1, 32, 0, s>>>(a);
+    CK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+extern "C" int fargo_nbody_rk5_async(int n, double *y, const double *mass, double mstar, double h,
+                                     const double *h_dev, const double *kick, int kick_stride,
+                                     const double *kick_star, int indirect, void *stream)
+{
+    if (!y || !mass || n < 1 || !(mstar >= 0.0) || !isfinite(mstar) || !isfinite(h)) return FARGO_ERR_BADARG;
+    if (kick && kick_stride < 3) return FARGO_ERR_BADARG;
+    if (kick_star && !kick) return FARGO_ERR_BADARG;
+    if (!aligned8(y) || !aligned8(mass) || !aligned8(h_dev) || !aligned8(kick) || !aligned8(kick_star))
+        return FARGO_ERR_BADARG;
+    if (n > kNbMax) return FARGO_ERR_SIZE;
+    return nbody_launch(n, y, mass, mstar, h, h_dev, kick, kick_stride, kick_star, indirect,
+                        static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int fargo_planets_advance_async(fargo_ctx *c, int n, double *y, const double *mass, double eps, int bm08,
+                                           int indirect)
+{
+    if (!c || !y || !mass || n < 1 || !(eps >= 0.0) || !isfinite(eps)) return FARGO_ERR_BADARG;
+    if (c->geom == FARGO_CART || !aligned8(y) || !aligned8(mass)) return FARGO_ERR_BADARG;
+    if (n > kNbMax) return FARGO_ERR_SIZE;
+    int rc = fargo_planets_force_async(c, n, y, 6, eps, bm08, c->pacc);
+    if (rc) return rc;
+    const double *star = nullptr;
+    if (indirect) {
+        // the star sits at the origin, which no cell of a cylindrical or spherical mesh contains
+        if ((rc = pforce_any(c, PfPlanet{0.0, 0.0, 0.0, nullptr}, 0.0, 0, c->pacc + 4 * kNbMax))) return rc;
+        star = c->pacc + 4 * kNbMax;
+    }
+    return nbody_launch(n, y, mass, c->star_mass, 0.0, &c->sc->dt, c->pacc, 4, star, indirect, c->stream);
 }
 
 extern "C" int fargo_sums(fargo_ctx *c, double out[3])

@@ -24,12 +24,32 @@
 
 namespace fk {
 
+// The planet's position: by value, or read from device memory (x, y, z at
+// dev) when dev is set, so that a planet integrated on the device needs no
+// round trip through the host.
+struct PfPlanet {
+    double x, y, z;
+    const double *dev;
+    __device__ __forceinline__ void get(double &px, double &py, double &pz) const
+    {
+        if (dev) {
+            px = dev[0];
+            py = dev[1];
+            pz = dev[2];
+        } else {
+            px = x;
+            py = y;
+            pz = z;
+        }
+    }
+};
+
 template <typename T>
 struct PForceArgs {
     const T *rho;
     const T *tab;                   // sin^2(dphi/2) [nx], sin(dphi) [nx] (each padded to the row pitch sj),
                                     // then per active ring R, R - R_p, Z - z_p, V
-    double cph, sph, Rp;            // the planet's azimuth and cylindrical radius
+    PfPlanet pl;                    // the planet's position
     T eps2;                         // squared softening
     int nx, j0, j1, k0, k1, nyt, sj, sk;
 };
@@ -40,13 +60,16 @@ struct PForceArgs {
 // (formed in FP64, so no nearby large numbers are subtracted in the field
 // precision) and the cell volume.  One thread per azimuth or ring.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pforce_tables(T *tab, int nx, int sj, double xmin, double dx, double php,
+__global__ void __launch_bounds__(256) k_pforce_tables(T *tab, int nx, int sj, double xmin, double dx, PfPlanet pl,
                                                        const double *Rd, const double *zcd, const double *vol,
-                                                       double Rp, double zp, int j0, int j1, int k0, int k1,
-                                                       int nyt)
+                                                       int j0, int j1, int k0, int k1, int nyt)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double px, py, pz;
+    pl.get(px, py, pz);
+    const double Rp = sqrt(px * px + py * py);
     if (t < nx) {
+        const double php = Rp > 0.0 ? atan2(py, px) : 0.0;
         const double d = (xmin + (t + 0.5) * dx) - php;
         const double h = sin(0.5 * d);
         tab[t] = (T)(h * h);
@@ -58,7 +81,7 @@ __global__ void __launch_bounds__(256) k_pforce_tables(T *tab, int nx, int sj, d
         T *rt = tab + 2 * (size_t)sj + 4 * (size_t)t;
         rt[0] = (T)Rd[ring];
         rt[1] = (T)(Rd[ring] - Rp);
-        rt[2] = (T)(zcd[ring] - zp);
+        rt[2] = (T)(zcd[ring] - pz);
         rt[3] = (T)vol[ring];
     }
 }
@@ -221,10 +244,14 @@ __global__ void __launch_bounds__(256, pforce_blocks_per_sm<T>()) k_planet_force
             bz += __ldcg(&part[3 * b + 2]);
         }
         // back from the planet's frame; the torque is R_p a_y' (z component of r_p x a)
-        out[0] = bx * a.cph - by * a.sph;
-        out[1] = bx * a.sph + by * a.cph;
+        double px, py, pz;
+        a.pl.get(px, py, pz);
+        const double Rp = sqrt(px * px + py * py);
+        const double cph = Rp > 0.0 ? px / Rp : 1.0, sph = Rp > 0.0 ? py / Rp : 0.0;
+        out[0] = bx * cph - by * sph;
+        out[1] = bx * sph + by * cph;
         out[2] = bz;
-        out[3] = a.Rp * by;
+        out[3] = Rp * by;
         *counter = 0u;
     }
 }

@@ -32,6 +32,8 @@ CASES = [
     # halo, at 600 cells; two at 480)
     (W.CYL, 600, 9, 1, True, 1e-3, W.BC_FROZEN),
     (W.SPH, 480, 10, 6, False, 1e-3, W.BC_REFLECT),
+    # one azimuthal cell: an axisymmetric disk (no X derivatives, no X sweep)
+    (W.CYL, 1, 40, 1, True, 1e-3, W.BC_ZEROGRAD),
 ]
 IDS = [f"g{c[0]}-{c[1]}x{c[2]}x{c[3]}-{'iso' if c[4] else 'adi'}-nu{c[5]}-bc{c[6]}" for c in CASES]
 

@@ -211,6 +211,63 @@ def disk3d(nx=1536, ny=512, nz=96, h=0.05, alpha=1e-3, q=3e-4, g=3, rho0=1e-3,
     return w
 
 
+def viscous_ring_profile(r, t, nu=1e-5, mass=1.0, r0=1.0):
+    """Surface density and radial velocity of a ring of mass `mass`, started
+    infinitely narrow at radius r0, spreading under a constant viscosity nu
+    (Sec. 5.1, viscous spread of a gaseous ring): with u = r/r0 and
+    tau = 12 nu t / r0^2,
+        Sigma = mass / (pi r0^2) / (tau u^(1/4)) I_n(2u/tau) exp(-(1 + u^2)/tau),
+        v_r   = 6 nu / (tau r0) (u - I_(n-1)(2u/tau) / I_n(2u/tau)),
+    n = 1/4 (the order the paper leaves unnamed; with it the v_r expression
+    follows from the flux r Sigma v_r = -3 sqrt(r) d/dr (nu sqrt(r) Sigma)).
+    The Bessel functions are taken exponentially scaled, I_n(x) =
+    ive(n, x) e^x, so that the exponents combine to -(1 - u)^2 / tau and
+    nothing overflows for narrow rings."""
+    from scipy.special import ive
+    r = np.asarray(r, dtype=np.float64)
+    tau = 12.0 * nu * t / (r0 * r0)
+    u = r / r0
+    x = 2.0 * u / tau
+    i_n = ive(0.25, x)
+    sigma = mass / (math.pi * r0 * r0) / (tau * u ** 0.25) * i_n * np.exp(-(1.0 - u) ** 2 / tau)
+    vr = 6.0 * nu / (tau * r0) * (u - ive(-0.75, x) / i_n)
+    return sigma, vr
+
+
+def viscous_ring(ny=512, nx=1, nu=1e-5, t0=100.0, t_end=1100.0, cs=0.0, floor=1e-10, g=3, cq=1.41):
+    """The viscous-ring test of Sec. 5.1: an axisymmetric Keplerian ring of
+    unit mass at r0 = 1 around a unit-mass star, constant viscosity nu,
+    0.1 <= r <= 1.6 on ny evenly spaced cylindrical cells, zero-gradient
+    radial boundaries, started from the analytic profile at t0 and run to
+    t_end.  Pressure is neglected, as in the analytic solution: isothermal
+    with a uniform sound speed cs = 0 by default (already cs = 1e-3 spreads
+    the ring by pressure about as fast as the viscosity does, since the
+    viscous drift is only ~1e-4).  The density is floored at `floor` times its peak
+    so that the exponentially small wings stay well inside FP32's range.
+    v_phi is Keplerian at cell centres, v_r the analytic value at the radial
+    faces.  nx azimuthal cells carry identical copies (no orbital advection:
+    the ring is axisymmetric)."""
+    yf = faces(ny, g, 0.1, 1.6)
+    zf = faces(1, g, -0.5, 0.5)
+    w = Workload("viscous_ring", CYL, nx, ny, 1, g, -math.pi, math.pi, yf, zf, 1.4, True,
+                 None, None, 0.44, cq, False, 0.0,
+                 (BC_ZEROGRAD, BC_ZEROGRAD), (BC_ZEROGRAD, BC_ZEROGRAD),
+                 1.0, 0.0, 1.0, 0.0, False, t0, t_end, {})
+    w.cs = np.full((w.nz_t, w.ny_t), cs)
+    w.nu = np.full((w.nz_t, w.ny_t), nu)
+    w.ring_nu = nu
+    ym = centres(yf)
+    sig, _ = viscous_ring_profile(ym, t0, nu)
+    _, vr = viscous_ring_profile(yf[:w.ny_t + 1], t0, nu)
+    sig = np.maximum(sig, floor * sig.max())
+    st = _empty(w.shape)
+    st["rho"][:w.nz_t, :w.ny_t, :] = sig[None, :, None]
+    st["vx"][:w.nz_t, :w.ny_t, :] = np.sqrt(1.0 / ym)[None, :, None]
+    st["vy"][:w.nz_t, :w.ny_t + 1, :] = vr[None, :, None]
+    w.state = st
+    return w
+
+
 def batch_params(n=256, seed=1602):
     """Parameter draws of the batched disk sweep (numpy PCG64, fixed seed).
 
