@@ -31,6 +31,7 @@ same workload on the host cores (rank 0 only).
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -641,6 +642,75 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
             "state_gb": cells * 2 * 22 * 4 / 1e9}
 
 
+def vorticity_rms_diff(w, v_a, v_b):
+    """r.m.s. over the active mesh of the difference of the vertical
+    vorticity (1/r) d(r v_phi)/dr of two azimuthal-velocity fields (inertial
+    v_phi = v_x + Omega_f r, radial differences at the faces between rings),
+    both evaluated in FP64 from the stored values."""
+    import numpy as np
+    r = W.centres(w.yf)[w.gy:w.gy + w.ny]
+    rf = w.yf[w.gy + 1:w.gy + w.ny]
+
+    def omz(v):
+        vp = w.active(v).astype(np.float64)[0] + w.omega_f * r[:, None]
+        rv = r[:, None] * vp
+        return (rv[1:] - rv[:-1]) / (r[1:] - r[:-1])[:, None] / rf[:, None]
+
+    d = omz(v_a) - omz(v_b)
+    return float(np.sqrt(np.mean(d * d)))
+
+
+def precision_study(torch, fb, orbits=8.0):
+    """Single versus double precision on the laminar planet disk (Sec. 6):
+    the 4000 x 2000 inviscid disk with an Earth-mass planet in the frame
+    corotating with it, run in FP64 and in the FP32 path side by side; the
+    specific torque on the planet every quarter orbit, and the r.m.s.
+    differences of the azimuthal velocity and of the vorticity between the
+    two runs at the start and at the end.  One JSON line."""
+    import numpy as np
+    w = W.laminar_disk(orbits=orbits)
+    c64 = fb.Fargo(w, fb.F64)
+    c32 = fb.Fargo(w, fb.F32)
+    for c in (c64, c32):
+        c.set_state(w.state)
+        c.set_time(0.0, w.t_end)
+    w.state = None
+
+    def vdiff():
+        v64, v32 = c64.get_field("vx"), c32.get_field("vx")
+        d = w.active(v32).astype(np.float64) - w.active(v64)
+        return float(np.sqrt(np.mean(d * d))), vorticity_rms_diff(w, v32, v64)
+
+    s0, om0 = vdiff()
+    rp = (w.planet_a, 0.0, 0.0)
+    samples = []
+    t0 = time.perf_counter()
+    nq = int(round(4 * orbits))
+    for k in range(1, nq + 1):
+        t = 0.25 * k * 2 * math.pi
+        c64.run_to(t, poll=512)
+        c32.run_to(t, poll=512)
+        a, b = c64.scalars(), c32.scalars()
+        if a[3] or b[3]:
+            raise SystemExit(f"device error {a[3]} / {b[3]} in the precision study")
+        samples.append([round(0.25 * k, 4), c64.planet_force(rp, w.planet_eps)[3],
+                        c32.planet_force(rp, w.planet_eps)[3], a[2], b[2]])
+    wall = time.perf_counter() - t0
+    s1, om1 = vdiff()
+    h = np.array([x[:3] for x in samples])
+    scale = float(np.max(np.abs(h[h[:, 0] <= 1.0, 1])))
+    rel = np.abs(h[:, 2] - h[:, 1]) / scale
+    print(json.dumps({
+        "metric": "sp_dp_torque_study", "workload": f"laminar disk {w.nx} x {w.ny}, q = {w.planet_q}, h = 0.05, "
+        f"r in [0.6, 1.4], corotating, inviscid", "orbits": orbits,
+        "columns": ["orbits", "torque_fp64", "torque_fp32", "steps_fp64", "steps_fp32"], "samples": samples,
+        "torque_scale_first_orbit": scale, "diff_over_scale": [round(float(x), 4) for x in rel],
+        "rms_dvx_t0": s0, "rms_dvorticity_t0": om0, "rms_dvx_end": s1, "rms_dvorticity_end": om1,
+        "dr": float(w.yf[w.gy + 1] - w.yf[w.gy]), "wall_s": round(wall, 1)}))
+    c64.close()
+    c32.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,7 +718,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="batch256",
-                    choices=["batch256", "batch-small", "batch-medium", "disk3d", "disk2d", "disk3d-small"])
+                    choices=["batch256", "batch-small", "batch-medium", "disk3d", "disk2d", "disk3d-small",
+                             "precision-study"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -666,6 +737,10 @@ def main():
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local if ws > 1 else 0)
+    if args.workload == "precision-study":
+        if rank == 0:
+            precision_study(torch, fb)
+        return
     ranks = Ranks(torch)
     dev = torch.cuda.current_device()
     barrier = ranks.barrier

@@ -205,23 +205,27 @@ struct BOrbOp {
 };
 
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) kb_tx(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems)
+__global__ void __launch_bounds__(512, 2) kb_tx(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems,
+                                                 int nbuf)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     ring_bars_init(bar);
-    BTxOp<T, C> op{P, g, ring_meta<T>(smem_raw, stride)};
-    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nitems);
+    BTxOp<T, C> op{P, g, ring_meta<T>(smem_raw, stride, nbuf)};
+    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nitems,
+                     nbuf);
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) kb_orb(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems)
+__global__ void __launch_bounds__(512, 2) kb_orb(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems,
+                                                 int nbuf)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     ring_bars_init(bar);
-    BOrbOp<T, C> op{P, g, ring_meta<T>(smem_raw, stride)};
-    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nitems);
+    BOrbOp<T, C> op{P, g, ring_meta<T>(smem_raw, stride, nbuf)};
+    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nitems,
+                     nbuf);
 }
 
 // Tensor maps of every member live in global memory (64-byte aligned).
@@ -465,7 +469,8 @@ static int batch_setup(fargo_batch *b)
             x.rs.threads = x.threads = threads;
             x.rs.stride = stride;
             x.rs.chunk = x.key;
-            x.rs.smem = x.smem = 2 * (size_t)stride * sizeof(T);
+            x.rs.nbuf = ring_nbuf(stride, (int)sizeof(T));
+            x.rs.smem = x.smem = (size_t)x.rs.nbuf * stride * sizeof(T);
         } else if (x.kind == L_SWEEP) {
             x.threads = TmaTile<T>::TW + 32;
             x.smem = x.arg == 1 ? sweep_tma_smem<T, 1>(x.key) : sweep_tma_smem<T, 2>(x.key);
@@ -524,21 +529,21 @@ static void launch_ring(const BLaunch &x, const StepPlan<T> *P, cudaStream_t s)
     const RingShape &r = x.rs;
     if (x.kind == L_TX) {
         switch (x.key) {
-        case 1: kb_tx<T, 1><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 2: kb_tx<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 3: kb_tx<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 4: kb_tx<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 6: kb_tx<T, 6><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        default: kb_tx<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 1: kb_tx<T, 1><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 2: kb_tx<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 3: kb_tx<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 4: kb_tx<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 6: kb_tx<T, 6><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        default: kb_tx<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
         }
     } else {
         switch (x.key) {
-        case 1: kb_orb<T, 1><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 2: kb_orb<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 3: kb_orb<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 4: kb_orb<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        case 6: kb_orb<T, 6><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
-        default: kb_orb<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n); break;
+        case 1: kb_orb<T, 1><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 2: kb_orb<T, 2><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 3: kb_orb<T, 3><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 4: kb_orb<T, 4><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        case 6: kb_orb<T, 6><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
+        default: kb_orb<T, 8><<<r.grid, r.threads, r.smem, s>>>(P, g, r.stride, n, r.nbuf); break;
         }
     }
 }

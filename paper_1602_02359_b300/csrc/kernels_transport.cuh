@@ -135,13 +135,33 @@ struct RingMeta {
 // flight land before the CTA exits.
 template <typename T, class Op>
 __device__ __forceinline__ void ring_pipeline(Op &op, T *buf, size_t stride, uint64_t *bar, int first, int step,
-                                              int n)
+                                              int n, int nbuf)
 {
     if (first >= n) return;
     const int K = (n - first + step - 1) / step;
     for (int it = threadIdx.x; it < K; it += blockDim.x) op.prepare(it, first + it * step);
     __syncthreads();
     if (threadIdx.x == 0) op.issue(0, buf, &bar[0]);
+    if (nbuf == 1) {
+        // one buffer (rings too long for two): the next copy is issued once
+        // the current ring has been computed
+        unsigned use = 0u;
+        for (int it = 0; it < K; it++) {
+            const bool ok = __syncthreads_and(mbar_wait(&bar[0], use & 1u));
+            use++;
+            if (!ok) {
+                if (threadIdx.x == 0) op.fail(it);
+                return;
+            }
+            op.compute(it, buf);
+            __syncthreads();
+            if (threadIdx.x == 0 && it + 1 < K) {
+                fence_proxy_async_smem();
+                op.issue(it + 1, buf, &bar[0]);
+            }
+        }
+        return;
+    }
     unsigned uses[2] = {0u, 0u};
     for (int it = 0; it < K; it++) {
         const int b = it & 1;
@@ -657,13 +677,12 @@ struct OrbOp {
     __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
 };
 
-// stride: values per ring buffer (two buffers in the dynamic shared memory)
-// Dynamic shared memory of a ring kernel: two ring buffers of `stride`
-// values, then the per-iteration table.
+// Dynamic shared memory of a ring kernel: nbuf (2, or 1 for rings too long
+// for two) ring buffers of `stride` values, then the per-iteration table.
 template <typename T>
-__device__ __forceinline__ RingMeta<T> *ring_meta(unsigned char *smem, int stride)
+__device__ __forceinline__ RingMeta<T> *ring_meta(unsigned char *smem, int stride, int nbuf)
 {
-    return reinterpret_cast<RingMeta<T> *>(smem + 2 * (size_t)stride * sizeof(T));
+    return reinterpret_cast<RingMeta<T> *>(smem + (size_t)nbuf * stride * sizeof(T));
 }
 
 // The parameters are __grid_constant__: the ring operations hold references
@@ -671,30 +690,31 @@ __device__ __forceinline__ RingMeta<T> *ring_meta(unsigned char *smem, int strid
 template <typename T, int C>
 __global__ void __launch_bounds__(512, 2)
     k_transport_x(const __grid_constant__ MeshD m, const __grid_constant__ Tab<T> tb, const __grid_constant__ Fld<T> in,
-                  const __grid_constant__ QSet<T> out, const double *v0, Scal *sc, int stride)
+                  const __grid_constant__ QSet<T> out, const double *v0, Scal *sc, int stride, int nbuf)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     ring_bars_init(bar);
-    TxOp<T, C> op{m, tb, in, out, v0, sc, dt, ring_meta<T>(smem_raw, stride)};
+    TxOp<T, C> op{m, tb, in, out, v0, sc, dt, ring_meta<T>(smem_raw, stride, nbuf)};
     ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x,
-                     m.nyt * m.nzt);
+                     m.nyt * m.nzt, nbuf);
 }
 
 template <typename T, int C>
 __global__ void __launch_bounds__(512, 2)
     k_orbital(const __grid_constant__ MeshD m, const __grid_constant__ Tab<T> tb, const __grid_constant__ QSet<T> qs,
-              const double *v0, Scal *sc, int nrings, int stride)
+              const double *v0, Scal *sc, int nrings, int stride, int nbuf)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     const T dt = step_dt<T>(sc);
     if (!(dt > T(0))) return;
     ring_bars_init(bar);
-    OrbOp<T, C> op{m, tb, qs, v0, sc, dt, ring_meta<T>(smem_raw, stride)};
-    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nrings);
+    OrbOp<T, C> op{m, tb, qs, v0, sc, dt, ring_meta<T>(smem_raw, stride, nbuf)};
+    ring_pipeline<T>(op, reinterpret_cast<T *>(smem_raw), (size_t)stride, bar, blockIdx.x, gridDim.x, nrings,
+                     nbuf);
 }
 
 // Cells per thread of a ring kernel whose CTA stages `rows` rows of `pitch`
@@ -713,10 +733,10 @@ static inline int ring_threads(int nx, int C, bool halo)
     return halo && C >= 3 && C <= 6 ? 32 * ((nx + 30 * C - 1) / (30 * C)) : ((nx + C - 1) / C + 31) / 32 * 32;
 }
 
-static inline int ring_chunk(int nx, int rows, int pitch, int esz, bool halo)
+static inline int ring_chunk(int nx, int rows, int pitch, int esz, bool halo, int nbuf)
 {
     const int cs[6] = {1, 2, 3, 4, 6, 8};
-    const size_t smem = 2 * (size_t)rows * ring_row(pitch) * esz + 2048;
+    const size_t smem = (size_t)nbuf * rows * ring_row(pitch) * esz + 2048;
     int best = 0;
     for (int c : cs) {
         const int th = ring_threads(nx, c, halo);
@@ -738,19 +758,24 @@ struct RingShape {
     int threads, stride, grid;
     size_t smem;
     int chunk;   // cells per thread (ring_chunk)
+    int nbuf;    // ring buffers: 2 (double buffering), 1 when two do not fit
 };
+
+// Ring buffers of a ring kernel staging `stride` values of esz bytes: two
+// while they and the per-iteration table fit the 227 KB a CTA can have.
+static inline int ring_nbuf(int stride, int esz) { return 2 * (size_t)stride * esz + 4096 <= 232448 ? 2 : 1; }
 
 template <typename T, int C>
 static void launch_tx_c(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
                         Scal *sc, const RingShape &rs, cudaStream_t s)
 {
-    k_transport_x<T, C><<<rs.grid, rs.threads, rs.smem, s>>>(m, tb, in, out, v0, sc, rs.stride);
+    k_transport_x<T, C><<<rs.grid, rs.threads, rs.smem, s>>>(m, tb, in, out, v0, sc, rs.stride, rs.nbuf);
 }
 template <typename T, int C>
 static void launch_orb_c(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, const double *v0, Scal *sc,
                          int nrings, const RingShape &rs, cudaStream_t s)
 {
-    k_orbital<T, C><<<rs.grid, rs.threads, rs.smem, s>>>(m, tb, qs, v0, sc, nrings, rs.stride);
+    k_orbital<T, C><<<rs.grid, rs.threads, rs.smem, s>>>(m, tb, qs, v0, sc, nrings, rs.stride, rs.nbuf);
 }
 
 template <typename T>
@@ -773,11 +798,12 @@ template <typename T>
 static RingShape ring_shape(int nx, int rows, int pitch, bool halo)
 {
     RingShape rs{};
-    const int C = ring_chunk(nx, rows, pitch, (int)sizeof(T), halo);
+    rs.stride = rows * ring_row(pitch);
+    rs.nbuf = ring_nbuf(rs.stride, (int)sizeof(T));
+    const int C = ring_chunk(nx, rows, pitch, (int)sizeof(T), halo, rs.nbuf);
     rs.chunk = C;
     rs.threads = C ? ring_threads(nx, C, halo) : 0;
-    rs.stride = rows * ring_row(pitch);
-    rs.smem = 2 * (size_t)rs.stride * sizeof(T);
+    rs.smem = (size_t)rs.nbuf * rs.stride * sizeof(T);
     return rs;
 }
 
@@ -807,7 +833,7 @@ static cudaError_t ring_grid(K *kernel, RingShape &rs, int nitems)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const size_t bufs = 2 * (size_t)rs.stride * sizeof(T);
+    const size_t bufs = (size_t)rs.nbuf * rs.stride * sizeof(T);
     const int n = nitems > 0 ? nitems : 1;
     int grid = n;
     for (int pass = 0; pass < 4; pass++) {

@@ -34,6 +34,9 @@ CASES = [
     (W.SPH, 480, 10, 6, False, 1e-3, W.BC_REFLECT),
     # one azimuthal cell: an axisymmetric disk (no X derivatives, no X sweep)
     (W.CYL, 1, 40, 1, True, 1e-3, W.BC_ZEROGRAD),
+    # rings too long for two FP64 staging buffers: the ring kernels stage
+    # one ring at a time
+    (W.CYL, 4000, 6, 1, True, 1e-3, W.BC_FROZEN),
 ]
 IDS = [f"g{c[0]}-{c[1]}x{c[2]}x{c[3]}-{'iso' if c[4] else 'adi'}-nu{c[5]}-bc{c[6]}" for c in CASES]
 
@@ -253,6 +256,34 @@ def test_disk2d_fp64_ten_steps_full_size():
         else:
             assert abs(dt_g - dt_o) <= 1e-12 * dt_o, (n, dt_g, dt_o)
     compare_state(w, c.get_state(), st, 1e-11)
+
+
+def test_corotating_laminar_disk_fp64_steps():
+    """The precision study's disk (frame corotating with the planet, uniform
+    surface density, linear radial spacing), reduced to 300 x 120: five
+    steps against the oracle, bit-exact first dt.  The disk starts in
+    equilibrium, so v_r is the small residual of gravity, the centrifugal
+    force and the pressure, each of order one: its round-off is measured
+    against the velocity scale max |v_phi| (1e-13), the other fields
+    against their own size (1e-11)."""
+    w = W.laminar_disk(nx=300, ny=120)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    c = make_ctx(w, t=0.0, t_end=w.t_end)
+    t = 0.0
+    for n in range(5):
+        dt_o = o.step(st, t, w.t_end)
+        t += dt_o
+        dt_g = c.step()
+        if n == 0:
+            assert dt_g == dt_o, (dt_g, dt_o)
+        else:
+            assert abs(dt_g - dt_o) <= 1e-12 * dt_o, (n, dt_g, dt_o)
+    g = c.get_state()
+    for k in ("rho", "vx"):
+        assert rel_linf(active_faces(w, k, g[k]), active_faces(w, k, st[k])) < 1e-11, k
+    dvy = np.max(np.abs(active_faces(w, "vy", g["vy"]) - active_faces(w, "vy", st["vy"])))
+    assert dvy < 1e-13 * np.max(np.abs(w.active(st["vx"]))), dvy
 
 
 def test_fp32_disk_within_stated_tolerance():

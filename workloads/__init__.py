@@ -268,6 +268,34 @@ def viscous_ring(ny=512, nx=1, nu=1e-5, t0=100.0, t_end=1100.0, cs=0.0, floor=1e
     return w
 
 
+def laminar_disk(nx=4000, ny=2000, h=0.05, q=3e-6, sigma0=1e-3, g=3, rmin=0.6, rmax=1.4, eps_h=0.6,
+                 orbits=8.0, cq=1.41):
+    """The laminar disk of the precision study (Sec. 6, single or double
+    precision): a 2D cylindrical, locally isothermal, inviscid disk of
+    uniform surface density sigma0 and aspect ratio h (c_s = h r^-1/2), on
+    rmin <= r <= rmax with ny evenly spaced radial cells (Delta r = 4e-4 at
+    the paper's 2000) and nx azimuthal cells, an Earth-mass planet
+    (q = 3e-6) at a = 1 with smoothing eps_h H.  The frame corotates with
+    the planet (Omega_f = sqrt(1 + q), so the planet stays at azimuth 0);
+    v_phi = sqrt((1 - h^2)/r) balances gravity and the pressure of this
+    disk, less Omega_f r in the rotating frame; v_r = 0.  Radial ghosts are
+    frozen to the initial state."""
+    yf = faces(ny, g, rmin, rmax)
+    zf = faces(1, g, -0.5, 0.5)
+    om_f = math.sqrt(1.0 + q)
+    w = Workload("laminar_disk", CYL, nx, ny, 1, g, -math.pi, math.pi, yf, zf, 1.4, True,
+                 None, None, 0.44, cq, True, om_f,
+                 (BC_FROZEN, BC_FROZEN), (BC_FROZEN, BC_FROZEN),
+                 1.0, q, 1.0, eps_h * h, True, 0.0, orbits * 2.0 * math.pi, {})
+    ym = centres(yf)
+    w.cs = np.broadcast_to(h * ym ** -0.5, (w.nz_t, w.ny_t)).copy()
+    st = _empty(w.shape)
+    st["rho"][:w.nz_t, :w.ny_t, :] = sigma0
+    st["vx"][:w.nz_t, :w.ny_t, :] = (np.sqrt((1.0 - h * h) / ym) - om_f * ym)[None, :, None]
+    w.state = st
+    return w
+
+
 def batch_params(n=256, seed=1602):
     """Parameter draws of the batched disk sweep (numpy PCG64, fixed seed).
 
