@@ -469,7 +469,7 @@ static int batch_setup(fargo_batch *b)
             x.rs.threads = x.threads = threads;
             x.rs.stride = stride;
             x.rs.chunk = x.key;
-            x.rs.nbuf = ring_nbuf(stride, (int)sizeof(T));
+            x.rs.nbuf = ring_nbuf(stride, (int)sizeof(T), x.kind == L_ORB);
             x.rs.smem = x.smem = (size_t)x.rs.nbuf * stride * sizeof(T);
         } else if (x.kind == L_SWEEP) {
             x.threads = TmaTile<T>::TW + 32;

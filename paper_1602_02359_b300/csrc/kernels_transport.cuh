@@ -761,9 +761,18 @@ struct RingShape {
     int nbuf;    // ring buffers: 2 (double buffering), 1 when two do not fit
 };
 
-// Ring buffers of a ring kernel staging `stride` values of esz bytes: two
-// while they and the per-iteration table fit the 227 KB a CTA can have.
-static inline int ring_nbuf(int stride, int esz) { return 2 * (size_t)stride * esz + 4096 <= 232448 ? 2 : 1; }
+// Ring buffers of a ring kernel staging `stride` values of esz bytes.  The
+// orbital step (halo: the heavier per-cell work) double-buffers while two
+// buffers and the per-iteration table fit the 227 KB a CTA can have: its
+// CTAs need their own prefetch.  The X sweep stages one ring at a time: its
+// lighter work leaves the copy latency to the other CTAs on the SM, which
+// the halved staging admits (measured on the 3D disk: 1.37 -> 1.19 ms; on
+// the 256-disk sweep 1.27 -> 1.21 ms; the orbital step there went
+// 1.54 -> 2.09 ms with one buffer).
+static inline int ring_nbuf(int stride, int esz, bool halo)
+{
+    return halo && 2 * (size_t)stride * esz + 4096 <= 232448 ? 2 : 1;
+}
 
 template <typename T, int C>
 static void launch_tx_c(const MeshD &m, const Tab<T> &tb, const Fld<T> &in, const QSet<T> &out, const double *v0,
@@ -799,7 +808,7 @@ static RingShape ring_shape(int nx, int rows, int pitch, bool halo)
 {
     RingShape rs{};
     rs.stride = rows * ring_row(pitch);
-    rs.nbuf = ring_nbuf(rs.stride, (int)sizeof(T));
+    rs.nbuf = ring_nbuf(rs.stride, (int)sizeof(T), halo);
     const int C = ring_chunk(nx, rows, pitch, (int)sizeof(T), halo, rs.nbuf);
     rs.chunk = C;
     rs.threads = C ? ring_threads(nx, C, halo) : 0;
