@@ -711,6 +711,34 @@ def precision_study(torch, fb, orbits=8.0):
     c32.close()
 
 
+def vortex_study(torch, fb, orbits=10.0, resolutions=((1024, 256), (2048, 512))):
+    """Orbital advection and vortensity (Sec. 6): the vortex in a Keplerian
+    disk, FP64, with and without orbital advection, at each resolution;
+    the vortensity minimum every half orbit of the vortex, the steps taken
+    and the device time.  One JSON line."""
+    res = []
+    for nx, ny in resolutions:
+        for fargo in (True, False):
+            w = W.keplerian_vortex(nx=nx, ny=ny, fargo=fargo, orbits=orbits)
+            c = fb.Fargo(w, fb.F64)
+            c.set_state(w.state)
+            c.set_time(0.0, w.t_end)
+            hist = [[0.0, float(W.vortensity(w, w.state).min())]]
+            t0 = time.perf_counter()
+            for k in range(1, int(round(2 * orbits)) + 1):
+                c.run_to(0.5 * k * 2 * math.pi, poll=2048)
+                if c.scalars()[3]:
+                    raise SystemExit(f"device error in the vortex study ({nx} x {ny}, fargo={fargo})")
+                hist.append([0.5 * k, float(W.vortensity(w, c.get_state()).min())])
+            wall = time.perf_counter() - t0
+            res.append({"nx": nx, "ny": ny, "orbital_advection": fargo, "steps": c.scalars()[2],
+                        "wall_s": round(wall, 2), "vortensity_min": hist})
+            c.close()
+    print(json.dumps({"metric": "vortensity_min_decay", "workload": "Keplerian vortex, M = 10, K = -1, "
+                      "h = c_s/(2 Omega), r in [0.4, 2], adiabatic, inviscid, FP64", "orbits": orbits,
+                      "runs": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -719,7 +747,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="batch256",
                     choices=["batch256", "batch-small", "batch-medium", "disk3d", "disk2d", "disk3d-small",
-                             "precision-study"])
+                             "precision-study", "vortex-study"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -737,9 +765,9 @@ def main():
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local if ws > 1 else 0)
-    if args.workload == "precision-study":
+    if args.workload in ("precision-study", "vortex-study"):
         if rank == 0:
-            precision_study(torch, fb)
+            (precision_study if args.workload == "precision-study" else vortex_study)(torch, fb)
         return
     ranks = Ranks(torch)
     dev = torch.cuda.current_device()

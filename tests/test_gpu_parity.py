@@ -286,6 +286,27 @@ def test_corotating_laminar_disk_fp64_steps():
     assert dvy < 1e-13 * np.max(np.abs(w.active(st["vx"]))), dvy
 
 
+@pytest.mark.parametrize("fargo", [True, False])
+def test_keplerian_vortex_fp64_steps(fargo):
+    """The vortex of the orbital-advection study (adiabatic, no planet,
+    uniform surface density) at 160 x 48, with and without orbital
+    advection: five steps against the oracle, bit-exact first dt."""
+    w = W.keplerian_vortex(nx=160, ny=48, fargo=fargo)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    c = make_ctx(w, t=0.0, t_end=w.t_end)
+    t = 0.0
+    for n in range(5):
+        dt_o = o.step(st, t, w.t_end)
+        t += dt_o
+        dt_g = c.step()
+        if n == 0:
+            assert dt_g == dt_o, (dt_g, dt_o)
+        else:
+            assert abs(dt_g - dt_o) <= 1e-12 * dt_o, (n, dt_g, dt_o)
+    compare_state(w, c.get_state(), st, 1e-11)
+
+
 def test_fp32_disk_within_stated_tolerance():
     """FP32 bulk with FP64 islands against the FP64 oracle after 100 steps of
     a planet disk: 2e-5 relative L1 on density, 1e-4 relative L1 on the

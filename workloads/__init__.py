@@ -296,6 +296,73 @@ def laminar_disk(nx=4000, ny=2000, h=0.05, q=3e-6, sigma0=1e-3, g=3, rmin=0.6, r
     return w
 
 
+def keplerian_vortex(nx=1024, ny=256, fargo=True, mach=10.0, gamma=5.0 / 3.0, k_amp=-1.0, r0=1.0,
+                     phi0=0.25 * math.pi, rmin=0.4, rmax=2.0, g=3, orbits=10.0, cq=1.41):
+    """A vortex in a two-dimensional Keplerian disk (Sec. 6, impact of
+    orbital advection): a disk around a unit mass, Phi = -1/r, of uniform
+    surface density 1 and pressure 1/(gamma M^2) (M = 10, the Keplerian Mach
+    number at r0 = 1: c_s = 1/M), adiabatic, inviscid, so the unperturbed
+    flow is exactly Keplerian.  On it, a velocity perturbation
+    K exp(-(x^2 + y^2)/h^2) (-y, x) in Cartesian components about the
+    vortex centre (r0, phi0 = pi/4), turned into (v_phi, v_r) at each
+    point, with h = c_s(r0) / (2 Omega(r0)) and K = -1 (anticyclonic).
+    nx azimuthal by ny linearly spaced radial cells on [rmin, rmax]; radial
+    ghosts frozen to the initial state; fargo toggles orbital advection."""
+    yf = faces(ny, g, rmin, rmax)
+    zf = faces(1, g, -0.5, 0.5)
+    w = Workload("keplerian_vortex", CYL, nx, ny, 1, g, 0.0, 2.0 * math.pi, yf, zf, gamma, False,
+                 None, None, 0.44, cq, fargo, 0.0,
+                 (BC_FROZEN, BC_FROZEN), (BC_FROZEN, BC_FROZEN),
+                 1.0, 0.0, 1.0, 0.0, False, 0.0, orbits * 2.0 * math.pi, {})
+    cs0 = 1.0 / mach
+    h = cs0 / (2.0 * r0 ** -1.5)
+    p = 1.0 / (gamma * mach * mach)
+    w.vortex = dict(r0=r0, phi0=phi0, h=h, k=k_amp)
+    st = _empty(w.shape)
+    rc = centres(yf)                                  # cell-centre radii (v_phi, rho, e)
+    pc = (np.arange(nx) + 0.5) * (2.0 * math.pi / nx)  # cell-centre azimuths (v_r)
+    pf = np.arange(nx) * (2.0 * math.pi / nx)          # azimuthal faces (v_phi)
+    xc0, yc0 = r0 * math.cos(phi0), r0 * math.sin(phi0)
+
+    def pert(r, ph):
+        x = r * np.cos(ph) - xc0
+        y = r * np.sin(ph) - yc0
+        a = k_amp * np.exp(-(x * x + y * y) / (h * h))
+        ux, uy = -y * a, x * a
+        return -ux * np.sin(ph) + uy * np.cos(ph), ux * np.cos(ph) + uy * np.sin(ph)
+
+    dvp, _ = pert(rc[:, None], pf[None, :])
+    _, dvr = pert(yf[:w.ny_t + 1, None], pc[None, :])
+    st["rho"][:w.nz_t, :w.ny_t, :] = 1.0
+    st["e"][:w.nz_t, :w.ny_t, :] = p / (gamma - 1.0)
+    st["vx"][:w.nz_t, :w.ny_t, :] = (np.sqrt(1.0 / rc)[:, None] + dvp)[None]
+    st["vy"][:w.nz_t, :w.ny_t + 1, :] = dvr[None]
+    w.state = st
+    return w
+
+
+def vortensity(w, st):
+    """Vertical vortensity (curl v)_z / Sigma in the inertial frame at the
+    cell corners (r_j faces, phi_i faces) of the active mesh, from the
+    staggered fields: ((1/r) d(r v_phi)/dr - (1/r) dv_r/dphi) / Sigma, with
+    Sigma the mean of the four cells around the corner.  A diagnostic of the
+    flow, not a step of the method."""
+    rc = centres(w.yf)
+    rf = w.yf
+    dphi = (w.xmax - w.xmin) / w.nx
+    gy = w.gy
+    vp = st["vx"][0, :w.ny_t, :] + w.omega_f * rc[:, None]     # at (rc_j, phi-face i)
+    vr = st["vy"][0, :w.ny_t + 1, :]                           # at (r-face j, phi-centre i)
+    rho = st["rho"][0, :w.ny_t, :]
+    j = np.arange(gy + 1, gy + w.ny)                           # interior radial faces
+    r = rf[j][:, None]
+    d_rvp = (rc[j][:, None] * vp[j] - rc[j - 1][:, None] * vp[j - 1]) / (rc[j] - rc[j - 1])[:, None]
+    d_vr = (vr[j] - np.roll(vr[j], 1, axis=1)) / dphi          # at phi-face i (between cells i-1, i)
+    curl = (d_rvp - d_vr) / r
+    sig = 0.25 * (rho[j] + rho[j - 1] + np.roll(rho[j], 1, axis=1) + np.roll(rho[j - 1], 1, axis=1))
+    return curl / sig
+
+
 def batch_params(n=256, seed=1602):
     """Parameter draws of the batched disk sweep (numpy PCG64, fixed seed).
 
