@@ -551,9 +551,11 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     c->sc = (Scal *)p;
     c->nrings_active = ny * nz;
     c->cfl_blocks = (c->nrings_active + 7) / 8;
-    if ((rc = dalloc(c, &p, sizeof(double) * (size_t)c->nyt * c->nzt))) goto fail;
+    // v0 per ring, then the bulk angular rate v0 / (R dx) per ring (shear limit)
+    if ((rc = dalloc(c, &p, sizeof(double) * 2 * (size_t)c->nyt * c->nzt))) goto fail;
     c->v0 = (double *)p;
-    if ((rc = dalloc(c, &p, sizeof(double) * c->cfl_blocks))) goto fail;
+    // Courant partials per block: the rate maximum, then the shear maximum
+    if ((rc = dalloc(c, &p, sizeof(double) * 2 * c->cfl_blocks))) goto fail;
     c->part = (double *)p;
     if ((rc = dalloc(c, &p, sizeof(float) * c->nrings_active))) goto fail;
     c->ringmax = (float *)p;

@@ -65,7 +65,7 @@ struct QSet {
 
 // Device scalars of the run.  `counter` serves the last-block reductions.
 struct Scal {
-    double t, t_end, dt, xp, yp, dt_fixed, m32, wsh;
+    double t, t_end, dt, xp, yp, dt_fixed, m32;
     long long nstep;
     int err, fixed;
     unsigned int counter, counter2;

@@ -175,7 +175,7 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
                                                 int nblk)
 {
     __shared__ float s_red[8];
-    __shared__ double s_w[8], s_m[8];
+    __shared__ double s_m[8];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = bid * 8 + warp;
@@ -215,7 +215,12 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
                     }
             }
             v0r = __dmul_rn(0.5, __dadd_rn(warp_max((double)mx), warp_min((double)mn)));
-            if (lane == 0) v0[ring] = v0r;
+            if (lane == 0) {
+                v0[ring] = v0r;
+                // the ring's bulk angular rate v0 / (R dx) for the shear limit (Eq. 38),
+                // kept after the nyt*nzt v0 values
+                v0[(size_t)m.nyt * m.nzt + ring] = __ddiv_rn(v0r, tb.lx[ring]);
+            }
         }
         const T v0hi = (T)v0r, v0lo = (T)(v0r - (double)v0hi);
         // per-ring reciprocals: the estimate needs no division per cell and no
@@ -305,33 +310,14 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double mx = 0.0, wsh = 0.0;
+    double mx = 0.0;
     for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
-    if (m.fargo && m.hasY && !skip) {
-        const int ny = m.j1 - m.j0, nz = m.k1 - m.k0;
-        const int npairs = (ny - 1) * nz;
-        for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-            const int j = m.j0 + p % (ny - 1), k = m.k0 + p / (ny - 1);
-            const int ring = k * m.nyt + j;
-            const double a = __ddiv_rn(__ldcg(&v0[ring]), tb.lx[ring]);
-            const double b = __ddiv_rn(__ldcg(&v0[ring + 1]), tb.lx[ring + 1]);
-            wsh = fmax(wsh, fabs(__dsub_rn(a, b)));
-        }
-    }
     mx = warp_max(mx);
-    wsh = warp_max(wsh);
-    if (lane == 0) {
-        s_w[warp] = wsh;
-        s_m[warp] = mx;
-    }
+    if (lane == 0) s_m[warp] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; w++) {
-            mx = fmax(mx, s_m[w]);
-            wsh = fmax(wsh, s_w[w]);
-        }
+        for (int w = 1; w < 8; w++) mx = fmax(mx, s_m[w]);
         sc->m32 = mx;
-        sc->wsh = wsh;
         sc->counter = 0u;
     }
 }
@@ -394,28 +380,53 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
             smax = fmax(smax, s);
         }
     }
+    // shear limit (Eq. 38) of the block's eight rings and their outer
+    // neighbours, from the bulk angular rates the screen stored after v0
+    double wsh = 0.0;
+    if (warp == 0 && lane < 8 && m.fargo && m.hasY && !skip) {
+        const int r = bid * 8 + lane;
+        const int ny = m.j1 - m.j0;
+        if (r < nrings && r % ny < ny - 1) {
+            const int ring = (m.k0 + r / ny) * m.nyt + m.j0 + r % ny;
+            const double *om = v0 + (size_t)m.nyt * m.nzt;
+            wsh = fabs(__dsub_rn(__ldcg(&om[ring]), __ldcg(&om[ring + 1])));
+        }
+    }
     smax = warp_max(smax);
+    if (warp == 0) wsh = warp_max(wsh);
     if (lane == 0) s_red[warp] = smax;
     __syncthreads();
     if (threadIdx.x == 0) {
         double b = s_red[0];
         for (int w = 1; w < 8; w++) b = fmax(b, s_red[w]);
         part[bid] = b;
+        part[nblk + bid] = wsh;
         __threadfence();
         s_last = atomicAdd(&sc->counter, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double mx = 0.0;
-    for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x) mx = fmax(mx, __ldcg(&part[b]));
+    double mx = 0.0, ws = 0.0;
+    for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x) {
+        mx = fmax(mx, __ldcg(&part[b]));
+        ws = fmax(ws, __ldcg(&part[nblk + b]));
+    }
     mx = warp_max(mx);
-    if (lane == 0) s_red[warp] = mx;
+    ws = warp_max(ws);
+    __shared__ double s_ws[8];
+    if (lane == 0) {
+        s_red[warp] = mx;
+        s_ws[warp] = ws;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; w++) mx = fmax(mx, s_red[w]);
+        for (int w = 1; w < 8; w++) {
+            mx = fmax(mx, s_red[w]);
+            ws = fmax(ws, s_ws[w]);
+        }
         int err = atomicOr(&sc->err, 0);
-        const double t = sc->t, te = sc->t_end, wsh = sc->wsh;
+        const double t = sc->t, te = sc->t_end, wsh = ws;
         double dt = 0.0;
         if (!skip) {
             if (sc->fixed) {
