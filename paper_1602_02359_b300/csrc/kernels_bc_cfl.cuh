@@ -348,9 +348,47 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
         const double nu = m.has_nu ? tb.nud[ring] : 0.0;
         const double r4 = nu > 0.0 ? __ddiv_rn(__dmul_rn(4.0, nu), __dmul_rn(dmin, dmin)) : 0.0;
         const double csr = m.iso ? tb.csd[ring] : 0.0;
+        // the screen's FP32 estimate per cell (same terms; per-ring factors in
+        // FP32): a cell whose estimate falls below thr cannot hold the exact
+        // maximum, by the argument that admits the ring (the estimate errs by
+        // about 1e-6, the margin is 2^-12), so only the others are evaluated
+        // in FP64
+        const float ilx = 1.0f / (float)tb.lenx[ring], ily = 1.0f / (float)tb.dy[j];
+        const float ilz = 1.0f / (float)tb.lenz[ring];
+        const float dmf = (float)tb.dminT[ring];
+        const float idm2 = 1.0f / (dmf * dmf);
+        const float r4f = m.has_nu ? (float)tb.r4[ring] : 0.0f;
+        const float c1 = m.iso ? (float)csr * (float)csr * idm2 : (float)tb.g1 * idm2;
+        const bool lit = m.av_lit != 0, avon = m.has_av != 0;
+        const float k4 = (float)tb.k4;
+        const T v0hi = (T)v0r, v0lo = (T)(v0r - (double)v0hi);
         for (int i = threadIdx.x; i < m.nx; i += blockDim.x) {
             const idx_t c = base + i;
             const int ip = i + 1 == m.nx ? 0 : i + 1;
+            {
+                const float rf = (float)f.rho[c];
+                float est = m.iso ? c1 : c1 * __fdividef((float)f.e[c], rf);
+                float e2 = 0.0f, e3 = 0.0f;
+                if (m.hasX) {
+                    const T vc = f.vx[c], vp = f.vx[base + ip];
+                    const float a = fabsf((float)sub_split(vc, v0hi, v0lo));
+                    const float b = fabsf((float)sub_split(vp, v0hi, v0lo));
+                    e2 = fmaxf(e2, fmaxf(a, b) * ilx);
+                    if (avon) e3 = fmaxf(e3, av_ratef(lit, k4, (float)(vp - vc), ilx));
+                }
+                if (m.hasY) {
+                    const T vc = f.vy[c], vp = f.vy[c + m.sj];
+                    e2 = fmaxf(e2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ily);
+                    if (avon) e3 = fmaxf(e3, av_ratef(lit, k4, (float)(vp - vc), ily));
+                }
+                if (m.hasZ) {
+                    const T vc = f.vz[c], vp = f.vz[c + m.sk];
+                    e2 = fmaxf(e2, fmaxf(fabsf((float)vc), fabsf((float)vp)) * ilz);
+                    if (avon) e3 = fmaxf(e3, av_ratef(lit, k4, (float)(vp - vc), ilz));
+                }
+                est += e2 * e2 + e3 * e3 + r4f * r4f;
+                if ((double)est < thr) continue;
+            }
             const double rho = (double)f.rho[c];
             const double cs = m.iso ? csr : __dsqrt_rn(__ddiv_rn(__dmul_rn(m.g1, (double)f.e[c]), rho));
             const double r1 = __ddiv_rn(cs, dmin);
