@@ -74,15 +74,15 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 21.85, "substep1": 33.42, "artvisc": 36.5, "visc_tau": 36.56, "visc_apply": 54.6, "transport_x": 55.76, "transport_y": 64.7, "transport_z": 65.84, "orbital": 58.11, "newvel": 41.66}
-KERNEL_SRC_HASH = "b17975553c9be440"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.45, "substep1": 33.46, "artvisc": 36.56, "visc_tau": 36.61, "visc_apply": 54.62, "transport_x": 56.91, "transport_y": 64.71, "transport_z": 65.82, "orbital": 58.15, "newvel": 41.7}
+KERNEL_SRC_HASH = "f9b4d740b0ebd452"
 
 # The same for the batched step: DRAM bytes per active cell of every batched
 # phase (all its launches of one step summed), measured on batch-medium (the
 # first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
 # whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
-TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 12.27, "substep1": 17.5, "artvisc": 18.05, "visc_tau": 20.68, "visc_apply": 33.32, "transport_x": 24.77, "transport_y": 42.85, "orbital": 32.27, "newvel": 27.13}
-BATCH_SRC_HASH = "621ea52e7d61ba77"
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.31, "substep1": 17.85, "artvisc": 18.03, "visc_tau": 20.65, "visc_apply": 33.39, "transport_x": 24.29, "transport_y": 42.84, "orbital": 32.27, "newvel": 27.12}
+BATCH_SRC_HASH = "d3031bdbafb974dc"
 
 
 # Sources of the single-instance step's kernels (the traffic table above

@@ -236,12 +236,34 @@ __global__ void __launch_bounds__(256, pforce_blocks_per_sm<T>()) k_planet_force
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
+    // the block partials, by the whole last block in a fixed order: thread t
+    // takes blocks t, t + 256, ...; then lanes and warps as above
+    {
         double bx = 0.0, by = 0.0, bz = 0.0;
-        for (unsigned b = 0; b < gridDim.x; b++) {
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
             bx += __ldcg(&part[3 * b]);
             by += __ldcg(&part[3 * b + 1]);
             bz += __ldcg(&part[3 * b + 2]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            bx += __shfl_xor_sync(0xffffffffu, bx, o);
+            by += __shfl_xor_sync(0xffffffffu, by, o);
+            bz += __shfl_xor_sync(0xffffffffu, bz, o);
+        }
+        __syncthreads();   // s_red was read by thread 0 above
+        if (lane == 0) {
+            s_red[0][warp] = bx;
+            s_red[1][warp] = by;
+            s_red[2][warp] = bz;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double bx = 0.0, by = 0.0, bz = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            bx += s_red[0][w];
+            by += s_red[1][w];
+            bz += s_red[2][w];
         }
         // back from the planet's frame; the torque is R_p a_y' (z component of r_p x a)
         double px, py, pz;

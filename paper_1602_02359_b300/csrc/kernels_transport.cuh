@@ -1270,16 +1270,26 @@ __device__ void sums_reduce(const SumInput<T> &in, double *part, unsigned *count
         s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
+    // the block partials, by the whole last block in a fixed order: thread t
+    // merges blocks t, t + blockDim, ..., then the same tree as above
     for (int q = 0; q < 3; q++) {
         KB a = {0, 0};
-        for (unsigned b = 0; b < gridDim.x; b++) {
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
             KB x = {__ldcg(&part[(b * 3 + q) * 2]), __ldcg(&part[(b * 3 + q) * 2 + 1])};
             kb_merge(a, x);
         }
-        result[q] = a.s + a.c;
+        sh[q][threadIdx.x] = a;
     }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int q = 0; q < 3; q++) kb_merge(sh[q][threadIdx.x], sh[q][threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; q++) result[q] = sh[q][0].s + sh[q][0].c;
     *counter = 0u;
 }
 
