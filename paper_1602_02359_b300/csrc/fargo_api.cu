@@ -346,7 +346,7 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     // cells 3-6
     k_cfl_screen<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_screen");
-    k_cfl_exact<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
+    k_cfl_exact<T><<<cfl_exact_grid(P.cfl_blocks), 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_exact");
     // cell 7
     launch_source<T>(SRC_SUB1, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("substep1");
@@ -1030,7 +1030,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     case 1:
         k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
                                                       c->nrings_active);
-        k_cfl_exact<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
+        k_cfl_exact<T><<<cfl_exact_grid(c->cfl_blocks), 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
                                                      c->nrings_active);
         break;
     case 2:

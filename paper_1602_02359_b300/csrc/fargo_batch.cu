@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(256) kb_cfl_exact(const StepPlan<T> *__restric
 {
     int local;
     const StepPlan<T> &p = P[group_member(g, blockIdx.x, local)];
-    cfl_exact_body(p.m, p.tb, p.A, p.v0, p.ringmax, p.part, p.sc, p.nrings_active, local, p.cfl_blocks);
+    cfl_exact_body(p.m, p.tb, p.A, p.v0, p.ringmax, p.part, p.sc, p.nrings_active, local,
+                   cfl_exact_grid(p.cfl_blocks));
 }
 
 // Per-cell phases: a member's cells of the augmented mesh (rows, planes as
@@ -429,7 +430,7 @@ static int batch_setup(fargo_batch *b)
     L = BLaunch{L_SCREEN}; L.name = "cfl_screen";
     add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
     L = BLaunch{L_EXACT}; L.name = "cfl_exact";
-    add_phase(b, L, all, one, [](const fargo_ctx *c) { return c->cfl_blocks; });
+    add_phase(b, L, all, one, [](const fargo_ctx *c) { return cfl_exact_grid(c->cfl_blocks); });
     // the per-cell phases launch once per configuration class (cfg_of)
     auto cfg = [](const fargo_ctx *c) { return cfg_of(c->m); };
     L = BLaunch{L_CELL}; L.arg = PH_SUB1; L.name = "substep1";

@@ -333,11 +333,15 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
     const bool skip = cfl_skip(sc);
     const double M = sc->m32;
     const double thr = M < 1e-30 ? -1.0 : M * (1.0 - 1.0 / 4096.0);
-    double smax = 0.0;
-    // the block's eight rings; each candidate is evaluated by the whole block
-    // (its FP64 divisions then use every sub-partition's FP64 unit)
+    double smax = 0.0, wsh = 0.0;
+    // chunks of eight rings, chunk ch for block ch mod nblk (the launch has an
+    // eighth of the screen's blocks: the per-block overhead dominated); each
+    // candidate ring is evaluated by the whole block (its FP64 divisions then
+    // use every sub-partition's FP64 unit)
+    const int nchunks = (nrings + 7) / 8;
+    for (int ch = bid; ch < nchunks; ch += nblk) {
     for (int w = 0; w < 8 && !skip; w++) {
-        const int r = bid * 8 + w;
+        const int r = ch * 8 + w;
         if (r >= nrings || !((double)ringmax[r] >= thr)) continue;
         const int ny = m.j1 - m.j0;
         const int j = m.j0 + r % ny, k = m.k0 + r / ny;
@@ -418,17 +422,17 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
             smax = fmax(smax, s);
         }
     }
-    // shear limit (Eq. 38) of the block's eight rings and their outer
+    // shear limit (Eq. 38) of the chunk's eight rings and their outer
     // neighbours, from the bulk angular rates the screen stored after v0
-    double wsh = 0.0;
     if (warp == 0 && lane < 8 && m.fargo && m.hasY && !skip) {
-        const int r = bid * 8 + lane;
+        const int r = ch * 8 + lane;
         const int ny = m.j1 - m.j0;
         if (r < nrings && r % ny < ny - 1) {
             const int ring = (m.k0 + r / ny) * m.nyt + m.j0 + r % ny;
             const double *om = v0 + (size_t)m.nyt * m.nzt;
-            wsh = fabs(__dsub_rn(__ldcg(&om[ring]), __ldcg(&om[ring + 1])));
+            wsh = fmax(wsh, fabs(__dsub_rn(__ldcg(&om[ring]), __ldcg(&om[ring + 1]))));
         }
+    }
     }
     smax = warp_max(smax);
     if (warp == 0) wsh = warp_max(wsh);
@@ -486,6 +490,9 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
         sc->counter = 0u;
     }
 }
+
+// Blocks of the exact pass for a screen of cfl_blocks blocks (eight rings each).
+__host__ __device__ __forceinline__ int cfl_exact_grid(int cfl_blocks) { return (cfl_blocks + 7) / 8; }
 
 // (six blocks per SM: the screen is latency-bound, and the occupancy a
 // 40-register budget buys outweighs its few spills)
