@@ -202,6 +202,19 @@ int fargo_nbody_rk5_async(int n, double *y, const double *mass, double mstar, do
 int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *mass, double eps, int bm08,
                                 int indirect);
 
+/* Change the frame's rotation rate to omega_new at the current time (Sec.
+ * 3.2, Eq. 13): every azimuthal velocity, ghosts included, becomes
+ * v_phi - (omega_new - Omega_f) R, R the cylindrical radius of its ring (the
+ * lever arm at the face where v_phi is stored), formed in FP64 and rounded
+ * once, so the inertial velocity and the angular momentum are unchanged.
+ * The planet keeps its azimuth: its phase is continuous at the current time
+ * and then advances at the new relative rate.  Later steps use the new
+ * rate in the Coriolis and centrifugal terms and in the momenta.  Cylindrical
+ * and spherical meshes; a context held by a batch cannot change frame (the
+ * batch holds its members' frames).  Synchronises.  Errors: BADARG (NULL,
+ * non-finite omega_new, Cartesian mesh, context held by a batch), CUDA. */
+int fargo_change_frame(fargo_ctx *ctx, double omega_new);
+
 /* Conserved totals over active cells with compensated FP64 sums:
  * out[0] = sum rho V, out[1] = sum e V, out[2] = sum (Pi-_x + Pi+_x)/2 V
  * (X momentum, angular momentum in cyl/sph; Eqs. 16-17, Tab. momenta).

@@ -31,7 +31,7 @@ class OrParams(C.Structure):
                 ("omega_f", C.c_double), ("fargo", C.c_int),
                 ("bc_ylo", C.c_int), ("bc_yhi", C.c_int), ("bc_zlo", C.c_int), ("bc_zhi", C.c_int),
                 ("star_mass", C.c_double), ("planet_q", C.c_double), ("planet_a", C.c_double),
-                ("planet_eps", C.c_double), ("indirect", C.c_int)]
+                ("planet_eps", C.c_double), ("indirect", C.c_int), ("planet_phase0", C.c_double)]
 
 
 class OrState(C.Structure):
@@ -67,6 +67,7 @@ def lib():
         L.or_cfl.argtypes = [pp, ps, P, C.c_double, C.c_double, P]
         L.or_cfl.restype = C.c_int
         L.or_potential.argtypes = [pp, C.c_double, P]
+        L.or_change_frame.argtypes = [pp, ps, C.c_double, C.c_double]
         L.or_substep1.argtypes = [pp, ps, P, C.c_double]
         for name in ("or_artificial_viscosity", "or_compression_heating", "or_viscosity"):
             getattr(L, name).argtypes = [pp, ps, C.c_double]
@@ -136,6 +137,10 @@ class Oracle:
             t = t + dt
             n += 1
         return t, n
+
+    def change_frame(self, st, omega_new, t):
+        """Frame change at time t to the rate omega_new (Eq. 13), in place."""
+        lib().or_change_frame(C.byref(self.p), C.byref(self._state(st)), float(omega_new), float(t))
 
     def bc_fill(self, st):
         lib().or_bc_fill(C.byref(self.p), C.byref(self._state(st)))

@@ -403,7 +403,8 @@ int or_cfl(const or_params *p, const or_state *s, const double *v0, double t, do
 /* Cell 5: gravitational potential at cell centres at time t.  Reading: a    */
 /* central mass (Phi = -M/r with r the spherical radius), a planet of mass q */
 /* on a fixed circular orbit of radius a in the midplane at phase            */
-/* (Omega_p - Omega_f) t, Omega_p = sqrt((M+q)/a^3), Plummer smoothing eps,   */
+/* phi_0 + (Omega_p - Omega_f) t, Omega_p = sqrt((M+q)/a^3) (phi_0 = 0 until  */
+/* a frame change moves it), Plummer smoothing eps,                           */
 /* and the indirect term q (r . r_p)/a^3.                                     */
 /* ------------------------------------------------------------------------ */
 void or_potential(const or_params *p, double t, double *phi)
@@ -412,7 +413,7 @@ void or_potential(const or_params *p, double t, double *phi)
     mesh_init(&m, p);
     double M = p->star_mass, q = p->planet_q, a = p->planet_a;
     double om = q > 0.0 ? sqrt((M + q) / (a * a * a)) : 0.0;
-    double ph = (om - p->omega_f) * t;
+    double ph = p->planet_phase0 + (om - p->omega_f) * t;
     double xp = a * cos(ph), yp = a * sin(ph);
     for (int k = 0; k < m.nzt; k++)
         for (int j = 0; j < m.nyt; j++)
@@ -1289,5 +1290,31 @@ void or_planet_force(const or_params *p, const or_state *st, const double rp[3],
     out[1] = ay.s + ay.c;
     out[2] = az.s + az.c;
     out[3] = rp[0] * out[1] - rp[1] * out[0];
+    mesh_free(&m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Frame change, Sec. 3.2, Eq. 13: when the frame's rotation rate changes   */
+/* from Omega_f to Omega_f', every azimuthal velocity becomes               */
+/* v_phi - (Omega_f' - Omega_f) R, R the lever arm at the face where v_phi  */
+/* is stored (the ring's cylindrical radius), so the inertial velocity is   */
+/* unchanged.  Ghost cells are corrected too.  The planet keeps its azimuth */
+/* at time t: its phase offset moves by (Omega_f' - Omega_f) t.             */
+/* ------------------------------------------------------------------------ */
+void or_change_frame(or_params *p, or_state *s, double omega_new, double t)
+{
+    mesh m;
+    mesh_init(&m, p);
+    double dom = omega_new - p->omega_f;
+    for (int k = 0; k < m.nzt; k++)
+        for (int j = 0; j < m.nyt; j++) {
+            double R = ring_R(&m, j, k);
+            for (int i = 0; i < m.nx; i++) {
+                size_t c = IDX(&m, i, j, k);
+                s->vx[c] = s->vx[c] - dom * R;
+            }
+        }
+    p->planet_phase0 += dom * t;
+    p->omega_f = omega_new;
     mesh_free(&m);
 }

@@ -35,6 +35,7 @@ typedef struct {
     int bc_ylo, bc_yhi, bc_zlo, bc_zhi;
     double star_mass, planet_q, planet_a, planet_eps;
     int indirect;
+    double planet_phase0;       /* planet azimuth at t = 0 in the current frame (moved by frame changes) */
 } or_params;
 
 typedef struct { double *rho, *e, *vx, *vy, *vz; } or_state;
@@ -45,6 +46,9 @@ int  or_step(const or_params *p, or_state *s, double t, double t_end, double dt_
 
 /* Individual sub-steps (each cites its section inside the source). */
 void or_bc_fill(const or_params *p, or_state *s);
+/* Frame change at time t to the rotation rate omega_new (Sec. 3.2, Eq. 13):
+ * corrects v_x everywhere and updates p (omega_f, planet_phase0). */
+void or_change_frame(or_params *p, or_state *s, double omega_new, double t);
 void or_v0(const or_params *p, const or_state *s, double *v0 /* [nz_t][ny_t] */);
 int  or_cfl(const or_params *p, const or_state *s, const double *v0, double t, double t_end, double *dt);
 void or_potential(const or_params *p, double t, double *phi /* full cell array */);

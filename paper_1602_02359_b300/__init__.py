@@ -29,7 +29,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
             "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -96,6 +96,7 @@ def lib():
         L.fargo_nbody_rk5_async.argtypes = [C.c_int, vp, vp, C.c_double, C.c_double, vp, vp, C.c_int, vp, C.c_int,
                                             vp]
         L.fargo_planets_advance_async.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int]
+        L.fargo_change_frame.argtypes = [vp, C.c_double]
         L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
         L.fargo_get_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
         L.fargo_set_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
@@ -260,6 +261,11 @@ class Fargo:
         r = (C.c_double * 3)(*[float(v) for v in rp])
         _check(lib().fargo_planet_force_async(self.h, r, float(eps), int(bool(bm08)), C.c_void_p(out_ptr)),
                "fargo_planet_force_async")
+
+    def change_frame(self, omega_new):
+        """fargo_change_frame: the frame's rotation rate becomes omega_new at
+        the current time (Eq. 13)."""
+        _check(lib().fargo_change_frame(self.h, float(omega_new)), "fargo_change_frame")
 
     def planets_force_async(self, n, y_ptr, stride, eps, out_ptr, bm08=False):
         """fargo_planets_force_async: the gas force on n planets whose

@@ -69,6 +69,7 @@ struct fargo_ctx {
     double *pf = nullptr;   // planet force: result (4), then the azimuth and ring tables of one call
     double *pacc = nullptr; // planetary step: gas accelerations of up to kNbMax planets and of the star (4 each)
     double star_mass = 0.0;
+    int batch_refs = 0;     // batches holding this context (their plans snapshot its frame)
     float *ringmax = nullptr;
     int nrings_active = 0, cfl_blocks = 0, sum_blocks = 0;
     fk::Buffers<double> b64;

@@ -981,6 +981,59 @@ extern "C" int fargo_planets_advance_async(fargo_ctx *c, int n, double *y, const
     return nbody_launch(n, y, mass, c->star_mass, 0.0, &c->sc->dt, c->pacc, 4, star, indirect, c->stream);
 }
 
+// Frame change (Sec. 3.2, Eq. 13): v_phi -= (Omega' - Omega) R at every
+// v_phi point of the array, ghosts included (frozen ghosts hold state in the
+// frame too).  R is the ring's lever arm at the face centre where v_phi
+// lives (cylindrical radius).  Formed in FP64 and rounded once.
+template <typename T>
+__global__ void __launch_bounds__(256) k_change_frame(T *vx, const double *Rd, double dom, int nx, int nyt, int nzt,
+                                                      int sj, int sk)
+{
+    const long long n = (long long)nx * nyt * nzt;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % nx);
+        const long long r = t / nx;
+        const int j = (int)(r % nyt), k = (int)(r / nyt);
+        const long long c = (long long)k * sk + (long long)j * sj + i;
+        vx[c] = (T)((double)vx[c] - dom * Rd[(size_t)k * nyt + j]);
+    }
+}
+
+template <typename T>
+static int change_frame_impl(fargo_ctx *c, Buffers<T> &b, double omega_new)
+{
+    Scal sh;
+    int rc = read_scal(c, &sh);   // the current time (synchronises)
+    if (rc) return rc;
+    MeshD &m = c->m;
+    const double dom = omega_new - m.omega;
+    const long long n = (long long)m.nx * m.nyt * m.nzt;
+    k_change_frame<T><<<grid_for(n, 256), 256, 0, c->stream>>>(b.A.vx, b.tab.Rd, dom, m.nx, m.nyt, m.nzt, m.sj,
+                                                                 m.sk);
+    CK(cudaGetLastError());
+    // the planet keeps its azimuth: php0 + om_rel t is continuous at t
+    if (m.has_planet) {
+        m.php0 += dom * sh.t;
+        m.om_rel -= dom;
+    }
+    m.omega = omega_new;
+    b.tab.omega = (T)omega_new;
+    if (c->gexec) {   // the captured step holds the old frame
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_change_frame(fargo_ctx *c, double omega_new)
+{
+    if (!c || !isfinite(omega_new) || c->geom == FARGO_CART) return FARGO_ERR_BADARG;
+    if (c->batch_refs > 0) return FARGO_ERR_BADARG;
+    return c->prec == FARGO_F64 ? change_frame_impl<double>(c, c->b64, omega_new)
+                                : change_frame_impl<float>(c, c->b32, omega_new);
+}
+
 extern "C" int fargo_sums(fargo_ctx *c, double out[3])
 {
     if (!c || !out) return FARGO_ERR_BADARG;
@@ -1010,7 +1063,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     sh.dt_fixed = dt;
     sh.counter = 0;
     if (m.has_planet) {
-        const double ph = m.om_rel * sh.t;
+        const double ph = m.php0 + m.om_rel * sh.t;
         sh.xp = m.pa * cos(ph);
         sh.yp = m.pa * sin(ph);
     }

@@ -633,6 +633,7 @@ extern "C" int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, 
     b->n = n;
     b->prec = prec;
     b->mem.assign(members, members + n);
+    for (fargo_ctx *m : b->mem) m->batch_refs++;   // released by fargo_batch_destroy
     int rc = FARGO_OK;
     if (stream) {
         b->stream = (cudaStream_t)stream;
@@ -659,6 +660,7 @@ extern "C" int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, 
 extern "C" void fargo_batch_destroy(fargo_batch *b)
 {
     if (!b) return;
+    for (fargo_ctx *m : b->mem) m->batch_refs--;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);

@@ -16,6 +16,7 @@ struct MeshD {
     int sj, sk;                  // row pitch, plane stride (elements)
     long long ntot;              // elements per field (below 2^31, checked at creation)
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
+    double php0;                 // planet azimuth at t = 0 in the current frame (moved by frame changes)
 };
 
 // Geometry tables (Appendix A) in the field precision T, plus the FP64

@@ -183,7 +183,7 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
     // planet angle tables for this step (time t^n)
     if (m.has_planet) {
         for (int i = bid * blockDim.x + threadIdx.x; i < m.nx; i += nblk * blockDim.x) {
-            const double dphi = (m.xmin + (i + 0.5) * m.dx) - m.om_rel * sc->t;
+            const double dphi = (m.xmin + (i + 0.5) * m.dx) - (m.php0 + m.om_rel * sc->t);
             const double sh = sin(0.5 * dphi);
             tb.ps[i] = (T)(sh * sh);
             tb.pc[i] = (T)cos(dphi);
