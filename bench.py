@@ -74,16 +74,23 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.45, "substep1": 33.46, "artvisc": 36.56, "visc_tau": 36.61, "visc_apply": 54.62, "transport_x": 56.91, "transport_y": 64.71, "transport_z": 65.82, "orbital": 58.15, "newvel": 41.7}
-KERNEL_SRC_HASH = "f9b4d740b0ebd452"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.41, "substep1": 33.4, "artvisc": 36.48, "visc_tau": 36.54, "visc_apply": 54.67, "transport_x": 56.92, "transport_y": 64.73, "transport_z": 65.84, "orbital": 58.12, "newvel": 41.72}
+KERNEL_SRC_HASH = "d94b9756fad87d6d"
 
 # The same for the batched step: DRAM bytes per active cell of every batched
 # phase (all its launches of one step summed), measured on batch-medium (the
 # first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
 # whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
-TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.31, "substep1": 17.85, "artvisc": 18.03, "visc_tau": 20.65, "visc_apply": 33.39, "transport_x": 24.29, "transport_y": 42.84, "orbital": 32.27, "newvel": 27.12}
-BATCH_SRC_HASH = "d3031bdbafb974dc"
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.32, "substep1": 17.69, "artvisc": 18.02, "visc_tau": 20.66, "visc_apply": 33.37, "transport_x": 24.3, "transport_y": 42.84, "orbital": 32.26, "newvel": 27.11}
+BATCH_SRC_HASH = "f392a9f76242857c"
 
+
+# DRAM bytes per launch of the direct-sum planet force on the 3D disk (ncu,
+# full size, one pass: dram__bytes_read.sum + dram__bytes_write.sum, median of
+# four launches), valid while kernels_planet.cuh keeps PFORCE_SRC_HASH
+# (profiles/planet_force_disk3d_ncu.md).
+PFORCE_TRAFFIC_3D = 302.97e6
+PFORCE_SRC_HASH = "8df4b5ffdd3c4d95"
 
 # Sources of the single-instance step's kernels (the traffic table above
 # applies to them only).
@@ -555,8 +562,11 @@ def planet_force_timing(torch, c, stream, w, esz, dev, reps=20):
     hbm, kind = peaks()
     rp = (w.planet_a, 0.0, 0.0)
     res = torch.empty(4, dtype=torch.float64, device=dev)
+    full_3d = w.name == "disk3d" and w.cells == 1536 * 512 * 96 and esz == 4
+    traffic = (PFORCE_TRAFFIC_3D if full_3d and kernel_source_hash(("kernels_planet.cuh",)) == PFORCE_SRC_HASH
+               else None)
     out = {"bound": "hbm", "peak": hbm, "peak_kind": f"{kind} copy bandwidth (burst)", "unit": "GB/s",
-           "alg_bytes_per_call": w.cells * esz, "launches_per_call": 2}
+           "alg_bytes_per_call": w.cells * esz, "launches_per_call": 2, "traffic_direct": traffic}
     for bm08 in (False, True):
         with torch.cuda.stream(stream):
             for _ in range(3):
