@@ -31,7 +31,8 @@ class OrParams(C.Structure):
                 ("omega_f", C.c_double), ("fargo", C.c_int),
                 ("bc_ylo", C.c_int), ("bc_yhi", C.c_int), ("bc_zlo", C.c_int), ("bc_zhi", C.c_int),
                 ("star_mass", C.c_double), ("planet_q", C.c_double), ("planet_a", C.c_double),
-                ("planet_eps", C.c_double), ("indirect", C.c_int), ("planet_phase0", C.c_double)]
+                ("planet_eps", C.c_double), ("indirect", C.c_int), ("planet_phase0", C.c_double),
+                ("shearing", C.c_int), ("oort_a", C.c_double)]
 
 
 class OrState(C.Structure):
@@ -113,6 +114,8 @@ class Oracle:
                           w.gamma, int(w.iso), _ptr(cs), _ptr(nu), w.cfl, w.cq, int(w.av_dt_literal),
                           w.omega_f, int(w.fargo), w.bc_y[0], w.bc_y[1], w.bc_z[0], w.bc_z[1],
                           w.star_mass, w.planet_q, w.planet_a, w.planet_eps, int(w.indirect))
+        self.p.shearing = int(bool(getattr(w, "shearing", False)))
+        self.p.oort_a = float(getattr(w, "oort_a", 0.0))
         self.shape = w.shape
         self.nrings = w.nz_t * w.ny_t
 

@@ -87,6 +87,16 @@ static double ring_R(const mesh *m, int j, int k)
     default: return 1.0;
     }
 }
+/* The frame's share of the X momentum per unit mass of ring (j,k) (Tab.     */
+/* momenta): R^2 Omega_f in cylindrical and spherical geometry, 2 Omega_f y  */
+/* in the shearing sheet (y the cell-centre Y), none in plain Cartesian.     */
+static double frame_w(const mesh *m, int j, int k)
+{
+    const or_params *p = m->p;
+    if (p->geom == OR_CART) return p->shearing ? 2.0 * p->omega_f * m->ym[j] : 0.0;
+    double R = ring_R(m, j, k);
+    return R * R * p->omega_f;
+}
 /* Azimuthal (X) cell length of ring (j,k). */
 static double len_x(const mesh *m, int j, int k) { return ring_R(m, j, k) * m->dx; }
 /* Z cell length and centre-to-centre distance across Z face k. */
@@ -494,6 +504,13 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
                             cen += vth * vth;
                         }
                         acc += cen / p->yf[j];
+                    } else if (p->shearing) {
+                        /* shearing sheet (Sec. 3.3, its Y equation): Coriolis 2 Omega_f v_x with
+                           v_x averaged over the four faces around the Y face, and the tidal
+                           term -4 A Omega_f y at the face */
+                        int ip = IP(&m, i);
+                        double vxa = 0.25 * (vx[c] + vx[IDX(&m, ip, j, k)] + vx[cm] + vx[IDX(&m, ip, j - 1, k)]);
+                        acc += 2.0 * om * vxa - 4.0 * p->oort_a * om * p->yf[j];
                     }
                     s->vy[c] = vy[c] + dt * acc;
                 }
@@ -841,7 +858,7 @@ void or_momenta(const or_params *p, const or_state *s, double *pi[6])
     for (int k = 0; k < m.nzt; k++)
         for (int j = 0; j < m.nyt; j++) {
             double R = ring_R(&m, j, k);
-            double w = R * R * p->omega_f;
+            double w = frame_w(&m, j, k);
             double fz = p->geom == OR_SPH ? m.ym[j] : 1.0;
             for (int i = 0; i < m.nx; i++) {
                 size_t c = IDX(&m, i, j, k);
@@ -1164,7 +1181,7 @@ void or_new_velocities(const or_params *p, or_state *s, double *pi[6])
     const double *rho = s->rho;
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++) {
-            double R = ring_R(&m, j, k), w = R * R * p->omega_f;
+            double R = ring_R(&m, j, k), w = frame_w(&m, j, k);
             for (int i = 0; i < m.nx; i++) {
                 size_t c = IDX(&m, i, j, k), cm = IDX(&m, IM(&m, i), j, k);
                 s->vx[c] = ((pi[1][cm] + pi[0][c]) / (rho[cm] + rho[c]) - w) / R;

@@ -36,6 +36,8 @@ typedef struct {
     double star_mass, planet_q, planet_a, planet_eps;
     int indirect;
     double planet_phase0;       /* planet azimuth at t = 0 in the current frame (moved by frame changes) */
+    int shearing;               /* Cartesian shearing sheet (Sec. 2): X along the shear flow, Y across it */
+    double oort_a;              /* its shear rate A (the unperturbed flow is v_x = 2 A y) */
 } or_params;
 
 typedef struct { double *rho, *e, *vx, *vy, *vz; } or_state;

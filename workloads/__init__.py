@@ -61,6 +61,8 @@ class Workload:
     t_end: float
     state: dict               # field name -> (nz_t+1, ny_t+1, nx) float64
     av_dt_literal: bool = False
+    shearing: bool = False    # Cartesian shearing sheet (X along the shear flow)
+    oort_a: float = 0.0       # its shear rate A: unperturbed v_x = 2 A y
 
     @property
     def ny_t(self):
@@ -361,6 +363,31 @@ def vortensity(w, st):
     curl = (d_rvp - d_vr) / r
     sig = 0.25 * (rho[j] + rho[j - 1] + np.roll(rho[j], 1, axis=1) + np.roll(rho[j - 1], 1, axis=1))
     return curl / sig
+
+
+def shearing_sheet(nx=16, ny=64, omega=1.0, oort_a=-0.75, cs=1e-3, ly=2.0, lx=0.5, u0=0.0, w0=0.0,
+                   fargo=True, g=3, cq=1.41):
+    """A 2D Cartesian shearing sheet (Sec. 2 and Sec. 3.3): the frame turns
+    at Omega, X runs along the shear flow v_x = 2 A y (A = -3/4 Omega for
+    Keplerian shear) and Y across it, y in [-ly/2, ly/2] on ny cells and x
+    periodic over lx on nx cells.  Uniform density 1, isothermal with sound
+    speed cs, no potential.  A uniform velocity perturbation (u0 along X,
+    w0 along Y) rides on the shear flow.  Y ghosts frozen to the initial
+    state."""
+    yf = faces(ny, g, -0.5 * ly, 0.5 * ly)
+    zf = faces(1, g, -0.5, 0.5)
+    w = Workload("shearing_sheet", CART, nx, ny, 1, g, 0.0, lx, yf, zf, 1.4, True,
+                 None, None, 0.44, cq, fargo, omega,
+                 (BC_FROZEN, BC_FROZEN), (BC_FROZEN, BC_FROZEN),
+                 0.0, 0.0, 1.0, 0.0, False, 0.0, 1e30, {}, shearing=True, oort_a=oort_a)
+    w.cs = np.full((w.nz_t, w.ny_t), cs)
+    ym = centres(yf)
+    st = _empty(w.shape)
+    st["rho"][:w.nz_t, :w.ny_t, :] = 1.0
+    st["vx"][:w.nz_t, :w.ny_t, :] = (2.0 * oort_a * ym + u0)[None, :, None]
+    st["vy"][:w.nz_t, :w.ny_t + 1, :] = w0
+    w.state = st
+    return w
 
 
 def batch_params(n=256, seed=1602):
