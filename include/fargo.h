@@ -82,6 +82,10 @@ typedef struct {
     double star_mass;           /* central mass M (cyl/sph); 0 = none */
     int precision;              /* FARGO_F64 or FARGO_F32 */
     void *stream;               /* cudaStream_t, NULL = legacy default stream */
+    int shearing;               /* 1: Cartesian shearing sheet (Sec. 2): X along the shear flow, Y
+                                   across it; X momentum rho (v_x + 2 Omega_f y) (Tab. momenta), and
+                                   the Y source 2 Omega_f v_x - 4 A Omega_f y; Cartesian meshes only */
+    double oort_a;              /* the sheet's shear rate A (unperturbed flow v_x = 2 A y) */
 } fargo_params;
 
 /* Create a context for an nx * ny * nz active mesh with `ghost` ghost layers

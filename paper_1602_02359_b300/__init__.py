@@ -64,7 +64,7 @@ class Params(C.Structure):
                 ("cs", PD), ("nu", PD), ("cfl", C.c_double), ("cq", C.c_double),
                 ("av_dt_literal", C.c_int), ("omega_frame", C.c_double), ("fargo", C.c_int),
                 ("bc_y", C.c_int * 2), ("bc_z", C.c_int * 2), ("star_mass", C.c_double),
-                ("precision", C.c_int), ("stream", C.c_void_p)]
+                ("precision", C.c_int), ("stream", C.c_void_p), ("shearing", C.c_int), ("oort_a", C.c_double)]
 
 
 _lib = None
@@ -168,6 +168,8 @@ class Fargo:
         p.star_mass = w.star_mass
         p.precision = precision
         p.stream = stream
+        p.shearing = int(bool(getattr(w, "shearing", False)))
+        p.oort_a = float(getattr(w, "oort_a", 0.0))
         pl = Planet(w.planet_q, w.planet_a, w.planet_eps, int(w.indirect))
         h = C.c_void_p()
         gamma = -1.0 if w.iso else w.gamma

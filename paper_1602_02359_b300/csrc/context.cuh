@@ -31,6 +31,7 @@ struct HostGeom {
     std::vector<double> ym, dy, zm, dz, dyc, lx, ly, lz, dmin, R, zc, vol, fz, dzc;
     std::vector<double> sx, vinv, sy, sz, lenz, gphy, gphz, cosx, sinx, cs, nu;
     std::vector<double> rma, fra, z2, qar;
+    std::vector<double> wfr, tid;   // frame term of the X momentum per ring; shearing-sheet tide per Y face
 };
 
 // Everything one step of one instance needs on the device: the mesh, its

@@ -124,6 +124,9 @@ static void build_geometry(fargo_ctx *c, const fargo_params *p, double gamma, co
     h.vinv.assign(nr, 0); h.lenz.assign(nr, 0); h.gphy.assign(nr, 0); h.gphz.assign(nr, 0);
     h.cs.assign(nr, 0); h.nu.assign(nr, 0);
     h.rma.assign(nr, 0); h.fra.assign(nr, 0); h.z2.assign(nr, 0); h.qar.assign(nr, 0);
+    h.wfr.assign(nr, 0); h.tid.assign(nyt + 1, 0);
+    if (p->shearing)   // the shearing sheet's tide per Y face, 4 A Omega_f y (subtracted)
+        for (int j = 0; j <= nyt; j++) h.tid[j] = 4.0 * p->oort_a * p->omega_frame * yf[j];
     h.sy.assign(nf, 0); h.sz.assign(nf, 0);
     auto syk = [&](int k) {
         if (geom == FARGO_CYL) return zf[k + 1] - zf[k];
@@ -162,6 +165,9 @@ static void build_geometry(fargo_ctx *c, const fargo_params *p, double gamma, co
             if (geom == FARGO_CYL) R = h.ym[j];
             else if (geom == FARGO_SPH) R = h.ym[j] * sin(h.zm[k]);
             h.R[r] = R;
+            // the frame's share of the X momentum (Tab. momenta)
+            if (geom != FARGO_CART) h.wfr[r] = R * R * p->omega_frame;
+            else if (p->shearing) h.wfr[r] = 2.0 * p->omega_frame * h.ym[j];
             h.lx[r] = R * dx;
             h.ly[r] = h.dy[j];
             h.lz[r] = geom == FARGO_SPH ? h.ym[j] * h.dz[k] : h.dz[k];
@@ -234,6 +240,7 @@ static int build_tables(fargo_ctx *c, Tab<T> &t)
     UP(R, h.R); UP(lenx, h.lx); UP(lenz, h.lenz); UP(dzc, h.dzc); UP(sx, h.sx); UP(vinv, h.vinv);
     UP(cs, h.cs); UP(nu, h.nu); UP(gphy, h.gphy); UP(gphz, h.gphz); UP(fz, h.fz);
     UP(sy, h.sy); UP(sz, h.sz);
+    UP(wfr, h.wfr); UP(tid, h.tid); UPD(wfrd, h.wfr);
     UPD(lx, h.lx); UPD(ly, h.ly); UPD(lz, h.lz); UPD(dmin, h.dmin); UPD(csd, h.cs); UPD(nud, h.nu);
     UPD(Rd, h.R); UPD(zcd, h.zc); UPD(cosx, h.cosx); UPD(sinx, h.sinx);
     UP(rma, h.rma); UP(fra, h.fra); UP(z2, h.z2); UP(qar, h.qar);
@@ -476,6 +483,7 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     if ((ny > 1 || nz > 1) && ghost < 2) return FARGO_ERR_BADARG;
     if (!prm->yfaces || !prm->zfaces || !(prm->xmax > prm->xmin)) return FARGO_ERR_BADARG;
     if (prm->precision != FARGO_F64 && prm->precision != FARGO_F32) return FARGO_ERR_BADARG;
+    if (prm->shearing && (geom != FARGO_CART || !isfinite(prm->oort_a))) return FARGO_ERR_BADARG;
     if (gamma <= 0.0 && !prm->cs) return FARGO_ERR_BADARG;
     if (!(prm->cfl > 0.0)) return FARGO_ERR_BADARG;
     for (int s = 0; s < 2; s++)
@@ -534,6 +542,7 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     m.cq = prm->cq;
     m.cfl = prm->cfl;
     m.omega = prm->omega_frame;
+    m.shearing = prm->shearing ? 1 : 0;
     m.av_c2 = 4.0 * sqrt(2.0);
     if (m.has_planet) {
         m.pq = planet->q; m.pa = planet->a; m.pa3 = planet->a * planet->a * planet->a;
@@ -780,6 +789,7 @@ static int sums_impl(fargo_ctx *c, Buffers<T> &b, double out[3])
     const MeshD &m = c->m;
     SumInput<T> in{b.A.rho, m.iso ? nullptr : b.A.e, b.A.vx, c->vol, b.tab.Rd, m.omega,
                    m.nx, m.j0, m.j1, m.k0, m.k1, m.nyt, m.sj, m.sk};
+    if (c->geom == FARGO_CART) in.wfr = b.tab.wfrd;   // the shearing sheet's 2 Omega_f y (0 otherwise)
     k_sums<T><<<c->sum_blocks, 256, 0, c->stream>>>(in, c->part2, &c->sc->counter2, c->sums);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, c->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -17,6 +17,7 @@ struct MeshD {
     long long ntot;              // elements per field (below 2^31, checked at creation)
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
     double php0;                 // planet azimuth at t = 0 in the current frame (moved by frame changes)
+    int shearing;                // Cartesian shearing sheet
 };
 
 // Geometry tables (Appendix A) in the field precision T, plus the FP64
@@ -44,6 +45,11 @@ struct Tab {
     T gm1, cq2, omega, pq, peps2, dx, half_gm1, g1, k4;
     // Courant screening: 4 nu / dmin^2 and dmin per ring
     const T *r4, *dminT;
+    // the frame's share of the X momentum per unit mass, per ring: R^2 Omega_f
+    // (cylindrical, spherical), 2 Omega_f y (shearing sheet), 0 (Cartesian);
+    // and the shearing sheet's tidal acceleration -4 A Omega_f y per Y face
+    const T *wfr, *tid;
+    const double *wfrd;
     // inverse centre-to-centre distances across Y faces (per j) and Z faces (per ring)
     const T *idyc, *idzc;
     // reciprocals of mesh lengths: per ring 1/lenx, 1/lenz, 1/R; per j 1/dy,
@@ -88,6 +94,7 @@ struct CfgRun {
     __host__ __device__ static bool indirect(const MeshD &m) { return m.indirect; }
     __host__ __device__ static bool star(const MeshD &m) { return m.has_star; }
     __host__ __device__ static bool av(const MeshD &m) { return m.has_av; }
+    __host__ __device__ static bool shearing(const MeshD &m) { return m.shearing; }
 };
 template <int GEOM, bool Z, bool ISO>
 struct CfgDisk {
@@ -100,6 +107,7 @@ struct CfgDisk {
     __host__ __device__ static constexpr bool indirect(const MeshD &) { return true; }
     __host__ __device__ static constexpr bool star(const MeshD &) { return true; }
     __host__ __device__ static constexpr bool av(const MeshD &) { return true; }
+    __host__ __device__ static constexpr bool shearing(const MeshD &) { return false; }
 };
 typedef CfgDisk<SPH, true, false> CfgDisk3D;   // spherical, adiabatic
 typedef CfgDisk<CYL, false, true> CfgDisk2D;   // cylindrical, isothermal

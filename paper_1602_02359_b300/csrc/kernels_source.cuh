@@ -101,6 +101,12 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
                     cen += vth * vth;
                 }
                 acc += cen * tb.iyf[j];
+            } else if (F::shearing(m)) {
+                // shearing sheet: Coriolis 2 Omega_f v_x (v_x averaged over the four
+                // faces around the Y face) and the tide -4 A Omega_f y
+                const idx_t cp = c - i + ip, cmp = cm - i + ip;
+                const T vxa = T(0.25) * (in.vx[c] + in.vx[cp] + in.vx[cm] + in.vx[cmp]);
+                acc += T(2) * om * vxa - tb.tid[j];
             }
             v = v + dt * acc;
         }

@@ -275,7 +275,8 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     const idx_t base = IX(m, 0, j, k);
     const bool adi = !m.iso;
     const bool sweep = active && m.hasX;
-    const T R = tb.R[ring], w = R * R * tb.omega, fz = tb.fz[ring];
+    // the frame term of the X momentum: R^2 Omega_f, or the Cartesian table (shearing sheet)
+    const T R = tb.R[ring], w = m.geom == CART ? tb.wfr[ring] : R * R * tb.omega, fz = tb.fz[ring];
     const T *Rho = sm, *Vx = sm + (size_t)rw.rVX * rp;
     // ratio of quantity q to the density at cell i, as scale * row[i + off] +
     // shift (or e / rho), for the order rho, e, Pi-x, Pi+x, Pi-y, Pi+y,
@@ -1158,7 +1159,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     if (j < m.nyt && k < m.nzt) {
         if (jact && kact) {
             const idx_t cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
-            const T R = tb.R[ring], w = R * R * tb.omega;
+            const T R = tb.R[ring], w = F::geom(m) == CART ? tb.wfr[ring] : R * R * tb.omega;
             // divisions, not reciprocal products: v_x is rebuilt from R v_x every
             // step, and a rounded 1/R would bias it by R (1/R) - 1 each time
             state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
@@ -1226,6 +1227,7 @@ struct SumInput {
     double omega;
     int nx, j0, j1, k0, k1, nyt;
     long long sj, sk;
+    const double *wfr;   // the frame term of the X momentum per ring, or null for R^2 omega
 };
 
 // Per-block compensated partials of the three totals, then the last block to
@@ -1249,7 +1251,7 @@ __device__ void sums_reduce(const SumInput<T> &in, double *part, unsigned *count
         const double rho = (double)in.rho[c];
         kb_add(acc[0], rho * V);
         if (in.e) kb_add(acc[1], (double)in.e[c] * V);
-        const double R = in.R[ring], w = R * R * in.omega;
+        const double R = in.R[ring], w = in.wfr ? in.wfr[ring] : R * R * in.omega;
         const int ip = i + 1 == in.nx ? 0 : i + 1;
         const double pm = rho * (R * (double)in.vx[c] + w), pp = rho * (R * (double)in.vx[c - i + ip] + w);
         kb_add(acc[2], 0.5 * (pm + pp) * V);
