@@ -201,10 +201,26 @@ int fargo_nbody_rk5_async(int n, double *y, const double *mass, double mstar, do
  *   3. fargo_nbody_rk5_async with h = the dt of the context's last step,
  *      read on the device, and the context's star mass.
  * y ([n][6]) and mass ([n]) are device memory owned by the caller; y is
- * updated in place.  The force scratch belongs to the context.  Errors: as
- * fargo_planets_force_async. */
+ * updated in place.  The force scratch belongs to the context.  The
+ * integrator's star-centred, non-rotating coordinates are taken as the
+ * mesh's, so the context's frame must not rotate (Omega_f = 0).  Errors: as
+ * fargo_planets_force_async, plus BADARG for a rotating frame. */
 int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *mass, double eps, int bm08,
                                 int indirect);
+
+/* Where the step's planet is (Sec. 3.7, cell 5a feeding cell 5): pos, when
+ * not NULL, is a device address holding the planet's (x, y, z), read at the
+ * start of every later step (the potential's azimuth and per-ring tables are
+ * rebuilt from it on the device, the z part of the indirect term included),
+ * for example planet 0's row of the state that fargo_planets_advance_async
+ * updates, so that integrator and step alternate on the stream with no host
+ * round trip.  The planet's mass stays the one given at creation.  NULL
+ * returns to the fixed circular orbit (synchronises).  Requires a planet, a
+ * cylindrical or spherical mesh and a non-rotating frame (the integrator's
+ * coordinates are the mesh's); pos 8-byte aligned, owned by the caller and
+ * valid while set.  Errors: BADARG (no planet, Cartesian mesh, Omega_f != 0,
+ * context held by a batch, misaligned pos), CUDA. */
+int fargo_set_planet_source(fargo_ctx *ctx, const double *pos);
 
 /* Change the frame's rotation rate to omega_new at the current time (Sec.
  * 3.2, Eq. 13): every azimuthal velocity, ghosts included, becomes

@@ -32,7 +32,8 @@ class OrParams(C.Structure):
                 ("bc_ylo", C.c_int), ("bc_yhi", C.c_int), ("bc_zlo", C.c_int), ("bc_zhi", C.c_int),
                 ("star_mass", C.c_double), ("planet_q", C.c_double), ("planet_a", C.c_double),
                 ("planet_eps", C.c_double), ("indirect", C.c_int), ("planet_phase0", C.c_double),
-                ("shearing", C.c_int), ("oort_a", C.c_double)]
+                ("shearing", C.c_int), ("oort_a", C.c_double), ("planet_live", C.c_int),
+                ("planet_pos", C.c_double * 3)]
 
 
 class OrState(C.Structure):
@@ -140,6 +141,16 @@ class Oracle:
             t = t + dt
             n += 1
         return t, n
+
+    def set_planet_position(self, pos):
+        """The planet at pos (x, y, z) for the following steps (an integrated
+        planet); None returns to the circular orbit."""
+        if pos is None:
+            self.p.planet_live = 0
+        else:
+            self.p.planet_live = 1
+            for q in range(3):
+                self.p.planet_pos[q] = float(pos[q])
 
     def change_frame(self, st, omega_new, t):
         """Frame change at time t to the rate omega_new (Eq. 13), in place."""

@@ -414,7 +414,8 @@ int or_cfl(const or_params *p, const or_state *s, const double *v0, double t, do
 /* central mass (Phi = -M/r with r the spherical radius), a planet of mass q */
 /* on a fixed circular orbit of radius a in the midplane at phase            */
 /* phi_0 + (Omega_p - Omega_f) t, Omega_p = sqrt((M+q)/a^3) (phi_0 = 0 until  */
-/* a frame change moves it), Plummer smoothing eps,                           */
+/* a frame change moves it), or at the given position of an integrated      */
+/* planet (Sec. 3.7, cell 5a), Plummer smoothing eps,                         */
 /* and the indirect term q (r . r_p)/a^3.                                     */
 /* ------------------------------------------------------------------------ */
 void or_potential(const or_params *p, double t, double *phi)
@@ -424,7 +425,12 @@ void or_potential(const or_params *p, double t, double *phi)
     double M = p->star_mass, q = p->planet_q, a = p->planet_a;
     double om = q > 0.0 ? sqrt((M + q) / (a * a * a)) : 0.0;
     double ph = p->planet_phase0 + (om - p->omega_f) * t;
-    double xp = a * cos(ph), yp = a * sin(ph);
+    double xp = a * cos(ph), yp = a * sin(ph), zp = 0.0, rp3 = a * a * a;
+    if (p->planet_live) {
+        xp = p->planet_pos[0]; yp = p->planet_pos[1]; zp = p->planet_pos[2];
+        double r2 = xp * xp + yp * yp + zp * zp;
+        rp3 = r2 * sqrt(r2);
+    }
     for (int k = 0; k < m.nzt; k++)
         for (int j = 0; j < m.nyt; j++)
             for (int i = 0; i < m.nx; i++) {
@@ -445,9 +451,9 @@ void or_potential(const or_params *p, double t, double *phi)
                 double v = 0.0;
                 if (M > 0.0 && p->geom != OR_CART) v -= M / rs;
                 if (q > 0.0) {
-                    double d2 = (X - xp) * (X - xp) + (Y - yp) * (Y - yp) + Z * Z;
+                    double d2 = (X - xp) * (X - xp) + (Y - yp) * (Y - yp) + (Z - zp) * (Z - zp);
                     v -= q / sqrt(d2 + p->planet_eps * p->planet_eps);
-                    if (p->indirect) v += q * (X * xp + Y * yp) / (a * a * a);
+                    if (p->indirect) v += q * (X * xp + Y * yp + Z * zp) / rp3;
                 }
                 phi[IDX(&m, i, j, k)] = v;
             }

@@ -29,7 +29,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
             "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_set_planet_source", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -97,6 +97,7 @@ def lib():
                                             vp]
         L.fargo_planets_advance_async.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int]
         L.fargo_change_frame.argtypes = [vp, C.c_double]
+        L.fargo_set_planet_source.argtypes = [vp, vp]
         L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
         L.fargo_get_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
         L.fargo_set_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
@@ -263,6 +264,12 @@ class Fargo:
         r = (C.c_double * 3)(*[float(v) for v in rp])
         _check(lib().fargo_planet_force_async(self.h, r, float(eps), int(bool(bm08)), C.c_void_p(out_ptr)),
                "fargo_planet_force_async")
+
+    def set_planet_source(self, pos_ptr):
+        """fargo_set_planet_source: read the step's planet position from the
+        device address pos_ptr each step (None: the fixed circular orbit)."""
+        _check(lib().fargo_set_planet_source(self.h, C.c_void_p(pos_ptr) if pos_ptr else None),
+               "fargo_set_planet_source")
 
     def change_frame(self, omega_new):
         """fargo_change_frame: the frame's rotation rate becomes omega_new at

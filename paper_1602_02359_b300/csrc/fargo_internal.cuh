@@ -18,6 +18,7 @@ struct MeshD {
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
     double php0;                 // planet azimuth at t = 0 in the current frame (moved by frame changes)
     int shearing;                // Cartesian shearing sheet
+    const double *pl_pos;        // planet position read on the device each step (x, y, z), or null
 };
 
 // Geometry tables (Appendix A) in the field precision T, plus the FP64
@@ -41,6 +42,11 @@ struct Tab {
     // cos(dphi) of the offset to the planet
     const T *rma, *fra, *z2, *qar;
     T *ps, *pc;
+    // a planet whose position is read each step (pl_pos): the per-ring
+    // tables above rewritten at the step's start, and the z part of the
+    // indirect term, q Z z_p / |r_p|^3, per ring (writable aliases)
+    const T *zq;
+    T *pw[5];
     // run constants in the field precision (no FP64 work in FP32 kernels)
     T gm1, cq2, omega, pq, peps2, dx, half_gm1, g1, k4;
     // Courant screening: 4 nu / dmin^2 and dmin per ring
@@ -95,6 +101,7 @@ struct CfgRun {
     __host__ __device__ static bool star(const MeshD &m) { return m.has_star; }
     __host__ __device__ static bool av(const MeshD &m) { return m.has_av; }
     __host__ __device__ static bool shearing(const MeshD &m) { return m.shearing; }
+    __host__ __device__ static bool live(const MeshD &m) { return m.pl_pos != nullptr; }
 };
 template <int GEOM, bool Z, bool ISO>
 struct CfgDisk {
@@ -108,6 +115,7 @@ struct CfgDisk {
     __host__ __device__ static constexpr bool star(const MeshD &) { return true; }
     __host__ __device__ static constexpr bool av(const MeshD &) { return true; }
     __host__ __device__ static constexpr bool shearing(const MeshD &) { return false; }
+    __host__ __device__ static constexpr bool live(const MeshD &) { return false; }
 };
 typedef CfgDisk<SPH, true, false> CfgDisk3D;   // spherical, adiabatic
 typedef CfgDisk<CYL, false, true> CfgDisk2D;   // cylindrical, isothermal
@@ -118,7 +126,8 @@ inline bool cfg_matches(const MeshD &m)
 {
     return F::geom(m) == m.geom && F::hasX(m) == (m.hasX != 0) && F::hasY(m) == (m.hasY != 0) &&
            F::hasZ(m) == (m.hasZ != 0) && F::iso(m) == (m.iso != 0) && F::planet(m) == (m.has_planet != 0) &&
-           F::indirect(m) == (m.indirect != 0) && F::star(m) == (m.has_star != 0) && F::av(m) == (m.has_av != 0);
+           F::indirect(m) == (m.indirect != 0) && F::star(m) == (m.has_star != 0) && F::av(m) == (m.has_av != 0) &&
+           F::shearing(m) == (m.shearing != 0) && F::live(m) == (m.pl_pos != nullptr);
 }
 inline int cfg_of(const MeshD &m)
 {

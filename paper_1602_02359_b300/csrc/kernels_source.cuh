@@ -46,7 +46,10 @@ __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i,
     T v;
     if (sizeof(T) == 8) v = -tb.pq / sqrt(d2);
     else v = -tb.pq * rsqrtf((float)d2);
-    if (F::indirect(m)) v += tb.qar[ring] * tb.pc[i];
+    if (F::indirect(m)) {
+        v += tb.qar[ring] * tb.pc[i];
+        if (F::live(m)) v += tb.zq[ring];
+    }
     return v;
 }
 

@@ -13,7 +13,7 @@ import pytest
 import oracle
 import workloads as W
 from oracle import nbody as NB
-from tests.gpu_util import make_ctx, record
+from tests.gpu_util import compare_state, make_ctx, record
 
 pytestmark = pytest.mark.gpu
 
@@ -131,3 +131,63 @@ def test_planets_advance_matches_oracle(indirect, bm08):
     record("planets_advance_vs_oracle", indirect=int(indirect), bm08=int(bm08), max_abs=e)
     assert e < 1e-12
     c.close()
+
+
+def test_planet_coupled_to_the_step_matches_oracle():
+    """The step's planet read from the integrator's state on the device
+    (fargo_set_planet_source): four rounds of step, gas force, kick and
+    Cash-Karp step, against the same loop in the oracle (the planet's
+    position fed to its potential each step)."""
+    import torch
+    w = lumpy_disk(12)
+    eps = w.planet_eps
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    c = make_ctx(w)
+    q = w.planet_q
+    y = np.array([[1.0, 0.0, 0.0, 0.0, math.sqrt(1.0 + q), 0.0],
+                  [1.45, 0.35, 0.0, -0.2, 0.75, 0.0]])
+    m = np.array([q, 1e-5])
+    yd, md = dev(y), dev(m)
+    c.set_planet_source(yd.data_ptr())
+    t = 0.0
+    for n in range(4):
+        dt_g = c.step()
+        c.planets_advance_async(2, yd.data_ptr(), md.data_ptr(), eps, False, True)
+        o.set_planet_position(y[0, :3])
+        dt_o = o.step(st, t)
+        t += dt_o
+        assert abs(dt_g - dt_o) <= 1e-12 * dt_o, (n, dt_g, dt_o)
+        acc = np.array([o.planet_force(st, tuple(y[i, :3]), eps)[:3] for i in range(2)])
+        acc -= np.array(o.planet_force(st, (0.0, 0.0, 0.0), 0.0)[:3])[None, :]
+        y = NB.nbody_step(y, m, 1.0, dt_o, kick=acc)
+    torch.cuda.synchronize()
+    compare_state(w, c.get_state(), st, 1e-11)
+    e = np.max(np.abs(yd.cpu().numpy() - y))
+    record("planet_coupled_vs_oracle", max_abs=e)
+    assert e < 1e-12
+    c.close()
+
+
+def test_clearing_the_planet_source_restores_the_circular_orbit():
+    import paper_1602_02359_b300 as fb
+    w = lumpy_disk(13)
+    a, b = make_ctx(w), make_ctx(w)
+    pos = dev([0.9, 0.3, 0.0])
+    a.set_planet_source(pos.data_ptr())
+    a.step()                       # rewrites the planet tables
+    a.set_state(w.state)
+    a.set_time(0.0)
+    a.set_planet_source(None)      # back to the circular orbit
+    a.step()
+    b.step()
+    ga, gb = a.get_state(), b.get_state()
+    for k in ("rho", "vx", "vy"):
+        assert np.array_equal(ga[k], gb[k]), k
+    with pytest.raises(fb.FargoError):
+        make_ctx(W.random_box(W.CART, 16, 8, 1, seed=1, planet=False)).set_planet_source(pos.data_ptr())
+    wr = W.random_box(W.CYL, 32, 16, 1, seed=2, omega_f=0.5)
+    with pytest.raises(fb.FargoError):
+        make_ctx(wr).set_planet_source(pos.data_ptr())
+    a.close()
+    b.close()

@@ -131,3 +131,22 @@ def test_kick_updates_the_velocity_before_the_drift():
     v = y[:, 3:] + h * a
     assert np.allclose(out[:, 3:], v, rtol=0, atol=1e-15)
     assert np.allclose(out[:, :3], y[:, :3] + h * v, rtol=0, atol=1e-15)
+
+
+def test_integrated_planet_on_the_circular_orbit_gives_the_same_potential():
+    """The oracle's potential with the planet placed at a given position
+    (an integrated planet) reproduces the circular orbit's at that
+    position, in a cylindrical and a spherical mesh, and clearing it
+    restores the circular orbit."""
+    import oracle
+    import workloads as W
+    for w in (W.disk2d(nx=64, ny=24, q=1e-3), W.random_box(W.SPH, 48, 16, 10, seed=4)):
+        o = oracle.Oracle(w)
+        t = 1.7
+        om = math.sqrt((w.star_mass + w.planet_q) / w.planet_a ** 3) - w.omega_f
+        ref = o.potential(t)
+        o.set_planet_position((w.planet_a * math.cos(om * t), w.planet_a * math.sin(om * t), 0.0))
+        live = o.potential(t)
+        assert np.max(np.abs(live - ref)) <= 1e-14 * np.max(np.abs(ref))
+        o.set_planet_position(None)
+        assert np.array_equal(o.potential(t), ref)
