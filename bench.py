@@ -74,15 +74,15 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.41, "substep1": 33.4, "artvisc": 36.48, "visc_tau": 36.54, "visc_apply": 54.67, "transport_x": 56.92, "transport_y": 64.73, "transport_z": 65.84, "orbital": 58.12, "newvel": 41.72}
-KERNEL_SRC_HASH = "d94b9756fad87d6d"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.42, "substep1": 33.46, "artvisc": 36.54, "visc_tau": 36.61, "visc_apply": 54.63, "transport_x": 57.01, "transport_y": 64.73, "transport_z": 65.86, "orbital": 58.16, "newvel": 41.71}
+KERNEL_SRC_HASH = "08222bf0d94e6971"
 
 # The same for the batched step: DRAM bytes per active cell of every batched
 # phase (all its launches of one step summed), measured on batch-medium (the
 # first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
 # whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
-TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.32, "substep1": 17.69, "artvisc": 18.02, "visc_tau": 20.66, "visc_apply": 33.37, "transport_x": 24.3, "transport_y": 42.84, "orbital": 32.26, "newvel": 27.11}
-BATCH_SRC_HASH = "f392a9f76242857c"
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.33, "substep1": 17.86, "artvisc": 18.03, "visc_tau": 20.65, "visc_apply": 33.38, "transport_x": 24.3, "transport_y": 42.84, "orbital": 32.27, "newvel": 27.12}
+BATCH_SRC_HASH = "a33ee3976da7ac2e"
 
 
 # DRAM bytes per launch of the direct-sum planet force on the 3D disk (ncu,
