@@ -30,6 +30,8 @@ def lumpy(w, seed):
 CASES = [
     ("disk2d", lambda: lumpy(W.disk2d(nx=300, ny=70, q=1e-3), 1)),
     ("sph", lambda: lumpy(W.random_box(W.SPH, 96, 24, 14, seed=2, iso=False, nu=1e-3), 2)),
+    # rings of 301 cells: a ragged tail after the last 16-byte pack in FP32 and FP64
+    ("ragged", lambda: lumpy(W.disk2d(nx=301, ny=37, q=1e-3), 3)),
 ]
 PLANETS = [(1.0, 0.0, 0.0), (0.7, 0.75, 0.0), (-0.9, 0.2, 0.05)]
 
