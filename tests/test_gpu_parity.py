@@ -407,6 +407,18 @@ def test_bad_arguments_are_rejected():
     assert e.value.code == -6
 
 
+def test_rings_beyond_one_staging_buffer_are_refused():
+    """An FP64 2D disk of 8000-cell rings: the orbital step's five staged
+    rows need about 320 KB even in one buffer, over the 227 KB a CTA can
+    have, so fargo_create refuses the mesh (FARGO_ERR_SIZE) before any
+    launch; 4000-cell rings (one buffer, 161 KB) are accepted."""
+    import paper_1602_02359_b300 as fb
+    with pytest.raises(fb.FargoError) as e:
+        fb.Fargo(W.disk2d(nx=8000, ny=8), fb.F64)
+    assert e.value.code == -6
+    fb.Fargo(W.disk2d(nx=4000, ny=8), fb.F64).close()
+
+
 def test_run_to_lands_on_end_time_and_stops():
     w = W.sod(ny=64)
     c = make_ctx(w, t=0.0, t_end=0.05)
