@@ -146,6 +146,16 @@ int fargo_get_scalars(fargo_ctx *ctx, double *t, double *dt_last, long long *nst
  * mesh), CUDA. */
 int fargo_planet_force(fargo_ctx *ctx, const double rp[3], double eps, int bm08, double out[4]);
 
+/* The torque diagnostic's radial profile (Sec. 3.7): each active ring's share
+ * of the specific torque of fargo_planet_force, written to ring (host,
+ * ny * nz doubles, ring (j, k) of the active mesh at (k - k0) * ny + (j -
+ * j0), j fastest); the shares sum to the total.  Per ring, the lanes' sums
+ * in the field precision are added in FP64.  out (host, 4 values, may be
+ * NULL) receives fargo_planet_force's result for the same call.
+ * Synchronises.  Errors: as fargo_planet_force. */
+int fargo_planet_torque_profile(fargo_ctx *ctx, const double rp[3], double eps, int bm08, double *ring,
+                                double out[4]);
+
 /* fargo_planet_force without the synchronisation: the work is queued on the
  * context's stream after whatever is queued there (a step, a field upload),
  * and the 4 FP64 results are written to out, memory the device can write

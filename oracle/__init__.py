@@ -82,6 +82,7 @@ def lib():
         L.or_new_velocities.argtypes = [pp, ps, PP6]
         L.or_geometry.argtypes = [pp, P, P, P, P, P, P]
         L.or_planet_force.argtypes = [pp, ps, P, C.c_double, C.c_int, P]
+        L.or_planet_torque_profile.argtypes = [pp, ps, P, C.c_double, C.c_int, P]
         L.or_vanleer_slope.argtypes = [C.c_double] * 5
         L.or_vanleer_slope.restype = C.c_double
         L.or_ppa_faces.argtypes = [C.c_int, P, C.c_double, P]
@@ -229,6 +230,17 @@ class Oracle:
         assert rho.dtype == np.float64 and rho.flags.c_contiguous and rho.shape == self.shape
         s = OrState(_ptr(rho), None, None, None, None)
         lib().or_planet_force(C.byref(self.p), C.byref(s), _ptr(r), float(eps), int(bm08), _ptr(out))
+        return out
+
+    def planet_torque_profile(self, st, rp, eps, bm08=False):
+        """Each active ring's share of the specific torque, shape (nz, ny)."""
+        w = self.w
+        out = np.zeros((w.nz, w.ny))
+        r = np.ascontiguousarray(rp, dtype=np.float64)
+        rho = st["rho"]
+        assert rho.dtype == np.float64 and rho.flags.c_contiguous and rho.shape == self.shape
+        s = OrState(_ptr(rho), None, None, None, None)
+        lib().or_planet_torque_profile(C.byref(self.p), C.byref(s), _ptr(r), float(eps), int(bm08), _ptr(out))
         return out
 
     def sums(self, st):

@@ -1316,6 +1316,48 @@ void or_planet_force(const or_params *p, const or_state *st, const double rp[3],
     mesh_free(&m);
 }
 
+/* Radial profile of the torque (Sec. 3.7, the torque of the gas on the     */
+/* planet resolved by ring): each active ring's share of the specific       */
+/* torque r_p x a (z component), summed like or_planet_force.               */
+void or_planet_torque_profile(const or_params *p, const or_state *st, const double rp[3], double eps, int bm08,
+                              double *ring)
+{
+    mesh m;
+    mesh_init(&m, p);
+    int ny = m.j1 - m.j0;
+    for (int k = m.k0; k < m.k1; k++)
+        for (int j = m.j0; j < m.j1; j++) {
+            double mean = 0.0;
+            if (bm08) {
+                nsum r = {0, 0};
+                for (int i = 0; i < m.nx; i++) nsum_add(&r, st->rho[IDX(&m, i, j, k)]);
+                mean = (r.s + r.c) / m.nx;
+            }
+            double V = 1.0 / inv_vol(&m, j, k);
+            nsum tq = {0, 0};
+            for (int i = 0; i < m.nx; i++) {
+                double x = p->xmin + (i + 0.5) * m.dx;
+                double X, Y, Z;
+                if (p->geom == OR_CYL) {
+                    double r = m.ym[j];
+                    X = r * cos(x); Y = r * sin(x); Z = m.zm[k];
+                } else if (p->geom == OR_SPH) {
+                    double r = m.ym[j], sn = sin(m.zm[k]);
+                    X = r * sn * cos(x); Y = r * sn * sin(x); Z = r * cos(m.zm[k]);
+                } else {
+                    X = x; Y = m.ym[j]; Z = m.zm[k];
+                }
+                double mc = (st->rho[IDX(&m, i, j, k)] - mean) * V;
+                double dx = X - rp[0], dy = Y - rp[1], dz = Z - rp[2];
+                double d2 = dx * dx + dy * dy + dz * dz + eps * eps;
+                double w = mc / (d2 * sqrt(d2));
+                nsum_add(&tq, rp[0] * (w * dy) - rp[1] * (w * dx));
+            }
+            ring[(size_t)(k - m.k0) * ny + (j - m.j0)] = tq.s + tq.c;
+        }
+    mesh_free(&m);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Frame change, Sec. 3.2, Eq. 13: when the frame's rotation rate changes   */
 /* from Omega_f to Omega_f', every azimuthal velocity becomes               */

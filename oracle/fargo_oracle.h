@@ -75,6 +75,11 @@ void or_geometry(const or_params *p, double *sx, double *sy, double *sz, double 
 /* Force of the active cells' gas on a planet at rp (per unit planet mass),
  * Plummer softening eps; bm08 = 1 subtracts each ring's mean density first.
  * out = (a_x, a_y, a_z, specific torque z). */
+/* The specific torque of each active ring on the planet (the torque
+ * diagnostic's radial profile): ring[(k - k0) * ny + (j - j0)], summing to
+ * or_planet_force's out[3]. */
+void or_planet_torque_profile(const or_params *p, const or_state *st, const double rp[3], double eps, int bm08,
+                              double *ring);
 void or_planet_force(const or_params *p, const or_state *st, const double rp[3], double eps, int bm08,
                      double out[4]);
 

@@ -29,7 +29,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
             "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_set_planet_source", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_set_planet_source", "fargo_planet_torque_profile", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -98,6 +98,7 @@ def lib():
         L.fargo_planets_advance_async.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int]
         L.fargo_change_frame.argtypes = [vp, C.c_double]
         L.fargo_set_planet_source.argtypes = [vp, vp]
+        L.fargo_planet_torque_profile.argtypes = [vp, PD, C.c_double, C.c_int, vp, PD]
         L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
         L.fargo_get_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
         L.fargo_set_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
@@ -257,6 +258,17 @@ class Fargo:
         out = (C.c_double * 4)()
         _check(lib().fargo_planet_force(self.h, r, float(eps), int(bool(bm08)), out), "fargo_planet_force")
         return tuple(out)
+
+    def planet_torque_profile(self, rp, eps, bm08=False):
+        """fargo_planet_torque_profile: each active ring's share of the
+        specific torque, shape (nz, ny), and the call's (a_x, a_y, a_z,
+        torque)."""
+        r = (C.c_double * 3)(*[float(v) for v in rp])
+        ring = np.empty((self.w.nz, self.w.ny), dtype=np.float64)
+        out = (C.c_double * 4)()
+        _check(lib().fargo_planet_torque_profile(self.h, r, float(eps), int(bool(bm08)), ring.ctypes.data, out),
+               "fargo_planet_torque_profile")
+        return ring, tuple(out)
 
     def planet_force_async(self, rp, eps, out_ptr, bm08=False):
         """fargo_planet_force_async: queue the force on the context's stream,

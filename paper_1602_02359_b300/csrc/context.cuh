@@ -70,6 +70,7 @@ struct fargo_ctx {
     double *v0 = nullptr, *part = nullptr, *part2 = nullptr, *sums = nullptr, *vol = nullptr;
     double *pf = nullptr;   // planet force: result (4), then the azimuth and ring tables of one call
     double *pacc = nullptr; // planetary step: gas accelerations of up to kNbMax planets and of the star (4 each)
+    double *pprof = nullptr; // torque profile: each active ring's planet-frame y force
     double star_mass = 0.0;
     int batch_refs = 0;     // batches holding this context (their plans snapshot its frame)
     float *ringmax = nullptr;

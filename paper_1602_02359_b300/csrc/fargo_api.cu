@@ -583,6 +583,8 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     c->pf = (double *)p;
     if ((rc = dalloc(c, &p, sizeof(double) * 4 * (kNbMax + 1)))) goto fail;
     c->pacc = (double *)p;
+    if ((rc = dalloc(c, &p, sizeof(double) * (size_t)c->nrings_active))) goto fail;
+    c->pprof = (double *)p;
     if ((rc = upload<double>(c, (const double **)&c->vol, c->hg.vol))) goto fail;
     if (c->prec == FARGO_F64) {
         if ((rc = alloc_fields<double>(c, c->b64))) goto fail;
@@ -866,7 +868,8 @@ extern "C" int fargo_sums_noalloc(const void *rho, const void *e, const void *vx
 // Force of the gas on a planet (kernels_planet.cuh).
 // ---------------------------------------------------------------------------
 template <typename T>
-static int pforce_impl(fargo_ctx *c, Buffers<T> &b, PfPlanet pl, double eps, int bm08, double *out)
+static int pforce_impl(fargo_ctx *c, Buffers<T> &b, PfPlanet pl, double eps, int bm08, double *out,
+                       double *ring_fy = nullptr)
 {
     const MeshD &m = c->m;
     cudaStream_t s = c->stream;
@@ -889,7 +892,12 @@ static int pforce_impl(fargo_ctx *c, Buffers<T> &b, PfPlanet pl, double eps, int
     a.sk = m.sk;
     // one resident wave; part2 holds 3 partials for up to 2 * sum_blocks blocks
     const int grid = std::min(148 * pforce_blocks_per_sm<T>(), 2 * c->sum_blocks);
-    if (bm08)
+    a.ring_fy = ring_fy;
+    if (ring_fy && bm08)
+        k_planet_force<T, true, true><<<grid, 256, 0, s>>>(a, c->part2, &c->sc->counter2, out);
+    else if (ring_fy)
+        k_planet_force<T, false, true><<<grid, 256, 0, s>>>(a, c->part2, &c->sc->counter2, out);
+    else if (bm08)
         k_planet_force<T, true><<<grid, 256, 0, s>>>(a, c->part2, &c->sc->counter2, out);
     else
         k_planet_force<T, false><<<grid, 256, 0, s>>>(a, c->part2, &c->sc->counter2, out);
@@ -929,6 +937,27 @@ extern "C" int fargo_planet_force(fargo_ctx *c, const double rp[3], double eps, 
     if ((rc = pforce_any(c, PfPlanet{rp[0], rp[1], rp[2], nullptr}, eps, bm08, c->pf))) return rc;
     CK(cudaMemcpyAsync(out, c->pf, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_planet_torque_profile(fargo_ctx *c, const double rp[3], double eps, int bm08, double *ring,
+                                           double out[4])
+{
+    int rc = pforce_check(c, rp, eps, ring);
+    if (rc) return rc;
+    rc = c->prec == FARGO_F64
+             ? pforce_impl<double>(c, c->b64, PfPlanet{rp[0], rp[1], rp[2], nullptr}, eps, bm08, c->pf, c->pprof)
+             : pforce_impl<float>(c, c->b32, PfPlanet{rp[0], rp[1], rp[2], nullptr}, eps, bm08, c->pf, c->pprof);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ring, c->pprof, sizeof(double) * (size_t)c->nrings_active, cudaMemcpyDeviceToHost,
+                       c->stream));
+    double tot[4];
+    CK(cudaMemcpyAsync(tot, c->pf, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double Rp = sqrt(rp[0] * rp[0] + rp[1] * rp[1]);
+    for (int r = 0; r < c->nrings_active; r++) ring[r] *= Rp;
+    if (out)
+        for (int q = 0; q < 4; q++) out[q] = tot[q];
     return FARGO_OK;
 }
 

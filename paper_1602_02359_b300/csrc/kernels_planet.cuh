@@ -51,6 +51,7 @@ struct PForceArgs {
                                     // then per active ring R, R - R_p, Z - z_p, V
     PfPlanet pl;                    // the planet's position
     T eps2;                         // squared softening
+    double *ring_fy;                // with the profile option: each active ring's planet-frame y force
     int nx, j0, j1, k0, k1, nyt, sj, sk;
 };
 
@@ -137,7 +138,7 @@ constexpr int pforce_blocks_per_sm()
 {
     return sizeof(T) == 4 ? 3 : 2;
 }
-template <typename T, bool BM08>
+template <typename T, bool BM08, bool PROF = false>
 __global__ void __launch_bounds__(256, pforce_blocks_per_sm<T>()) k_planet_force(PForceArgs<T> a, double *part, unsigned *counter, double *out)
 {
     constexpr int W = Pack<T>::W;
@@ -203,6 +204,11 @@ __global__ void __launch_bounds__(256, pforce_blocks_per_sm<T>()) k_planet_force
         for (int i = itail + lane; i < a.nx; i += 32)
             pforce_cell((BM08 ? sub_split(row[i], mu_hi, mu_lo) : row[i]) * V, s2t[i], snt[i], R, dR, dZ, a.eps2,
                         tx, ty, tz);
+        if (PROF) {   // the ring's share of the planet-frame y force, summed over lanes in FP64
+            double ry = (double)ty;
+            for (int o = 16; o > 0; o >>= 1) ry += __shfl_xor_sync(0xffffffffu, ry, o);
+            if (lane == 0) a.ring_fy[r] = ry;
+        }
         csum_add(sx, cx, tx);
         csum_add(sy, cy, ty);
         csum_add(sz, cz, tz);

@@ -143,3 +143,31 @@ def test_planet_force_async_equals_the_synchronous_call():
     with pytest.raises(fb.FargoError):
         c.planet_force_async((0.7, 0.75, 0.0), 0.03, res.data_ptr() + 4)
     c.close()
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec_name", ["F64", "F32"])
+def test_torque_profile_matches_oracle(name, make, prec_name):
+    """fargo_planet_torque_profile: each ring's share against the oracle's
+    (relative to the largest share: FP64 1e-11, FP32 2e-5 against the
+    oracle fed the FP32-rounded density), and the shares summing to the
+    call's total torque."""
+    import paper_1602_02359_b300 as fb
+    w = make()
+    prec = getattr(fb, prec_name)
+    c = make_ctx(w, prec)
+    st = dict(w.state)
+    if prec_name == "F32":
+        st["rho"] = w.state["rho"].astype(np.float32).astype(np.float64)
+    o = oracle.Oracle(w)
+    tol = 1e-11 if prec_name == "F64" else 2e-5
+    for bm08 in (False, True):
+        rp = (0.7, 0.75, 0.0)
+        g, tot = c.planet_torque_profile(rp, 0.03, bm08)
+        f = o.planet_torque_profile(st, rp, 0.03, bm08)
+        scale = np.max(np.abs(f))
+        e = np.max(np.abs(g - f)) / scale
+        record(f"torque_profile_{name}_{prec_name}", bm08=bm08, rel=e)
+        assert e < tol, e
+        assert abs(g.sum() - tot[3]) <= 1e-6 * np.abs(g).sum()
+    c.close()

@@ -769,3 +769,25 @@ def test_planet_force_turns_with_the_disk():
     c, s = math.cos(dphi), math.sin(dphi)
     assert np.allclose(f1[:2], [c * f0[0] - s * f0[1], s * f0[0] + c * f0[1]], rtol=1e-11, atol=1e-15)
     assert abs(f1[3] - f0[3]) <= 1e-11 * (abs(f0[0]) + abs(f0[1]))
+
+
+def test_torque_profile_sums_to_the_torque_and_places_it_by_ring():
+    """The torque diagnostic's radial profile: the rings' shares sum to the
+    total torque; with BM08 on a disk that is axisymmetric but for one
+    lumpy ring, that ring alone carries torque (the axisymmetric rings
+    exert none), at its own index."""
+    w = W.disk2d(nx=120, ny=30, q=1e-3)
+    st = w.copy().state
+    rng = np.random.default_rng(3)
+    jl = w.gy + 11
+    st["rho"][0, jl, :] *= 1.0 + 0.2 * rng.uniform(-1, 1, size=w.nx)
+    o = oracle.Oracle(w)
+    rp = (0.9, 0.4, 0.0)
+    for bm08 in (False, True):
+        prof = o.planet_torque_profile(st, rp, 0.03, bm08)
+        tot = o.planet_force(st, rp, 0.03, bm08)[3]
+        assert abs(prof.sum() - tot) <= 1e-12 * np.abs(prof).sum()
+    prof = o.planet_torque_profile(st, rp, 0.03, True)
+    assert prof[0, 11] != 0.0
+    others = np.delete(prof[0], 11)
+    assert np.max(np.abs(others)) <= 1e-12 * abs(prof[0, 11])
