@@ -218,19 +218,25 @@ int fargo_nbody_rk5_async(int n, double *y, const double *mass, double mstar, do
 int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *mass, double eps, int bm08,
                                 int indirect);
 
-/* Where the step's planet is (Sec. 3.7, cell 5a feeding cell 5): pos, when
- * not NULL, is a device address holding the planet's (x, y, z), read at the
- * start of every later step (the potential's azimuth and per-ring tables are
- * rebuilt from it on the device, the z part of the indirect term included),
- * for example planet 0's row of the state that fargo_planets_advance_async
- * updates, so that integrator and step alternate on the stream with no host
- * round trip.  The planet's mass stays the one given at creation.  NULL
- * returns to the fixed circular orbit (synchronises).  Requires a planet, a
- * cylindrical or spherical mesh and a non-rotating frame (the integrator's
- * coordinates are the mesh's); pos 8-byte aligned, owned by the caller and
- * valid while set.  Errors: BADARG (no planet, Cartesian mesh, Omega_f != 0,
- * context held by a batch, misaligned pos), CUDA. */
-int fargo_set_planet_source(fargo_ctx *ctx, const double *pos);
+/* Where the step's planets are (Sec. 3.7: the planets interact with the gas;
+ * cell 5a feeding cell 5).  pos, when not NULL, is a device address: planet
+ * p's (x, y, z) at pos + p * stride (stride >= 3 doubles, 6 for the state
+ * rows of fargo_nbody_rk5_async), p < n <= FARGO_MAX_POT_PLANETS, read at
+ * the start of every later step.  The potential then sums the n planets'
+ * softened potentials (the context's softening) and indirect terms, each
+ * planet's azimuth and per-ring tables rebuilt on the device, the indirect
+ * term's z part included; mass (device, n values) gives their masses, and
+ * may be NULL only for n = 1 (the planet of creation's mass).  So the
+ * integrator (fargo_planets_advance_async on the same rows) and the step
+ * alternate on the stream with no host round trip.  NULL pos returns to
+ * the fixed circular orbit.  Requires a planet at creation, a cylindrical or
+ * spherical mesh and a non-rotating frame (the integrator's coordinates are
+ * the mesh's); pos and mass 8-byte aligned, owned by the caller and valid
+ * while set.  Errors: BADARG (no planet, Cartesian mesh, Omega_f != 0,
+ * context held by a batch, n < 1, stride < 3, n > 1 without masses,
+ * misaligned pointer), SIZE (n > FARGO_MAX_POT_PLANETS). */
+#define FARGO_MAX_POT_PLANETS 8
+int fargo_set_planet_source(fargo_ctx *ctx, const double *pos, int n, int stride, const double *mass);
 
 /* Change the frame's rotation rate to omega_new at the current time (Sec.
  * 3.2, Eq. 13): every azimuthal velocity, ghosts included, becomes

@@ -33,7 +33,7 @@ class OrParams(C.Structure):
                 ("star_mass", C.c_double), ("planet_q", C.c_double), ("planet_a", C.c_double),
                 ("planet_eps", C.c_double), ("indirect", C.c_int), ("planet_phase0", C.c_double),
                 ("shearing", C.c_int), ("oort_a", C.c_double), ("planet_live", C.c_int),
-                ("planet_pos", C.c_double * 3)]
+                ("planet_pos", C.c_double * 24), ("planet_mass", C.c_double * 8)]
 
 
 class OrState(C.Structure):
@@ -143,15 +143,22 @@ class Oracle:
             n += 1
         return t, n
 
-    def set_planet_position(self, pos):
-        """The planet at pos (x, y, z) for the following steps (an integrated
-        planet); None returns to the circular orbit."""
+    def set_planet_position(self, pos, mass=None):
+        """The planets at pos (one (x, y, z) or several rows) with masses
+        `mass` (default: the planet of the workload's mass, one planet) for
+        the following steps (integrated planets); None returns to the
+        circular orbit."""
         if pos is None:
             self.p.planet_live = 0
-        else:
-            self.p.planet_live = 1
+            return
+        pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+        mass = [self.w.planet_q] if mass is None else list(mass)
+        assert len(pos) == len(mass) <= 8
+        self.p.planet_live = len(pos)
+        for n in range(len(pos)):
             for q in range(3):
-                self.p.planet_pos[q] = float(pos[q])
+                self.p.planet_pos[3 * n + q] = float(pos[n, q])
+            self.p.planet_mass[n] = float(mass[n])
 
     def change_frame(self, st, omega_new, t):
         """Frame change at time t to the rate omega_new (Eq. 13), in place."""

@@ -425,11 +425,19 @@ void or_potential(const or_params *p, double t, double *phi)
     double M = p->star_mass, q = p->planet_q, a = p->planet_a;
     double om = q > 0.0 ? sqrt((M + q) / (a * a * a)) : 0.0;
     double ph = p->planet_phase0 + (om - p->omega_f) * t;
-    double xp = a * cos(ph), yp = a * sin(ph), zp = 0.0, rp3 = a * a * a;
-    if (p->planet_live) {
-        xp = p->planet_pos[0]; yp = p->planet_pos[1]; zp = p->planet_pos[2];
-        double r2 = xp * xp + yp * yp + zp * zp;
-        rp3 = r2 * sqrt(r2);
+    /* the planets: one on the circular orbit, or the integrated ones */
+    int np = p->planet_live > 0 ? p->planet_live : 1;
+    double xs[8], ys[8], zs[8], qs[8], r3s[8];
+    for (int n = 0; n < np; n++) {
+        if (p->planet_live > 0) {
+            xs[n] = p->planet_pos[n][0]; ys[n] = p->planet_pos[n][1]; zs[n] = p->planet_pos[n][2];
+            qs[n] = p->planet_mass[n];
+        } else {
+            xs[n] = a * cos(ph); ys[n] = a * sin(ph); zs[n] = 0.0;
+            qs[n] = q;
+        }
+        double r2 = xs[n] * xs[n] + ys[n] * ys[n] + zs[n] * zs[n];
+        r3s[n] = p->planet_live > 0 ? r2 * sqrt(r2) : a * a * a;
     }
     for (int k = 0; k < m.nzt; k++)
         for (int j = 0; j < m.nyt; j++)
@@ -450,11 +458,13 @@ void or_potential(const or_params *p, double t, double *phi)
                 }
                 double v = 0.0;
                 if (M > 0.0 && p->geom != OR_CART) v -= M / rs;
-                if (q > 0.0) {
-                    double d2 = (X - xp) * (X - xp) + (Y - yp) * (Y - yp) + (Z - zp) * (Z - zp);
-                    v -= q / sqrt(d2 + p->planet_eps * p->planet_eps);
-                    if (p->indirect) v += q * (X * xp + Y * yp + Z * zp) / rp3;
-                }
+                if (q > 0.0)
+                    for (int n = 0; n < np; n++) {
+                        double dx = X - xs[n], dy = Y - ys[n], dz = Z - zs[n];
+                        double d2 = dx * dx + dy * dy + dz * dz;
+                        v -= qs[n] / sqrt(d2 + p->planet_eps * p->planet_eps);
+                        if (p->indirect) v += qs[n] * (X * xs[n] + Y * ys[n] + Z * zs[n]) / r3s[n];
+                    }
                 phi[IDX(&m, i, j, k)] = v;
             }
     mesh_free(&m);

@@ -38,8 +38,9 @@ typedef struct {
     double planet_phase0;       /* planet azimuth at t = 0 in the current frame (moved by frame changes) */
     int shearing;               /* Cartesian shearing sheet (Sec. 2): X along the shear flow, Y across it */
     double oort_a;              /* its shear rate A (the unperturbed flow is v_x = 2 A y) */
-    int planet_live;            /* 1: the planet sits at planet_pos (an integrated planet) */
-    double planet_pos[3];       /* its position (x, y, z) when planet_live */
+    int planet_live;            /* n > 0: n integrated planets at planet_pos, masses planet_mass */
+    double planet_pos[8][3];    /* their positions (x, y, z) */
+    double planet_mass[8];      /* their masses */
 } or_params;
 
 typedef struct { double *rho, *e, *vx, *vy, *vz; } or_state;

@@ -97,7 +97,7 @@ def lib():
                                             vp]
         L.fargo_planets_advance_async.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int]
         L.fargo_change_frame.argtypes = [vp, C.c_double]
-        L.fargo_set_planet_source.argtypes = [vp, vp]
+        L.fargo_set_planet_source.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.fargo_planet_torque_profile.argtypes = [vp, PD, C.c_double, C.c_int, vp, PD]
         L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
         L.fargo_get_aux.argtypes = [vp, C.c_int, vp, C.c_size_t]
@@ -277,10 +277,13 @@ class Fargo:
         _check(lib().fargo_planet_force_async(self.h, r, float(eps), int(bool(bm08)), C.c_void_p(out_ptr)),
                "fargo_planet_force_async")
 
-    def set_planet_source(self, pos_ptr):
-        """fargo_set_planet_source: read the step's planet position from the
-        device address pos_ptr each step (None: the fixed circular orbit)."""
-        _check(lib().fargo_set_planet_source(self.h, C.c_void_p(pos_ptr) if pos_ptr else None),
+    def set_planet_source(self, pos_ptr, n=1, stride=3, mass_ptr=None):
+        """fargo_set_planet_source: read the step's n planets' positions from
+        the device address pos_ptr (rows of `stride` doubles) each step, with
+        masses at mass_ptr (None for n = 1: the planet of creation's mass);
+        pos_ptr None: the fixed circular orbit."""
+        _check(lib().fargo_set_planet_source(self.h, C.c_void_p(pos_ptr) if pos_ptr else None, int(n),
+                                             int(stride), C.c_void_p(mass_ptr) if mass_ptr else None),
                "fargo_set_planet_source")
 
     def change_frame(self, omega_new):

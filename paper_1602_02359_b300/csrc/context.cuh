@@ -32,7 +32,6 @@ struct HostGeom {
     std::vector<double> sx, vinv, sy, sz, lenz, gphy, gphz, cosx, sinx, cs, nu;
     std::vector<double> rma, fra, z2, qar;
     std::vector<double> wfr, tid;   // frame term of the X momentum per ring; shearing-sheet tide per Y face
-    std::vector<double> zq;         // z part of a live planet's indirect term per ring (zero until set)
 };
 
 // Everything one step of one instance needs on the device: the mesh, its

@@ -124,7 +124,7 @@ static void build_geometry(fargo_ctx *c, const fargo_params *p, double gamma, co
     h.vinv.assign(nr, 0); h.lenz.assign(nr, 0); h.gphy.assign(nr, 0); h.gphz.assign(nr, 0);
     h.cs.assign(nr, 0); h.nu.assign(nr, 0);
     h.rma.assign(nr, 0); h.fra.assign(nr, 0); h.z2.assign(nr, 0); h.qar.assign(nr, 0);
-    h.wfr.assign(nr, 0); h.tid.assign(nyt + 1, 0); h.zq.assign(nr, 0);
+    h.wfr.assign(nr, 0); h.tid.assign(nyt + 1, 0);
     if (p->shearing)   // the shearing sheet's tide per Y face, 4 A Omega_f y (subtracted)
         for (int j = 0; j <= nyt; j++) h.tid[j] = 4.0 * p->oort_a * p->omega_frame * yf[j];
     h.sy.assign(nf, 0); h.sz.assign(nf, 0);
@@ -240,15 +240,10 @@ static int build_tables(fargo_ctx *c, Tab<T> &t)
     UP(R, h.R); UP(lenx, h.lx); UP(lenz, h.lenz); UP(dzc, h.dzc); UP(sx, h.sx); UP(vinv, h.vinv);
     UP(cs, h.cs); UP(nu, h.nu); UP(gphy, h.gphy); UP(gphz, h.gphz); UP(fz, h.fz);
     UP(sy, h.sy); UP(sz, h.sz);
-    UP(wfr, h.wfr); UP(tid, h.tid); UPD(wfrd, h.wfr); UP(zq, h.zq);
-    t.pw[4] = const_cast<T *>(t.zq);
+    UP(wfr, h.wfr); UP(tid, h.tid); UPD(wfrd, h.wfr);
     UPD(lx, h.lx); UPD(ly, h.ly); UPD(lz, h.lz); UPD(dmin, h.dmin); UPD(csd, h.cs); UPD(nud, h.nu);
     UPD(Rd, h.R); UPD(zcd, h.zc); UPD(cosx, h.cosx); UPD(sinx, h.sinx);
     UP(rma, h.rma); UP(fra, h.fra); UP(z2, h.z2); UP(qar, h.qar);
-    t.pw[0] = const_cast<T *>(t.rma);
-    t.pw[1] = const_cast<T *>(t.fra);
-    t.pw[2] = const_cast<T *>(t.z2);
-    t.pw[3] = const_cast<T *>(t.qar);
     {
         const MeshD &m = c->m;
         t.gm1 = (T)(m.gamma - 1.0);
@@ -291,11 +286,18 @@ static int build_tables(fargo_ctx *c, Tab<T> &t)
         t.idx = (T)(1.0 / c->m.dx);
     }
     {
+        // azimuth tables of up to kPotPlanets planets (planet p at p * nx),
+        // and the live planets' per-ring tables and masses
+        const int np = c->m.has_planet ? kPotPlanets : 1;
         void *q;
-        if ((rc = dalloc(c, &q, sizeof(T) * c->nx))) return rc;
+        if ((rc = dalloc(c, &q, sizeof(T) * (size_t)np * c->nx))) return rc;
         t.ps = (T *)q;
-        if ((rc = dalloc(c, &q, sizeof(T) * c->nx))) return rc;
+        if ((rc = dalloc(c, &q, sizeof(T) * (size_t)np * c->nx))) return rc;
         t.pc = (T *)q;
+        if ((rc = dalloc(c, &q, sizeof(T) * (size_t)np * 5 * nyt * nzt))) return rc;
+        t.mring = (T *)q;
+        if ((rc = dalloc(c, &q, sizeof(T) * kPotPlanets))) return rc;
+        t.mq = (T *)q;
     }
 #undef UP
 #undef UPD
@@ -1080,34 +1082,16 @@ extern "C" int fargo_change_frame(fargo_ctx *c, double omega_new)
                                 : change_frame_impl<float>(c, c->b32, omega_new);
 }
 
-// The circular orbit's per-ring planet tables back from the host copies
-// (after a live planet rewrote them), and a zero z part of the indirect term.
-template <typename T>
-static int restore_planet_tables(fargo_ctx *c, Buffers<T> &b)
-{
-    const HostGeom &h = c->hg;
-    const std::vector<double> *src[4] = {&h.rma, &h.fra, &h.z2, &h.qar};
-    for (int q = 0; q < 4; q++) {
-        std::vector<T> v(src[q]->size());
-        for (size_t i = 0; i < v.size(); i++) v[i] = (T)(*src[q])[i];
-        CK(cudaMemcpyAsync(b.tab.pw[q], v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-    }
-    CK(cudaMemsetAsync(b.tab.pw[4], 0, h.zq.size() * sizeof(T), c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return FARGO_OK;
-}
-
-extern "C" int fargo_set_planet_source(fargo_ctx *c, const double *pos)
+extern "C" int fargo_set_planet_source(fargo_ctx *c, const double *pos, int n, int stride, const double *mass)
 {
     if (!c || !c->m.has_planet || c->geom == FARGO_CART) return FARGO_ERR_BADARG;
-    if (c->m.omega != 0.0 || c->batch_refs > 0 || !aligned8(pos)) return FARGO_ERR_BADARG;
-    if (!pos && c->m.pl_pos) {
-        const int rc = c->prec == FARGO_F64 ? restore_planet_tables<double>(c, c->b64)
-                                            : restore_planet_tables<float>(c, c->b32);
-        if (rc) return rc;
-    }
+    if (c->m.omega != 0.0 || c->batch_refs > 0 || !aligned8(pos) || !aligned8(mass)) return FARGO_ERR_BADARG;
+    if (pos && (n < 1 || stride < 3 || (n > 1 && !mass))) return FARGO_ERR_BADARG;
+    if (pos && n > kPotPlanets) return FARGO_ERR_SIZE;
     c->m.pl_pos = pos;
+    c->m.pl_n = pos ? n : 0;
+    c->m.pl_stride = pos ? stride : 0;
+    c->m.pl_mass = pos ? mass : nullptr;
     if (c->gexec) {   // the captured step holds the old mesh record
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;

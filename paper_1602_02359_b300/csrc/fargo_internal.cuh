@@ -18,7 +18,10 @@ struct MeshD {
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
     double php0;                 // planet azimuth at t = 0 in the current frame (moved by frame changes)
     int shearing;                // Cartesian shearing sheet
-    const double *pl_pos;        // planet position read on the device each step (x, y, z), or null
+    const double *pl_pos;        // planets' positions read on the device each step (x, y, z at pl_pos +
+                                 // p * pl_stride), or null for the fixed circular orbit
+    const double *pl_mass;       // their masses (device), or null: the planet of creation's q
+    int pl_n, pl_stride;
 };
 
 // Geometry tables (Appendix A) in the field precision T, plus the FP64
@@ -42,11 +45,11 @@ struct Tab {
     // cos(dphi) of the offset to the planet
     const T *rma, *fra, *z2, *qar;
     T *ps, *pc;
-    // a planet whose position is read each step (pl_pos): the per-ring
-    // tables above rewritten at the step's start, and the z part of the
-    // indirect term, q Z z_p / |r_p|^3, per ring (writable aliases)
-    const T *zq;
-    T *pw[5];
+    // planets whose positions are read each step (pl_pos), rebuilt at the
+    // step's start: per planet p, five per-ring tables at mring + (5 p + t) *
+    // nyt * nzt (R - a_p, 4 R a_p, (Z - z_p)^2, q_p R a_p / |r_p|^3 and
+    // q_p Z z_p / |r_p|^3), its azimuth tables at ps / pc + p * nx, its mass
+    T *mring, *mq;
     // run constants in the field precision (no FP64 work in FP32 kernels)
     T gm1, cq2, omega, pq, peps2, dx, half_gm1, g1, k4;
     // Courant screening: 4 nu / dmin^2 and dmin per ring
@@ -90,6 +93,10 @@ struct Scal {
 // azimuth and the radius present, a planet with the indirect term, the
 // star, artificial viscosity), which turns those uniform branches into
 // straight-line code.  cfg_of picks the class a mesh runs with.
+// Planets that a step's potential can feel when their positions are read on
+// the device (fargo_set_planet_source).
+constexpr int kPotPlanets = 8;
+
 struct CfgRun {
     __host__ __device__ static int geom(const MeshD &m) { return m.geom; }
     __host__ __device__ static bool hasX(const MeshD &m) { return m.hasX; }

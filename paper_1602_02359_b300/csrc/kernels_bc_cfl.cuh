@@ -181,34 +181,42 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
     const int r = bid * 8 + warp;
     const bool skip = cfl_skip(sc);
     // planet tables for this step (time t^n): the planet on its circular
-    // orbit, or read from pl_pos (a planet integrated on the device), when
-    // the per-ring tables are rewritten too
+    // orbit, or the planets read from pl_pos (integrated on the device), each
+    // with its azimuth and per-ring tables
     if (m.has_planet) {
-        double php = m.php0 + m.om_rel * sc->t, ap = 0.0, zp = 0.0, irp3 = 0.0;
-        if (m.pl_pos) {
-            const double px = m.pl_pos[0], py = m.pl_pos[1];
-            zp = m.pl_pos[2];
-            ap = sqrt(px * px + py * py);
-            php = ap > 0.0 ? atan2(py, px) : 0.0;
-            const double r2 = ap * ap + zp * zp;
-            irp3 = 1.0 / (r2 * sqrt(r2));
-        }
         const int gt = bid * blockDim.x + threadIdx.x, gs = nblk * blockDim.x;
-        for (int i = gt; i < m.nx; i += gs) {
-            const double dphi = (m.xmin + (i + 0.5) * m.dx) - php;
-            const double sh = sin(0.5 * dphi);
-            tb.ps[i] = (T)(sh * sh);
-            tb.pc[i] = (T)cos(dphi);
-        }
-        if (m.pl_pos)
-            for (int r = gt; r < m.nyt * m.nzt; r += gs) {
-                const double R = tb.Rd[r], Z = tb.zcd[r], dz = Z - zp;
-                tb.pw[0][r] = (T)(R - ap);
-                tb.pw[1][r] = (T)(4.0 * R * ap);
-                tb.pw[2][r] = (T)(dz * dz);
-                tb.pw[3][r] = (T)(m.pq * R * ap * irp3);
-                tb.pw[4][r] = (T)(m.pq * Z * zp * irp3);
+        const int np = m.pl_pos ? m.pl_n : 1, NR = m.nyt * m.nzt;
+        for (int p = 0; p < np; p++) {
+            double php = m.php0 + m.om_rel * sc->t, ap = 0.0, zp = 0.0, irp3 = 0.0, qp = m.pq;
+            if (m.pl_pos) {
+                const double *pos = m.pl_pos + (size_t)p * m.pl_stride;
+                const double px = pos[0], py = pos[1];
+                zp = pos[2];
+                ap = sqrt(px * px + py * py);
+                php = ap > 0.0 ? atan2(py, px) : 0.0;
+                const double r2 = ap * ap + zp * zp;
+                irp3 = 1.0 / (r2 * sqrt(r2));
+                if (m.pl_mass) qp = m.pl_mass[p];
+                if (gt == 0) tb.mq[p] = (T)qp;
             }
+            for (int i = gt; i < m.nx; i += gs) {
+                const double dphi = (m.xmin + (i + 0.5) * m.dx) - php;
+                const double sh = sin(0.5 * dphi);
+                tb.ps[p * m.nx + i] = (T)(sh * sh);
+                tb.pc[p * m.nx + i] = (T)cos(dphi);
+            }
+            if (m.pl_pos) {
+                T *tp = tb.mring + (size_t)p * 5 * NR;
+                for (int r = gt; r < NR; r += gs) {
+                    const double R = tb.Rd[r], Z = tb.zcd[r], dz = Z - zp;
+                    tp[r] = (T)(R - ap);
+                    tp[NR + r] = (T)(4.0 * R * ap);
+                    tp[2 * NR + r] = (T)(dz * dz);
+                    tp[3 * NR + r] = (T)(qp * R * ap * irp3);
+                    tp[4 * NR + r] = (T)(qp * Z * zp * irp3);
+                }
+            }
+        }
     }
     float smax = 0.0f;
     int bad = 0;

@@ -41,15 +41,26 @@ __device__ __forceinline__ T pressure(const MeshD &m, const Tab<T> &tb, const Fl
 template <typename T, class F = CfgRun>
 __device__ __forceinline__ T phi_planet(const MeshD &m, const Tab<T> &tb, int i, int ring)
 {
+    if (F::live(m)) {   // planets read on the device, each with its own tables
+        const int NR = m.nyt * m.nzt;
+        T v = T(0);
+        for (int p = 0; p < m.pl_n; p++) {
+            const T *tp = tb.mring + (size_t)p * 5 * NR;
+            const T rm = tp[ring];
+            const T d2 = rm * rm + tp[NR + ring] * tb.ps[p * m.nx + i] + tp[2 * NR + ring] + tb.peps2;
+            const T qp = tb.mq[p];
+            if (sizeof(T) == 8) v -= qp / sqrt(d2);
+            else v -= qp * rsqrtf((float)d2);
+            if (F::indirect(m)) v += tp[3 * NR + ring] * tb.pc[p * m.nx + i] + tp[4 * NR + ring];
+        }
+        return v;
+    }
     const T rm = tb.rma[ring];
     const T d2 = rm * rm + tb.fra[ring] * tb.ps[i] + tb.z2[ring] + tb.peps2;
     T v;
     if (sizeof(T) == 8) v = -tb.pq / sqrt(d2);
     else v = -tb.pq * rsqrtf((float)d2);
-    if (F::indirect(m)) {
-        v += tb.qar[ring] * tb.pc[i];
-        if (F::live(m)) v += tb.zq[ring];
-    }
+    if (F::indirect(m)) v += tb.qar[ring] * tb.pc[i];
     return v;
 }
 

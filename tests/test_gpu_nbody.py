@@ -169,6 +169,39 @@ def test_planet_coupled_to_the_step_matches_oracle():
     c.close()
 
 
+def test_two_planets_in_the_potential_coupled_to_the_step_match_oracle():
+    """Both integrated planets drive the step's potential (n = 2, masses on
+    the device): four coupled rounds against the oracle's loop."""
+    import torch
+    w = lumpy_disk(14)
+    eps = w.planet_eps
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    c = make_ctx(w)
+    y = np.array([[1.0, 0.0, 0.0, 0.0, math.sqrt(1.0 + w.planet_q), 0.0],
+                  [1.5, 0.4, 0.0, -0.25, 0.76, 0.0]])
+    m = np.array([w.planet_q, 3e-4])
+    yd, md = dev(y), dev(m)
+    c.set_planet_source(yd.data_ptr(), 2, 6, md.data_ptr())
+    t = 0.0
+    for n in range(4):
+        dt_g = c.step()
+        c.planets_advance_async(2, yd.data_ptr(), md.data_ptr(), eps, False, True)
+        o.set_planet_position(y[:, :3], m)
+        dt_o = o.step(st, t)
+        t += dt_o
+        assert abs(dt_g - dt_o) <= 1e-12 * dt_o, (n, dt_g, dt_o)
+        acc = np.array([o.planet_force(st, tuple(y[i, :3]), eps)[:3] for i in range(2)])
+        acc -= np.array(o.planet_force(st, (0.0, 0.0, 0.0), 0.0)[:3])[None, :]
+        y = NB.nbody_step(y, m, 1.0, dt_o, kick=acc)
+    torch.cuda.synchronize()
+    compare_state(w, c.get_state(), st, 1e-11)
+    e = np.max(np.abs(yd.cpu().numpy() - y))
+    record("two_planets_coupled_vs_oracle", max_abs=e)
+    assert e < 1e-12
+    c.close()
+
+
 def test_clearing_the_planet_source_restores_the_circular_orbit():
     import paper_1602_02359_b300 as fb
     w = lumpy_disk(13)
@@ -189,5 +222,10 @@ def test_clearing_the_planet_source_restores_the_circular_orbit():
     wr = W.random_box(W.CYL, 32, 16, 1, seed=2, omega_f=0.5)
     with pytest.raises(fb.FargoError):
         make_ctx(wr).set_planet_source(pos.data_ptr())
+    with pytest.raises(fb.FargoError):   # several planets need their masses
+        a.set_planet_source(pos.data_ptr(), 2, 3)
+    big = dev(np.zeros((9, 3)))
+    with pytest.raises(fb.FargoError):   # beyond FARGO_MAX_POT_PLANETS
+        a.set_planet_source(big.data_ptr(), 9, 3, dev(np.ones(9)).data_ptr())
     a.close()
     b.close()

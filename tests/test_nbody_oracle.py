@@ -150,3 +150,24 @@ def test_integrated_planet_on_the_circular_orbit_gives_the_same_potential():
         assert np.max(np.abs(live - ref)) <= 1e-14 * np.max(np.abs(ref))
         o.set_planet_position(None)
         assert np.array_equal(o.potential(t), ref)
+
+
+def test_potential_of_several_integrated_planets_superposes():
+    """Two integrated planets (one off the midplane) in a spherical mesh:
+    the potential is the sum of each planet's alone, less the star's,
+    which a massless planet leaves (phi_AB - phi_A - phi_B + phi_0 = 0)."""
+    import oracle
+    import workloads as W
+    w = W.random_box(W.SPH, 48, 16, 10, seed=4)
+    o = oracle.Oracle(w)
+    a, b = (0.9, 0.3, 0.02), (-0.6, 1.1, -0.05)
+    o.set_planet_position([a, b], [1e-3, 4e-4])
+    ab = o.potential(0.5)
+    o.set_planet_position([a], [1e-3])
+    pa = o.potential(0.5)
+    o.set_planet_position([b], [4e-4])
+    pb = o.potential(0.5)
+    o.set_planet_position([a], [0.0])
+    p0 = o.potential(0.5)
+    assert np.max(np.abs(ab - pa - pb + p0)) <= 1e-14 * np.max(np.abs(ab))
+    assert np.max(np.abs(pa - p0)) > 1e-6
