@@ -74,22 +74,22 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.42, "substep1": 33.41, "artvisc": 36.5, "visc_tau": 36.56, "visc_apply": 54.65, "transport_x": 56.91, "transport_y": 64.74, "transport_z": 65.81, "orbital": 58.16, "newvel": 41.69}
-KERNEL_SRC_HASH = "09066d4adb830956"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.39, "substep1": 33.43, "artvisc": 36.54, "visc_tau": 36.61, "visc_apply": 54.67, "transport_x": 56.97, "transport_y": 64.7, "transport_z": 65.9, "orbital": 58.11, "newvel": 41.68}
+KERNEL_SRC_HASH = "da9f11ebd0d1dc7d"
 
 # The same for the batched step: DRAM bytes per active cell of every batched
 # phase (all its launches of one step summed), measured on batch-medium (the
 # first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
 # whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
-TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.31, "substep1": 17.86, "artvisc": 18.01, "visc_tau": 20.66, "visc_apply": 33.38, "transport_x": 24.29, "transport_y": 42.84, "orbital": 32.26, "newvel": 27.11}
-BATCH_SRC_HASH = "ef7a256cfb7fede7"
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.59, "substep1": 17.87, "artvisc": 18.01, "visc_tau": 20.66, "visc_apply": 33.41, "transport_x": 24.29, "transport_y": 42.83, "orbital": 32.26, "newvel": 27.15}
+BATCH_SRC_HASH = "e649dfb66c44d0bd"
 
 
 # DRAM bytes per launch of the direct-sum planet force on the 3D disk (ncu,
 # full size, one pass: dram__bytes_read.sum + dram__bytes_write.sum, median of
 # four launches), valid while kernels_planet.cuh keeps PFORCE_SRC_HASH
 # (profiles/planet_force_disk3d_ncu.md).
-PFORCE_TRAFFIC_3D = 303.15e6
+PFORCE_TRAFFIC_3D = 302.91e6
 PFORCE_SRC_HASH = "17d5c57fa4766b55"
 
 # Sources of the single-instance step's kernels (the traffic table above
