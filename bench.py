@@ -723,14 +723,14 @@ def precision_study(torch, fb, orbits=8.0):
 
 def vortex_study(torch, fb, orbits=10.0, resolutions=((1024, 256), (2048, 512))):
     """Orbital advection and vortensity (Sec. 6): the vortex in a Keplerian
-    disk, FP64, with and without orbital advection, at each resolution;
-    the vortensity minimum every half orbit of the vortex, the steps taken
-    and the device time.  One JSON line."""
+    disk, with and without orbital advection, at each resolution, in FP64
+    and in the FP32 path; the vortensity minimum every half orbit of the
+    vortex, the steps taken and the device time.  One JSON line."""
     res = []
-    for nx, ny in resolutions:
+    for (nx, ny), prec in [(r, p) for r in resolutions for p in ("f64", "f32")]:
         for fargo in (True, False):
             w = W.keplerian_vortex(nx=nx, ny=ny, fargo=fargo, orbits=orbits)
-            c = fb.Fargo(w, fb.F64)
+            c = fb.Fargo(w, fb.F64 if prec == "f64" else fb.F32)
             c.set_state(w.state)
             c.set_time(0.0, w.t_end)
             hist = [[0.0, float(W.vortensity(w, w.state).min())]]
@@ -741,11 +741,11 @@ def vortex_study(torch, fb, orbits=10.0, resolutions=((1024, 256), (2048, 512)))
                     raise SystemExit(f"device error in the vortex study ({nx} x {ny}, fargo={fargo})")
                 hist.append([0.5 * k, float(W.vortensity(w, c.get_state()).min())])
             wall = time.perf_counter() - t0
-            res.append({"nx": nx, "ny": ny, "orbital_advection": fargo, "steps": c.scalars()[2],
+            res.append({"nx": nx, "ny": ny, "dtype": prec, "orbital_advection": fargo, "steps": c.scalars()[2],
                         "wall_s": round(wall, 2), "vortensity_min": hist})
             c.close()
     print(json.dumps({"metric": "vortensity_min_decay", "workload": "Keplerian vortex, M = 10, K = -1, "
-                      "h = c_s/(2 Omega), r in [0.4, 2], adiabatic, inviscid, FP64", "orbits": orbits,
+                      "h = c_s/(2 Omega), r in [0.4, 2], adiabatic, inviscid", "orbits": orbits,
                       "runs": res}))
 
 
