@@ -581,6 +581,8 @@ static int batch_enqueue(fargo_batch *b, cudaEvent_t *marks = nullptr)
         case L_CELL:
             if (x.key == CFG_DISK3D) launch_cell_cfg<T, CfgDisk3D>(x.arg, nb, P, g, s);
             else if (x.key == CFG_DISK2D) launch_cell_cfg<T, CfgDisk2D>(x.arg, nb, P, g, s);
+            else if (x.key == CFG_DISK3D_LIVE) launch_cell_cfg<T, CfgDisk3DLive>(x.arg, nb, P, g, s);
+            else if (x.key == CFG_DISK2D_LIVE) launch_cell_cfg<T, CfgDisk2DLive>(x.arg, nb, P, g, s);
             else launch_cell_cfg<T, CfgRun>(x.arg, nb, P, g, s);
             break;
         case L_TX:

@@ -110,7 +110,7 @@ struct CfgRun {
     __host__ __device__ static bool shearing(const MeshD &m) { return m.shearing; }
     __host__ __device__ static bool live(const MeshD &m) { return m.pl_pos != nullptr; }
 };
-template <int GEOM, bool Z, bool ISO>
+template <int GEOM, bool Z, bool ISO, bool LIVE = false>
 struct CfgDisk {
     __host__ __device__ static constexpr int geom(const MeshD &) { return GEOM; }
     __host__ __device__ static constexpr bool hasX(const MeshD &) { return true; }
@@ -122,11 +122,14 @@ struct CfgDisk {
     __host__ __device__ static constexpr bool star(const MeshD &) { return true; }
     __host__ __device__ static constexpr bool av(const MeshD &) { return true; }
     __host__ __device__ static constexpr bool shearing(const MeshD &) { return false; }
-    __host__ __device__ static constexpr bool live(const MeshD &) { return false; }
+    __host__ __device__ static constexpr bool live(const MeshD &) { return LIVE; }
 };
 typedef CfgDisk<SPH, true, false> CfgDisk3D;   // spherical, adiabatic
 typedef CfgDisk<CYL, false, true> CfgDisk2D;   // cylindrical, isothermal
-enum { CFG_RUN = 0, CFG_DISK3D = 1, CFG_DISK2D = 2 };
+// the same disks with their planets read on the device (fargo_set_planet_source)
+typedef CfgDisk<SPH, true, false, true> CfgDisk3DLive;
+typedef CfgDisk<CYL, false, true, true> CfgDisk2DLive;
+enum { CFG_RUN = 0, CFG_DISK3D = 1, CFG_DISK2D = 2, CFG_DISK3D_LIVE = 3, CFG_DISK2D_LIVE = 4 };
 
 template <class F>
 inline bool cfg_matches(const MeshD &m)
@@ -140,6 +143,8 @@ inline int cfg_of(const MeshD &m)
 {
     if (cfg_matches<CfgDisk3D>(m)) return CFG_DISK3D;
     if (cfg_matches<CfgDisk2D>(m)) return CFG_DISK2D;
+    if (cfg_matches<CfgDisk3DLive>(m)) return CFG_DISK3D_LIVE;
+    if (cfg_matches<CfgDisk2DLive>(m)) return CFG_DISK2D_LIVE;
     return CFG_RUN;
 }
 

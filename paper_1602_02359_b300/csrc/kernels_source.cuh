@@ -608,6 +608,8 @@ static void launch_source(int which, const MeshD &m, dim3 g, dim3 b, cudaStream_
     switch (cfg_of(m)) {
     case CFG_DISK3D: launch_source_cfg<T, CfgDisk3D>(which, m, g, b, s, tb, in, out, tau, sc); break;
     case CFG_DISK2D: launch_source_cfg<T, CfgDisk2D>(which, m, g, b, s, tb, in, out, tau, sc); break;
+    case CFG_DISK3D_LIVE: launch_source_cfg<T, CfgDisk3DLive>(which, m, g, b, s, tb, in, out, tau, sc); break;
+    case CFG_DISK2D_LIVE: launch_source_cfg<T, CfgDisk2DLive>(which, m, g, b, s, tb, in, out, tau, sc); break;
     default: launch_source_cfg<T, CfgRun>(which, m, g, b, s, tb, in, out, tau, sc); break;
     }
 }

@@ -1309,6 +1309,8 @@ static void launch_newvel(const MeshD &m, dim3 g, dim3 b, cudaStream_t s, const 
     switch (cfg_of(m)) {
     case CFG_DISK3D: k_newvel<T, CfgDisk3D><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
     case CFG_DISK2D: k_newvel<T, CfgDisk2D><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
+    case CFG_DISK3D_LIVE: k_newvel<T, CfgDisk3DLive><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
+    case CFG_DISK2D_LIVE: k_newvel<T, CfgDisk2DLive><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
     default: k_newvel<T, CfgRun><<<g, b, 0, s>>>(m, tb, fin, vsrc, state, sc, copy_scalars); break;
     }
 }
