@@ -74,15 +74,15 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.39, "substep1": 33.43, "artvisc": 36.54, "visc_tau": 36.61, "visc_apply": 54.67, "transport_x": 56.97, "transport_y": 64.7, "transport_z": 65.9, "orbital": 58.11, "newvel": 41.68}
-KERNEL_SRC_HASH = "da9f11ebd0d1dc7d"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 23.44, "substep1": 33.45, "artvisc": 36.56, "visc_tau": 36.56, "visc_apply": 54.68, "transport_x": 56.92, "transport_y": 64.73, "transport_z": 65.86, "orbital": 58.17, "newvel": 41.7}
+KERNEL_SRC_HASH = "8f494b38e6f678f7"
 
 # The same for the batched step: DRAM bytes per active cell of every batched
 # phase (all its launches of one step summed), measured on batch-medium (the
 # first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
 # whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
-TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.59, "substep1": 17.87, "artvisc": 18.01, "visc_tau": 20.66, "visc_apply": 33.41, "transport_x": 24.29, "transport_y": 42.83, "orbital": 32.26, "newvel": 27.15}
-BATCH_SRC_HASH = "e649dfb66c44d0bd"
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 15.57, "substep1": 17.87, "artvisc": 18.01, "visc_tau": 20.65, "visc_apply": 33.42, "transport_x": 24.29, "transport_y": 42.83, "orbital": 32.26, "newvel": 27.16}
+BATCH_SRC_HASH = "0c2adf3e3b5125b3"
 
 
 # DRAM bytes per launch of the direct-sum planet force on the 3D disk (ncu,
