@@ -123,7 +123,9 @@ int fargo_step(fargo_ctx *ctx, double *dt_out);
 int fargo_step_fixed(fargo_ctx *ctx, double dt);
 
 /* Advance until t = t_end (the last step lands on it) or max_steps steps,
- * polling the device time every `poll` graph launches (>= 1).
+ * polling the device time every `poll` graph launches (>= 1).  t_end
+ * becomes the context's end time: later fargo_step calls at t >= t_end are
+ * void steps (dt = 0) until fargo_set_time or another fargo_run_to moves it.
  * steps_done may be NULL.  Errors: CUDA, NONFINITE, DT. */
 int fargo_run_to(fargo_ctx *ctx, double t_end, long long max_steps, int poll, long long *steps_done);
 

@@ -236,6 +236,8 @@ class Fargo:
         _check(lib().fargo_step_fixed(self.h, dt), "fargo_step_fixed")
 
     def run_to(self, t_end, max_steps=10 ** 12, poll=64):
+        """fargo_run_to: step until t_end, which becomes the context's end
+        time (later steps are void until set_time moves it)."""
         n = C.c_longlong()
         _check(lib().fargo_run_to(self.h, t_end, max_steps, poll, C.byref(n)), "fargo_run_to")
         return n.value
