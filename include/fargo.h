@@ -272,25 +272,37 @@ int fargo_sums(fargo_ctx *ctx, double out[3]);
  * pitch of nx values, i.e. shape (nz_t+1, ny_t+1, nx) for the mesh
  * nx*ny*nz with `ghost` ghost layers; vol and R, the cell volume and the
  * azimuthal lever arm (1 Cartesian, r cylindrical, r sin(theta) spherical)
- * per ring, nz_t*ny_t FP64 values (j fastest); omega_frame as for the
- * context.  Output: out, a device pointer to 3 FP64 values, written on
- * `stream` (NULL = legacy default stream) in the order of fargo_sums.
- * The call returns once the work is queued; synchronise the stream before
- * reading out.
+ * per ring, nz_t*ny_t FP64 values (j fastest).  The X momentum carries the
+ * frame's share w per unit mass (Tab. momenta): wframe, when not NULL, gives
+ * it per ring (nz_t*ny_t FP64 values on the device); NULL means
+ * w = R^2 omega_frame, the cylindrical and spherical term.  A Cartesian
+ * caller must pass wframe to match fargo_sums: zeros for a plain box (the
+ * context adds no frame term there whatever its Omega_f), 2 Omega_f y at the
+ * cell-centre Y for the shearing sheet; with NULL, R = 1 would add
+ * omega_frame times the mass.  Output: out, a device pointer to 3 FP64
+ * values, written on `stream` (NULL = legacy default stream) in the order
+ * of fargo_sums.  The call returns once the work is queued; synchronise the
+ * stream before reading out.
  *
  * Scratch: a library-wide device array of 1184 * 6 + 2 doubles (about
- * 57 KB), allocated when the library is loaded and held by every GPU that
- * loads it until the process exits.  nblocks (0 = four per SM) is the
- * number of thread blocks, at most 1184; a larger value returns
- * FARGO_ERR_SIZE.  The first call on each device (with that device
- * current) looks up the array's device address; make that first call
- * before any stream capture.  Every call shares the one array and the call
- * clears its counter itself, so calls that overlap on the GPU (for example
- * on two streams at once) race and must be serialised by the caller.
+ * 57 KB).  The CUDA runtime creates it with the library's device code in
+ * each context that uses the library (at load or, with lazy module loading,
+ * at first use), and every GPU that holds it keeps it until the process
+ * exits.  nblocks (0 = four per SM) is the number of thread blocks, at most
+ * 1184; a larger value returns FARGO_ERR_SIZE.  The first call on each
+ * device (with that device current) looks up the array's device address
+ * and caches it for the process; make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset, or a reset of the primary
+ * context) invalidates the cached address: do not call this entry point
+ * after one.  Every call shares the one array and the call clears its
+ * counter itself, so calls that overlap on the GPU race and must be
+ * serialised by the caller: two streams at once, and equally graph replays
+ * of a captured call that may run concurrently (on different streams, or
+ * several such nodes in one graph without a dependency between them).
  * Errors: BADARG, SIZE, CUDA. */
 int fargo_sums_noalloc(const void *rho, const void *e, const void *vx, int precision, int nx, int ny, int nz,
-                       int ghost, const double *vol, const double *R, double omega_frame, int nblocks,
-                       double *out, void *stream);
+                       int ghost, const double *vol, const double *R, const double *wframe, double omega_frame,
+                       int nblocks, double *out, void *stream);
 
 /* Kernel-level access, for parity tests of single sub-steps.
  * phase: 0 ghost fill, 1 v0 + Courant reduction (the caller's dt is

@@ -106,7 +106,7 @@ def lib():
         L.fargo_launches_per_step.argtypes = [vp]
         L.fargo_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int),
                                          C.POINTER(C.c_char_p)]
-        L.fargo_sums_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
+        L.fargo_sums_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp,
                                          C.c_double, C.c_int, vp, vp]
         L.fargo_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
         L.fargo_batch_destroy.argtypes = [vp]
@@ -352,17 +352,21 @@ def debug_wait_timeout(spin_limit=1000):
     return lib().fargo_debug_wait_timeout(spin_limit)
 
 
-def sums_noalloc(rho, e, vx, precision, nx, ny, nz, ghost, vol, R, omega_frame, out, nblocks=0, stream=None):
+def sums_noalloc(rho, e, vx, precision, nx, ny, nz, ghost, vol, R, omega_frame, out, nblocks=0, stream=None,
+                 wframe=None):
     """Conserved totals of caller-owned device buffers without any device
     allocation by the library (see fargo_sums_noalloc in include/fargo.h).
     Buffers are torch CUDA tensors (or raw device addresses); `out` receives
-    3 FP64 values on `stream` (a raw cudaStream_t, None = legacy default)."""
+    3 FP64 values on `stream` (a raw cudaStream_t, None = legacy default).
+    wframe: the frame term of the X momentum per ring (None = R^2
+    omega_frame; Cartesian callers pass it, zeros for a plain box)."""
     def addr(t):
         if t is None:
             return None
         return C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
     _check(lib().fargo_sums_noalloc(addr(rho), addr(e), addr(vx), precision, nx, ny, nz, ghost, addr(vol),
-                                    addr(R), omega_frame, nblocks, addr(out), stream), "fargo_sums_noalloc")
+                                    addr(R), addr(wframe), omega_frame, nblocks, addr(out), stream),
+           "fargo_sums_noalloc")
 
 
 class FargoBatch:

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "context.cuh"
@@ -810,25 +811,28 @@ static int sums_impl(fargo_ctx *c, Buffers<T> &b, double out[3])
 // Conserved totals without any device allocation: the block partials and
 // the ticket counter of the sums kernel live in a file-scope device array
 // instead of context memory.  The array is looked up once per device with
-// cudaGetSymbolAddress (its name is only a host-side stand-in in host code).
+// cudaGetSymbolAddress (its name is only a host-side stand-in in host code);
+// the lookup is guarded by a mutex so that host threads can make their first
+// calls concurrently.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kNoallocMaxBlocks = 1184;                            // 8 blocks per SM on 148 SMs
 constexpr int kNoallocScratch = 6 * kNoallocMaxBlocks + 2;         // partials + ticket word
 constexpr int kNoallocMaxDevices = 64;
 double *g_noalloc_ptr[kNoallocMaxDevices] = {};
+std::mutex g_noalloc_mu;
 }  // namespace
 static __device__ __align__(256) double g_sums_scratch[kNoallocScratch];
 
 template <typename T>
 static int sums_noalloc_impl(const void *rho, const void *e, const void *vx, int nx, int ny, int nz, int ghost,
-                             const double *vol, const double *R, double omega, int nblocks, double *out,
-                             cudaStream_t s, double *scratch)
+                             const double *vol, const double *R, const double *wframe, double omega, int nblocks,
+                             double *out, cudaStream_t s, double *scratch)
 {
     const int nyt = ny > 1 ? ny + 2 * ghost : 1;
     const int gy = ny > 1 ? ghost : 0, gz = nz > 1 ? ghost : 0;
     SumInput<T> in{(const T *)rho, (const T *)e, (const T *)vx, vol, R, omega,
-                   nx, gy, gy + ny, gz, gz + nz, nyt, (long long)nx, (long long)(nyt + 1) * nx};
+                   nx, gy, gy + ny, gz, gz + nz, nyt, (long long)nx, (long long)(nyt + 1) * nx, wframe};
     unsigned *counter = reinterpret_cast<unsigned *>(scratch + 6 * kNoallocMaxBlocks);
     CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));   // the ticket must start at zero
     k_sums<T><<<nblocks, 256, 0, s>>>(in, scratch, counter, out);
@@ -837,8 +841,8 @@ static int sums_noalloc_impl(const void *rho, const void *e, const void *vx, int
 }
 
 extern "C" int fargo_sums_noalloc(const void *rho, const void *e, const void *vx, int precision, int nx, int ny,
-                                  int nz, int ghost, const double *vol, const double *R, double omega_frame,
-                                  int nblocks, double *out, void *stream)
+                                  int nz, int ghost, const double *vol, const double *R, const double *wframe,
+                                  double omega_frame, int nblocks, double *out, void *stream)
 {
     if (!rho || !vx || !vol || !R || !out) return FARGO_ERR_BADARG;
     if (precision != FARGO_F64 && precision != FARGO_F32) return FARGO_ERR_BADARG;
@@ -847,11 +851,16 @@ extern "C" int fargo_sums_noalloc(const void *rho, const void *e, const void *vx
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoallocMaxDevices) return FARGO_ERR_SIZE;
-    if (!g_noalloc_ptr[dev]) {
-        // first call on this device (with it current): resolve the array's device address
-        double *p = nullptr;
-        CK(cudaGetSymbolAddress((void **)&p, g_sums_scratch));
-        g_noalloc_ptr[dev] = p;
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // first call on this device (with it current): resolve the array's device address
+            double *p = nullptr;
+            CK(cudaGetSymbolAddress((void **)&p, g_sums_scratch));
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
     }
     if (nblocks == 0) {
         int sms = 0;
@@ -860,10 +869,10 @@ extern "C" int fargo_sums_noalloc(const void *rho, const void *e, const void *vx
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == FARGO_F64)
-        return sums_noalloc_impl<double>(rho, e, vx, nx, ny, nz, ghost, vol, R, omega_frame, nblocks, out, st,
-                                         g_noalloc_ptr[dev]);
-    return sums_noalloc_impl<float>(rho, e, vx, nx, ny, nz, ghost, vol, R, omega_frame, nblocks, out, st,
-                                    g_noalloc_ptr[dev]);
+        return sums_noalloc_impl<double>(rho, e, vx, nx, ny, nz, ghost, vol, R, wframe, omega_frame, nblocks, out,
+                                         st, scratch);
+    return sums_noalloc_impl<float>(rho, e, vx, nx, ny, nz, ghost, vol, R, wframe, omega_frame, nblocks, out, st,
+                                    scratch);
 }
 
 // ---------------------------------------------------------------------------

@@ -85,11 +85,14 @@ def momentum_density(w, st):
 
 
 def record(name, **vals):
-    """Append measured parity figures to gpurun_out/parity_record.jsonl when
-    that folder exists (kept for the write-up; never read by a test)."""
+    """Report measured parity figures: printed (visible with pytest -s), and
+    appended as one JSON line to the file named by the environment variable
+    FARGO_PARITY_RECORD when it is set.  Never read by a test."""
     import json
     import os
-    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(d):
-        with open(os.path.join(d, "parity_record.jsonl"), "a") as f:
-            f.write(json.dumps({"case": name, **{k: float(v) for k, v in vals.items()}}) + "\n")
+    line = json.dumps({"case": name, **{k: float(v) for k, v in vals.items()}})
+    print(line)
+    path = os.environ.get("FARGO_PARITY_RECORD")
+    if path:
+        with open(path, "a") as f:
+            f.write(line + "\n")

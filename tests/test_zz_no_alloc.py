@@ -15,16 +15,31 @@ from tests.gpu_util import make_ctx
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(W.SPH, 64, 24, 14, False), (W.CYL, 70, 33, 1, True), (W.CART, 37, 21, 1, False)]
+# (name, workload factory, per-ring frame term passed by the caller)
+#   "none": NULL, the library forms R^2 Omega_f (cylindrical, spherical);
+#   "zero": a plain Cartesian box carries no frame term whatever its Omega_f;
+#   "sheet": the shearing sheet's 2 Omega_f y.
+CASES = [
+    ("sph3d", lambda: W.random_box(W.SPH, 64, 24, 14, g=3, seed=21, nu=1e-3, planet=False), "none"),
+    ("cyl2d-iso", lambda: W.random_box(W.CYL, 70, 33, 1, g=3, seed=21, iso=True, nu=1e-3, planet=False), "none"),
+    ("cart2d", lambda: W.random_box(W.CART, 37, 21, 1, g=3, seed=21, nu=1e-3, planet=False), "zero"),
+    ("sph3d-rotating", lambda: W.random_box(W.SPH, 40, 20, 10, g=3, seed=22, nu=1e-3, planet=False,
+                                            omega_f=0.7), "none"),
+    ("cyl2d-rotating", lambda: W.random_box(W.CYL, 70, 33, 1, g=3, seed=23, iso=True, nu=1e-3, planet=False,
+                                            omega_f=-0.4), "none"),
+    ("cart2d-rotating", lambda: W.random_box(W.CART, 37, 21, 1, g=3, seed=24, nu=1e-3, planet=False,
+                                             omega_f=0.9), "zero"),
+    ("shearing-sheet", lambda: W.perturb(W.shearing_sheet(nx=40, ny=48, omega=1.3), seed=25, amp=1e-2), "sheet"),
+]
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["f64", "f32"])
-@pytest.mark.parametrize("case", CASES, ids=["sph3d", "cyl2d-iso", "cart2d"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_sums_without_allocation_match_context_sums(case, precision):
     import torch
     import paper_1602_02359_b300 as fb
-    geom, nx, ny, nz, iso = case
-    w = W.random_box(geom, nx, ny, nz, g=3, seed=21, iso=iso, nu=1e-3, planet=False)
+    _, make, frame = case
+    w = make()
     c = make_ctx(w, precision)
     want = c.sums()
     dt = torch.float64 if precision == fb.F64 else torch.float32
@@ -38,12 +53,19 @@ def test_sums_without_allocation_match_context_sums(case, precision):
     dx = (w.xmax - w.xmin) / w.nx
     vol_t = torch.tensor(np.ascontiguousarray(vol[:w.nz_t, :w.ny_t]), dtype=torch.float64, device=dev)
     R_t = torch.tensor(np.ascontiguousarray(dxr[:w.nz_t, :w.ny_t] / dx), dtype=torch.float64, device=dev)
+    wf = None
+    if frame == "zero":
+        wf = torch.zeros((w.nz_t, w.ny_t), dtype=torch.float64, device=dev)
+    elif frame == "sheet":
+        ym = W.centres(np.asarray(w.yf))[:w.ny_t]
+        wf = torch.tensor(np.broadcast_to(2.0 * w.omega_f * ym, (w.nz_t, w.ny_t)).copy(), dtype=torch.float64,
+                          device=dev)
     out = torch.zeros(3, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream().cuda_stream
     for _ in range(2):   # two calls in a row share the scratch array
         out.zero_()
-        fb.sums_noalloc(fields["rho"], None if iso else fields["e"], fields["vx"], precision, w.nx, w.ny, w.nz,
-                        w.g, vol_t, R_t, w.omega_f, out, stream=stream)
+        fb.sums_noalloc(fields["rho"], None if w.iso else fields["e"], fields["vx"], precision, w.nx, w.ny, w.nz,
+                        w.g, vol_t, R_t, w.omega_f, out, stream=stream, wframe=wf)
         torch.cuda.current_stream().synchronize()
         got = out.cpu().numpy()
         for a, b in zip(got, want):
