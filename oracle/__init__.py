@@ -45,7 +45,7 @@ def build(force=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "fargo_oracle.h"))):
         return LIB
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
            "-o", LIB + ".tmp", SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
@@ -61,6 +61,10 @@ def lib():
         build()
         L = C.CDLL(LIB)
         pp, ps = C.POINTER(OrParams), C.POINTER(OrState)
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_set_threads.restype = None
+        L.or_get_threads.restype = C.c_int
+        L.or_set_threads(int(os.environ.get("FARGO_ORACLE_THREADS", "1")))
         L.or_step.argtypes = [pp, ps, C.c_double, C.c_double, C.c_double, P]
         L.or_step.restype = C.c_int
         for name in ("or_bc_fill",):
@@ -266,6 +270,15 @@ class Oracle:
         e = math.fsum((w.active(st["e"]) * V).ravel())
         lx = math.fsum((mom * V).ravel())
         return m, e, lx
+
+
+def set_threads(n):
+    """Threads of the oracle's loops (results are bit-identical for any n)."""
+    lib().or_set_threads(int(n))
+
+
+def threads():
+    return lib().or_get_threads()
 
 
 def vanleer_slope(qm, q0, qp, dxm, dxp):

@@ -10,12 +10,43 @@
  * Compile with -ffp-contract=off so that no multiply-add is fused: the
  * Courant step, the mean azimuthal velocity and the integer shift must be
  * reproducible bit for bit.
+ *
+ * Built with OpenMP, the loops over rings (or lines) are shared among
+ * threads (PAR2 below, or a parallel region around the ring loop).  Every
+ * ring's arithmetic is unchanged and each iteration writes only its own
+ * cells; the one reduction, the Courant minimum, is exact in any order, so
+ * the results are bit-identical to a single thread.  Without OpenMP the
+ * pragmas are ignored.
  */
 #include "fargo_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PAR2 _Pragma("omp parallel for collapse(2) schedule(static)")
+
+/* Threads used by the loops above (1 when built without OpenMP). */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Mesh bookkeeping                                                          */
@@ -296,6 +327,7 @@ void or_v0(const or_params *p, const or_state *s, double *v0)
     mesh_init(&m, p);
     for (size_t o = 0; o < (size_t)m.nzt * m.nyt; o++) v0[o] = 0.0;
     if (p->fargo)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++) {
                 double mx = s->vx[IDX(&m, 0, j, k)], mn = mx;
@@ -326,6 +358,7 @@ int or_cfl(const or_params *p, const or_state *s, const double *v0, double t, do
     double best = INFINITY;
     int bad = 0;
     const double g1 = p->gamma * (p->gamma - 1.0);
+    _Pragma("omp parallel for collapse(2) schedule(static) reduction(min:best) reduction(|:bad)")
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++) {
             double v0r = p->fargo ? v0[(size_t)k * m.nyt + j] : 0.0;
@@ -439,6 +472,7 @@ void or_potential(const or_params *p, double t, double *phi)
         double r2 = xs[n] * xs[n] + ys[n] * ys[n] + zs[n] * zs[n];
         r3s[n] = p->planet_live > 0 ? r2 * sqrt(r2) : a * a * a;
     }
+    PAR2
     for (int k = 0; k < m.nzt; k++)
         for (int j = 0; j < m.nyt; j++)
             for (int i = 0; i < m.nx; i++) {
@@ -482,6 +516,7 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
     mesh m;
     mesh_init(&m, p);
     double *P = zalloc(m.n);
+    PAR2
     for (int k = 0; k < m.nzt; k++)
         for (int j = 0; j < m.nyt; j++)
             for (int i = 0; i < m.nx; i++) {
@@ -492,6 +527,7 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
     const double *rho = s->rho;
     double om = p->omega_f;
     if (m.hasX)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -502,6 +538,7 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
                     s->vx[c] = vx[c] + dt * acc;
                 }
     if (m.hasY)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0 + 1; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -531,6 +568,7 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
                     s->vy[c] = vy[c] + dt * acc;
                 }
     if (m.hasZ)
+        PAR2
         for (int k = m.k0 + 1; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -568,6 +606,7 @@ void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
     double *qx = zalloc(m.n), *qy = zalloc(m.n), *qz = zalloc(m.n);
     double *dvx = zalloc(m.n), *dvy = zalloc(m.n), *dvz = zalloc(m.n);
     const double *rho = s->rho;
+    PAR2
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++)
             for (int i = 0; i < m.nx; i++) {
@@ -589,6 +628,7 @@ void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
                 }
             }
     if (!p->iso)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -600,6 +640,7 @@ void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
                     s->e[c] -= dt * h;
                 }
     if (m.hasX)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -607,6 +648,7 @@ void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
                     s->vx[c] -= dt * 2.0 * (qx[c] - qx[cm]) / (len_x(&m, j, k) * (rho[c] + rho[cm]));
                 }
     if (m.hasY)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0 + 1; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -614,6 +656,7 @@ void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
                     s->vy[c] -= dt * 2.0 * (qy[c] - qy[cm]) / (dist_y(&m, j) * (rho[c] + rho[cm]));
                 }
     if (m.hasZ)
+        PAR2
         for (int k = m.k0 + 1; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -646,6 +689,7 @@ void or_compression_heating(const or_params *p, or_state *s, double dt)
     if (p->iso) return;
     mesh m;
     mesh_init(&m, p);
+    PAR2
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++)
             for (int i = 0; i < m.nx; i++) {
@@ -681,6 +725,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
     double *txy = zalloc(m.n), *txz = zalloc(m.n), *tyz = zalloc(m.n);
 #define NU(j, k) (p->nu[(size_t)(k) * m.nyt + (j)])
     /* diagonal components at active cell centres */
+    PAR2
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++)
             for (int i = 0; i < m.nx; i++) {
@@ -711,6 +756,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
             }
     /* tau_xy on the z-directed edge (i-1/2, j-1/2, k) */
     if (m.hasY)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0; j <= m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -733,6 +779,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
                 }
     /* tau_xz on the y-directed edge (i-1/2, j, k-1/2) */
     if (m.hasZ)
+        PAR2
         for (int k = m.k0; k <= m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -754,6 +801,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
                 }
     /* tau_yz on the x-directed edge (i, j-1/2, k-1/2) */
     if (m.hasY && m.hasZ)
+        PAR2
         for (int k = m.k0; k <= m.k1; k++)
             for (int j = m.j0; j <= m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -771,6 +819,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
                     tyz[c] = -rb * nb * t;
                 }
     /* v_x update on faces (i-1/2, j, k) */
+    PAR2
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++)
             for (int i = 0; i < m.nx; i++) {
@@ -800,6 +849,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
             }
     /* v_y update on interior faces (i, j-1/2, k) */
     if (m.hasY)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0 + 1; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -828,6 +878,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
                 }
     /* v_z update on interior faces (i, j, k-1/2) */
     if (m.hasZ)
+        PAR2
         for (int k = m.k0 + 1; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -871,6 +922,7 @@ void or_momenta(const or_params *p, const or_state *s, double *pi[6])
     mesh m;
     mesh_init(&m, p);
     for (int q = 0; q < 6; q++) memset(pi[q], 0, sizeof(double) * m.n);
+    PAR2
     for (int k = 0; k < m.nzt; k++)
         for (int j = 0; j < m.nyt; j++) {
             double R = ring_R(&m, j, k);
@@ -1038,28 +1090,33 @@ void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double
     double *fld[8];
     int nq = gather_quantities(&m, s, pi, fld);
     int nx = m.nx, n = nx + 4;
-    double **lq = malloc(sizeof(double *) * nq);
-    for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
-    double *cen = zalloc(n), *wid = zalloc(n), *vel = zalloc(n), *area = zalloc(n), *vinv = zalloc(n);
-    for (int k = m.k0; k < m.k1; k++)
-        for (int j = m.j0; j < m.j1; j++) {
-            double dX = len_x(&m, j, k);
-            double vr0 = p->fargo ? v0[(size_t)k * m.nyt + j] : 0.0;
-            double S = area_x(&m, j, k), Vi = inv_vol(&m, j, k);
-            /* the ring padded by two periodic images on each side */
-            for (int c = 0; c < n; c++) {
-                int i = ((c - 2) % nx + nx) % nx;
-                cen[c] = c * dX; wid[c] = dX; area[c] = S; vinv[c] = Vi;
-                vel[c] = s->vx[IDX(&m, i, j, k)] - vr0;
-                for (int q = 0; q < nq; q++) lq[q][c] = fld[q][IDX(&m, i, j, k)];
+    _Pragma("omp parallel")
+    {
+        /* line buffers of this thread */
+        double **lq = malloc(sizeof(double *) * nq);
+        for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
+        double *cen = zalloc(n), *wid = zalloc(n), *vel = zalloc(n), *area = zalloc(n), *vinv = zalloc(n);
+        _Pragma("omp for collapse(2) schedule(static)")
+        for (int k = m.k0; k < m.k1; k++)
+            for (int j = m.j0; j < m.j1; j++) {
+                double dX = len_x(&m, j, k);
+                double vr0 = p->fargo ? v0[(size_t)k * m.nyt + j] : 0.0;
+                double S = area_x(&m, j, k), Vi = inv_vol(&m, j, k);
+                /* the ring padded by two periodic images on each side */
+                for (int c = 0; c < n; c++) {
+                    int i = ((c - 2) % nx + nx) % nx;
+                    cen[c] = c * dX; wid[c] = dX; area[c] = S; vinv[c] = Vi;
+                    vel[c] = s->vx[IDX(&m, i, j, k)] - vr0;
+                    for (int q = 0; q < nq; q++) lq[q][c] = fld[q][IDX(&m, i, j, k)];
+                }
+                line_t L = { n, nq, lq, cen, wid, vel, area, vinv };
+                sweep_line(&L, 2, nx + 2, dt);
+                for (int q = 0; q < nq; q++)
+                    for (int i = 0; i < nx; i++) fld[q][IDX(&m, i, j, k)] = lq[q][i + 2];
             }
-            line_t L = { n, nq, lq, cen, wid, vel, area, vinv };
-            sweep_line(&L, 2, nx + 2, dt);
-            for (int q = 0; q < nq; q++)
-                for (int i = 0; i < nx; i++) fld[q][IDX(&m, i, j, k)] = lq[q][i + 2];
-        }
-    for (int q = 0; q < nq; q++) free(lq[q]);
-    free(lq); free(cen); free(wid); free(vel); free(area); free(vinv);
+        for (int q = 0; q < nq; q++) free(lq[q]);
+        free(lq); free(cen); free(wid); free(vel); free(area); free(vinv);
+    }
     mesh_free(&m);
 }
 
@@ -1080,7 +1137,10 @@ void or_orbital_shift(const or_params *p, or_state *s, double *pi[6], const doub
     double *fld[8];
     int nq = gather_quantities(&m, s, pi, fld);
     int nx = m.nx;
-    double *ring = zalloc(nx), *fs = zalloc(nx);
+    _Pragma("omp parallel")
+    {
+    double *ring = zalloc(nx), *fs = zalloc(nx);    /* buffers of this thread */
+    _Pragma("omp for collapse(2) schedule(static)")
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++) {
             double dX = len_x(&m, j, k);
@@ -1115,6 +1175,7 @@ void or_orbital_shift(const or_params *p, or_state *s, double *pi[6], const doub
             free(fl); free(flux0);
         }
     free(ring); free(fs);
+    }
     mesh_free(&m);
 }
 
@@ -1129,9 +1190,12 @@ void or_transport_y(const or_params *p, or_state *s, double *pi[6], double dt)
     double *fld[8];
     int nq = gather_quantities(&m, s, pi, fld);
     int n = m.nyt;
-    double **lq = malloc(sizeof(double *) * nq);
+    _Pragma("omp parallel")
+    {
+    double **lq = malloc(sizeof(double *) * nq);    /* line buffers of this thread */
     for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
     double *vel = zalloc(n + 1), *area = zalloc(n + 1), *vinv = zalloc(n);
+    _Pragma("omp for collapse(2) schedule(static)")
     for (int k = m.k0; k < m.k1; k++)
         for (int i = 0; i < m.nx; i++) {
             for (int j = 0; j < n; j++) {
@@ -1148,6 +1212,7 @@ void or_transport_y(const or_params *p, or_state *s, double *pi[6], double dt)
         }
     for (int q = 0; q < nq; q++) free(lq[q]);
     free(lq); free(vel); free(area); free(vinv);
+    }
     mesh_free(&m);
 }
 
@@ -1161,9 +1226,12 @@ void or_transport_z(const or_params *p, or_state *s, double *pi[6], double dt)
     double *fld[8];
     int nq = gather_quantities(&m, s, pi, fld);
     int n = m.nzt;
-    double **lq = malloc(sizeof(double *) * nq);
+    _Pragma("omp parallel")
+    {
+    double **lq = malloc(sizeof(double *) * nq);    /* line buffers of this thread */
     for (int q = 0; q < nq; q++) lq[q] = zalloc(n);
     double *vel = zalloc(n + 1), *area = zalloc(n + 1), *vinv = zalloc(n), *cen = zalloc(n), *wid = zalloc(n);
+    _Pragma("omp for schedule(static)")
     for (int j = m.j0; j < m.j1; j++) {
         double f = p->geom == OR_SPH ? m.ym[j] : 1.0;
         for (int k = 0; k < n; k++) { cen[k] = f * m.zm[k]; wid[k] = f * m.dz[k]; }
@@ -1183,6 +1251,7 @@ void or_transport_z(const or_params *p, or_state *s, double *pi[6], double dt)
     }
     for (int q = 0; q < nq; q++) free(lq[q]);
     free(lq); free(vel); free(area); free(vinv); free(cen); free(wid);
+    }
     mesh_free(&m);
 }
 
@@ -1195,6 +1264,7 @@ void or_new_velocities(const or_params *p, or_state *s, double *pi[6])
     mesh m;
     mesh_init(&m, p);
     const double *rho = s->rho;
+    PAR2
     for (int k = m.k0; k < m.k1; k++)
         for (int j = m.j0; j < m.j1; j++) {
             double R = ring_R(&m, j, k), w = frame_w(&m, j, k);
@@ -1204,6 +1274,7 @@ void or_new_velocities(const or_params *p, or_state *s, double *pi[6])
             }
         }
     if (m.hasY)
+        PAR2
         for (int k = m.k0; k < m.k1; k++)
             for (int j = m.j0 + 1; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
@@ -1211,6 +1282,7 @@ void or_new_velocities(const or_params *p, or_state *s, double *pi[6])
                     s->vy[c] = (pi[3][cm] + pi[2][c]) / (rho[cm] + rho[c]);
                 }
     if (m.hasZ)
+        PAR2
         for (int k = m.k0 + 1; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++) {
                 double f = p->geom == OR_SPH ? m.ym[j] : 1.0;

@@ -47,6 +47,10 @@ typedef struct { double *rho, *e, *vx, *vy, *vz; } or_state;
 
 /* Full step: cells 2..12 of the flow chart (Fig. 2).  dt_fixed > 0 skips the
  * Courant reduction and uses the given step.  Returns 0 or a negative code. */
+/* Threads of the OpenMP loops (no effect without OpenMP), and their number. */
+void or_set_threads(int n);
+int  or_get_threads(void);
+
 int  or_step(const or_params *p, or_state *s, double t, double t_end, double dt_fixed, double *dt_out);
 
 /* Individual sub-steps (each cites its section inside the source). */

@@ -486,6 +486,45 @@ def test_artificial_viscosity_conserves_ring_momentum_and_heats():
     assert st["e"].sum() > e0       # compressions only ever heat
 
 
+def test_artificial_viscosity_trades_kinetic_for_internal_energy():
+    """The artificial pressure q does work on the faces exactly where it
+    heats the gas: with face masses (rho_{i-1} + rho_i) dx / 2, the kinetic
+    energy it removes equals, to first order in dt, the internal energy it
+    adds (summation by parts over a periodic ring), so the total energy
+    changes at O(dt^2) while each part changes at O(dt); and q, hence both
+    parts, scales as C_q^2.  A missing factor 2 or a one-sided density in
+    the face update, or a wrong width in the heating, breaks the first-order
+    balance."""
+    w = W.random_box(W.CART, 64, 1, 1, g=2, seed=17, iso=False, nu=0.0, planet=False)
+    rng = np.random.default_rng(11)
+    w.state["vx"][:] = rng.normal(size=w.state["vx"].shape)
+    w.state["rho"][:] = 0.5 + rng.uniform(size=w.state["rho"].shape)
+    dx = (w.xmax - w.xmin) / w.nx
+
+    def energies(st):
+        rho, v = st["rho"][0, 0], st["vx"][0, 0]
+        mf = 0.5 * (rho + np.roll(rho, 1)) * dx
+        return math.fsum(0.5 * mf * v * v), math.fsum(st["e"][0, 0] * dx)
+
+    def change(dt, cq=1.41):
+        w.cq = cq
+        st = {k: v.copy() for k, v in w.state.items()}
+        k0, i0 = energies(st)
+        oracle.Oracle(w).artificial_viscosity(st, dt)
+        k1, i1 = energies(st)
+        return k1 - k0, i1 - i0
+
+    dk1, di1 = change(1e-5)
+    dk2, di2 = change(5e-6)
+    assert di1 > 0 and dk1 < 0
+    assert abs(di1 / di2 - 2.0) < 1e-12          # heating is linear in dt
+    tot1, tot2 = dk1 + di1, dk2 + di2
+    assert abs(tot1) < 1e-2 * di1                 # first orders cancel
+    assert 3.9 < tot1 / tot2 < 4.1                # the rest is O(dt^2)
+    dk4, di4 = change(1e-5, cq=2 * 1.41)
+    assert abs(di4 / di1 - 4.0) < 1e-12          # q ~ C_q^2
+
+
 # --------------------------------------------------------------------------
 # Courant condition (Sec. 3.4, Eq. cfl2, and Sec. 3.4.2)
 # --------------------------------------------------------------------------
