@@ -55,6 +55,8 @@ typedef struct {
     const or_params *p;
     int nx, nyt, nzt, gy, gz, j0, j1, k0, k1;
     int hasX, hasY, hasZ;
+    int pery, perz;      /* periodic Y / Z (both sides) */
+    int jf, kf;          /* first interior Y / Z face: j0 + 1, or j0 on a periodic axis */
     size_t sj, sk, n;
     double dx;
     double *ym, *dy, *zm, *dz;
@@ -71,6 +73,10 @@ static void mesh_init(mesh *m, const or_params *p)
     m->j0 = m->gy; m->j1 = m->gy + p->ny;
     m->k0 = m->gz; m->k1 = m->gz + p->nz;
     m->hasX = p->nx > 1; m->hasY = p->ny > 1; m->hasZ = p->nz > 1;
+    m->pery = m->hasY && p->bc_ylo == OR_BC_PERIODIC;
+    m->perz = m->hasZ && p->bc_zlo == OR_BC_PERIODIC;
+    m->jf = m->j0 + (m->pery ? 0 : 1);
+    m->kf = m->k0 + (m->perz ? 0 : 1);
     m->sj = (size_t)p->nx;
     m->sk = (size_t)(m->nyt + 1) * p->nx;
     m->n = (size_t)(m->nzt + 1) * m->sk;
@@ -224,12 +230,29 @@ static double pressure(const mesh *m, const or_state *s, size_t c, int j, int k)
 /* tangential velocities about the wall and set the wall-normal velocity to  */
 /* zero on the wall face with odd mirroring beyond; frozen boundaries keep   */
 /* the values the ghosts were given; zero-gradient copies the last active    */
-/* cell (and the first interior normal face).                                */
+/* cell (and the first interior normal face).  Periodic (both sides of the   */
+/* axis): every ghost value is the value one period away, so the ghost      */
+/* layers below the first active cell hold the last active cells, and the   */
+/* normal face j1 (the upper face of the last active cell) is face j0.      */
 /* ------------------------------------------------------------------------ */
+static void fill_periodic(double *a, size_t base, size_t stride, int lo, int hi, int g, int normal, int side)
+{
+    int n = hi - lo;
+    if (side == 0)
+        for (int mm = 1; mm <= g; mm++) a[base + (size_t)(lo - mm) * stride] = a[base + (size_t)(lo - mm + n) * stride];
+    else
+        for (int mm = 0; mm < g + (normal ? 1 : 0); mm++)
+            a[base + (size_t)(hi + mm) * stride] = a[base + (size_t)(lo + mm) * stride];
+}
+
 static void fill_y(const mesh *m, double *a, int normal, int side, int bc, int k, int i)
 {
     int g = m->p->g, j0 = m->j0, j1 = m->j1;
     if (bc == OR_BC_FROZEN) return;
+    if (bc == OR_BC_PERIODIC) {
+        fill_periodic(a, IDX(m, i, 0, k), m->sj, j0, j1, g, normal, side);
+        return;
+    }
     for (int mm = 0; mm < g; mm++) {
         if (!normal) {
             int dst = side == 0 ? j0 - 1 - mm : j1 + mm;
@@ -260,6 +283,10 @@ static void fill_z(const mesh *m, double *a, int normal, int side, int bc, int j
 {
     int g = m->p->g, k0 = m->k0, k1 = m->k1;
     if (bc == OR_BC_FROZEN) return;
+    if (bc == OR_BC_PERIODIC) {
+        fill_periodic(a, IDX(m, i, j, 0), m->sk, k0, k1, g, normal, side);
+        return;
+    }
     if (!normal) {
         for (int mm = 0; mm < g; mm++) {
             int dst = side == 0 ? k0 - 1 - mm : k1 + mm;
@@ -315,6 +342,43 @@ void or_bc_fill(const or_params *p, or_state *s)
             }
     }
     mesh_free(&m);
+}
+
+/* Periodic images of one array on the periodic axes only (the other       */
+/* boundaries are filled at cells 2 and 9 alone).  On a periodic axis the    */
+/* method reads across the boundary the values one period away, so every    */
+/* sub-step that changes values near it refreshes their images before the   */
+/* next one reads them: the velocities after each source sub-step, the      */
+/* transported quantities after each sweep.  normal: a face-centred array   */
+/* along that axis (v_y for Y, v_z for Z).                                   */
+static void periodic_images(const mesh *m, double *a, int normal_y, int normal_z)
+{
+    int g = m->p->g;
+    if (m->pery) {
+        int kmax = normal_z ? m->nzt + 1 : m->nzt;
+        for (int k = 0; k < kmax; k++)
+            for (int i = 0; i < m->nx; i++)
+                for (int side = 0; side < 2; side++)
+                    fill_periodic(a, IDX(m, i, 0, k), m->sj, m->j0, m->j1, g, normal_y, side);
+    }
+    if (m->perz) {
+        int jmax = normal_y ? m->nyt + 1 : m->nyt;
+        for (int j = 0; j < jmax; j++)
+            for (int i = 0; i < m->nx; i++)
+                for (int side = 0; side < 2; side++)
+                    fill_periodic(a, IDX(m, i, j, 0), m->sk, m->k0, m->k1, g, normal_z, side);
+    }
+}
+
+static void periodic_state(const mesh *m, or_state *s, int velocities, int energy)
+{
+    if (!m->pery && !m->perz) return;
+    if (velocities) {
+        periodic_images(m, s->vx, 0, 0);
+        if (m->hasY) periodic_images(m, s->vy, 1, 0);
+        if (m->hasZ) periodic_images(m, s->vz, 0, 1);
+    }
+    if (energy && !m->p->iso) periodic_images(m, s->e, 0, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -423,11 +487,13 @@ int or_cfl(const or_params *p, const or_state *s, const double *v0, double t, do
         }
     double dt = p->cfl * best;
     /* Shear limit, Eq. 38, between radially adjacent rings. */
+    /* (on a periodic Y axis the last ring's outer neighbour is the first) */
     if (p->fargo && m.hasY)
         for (int k = m.k0; k < m.k1; k++)
-            for (int j = m.j0; j < m.j1 - 1; j++) {
+            for (int j = m.j0; j < m.j1 - (m.pery ? 0 : 1); j++) {
+                int jn = j + 1 < m.j1 ? j + 1 : m.j0;
                 double a = v0[(size_t)k * m.nyt + j] / len_x(&m, j, k);
-                double b = v0[(size_t)k * m.nyt + j + 1] / len_x(&m, j + 1, k);
+                double b = v0[(size_t)k * m.nyt + jn] / len_x(&m, jn, k);
                 double w = fabs(a - b);
                 if (w > 0.0) {
                     double ds = p->cfl / w;
@@ -540,7 +606,7 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
     if (m.hasY)
         PAR2
         for (int k = m.k0; k < m.k1; k++)
-            for (int j = m.j0 + 1; j < m.j1; j++)
+            for (int j = m.jf; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
                     size_t c = IDX(&m, i, j, k), cm = c - m.sj;
                     double d = dist_y(&m, j);
@@ -569,7 +635,7 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
                 }
     if (m.hasZ)
         PAR2
-        for (int k = m.k0 + 1; k < m.k1; k++)
+        for (int k = m.kf; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
                     size_t c = IDX(&m, i, j, k), cm = c - m.sk;
@@ -585,6 +651,7 @@ void or_substep1(const or_params *p, or_state *s, const double *phi, double dt)
                     }
                     s->vz[c] = vz[c] + dt * acc;
                 }
+    periodic_state(&m, s, 1, 0);
     free(P); free(vx); free(vy); free(vz);
     mesh_free(&m);
 }
@@ -627,6 +694,9 @@ void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
                     qz[c] = dv < 0.0 ? c2 * rho[c] * dv * dv : 0.0;
                 }
             }
+    /* on a periodic axis the first face reads q one period away */
+    periodic_images(&m, qy, 0, 0);
+    periodic_images(&m, qz, 0, 0);
     if (!p->iso)
         PAR2
         for (int k = m.k0; k < m.k1; k++)
@@ -650,19 +720,20 @@ void or_artificial_viscosity(const or_params *p, or_state *s, double dt)
     if (m.hasY)
         PAR2
         for (int k = m.k0; k < m.k1; k++)
-            for (int j = m.j0 + 1; j < m.j1; j++)
+            for (int j = m.jf; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
                     size_t c = IDX(&m, i, j, k), cm = c - m.sj;
                     s->vy[c] -= dt * 2.0 * (qy[c] - qy[cm]) / (dist_y(&m, j) * (rho[c] + rho[cm]));
                 }
     if (m.hasZ)
         PAR2
-        for (int k = m.k0 + 1; k < m.k1; k++)
+        for (int k = m.kf; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
                     size_t c = IDX(&m, i, j, k), cm = c - m.sk;
                     s->vz[c] -= dt * 2.0 * (qz[c] - qz[cm]) / (dist_z(&m, j, k) * (rho[c] + rho[cm]));
                 }
+    periodic_state(&m, s, 1, 1);
     free(qx); free(qy); free(qz); free(dvx); free(dvy); free(dvz);
     mesh_free(&m);
 }
@@ -697,6 +768,7 @@ void or_compression_heating(const or_params *p, or_state *s, double dt)
                 size_t c = IDX(&m, i, j, k);
                 s->e[c] = s->e[c] * (1.0 - th) / (1.0 + th);
             }
+    periodic_state(&m, s, 0, 1);
     mesh_free(&m);
 }
 
@@ -754,6 +826,11 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
                     tzz[c] = -rn * (2.0 * (dzz + vr / r) - 2.0 / 3.0 * dv);
                 }
             }
+    /* on a periodic axis the faces next to the boundary read the diagonal */
+    /* stresses one period away */
+    periodic_images(&m, txx, 0, 0);
+    periodic_images(&m, tyy, 0, 0);
+    periodic_images(&m, tzz, 0, 0);
     /* tau_xy on the z-directed edge (i-1/2, j-1/2, k) */
     if (m.hasY)
         PAR2
@@ -851,7 +928,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
     if (m.hasY)
         PAR2
         for (int k = m.k0; k < m.k1; k++)
-            for (int j = m.j0 + 1; j < m.j1; j++)
+            for (int j = m.jf; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
                     int ip = IP(&m, i);
                     size_t c = IDX(&m, i, j, k), cjm = c - m.sj, cp = IDX(&m, ip, j, k);
@@ -879,7 +956,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
     /* v_z update on interior faces (i, j, k-1/2) */
     if (m.hasZ)
         PAR2
-        for (int k = m.k0 + 1; k < m.k1; k++)
+        for (int k = m.kf; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
                     int ip = IP(&m, i);
@@ -905,6 +982,7 @@ void or_viscosity(const or_params *p, or_state *s, double dt)
                     s->vz[c] = vz[c] - dt * f / rf;
                 }
 #undef NU
+    periodic_state(&m, s, 1, 0);
     free(txx); free(tyy); free(tzz); free(txy); free(txz); free(tyz);
     free(v0s.vx); free(v0s.vy); free(v0s.vz);
     mesh_free(&m);
@@ -1075,6 +1153,13 @@ static int gather_quantities(const mesh *m, or_state *s, double *pi[6], double *
     return nq;
 }
 
+/* The transported quantities' periodic images after a sweep. */
+static void periodic_quantities(const mesh *m, double **fld, int nq)
+{
+    if (!m->pery && !m->perz) return;
+    for (int q = 0; q < nq; q++) periodic_images(m, fld[q], 0, 0);
+}
+
 /* ------------------------------------------------------------------------ */
 /* ------------------------------------------------------------------------ */
 /* Cells 12b-c along X, residual part (Sec. 3.4.1, Eq. fargo1): upwind       */
@@ -1117,6 +1202,7 @@ void or_transport_x(const or_params *p, or_state *s, double *pi[6], const double
         for (int q = 0; q < nq; q++) free(lq[q]);
         free(lq); free(cen); free(wid); free(vel); free(area); free(vinv);
     }
+    periodic_quantities(&m, fld, nq);
     mesh_free(&m);
 }
 
@@ -1176,6 +1262,7 @@ void or_orbital_shift(const or_params *p, or_state *s, double *pi[6], const doub
         }
     free(ring); free(fs);
     }
+    periodic_quantities(&m, fld, nq);
     mesh_free(&m);
 }
 
@@ -1213,6 +1300,7 @@ void or_transport_y(const or_params *p, or_state *s, double *pi[6], double dt)
     for (int q = 0; q < nq; q++) free(lq[q]);
     free(lq); free(vel); free(area); free(vinv);
     }
+    periodic_quantities(&m, fld, nq);
     mesh_free(&m);
 }
 
@@ -1252,6 +1340,7 @@ void or_transport_z(const or_params *p, or_state *s, double *pi[6], double dt)
     for (int q = 0; q < nq; q++) free(lq[q]);
     free(lq); free(vel); free(area); free(vinv); free(cen); free(wid);
     }
+    periodic_quantities(&m, fld, nq);
     mesh_free(&m);
 }
 
@@ -1276,14 +1365,14 @@ void or_new_velocities(const or_params *p, or_state *s, double *pi[6])
     if (m.hasY)
         PAR2
         for (int k = m.k0; k < m.k1; k++)
-            for (int j = m.j0 + 1; j < m.j1; j++)
+            for (int j = m.jf; j < m.j1; j++)
                 for (int i = 0; i < m.nx; i++) {
                     size_t c = IDX(&m, i, j, k), cm = c - m.sj;
                     s->vy[c] = (pi[3][cm] + pi[2][c]) / (rho[cm] + rho[c]);
                 }
     if (m.hasZ)
         PAR2
-        for (int k = m.k0 + 1; k < m.k1; k++)
+        for (int k = m.kf; k < m.k1; k++)
             for (int j = m.j0; j < m.j1; j++) {
                 double f = p->geom == OR_SPH ? m.ym[j] : 1.0;
                 for (int i = 0; i < m.nx; i++) {
@@ -1291,6 +1380,7 @@ void or_new_velocities(const or_params *p, or_state *s, double *pi[6])
                     s->vz[c] = (pi[5][cm] + pi[4][c]) / (rho[cm] + rho[c]) / f;
                 }
             }
+    periodic_state(&m, s, 1, 0);
     mesh_free(&m);
 }
 

@@ -18,7 +18,7 @@ extern "C" {
 #endif
 
 enum { OR_CART = 0, OR_CYL = 1, OR_SPH = 2 };
-enum { OR_BC_REFLECT = 0, OR_BC_FROZEN = 1, OR_BC_ZEROGRAD = 2 };
+enum { OR_BC_REFLECT = 0, OR_BC_FROZEN = 1, OR_BC_ZEROGRAD = 2, OR_BC_PERIODIC = 3 };
 
 typedef struct {
     int geom, nx, ny, nz, g;

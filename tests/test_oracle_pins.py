@@ -830,3 +830,117 @@ def test_torque_profile_sums_to_the_torque_and_places_it_by_ring():
     assert prof[0, 11] != 0.0
     others = np.delete(prof[0], 11)
     assert np.max(np.abs(others)) <= 1e-12 * abs(prof[0, 11])
+
+
+# --------------------------------------------------------------------------
+# Periodic Y/Z boundaries (Sec. 4.1, ghost zones at cells 2 and 9): every
+# value read across the boundary is the value one period away.
+# --------------------------------------------------------------------------
+def _periodic_box(geom, nx, ny, nz, seed, iso=False, nu=1e-2, fargo=True):
+    bcs = [W.BC_PERIODIC, W.BC_PERIODIC]
+    w = W.random_box(geom, nx, ny, nz, g=3, seed=seed, iso=iso, nu=nu, planet=False, fargo=fargo)
+    w.bc_y = tuple(bcs) if geom == W.CART else w.bc_y
+    w.bc_z = tuple(bcs)
+    return W.periodic_tables(w)
+
+
+def test_periodic_ghosts_are_the_images_one_period_away():
+    w = _periodic_box(W.CART, 8, 16, 8, seed=41)
+    st = w.state
+    oracle.Oracle(w).bc_fill(st)
+    g, ny, nz, nzt, nyt = w.g, w.ny, w.nz, w.nz_t, w.ny_t
+    for k in ("rho", "e", "vx"):
+        a = st[k][:nzt, :nyt]         # the extra row and plane only store face velocities
+        assert np.array_equal(a[:, :g], a[:, ny:ny + g]), k          # below j0: the last cells
+        assert np.array_equal(a[:, g + ny:], a[:, g:2 * g]), k
+        assert np.array_equal(a[:g], a[nz:nz + g]), k
+        assert np.array_equal(a[g + nz:], a[g:2 * g]), k
+    vy = st["vy"][:nzt]
+    assert np.array_equal(vy[:, g + ny:], vy[:, g:2 * g + 1])   # face j1 is face j0
+    assert np.array_equal(vy[:, :g], vy[:, ny:ny + g])
+    vz = st["vz"][:, :nyt]
+    assert np.array_equal(vz[g + nz:], vz[g:2 * g + 1])
+    assert np.array_equal(vz[:g], vz[nz:nz + g])
+
+
+@pytest.mark.parametrize("geom,dims", [(W.CART, (8, 16, 8)), (W.CART, (16, 32, 1)), (W.CYL, (16, 8, 16))])
+def test_periodic_box_conserves_mass_to_round_off(geom, dims):
+    """No boundary takes or gives mass on a periodic axis: over 20 steps the
+    total changes by round-off only (the closed-box pin's counterpart)."""
+    w = _periodic_box(geom, *dims, seed=42)
+    if geom == W.CYL:          # radial walls closed, z periodic
+        w.bc_y = (W.BC_REFLECT, W.BC_REFLECT)
+    o = oracle.Oracle(w)
+    st = w.state
+    m0 = o.sums(st)[0]
+    t = 0.0
+    for _ in range(20):
+        t += o.step(st, t)
+    assert abs(o.sums(st)[0] - m0) <= 2e-14 * m0
+
+
+def test_periodic_cartesian_box_conserves_momentum():
+    """A Cartesian box periodic in every direction has no external force:
+    pressure, artificial and viscous stresses and transport all telescope, so
+    the total momentum along X, Y and Z keeps its value to round-off."""
+    w = _periodic_box(W.CART, 8, 16, 8, seed=43)
+    o = oracle.Oracle(w)
+    st = w.state
+    o.bc_fill(st)
+
+    def totals():
+        a = lambda f: f[w.gz:w.gz + w.nz, w.gy:w.gy + w.ny, :]          # noqa: E731
+        rho = a(st["rho"])
+        px = rho * 0.5 * (a(st["vx"]) + np.roll(a(st["vx"]), -1, axis=2))
+        vy = st["vy"][w.gz:w.gz + w.nz, w.gy:w.gy + w.ny + 1]
+        vz = st["vz"][w.gz:w.gz + w.nz + 1, w.gy:w.gy + w.ny]
+        py = rho * 0.5 * (vy[:, :-1] + vy[:, 1:])
+        pz = rho * 0.5 * (vz[:-1] + vz[1:])
+        return [math.fsum(p.ravel()) for p in (px, py, pz)], math.fsum(np.abs(rho).ravel())
+
+    p0, scale = totals()
+    t = 0.0
+    for _ in range(20):
+        t += o.step(st, t)
+    p1, _ = totals()
+    for a, b in zip(p0, p1):
+        assert abs(a - b) <= 1e-13 * scale, (p0, p1)
+
+
+@pytest.mark.parametrize("geom,dims,shift", [(W.CART, (8, 16, 8), (3, 5)), (W.CYL, (16, 8, 16), (0, 5)),
+                                              (W.CART, (16, 32, 1), (7, 0))])
+def test_periodic_step_commutes_with_translation(geom, dims, shift):
+    """On a uniform periodic axis (faces at exact binary fractions) nothing
+    singles out a cell: a state translated by whole cells steps to the
+    translated result, bit for bit.  A face left out of the update, a ghost
+    not refreshed or a stress read on the wrong side breaks it."""
+    w = _periodic_box(geom, *dims, seed=44)
+    w.nu = np.full_like(w.nu, 1e-2)      # a translation moves the state, not the per-ring tables
+    if geom == W.CYL:
+        w.bc_y = (W.BC_FROZEN, W.BC_FROZEN)
+        w.star_mass = 0.0                 # the star's pull depends on z
+        w.zf = W.faces(w.nz, w.g, -0.125, 0.125)
+    o = oracle.Oracle(w)
+    st = w.state
+    o.bc_fill(st)
+    sy, sz = shift
+
+    def translate(a):
+        """Active rows moved by sy and active planes by sz, whole cells; the
+        frozen radial ghosts of the cylindrical box move with their planes."""
+        out = a.copy()
+        if sy:
+            out[:, w.gy:w.gy + w.ny] = np.roll(out[:, w.gy:w.gy + w.ny], sy, axis=1)
+        if sz:
+            out[w.gz:w.gz + w.nz] = np.roll(out[w.gz:w.gz + w.nz], sz, axis=0)
+        return out
+
+    moved = {k: translate(v) for k, v in st.items()}
+    o.bc_fill(moved)
+    a, b = {k: v.copy() for k, v in st.items()}, moved
+    dta, dtb = o.step(a, 0.0), o.step(b, 0.0)
+    assert dta == dtb
+    for k in ("rho", "e", "vx", "vy", "vz"):
+        want = translate(a[k])
+        act = (slice(w.gz, w.gz + w.nz), slice(w.gy, w.gy + w.ny))
+        assert np.array_equal(b[k][act], want[act]), k

@@ -25,7 +25,7 @@ from typing import Optional
 import numpy as np
 
 CART, CYL, SPH = 0, 1, 2
-BC_REFLECT, BC_FROZEN, BC_ZEROGRAD = 0, 1, 2
+BC_REFLECT, BC_FROZEN, BC_ZEROGRAD, BC_PERIODIC = 0, 1, 2, 3
 FIELDS = ("rho", "e", "vx", "vy", "vz")
 
 
@@ -495,6 +495,27 @@ def random_box(geom, nx, ny, nz, g=3, seed=0, iso=False, nu=1e-3, planet=True,
     if iso:
         st["e"][:] = 0.0
     w.state = st
+    return w
+
+
+def periodic_tables(w):
+    """On a periodic Y or Z axis the per-ring inputs (sound speed, viscosity)
+    of the ghost rings must repeat the active rings one period away, as the
+    state does: rewrite them so."""
+    for name in ("cs", "nu"):
+        a = getattr(w, name)
+        if a is None:
+            continue
+        a = a.copy()
+        if w.ny > 1 and w.bc_y[0] == BC_PERIODIC:
+            g, n = w.g, w.ny
+            a[:, :g] = a[:, n:n + g]
+            a[:, g + n:] = a[:, g:2 * g]
+        if w.nz > 1 and w.bc_z[0] == BC_PERIODIC:
+            g, n = w.g, w.nz
+            a[:g] = a[n:n + g]
+            a[g + n:] = a[g:2 * g]
+        setattr(w, name, a)
     return w
 
 
