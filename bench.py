@@ -358,12 +358,33 @@ def cpu_sample(wname):
     return (lambda k: W.disk2d(), "oracle on the full 768x256 disk")
 
 
-def cpu_baseline(wname, budget_s=20.0):
-    """The plain FP64 oracle on a bounded sample of the workload, host cores."""
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(wname, budget_s=12.0):
+    """The plain FP64 oracle on a bounded sample of the workload on the host
+    cores: its loops over rings shared by OpenMP threads on every core (the
+    reported value), and on one thread beside it (bit-identical results)."""
+    import oracle
     make, sample = cpu_sample(wname)
-    cells, el, n, k = oracle_steps(make, budget_s)
-    return {"value": cells / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample}; {n} steps of {k} instance(s) in {el:.1f} s"}
+    nproc = os.cpu_count() or 1
+    oracle.set_threads(1)
+    c1, e1, n1, k1 = oracle_steps(make, budget_s)
+    oracle.set_threads(nproc)
+    cn, en, nn, kn = oracle_steps(make, budget_s)
+    oracle.set_threads(1)
+    return {"value": cn / en, "unit": "cell-updates/s", "cores": nproc, "kind": "oracle",
+            "threads": nproc, "cpu": cpu_model(), "nproc": nproc,
+            "single_thread": {"value": c1 / e1, "cores": 1, "steps": n1, "s": round(e1, 1)},
+            "sample": f"{sample}; {nn} steps of {kn} instance(s) in {en:.1f} s on {nproc} OpenMP threads"}
 
 
 def workload_label(wname):
@@ -380,6 +401,9 @@ def run_reference(args):
         return
     wname = args.workload
     make, sample = cpu_sample(wname)
+    import oracle
+    nproc = os.cpu_count() or 1
+    oracle.set_threads(nproc)
     # each step: about one second of oracle work on the sample
     oracle_steps(make, 0.5 * args.warmup, max_steps=args.warmup)
     cells, el, n, k = oracle_steps(make, 1.0 * args.steps)
@@ -390,8 +414,10 @@ def run_reference(args):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_label(wname), "sample": sample,
                        "step": "about 1 s of oracle work on the sample per step"},
-            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{sample}; {n} oracle steps of {k} instance(s) in {el:.1f} s"},
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": nproc, "kind": "oracle",
+                             "cpu": cpu_model(),
+                             "sample": f"{sample}; {n} oracle steps of {k} instance(s) in {el:.1f} s "
+                                       f"on {nproc} OpenMP threads"},
             "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -424,6 +450,105 @@ def fp64_plain_disk2d(torch, fb, steps=50, warmup=5):
     return {"workload": "disk2d-cyl-isothermal-planet-768x256", "dtype": "f64",
             "value": w.cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms,
             "l2": "flushed (512 MB write) before every timed step", "err": err}
+
+
+# FP64 operations per active cell of one step of the 768 x 256 disk in FP64
+# (ncu: smsp__sass_thread_inst_executed_op_{dadd,dmul}_pred_on.sum + 2 x
+# ..._op_dfma_pred_on.sum over every launch of a step, divided by the
+# cells), valid while the step's sources keep FP64_FLOPS_SRC_HASH
+# (profiles/fp64_disk2d_step_ncu.md).
+FP64_FLOPS_PER_CELL_2D = 1095.2
+FP64_FLOPS_SRC_HASH = "6e7c073e68c8dd04"
+
+
+def fp64_roofline(fp64, alu):
+    """Roofline of the FP64 step against the measured FP64 multiply-add peak:
+    the per-cell kernels run about 400 FP64 operations per cell, so the FP64
+    units, not memory, bound it."""
+    flops = (FP64_FLOPS_PER_CELL_2D if FP64_FLOPS_SRC_HASH and kernel_source_hash() == FP64_FLOPS_SRC_HASH
+             else None)
+    peak = alu["fp64"] if alu else None
+    out = {"bound": "alu", "unit": "TFLOP/s", "peak": round(peak, 3) if peak else None,
+           "peak_kind": "measured FP64 multiply-add throughput (fargo_alu_peaks)",
+           "flops_per_cell": flops, "achieved": None, "frac": None}
+    if flops and peak:
+        ach = flops * fp64["value"] / 1e12
+        out.update({"achieved": round(ach, 3), "frac": round(ach / peak, 4)})
+    return out
+
+
+def sod_latency(torch, fb):
+    """The 1D Sod tube in FP64 (512 cells, Y axis, t = 0.2): 512 cells are
+    far too few to load the GPU, so what is reported is the latency of a
+    step: the run to t = 0.2 through fargo_run_to (graph replays, device time
+    polled every 64 steps), CUDA events around it, after one untimed run."""
+    w = W.sod()
+    stream = torch.cuda.Stream()
+    c = fb.Fargo(w, fb.F64, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        c.set_state(w.state)
+        c.set_time(0.0, w.t_end)
+        c.run_to(w.t_end, poll=64)
+        c.set_state(w.state)
+        c.set_time(0.0, w.t_end)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n = c.run_to(w.t_end, poll=64)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    t, _, _, err = c.scalars()
+    nl = c.launches_per_step()
+    c.close()
+    return {"workload": "sod1d-cart-adiabatic-512-t0.2", "dtype": "f64", "steps": n, "t": t, "err": err,
+            "ms_total": round(ms, 3), "us_per_step": round(1e3 * ms / n, 2), "launches_per_step": nl,
+            "value": w.cells * n / (ms * 1e-3), "unit": "cell-updates/s",
+            "bound": "launch latency (one CUDA graph of %d launches per step on 512 cells)" % nl}
+
+
+def disk2d_fp32(torch, fb, dev, steps=200, warmup=10):
+    """The 768 x 256 planet disk in FP32 (single context, CUDA graph).  Its
+    state (about 17 MB) stays in the 126 MB L2 between steps, so the line is
+    a cell-update rate; an HBM fraction would not mean anything here."""
+    w = W.disk2d()
+    stream = torch.cuda.Stream()
+    c = fb.Fargo(w, fb.F32, stream=stream.cuda_stream)
+    c.set_state(w.state)
+    c.set_time(0.0, 1e30)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            c.step(want_dt=False)
+        ms, clocks = timed_steps(torch, stream, lambda: c.step(want_dt=False), steps, dev, lambda: None)
+    err = c.scalars()[3]
+    c.close()
+    return {"workload": "disk2d-cyl-isothermal-planet-768x256", "dtype": "f32", "value": w.cells / (ms * 1e-3),
+            "unit": "cell-updates/s", "ms_per_step": round(ms, 4), "steps": steps, "err": err,
+            "l2": "L2-resident (state about 17 MB), no flush", "clocks": clocks}
+
+
+def batch_fp32_error(mem, ps, picks):
+    """FP32 error of sampled disks of the batch after the steps the bench
+    gave them, against the FP64 oracle run from the same initial state for
+    the same number of steps (relative L1 over the active cells: density and
+    the cell-centred momentum density); outside every timed region."""
+    import oracle
+    from tests.gpu_util import momentum_density, rel_l1
+    oracle.set_threads(os.cpu_count() or 1)
+    out = []
+    for i in picks:
+        w = W.batch_instance(ps[i])
+        m = mem[i]
+        n = m.scalars()[2]
+        st = w.copy().state
+        oracle.Oracle(w).run(st, 0.0, w.t_end, max_steps=n)
+        g = {k: v.astype(np.float64) for k, v in m.get_state().items()}
+        out.append({"member": i, "mesh": f"{w.nx}x{w.ny}", "steps": int(n),
+                    "rho": float(rel_l1(w.active(g["rho"]), w.active(st["rho"]))),
+                    "momentum": float(rel_l1(momentum_density(w, g), momentum_density(w, st)))})
+    oracle.set_threads(1)
+    return out
 
 
 # The method's minimum traffic per cell-update: read the state once for the
@@ -614,26 +739,24 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
     e2e = None
     if e2e_on:
         # public API end to end: every step uploads each disk's active state
-        # (rho, v_x, v_y) from pinned host memory and reads it back
+        # (rho, v_x, v_y) from pinned host memory and reads it back, each field
+        # of all disks as one packed buffer (member order, active cells)
         names = ["rho", "vx", "vy"]
-        host = []
-        for m in mem:
-            host.append({n: torch.empty(m.active_shape, dtype=torch.float32, pin_memory=True) for n in names})
-            for n in names:
-                m.get_field(n, region=fb.ACTIVE, out=host[-1][n].numpy())
-        bytes_io = sum(h.numel() * h.element_size() for d in host for h in d.values())
+        host = {n: torch.empty(cells, dtype=torch.float32, pin_memory=True) for n in names}
+        for n in names:
+            b.get_field_packed(n, host[n])
+        bytes_io = sum(h.numel() * h.element_size() for h in host.values())
         ksteps = max(3, min(args.steps, 6))
         with torch.cuda.stream(stream):
             torch.cuda.synchronize()
             barrier()
             t1 = time.perf_counter()
-            cols = {n: [d[n] for d in host] for n in names}
             for _ in range(ksteps):
                 for n in names:
-                    b.set_field(n, cols[n], region=fb.ACTIVE)   # queued on the batch's stream
+                    b.set_field_packed(n, host[n])      # queued on the batch's stream
                 b.step(sync=False)
                 for n in names:
-                    b.get_field(n, cols[n], region=fb.ACTIVE)   # the last one synchronises
+                    b.get_field_packed(n, host[n])      # one copy per field; synchronises
                 b.status()
             torch.cuda.synchronize()
             el = time.perf_counter() - t1
@@ -641,12 +764,17 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
         e2e = {"value": cells * ksteps / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": ksteps,
                "note": "every step uploads every disk's active rho, v_x, v_y from pinned host memory "
-                       "(fargo_batch_set_field, queued on the batch's stream), steps the batch and reads "
-                       "them back (fargo_batch_get_field); one host synchronisation per field read"}
+                       "(fargo_batch_set_field_packed: one copy per field for all disks plus a scatter "
+                       "kernel, queued on the batch's stream), steps the batch and reads them back "
+                       "(fargo_batch_get_field_packed: a gather kernel and one copy per field)"}
+    b.status()
+    picks = sorted(range(len(ps)), key=lambda i: (ps[i]["ny"], i))[:2]
+    fp32_err = batch_fp32_error(mem, ps, picks)
     b.close()
     for m in mem:
         m.close()
     return {"workload": batch_label(len(ps)), "cells": cells, "members": len(ps), "ms": ms, "clocks": clocks,
+            "fp32_error": fp32_err,
             "roofline": roof, "e2e": e2e, "launches": nl, "setup_s": round(setup_s, 1),
             "steps_advanced_min": int(min(nsteps)), "running": running,
             "state_gb": cells * 2 * 22 * 4 / 1e9}
@@ -811,6 +939,13 @@ def main():
     fp64 = None
     if rank == 0 and not args.no_fp64 and args.workload in ("disk3d",) + tuple(BATCH_WORKLOADS):
         fp64 = fp64_plain_disk2d(torch, fb)
+    alu = fb.alu_peaks(torch.cuda.current_stream().cuda_stream) if rank == 0 else None
+    if fp64 is not None:
+        fp64["roofline"] = fp64_roofline(fp64, alu)
+    extra_lines = {}
+    if rank == 0 and batched and not args.no_single:
+        extra_lines["sod_fp64"] = sod_latency(torch, fb)
+        extra_lines["disk2d_fp32"] = disk2d_fp32(torch, fb, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload not in ("disk3d-small", "batch-small", "batch-medium"):
@@ -849,6 +984,18 @@ def main():
             line["planet_force"] = r["planet_force"]
         if surrogate is not None:
             line["surrogate_kernels"] = surrogate
+        if alu is not None:
+            line["alu_peaks"] = {"fp64_tflops": round(alu["fp64"], 2), "fp32_tflops": round(alu["fp32"], 1),
+                                 "fp32x2_tflops": round(alu["fp32x2"], 1),
+                                 "how": "fargo_alu_peaks: independent multiply-add chains on every SM, "
+                                        "best of 3 launches, CUDA events"}
+        line.update(extra_lines)
+        if batched and r.get("fp32_error"):
+            line["fp32_error_vs_fp64_oracle"] = {
+                "members": r["fp32_error"],
+                "note": "sampled disks of the batch after the bench's steps, against the FP64 oracle from "
+                        "the same initial state; the errors at the sweep's run lengths (1000 steps, 500 "
+                        "orbits) are measured by tests/test_gpu_fp32_long.py"}
         print(json.dumps(line), flush=True)
     ranks.close()
 

@@ -41,8 +41,18 @@ typedef struct fargo_ctx fargo_ctx;
 enum { FARGO_CART = 0, FARGO_CYL = 1, FARGO_SPH = 2 };
 enum { FARGO_F64 = 0, FARGO_F32 = 1 };
 /* Y/Z boundary conditions (X is periodic, Sec. 3.4.1): reflecting wall,
- * frozen ghosts (keep the values given), zero gradient. */
-enum { FARGO_BC_REFLECT = 0, FARGO_BC_FROZEN = 1, FARGO_BC_ZEROGRAD = 2 };
+ * frozen ghosts (keep the values given), zero gradient, periodic (Sec. 4.1,
+ * ghost zones: every value read across the boundary is the value one period
+ * away).  Periodic goes on both sides of an axis or neither; Y may be
+ * periodic on Cartesian meshes, Z on Cartesian and cylindrical ones (the
+ * geometry does not change along those axes).  On a periodic axis the first
+ * face (j0 / k0) is interior and updated by every sub-step, the ghosts are
+ * refreshed with their images after each sub-step and sweep that changes
+ * the values they copy, the ghost cells' widths must equal those of their
+ * images, and so must the per-ring tables cs and nu (fargo_create checks
+ * both, to 1e-12 relative), and the axis needs more active cells than
+ * ghost layers. */
+enum { FARGO_BC_REFLECT = 0, FARGO_BC_FROZEN = 1, FARGO_BC_ZEROGRAD = 2, FARGO_BC_PERIODIC = 3 };
 enum { FARGO_RHO = 0, FARGO_ENERGY = 1, FARGO_VX = 2, FARGO_VY = 3, FARGO_VZ = 4 };
 enum { FARGO_ACTIVE = 0, FARGO_FULL = 1 };
 
@@ -350,6 +360,16 @@ int fargo_set_launch_shape(fargo_ctx *ctx, int cell_bs, int seg_y, int seg_z);
  * no hang and no fault.  Synchronises the legacy default stream. */
 int fargo_debug_wait_timeout(unsigned spin_limit);
 
+/* Arithmetic peaks of the current device, measured (a measurement aid; the
+ * paper has no counterpart): out[0] FP64, out[1] FP32 and out[2] packed
+ * two-lane FP32 multiply-add throughput in TFLOP/s (2 flops per lane and
+ * multiply-add), each the best of three timed launches of independent
+ * multiply-add chains filling every SM, after a warm-up launch.  Queued on
+ * `stream` (NULL = legacy default stream) and synchronised; allocates 2 KB
+ * for the duration of the call; changes no device setting.  The FP64 path
+ * of the step is bound by out[0], not by memory.  Errors: BADARG, CUDA. */
+int fargo_alu_peaks(double out[3], void *stream);
+
 /* Use (1) or bypass (0) the CUDA graph for fargo_step (default 1). */
 int fargo_use_graph(fargo_ctx *ctx, int enable);
 
@@ -380,10 +400,10 @@ const char *fargo_strerror(int code);
  * ------------------------------------------------------------------------ */
 typedef struct fargo_batch fargo_batch;
 
-/* members: n distinct contexts of one precision.  stream: cudaStream_t of the
- * batch (NULL = a stream the batch creates and owns).  Synchronises the
- * members' streams.  Errors: BADARG (NULL, duplicate or mixed precision),
- * OOM, CUDA. */
+/* members: n distinct contexts of one precision, none with a periodic Y or
+ * Z boundary.  stream: cudaStream_t of the batch (NULL = a stream the batch
+ * creates and owns).  Synchronises the members' streams.  Errors: BADARG
+ * (NULL, duplicate, mixed precision, a periodic member), OOM, CUDA. */
 int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, int n, void *stream);
 void fargo_batch_destroy(fargo_batch *b);
 
@@ -403,6 +423,20 @@ void fargo_batch_destroy(fargo_batch *b);
 int fargo_batch_set_field(fargo_batch *b, int field, int region, const void *const *src, const size_t *bytes);
 int fargo_batch_get_field(fargo_batch *b, int field, int region, void *const *dst, const size_t *bytes);
 
+/* One field of every member in or out as ONE contiguous buffer: the active
+ * cells (FARGO_ACTIVE layout) of member 0, then member 1, ..., each nz*ny*nx
+ * values X fastest, in the batch's precision; bytes must be the sum of the
+ * members' active sizes.  The buffer is host memory (pinned for an
+ * asynchronous copy) or device memory.  The batch stages it through a
+ * device buffer of the same size (allocated at the first packed transfer,
+ * freed with the batch) with one copy and one scatter (gather) kernel, so a
+ * field crosses the host link in a single transfer instead of one per row.
+ * set: queued on the batch's stream, no synchronisation (keep src unchanged
+ * until the next synchronising batch call); get: synchronises.  Errors:
+ * BADARG (a field some member does not have), SIZE, OOM, CUDA. */
+int fargo_batch_set_field_packed(fargo_batch *b, int field, const void *src, size_t bytes);
+int fargo_batch_get_field_packed(fargo_batch *b, int field, void *dst, size_t bytes);
+
 /* Queue one step of every member (one graph launch); no host sync. */
 int fargo_batch_step(fargo_batch *b);
 
@@ -421,6 +455,21 @@ int fargo_batch_use_graph(fargo_batch *b, int enable);
 
 /* Number of kernel launches one batched step queues. */
 int fargo_batch_launches_per_step(const fargo_batch *b);
+
+/* Autotuner of the batch's launch shapes that leave every result unchanged:
+ * the cells per thread of the per-cell phases (4, 8, 16, 32) and the
+ * segment length of the Y/Z sweeps for every member (the members' own
+ * setting, 0 = the default rule, 16 .. 128 rows).  Each candidate is timed
+ * by per-launch CUDA events over `reps` (>= 2, the first one warming up)
+ * batched steps, each started from a device snapshot of every member's state
+ * and time; the snapshot is restored at the end, so the run is unchanged.
+ * cfg (may be NULL) receives {cells per thread, segment length (-1: the
+ * members' own)}; ms_default and ms_tuned (may be NULL) the summed device
+ * time of one step with the shapes at entry and with the chosen ones.  The
+ * paper's code searches block sizes in a similar way (Sec. 4.2).  Allocates
+ * the snapshot (the members' state fields) for the duration of the call;
+ * synchronises.  Errors: BADARG, OOM, CUDA. */
+int fargo_batch_autotune(fargo_batch *b, int reps, int *cfg, float *ms_default, float *ms_tuned);
 
 /* One batched step launched kernel by kernel with CUDA events between
  * launches; as fargo_profile_step.  Synchronises. */

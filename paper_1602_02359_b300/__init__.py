@@ -27,9 +27,10 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_step", "fargo_step_fixed", "fargo_run_to", "fargo_get_scalars", "fargo_sums",
             "fargo_debug_phase", "fargo_get_aux", "fargo_set_aux", "fargo_use_graph",
             "fargo_launches_per_step", "fargo_strerror", "fargo_profile_step", "fargo_sums_noalloc",
-            "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
+            "fargo_alu_peaks", "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
-            "fargo_batch_profile_step", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_set_planet_source", "fargo_planet_torque_profile", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_profile_step", "fargo_batch_autotune", "fargo_batch_set_field_packed",
+            "fargo_batch_get_field_packed", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_set_planet_source", "fargo_planet_torque_profile", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -108,6 +109,7 @@ def lib():
                                          C.POINTER(C.c_char_p)]
         L.fargo_sums_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp,
                                          C.c_double, C.c_int, vp, vp]
+        L.fargo_alu_peaks.argtypes = [PD, vp]
         L.fargo_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
         L.fargo_batch_destroy.argtypes = [vp]
         L.fargo_batch_destroy.restype = None
@@ -118,6 +120,10 @@ def lib():
         L.fargo_batch_set_field.argtypes = [vp, C.c_int, C.c_int, C.POINTER(vp), C.POINTER(C.c_size_t)]
         L.fargo_batch_get_field.argtypes = [vp, C.c_int, C.c_int, C.POINTER(vp), C.POINTER(C.c_size_t)]
         L.fargo_batch_launches_per_step.argtypes = [vp]
+        L.fargo_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float),
+                                           C.POINTER(C.c_float)]
+        L.fargo_batch_set_field_packed.argtypes = [vp, C.c_int, vp, C.c_size_t]
+        L.fargo_batch_get_field_packed.argtypes = [vp, C.c_int, vp, C.c_size_t]
         L.fargo_batch_profile_step.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int),
                                                C.POINTER(C.c_char_p)]
         L.fargo_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
@@ -346,6 +352,14 @@ class Fargo:
         return lib().fargo_launches_per_step(self.h)
 
 
+def alu_peaks(stream=None):
+    """Measured multiply-add throughput of the device in TFLOP/s:
+    {"fp64": ..., "fp32": ..., "fp32x2": ...} (fargo_alu_peaks)."""
+    out = (C.c_double * 3)()
+    _check(lib().fargo_alu_peaks(out, stream), "fargo_alu_peaks")
+    return {"fp64": out[0], "fp32": out[1], "fp32x2": out[2]}
+
+
 def debug_wait_timeout(spin_limit=1000):
     """Run the bounded-wait failure check; returns the library's code
     (FARGO_ERR_BARRIER_TIMEOUT = -7 when the wait ran out, as expected)."""
@@ -453,6 +467,37 @@ class FargoBatch:
 
     def launches_per_step(self):
         return lib().fargo_batch_launches_per_step(self.h)
+
+    @staticmethod
+    def _ptr1(a):
+        if hasattr(a, "data_ptr"):
+            return C.c_void_p(a.data_ptr()), a.numel() * a.element_size()
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("the packed buffer must be contiguous")
+        return C.c_void_p(a.ctypes.data), a.nbytes
+
+    def set_field_packed(self, name, buf):
+        """fargo_batch_set_field_packed: field `name` of every member from one
+        buffer holding the members' active cells in member order (queued, no
+        synchronisation: keep buf unchanged until get/status)."""
+        p, nb = self._ptr1(buf)
+        _check(lib().fargo_batch_set_field_packed(self.h, FIELD_IDS[name], p, nb), "fargo_batch_set_field_packed")
+
+    def get_field_packed(self, name, buf):
+        """fargo_batch_get_field_packed: field `name` of every member into one
+        buffer (member order, active cells); synchronises."""
+        p, nb = self._ptr1(buf)
+        _check(lib().fargo_batch_get_field_packed(self.h, FIELD_IDS[name], p, nb), "fargo_batch_get_field_packed")
+        return buf
+
+    def autotune(self, reps=3):
+        """fargo_batch_autotune: pick the per-cell grouping and the sweep
+        segments by timing; the state is left unchanged.  Returns
+        ({"cells_per_thread": .., "segment": ..}, ms_default, ms_tuned)."""
+        cfg = (C.c_int * 2)()
+        a, b = C.c_float(), C.c_float()
+        _check(lib().fargo_batch_autotune(self.h, int(reps), cfg, C.byref(a), C.byref(b)), "fargo_batch_autotune")
+        return {"cells_per_thread": cfg[0], "segment": cfg[1]}, a.value, b.value
 
     def profile_step(self):
         """One batched step launched kernel by kernel; returns [(kernel, ms), ...]."""

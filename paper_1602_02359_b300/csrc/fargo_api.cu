@@ -332,9 +332,10 @@ static int alloc_fields(fargo_ctx *c, Buffers<T> &b)
 // lands in the state buffers.
 // ---------------------------------------------------------------------------
 // Optional per-launch event marks (fargo_profile_step).
+constexpr int kProfMax = 48;   // launches of one step, periodic images included
 struct Prof {
-    cudaEvent_t ev[32];
-    const char *name[32];
+    cudaEvent_t ev[kProfMax + 1];
+    const char *name[kProfMax];
     int n;
 };
 
@@ -363,13 +364,28 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     MARK("cfl_screen");
     k_cfl_exact<T><<<cfl_exact_grid(P.cfl_blocks), 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_exact");
+    // periodic images between the phases (periodic Y/Z axes only)
+    const bool per = m.pery || m.perz;
+#define PERIODIC(set, nm)                                                      \
+    do {                                                                       \
+        if (per) {                                                             \
+            const int k_ = launch_periodic<T>(m, set, P.sc, s);                \
+            for (int q_ = 0; q_ < k_; q_++) MARK(nm);                          \
+        }                                                                      \
+    } while (0)
     // cell 7
     launch_source<T>(SRC_SUB1, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("substep1");
+    PERIODIC(per_fields<T>(m, P.VB, true, false), "periodic");
     launch_source<T>(SRC_AV, m, cg, cb, s, P.tb, P.VB, P.A, P.tau, P.sc); MARK("artvisc");
+    PERIODIC(per_fields<T>(m, P.A, true, true), "periodic");
     if (m.has_nu) {
         // stresses once into the scratch momenta of set B (unused until the transport step)
         launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_tau");
+        QSet<T> diag = P.tau;
+        diag.nq = m.hasZ ? 3 : 2;
+        PERIODIC(per_quantities<T>(diag, diag), "periodic");
         launch_source<T>(SRC_VAPPLY, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
+        PERIODIC(per_fields<T>(m, P.VB, true, false), "periodic");
     }
     // cell 9
     if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_y9"); }
@@ -377,9 +393,15 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     // cell 12
     launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_rs, s);
     MARK("transport_x");
+    PERIODIC(per_quantities<T>(P.qx, P.qx), "periodic");
     if (m.hasY) {
         launch_sweep_tma<T, 1>(m, P.tb, c->mapsY, P.qy, P.sc, P.qx.nq, s, P.seg_y);
         MARK("transport_y");
+        // the Z sweep reads its ghost planes from the Y sweep's input
+        if (per && m.hasZ && m.perz) {
+            const int k_ = launch_periodic<T>(m, per_quantities<T>(P.qx, P.qy), P.sc, s, 2);
+            for (int q_ = 0; q_ < k_; q_++) MARK("periodic");
+        }
     }
     if (m.hasZ) {
         launch_sweep_tma<T, 2>(m, P.tb, c->mapsZ, P.qz, P.sc, P.qx.nq, s, P.seg_z);
@@ -390,7 +412,10 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         launch_orb<T>(m, P.tb, P.qfin, P.v0, P.sc, P.nrings_active, c->orb_rs, s);
         MARK("orbital");
     }
+    PERIODIC(per_quantities<T>(P.qfin, P.qfin), "periodic");
     launch_newvel<T>(m, cg, cb, s, P.tb, P.qfin, P.vsrc, P.A, P.sc, 0); MARK("newvel");
+    PERIODIC(per_fields<T>(m, P.A, true, false), "periodic");
+#undef PERIODIC
 #undef MARK
     c->launches = nl;
     if (prof) prof->n = nl;
@@ -482,6 +507,40 @@ static int set_kernel_attrs(fargo_ctx *c)
     return FARGO_OK;
 }
 
+// A periodic axis (Sec. 4.1): both sides periodic, a geometry that does not
+// change along the axis, more active cells than ghost layers, ghost widths
+// and per-ring tables (cs, nu) equal to their images one period away.
+static bool close_rel(double a, double b) { return fabs(a - b) <= 1e-12 * fmax(fabs(a), fabs(b)); }
+static bool periodic_ok(int geom, int nx, int ny, int nz, int g, const fargo_params *p)
+{
+    for (int ax = 0; ax < 2; ax++) {
+        const int *bc = ax == 0 ? p->bc_y : p->bc_z;
+        const int n = ax == 0 ? ny : nz;
+        if ((bc[0] == FARGO_BC_PERIODIC) != (bc[1] == FARGO_BC_PERIODIC)) return false;
+        if (bc[0] != FARGO_BC_PERIODIC || n == 1) continue;
+        if (ax == 0 && geom != FARGO_CART) return false;
+        if (ax == 1 && geom == FARGO_SPH) return false;
+        if (n <= g) return false;
+        const double *f = ax == 0 ? p->yfaces : p->zfaces;
+        const int lo = g, hi = g + n;
+        for (int mm = 1; mm <= g; mm++) {
+            if (!close_rel(f[lo - mm + 1] - f[lo - mm], f[hi - mm + 1] - f[hi - mm])) return false;
+            if (!close_rel(f[hi + mm - 1 + 1] - f[hi + mm - 1], f[lo + mm - 1 + 1] - f[lo + mm - 1])) return false;
+        }
+        const int nyt = ny > 1 ? ny + 2 * g : 1, nzt = nz > 1 ? nz + 2 * g : 1;
+        for (const double *tab : {p->cs, p->nu}) {
+            if (!tab) continue;
+            for (int a = 0; a < (ax == 0 ? nzt : nyt); a++)
+                for (int mm = 1; mm <= g; mm++) {
+                    auto at = [&](int b) { return ax == 0 ? tab[(size_t)a * nyt + b] : tab[(size_t)b * nyt + a]; };
+                    if (!close_rel(at(lo - mm), at(hi - mm)) || !close_rel(at(hi + mm - 1), at(lo + mm - 1)))
+                        return false;
+                }
+        }
+    }
+    return true;
+}
+
 extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, int ghost, double gamma,
                             const fargo_planet *planet, const fargo_params *prm)
 {
@@ -495,7 +554,8 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     if (gamma <= 0.0 && !prm->cs) return FARGO_ERR_BADARG;
     if (!(prm->cfl > 0.0)) return FARGO_ERR_BADARG;
     for (int s = 0; s < 2; s++)
-        if (prm->bc_y[s] < 0 || prm->bc_y[s] > 2 || prm->bc_z[s] < 0 || prm->bc_z[s] > 2) return FARGO_ERR_BADARG;
+        if (prm->bc_y[s] < 0 || prm->bc_y[s] > 3 || prm->bc_z[s] < 0 || prm->bc_z[s] > 3) return FARGO_ERR_BADARG;
+    if (!periodic_ok(geom, nx, ny, nz, ghost, prm)) return FARGO_ERR_BADARG;
     if (planet && planet->q > 0.0 && !(planet->a > 0.0)) return FARGO_ERR_BADARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return FARGO_ERR_NOTBUILT;
@@ -536,6 +596,10 @@ extern "C" int fargo_create(fargo_ctx **out, int geom, int nx, int ny, int nz, i
     m.indirect = m.has_planet && planet->indirect;
     m.has_star = prm->star_mass > 0.0 && geom != FARGO_CART;
     for (int s = 0; s < 2; s++) { m.bcy[s] = prm->bc_y[s]; m.bcz[s] = prm->bc_z[s]; }
+    m.pery = m.hasY && m.bcy[0] == BC_PERIODIC;
+    m.perz = m.hasZ && m.bcz[0] == BC_PERIODIC;
+    m.jf = m.j0 + (m.pery ? 0 : 1);
+    m.kf = m.k0 + (m.perz ? 0 : 1);
     if ((long long)(c->nzt + 1) * (c->nyt + 1) * c->pitch >= (1LL << 31)) {
         // field indices are 32-bit in the kernels
         if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1167,11 +1231,13 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         launch_source<T>(SRC_SUB1, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB,
                          QSet<T>{}, c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
+        launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
         break;
     case 3:
         if ((rc = copyv(b.vB, va))) return rc;
         launch_source<T>(SRC_AV, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, VB, A,
                          QSet<T>{}, c->sc);
+        launch_periodic<T>(m, per_fields<T>(m, A, true, true), c->sc, s);
         break;
     case 4: {
         if (!m.has_nu) break;
@@ -1179,13 +1245,18 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
         tau.nq = 6;
         launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB, tau, c->sc);
+        QSet<T> diag = tau;
+        diag.nq = m.hasZ ? 3 : 2;
+        launch_periodic<T>(m, per_quantities<T>(diag, diag), c->sc, s);
         launch_source<T>(SRC_VAPPLY, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB, tau,
                          c->sc);
         if ((rc = copyv(va, b.vB))) return rc;
+        launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
         break;
     }
     case 5:
         launch_tx<T>(m, b.tab, A, qa, c->v0, c->sc, c->tx_rs, s);
+        launch_periodic<T>(m, per_quantities<T>(qa, qa), c->sc, s);
         break;
     case 6:
     case 7: {
@@ -1196,14 +1267,18 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         if (phase == 6) launch_sweep_tma<T, 1>(m, b.tab, mp, qb, c->sc, qa.nq, s);
         else launch_sweep_tma<T, 2>(m, b.tab, mp, qb, c->sc, qa.nq, s);
         for (int q = 0; q < qa.nq; q++) CK(cudaMemcpyAsync(qa.q[q], qb.q[q], nbytes, cudaMemcpyDeviceToDevice, s));
+        launch_periodic<T>(m, per_quantities<T>(qa, qa), c->sc, s);
         break;
     }
     case 8:
         launch_newvel<T>(m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, qa, A, A, c->sc, 0);
+        launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
         break;
     case 9:
-        if (m.fargo && m.hasX)
+        if (m.fargo && m.hasX) {
             launch_orb<T>(m, b.tab, qa, c->v0, c->sc, c->nrings_active, c->orb_rs, s);
+            launch_periodic<T>(m, per_quantities<T>(qa, qa), c->sc, s);
+        }
         break;
     default:
         return FARGO_ERR_BADARG;
@@ -1281,7 +1356,7 @@ extern "C" int fargo_profile_step(fargo_ctx *c, int max_kernels, float *ms, int 
 {
     if (!c || !ms || !n_out || max_kernels < 1) return FARGO_ERR_BADARG;
     Prof prof{};
-    for (int i = 0; i < 32; i++) CK(cudaEventCreate(&prof.ev[i]));
+    for (int i = 0; i <= kProfMax; i++) CK(cudaEventCreate(&prof.ev[i]));
     CK(cudaEventRecord(prof.ev[0], c->stream));
     int rc = c->prec == FARGO_F64 ? enqueue_step<double>(c, c->b64, &prof) : enqueue_step<float>(c, c->b32, &prof);
     if (rc == FARGO_OK) {
@@ -1293,7 +1368,7 @@ extern "C" int fargo_profile_step(fargo_ctx *c, int max_kernels, float *ms, int 
         }
         *n_out = n;
     }
-    for (int i = 0; i < 32; i++) cudaEventDestroy(prof.ev[i]);
+    for (int i = 0; i <= kProfMax; i++) cudaEventDestroy(prof.ev[i]);
     return rc;
 }
 
@@ -1349,7 +1424,7 @@ static int time_step_kernels(fargo_ctx *c, Buffers<T> &b, Snapshot &sn, int reps
         int rc = snapshot_copy<T>(c, b, sn, false);
         if (rc) return rc;
         Prof prof{};
-        for (int i = 0; i < 32; i++) CK(cudaEventCreate(&prof.ev[i]));
+        for (int i = 0; i <= kProfMax; i++) CK(cudaEventCreate(&prof.ev[i]));
         CK(cudaEventRecord(prof.ev[0], c->stream));
         rc = enqueue_step<T>(c, b, &prof);
         if (rc == FARGO_OK) {
@@ -1362,7 +1437,7 @@ static int time_step_kernels(fargo_ctx *c, Buffers<T> &b, Snapshot &sn, int reps
                         if (r > 0) tot += ms;   // the first repetition warms up
                     }
         }
-        for (int i = 0; i < 32; i++) cudaEventDestroy(prof.ev[i]);
+        for (int i = 0; i <= kProfMax; i++) cudaEventDestroy(prof.ev[i]);
         if (rc) return rc;
     }
     *ms_out = tot;
@@ -1486,6 +1561,90 @@ extern "C" int fargo_debug_wait_timeout(unsigned spin_limit)
     }
     cudaFree(d);
     return rc ? rc : err_code(h);
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic peaks of the device, for the rooflines of the ALU-bound kernels
+// (the FP64 step): every thread runs 8 independent multiply-add chains, so
+// the units stay busy whatever their latency; the grid is 8 blocks of 256
+// threads per SM.  FP32 is measured in the scalar form the step's kernels
+// use and in the packed two-lane form of this architecture.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chains(T *sink, int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) x[c] = (T)(threadIdx.x + c);
+    for (int i = 0; i < iters; i++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) x[c] = fma(x[c], a, b);
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) s += x[c];
+    if (s == (T)-12345) sink[threadIdx.x] = s;   // keeps the chains alive; never true for |a| < 1
+}
+__global__ void __launch_bounds__(256) k_fma2_chains(float *sink, int iters, float a, float b)
+{
+    float2 x[8];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+    for (int c = 0; c < 8; c++) x[c] = make_float2((float)(threadIdx.x + c), (float)(threadIdx.x + c + 1));
+    for (int i = 0; i < iters; i++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) x[c] = __ffma2_rn(x[c], a2, b2);
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; c++) s += x[c].x + x[c].y;
+    if (s == -12345.f) sink[threadIdx.x] = s;
+}
+
+template <typename K, typename... A>
+static int time_chains(K kernel, int blocks, double flops, cudaStream_t st, double *tflops, A... args)
+{
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    kernel<<<blocks, 256, 0, st>>>(args...);   // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < 3; r++) {
+        CK(cudaEventRecord(e0, st));
+        kernel<<<blocks, 256, 0, st>>>(args...);
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return FARGO_OK;
+}
+
+extern "C" int fargo_alu_peaks(double out[3], void *stream)
+{
+    if (!out) return FARGO_ERR_BADARG;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    void *sink = nullptr;
+    CK(cudaMalloc(&sink, 256 * sizeof(double)));
+    const int blocks = 8 * sms;
+    const double threads = (double)blocks * 256;
+    const int it64 = 1 << 12, it32 = 1 << 15;
+    int rc = time_chains(k_fma_chains<double>, blocks, 2.0 * 8 * it64 * threads, st, &out[0], (double *)sink, it64,
+                         0.999999, 1e-7);
+    if (!rc)
+        rc = time_chains(k_fma_chains<float>, blocks, 2.0 * 8 * it32 * threads, st, &out[1], (float *)sink, it32,
+                         0.999999f, 1e-7f);
+    if (!rc)
+        rc = time_chains(k_fma2_chains, blocks, 4.0 * 8 * it32 * threads, st, &out[2], (float *)sink, it32,
+                         0.999999f, 1e-7f);
+    cudaFree(sink);
+    return rc;
 }
 
 extern "C" int fargo_use_graph(fargo_ctx *c, int enable)

@@ -93,16 +93,19 @@ __global__ void __launch_bounds__(256) kb_cfl_exact(const StepPlan<T> *__restric
 
 // Per-cell phases: a member's cells of the augmented mesh (rows, planes as
 // in the single-instance grid) are numbered row by row; a block takes
-// kCellsPerThread * blockDim.x consecutive cells, each thread every
-// blockDim.x-th of them, so the member lookup is paid once per block for
-// several cells and no block is padded to a row's end.
+// cpt * blockDim.x consecutive cells, each thread every blockDim.x-th of
+// them, so the member lookup is paid once per block for several cells and
+// no block is padded to a row's end.  cpt (cells per thread, 16 by default)
+// is a launch shape the batch autotuner may change: every cell runs the same
+// body whatever the grouping.
 constexpr int kCellsPerThread = 16;
 
 // Register budgets (measured): 32 per thread for sub-step 1 (eight 256-thread
 // blocks per SM), 48 for the viscous update (five blocks), 40 for the other
 // phases (six blocks).
 template <typename T, int PH, class F>
-__global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : (PH == PH_SUB1 ? 8 : 6)) kb_cell(const StepPlan<T> *__restrict__ P, Group g)
+__global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : (PH == PH_SUB1 ? 8 : 6)) kb_cell(const StepPlan<T> *__restrict__ P, Group g,
+                                                                                                int cpt)
 {
     int local;
     __shared__ PlanSmem<T> sp;
@@ -111,10 +114,10 @@ __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : (PH == PH_SUB1 ? 8 
     const unsigned nyr = PH == PH_TAU ? tau_rows(m) : m.nyt + 1;
     const unsigned rows = nyr * (PH == PH_TAU ? tau_planes(m) : cell_planes(m));
     const unsigned nx = (unsigned)m.nx;
-    const unsigned lin = (unsigned)local * (kCellsPerThread * blockDim.x) + threadIdx.x;
+    const unsigned lin = (unsigned)local * (cpt * blockDim.x) + threadIdx.x;
     unsigned row = lin / nx;
     unsigned i = lin - row * nx;
-    for (int u = 0; u < kCellsPerThread && row < rows; u++) {
+    for (int u = 0; u < cpt && row < rows; u++) {
         // one plane without a Z direction: the row is the Y index
         int j = F::hasZ(m) ? (int)(row % nyr) : (int)row, k = F::hasZ(m) ? (int)(row / nyr) : 0;
         if constexpr (PH == PH_TAU) {
@@ -242,6 +245,35 @@ __global__ void __launch_bounds__(TmaTile<T>::TW + 32) kb_sweep(const StepPlan<T
                             local);
 }
 
+// Packed field transfers: the active cells of one field of every member,
+// concatenated in member order (X fastest within a member), between the
+// members' padded field arrays and one contiguous staging buffer.  A block
+// covers 1024 consecutive cells of one member (found by the group search).
+constexpr int kPackCells = 1024;
+template <typename T>
+__global__ void __launch_bounds__(256) kb_pack(const StepPlan<T> *__restrict__ P, Group g,
+                                               const long long *__restrict__ pk, int field, T *stage, int to_fields)
+{
+    int local;
+    const int id = group_member(g, blockIdx.x, local);
+    const StepPlan<T> &p = P[id];
+    const MeshD &m = p.m;
+    T *const fl[5] = {p.A.rho, p.A.e, p.A.vx, p.A.vy, p.A.vz};
+    T *f = fl[field];
+    const int nx = m.nx, ny = m.j1 - m.j0, nz = m.k1 - m.k0;
+    const long long nact = (long long)nx * ny * nz;
+    T *s = stage + __ldg(&pk[id]);
+    for (int u = 0; u < kPackCells / 256; u++) {
+        const long long t = (long long)local * kPackCells + u * 256 + threadIdx.x;
+        if (t >= nact) return;
+        const int i = (int)(t % nx);
+        const long long r = t / nx;
+        const idx_t c = IX(m, i, m.j0 + (int)(r % ny), m.k0 + (int)(r / ny));
+        if (to_fields) f[c] = s[t];
+        else s[t] = f[c];
+    }
+}
+
 // out[0] = members still running, out[1] = OR of their error flags,
 // out[2] = lowest index of a failed member (n if none).
 __global__ void __launch_bounds__(256) kb_status(Scal *const *sc, int n, int *out)
@@ -308,6 +340,14 @@ struct fargo_batch {
     int *hstatus = nullptr;                   // pinned host copy
     std::vector<void *> allocs;
     std::vector<BLaunch> seq;                 // the launches of one step, in order
+    // packed field transfers: staging buffer (all members' active cells of
+    // one field), per-member packed offsets and the group of the pack launch
+    void *stage = nullptr;
+    long long *pk = nullptr;
+    int *pack_grp = nullptr;
+    int pack_blocks = 0;
+    size_t packed_bytes = 0;
+    int cpt = kCellsPerThread;                // cells per thread of the per-cell phases
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
@@ -397,11 +437,12 @@ static int batch_setup(fargo_batch *b)
     }
     auto all = [](const fargo_ctx *) { return true; };
     auto one = [](const fargo_ctx *) { return 0; };
-    auto cells = [](const fargo_ctx *c) {
-        return (int)grid_for((long long)c->nx * (c->nyt + 1) * cell_planes(c->m), 256 * kCellsPerThread);
+    const int cpt = b->cpt;
+    auto cells = [cpt](const fargo_ctx *c) {
+        return (int)grid_for((long long)c->nx * (c->nyt + 1) * cell_planes(c->m), 256 * cpt);
     };
-    auto tau_cells = [](const fargo_ctx *c) {
-        return (int)grid_for((long long)c->nx * tau_rows(c->m) * tau_planes(c->m), 256 * kCellsPerThread);
+    auto tau_cells = [cpt](const fargo_ctx *c) {
+        return (int)grid_for((long long)c->nx * tau_rows(c->m) * tau_planes(c->m), 256 * cpt);
     };
     auto hasY = [](const fargo_ctx *c) { return c->m.hasY != 0; };
     auto hasZ = [](const fargo_ctx *c) { return c->m.hasZ != 0; };
@@ -416,7 +457,8 @@ static int batch_setup(fargo_batch *b)
             const MeshD &m = c->m;
             const int np = axis == 1 ? m.j1 - m.j0 : m.k1 - m.k0;
             const int n2 = axis == 1 ? m.k1 - m.k0 : m.j1 - m.j0;
-            const int sl = sweep_seglen(np);
+            const int set = axis == 1 ? c->seg_y : c->seg_z;   // as make_plan
+            const int sl = set > 0 ? set : sweep_seglen(np);
             const int ntx = (m.nx + TmaTile<T>::TW - 1) / TmaTile<T>::TW;
             return ntx * n2 * ((np + sl - 1) / sl);
         };
@@ -511,14 +553,14 @@ static int batch_setup(fargo_batch *b)
 }
 
 template <typename T, class F>
-static void launch_cell_cfg(int ph, int nb, const StepPlan<T> *P, Group g, cudaStream_t s)
+static void launch_cell_cfg(int ph, int nb, const StepPlan<T> *P, Group g, int cpt, cudaStream_t s)
 {
     switch (ph) {
-    case PH_SUB1: kb_cell<T, PH_SUB1, F><<<nb, 256, 0, s>>>(P, g); break;
-    case PH_AV: kb_cell<T, PH_AV, F><<<nb, 256, 0, s>>>(P, g); break;
-    case PH_TAU: kb_cell<T, PH_TAU, F><<<nb, 256, 0, s>>>(P, g); break;
-    case PH_VAPPLY: kb_cell<T, PH_VAPPLY, F><<<nb, 256, 0, s>>>(P, g); break;
-    default: kb_cell<T, PH_NEWVEL, F><<<nb, 256, 0, s>>>(P, g); break;
+    case PH_SUB1: kb_cell<T, PH_SUB1, F><<<nb, 256, 0, s>>>(P, g, cpt); break;
+    case PH_AV: kb_cell<T, PH_AV, F><<<nb, 256, 0, s>>>(P, g, cpt); break;
+    case PH_TAU: kb_cell<T, PH_TAU, F><<<nb, 256, 0, s>>>(P, g, cpt); break;
+    case PH_VAPPLY: kb_cell<T, PH_VAPPLY, F><<<nb, 256, 0, s>>>(P, g, cpt); break;
+    default: kb_cell<T, PH_NEWVEL, F><<<nb, 256, 0, s>>>(P, g, cpt); break;
     }
 }
 
@@ -579,11 +621,11 @@ static int batch_enqueue(fargo_batch *b, cudaEvent_t *marks = nullptr)
         case L_SCREEN: kb_cfl_screen<T><<<nb, 256, 0, s>>>(P, g); break;
         case L_EXACT: kb_cfl_exact<T><<<nb, 256, 0, s>>>(P, g); break;
         case L_CELL:
-            if (x.key == CFG_DISK3D) launch_cell_cfg<T, CfgDisk3D>(x.arg, nb, P, g, s);
-            else if (x.key == CFG_DISK2D) launch_cell_cfg<T, CfgDisk2D>(x.arg, nb, P, g, s);
-            else if (x.key == CFG_DISK3D_LIVE) launch_cell_cfg<T, CfgDisk3DLive>(x.arg, nb, P, g, s);
-            else if (x.key == CFG_DISK2D_LIVE) launch_cell_cfg<T, CfgDisk2DLive>(x.arg, nb, P, g, s);
-            else launch_cell_cfg<T, CfgRun>(x.arg, nb, P, g, s);
+            if (x.key == CFG_DISK3D) launch_cell_cfg<T, CfgDisk3D>(x.arg, nb, P, g, b->cpt, s);
+            else if (x.key == CFG_DISK2D) launch_cell_cfg<T, CfgDisk2D>(x.arg, nb, P, g, b->cpt, s);
+            else if (x.key == CFG_DISK3D_LIVE) launch_cell_cfg<T, CfgDisk3DLive>(x.arg, nb, P, g, b->cpt, s);
+            else if (x.key == CFG_DISK2D_LIVE) launch_cell_cfg<T, CfgDisk2DLive>(x.arg, nb, P, g, b->cpt, s);
+            else launch_cell_cfg<T, CfgRun>(x.arg, nb, P, g, b->cpt, s);
             break;
         case L_TX:
         case L_ORB: launch_ring<T>(x, P, s); break;
@@ -628,6 +670,8 @@ extern "C" int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, 
     const int prec = members[0] ? members[0]->prec : -1;
     for (int i = 0; i < n; i++) {
         if (!members[i] || members[i]->prec != prec) return FARGO_ERR_BADARG;
+        // the batched phases have no periodic-image launches between them
+        if (members[i]->m.pery || members[i]->m.perz) return FARGO_ERR_BADARG;
         for (int k = 0; k < i; k++)
             if (members[k] == members[i]) return FARGO_ERR_BADARG;
     }
@@ -667,6 +711,9 @@ extern "C" void fargo_batch_destroy(fargo_batch *b)
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (void *p : b->allocs) cudaFree(p);
+    if (b->stage) cudaFree(b->stage);
+    if (b->pk) cudaFree(b->pk);
+    if (b->pack_grp) cudaFree(b->pack_grp);
     if (b->hstatus) cudaFreeHost(b->hstatus);
     // a stream handed in by the caller stays theirs; the member contexts too
     if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -693,6 +740,79 @@ extern "C" int fargo_batch_get_field(fargo_batch *b, int field, int region, void
         const int rc = fargo_queue_field(b->mem[i], field, region, dst[i], bytes[i], 0, b->stream);
         if (rc) return rc;
     }
+    CK(cudaStreamSynchronize(b->stream));
+    return FARGO_OK;
+}
+
+// The staging buffer and the pack launch's tables, made at the first packed
+// transfer and kept until the batch is destroyed.
+static int pack_setup(fargo_batch *b)
+{
+    if (b->stage) return FARGO_OK;
+    std::vector<long long> pk(b->n);
+    std::vector<int> ids(b->n), off(b->n + 1, 0);
+    long long tot = 0;
+    for (int i = 0; i < b->n; i++) {
+        const fargo_ctx *c = b->mem[i];
+        const long long nact = (long long)c->nx * c->ny * c->nz;
+        pk[i] = tot;
+        tot += nact;
+        ids[i] = i;
+        off[i + 1] = off[i] + (int)((nact + kPackCells - 1) / kPackCells);
+    }
+    const size_t esz = b->mem[0]->esz;
+    b->packed_bytes = (size_t)tot * esz;
+    CK(cudaMalloc(&b->stage, b->packed_bytes));
+    CK(cudaMalloc(&b->pk, sizeof(long long) * b->n));
+    CK(cudaMalloc(&b->pack_grp, sizeof(int) * (2 * b->n + 1)));
+    CK(cudaMemcpyAsync(b->pk, pk.data(), sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->pack_grp, ids.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->pack_grp + b->n, off.data(), sizeof(int) * (b->n + 1), cudaMemcpyHostToDevice, b->stream));
+    b->pack_blocks = off[b->n];
+    return FARGO_OK;
+}
+
+static int pack_launch(fargo_batch *b, int field, int to_fields)
+{
+    const Group g{b->pack_grp, b->pack_grp + b->n, b->n};
+    if (b->prec == FARGO_F64)
+        kb_pack<double><<<b->pack_blocks, 256, 0, b->stream>>>((const StepPlan<double> *)b->plans, g, b->pk, field,
+                                                               (double *)b->stage, to_fields);
+    else
+        kb_pack<float><<<b->pack_blocks, 256, 0, b->stream>>>((const StepPlan<float> *)b->plans, g, b->pk, field,
+                                                              (float *)b->stage, to_fields);
+    CK(cudaGetLastError());
+    return FARGO_OK;
+}
+
+static bool field_ok(const fargo_batch *b, int field)
+{
+    if (field < 0 || field > 4) return false;
+    for (const fargo_ctx *c : b->mem) {
+        if (field == FARGO_ENERGY && c->m.iso) return false;
+        if ((field == FARGO_VY && !c->m.hasY) || (field == FARGO_VZ && !c->m.hasZ)) return false;
+    }
+    return true;
+}
+
+extern "C" int fargo_batch_set_field_packed(fargo_batch *b, int field, const void *src, size_t bytes)
+{
+    if (!b || !src || !field_ok(b, field)) return FARGO_ERR_BADARG;
+    int rc = pack_setup(b);
+    if (rc) return rc;
+    if (bytes != b->packed_bytes) return FARGO_ERR_SIZE;
+    CK(cudaMemcpyAsync(b->stage, src, bytes, cudaMemcpyDefault, b->stream));
+    return pack_launch(b, field, 1);
+}
+
+extern "C" int fargo_batch_get_field_packed(fargo_batch *b, int field, void *dst, size_t bytes)
+{
+    if (!b || !dst || !field_ok(b, field)) return FARGO_ERR_BADARG;
+    int rc = pack_setup(b);
+    if (rc) return rc;
+    if (bytes != b->packed_bytes) return FARGO_ERR_SIZE;
+    if ((rc = pack_launch(b, field, 0))) return rc;
+    CK(cudaMemcpyAsync(dst, b->stage, bytes, cudaMemcpyDefault, b->stream));
     CK(cudaStreamSynchronize(b->stream));
     return FARGO_OK;
 }
@@ -776,5 +896,162 @@ extern "C" int fargo_batch_profile_step(fargo_batch *b, int max_kernels, float *
         b->steps++;
     }
     for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batch's launch shapes that leave every result unchanged:
+// the cells per thread of the per-cell phases (each cell runs the same body
+// whatever the grouping) and the segment length of the Y/Z sweeps (each
+// column marches the same arithmetic whatever the segmentation), the latter
+// set for every member.  Coordinate search: each candidate rebuilds the
+// launch sequence and is timed over `reps` profiled steps (per-launch CUDA
+// events, summed), every trial step starting from a device snapshot of the
+// members' states and times, which is restored at the end, so the run is
+// unchanged.  The paper's code searches block sizes per kernel in a similar
+// way (Sec. 4.2); the batch has no counterpart there.
+// ---------------------------------------------------------------------------
+namespace {
+struct BSnap {
+    std::vector<void *> dst;
+    std::vector<const void *> src;
+    std::vector<size_t> bytes;
+    void *mem = nullptr;
+};
+}  // namespace
+
+static int bsnap_copy(fargo_batch *b, BSnap &sn, bool save)
+{
+    for (size_t i = 0; i < sn.dst.size(); i++) {
+        void *to = save ? sn.dst[i] : const_cast<void *>(sn.src[i]);
+        const void *from = save ? sn.src[i] : sn.dst[i];
+        CK(cudaMemcpyAsync(to, from, sn.bytes[i], cudaMemcpyDeviceToDevice, b->stream));
+    }
+    return FARGO_OK;
+}
+
+static int bsnap_make(fargo_batch *b, BSnap &sn)
+{
+    size_t tot = 0;
+    std::vector<std::pair<const void *, size_t>> parts;
+    for (fargo_ctx *c : b->mem) {
+        const size_t nb = (size_t)c->m.ntot * c->esz;
+        void *f[5];
+        if (c->prec == FARGO_F64) {
+            const Fld<double> &A = c->b64.A;
+            f[0] = A.rho; f[1] = A.e; f[2] = A.vx; f[3] = A.vy; f[4] = A.vz;
+        } else {
+            const Fld<float> &A = c->b32.A;
+            f[0] = A.rho; f[1] = A.e; f[2] = A.vx; f[3] = A.vy; f[4] = A.vz;
+        }
+        for (int q = 0; q < 5; q++) {
+            if (q == 1 && c->m.iso) continue;
+            if ((q == 3 && !c->m.hasY) || (q == 4 && !c->m.hasZ)) continue;
+            parts.push_back({f[q], nb});
+            tot += (nb + 255) / 256 * 256;
+        }
+        parts.push_back({c->sc, sizeof(Scal)});
+        tot += 256;
+    }
+    CK(cudaMalloc(&sn.mem, tot));
+    size_t o = 0;
+    for (auto &p : parts) {
+        sn.src.push_back(p.first);
+        sn.dst.push_back((char *)sn.mem + o);
+        sn.bytes.push_back(p.second);
+        o += (p.second + 255) / 256 * 256;
+    }
+    return FARGO_OK;
+}
+
+// Rebuild the launch sequence (after a shape change) and drop the graph.
+static int batch_rebuild(fargo_batch *b)
+{
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    for (void *p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+    b->seq.clear();
+    return b->prec == FARGO_F64 ? batch_setup<double>(b) : batch_setup<float>(b);
+}
+
+// Summed device time (ms) of one profiled step, averaged over reps steps,
+// each from the snapshot.
+static int btime(fargo_batch *b, BSnap &sn, int reps, float *ms)
+{
+    std::vector<float> t(b->seq.size() + 1);
+    double tot = 0.0;
+    int rc;
+    for (int r = 0; r < reps; r++) {
+        if ((rc = bsnap_copy(b, sn, false))) return rc;
+        int n = 0;
+        if ((rc = fargo_batch_profile_step(b, (int)t.size(), t.data(), &n, nullptr))) return rc;
+        if (r == 0 && reps > 1) continue;   // warm-up
+        for (int i = 0; i < n; i++) tot += t[i];
+    }
+    *ms = (float)(tot / (reps > 1 ? reps - 1 : 1));
+    return FARGO_OK;
+}
+
+extern "C" int fargo_batch_autotune(fargo_batch *b, int reps, int *cfg, float *ms_default, float *ms_tuned)
+{
+    if (!b || reps < 2) return FARGO_ERR_BADARG;
+    BSnap sn;
+    int rc = bsnap_make(b, sn);
+    if (rc) return rc;
+    const long long steps0 = b->steps;
+    if ((rc = bsnap_copy(b, sn, true)) == FARGO_OK) {
+        const int cpt0 = b->cpt;
+        std::vector<int> seg0(b->n), segz0(b->n);
+        for (int i = 0; i < b->n; i++) {
+            seg0[i] = b->mem[i]->seg_y;
+            segz0[i] = b->mem[i]->seg_z;
+        }
+        float base = 0.f, best = 0.f;
+        rc = btime(b, sn, reps, &base);
+        best = base;
+        int best_cpt = cpt0, best_seg = -1;   // -1: the members' own segment settings
+        const int cpts[4] = {4, 8, 16, 32};
+        for (int k = 0; k < 4 && !rc; k++) {
+            if (cpts[k] == cpt0) continue;
+            b->cpt = cpts[k];
+            float t = 0.f;
+            if ((rc = batch_rebuild(b)) || (rc = btime(b, sn, reps, &t))) break;
+            if (t < best) {
+                best = t;
+                best_cpt = cpts[k];
+            }
+        }
+        b->cpt = best_cpt;
+        const int segs[5] = {0, 16, 32, 64, 128};
+        for (int k = 0; k < 5 && !rc; k++) {
+            for (fargo_ctx *c : b->mem) c->seg_y = c->seg_z = segs[k];
+            float t = 0.f;
+            if ((rc = batch_rebuild(b)) || (rc = btime(b, sn, reps, &t))) break;
+            if (t < best) {
+                best = t;
+                best_seg = segs[k];
+            }
+        }
+        for (int i = 0; i < b->n; i++) {
+            b->mem[i]->seg_y = best_seg >= 0 ? best_seg : seg0[i];
+            b->mem[i]->seg_z = best_seg >= 0 ? best_seg : segz0[i];
+        }
+        if (!rc) rc = batch_rebuild(b);
+        const int rc2 = bsnap_copy(b, sn, false);
+        if (!rc) rc = rc2;
+        if (cfg) {
+            cfg[0] = b->cpt;
+            cfg[1] = best_seg;
+        }
+        if (ms_default) *ms_default = base;
+        if (ms_tuned) *ms_tuned = best;
+    }
+    cudaStreamSynchronize(b->stream);
+    b->steps = steps0;
+    cudaFree(sn.mem);
     return rc;
 }

@@ -6,13 +6,15 @@
 namespace fk {
 
 enum { CART = 0, CYL = 1, SPH = 2 };
-enum { BC_REFLECT = 0, BC_FROZEN = 1, BC_ZEROGRAD = 2 };
+enum { BC_REFLECT = 0, BC_FROZEN = 1, BC_ZEROGRAD = 2, BC_PERIODIC = 3 };
 
 // Mesh description and run constants, passed by value to every kernel.
 struct MeshD {
     int nx, nyt, nzt, gy, gz, j0, j1, k0, k1, g;
     int hasX, hasY, hasZ, geom, iso, fargo, av_lit, has_nu, has_planet, indirect, has_star, has_av;
     int bcy[2], bcz[2];
+    int pery, perz;              // periodic Y / Z (both sides)
+    int jf, kf;                  // first interior Y / Z face: j0 + 1 and k0 + 1, or j0 / k0 when periodic
     int sj, sk;                  // row pitch, plane stride (elements)
     long long ntot;              // elements per field (below 2^31, checked at creation)
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;

@@ -17,6 +17,15 @@ __device__ void fill_line(T *a, idx_t base, idx_t stride, int lo, int hi, int g,
                           int bc)
 {
     if (bc == BC_FROZEN) return;
+    if (bc == BC_PERIODIC) {
+        // ghosts hold the values one period away; the upper normal face hi is face lo
+        const int n = hi - lo;
+        if (side == 0)
+            for (int mm = 1; mm <= g; mm++) a[base + (lo - mm) * stride] = a[base + (lo - mm + n) * stride];
+        else
+            for (int mm = 0; mm < g + (normal ? 1 : 0); mm++) a[base + (hi + mm) * stride] = a[base + (lo + mm) * stride];
+        return;
+    }
     if (!normal) {
         for (int mm = 0; mm < g; mm++) {
             int dst = side == 0 ? lo - 1 - mm : hi + mm;
@@ -85,6 +94,109 @@ __device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const
         if (j >= jmax) continue;
         fill_line(fl[q], j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Periodic images between the sub-steps: on a periodic axis every value read
+// across the boundary is the value one period away, so after a sub-step or a
+// sweep changes values next to the boundary, the ghosts that mirror them are
+// rewritten (the fills of cells 2 and 9 cover the other boundaries).  Up to
+// eight arrays, each with its own source (dst ghosts <- src active values,
+// the same array or the one a later kernel reads its ghosts from) and its
+// staggering (face-centred along Y for v_y, along Z for v_z).  One thread per
+// (azimuth, transverse index, side, array); Y before Z, so that the Z
+// images copy rows whose Y ghosts are already filled.  Skipped on void steps.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PerSet {
+    T *dst[8];
+    const T *src[8];
+    unsigned char fy[8], fz[8];   // face-centred along Y / along Z
+    int n;
+};
+
+template <typename T>
+__global__ void k_periodic(MeshD m, PerSet<T> p, const Scal *sc, int axis)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ntr = axis == 1 ? m.nzt + 1 : m.nyt + 1;
+    const long long n = (long long)m.nx * ntr * 2 * p.n;
+    if (tid >= n || !(sc->dt > 0.0)) return;
+    const int i = (int)(tid % m.nx);
+    long long r = tid / m.nx;
+    const int t = (int)(r % ntr);
+    r /= ntr;
+    const int side = (int)(r % 2), a = (int)(r / 2);
+    T *dst = p.dst[a];
+    const T *src = p.src[a];
+    if (axis == 1) {
+        if (t >= (p.fz[a] ? m.nzt + 1 : m.nzt)) return;
+        const idx_t base = t * m.sk + i;
+        const int lo = m.j0, hi = m.j1, len = hi - lo;
+        if (side == 0)
+            for (int mm = 1; mm <= m.g; mm++) dst[base + (lo - mm) * m.sj] = src[base + (lo - mm + len) * m.sj];
+        else
+            for (int mm = 0; mm < m.g + p.fy[a]; mm++) dst[base + (hi + mm) * m.sj] = src[base + (lo + mm) * m.sj];
+    } else {
+        if (t >= (p.fy[a] ? m.nyt + 1 : m.nyt)) return;
+        const idx_t base = t * m.sj + i;
+        const int lo = m.k0, hi = m.k1, len = hi - lo;
+        if (side == 0)
+            for (int mm = 1; mm <= m.g; mm++) dst[base + (lo - mm) * m.sk] = src[base + (lo - mm + len) * m.sk];
+        else
+            for (int mm = 0; mm < m.g + p.fz[a]; mm++) dst[base + (hi + mm) * m.sk] = src[base + (lo + mm) * m.sk];
+    }
+}
+
+// Queue the images of p on the periodic axes among `axes` (bit 0 = Y, bit 1 = Z).
+template <typename T>
+static int launch_periodic(const MeshD &m, const PerSet<T> &p, const Scal *sc, cudaStream_t s, int axes = 3)
+{
+    int nl = 0;
+    if ((axes & 1) && m.pery) {
+        const long long n = (long long)m.nx * (m.nzt + 1) * 2 * p.n;
+        k_periodic<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, p, sc, 1);
+        nl++;
+    }
+    if ((axes & 2) && m.perz) {
+        const long long n = (long long)m.nx * (m.nyt + 1) * 2 * p.n;
+        k_periodic<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, p, sc, 2);
+        nl++;
+    }
+    return nl;
+}
+
+// Image sets of the common cases: the velocities (and e) of a field set, a
+// quantity set (every member cell-centred), the diagonal viscous stresses.
+template <typename T>
+static PerSet<T> per_fields(const MeshD &m, const Fld<T> &f, bool vel, bool energy)
+{
+    PerSet<T> p{};
+    auto add = [&](T *a, int fy, int fz) {
+        p.dst[p.n] = a;
+        p.src[p.n] = a;
+        p.fy[p.n] = (unsigned char)fy;
+        p.fz[p.n] = (unsigned char)fz;
+        p.n++;
+    };
+    if (vel) {
+        add(f.vx, 0, 0);
+        if (m.hasY) add(f.vy, 1, 0);
+        if (m.hasZ) add(f.vz, 0, 1);
+    }
+    if (energy && !m.iso) add(f.e, 0, 0);
+    return p;
+}
+template <typename T>
+static PerSet<T> per_quantities(const QSet<T> &dst, const QSet<T> &src)
+{
+    PerSet<T> p{};
+    for (int q = 0; q < dst.nq; q++) {
+        p.dst[q] = dst.q[q];
+        p.src[q] = src.q[q];
+    }
+    p.n = dst.nq;
+    return p;
 }
 
 template <typename T>
@@ -456,10 +568,12 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
     if (warp == 0 && lane < 8 && m.fargo && m.hasY && !skip) {
         const int r = ch * 8 + lane;
         const int ny = m.j1 - m.j0;
-        if (r < nrings && r % ny < ny - 1) {
+        // (on a periodic Y axis the last ring's outer neighbour is the first)
+        if (r < nrings && (r % ny < ny - 1 || m.pery)) {
             const int ring = (m.k0 + r / ny) * m.nyt + m.j0 + r % ny;
+            const int next = r % ny < ny - 1 ? ring + 1 : ring - (ny - 1);
             const double *om = v0 + (size_t)m.nyt * m.nzt;
-            wsh = fmax(wsh, fabs(__dsub_rn(__ldcg(&om[ring]), __ldcg(&om[ring + 1]))));
+            wsh = fmax(wsh, fabs(__dsub_rn(__ldcg(&om[ring]), __ldcg(&om[next]))));
         }
     }
     }

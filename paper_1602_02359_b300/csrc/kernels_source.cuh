@@ -96,7 +96,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     }
     if (k < m.nzt) {
         T v = in.vy[c];
-        if (F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
+        if (F::hasY(m) && j >= m.jf && j < m.j1 && kact) {
             const idx_t cm = c - m.sj;
             const T id = tb.idyc[j];
             const T P0 = pressure<T, F>(m, tb, in, c, ring), Pm = pressure<T, F>(m, tb, in, cm, ring - 1);
@@ -128,7 +128,7 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     }
     if (F::hasZ(m) && j < m.nyt) {
         T v = in.vz[c];
-        if (k > m.k0 && k < m.k1 && jact) {
+        if (k >= m.kf && k < m.k1 && jact) {
             const idx_t cm = c - m.sk;
             const int rm = ring - m.nyt;
             const T id = tb.idzc[ring];
@@ -196,7 +196,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     }
     if (k < m.nzt) {
         T v = vy[c];
-        if (av && F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
+        if (av && F::hasY(m) && j >= m.jf && j < m.j1 && kact) {
             const idx_t cm = c - sj;
             const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
             const T qm = qvisc(c2, rho[cm], vy[c] - vy[cm]);
@@ -207,7 +207,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     }
     if (F::hasZ(m) && j < m.nyt) {
         T v = vz[c];
-        if (av && k > m.k0 && k < m.k1 && jact) {
+        if (av && k >= m.kf && k < m.k1 && jact) {
             const idx_t cm = c - sk;
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
             const T qm = qvisc(c2, rho[cm], vz[c] - vz[cm]);
@@ -250,7 +250,8 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     const int fr = k * (m.nyt + 1) + j;
     if (F::hasY(m)) {
         T vyu = vy[c + sj];
-        if (av && j + 1 < m.j1) {
+        // (on a periodic axis face j1 is face j0, an interior face)
+        if (av && (j + 1 < m.j1 || m.pery)) {
             const T qp = qvisc(c2, rho[c + sj], vy[c + 2 * sj] - vy[c + sj]);
             const T q0 = qvisc(c2, rho[c], vy[c + sj] - vy[c]);
             vyu -= div_fast(dt * T(2) * (qp - q0) * tb.idyc[j + 1], rho[c + sj] + rho[c]);
@@ -259,7 +260,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     }
     if (F::hasZ(m)) {
         T vzu = vz[c + sk];
-        if (av && k + 1 < m.k1) {
+        if (av && (k + 1 < m.k1 || m.perz)) {
             const T qp = qvisc(c2, rho[c + sk], vz[c + 2 * sk] - vz[c + sk]);
             const T q0 = qvisc(c2, rho[c], vz[c + sk] - vz[c]);
             vzu -= div_fast(dt * T(2) * (qp - q0) * tb.idzc[ring + m.nyt], rho[c + sk] + rho[c]);
@@ -436,7 +437,7 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
     }
     if (k < m.nzt) {
         T v = in.vy[c];
-        if (F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
+        if (F::hasY(m) && j >= m.jf && j < m.j1 && kact) {
             const idx_t cjm = c - m.sj;
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);
@@ -466,7 +467,7 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
     }
     if (F::hasZ(m) && j < m.nyt) {
         T v = in.vz[c];
-        if (k > m.k0 && k < m.k1 && jact) {
+        if (k >= m.kf && k < m.k1 && jact) {
             const idx_t ckm = c - m.sk;
             T a0, a1, a2, b0, b1, b2;
             V.diag(i, j, k, a0, a1, a2);

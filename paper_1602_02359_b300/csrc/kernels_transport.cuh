@@ -1172,7 +1172,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
         }
     }
     if (k < m.nzt) {
-        if (F::hasY(m) && j > m.j0 && j < m.j1 && kact) {
+        if (F::hasY(m) && j >= m.jf && j < m.j1 && kact) {
             const idx_t cm = c - m.sj;
             state.vy[c] = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
         } else if (vsrc.vy != state.vy) {
@@ -1180,7 +1180,7 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
         }
     }
     if (F::hasZ(m) && j < m.nyt) {
-        if (k > m.k0 && k < m.k1 && jact) {
+        if (k >= m.kf && k < m.k1 && jact) {
             const idx_t cm = c - m.sk;
             state.vz[c] = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
         } else if (vsrc.vz != state.vz) {

@@ -37,6 +37,11 @@ CASES = [
     # rings too long for two FP64 staging buffers: the ring kernels stage
     # one ring at a time
     (W.CYL, 4000, 6, 1, True, 1e-3, W.BC_FROZEN),
+    # periodic boundaries: a Cartesian box periodic in Y and Z, a 2D one in
+    # Y, a cylinder periodic in z (frozen radial walls)
+    (W.CART, 37, 21, 9, False, 1e-3, W.BC_PERIODIC),
+    (W.CART, 33, 20, 1, True, 1e-3, W.BC_PERIODIC),
+    (W.CYL, 41, 17, 12, False, 1e-3, W.BC_PERIODIC),
 ]
 IDS = [f"g{c[0]}-{c[1]}x{c[2]}x{c[3]}-{'iso' if c[4] else 'adi'}-nu{c[5]}-bc{c[6]}" for c in CASES]
 
@@ -44,6 +49,10 @@ IDS = [f"g{c[0]}-{c[1]}x{c[2]}x{c[3]}-{'iso' if c[4] else 'adi'}-nu{c[5]}-bc{c[6
 def box(case, seed=1):
     geom, nx, ny, nz, iso, nu, bc = case
     w = W.random_box(geom, nx, ny, nz, g=3, seed=seed, iso=iso, nu=nu, planet=(geom != W.CART), bc=bc)
+    if bc == W.BC_PERIODIC:
+        if geom != W.CART:
+            w.bc_y = (W.BC_FROZEN, W.BC_FROZEN)    # only z is periodic in a cylinder
+        W.periodic_tables(w)
     return w
 
 
@@ -305,6 +314,45 @@ def test_keplerian_vortex_fp64_steps(fargo):
         else:
             assert abs(dt_g - dt_o) <= 1e-12 * dt_o, (n, dt_g, dt_o)
     compare_state(w, c.get_state(), st, 1e-11)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[6] == W.BC_PERIODIC and c[0] == W.CART],
+                         ids=[i for c, i in zip(CASES, IDS) if c[6] == W.BC_PERIODIC and c[0] == W.CART])
+def test_periodic_box_conserves_mass_on_the_gpu(case):
+    """Periodic boundaries take and give no mass: 20 FP64 steps keep the
+    total within round-off, as in the oracle."""
+    w = box(case, seed=12)
+    c = make_ctx(w)
+    m0 = c.sums()[0]
+    for _ in range(20):
+        c.step(want_dt=False)
+    assert c.scalars()[3] == 0
+    assert abs(c.sums()[0] - m0) <= 2e-14 * m0
+
+
+def test_periodic_boundary_rules_are_enforced():
+    """Periodic on one side only, on a spherical or cylindrical radius, or
+    with ghost widths that differ from their images is refused."""
+    import paper_1602_02359_b300 as fb
+    w = box(CASES[-3])
+    w.bc_y = (W.BC_PERIODIC, W.BC_FROZEN)
+    with pytest.raises(fb.FargoError) as e:
+        fb.Fargo(w)
+    assert e.value.code == -1
+    w = W.random_box(W.CYL, 16, 12, 1, g=3, seed=1, bc=W.BC_PERIODIC)
+    with pytest.raises(fb.FargoError):
+        fb.Fargo(w)
+    w = box(CASES[-3])
+    w.yf = w.yf.copy()
+    w.yf[0] -= 0.01                      # a ghost wider than its image
+    with pytest.raises(fb.FargoError):
+        fb.Fargo(w)
+    w = box(CASES[-3])
+    w.nu = w.nu.copy()
+    w.nu[:, 0] *= 2.0                    # a ghost ring's viscosity unlike its image's
+    with pytest.raises(fb.FargoError):
+        fb.Fargo(w)
+    fb.Fargo(box(CASES[-3])).close()
 
 
 def test_fp32_disk_within_stated_tolerance():

@@ -68,3 +68,38 @@ def test_bounded_wait_reports_a_timeout_and_the_device_stays_usable():
     c = make_ctx(W.disk2d(nx=96, ny=32), fb.F64)
     dt = c.step()
     assert dt > 0 and c.scalars()[3] == 0
+
+
+def test_batch_autotune_leaves_the_run_unchanged():
+    """The batch autotuner changes the per-cell grouping and the sweep
+    segments of a batch of unequal disks, results-invariant shapes: after
+    tuning, the members' states and times are those before it, and steps
+    from there agree bit for bit with an untuned batch's."""
+    import paper_1602_02359_b300 as fb
+    ps = W.batch_params(n=6, seed=5)
+    ps = [dict(p, ny=p["ny"] // 4, nx=3 * (p["ny"] // 4)) for p in ps]
+    ws = [W.batch_instance(p) for p in ps]
+    ca = [make_ctx(w, fb.F32, t=0.0, t_end=w.t_end) for w in ws]
+    cb = [make_ctx(w, fb.F32, t=0.0, t_end=w.t_end) for w in ws]
+    A, B = fb.FargoBatch(ca), fb.FargoBatch(cb)
+    A.step()
+    B.step()
+    cfg, ms0, ms1 = A.autotune(reps=2)
+    assert cfg["cells_per_thread"] in (4, 8, 16, 32) and cfg["segment"] in (-1, 0, 16, 32, 64, 128)
+    assert 0 < ms1 <= ms0
+    A.status()
+    for x, y in zip(ca, cb):
+        assert x.scalars() == y.scalars()
+        for k, v in x.get_state().items():
+            assert np.array_equal(v, y.get_state()[k]), k
+    for _ in range(3):
+        A.step(sync=False)
+        B.step(sync=False)
+    A.status()
+    B.status()
+    for x, y in zip(ca, cb):
+        assert x.scalars() == y.scalars()
+        for k, v in x.get_state().items():
+            assert np.array_equal(v, y.get_state()[k]), k
+    A.close()
+    B.close()
