@@ -206,14 +206,15 @@ __device__ __forceinline__ void ring_bars_init(uint64_t *bar)
 // velocity is delta v = v_x - v0 (v0 = 0 for STANDARD transport).  Ghost
 // rings only get their momenta written (the Y/Z sweeps read them).
 struct TxRows {
-    int n, rE, rVX, rVY, rVZ;   // staged rows: rho, e, vx, vy(j), vy(j+1), vz(k), vz(k+1)
+    int n, rE, rVX, rVY, rVZ, rDX;   // staged rows: rho, e, vx, vy(j), vy(j+1), vz(k), vz(k+1), v_x increment
 };
-__device__ __forceinline__ TxRows tx_rows(const MeshD &m)
+__device__ __host__ __forceinline__ TxRows tx_rows(const MeshD &m, bool dx = false)
 {
-    TxRows r{0, -1, -1, -1, -1};
+    TxRows r{0, -1, -1, -1, -1, -1};
     r.n = 1;
     if (!m.iso) r.rE = r.n++;
     r.rVX = r.n++;
+    if (dx) r.rDX = r.n++;
     if (m.hasY) {
         r.rVY = r.n;
         r.n += 2;
@@ -242,7 +243,7 @@ __device__ __forceinline__ void tx_v0(const MeshD &m, const double *v0, int ring
 template <typename T>
 __device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int ring, T *dst, uint64_t *bar)
 {
-    const TxRows r = tx_rows(m);
+    const TxRows r = tx_rows(m, in.dx != nullptr);
     const int j = ring % m.nyt, k = ring / m.nyt;
     const idx_t base = IX(m, 0, j, k);
     const size_t rp = (size_t)ring_row(m.sj);
@@ -252,6 +253,7 @@ __device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int r
     bulk_load(dst, in.rho + base, bytes, bar);
     if (r.rE >= 0) bulk_load(dst + r.rE * rp, in.e + base, bytes, bar);
     bulk_load(dst + r.rVX * rp, in.vx + base, bytes, bar);
+    if (r.rDX >= 0) bulk_load(dst + r.rDX * rp, in.dx + base, bytes, bar);
     if (r.rVY >= 0) {
         bulk_load(dst + r.rVY * rp, in.vy + base, bytes, bar);
         bulk_load(dst + (r.rVY + 1) * rp, in.vy + base + m.sj, bytes, bar);
@@ -264,10 +266,10 @@ __device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int r
 
 template <typename T, int C>
 __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &out, int ring, T *buf,
-                                           T v0hi, T v0lo, T dt)
+                                           T v0hi, T v0lo, T dt, bool hasdx)
 {
     const int nx = m.nx, nq = out.nq, rp = ring_row(m.sj);
-    const TxRows rw = tx_rows(m);
+    const TxRows rw = tx_rows(m, hasdx);
     ring_frame(buf, rw.n, rp, nx);
     const T *sm = buf + kRingLead;   // cell i of staged row r: sm[r * rp + i], -kRingLead <= i < nx + kRingTail
     const int j = ring % m.nyt, k = ring / m.nyt;
@@ -278,37 +280,44 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     // the frame term of the X momentum: R^2 Omega_f, or the Cartesian table (shearing sheet)
     const T R = tb.R[ring], w = m.geom == CART ? tb.wfr[ring] : R * R * tb.omega, fz = tb.fz[ring];
     const T *Rho = sm, *Vx = sm + (size_t)rw.rVX * rp;
-    // ratio of quantity q to the density at cell i, as scale * row[i + off] +
-    // shift (or e / rho), for the order rho, e, Pi-x, Pi+x, Pi-y, Pi+y,
-    // Pi-z, Pi+z of the present components
+    const T *Dx = hasdx ? sm + (size_t)rw.rDX * rp : nullptr;   // v_x increment of the source step
+    // ratio of quantity q to the density at cell i, as scale * (row[i + off]
+    // + inc[i + off]) + shift (or e / rho), for the order rho, e, Pi-x, Pi+x,
+    // Pi-y, Pi+y, Pi-z, Pi+z of the present components
     struct RatioSpec {
-        const T *row;
+        const T *row, *inc;
         int off, div;
         T a, b;
     };
     auto spec = [&](int q) -> RatioSpec {
-        if (q == 0) return {Rho, 0, 0, T(1), T(0)};
+        if (q == 0) return {Rho, nullptr, 0, 0, T(1), T(0)};
         int o = q - 1;
         if (adi) {
-            if (o == 0) return {sm + (size_t)rw.rE * rp, 0, 1, T(1), T(0)};
+            if (o == 0) return {sm + (size_t)rw.rE * rp, nullptr, 0, 1, T(1), T(0)};
             o -= 1;
         }
-        if (o == 0) return {Vx, 0, 0, R, w};
-        if (o == 1) return {Vx, 1, 0, R, w};
+        if (o == 0) return {Vx, Dx, 0, 0, R, w};
+        if (o == 1) return {Vx, Dx, 1, 0, R, w};
         if (m.hasY) {
-            if (o == 2) return {sm + (size_t)rw.rVY * rp, 0, 0, T(1), T(0)};
-            if (o == 3) return {sm + (size_t)(rw.rVY + 1) * rp, 0, 0, T(1), T(0)};
+            if (o == 2) return {sm + (size_t)rw.rVY * rp, nullptr, 0, 0, T(1), T(0)};
+            if (o == 3) return {sm + (size_t)(rw.rVY + 1) * rp, nullptr, 0, 0, T(1), T(0)};
             o -= 2;
         }
-        if (o == 2) return {sm + (size_t)rw.rVZ * rp, 0, 0, fz, T(0)};
-        return {sm + (size_t)(rw.rVZ + 1) * rp, 0, 0, fz, T(0)};
+        if (o == 2) return {sm + (size_t)rw.rVZ * rp, nullptr, 0, 0, fz, T(0)};
+        return {sm + (size_t)(rw.rVZ + 1) * rp, nullptr, 0, 0, fz, T(0)};
+    };
+    // the ratio of the momenta: R (v + dv) + w, the increment added to the
+    // product of the stored value so that it is not absorbed in v first
+    auto ratio = [](const RatioSpec &sp, T v, int at) -> T {
+        const T r = sp.a * v + sp.b;
+        return sp.inc ? r + sp.a * sp.inc[at] : r;
     };
     if (!sweep) {
         for (int q = 0; q < nq; q++) {
             const RatioSpec sp = spec(q);
             for (int i = threadIdx.x; i < nx; i += blockDim.x) {
                 const T v = sp.row[i + sp.off];
-                out.q[q][base + i] = q == 0 ? v : (sp.div ? v : Rho[i] * (sp.a * v + sp.b));
+                out.q[q][base + i] = q == 0 ? v : (sp.div ? v : Rho[i] * ratio(sp, v, i + sp.off));
             }
         }
         return;
@@ -321,7 +330,10 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     const int cnt = min(C, nx - i0);
     T vf[C + 1], F0[C + 1];
 #pragma unroll
-    for (int u = 0; u <= C; u++) vf[u] = sub_split(Vx[i0 + u], v0hi, v0lo);
+    for (int u = 0; u <= C; u++) {
+        vf[u] = sub_split(Vx[i0 + u], v0hi, v0lo);
+        if (Dx) vf[u] += Dx[i0 + u];
+    }
     T rho[C + 4];
 #pragma unroll
     for (int s = 0; s < C + 4; s++) rho[s] = Rho[i0 - 2 + s];
@@ -336,7 +348,7 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
 #pragma unroll
         for (int s = 0; s < C + 4; s++) {
             const T v = win[s];
-            a[s] = sp.div ? v / rho[s] : sp.a * v + sp.b;
+            a[s] = sp.div ? v / rho[s] : ratio(sp, v, i0 - 2 + sp.off + s);
         }
         T sl[C + 2];  // van Leer slopes of cells i0-1 .. i0+C
 #pragma unroll
@@ -353,7 +365,8 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
 #pragma unroll
         for (int u = 0; u < C; u++)
             if (u < cnt) {
-                const T old = q == 0 ? a[u + 2] : rho[u + 2] * a[u + 2];
+                // the stored value itself for e; the momenta are formed here (Eqs. 16-17)
+                const T old = q == 0 ? a[u + 2] : (sp.div ? win[u + 2] : rho[u + 2] * a[u + 2]);
                 out.q[q][base + i0 + u] = old - dtVi * (F[u + 1] - F[u]);
             }
     }
@@ -649,7 +662,7 @@ struct TxOp {
     __device__ void issue(int it, T *dst, uint64_t *bar) { tx_issue(m, in, meta[it].local, dst, bar); }
     __device__ void compute(int it, T *src)
     {
-        tx_compute<T, C>(m, tb, out, meta[it].local, src, meta[it].a, meta[it].b, dt);
+        tx_compute<T, C>(m, tb, out, meta[it].local, src, meta[it].a, meta[it].b, dt, in.dx != nullptr);
     }
     __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
 };
@@ -974,7 +987,11 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
     auto width = [&](int d) -> T { return AXIS == 1 ? tb.dy[d] : tb.lenz[d * m.nyt + c2]; };
     auto area = [&](int f) -> T { return AXIS == 1 ? tb.sy[c2 * (m.nyt + 1) + f] : tb.sz[f * (m.nyt + 1) + c2]; };
     bool ok = true;
-    // fetch row r into ratios + face velocity, then release the stage
+    // fetch row r into ratios + face velocity; the stage is released by
+    // release(r) once the row is no longer needed: after the first fluxes for
+    // the two rows below the segment, after its own update for a row of the
+    // segment (which reads the quantities themselves from the stage, so that
+    // the update starts from the stored value and not from ratio x density)
     auto fetch = [&](int r, T *rat, T &vface) {
         const int slot = r % S;
         if (!mbar_wait(&full[slot], (r / S) & 1)) {
@@ -988,8 +1005,10 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
 #pragma unroll
         for (int q = 1; q < NQ; q++) rat[q] = src[q * TW] * ri;
         vface = src[NQ * TW];
+    };
+    auto release = [&](int r) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (lane == 0) mbar_arrive(&empty[r % S]);
     };
     T Rm2[NQ], Rm1[NQ], R0[NQ], R1[NQ], R2[NQ], aP[NQ], Flo[NQ];
     T vm2, vm1, v0f, v1f, v2f;
@@ -1020,14 +1039,17 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
             Flo[q] = q == 0 ? F0 : F0 * stv;
         }
     }
+    release(0);
+    release(1);
     for (int p = ps; p < pe; p++) {
         const T v = v1f;   // face p+1
         const T dn = icd(p + 1), dnn = icd(p + 2);
         const T wp = width(p), wn = width(p + 1);
         const T Sa = area(p + 1);
         const T dtVi = dt * tb.vinv[ring_of(p)];
-        const T rho = R0[0];
         const idx_t c = base + p * st;
+        const int rp = p - ps + 2;   // row index of p
+        const T *raw = stage + (size_t)(rp % S) * ROW + threadIdx.x;
         T F0 = 0;
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
@@ -1035,11 +1057,11 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
             const T stv = v >= T(0) ? R0[q] + aP[q] * (wp - v * dt) * T(0.5) : R1[q] - aN * (wn + v * dt) * T(0.5);
             if (q == 0) F0 = v * stv * Sa;
             const T Fup = q == 0 ? F0 : F0 * stv;
-            const T Q = q == 0 ? rho : R0[q] * rho;
-            if (col) out.q[q][c] = Q - dtVi * (Fup - Flo[q]);
+            if (col) out.q[q][c] = raw[q * TW] - dtVi * (Fup - Flo[q]);
             Flo[q] = Fup;
             aP[q] = aN;
         }
+        release(rp);
         if (p + 1 < pe) {
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
@@ -1163,6 +1185,8 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
             // divisions, not reciprocal products: v_x is rebuilt from R v_x every
             // step, and a rounded 1/R would bias it by R (1/R) - 1 each time
             state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
+        } else if (vsrc.dx) {
+            state.vx[c] = vsrc.vx[c] + vsrc.dx[c];   // the post-source value of a ghost ring's face
         } else if (vsrc.vx != state.vx) {
             state.vx[c] = vsrc.vx[c];
         }
