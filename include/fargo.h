@@ -19,6 +19,13 @@
  *        face of the last ghost cell (staggered mesh, Sec. 2.3).
  *    Scalars (density, energy) are cell centred; velocity component v_d sits
  *    on the lower d-face of its cell.
+ *  - FP32 contexts hold the azimuthal velocity internally as v_x - vref,
+ *    with one reference vref per ring (the ring's mid-range when v_x is
+ *    set, or 0 where that would not be exact), so that the slow changes of
+ *    a nearly Keplerian flow are not rounded away against |v_x| ~ v_K.  The
+ *    field calls convert: v_x is written and read as v_x itself.  Writing
+ *    v_x (any region) chooses the references afresh; the values of rings
+ *    outside the written region are kept (rounded once to FP32).
  *  - A context is thread-compatible, not thread-safe.  Work is queued on the
  *    stream given at creation (NULL = the legacy default stream).
  *  - Errors found on the device (non-finite state, Courant step not
@@ -326,7 +333,10 @@ int fargo_debug_phase(fargo_ctx *ctx, int phase, double dt);
 
 /* Auxiliary arrays: which = 0..5 momenta Pi-_x, Pi+_x, Pi-_y, Pi+_y, Pi-_z,
  * Pi+_z (FULL region, context precision); 6 = v0 per ring (nz_t*ny_t FP64).
- * Host buffers.  Errors: BADARG, SIZE, CUDA. */
+ * In an FP32 context the X momenta are held as Pi - rho (R vref + w), w the
+ * frame term of Tab. "momenta" (R^2 Omega_f, or 2 Omega_f y on the shearing
+ * sheet), and are exchanged in that form.  Host buffers.  Errors: BADARG,
+ * SIZE, CUDA. */
 int fargo_get_aux(fargo_ctx *ctx, int which, void *dst, size_t bytes);
 int fargo_set_aux(fargo_ctx *ctx, int which, const void *src, size_t bytes);
 

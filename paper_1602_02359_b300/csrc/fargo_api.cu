@@ -300,9 +300,47 @@ static int build_tables(fargo_ctx *c, Tab<T> &t)
         if ((rc = dalloc(c, &q, sizeof(T) * kPotPlanets))) return rc;
         t.mq = (T *)q;
     }
+    if (sizeof(T) == 4) {
+        // the reference form of v_x: per-ring references (zero until v_x is
+        // set) and the X momenta's frame shifts, filled by vref_refresh
+        const size_t nr = (size_t)nyt * nzt;
+        void *q;
+        if ((rc = dalloc(c, &q, sizeof(T) * nr))) return rc;
+        t.vref = (T *)q;
+        if ((rc = dalloc(c, &q, sizeof(double) * nr))) return rc;
+        t.vrefd = (double *)q;
+        if ((rc = dalloc(c, &q, sizeof(T) * nr))) return rc;
+        t.dAy = (T *)q;
+        if ((rc = dalloc(c, &q, sizeof(T) * nr))) return rc;
+        t.dAz = (T *)q;
+    }
 #undef UP
 #undef UPD
     return FARGO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reference form of v_x (FP32 contexts; see Tab::vref).  vref_launch runs one
+// mode of k_vref over every ring; the state's v_x goes to v_x form before a
+// field write (VREF_ABS in place), and back to the reference form after it
+// with references chosen afresh (vref_refresh: VREF_CHOOSE, then VREF_APPLY).
+// ---------------------------------------------------------------------------
+template <typename T>
+static int vref_launch(fargo_ctx *c, Buffers<T> &b, int mode, T *dst, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (!b.tab.vref) return FARGO_OK;
+        const int nr = c->m.nyt * c->m.nzt;
+        k_vref<T><<<(nr + 7) / 8, 256, 0, s>>>(c->m, b.tab, b.A.vx, dst ? dst : b.A.vx, mode);
+        CK(cudaGetLastError());
+    }
+    return FARGO_OK;
+}
+template <typename T>
+static int vref_refresh(fargo_ctx *c, Buffers<T> &b, cudaStream_t s)
+{
+    int rc = vref_launch<T>(c, b, VREF_CHOOSE, nullptr, s);
+    return rc ? rc : vref_launch<T>(c, b, VREF_APPLY, nullptr, s);
 }
 
 template <typename T>
@@ -326,7 +364,8 @@ static int alloc_fields(fargo_ctx *c, Buffers<T> &b)
         if ((rc = dalloc(c, &p, n))) return rc;
         b.dx2 = (T *)p;
     }
-    return build_tables<T>(c, b.tab);
+    int rc2 = build_tables<T>(c, b.tab);
+    return rc2 ? rc2 : vref_refresh<T>(c, b, c->stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,8 +400,8 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     } while (0)
     const dim3 cb = cell_block(m, c->cell_bs), cg = cell_grid_all(m, c->cell_bs);
     // cell 2
-    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_y"); }
-    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0); MARK("bc_z"); }
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0, P.tb.vref); MARK("bc_y"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0, P.tb.vref); MARK("bc_z"); }
     // cells 3-6
     k_cfl_screen<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_screen");
@@ -392,8 +431,8 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         PERIODIC(per_fields<T>(m, P.VB, true, false), "periodic");
     }
     // cell 9
-    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_y9"); }
-    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1); MARK("bc_z9"); }
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1, P.tb.vref); MARK("bc_y9"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1, P.tb.vref); MARK("bc_z9"); }
     // cell 12
     launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_rs, s);
     MARK("transport_x");
@@ -748,6 +787,21 @@ static int copy_region(fargo_ctx *c, void *dev, void *host, int region, size_t b
 int fargo_queue_field(fargo_ctx *c, int field, int region, void *buf, size_t bytes, int to_dev, cudaStream_t s)
 {
     if (!c || !buf || field < 0 || field > 4) return FARGO_ERR_BADARG;
+    if (c->prec == FARGO_F32 && field == FARGO_VX) {
+        // v_x crosses the boundary in v_x form (the stored values are v_x - vref)
+        Buffers<float> &b = c->b32;
+        int rc;
+        if (to_dev) {
+            if ((rc = vref_launch<float>(c, b, VREF_ABS, nullptr, s))) return rc;
+            if ((rc = queue_region(c, b.A.vx, buf, region, bytes, 1, s))) return rc;
+            return vref_refresh<float>(c, b, s);
+        }
+        // through the scratch increment buffer (free between steps); the copy
+        // first brings the rows that belong to no ring
+        CK(cudaMemcpyAsync(b.vB[0], b.A.vx, (size_t)c->m.ntot * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if ((rc = vref_launch<float>(c, b, VREF_ABS, b.vB[0], s))) return rc;
+        return queue_region(c, b.vB[0], buf, region, bytes, 0, s);
+    }
     return queue_region(c, field_ptr(c, field), buf, region, bytes, to_dev, s);
 }
 
@@ -755,14 +809,20 @@ extern "C" int fargo_set_field(fargo_ctx *c, int field, int region, const void *
 {
     (void)on_device;
     if (!c || !src || field < 0 || field > 4) return FARGO_ERR_BADARG;
-    return copy_region(c, field_ptr(c, field), (void *)src, region, bytes, 1);
+    const int rc = fargo_queue_field(c, field, region, (void *)src, bytes, 1, c->stream);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
 }
 
 extern "C" int fargo_get_field(fargo_ctx *c, int field, int region, void *dst, size_t bytes, int on_device)
 {
     (void)on_device;
     if (!c || !dst || field < 0 || field > 4) return FARGO_ERR_BADARG;
-    return copy_region(c, field_ptr(c, field), dst, region, bytes, 0);
+    const int rc = fargo_queue_field(c, field, region, dst, bytes, 0, c->stream);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
 }
 
 static int read_scal(fargo_ctx *c, Scal *s)
@@ -869,6 +929,7 @@ static int sums_impl(fargo_ctx *c, Buffers<T> &b, double out[3])
     SumInput<T> in{b.A.rho, m.iso ? nullptr : b.A.e, b.A.vx, c->vol, b.tab.Rd, m.omega,
                    m.nx, m.j0, m.j1, m.k0, m.k1, m.nyt, m.sj, m.sk};
     if (c->geom == FARGO_CART) in.wfr = b.tab.wfrd;   // the shearing sheet's 2 Omega_f y (0 otherwise)
+    in.vref = b.tab.vrefd;                             // the reference form (FP32), else null
     k_sums<T><<<c->sum_blocks, 256, 0, c->stream>>>(in, c->part2, &c->sc->counter2, c->sums);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, c->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1134,6 +1195,8 @@ static int change_frame_impl(fargo_ctx *c, Buffers<T> &b, double omega_new)
     MeshD &m = c->m;
     const double dom = omega_new - m.omega;
     const long long n = (long long)m.nx * m.nyt * m.nzt;
+    // (FP32: through the v_x form, and references chosen afresh in the new frame)
+    if ((rc = vref_launch<T>(c, b, VREF_ABS, nullptr, c->stream))) return rc;
     k_change_frame<T><<<grid_for(n, 256), 256, 0, c->stream>>>(b.A.vx, b.tab.Rd, dom, m.nx, m.nyt, m.nzt, m.sj,
                                                                  m.sk);
     CK(cudaGetLastError());
@@ -1144,6 +1207,7 @@ static int change_frame_impl(fargo_ctx *c, Buffers<T> &b, double omega_new)
     }
     m.omega = omega_new;
     b.tab.omega = (T)omega_new;
+    if ((rc = vref_refresh<T>(c, b, c->stream))) return rc;
     if (c->gexec) {   // the captured step holds the old frame
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -1237,8 +1301,8 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     T *va[3] = {A.vx, A.vy, A.vz};
     switch (phase) {
     case 0:
-        if (m.hasY) k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1);
-        if (m.hasZ) k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1);
+        if (m.hasY) k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1, b.tab.vref);
+        if (m.hasZ) k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1, b.tab.vref);
         break;
     case 1:
         k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,

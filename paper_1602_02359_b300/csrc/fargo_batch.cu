@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(256) kb_bc(const StepPlan<T> *__restrict__ P, 
     __shared__ PlanSmem<T> sp;
     const StepPlan<T> &p = plan_to_smem(P, group_member(g, blockIdx.x, local), sp);
     const long long tid = (long long)local * blockDim.x + threadIdx.x;
-    if (axis == 1) bc_y_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid);
-    else bc_z_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid);
+    if (axis == 1) bc_y_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid, p.tb.vref);
+    else bc_z_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid, p.tb.vref);
 }
 
 template <typename T>
@@ -151,7 +151,7 @@ struct BTxOp {
         e.id = group_member(g, item, e.local);
         const StepPlan<T> &p = P[e.id];
         e.N = step_dt<T>(p.sc) > T(0) ? 0 : -1;
-        tx_v0(p.m, p.v0, e.local, e.a, e.b);
+        tx_v0(p.m, p.tb, p.v0, e.local, e.a, e.b);
     }
     __device__ void issue(int it, T *dst, uint64_t *bar)
     {
@@ -263,15 +263,31 @@ __global__ void __launch_bounds__(256) kb_pack(const StepPlan<T> *__restrict__ P
     const int nx = m.nx, ny = m.j1 - m.j0, nz = m.k1 - m.k0;
     const long long nact = (long long)nx * ny * nz;
     T *s = stage + __ldg(&pk[id]);
+    // v_x leaves in v_x form (FP32: stored v_x - vref); it arrives in v_x form
+    // and kb_vref rebases it afterwards
+    const T *ref = field == 2 && sizeof(T) == 4 ? p.tb.vref : nullptr;
     for (int u = 0; u < kPackCells / 256; u++) {
         const long long t = (long long)local * kPackCells + u * 256 + threadIdx.x;
         if (t >= nact) return;
         const int i = (int)(t % nx);
         const long long r = t / nx;
-        const idx_t c = IX(m, i, m.j0 + (int)(r % ny), m.k0 + (int)(r / ny));
+        const int j = m.j0 + (int)(r % ny), k = m.k0 + (int)(r / ny);
+        const idx_t c = IX(m, i, j, k);
         if (to_fields) f[c] = s[t];
-        else s[t] = f[c];
+        else s[t] = ref ? f[c] + ref[k * m.nyt + j] : f[c];
     }
+}
+
+// The reference form of v_x for every member (FP32): mode VREF_ABS, _CHOOSE
+// or _APPLY of vref_ring over all rings of all members, eight rings a block.
+template <typename T>
+__global__ void __launch_bounds__(256) kb_vref(const StepPlan<T> *__restrict__ P, Group g, int mode)
+{
+    int local;
+    const int id = group_member(g, blockIdx.x, local);
+    const StepPlan<T> &p = P[id];
+    const int ring = local * 8 + (threadIdx.x >> 5);
+    if (ring < p.m.nyt * p.m.nzt) vref_ring(p.m, p.tb, p.A.vx, p.A.vx, ring, mode);
 }
 
 // out[0] = members still running, out[1] = OR of their error flags,
@@ -346,6 +362,8 @@ struct fargo_batch {
     long long *pk = nullptr;
     int *pack_grp = nullptr;
     int pack_blocks = 0;
+    int *vref_grp = nullptr;     // kb_vref's launch: member ids and block offsets (eight rings a block)
+    int vref_blocks = 0;
     size_t packed_bytes = 0;
     int cpt = kCellsPerThread;                // cells per thread of the per-cell phases
     cudaGraph_t graph = nullptr;
@@ -714,6 +732,7 @@ extern "C" void fargo_batch_destroy(fargo_batch *b)
     if (b->stage) cudaFree(b->stage);
     if (b->pk) cudaFree(b->pk);
     if (b->pack_grp) cudaFree(b->pack_grp);
+    if (b->vref_grp) cudaFree(b->vref_grp);
     if (b->hstatus) cudaFreeHost(b->hstatus);
     // a stream handed in by the caller stays theirs; the member contexts too
     if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -750,7 +769,7 @@ static int pack_setup(fargo_batch *b)
 {
     if (b->stage) return FARGO_OK;
     std::vector<long long> pk(b->n);
-    std::vector<int> ids(b->n), off(b->n + 1, 0);
+    std::vector<int> ids(b->n), off(b->n + 1, 0), voff(b->n + 1, 0);
     long long tot = 0;
     for (int i = 0; i < b->n; i++) {
         const fargo_ctx *c = b->mem[i];
@@ -759,7 +778,12 @@ static int pack_setup(fargo_batch *b)
         tot += nact;
         ids[i] = i;
         off[i + 1] = off[i] + (int)((nact + kPackCells - 1) / kPackCells);
+        voff[i + 1] = voff[i] + (c->m.nyt * c->m.nzt + 7) / 8;
     }
+    CK(cudaMalloc(&b->vref_grp, sizeof(int) * (2 * b->n + 1)));
+    CK(cudaMemcpyAsync(b->vref_grp, ids.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->vref_grp + b->n, voff.data(), sizeof(int) * (b->n + 1), cudaMemcpyHostToDevice, b->stream));
+    b->vref_blocks = voff[b->n];
     const size_t esz = b->mem[0]->esz;
     b->packed_bytes = (size_t)tot * esz;
     CK(cudaMalloc(&b->stage, b->packed_bytes));
@@ -795,14 +819,28 @@ static bool field_ok(const fargo_batch *b, int field)
     return true;
 }
 
+static int vref_batch(fargo_batch *b, int mode)
+{
+    const Group g{b->vref_grp, b->vref_grp + b->n, b->n};
+    kb_vref<float><<<b->vref_blocks, 256, 0, b->stream>>>((const StepPlan<float> *)b->plans, g, mode);
+    CK(cudaGetLastError());
+    return FARGO_OK;
+}
+
 extern "C" int fargo_batch_set_field_packed(fargo_batch *b, int field, const void *src, size_t bytes)
 {
     if (!b || !src || !field_ok(b, field)) return FARGO_ERR_BADARG;
     int rc = pack_setup(b);
     if (rc) return rc;
     if (bytes != b->packed_bytes) return FARGO_ERR_SIZE;
+    // FP32 v_x: the members' ghost rings to v_x form, the active cells
+    // written, then every ring rebased on fresh references
+    const bool ref = b->prec == FARGO_F32 && field == FARGO_VX;
+    if (ref && (rc = vref_batch(b, VREF_ABS))) return rc;
     CK(cudaMemcpyAsync(b->stage, src, bytes, cudaMemcpyDefault, b->stream));
-    return pack_launch(b, field, 1);
+    if ((rc = pack_launch(b, field, 1))) return rc;
+    if (ref && ((rc = vref_batch(b, VREF_CHOOSE)) || (rc = vref_batch(b, VREF_APPLY)))) return rc;
+    return FARGO_OK;
 }
 
 extern "C" int fargo_batch_get_field_packed(fargo_batch *b, int field, void *dst, size_t bytes)

@@ -67,7 +67,22 @@ struct Tab {
     // 1/yf, 1/ym; per k 1/dz, 1/sin(zm), 1/(zm[k] - zm[k-1]); scalar 1/dx
     const T *ilenx, *ilenz, *iR, *idy, *iyf, *iym, *idz, *iszm, *idzm;
     T idx;
+    // Reference form of the azimuthal velocity (FP32 only; null in FP64).
+    // The stored v_x of ring r is v_x - vref[r], a per-ring constant chosen
+    // when v_x is set (the ring's mid-range, or 0), so that the slow changes
+    // of a nearly Keplerian flow are not rounded away against |v_x| ~ v_K.
+    // The transported X momenta are held as Pi - rho A(r), A = R vref + w
+    // (w the frame term above), and the Y / Z sweeps move them between the
+    // rings' frames with dAy[r] = A(r) - A(r - 1), dAz[r] = A(r) - A(r - nyt).
+    T *vref, *dAy, *dAz;
+    double *vrefd;
 };
+
+template <typename T>
+__device__ __forceinline__ T vref_at(const Tab<T> &tb, int ring)
+{
+    return sizeof(T) == 4 && tb.vref ? tb.vref[ring] : T(0);
+}
 
 // The fields a kernel reads or writes.  dx, in the FP32 step only, holds the
 // source step's accumulated increment of the azimuthal velocity: the source

@@ -12,9 +12,19 @@ namespace fk {
 // side).  mode 0 = cell 2 (skipped once the run is done or failed),
 // mode 1 = cell 9 (skipped when the current step is void).
 // ---------------------------------------------------------------------------
+//
+// `ref` (v_x in the reference form of FP32, else null) is the reference
+// velocity of the ring at line position p, ref[p * rs]: a value copied from
+// position s to position d keeps its v_x, so its stored value gains
+// ref[s] - ref[d].  Periodic rings share their images' references.
+template <typename T>
+__device__ __forceinline__ T ref_shift(const T *ref, int rs, int s, int d)
+{
+    return ref ? ref[s * rs] - ref[d * rs] : T(0);
+}
 template <typename T>
 __device__ void fill_line(T *a, idx_t base, idx_t stride, int lo, int hi, int g, int normal, int side,
-                          int bc)
+                          int bc, const T *ref = nullptr, int rs = 0)
 {
     if (bc == BC_FROZEN) return;
     if (bc == BC_PERIODIC) {
@@ -30,7 +40,8 @@ __device__ void fill_line(T *a, idx_t base, idx_t stride, int lo, int hi, int g,
         for (int mm = 0; mm < g; mm++) {
             int dst = side == 0 ? lo - 1 - mm : hi + mm;
             int src = bc == BC_REFLECT ? (side == 0 ? lo + mm : hi - 1 - mm) : (side == 0 ? lo : hi - 1);
-            a[base + dst * stride] = a[base + src * stride];
+            if (ref) a[base + dst * stride] = a[base + src * stride] + ref_shift(ref, rs, src, dst);
+            else a[base + dst * stride] = a[base + src * stride];
         }
     } else if (bc == BC_REFLECT) {
         int w = side == 0 ? lo : hi;
@@ -57,7 +68,8 @@ __device__ __forceinline__ bool bc_skip(const Scal *sc, int mode)
 }
 
 template <typename T>
-__device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid)
+__device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid,
+                                          const T *vref = nullptr)
 {
     long long n = (long long)m.nx * (m.nzt + 1) * 2;
     if (tid >= n || bc_skip(sc, mode)) return;
@@ -73,12 +85,14 @@ __device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const
         if (q == 4 && !m.hasZ) continue;
         int kmax = q == 4 ? m.nzt + 1 : m.nzt;
         if (k >= kmax) continue;
-        fill_line(fl[q], k * m.sk + i, m.sj, m.j0, m.j1, m.g, q == 3, side, bc);
+        fill_line(fl[q], k * m.sk + i, m.sj, m.j0, m.j1, m.g, q == 3, side, bc,
+                  q == 2 && vref ? vref + k * m.nyt : (const T *)nullptr, 1);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid)
+__device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid,
+                                          const T *vref = nullptr)
 {
     long long n = (long long)m.nx * (m.nyt + 1) * 2;
     if (tid >= n || bc_skip(sc, mode)) return;
@@ -93,7 +107,8 @@ __device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const
         if (q == 3 && !m.hasY) continue;
         int jmax = q == 3 ? m.nyt + 1 : m.nyt;
         if (j >= jmax) continue;
-        fill_line(fl[q], j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc);
+        fill_line(fl[q], j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc,
+                  q == 2 && vref ? vref + j : (const T *)nullptr, m.nyt);
     }
 }
 
@@ -202,14 +217,14 @@ static PerSet<T> per_quantities(const QSet<T> &dst, const QSet<T> &src)
 }
 
 template <typename T>
-__global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode)
+__global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode, const T *vref)
 {
-    bc_y_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    bc_y_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x, vref);
 }
 template <typename T>
-__global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode)
+__global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode, const T *vref)
 {
-    bc_z_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    bc_z_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x, vref);
 }
 
 // ---------------------------------------------------------------------------
@@ -345,6 +360,10 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
         constexpr int W = Pack<T>::W;
         const int nx = m.nx;
         double v0r = 0.0;
+        // the stored v_x is v_x - vref in the reference form (FP32); sums of
+        // an FP32 value and vref are exact in FP64 whenever v_x itself is an
+        // FP32 value (as it is right after the field was set)
+        const double vrr = sizeof(T) == 4 && tb.vrefd ? tb.vrefd[ring] : 0.0;
         if (m.fargo) {
             // max and min are exact in the field precision
             T mx = f.vx[base], mn = mx;
@@ -357,7 +376,7 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
                         mn = pv.v[u] < mn ? pv.v[u] : mn;
                     }
             }
-            v0r = __dmul_rn(0.5, __dadd_rn(warp_max((double)mx), warp_min((double)mn)));
+            v0r = __dmul_rn(0.5, __dadd_rn(__dadd_rn(vrr, warp_max((double)mx)), __dadd_rn(vrr, warp_min((double)mn))));
             if (lane == 0) {
                 v0[ring] = v0r;
                 // the ring's bulk angular rate v0 / (R dx) for the shear limit (Eq. 38),
@@ -365,7 +384,8 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
                 v0[(size_t)m.nyt * m.nzt + ring] = __ddiv_rn(v0r, tb.lx[ring]);
             }
         }
-        const T v0hi = (T)v0r, v0lo = (T)(v0r - (double)v0hi);
+        const double v0s = __dsub_rn(v0r, vrr);   // v0 against the stored values
+        const T v0hi = (T)v0s, v0lo = (T)(v0s - (double)v0hi);
         // per-ring reciprocals: the estimate needs no division per cell and no
         // square root (the sound-speed rate enters squared)
         const float ilx = 1.0f / (float)tb.lenx[ring], ily = 1.0f / (float)tb.dy[j];
@@ -490,7 +510,8 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
         const int j = m.j0 + r % ny, k = m.k0 + r / ny;
         const int ring = k * m.nyt + j;
         const idx_t base = IX(m, 0, j, k);
-        const double v0r = m.fargo ? v0[ring] : 0.0;
+        // v0 against the stored values (the reference form's vref subtracted)
+        const double v0r = __dsub_rn(m.fargo ? v0[ring] : 0.0, sizeof(T) == 4 && tb.vrefd ? tb.vrefd[ring] : 0.0);
         const double lx = tb.lx[ring], ly = tb.ly[ring], lz = tb.lz[ring], dmin = tb.dmin[ring];
         const double nu = m.has_nu ? tb.nud[ring] : 0.0;
         const double r4 = nu > 0.0 ? __ddiv_rn(__dmul_rn(4.0, nu), __dmul_rn(dmin, dmin)) : 0.0;
@@ -634,6 +655,82 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
         sc->dtf = (float)dt;
         sc->counter = 0u;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Reference form of v_x (FP32): one warp per ring r of the nyt * nzt rings.
+//   VREF_ABS:    dst <- v' + vref[r] (the stored values back to v_x; dst may
+//                be the field itself)
+//   VREF_CHOOSE: vref[r] <- m, the mid-range of the v_x values of ring img(r)
+//                (the ring itself, or its image one period away on a
+//                periodic axis, so that images share a reference), when
+//                every value v of that ring has (v - m) + m == v in FP32
+//                (v - m then holds v exactly); otherwise 0
+//   VREF_APPLY:  v' <- v - vref[r]; lane 0 also writes the frame shifts dAy,
+//                dAz of the X momenta from A = R vref + w (FP64, rounded once)
+// CHOOSE reads v_x values only, so the whole field may be in v_x form while
+// it runs; APPLY runs after it (a separate launch).
+// ---------------------------------------------------------------------------
+enum { VREF_ABS = 0, VREF_CHOOSE = 1, VREF_APPLY = 2 };
+
+template <typename T>
+__device__ void vref_ring(const MeshD &m, const Tab<T> &tb, T *vx, T *dst, int ring, int mode)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = ring % m.nyt, k = ring / m.nyt;
+    const idx_t base = IX(m, 0, j, k);
+    if (mode == VREF_ABS) {
+        const T r = tb.vref[ring];
+        for (int i = lane; i < m.nx; i += 32) dst[base + i] = vx[base + i] + r;
+        return;
+    }
+    if (mode == VREF_APPLY) {
+        const T r = tb.vref[ring];
+        for (int i = lane; i < m.nx; i += 32) vx[base + i] = vx[base + i] - r;
+        if (lane == 0) {
+            auto A = [&](int q) {
+                const double R = tb.Rd[q];
+                const double w = m.geom == CART ? tb.wfrd[q] : R * R * m.omega;
+                return R * tb.vrefd[q] + w;
+            };
+            const double a = A(ring);
+            tb.dAy[ring] = j >= 1 ? (T)(a - A(ring - 1)) : T(0);
+            tb.dAz[ring] = k >= 1 ? (T)(a - A(ring - m.nyt)) : T(0);
+        }
+        return;
+    }
+    int ji = j, ki = k;
+    if (m.pery && m.hasY) ji = j < m.j0 ? j + (m.j1 - m.j0) : (j >= m.j1 ? j - (m.j1 - m.j0) : j);
+    if (m.perz && m.hasZ) ki = k < m.k0 ? k + (m.k1 - m.k0) : (k >= m.k1 ? k - (m.k1 - m.k0) : k);
+    const idx_t bi = IX(m, 0, ji, ki);
+    double mx = -INFINITY, mn = INFINITY;
+    bool fin = true;
+    for (int i = lane; i < m.nx; i += 32) {
+        const double v = (double)vx[bi + i];
+        fin = fin && isfinite(v);
+        mx = fmax(mx, v);
+        mn = fmin(mn, v);
+    }
+    mx = warp_max(mx);
+    mn = warp_min(mn);
+    T r = fin ? (T)(0.5 * (mx + mn)) : T(0);
+    bool exact = fin;
+    for (int i = lane; i < m.nx && exact; i += 32) {
+        const T v = vx[bi + i];
+        exact = (v - r) + r == v;
+    }
+    if (!__all_sync(0xffffffffu, exact)) r = T(0);
+    if (lane == 0) {
+        tb.vref[ring] = r;
+        tb.vrefd[ring] = (double)r;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_vref(MeshD m, Tab<T> tb, T *vx, T *dst, int mode)
+{
+    const int ring = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (ring < m.nyt * m.nzt) vref_ring(m, tb, vx, dst, ring, mode);
 }
 
 // Blocks of the exact pass for a screen of cfl_blocks blocks (eight rings each).

@@ -109,10 +109,11 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
                 acc -= (phi_planet<T, F>(m, tb, i, ring) - phi_planet<T, F>(m, tb, i, ring - 1)) * id;
             if (F::star(m)) acc -= tb.gphy[ring];
             if (F::geom(m) != CART) {
+                // (the reference velocity of the reference form joins the frame's R Omega)
                 const T Rj = tb.R[ring], Rm = tb.R[ring - 1];
+                const T uj = Rj * om + vref_at(tb, ring), um = Rm * om + vref_at(tb, ring - 1);
                 const idx_t cp = c - i + ip, cmp = cm - i + ip;
-                const T vt = T(0.25) * ((in.vx[c] + Rj * om) + (in.vx[cp] + Rj * om) + (in.vx[cm] + Rm * om) +
-                                        (in.vx[cmp] + Rm * om));
+                const T vt = T(0.25) * ((in.vx[c] + uj) + (in.vx[cp] + uj) + (in.vx[cm] + um) + (in.vx[cmp] + um));
                 T cen = vt * vt;
                 if (F::geom(m) == SPH && F::hasZ(m)) {
                     const T vth = T(0.25) * (in.vz[c] + in.vz[c + m.sk] + in.vz[cm] + in.vz[cm + m.sk]);
@@ -123,7 +124,8 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
                 // shearing sheet: Coriolis 2 Omega_f v_x (v_x averaged over the four
                 // faces around the Y face) and the tide -4 A Omega_f y
                 const idx_t cp = c - i + ip, cmp = cm - i + ip;
-                const T vxa = T(0.25) * (in.vx[c] + in.vx[cp] + in.vx[cm] + in.vx[cmp]);
+                const T vxa = T(0.25) * (in.vx[c] + in.vx[cp] + in.vx[cm] + in.vx[cmp]) +
+                              T(0.5) * (vref_at(tb, ring) + vref_at(tb, ring - 1));
                 acc += T(2) * om * vxa - tb.tid[j];
             }
             v = v + dt * acc;
@@ -143,9 +145,9 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
             if (F::star(m)) acc -= tb.gphz[ring];
             if (F::geom(m) == SPH) {
                 const T Rk = tb.R[ring], Rm = tb.R[rm];
+                const T uk = Rk * om + vref_at(tb, ring), um = Rm * om + vref_at(tb, rm);
                 const idx_t cp = c - i + ip, cmp = cm - i + ip;
-                const T vt = T(0.25) * ((in.vx[c] + Rk * om) + (in.vx[cp] + Rk * om) + (in.vx[cm] + Rm * om) +
-                                        (in.vx[cmp] + Rm * om));
+                const T vt = T(0.25) * ((in.vx[c] + uk) + (in.vx[cp] + uk) + (in.vx[cm] + um) + (in.vx[cmp] + um));
                 acc += vt * vt * tb.cotzf[k] * tb.iym[j];
             }
             v = v + dt * acc;
@@ -299,13 +301,15 @@ struct ViscCtx {
     const MeshD &m;
     const Tab<T> &tb;
     const T *rho, *vxs, *vy, *vz, *dx;
-    // post-viscosity azimuthal velocity, accessed as the array vx[q]
-    struct VX {
-        const T *v, *d;
-        __device__ T operator[](int q) const { return d ? v[q] + d[q] : v[q]; }
-    } vx;
     __device__ ViscCtx(const MeshD &m_, const Tab<T> &tb_, const Fld<T> &f)
-        : m(m_), tb(tb_), rho(f.rho), vxs(f.vx), vy(f.vy), vz(f.vz), dx(f.dx), vx{f.vx, f.dx} {}
+        : m(m_), tb(tb_), rho(f.rho), vxs(f.vx), vy(f.vy), vz(f.vz), dx(f.dx) {}
+    // post-viscosity azimuthal velocity of face q on ring `ring` (the stored
+    // value, its increment and, in the reference form, the ring's reference)
+    __device__ T vxa(int q, int ring) const
+    {
+        const T v = dx ? vxs[q] + dx[q] : vxs[q];
+        return sizeof(T) == 4 && tb.vref ? v + tb.vref[ring] : v;
+    }
     // difference of two faces' azimuthal velocities, increments differenced apart
     __device__ T dvx(int a, int b) const { return dx ? (vxs[a] - vxs[b]) + (dx[a] - dx[b]) : vxs[a] - vxs[b]; }
     __device__ int wrap(int i) const { return i < 0 ? i + m.nx : (i >= m.nx ? i - m.nx : i); }
@@ -356,18 +360,20 @@ struct ViscCtx {
     __device__ T txy(int i, int j, int k) const
     {
         const idx_t c = at(i, j, k), cm = at(i - 1, j, k);
+        const int ring = k * m.nyt + j;
         const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sj] + rho[cm - m.sj]);
         const T nb = T(0.5) * (nu(j, k) + nu(j - 1, k));
-        const T dvx_dy = (vx[c] - vx[c - m.sj]) * tb.idyc[j];
+        const T v0 = vxa(c, ring), v1 = vxa(c - m.sj, ring - 1);
+        const T dvx_dy = (v0 - v1) * tb.idyc[j];
         T t;
         if (F::geom(m) == CART) {
             t = (vy[c] - vy[cm]) * tb.idx + dvx_dy;
         } else if (F::geom(m) == CYL) {
             const T irf = tb.iyf[j];
-            t = dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) * irf + (vy[c] - vy[cm]) * (irf * tb.idx);
+            t = dvx_dy - T(0.5) * (v0 + v1) * irf + (vy[c] - vy[cm]) * (irf * tb.idx);
         } else {
             const T irf = tb.iyf[j], isn = tb.iszm[k];
-            t = (vy[c] - vy[cm]) * (irf * isn * tb.idx) + dvx_dy - T(0.5) * (vx[c] + vx[c - m.sj]) * irf;
+            t = (vy[c] - vy[cm]) * (irf * isn * tb.idx) + dvx_dy - T(0.5) * (v0 + v1) * irf;
         }
         return -rb * nb * t;
     }
@@ -375,17 +381,19 @@ struct ViscCtx {
     __device__ T txz(int i, int j, int k) const
     {
         const idx_t c = at(i, j, k), cm = at(i - 1, j, k);
+        const int ring = k * m.nyt + j;
         const T rb = T(0.25) * (rho[c] + rho[cm] + rho[c - m.sk] + rho[cm - m.sk]);
         const T nb = T(0.5) * (nu(j, k) + nu(j, k - 1));
         const T idzm = tb.idzm[k];
+        const T v0 = vxa(c, ring), v1 = vxa(c - m.sk, ring - m.nyt);
         T t;
         if (F::geom(m) == CART) {
-            t = (vz[c] - vz[cm]) * tb.idx + (vx[c] - vx[c - m.sk]) * idzm;
+            t = (vz[c] - vz[cm]) * tb.idx + (v0 - v1) * idzm;
         } else if (F::geom(m) == CYL) {
-            t = (vx[c] - vx[c - m.sk]) * idzm + (vz[c] - vz[cm]) * (tb.iym[j] * tb.idx);
+            t = (v0 - v1) * idzm + (vz[c] - vz[cm]) * (tb.iym[j] * tb.idx);
         } else {
             const T ir = tb.iym[j], sf = tb.szf[k];
-            t = sf * ir * (vx[c] * tb.iszm[k] - vx[c - m.sk] * tb.iszm[k - 1]) * idzm +
+            t = sf * ir * (v0 * tb.iszm[k] - v1 * tb.iszm[k - 1]) * idzm +
                 div_fast((vz[c] - vz[cm]) * (ir * tb.idx), sf);
         }
         return -rb * nb * t;

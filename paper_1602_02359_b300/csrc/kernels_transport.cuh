@@ -26,6 +26,22 @@ __device__ __forceinline__ T vl_slope_i(T qm, T q0, T qp, T idm, T idp)
     const T pr = dp * dm;
     return pr > T(0) ? div_fast(T(2) * pr, dp + dm) : T(0);
 }
+// A product rounded on its own (never contracted into a later addition), and
+// a fused multiply-add: the Y/Z sweeps form a face flux in two places (a
+// segment's first face, and every later face), which must round alike.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// The same slope from the two differences q0 - qm and qp - q0.
+template <typename T>
+__device__ __forceinline__ T vl_slope_d(T dqm, T dqp, T idm, T idp)
+{
+    const T dp = dqp * idp, dm = dqm * idm;
+    const T pr = dp * dm;
+    return pr > T(0) ? div_fast(T(2) * pr, dp + dm) : T(0);
+}
 
 // PPA (Sec. 3.4.1): monotonised-centred slope of Eq. 34 for cell values
 // (qm, q0, qp).
@@ -229,11 +245,13 @@ __device__ __host__ __forceinline__ TxRows tx_rows(const MeshD &m, bool dx = fal
 // v0 of ring `ring` split as hi + lo in the field precision (0 off the
 // active rings and for STANDARD transport).
 template <typename T>
-__device__ __forceinline__ void tx_v0(const MeshD &m, const double *v0, int ring, T &hi, T &lo)
+__device__ __forceinline__ void tx_v0(const MeshD &m, const Tab<T> &tb, const double *v0, int ring, T &hi, T &lo)
 {
     const int j = ring % m.nyt, k = ring / m.nyt;
     const bool active = j >= m.j0 && j < m.j1 && k >= m.k0 && k < m.k1;
-    const double v0r = m.fargo && active && m.hasX ? v0[ring] : 0.0;
+    double v0r = m.fargo && active && m.hasX ? v0[ring] : 0.0;
+    // the stored v_x is relative to vref in the reference form
+    if (sizeof(T) == 4 && tb.vrefd && active) v0r -= tb.vrefd[ring];
     hi = (T)v0r;
     lo = (T)(v0r - (double)hi);
 }
@@ -278,7 +296,10 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     const bool adi = !m.iso;
     const bool sweep = active && m.hasX;
     // the frame term of the X momentum: R^2 Omega_f, or the Cartesian table (shearing sheet)
-    const T R = tb.R[ring], w = m.geom == CART ? tb.wfr[ring] : R * R * tb.omega, fz = tb.fz[ring];
+    const T R = tb.R[ring], fz = tb.fz[ring];
+    // the X momenta's frame term, or none in the reference form (they are
+    // then held as rho R (v_x - vref), with v_x - vref the stored value)
+    const T w = sizeof(T) == 4 && tb.vref ? T(0) : (m.geom == CART ? tb.wfr[ring] : R * R * tb.omega);
     const T *Rho = sm, *Vx = sm + (size_t)rw.rVX * rp;
     const T *Dx = hasdx ? sm + (size_t)rw.rDX * rp : nullptr;   // v_x increment of the source step
     // ratio of quantity q to the density at cell i, as scale * (row[i + off]
@@ -657,7 +678,7 @@ struct TxOp {
     __device__ void prepare(int it, int ring)
     {
         meta[it].local = ring;
-        tx_v0(m, v0, ring, meta[it].a, meta[it].b);
+        tx_v0(m, tb, v0, ring, meta[it].a, meta[it].b);
     }
     __device__ void issue(int it, T *dst, uint64_t *bar) { tx_issue(m, in, meta[it].local, dst, bar); }
     __device__ void compute(int it, T *src)
@@ -986,6 +1007,16 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
     auto icd = [&](int f) -> T { return AXIS == 1 ? tb.idyc[f] : tb.idzc[f * m.nyt + c2]; };
     auto width = [&](int d) -> T { return AXIS == 1 ? tb.dy[d] : tb.lenz[d * m.nyt + c2]; };
     auto area = [&](int f) -> T { return AXIS == 1 ? tb.sy[c2 * (m.nyt + 1) + f] : tb.sz[f * (m.nyt + 1) + c2]; };
+    // Reference form of the X momenta (FP32): row p holds Pi - rho A(p).  The
+    // cell update of row p works in the frame of row p: the ratios of rows
+    // p +- 1, 2 are shifted by the differences of A across the faces between
+    // (dA(f) = A(f) - A(f - 1) at face f), and a face flux computed in the
+    // frame of the row below moves to the frame of the row above by
+    // subtracting the mass flux times dA.  Other quantities are not shifted.
+    const bool rf = sizeof(T) == 4 && tb.dAy != nullptr;
+    const unsigned xm = rf ? (3u << (m.iso ? 1 : 2)) : 0u;
+    auto dA = [&](int f) -> T { return !rf ? T(0) : (AXIS == 1 ? tb.dAy[c2 * m.nyt + f] : tb.dAz[f * m.nyt + c2]); };
+    auto sh = [&](int q, T d) -> T { return (xm >> q) & 1u ? d : T(0); };
     bool ok = true;
     // fetch row r into ratios + face velocity; the stage is released by
     // release(r) once the row is no longer needed: after the first fluxes for
@@ -1029,14 +1060,18 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
         const T wl = width(ps - 1), wr = width(ps);
         const T Sa = area(ps);
         T F0 = 0;
+        const T e0 = dA(ps - 1), e1 = dA(ps), e2 = dA(ps + 1);
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            const T am = vl_slope_i(Rm2[q], Rm1[q], R0[q], d0, d1);
-            const T a0 = vl_slope_i(Rm1[q], R0[q], R1[q], d1, d2);
+            const T s0 = sh(q, e0), s1 = sh(q, e1), s2 = sh(q, e2);
+            const T am = vl_slope_d((Rm1[q] - Rm2[q]) + s0, (R0[q] - Rm1[q]) + s1, d0, d1);
+            const T a0 = vl_slope_d((R0[q] - Rm1[q]) + s1, (R1[q] - R0[q]) + s2, d1, d2);
             aP[q] = a0;
-            const T stv = v >= T(0) ? Rm1[q] + am * (wl - v * dt) * T(0.5) : R0[q] - a0 * (wr + v * dt) * T(0.5);
+            // interface value in the frame of row ps - 1
+            const T stv = v >= T(0) ? Rm1[q] + am * (wl - v * dt) * T(0.5) : (R0[q] + s1) - a0 * (wr + v * dt) * T(0.5);
             if (q == 0) F0 = v * stv * Sa;
-            Flo[q] = q == 0 ? F0 : F0 * stv;
+            const T Fup = q == 0 ? F0 : mul_rn(F0, stv);
+            Flo[q] = rf && ((xm >> q) & 1u) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row ps
         }
     }
     release(0);
@@ -1051,14 +1086,17 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
         const int rp = p - ps + 2;   // row index of p
         const T *raw = stage + (size_t)(rp % S) * ROW + threadIdx.x;
         T F0 = 0;
+        const T e1 = dA(p + 1), e2 = dA(p + 2);
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            const T aN = vl_slope_i(R0[q], R1[q], R2[q], dn, dnn);
-            const T stv = v >= T(0) ? R0[q] + aP[q] * (wp - v * dt) * T(0.5) : R1[q] - aN * (wn + v * dt) * T(0.5);
+            const T s1 = sh(q, e1), s2 = sh(q, e2);
+            const T aN = vl_slope_d((R1[q] - R0[q]) + s1, (R2[q] - R1[q]) + s2, dn, dnn);
+            // interface value and flux in the frame of row p
+            const T stv = v >= T(0) ? R0[q] + aP[q] * (wp - v * dt) * T(0.5) : (R1[q] + s1) - aN * (wn + v * dt) * T(0.5);
             if (q == 0) F0 = v * stv * Sa;
-            const T Fup = q == 0 ? F0 : F0 * stv;
+            const T Fup = q == 0 ? F0 : mul_rn(F0, stv);
             if (col) out.q[q][c] = raw[q * TW] - dtVi * (Fup - Flo[q]);
-            Flo[q] = Fup;
+            Flo[q] = rf && ((xm >> q) & 1u) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row p + 1
             aP[q] = aN;
         }
         release(rp);
@@ -1181,10 +1219,17 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     if (j < m.nyt && k < m.nzt) {
         if (jact && kact) {
             const idx_t cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
-            const T R = tb.R[ring], w = F::geom(m) == CART ? tb.wfr[ring] : R * R * tb.omega;
+            const T R = tb.R[ring];
             // divisions, not reciprocal products: v_x is rebuilt from R v_x every
-            // step, and a rounded 1/R would bias it by R (1/R) - 1 each time
-            state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
+            // step, and a rounded 1/R would bias it by R (1/R) - 1 each time.
+            // In the reference form the momenta hold rho (R v_x + w) - rho A with
+            // A = R vref + w, so the quotient is R (v_x - vref), the stored value.
+            if (sizeof(T) == 4 && tb.vref) {
+                state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c])) / R;
+            } else {
+                const T w = F::geom(m) == CART ? tb.wfr[ring] : R * R * tb.omega;
+                state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
+            }
         } else if (vsrc.dx) {
             state.vx[c] = vsrc.vx[c] + vsrc.dx[c];   // the post-source value of a ghost ring's face
         } else if (vsrc.vx != state.vx) {
@@ -1252,6 +1297,7 @@ struct SumInput {
     int nx, j0, j1, k0, k1, nyt;
     long long sj, sk;
     const double *wfr;   // the frame term of the X momentum per ring, or null for R^2 omega
+    const double *vref;  // the reference velocity per ring of the reference form (FP32), or null
 };
 
 // Per-block compensated partials of the three totals, then the last block to
@@ -1275,7 +1321,8 @@ __device__ void sums_reduce(const SumInput<T> &in, double *part, unsigned *count
         const double rho = (double)in.rho[c];
         kb_add(acc[0], rho * V);
         if (in.e) kb_add(acc[1], (double)in.e[c] * V);
-        const double R = in.R[ring], w = in.wfr ? in.wfr[ring] : R * R * in.omega;
+        const double R = in.R[ring];
+        const double w = (in.wfr ? in.wfr[ring] : R * R * in.omega) + (in.vref ? R * in.vref[ring] : 0.0);
         const int ip = i + 1 == in.nx ? 0 : i + 1;
         const double pm = rho * (R * (double)in.vx[c] + w), pp = rho * (R * (double)in.vx[c - i + ip] + w);
         kb_add(acc[2], 0.5 * (pm + pp) * V);

@@ -14,7 +14,13 @@ measured where the workloads are run:
   - the two smallest disks of the sweep run to 500 orbits by the batched
     engine, against stored oracle states.
 Errors are relative L1 norms over the active cells: density, energy, and the
-cell-centred momentum density (Eq. 19) of all components together.
+cell-centred momentum density (Eq. 19) of all components together.  The
+stated tolerance, 2e-5 on density (and energy) and 1e-4 on the momentum
+density, is asserted at 10 orbits, 200 steps and 1000 steps (measured: at
+most 1.3e-6).  The error keeps growing with the number of steps, about
+1e-6 per thousand, and the two runs' Courant steps part by a fraction of a
+percent, so after 500 orbits (1e5 steps and more) it is 6e-4 and 4e-3:
+those runs are bounded at about twice that.
 """
 import os
 
@@ -67,7 +73,7 @@ def test_disk2d_fp32_ten_orbits():
     e = errors(w, {k: v.astype(np.float64) for k, v in c.get_state().items()}, ref)
     record("fp32_disk2d_768x256_10orbits", steps=n, oracle_steps=n_ref, **e)
     assert abs(n - n_ref) <= 2
-    assert e["rho"] < 1e-2 and e["momentum"] < 1e-2
+    assert e["rho"] < 2e-5 and e["momentum"] < 1e-4, e
     c.close()
 
 
@@ -110,11 +116,11 @@ def test_sweep_disks_fp32_batched_1000_steps():
         for k, v in e.items():
             worst[k] = max(worst.get(k, 0.0), v)
         c.close()
-    assert worst["rho"] < 1e-2 and worst["momentum"] < 1e-2, worst
+    assert worst["rho"] < 2e-5 and worst["momentum"] < 1e-4, worst
 
 
-@pytest.mark.parametrize("member", [156, 126])
-def test_smallest_sweep_disks_fp32_batched_500_orbits(member):
+@pytest.mark.parametrize("member,bound", [(156, 1.5e-3), (126, 1e-2)])
+def test_smallest_sweep_disks_fp32_batched_500_orbits(member, bound):
     import paper_1602_02359_b300 as fb
     w = W.batch_instance(W.batch_params()[member])
     ref, t_end, n_ref = stored_state(w, os.path.join(GOLDEN, f"batch_member{member}_500orbits.npz"))
@@ -126,5 +132,6 @@ def test_smallest_sweep_disks_fp32_batched_500_orbits(member):
     assert err == 0 and running == 0 and t == t_end
     e = errors(w, {k: v.astype(np.float64) for k, v in c.get_state().items()}, ref)
     record(f"fp32_batch_member{member}_500orbits", steps=n, oracle_steps=n_ref, **e)
-    assert e["rho"] < 1e-1 and e["momentum"] < 1e-1
+    assert abs(n - n_ref) < 0.01 * n_ref, (n, n_ref)
+    assert e["rho"] < bound and e["momentum"] < bound, e
     c.close()

@@ -86,13 +86,13 @@ def run_ring(ny, times):
 
 
 def test_oracle_follows_the_spreading_ring():
-    """t = 300: L1 error 0.14 %, peak error 0.29 %; t = 1100 (the paper's
+    """t = 300: L1 error 0.16 %, peak error 0.32 %; t = 1100 (the paper's
     last comparison time, when the ring reaches the inner boundary and about
-    2 % of the mass has left through it): L1 0.81 %.  Bounds at about twice
+    2 % of the mass has left through it): L1 0.58 %.  Bounds at about twice
     these."""
     (l1a, mxa), (l1b, _) = run_ring(512, (300.0, 1100.0))
     assert l1a < 3e-3 and mxa < 6e-3, (l1a, mxa)
-    assert l1b < 1.6e-2, l1b
+    assert l1b < 1.2e-2, l1b
 
 
 def test_oracle_ring_error_falls_with_resolution():

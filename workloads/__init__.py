@@ -236,7 +236,7 @@ def viscous_ring_profile(r, t, nu=1e-5, mass=1.0, r0=1.0):
     return sigma, vr
 
 
-def viscous_ring(ny=512, nx=1, nu=1e-5, t0=100.0, t_end=1100.0, cs=0.0, floor=1e-10, g=3, cq=1.41):
+def viscous_ring(ny=512, nx=1, nu=1e-5, t0=100.0, t_end=1100.0, cs=0.0, floor=1e-10, g=3, cq=1.41, cfl=0.3):
     """The viscous-ring test of Sec. 5.1: an axisymmetric Keplerian ring of
     unit mass at r0 = 1 around a unit-mass star, constant viscosity nu,
     0.1 <= r <= 1.6 on ny evenly spaced cylindrical cells, zero-gradient
@@ -248,11 +248,16 @@ def viscous_ring(ny=512, nx=1, nu=1e-5, t0=100.0, t_end=1100.0, cs=0.0, floor=1e
     so that the exponentially small wings stay well inside FP32's range.
     v_phi is Keplerian at cell centres, v_r the analytic value at the radial
     faces.  nx azimuthal cells carry identical copies (no orbital advection:
-    the ring is axisymmetric)."""
+    the ring is axisymmetric).  Courant number 0.3 rather than the usual
+    0.44: at 0.44 the pressureless floor gas next to the inner edge, whose
+    discrete centrifugal balance is not exact, runs a shock train that sets
+    the time step, and that train runs away on some trajectories (1 in 12
+    of the runs started from states perturbed at 1e-6, in either
+    precision); at 0.3 it stays calm."""
     yf = faces(ny, g, 0.1, 1.6)
     zf = faces(1, g, -0.5, 0.5)
     w = Workload("viscous_ring", CYL, nx, ny, 1, g, -math.pi, math.pi, yf, zf, 1.4, True,
-                 None, None, 0.44, cq, False, 0.0,
+                 None, None, cfl, cq, False, 0.0,
                  (BC_ZEROGRAD, BC_ZEROGRAD), (BC_ZEROGRAD, BC_ZEROGRAD),
                  1.0, 0.0, 1.0, 0.0, False, t0, t_end, {})
     w.cs = np.full((w.nz_t, w.ny_t), cs)
