@@ -23,7 +23,6 @@ struct Buffers {
     T *vB[3] = {nullptr, nullptr, nullptr};
     T *piA[6] = {}, *piB[6] = {};
     T *rhoB = nullptr, *eB = nullptr;
-    T *dx2 = nullptr;           // FP32: the azimuthal-velocity increment after the artificial viscosity
     Tab<T> tab{};
 };
 
@@ -45,7 +44,6 @@ struct StepPlan {
     MeshD m;
     Tab<T> tb;
     Fld<T> A, VB;      // state and the scratch velocities of the source step
-    Fld<T> Ax;         // the artificial viscosity's output (the state with, in FP32, its v_x increment)
     Fld<T> vsrc;       // post-source velocities (VB with viscosity, else A)
     Fld<T> txin;       // input of the X sweep: state scalars, post-source velocities
     QSet<T> qx, qy, qz;   // outputs of the X, Y and Z sweeps
@@ -133,18 +131,9 @@ static StepPlan<T> make_plan(const fargo_ctx *c, const Buffers<T> &b)
     p.m = m;
     p.tb = b.tab;
     p.A = b.A;
-    if (sizeof(T) == 4) {
-        // FP32: the source step keeps the stored v_x and carries its change in
-        // an increment (vB[0] after sub-step 1 and the viscosity, dx2 after the
-        // artificial viscosity); see Fld
-        p.VB = {b.A.rho, b.A.e, b.A.vx, b.vB[1], b.vB[2], b.vB[0]};
-        p.Ax = {b.A.rho, b.A.e, b.A.vx, b.A.vy, b.A.vz, b.dx2};
-    } else {
-        p.VB = {b.A.rho, b.A.e, b.vB[0], b.vB[1], b.vB[2], nullptr};
-        p.Ax = p.A;
-    }
-    p.vsrc = m.has_nu ? p.VB : p.Ax;
-    p.txin = {b.A.rho, b.A.e, p.vsrc.vx, p.vsrc.vy, p.vsrc.vz, p.vsrc.dx};
+    p.VB = {b.A.rho, b.A.e, b.vB[0], b.vB[1], b.vB[2]};
+    p.vsrc = m.has_nu ? p.VB : p.A;
+    p.txin = {b.A.rho, b.A.e, p.vsrc.vx, p.vsrc.vy, p.vsrc.vz};
     for (int q = 0; q < 6; q++) p.tau.q[q] = b.piB[q];
     p.tau.nq = 6;
     QSet<T> qa = qset<T>(c, b.A.rho, b.A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);

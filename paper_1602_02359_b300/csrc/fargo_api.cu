@@ -360,10 +360,6 @@ static int alloc_fields(fargo_ctx *c, Buffers<T> &b)
         if ((rc = dalloc(c, &p, n))) return rc;
         b.piB[q] = (T *)p;
     }
-    if (sizeof(T) == 4) {   // the FP32 step's second v_x increment buffer
-        if ((rc = dalloc(c, &p, n))) return rc;
-        b.dx2 = (T *)p;
-    }
     int rc2 = build_tables<T>(c, b.tab);
     return rc2 ? rc2 : vref_refresh<T>(c, b, c->stream);
 }
@@ -419,15 +415,15 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     // cell 7
     launch_source<T>(SRC_SUB1, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("substep1");
     PERIODIC(per_fields<T>(m, P.VB, true, false), "periodic");
-    launch_source<T>(SRC_AV, m, cg, cb, s, P.tb, P.VB, P.Ax, P.tau, P.sc); MARK("artvisc");
-    PERIODIC(per_fields<T>(m, P.Ax, true, true), "periodic");
+    launch_source<T>(SRC_AV, m, cg, cb, s, P.tb, P.VB, P.A, P.tau, P.sc); MARK("artvisc");
+    PERIODIC(per_fields<T>(m, P.A, true, true), "periodic");
     if (m.has_nu) {
         // stresses once into the scratch momenta of set B (unused until the transport step)
-        launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cb, s, P.tb, P.Ax, P.VB, P.tau, P.sc); MARK("visc_tau");
+        launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_tau");
         QSet<T> diag = P.tau;
         diag.nq = m.hasZ ? 3 : 2;
         PERIODIC(per_quantities<T>(diag, diag), "periodic");
-        launch_source<T>(SRC_VAPPLY, m, cg, cb, s, P.tb, P.Ax, P.VB, P.tau, P.sc); MARK("visc_apply");
+        launch_source<T>(SRC_VAPPLY, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
         PERIODIC(per_fields<T>(m, P.VB, true, false), "periodic");
     }
     // cell 9
@@ -538,8 +534,7 @@ static int set_kernel_attrs(fargo_ctx *c)
     int maxsm = 0;
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int nq = 3 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
-    // staged rows of the X sweep (tx_rows): rho, e, v_x, its FP32 increment, v_y pair, v_z pair
-    const int txrows = tx_rows(c->m, sizeof(T) == 4).n;
+    const int txrows = 2 + (c->m.iso ? 0 : 1) + (c->m.hasY ? 2 : 0) + (c->m.hasZ ? 2 : 0);
     // two ring buffers per CTA (double buffering)
     c->tx_rs = ring_shape<T>(c->nx, txrows, c->pitch, false);
     c->orb_rs = ring_shape<T>(c->nx, nq, c->pitch, true);
@@ -1248,17 +1243,8 @@ extern "C" int fargo_sums(fargo_ctx *c, double out[3])
 }
 
 // ---------------------------------------------------------------------------
-// Single sub-steps for kernel-level parity tests.  In FP32 the source
-// sub-steps run in the increment form of the step (a zero increment on
-// entry) and the increment is added to the stored v_x afterwards.
+// Single sub-steps for kernel-level parity tests.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_fold_increment(T *__restrict__ v, const T *__restrict__ d, idx_t n)
-{
-    for (idx_t q = blockIdx.x * (idx_t)blockDim.x + threadIdx.x; q < n; q += (idx_t)gridDim.x * blockDim.x)
-        v[q] += d[q];
-}
-
 template <typename T>
 static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
 {
@@ -1267,15 +1253,7 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
     const int bs = 256;
     const size_t nbytes = (size_t)m.ntot * sizeof(T);
     Fld<T> A = b.A;
-    Fld<T> VB = {A.rho, A.e, b.vB[0], b.vB[1], b.vB[2], nullptr};
-    const bool inc = sizeof(T) == 4;
-    // the increment form: v_x stays in A, its change goes to vB[0] (sub-step 1,
-    // viscosity) or dx2 (artificial viscosity)
-    const Fld<T> VBi = inc ? Fld<T>{A.rho, A.e, A.vx, b.vB[1], b.vB[2], b.vB[0]} : VB;
-    const Fld<T> Ai = inc ? Fld<T>{A.rho, A.e, A.vx, A.vy, A.vz, b.dx2} : A;
-    auto fold = [&](const T *d) {
-        k_fold_increment<T><<<grid_for(m.ntot, bs), bs, 0, s>>>(A.vx, d, m.ntot);
-    };
+    Fld<T> VB = {A.rho, A.e, b.vB[0], b.vB[1], b.vB[2]};
     QSet<T> qa = qset<T>(c, A.rho, A.e, b.piA), qb = qset<T>(c, b.rhoB, b.eB, b.piB);
     Scal sh;
     int rc = read_scal(c, &sh);
@@ -1292,9 +1270,9 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         sh.yp = m.pa * sin(ph);
     }
     CK(cudaMemcpyAsync(c->sc, &sh, sizeof(Scal), cudaMemcpyHostToDevice, s));
-    auto copyv = [&](T *const *dst, T *const *src, int from = 0) -> int {
+    auto copyv = [&](T *const *dst, T *const *src) -> int {
         // v_z only exists with a Z direction
-        for (int q = from; q < (m.hasZ ? 3 : 2); q++)
+        for (int q = 0; q < (m.hasZ ? 3 : 2); q++)
             CK(cudaMemcpyAsync(dst[q], src[q], nbytes, cudaMemcpyDeviceToDevice, s));
         return FARGO_OK;
     };
@@ -1314,23 +1292,15 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         // the screening launch fills the per-step planet angle tables
         k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
                                                       c->nrings_active);
-        if (inc) CK(cudaMemsetAsync(b.vB[0], 0, nbytes, s));   // (row padding included)
-        launch_source<T>(SRC_SUB1, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VBi,
+        launch_source<T>(SRC_SUB1, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB,
                          QSet<T>{}, c->sc);
-        if (inc) {
-            if ((rc = copyv(va, b.vB, 1))) return rc;
-            fold(b.vB[0]);
-        } else if ((rc = copyv(va, b.vB))) {
-            return rc;
-        }
+        if ((rc = copyv(va, b.vB))) return rc;
         launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
         break;
     case 3:
         if ((rc = copyv(b.vB, va))) return rc;
-        if (inc) CK(cudaMemsetAsync(b.vB[0], 0, nbytes, s));
-        launch_source<T>(SRC_AV, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, VBi, Ai,
+        launch_source<T>(SRC_AV, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, VB, A,
                          QSet<T>{}, c->sc);
-        if (inc) fold(b.dx2);
         launch_periodic<T>(m, per_fields<T>(m, A, true, true), c->sc, s);
         break;
     case 4: {
@@ -1338,22 +1308,13 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         QSet<T> tau{};
         for (int q = 0; q < 6; q++) tau.q[q] = b.piB[q];
         tau.nq = 6;
-        if (inc) {
-            CK(cudaMemsetAsync(b.dx2, 0, nbytes, s));
-            CK(cudaMemsetAsync(b.vB[0], 0, nbytes, s));
-        }
-        launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, Ai, VB, tau, c->sc);
+        launch_source<T>(SRC_TAU, m, tau_grid(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB, tau, c->sc);
         QSet<T> diag = tau;
         diag.nq = m.hasZ ? 3 : 2;
         launch_periodic<T>(m, per_quantities<T>(diag, diag), c->sc, s);
-        launch_source<T>(SRC_VAPPLY, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, Ai, VBi,
-                         tau, c->sc);
-        if (inc) {
-            if ((rc = copyv(va, b.vB, 1))) return rc;
-            fold(b.vB[0]);
-        } else if ((rc = copyv(va, b.vB))) {
-            return rc;
-        }
+        launch_source<T>(SRC_VAPPLY, m, cell_grid_all(m, c->cell_bs), cell_block(m, c->cell_bs), s, b.tab, A, VB, tau,
+                         c->sc);
+        if ((rc = copyv(va, b.vB))) return rc;
         launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
         break;
     }

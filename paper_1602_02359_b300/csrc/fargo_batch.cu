@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(256, PH == PH_VAPPLY ? 5 : (PH == PH_SUB1 ? 8 
             k += m.k0;
         }
         if constexpr (PH == PH_SUB1) substep1_body<T, F>(m, p.tb, p.A, p.VB, p.sc, (int)i, j, k);
-        else if constexpr (PH == PH_AV) artvisc_body<T, F>(m, p.tb, p.VB, p.Ax, p.sc, (int)i, j, k);
-        else if constexpr (PH == PH_TAU) visc_tau_body<T, F>(m, p.tb, p.Ax, p.tau, p.sc, (int)i, j, k);
-        else if constexpr (PH == PH_VAPPLY) visc_apply_body<T, F>(m, p.tb, p.Ax, p.VB, p.tau, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_AV) artvisc_body<T, F>(m, p.tb, p.VB, p.A, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_TAU) visc_tau_body<T, F>(m, p.tb, p.A, p.tau, p.sc, (int)i, j, k);
+        else if constexpr (PH == PH_VAPPLY) visc_apply_body<T, F>(m, p.tb, p.A, p.VB, p.tau, p.sc, (int)i, j, k);
         else newvel_body<T, F>(m, p.tb, p.qfin, p.vsrc, p.A, p.sc, 0, (int)i, j, k);
         i += blockDim.x;
         while (i >= nx) {
@@ -168,7 +168,7 @@ struct BTxOp {
         const RingMeta<T> &e = meta[it];
         if (e.N < 0) return;
         const StepPlan<T> &p = P[e.id];
-        tx_compute<T, C>(p.m, p.tb, p.qx, e.local, src, e.a, e.b, step_dt<T>(p.sc), p.txin.dx != nullptr);
+        tx_compute<T, C>(p.m, p.tb, p.qx, e.local, src, e.a, e.b, step_dt<T>(p.sc));
     }
     __device__ void fail(int it) { atomicOr(&P[meta[it].id].sc->err, kErrTimeout); }
 };

@@ -84,31 +84,11 @@ __device__ __forceinline__ T vref_at(const Tab<T> &tb, int ring)
     return sizeof(T) == 4 && tb.vref ? tb.vref[ring] : T(0);
 }
 
-// The fields a kernel reads or writes.  dx, in the FP32 step only, holds the
-// source step's accumulated increment of the azimuthal velocity: the source
-// sub-steps leave the stored v_x untouched and add their changes to dx, so
-// that changes far below the FP32 resolution of v_x (a thin disk's viscous
-// torque changes v_phi by about 1e-7 of itself per step) are not rounded
-// away sub-step after sub-step; the post-source azimuthal velocity is
-// vx + dx, and the transport step takes both.  Null in FP64.
+// The fields a kernel reads or writes.
 template <typename T>
 struct Fld {
     T *rho, *e, *vx, *vy, *vz;
-    T *dx;
 };
-
-// The post-source azimuthal velocity of face q, and the difference of two
-// faces with the increments differenced apart (no absorption of dx in vx).
-template <typename T>
-__device__ __forceinline__ T vx_at(const Fld<T> &f, int q)
-{
-    return f.dx ? f.vx[q] + f.dx[q] : f.vx[q];
-}
-template <typename T>
-__device__ __forceinline__ T vx_diff(const Fld<T> &f, int a, int b)
-{
-    return f.dx ? (f.vx[a] - f.vx[b]) + (f.dx[a] - f.dx[b]) : f.vx[a] - f.vx[b];
-}
 
 // Up to eight transported quantities: rho, e, Pi-x, Pi+x, Pi-y, Pi+y, Pi-z, Pi+z.
 template <typename T>

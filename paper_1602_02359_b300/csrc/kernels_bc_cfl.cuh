@@ -78,9 +78,8 @@ __device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const
     int k = (int)(r % (m.nzt + 1));
     int side = (int)(r / (m.nzt + 1));
     int bc = m.bcy[side];
-    // (the increment of the azimuthal velocity, when present, is filled as v_x is)
-    T *fl[6] = {f.rho, m.iso ? nullptr : f.e, f.vx, f.vy, f.vz, f.dx};
-    for (int q = 0; q < 6; q++) {
+    T *fl[5] = {f.rho, m.iso ? nullptr : f.e, f.vx, f.vy, f.vz};
+    for (int q = 0; q < 5; q++) {
         if (!fl[q]) continue;
         if (q == 4 && !m.hasZ) continue;
         int kmax = q == 4 ? m.nzt + 1 : m.nzt;
@@ -101,8 +100,8 @@ __device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const
     int j = (int)(r % (m.nyt + 1));
     int side = (int)(r / (m.nyt + 1));
     int bc = m.bcz[side];
-    T *fl[6] = {f.rho, m.iso ? nullptr : f.e, f.vx, f.vy, f.vz, f.dx};
-    for (int q = 0; q < 6; q++) {
+    T *fl[5] = {f.rho, m.iso ? nullptr : f.e, f.vx, f.vy, f.vz};
+    for (int q = 0; q < 5; q++) {
         if (!fl[q]) continue;
         if (q == 3 && !m.hasY) continue;
         int jmax = q == 3 ? m.nyt + 1 : m.nyt;
@@ -197,7 +196,6 @@ static PerSet<T> per_fields(const MeshD &m, const Fld<T> &f, bool vel, bool ener
     };
     if (vel) {
         add(f.vx, 0, 0);
-        if (f.dx) add(f.dx, 0, 0);
         if (m.hasY) add(f.vy, 1, 0);
         if (m.hasZ) add(f.vz, 0, 1);
     }

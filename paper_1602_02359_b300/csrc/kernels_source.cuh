@@ -83,7 +83,6 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     const int ip = i + 1 == m.nx ? 0 : i + 1;
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
-        T inc = T(0);
         if (F::hasX(m) && jact && kact) {
             const idx_t cm = c - i + im;
             const T id = tb.ilenx[ring];
@@ -92,11 +91,8 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
             if (F::planet(m))
                 acc -= (phi_planet<T, F>(m, tb, i, ring) - phi_planet<T, F>(m, tb, im, ring)) * id;
             v = v + dt * acc;
-            inc = dt * acc;
         }
-        // the increment form keeps the stored v_x and starts the increment
-        if (out.dx) out.dx[c] = inc;
-        else out.vx[c] = v;
+        out.vx[c] = v;
     }
     if (k < m.nzt) {
         T v = in.vy[c];
@@ -187,27 +183,18 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     const int ipp = ip + 1 == m.nx ? 0 : ip + 1;
     const T *vx = in.vx, *vy = in.vy, *vz = in.vz, *rho = in.rho;
     const idx_t sj = m.sj, sk = m.sk;
-    // own lower faces (in the increment form of v_x: vxl the stored value,
-    // dxl the post-viscosity increment; otherwise vxl the post-viscosity value)
-    T vxl = 0, dxl = 0, vyl = 0, vzl = 0;
+    // own lower faces
+    T vxl = 0, vyl = 0, vzl = 0;
     if (j < m.nyt && k < m.nzt) {
         T v = vx[c];
-        T inc = T(0);
         if (av && F::hasX(m) && jact && kact) {
             const idx_t cm = c - i + im, cp = c - i + ip;
-            const T q0 = qvisc(c2, rho[c], vx_diff(in, cp, c));
-            const T qm = qvisc(c2, rho[cm], vx_diff(in, c, cm));
-            inc = div_fast(dt * T(2) * (q0 - qm) * tb.ilenx[ring], rho[c] + rho[cm]);
-            v -= inc;
+            const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
+            const T qm = qvisc(c2, rho[cm], vx[c] - vx[cm]);
+            v -= div_fast(dt * T(2) * (q0 - qm) * tb.ilenx[ring], rho[c] + rho[cm]);
         }
-        if (out.dx) {
-            dxl = in.dx[c] - inc;
-            out.dx[c] = dxl;
-        } else {
-            out.vx[c] = v;
-        }
+        out.vx[c] = v;
         vxl = v;
-        if (out.dx) vxl = vx[c];
     }
     if (k < m.nzt) {
         T v = vy[c];
@@ -237,7 +224,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     T h = 0;
     if (av) {
         if (F::hasX(m)) {
-            const T dv = vx_diff(in, c - i + ip, c);
+            const T dv = vx[c - i + ip] - vx[c];
             h += qvisc(c2, rho[c], dv) * dv * tb.ilenx[ring];
         }
         if (F::hasY(m)) {
@@ -254,15 +241,13 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     T div = 0;
     if (F::hasX(m)) {
         const idx_t cp = c - i + ip, cpp = c - i + ipp;
-        T vxu = vx[cp], dxu = in.dx ? in.dx[cp] : T(0);
+        T vxu = vx[cp];
         if (av) {
-            const T qp = qvisc(c2, rho[cp], vx_diff(in, cpp, cp));
-            const T q0 = qvisc(c2, rho[c], vx_diff(in, cp, c));
-            const T inc = div_fast(dt * T(2) * (qp - q0) * tb.ilenx[ring], rho[cp] + rho[c]);
-            if (in.dx) dxu -= inc;
-            else vxu -= inc;
+            const T qp = qvisc(c2, rho[cp], vx[cpp] - vx[cp]);
+            const T q0 = qvisc(c2, rho[c], vx[cp] - vx[c]);
+            vxu -= div_fast(dt * T(2) * (qp - q0) * tb.ilenx[ring], rho[cp] + rho[c]);
         }
-        div += tb.sx[ring] * ((vxu - vxl) + (dxu - dxl));
+        div += tb.sx[ring] * (vxu - vxl);
     }
     const int fr = k * (m.nyt + 1) + j;
     if (F::hasY(m)) {
@@ -300,18 +285,12 @@ template <typename T, class F = CfgRun>
 struct ViscCtx {
     const MeshD &m;
     const Tab<T> &tb;
-    const T *rho, *vxs, *vy, *vz, *dx;
+    const T *rho, *vx, *vy, *vz;
     __device__ ViscCtx(const MeshD &m_, const Tab<T> &tb_, const Fld<T> &f)
-        : m(m_), tb(tb_), rho(f.rho), vxs(f.vx), vy(f.vy), vz(f.vz), dx(f.dx) {}
-    // post-viscosity azimuthal velocity of face q on ring `ring` (the stored
-    // value, its increment and, in the reference form, the ring's reference)
-    __device__ T vxa(int q, int ring) const
-    {
-        const T v = dx ? vxs[q] + dx[q] : vxs[q];
-        return sizeof(T) == 4 && tb.vref ? v + tb.vref[ring] : v;
-    }
-    // difference of two faces' azimuthal velocities, increments differenced apart
-    __device__ T dvx(int a, int b) const { return dx ? (vxs[a] - vxs[b]) + (dx[a] - dx[b]) : vxs[a] - vxs[b]; }
+        : m(m_), tb(tb_), rho(f.rho), vx(f.vx), vy(f.vy), vz(f.vz) {}
+    // azimuthal velocity of face q on ring `ring` (in the reference form the
+    // stored value plus the ring's reference)
+    __device__ T vxa(int q, int ring) const { return sizeof(T) == 4 && tb.vref ? vx[q] + tb.vref[ring] : vx[q]; }
     __device__ int wrap(int i) const { return i < 0 ? i + m.nx : (i >= m.nx ? i - m.nx : i); }
     __device__ idx_t at(int i, int j, int k) const { return IX(m, wrap(i), j, k); }
     __device__ T nu(int j, int k) const { return tb.nu[k * m.nyt + j]; }
@@ -321,7 +300,7 @@ struct ViscCtx {
         const idx_t c = at(i, j, k);
         const int ring = k * m.nyt + j, fr = k * (m.nyt + 1) + j;
         T f = 0;
-        if (F::hasX(m)) f += tb.sx[ring] * dvx(at(i + 1, j, k), c);
+        if (F::hasX(m)) f += tb.sx[ring] * (vx[at(i + 1, j, k)] - vx[c]);
         if (F::hasY(m)) f += tb.sy[fr + 1] * vy[c + m.sj] - tb.sy[fr] * vy[c];
         if (F::hasZ(m)) f += tb.sz[fr + m.nyt + 1] * vz[c + m.sk] - tb.sz[fr] * vz[c];
         return f * tb.vinv[ring];
@@ -333,7 +312,7 @@ struct ViscCtx {
         const int ring = k * m.nyt + j;
         const T dv = divv(i, j, k);
         const T rn = rho[c] * nu(j, k);
-        const T dxx = dvx(at(i + 1, j, k), c) * tb.ilenx[ring];
+        const T dxx = (vx[at(i + 1, j, k)] - vx[c]) * tb.ilenx[ring];
         const T dyy = F::hasY(m) ? (vy[c + m.sj] - vy[c]) * tb.idy[j] : T(0);
         const T dzz = F::hasZ(m) ? (vz[c + m.sk] - vz[c]) * tb.ilenz[ring] : T(0);
         const T tw = T(2.0 / 3.0) * dv;
@@ -427,7 +406,6 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
     const T *rho = in.rho;
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
-        T dv = in.dx ? in.dx[c] : T(0);
         if (jact && kact) {
             const idx_t cm = V.at(i - 1, j, k);
             T a0, a1, a2, b0, b1, b2;
@@ -462,12 +440,9 @@ __device__ __forceinline__ void visc_apply(const MeshD &m, const Tab<T> &tb, con
                 if (F::hasY(m)) f += T(0.5) * (ty0 + ty1) * ir;
                 if (F::hasZ(m)) f += T(2) * T(0.5) * (tz0 + tz1) * ct * ir;
             }
-            const T inc = div_fast(T(2) * dt * f, rho[c] + rho[cm]);
-            v = v - inc;
-            dv -= inc;
+            v = v - div_fast(T(2) * dt * f, rho[c] + rho[cm]);
         }
-        if (out.dx) out.dx[c] = dv;
-        else out.vx[c] = v;
+        out.vx[c] = v;
     }
     if (k < m.nzt) {
         T v = in.vy[c];

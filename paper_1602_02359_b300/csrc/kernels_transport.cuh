@@ -222,15 +222,14 @@ __device__ __forceinline__ void ring_bars_init(uint64_t *bar)
 // velocity is delta v = v_x - v0 (v0 = 0 for STANDARD transport).  Ghost
 // rings only get their momenta written (the Y/Z sweeps read them).
 struct TxRows {
-    int n, rE, rVX, rVY, rVZ, rDX;   // staged rows: rho, e, vx, vy(j), vy(j+1), vz(k), vz(k+1), v_x increment
+    int n, rE, rVX, rVY, rVZ;   // staged rows: rho, e, vx, vy(j), vy(j+1), vz(k), vz(k+1)
 };
-__device__ __host__ __forceinline__ TxRows tx_rows(const MeshD &m, bool dx = false)
+__device__ __forceinline__ TxRows tx_rows(const MeshD &m)
 {
-    TxRows r{0, -1, -1, -1, -1, -1};
+    TxRows r{0, -1, -1, -1, -1};
     r.n = 1;
     if (!m.iso) r.rE = r.n++;
     r.rVX = r.n++;
-    if (dx) r.rDX = r.n++;
     if (m.hasY) {
         r.rVY = r.n;
         r.n += 2;
@@ -261,7 +260,7 @@ __device__ __forceinline__ void tx_v0(const MeshD &m, const Tab<T> &tb, const do
 template <typename T>
 __device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int ring, T *dst, uint64_t *bar)
 {
-    const TxRows r = tx_rows(m, in.dx != nullptr);
+    const TxRows r = tx_rows(m);
     const int j = ring % m.nyt, k = ring / m.nyt;
     const idx_t base = IX(m, 0, j, k);
     const size_t rp = (size_t)ring_row(m.sj);
@@ -271,7 +270,6 @@ __device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int r
     bulk_load(dst, in.rho + base, bytes, bar);
     if (r.rE >= 0) bulk_load(dst + r.rE * rp, in.e + base, bytes, bar);
     bulk_load(dst + r.rVX * rp, in.vx + base, bytes, bar);
-    if (r.rDX >= 0) bulk_load(dst + r.rDX * rp, in.dx + base, bytes, bar);
     if (r.rVY >= 0) {
         bulk_load(dst + r.rVY * rp, in.vy + base, bytes, bar);
         bulk_load(dst + (r.rVY + 1) * rp, in.vy + base + m.sj, bytes, bar);
@@ -284,10 +282,10 @@ __device__ __forceinline__ void tx_issue(const MeshD &m, const Fld<T> &in, int r
 
 template <typename T, int C>
 __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, const QSet<T> &out, int ring, T *buf,
-                                           T v0hi, T v0lo, T dt, bool hasdx)
+                                           T v0hi, T v0lo, T dt)
 {
     const int nx = m.nx, nq = out.nq, rp = ring_row(m.sj);
-    const TxRows rw = tx_rows(m, hasdx);
+    const TxRows rw = tx_rows(m);
     ring_frame(buf, rw.n, rp, nx);
     const T *sm = buf + kRingLead;   // cell i of staged row r: sm[r * rp + i], -kRingLead <= i < nx + kRingTail
     const int j = ring % m.nyt, k = ring / m.nyt;
@@ -301,44 +299,37 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     // then held as rho R (v_x - vref), with v_x - vref the stored value)
     const T w = sizeof(T) == 4 && tb.vref ? T(0) : (m.geom == CART ? tb.wfr[ring] : R * R * tb.omega);
     const T *Rho = sm, *Vx = sm + (size_t)rw.rVX * rp;
-    const T *Dx = hasdx ? sm + (size_t)rw.rDX * rp : nullptr;   // v_x increment of the source step
-    // ratio of quantity q to the density at cell i, as scale * (row[i + off]
-    // + inc[i + off]) + shift (or e / rho), for the order rho, e, Pi-x, Pi+x,
-    // Pi-y, Pi+y, Pi-z, Pi+z of the present components
+    // ratio of quantity q to the density at cell i, as scale * row[i + off] +
+    // shift (or e / rho), for the order rho, e, Pi-x, Pi+x, Pi-y, Pi+y,
+    // Pi-z, Pi+z of the present components
     struct RatioSpec {
-        const T *row, *inc;
+        const T *row;
         int off, div;
         T a, b;
     };
     auto spec = [&](int q) -> RatioSpec {
-        if (q == 0) return {Rho, nullptr, 0, 0, T(1), T(0)};
+        if (q == 0) return {Rho, 0, 0, T(1), T(0)};
         int o = q - 1;
         if (adi) {
-            if (o == 0) return {sm + (size_t)rw.rE * rp, nullptr, 0, 1, T(1), T(0)};
+            if (o == 0) return {sm + (size_t)rw.rE * rp, 0, 1, T(1), T(0)};
             o -= 1;
         }
-        if (o == 0) return {Vx, Dx, 0, 0, R, w};
-        if (o == 1) return {Vx, Dx, 1, 0, R, w};
+        if (o == 0) return {Vx, 0, 0, R, w};
+        if (o == 1) return {Vx, 1, 0, R, w};
         if (m.hasY) {
-            if (o == 2) return {sm + (size_t)rw.rVY * rp, nullptr, 0, 0, T(1), T(0)};
-            if (o == 3) return {sm + (size_t)(rw.rVY + 1) * rp, nullptr, 0, 0, T(1), T(0)};
+            if (o == 2) return {sm + (size_t)rw.rVY * rp, 0, 0, T(1), T(0)};
+            if (o == 3) return {sm + (size_t)(rw.rVY + 1) * rp, 0, 0, T(1), T(0)};
             o -= 2;
         }
-        if (o == 2) return {sm + (size_t)rw.rVZ * rp, nullptr, 0, 0, fz, T(0)};
-        return {sm + (size_t)(rw.rVZ + 1) * rp, nullptr, 0, 0, fz, T(0)};
-    };
-    // the ratio of the momenta: R (v + dv) + w, the increment added to the
-    // product of the stored value so that it is not absorbed in v first
-    auto ratio = [](const RatioSpec &sp, T v, int at) -> T {
-        const T r = sp.a * v + sp.b;
-        return sp.inc ? r + sp.a * sp.inc[at] : r;
+        if (o == 2) return {sm + (size_t)rw.rVZ * rp, 0, 0, fz, T(0)};
+        return {sm + (size_t)(rw.rVZ + 1) * rp, 0, 0, fz, T(0)};
     };
     if (!sweep) {
         for (int q = 0; q < nq; q++) {
             const RatioSpec sp = spec(q);
             for (int i = threadIdx.x; i < nx; i += blockDim.x) {
                 const T v = sp.row[i + sp.off];
-                out.q[q][base + i] = q == 0 ? v : (sp.div ? v : Rho[i] * ratio(sp, v, i + sp.off));
+                out.q[q][base + i] = q == 0 ? v : (sp.div ? v : Rho[i] * (sp.a * v + sp.b));
             }
         }
         return;
@@ -351,10 +342,7 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
     const int cnt = min(C, nx - i0);
     T vf[C + 1], F0[C + 1];
 #pragma unroll
-    for (int u = 0; u <= C; u++) {
-        vf[u] = sub_split(Vx[i0 + u], v0hi, v0lo);
-        if (Dx) vf[u] += Dx[i0 + u];
-    }
+    for (int u = 0; u <= C; u++) vf[u] = sub_split(Vx[i0 + u], v0hi, v0lo);
     T rho[C + 4];
 #pragma unroll
     for (int s = 0; s < C + 4; s++) rho[s] = Rho[i0 - 2 + s];
@@ -369,7 +357,7 @@ __device__ __forceinline__ void tx_compute(const MeshD &m, const Tab<T> &tb, con
 #pragma unroll
         for (int s = 0; s < C + 4; s++) {
             const T v = win[s];
-            a[s] = sp.div ? v / rho[s] : ratio(sp, v, i0 - 2 + sp.off + s);
+            a[s] = sp.div ? v / rho[s] : sp.a * v + sp.b;
         }
         T sl[C + 2];  // van Leer slopes of cells i0-1 .. i0+C
 #pragma unroll
@@ -683,7 +671,7 @@ struct TxOp {
     __device__ void issue(int it, T *dst, uint64_t *bar) { tx_issue(m, in, meta[it].local, dst, bar); }
     __device__ void compute(int it, T *src)
     {
-        tx_compute<T, C>(m, tb, out, meta[it].local, src, meta[it].a, meta[it].b, dt, in.dx != nullptr);
+        tx_compute<T, C>(m, tb, out, meta[it].local, src, meta[it].a, meta[it].b, dt);
     }
     __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
 };
@@ -1013,10 +1001,14 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
     // (dA(f) = A(f) - A(f - 1) at face f), and a face flux computed in the
     // frame of the row below moves to the frame of the row above by
     // subtracting the mass flux times dA.  Other quantities are not shifted.
+    // The X momenta are quantities QX and QX + 1: after rho and, for an
+    // adiabatic gas, e; the quantity count is odd exactly when the gas is
+    // isothermal (rho, then pairs of momenta).
+    constexpr int QX = NQ % 2 == 1 ? 1 : 2;
     const bool rf = sizeof(T) == 4 && tb.dAy != nullptr;
-    const unsigned xm = rf ? (3u << (m.iso ? 1 : 2)) : 0u;
     auto dA = [&](int f) -> T { return !rf ? T(0) : (AXIS == 1 ? tb.dAy[c2 * m.nyt + f] : tb.dAz[f * m.nyt + c2]); };
-    auto sh = [&](int q, T d) -> T { return (xm >> q) & 1u ? d : T(0); };
+    auto isx = [](int q) { return q == QX || q == QX + 1; };
+    auto sh = [&](int q, T d) -> T { return isx(q) ? d : T(0); };
     bool ok = true;
     // fetch row r into ratios + face velocity; the stage is released by
     // release(r) once the row is no longer needed: after the first fluxes for
@@ -1071,12 +1063,16 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
             const T stv = v >= T(0) ? Rm1[q] + am * (wl - v * dt) * T(0.5) : (R0[q] + s1) - a0 * (wr + v * dt) * T(0.5);
             if (q == 0) F0 = v * stv * Sa;
             const T Fup = q == 0 ? F0 : mul_rn(F0, stv);
-            Flo[q] = rf && ((xm >> q) & 1u) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row ps
+            Flo[q] = rf && isx(q) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row ps
         }
     }
     release(0);
     release(1);
+    // frame shifts of faces p + 1 and p + 2; the next ones are loaded two
+    // iterations ahead (a load per row, off the critical path)
+    T e1 = dA(ps + 1), e2 = dA(ps + 2), e3 = ps + 2 <= pe ? dA(ps + 3) : T(0);
     for (int p = ps; p < pe; p++) {
+        const T e4 = p + 3 <= pe ? dA(p + 4) : T(0);   // face p + 4 <= pe + 1, inside the table
         const T v = v1f;   // face p+1
         const T dn = icd(p + 1), dnn = icd(p + 2);
         const T wp = width(p), wn = width(p + 1);
@@ -1086,7 +1082,6 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
         const int rp = p - ps + 2;   // row index of p
         const T *raw = stage + (size_t)(rp % S) * ROW + threadIdx.x;
         T F0 = 0;
-        const T e1 = dA(p + 1), e2 = dA(p + 2);
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
             const T s1 = sh(q, e1), s2 = sh(q, e2);
@@ -1096,10 +1091,13 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
             if (q == 0) F0 = v * stv * Sa;
             const T Fup = q == 0 ? F0 : mul_rn(F0, stv);
             if (col) out.q[q][c] = raw[q * TW] - dtVi * (Fup - Flo[q]);
-            Flo[q] = rf && ((xm >> q) & 1u) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row p + 1
+            Flo[q] = rf && isx(q) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row p + 1
             aP[q] = aN;
         }
         release(rp);
+        e1 = e2;
+        e2 = e3;
+        e3 = e4;
         if (p + 1 < pe) {
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
@@ -1230,8 +1228,6 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
                 const T w = F::geom(m) == CART ? tb.wfr[ring] : R * R * tb.omega;
                 state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
             }
-        } else if (vsrc.dx) {
-            state.vx[c] = vsrc.vx[c] + vsrc.dx[c];   // the post-source value of a ghost ring's face
         } else if (vsrc.vx != state.vx) {
             state.vx[c] = vsrc.vx[c];
         }

@@ -82,9 +82,8 @@ def test_viscous_ring_fp32_follows_analytic():
     0.16 % and 0.62 % in FP64.  Each step changes the Keplerian v_phi by
     about 3e-7 of itself through the viscous torque, a few FP32 units in
     the last place of v_phi; the FP32 step keeps v_phi relative to a
-    per-ring reference and its source-step change as a separate increment,
-    so the torque is not rounded away (stored as v_phi itself it was: 0.95 %
-    and 2.3 %, the precision question of Sec. 6).  Bounds at about twice
+    per-ring reference, so the torque is not rounded away (stored as v_phi
+    itself it was: 0.95 % and 2.3 %, the precision question of Sec. 6).  Bounds at about twice
     the measured errors."""
     import paper_1602_02359_b300 as fb
     w = W.viscous_ring()
