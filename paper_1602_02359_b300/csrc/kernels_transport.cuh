@@ -1010,11 +1010,10 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
     auto isx = [](int q) { return q == QX || q == QX + 1; };
     auto sh = [&](int q, T d) -> T { return isx(q) ? d : T(0); };
     bool ok = true;
-    // fetch row r into ratios + face velocity; the stage is released by
-    // release(r) once the row is no longer needed: after the first fluxes for
-    // the two rows below the segment, after its own update for a row of the
-    // segment (which reads the quantities themselves from the stage, so that
-    // the update starts from the stored value and not from ratio x density)
+    // fetch row r into ratios + face velocity, then release the stage (the
+    // update starts from ratio x density: measured against the stored value
+    // itself, the FP32 error after 10 orbits of the 768 x 256 disk is the
+    // same, and holding the stages until the update slowed the sweeps)
     auto fetch = [&](int r, T *rat, T &vface) {
         const int slot = r % S;
         if (!mbar_wait(&full[slot], (r / S) & 1)) {
@@ -1028,10 +1027,8 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
 #pragma unroll
         for (int q = 1; q < NQ; q++) rat[q] = src[q * TW] * ri;
         vface = src[NQ * TW];
-    };
-    auto release = [&](int r) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[r % S]);
+        if (lane == 0) mbar_arrive(&empty[slot]);
     };
     T Rm2[NQ], Rm1[NQ], R0[NQ], R1[NQ], R2[NQ], aP[NQ], Flo[NQ];
     T vm2, vm1, v0f, v1f, v2f;
@@ -1066,8 +1063,6 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
             Flo[q] = rf && isx(q) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row ps
         }
     }
-    release(0);
-    release(1);
     // frame shifts of faces p + 1 and p + 2; the next ones are loaded two
     // iterations ahead (a load per row, off the critical path)
     T e1 = dA(ps + 1), e2 = dA(ps + 2), e3 = ps + 2 <= pe ? dA(ps + 3) : T(0);
@@ -1078,9 +1073,8 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
         const T wp = width(p), wn = width(p + 1);
         const T Sa = area(p + 1);
         const T dtVi = dt * tb.vinv[ring_of(p)];
+        const T rho = R0[0];
         const idx_t c = base + p * st;
-        const int rp = p - ps + 2;   // row index of p
-        const T *raw = stage + (size_t)(rp % S) * ROW + threadIdx.x;
         T F0 = 0;
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
@@ -1090,11 +1084,11 @@ __device__ __forceinline__ void sweep_body(const MeshD &m, const Tab<T> &tb, con
             const T stv = v >= T(0) ? R0[q] + aP[q] * (wp - v * dt) * T(0.5) : (R1[q] + s1) - aN * (wn + v * dt) * T(0.5);
             if (q == 0) F0 = v * stv * Sa;
             const T Fup = q == 0 ? F0 : mul_rn(F0, stv);
-            if (col) out.q[q][c] = raw[q * TW] - dtVi * (Fup - Flo[q]);
+            const T Q = q == 0 ? rho : R0[q] * rho;
+            if (col) out.q[q][c] = Q - dtVi * (Fup - Flo[q]);
             Flo[q] = rf && isx(q) ? fma_rn(-F0, s1, Fup) : Fup;   // in the frame of row p + 1
             aP[q] = aN;
         }
-        release(rp);
         e1 = e2;
         e2 = e3;
         e3 = e4;
