@@ -230,10 +230,13 @@ int fargo_nbody_rk5_async(int n, double *y, const double *mass, double mstar, do
  *   3. fargo_nbody_rk5_async with h = the dt of the context's last step,
  *      read on the device, and the context's star mass.
  * y ([n][6]) and mass ([n]) are device memory owned by the caller; y is
- * updated in place.  The force scratch belongs to the context.  The
- * integrator's star-centred, non-rotating coordinates are taken as the
- * mesh's, so the context's frame must not rotate (Omega_f = 0).  Errors: as
- * fargo_planets_force_async, plus BADARG for a rotating frame. */
+ * updated in place.  The force scratch belongs to the context.  y is in the
+ * integrator's star-centred, non-rotating axes; the mesh's axes make the
+ * frame angle theta(t) with them (theta = 0 at t = 0 and in a frame that
+ * has never rotated; theta advances at Omega_f and stays continuous through
+ * fargo_change_frame and fargo_track_frame), so positions are turned by
+ * -theta onto the mesh and the forces back by +theta (fargo_planets_force_async
+ * likewise).  Errors: as fargo_planets_force_async. */
 int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *mass, double eps, int bm08,
                                 int indirect);
 
@@ -248,12 +251,13 @@ int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *
  * may be NULL only for n = 1 (the planet of creation's mass).  So the
  * integrator (fargo_planets_advance_async on the same rows) and the step
  * alternate on the stream with no host round trip.  NULL pos returns to
- * the fixed circular orbit.  Requires a planet at creation, a cylindrical or
- * spherical mesh and a non-rotating frame (the integrator's coordinates are
- * the mesh's); pos and mass 8-byte aligned, owned by the caller and valid
- * while set.  Errors: BADARG (no planet, Cartesian mesh, Omega_f != 0,
- * context held by a batch, n < 1, stride < 3, n > 1 without masses,
- * misaligned pointer), SIZE (n > FARGO_MAX_POT_PLANETS). */
+ * the fixed circular orbit.  The positions are in the integrator's
+ * non-rotating axes and are turned onto the mesh by the frame angle at the
+ * step's time (see fargo_planets_advance_async).  Requires a planet at
+ * creation and a cylindrical or spherical mesh; pos and mass 8-byte
+ * aligned, owned by the caller and valid while set.  Errors: BADARG (no
+ * planet, Cartesian mesh, context held by a batch, n < 1, stride < 3,
+ * n > 1 without masses, misaligned pointer), SIZE (n > FARGO_MAX_POT_PLANETS). */
 #define FARGO_MAX_POT_PLANETS 8
 int fargo_set_planet_source(fargo_ctx *ctx, const double *pos, int n, int stride, const double *mass);
 
@@ -266,9 +270,24 @@ int fargo_set_planet_source(fargo_ctx *ctx, const double *pos, int n, int stride
  * and then advances at the new relative rate.  Later steps use the new
  * rate in the Coriolis and centrifugal terms and in the momenta.  Cylindrical
  * and spherical meshes; a context held by a batch cannot change frame (the
- * batch holds its members' frames).  Synchronises.  Errors: BADARG (NULL,
+ * batch holds its members' frames).  In FP32 the per-ring references of v_x
+ * are chosen afresh in the new frame.  Synchronises.  Errors: BADARG (NULL,
  * non-finite omega_new, Cartesian mesh, context held by a batch), CUDA. */
 int fargo_change_frame(fargo_ctx *ctx, double omega_new);
+
+/* Frame tracking (Sec. 3.2, cell 5b of Fig. 2: the x axis follows a planet),
+ * called before a step: the frame rate becomes the angular velocity about
+ * the polar axis of body `index` of the planetary state y (rows of 6
+ * doubles x, y, z, vx, vy, vz in the integrator's non-rotating axes, device
+ * memory, as for fargo_nbody_rk5_async), (x vy - y vx) / (x^2 + y^2), and
+ * the azimuthal velocities are corrected by Eq. 13 as in fargo_change_frame
+ * (the frame's time derivative enters the method only through this
+ * correction).  In FP32 the stored v_x - vref is corrected in place and the
+ * references are kept.  The frame angle stays continuous.  Synchronises
+ * (reads the body's six values).  omega_out, when not NULL, receives the new
+ * rate.  Errors: BADARG (NULL y, index outside 0..31, body on the polar
+ * axis, Cartesian mesh, context held by a batch, misaligned y), CUDA. */
+int fargo_track_frame(fargo_ctx *ctx, const double *y, int index, double *omega_out);
 
 /* Conserved totals over active cells with compensated FP64 sums:
  * out[0] = sum rho V, out[1] = sum e V, out[2] = sum (Pi-_x + Pi+_x)/2 V

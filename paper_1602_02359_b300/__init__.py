@@ -30,7 +30,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_alu_peaks", "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
             "fargo_batch_profile_step", "fargo_batch_autotune", "fargo_batch_set_field_packed",
-            "fargo_batch_get_field_packed", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_set_planet_source", "fargo_planet_torque_profile", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_get_field_packed", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_track_frame", "fargo_set_planet_source", "fargo_planet_torque_profile", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -98,6 +98,7 @@ def lib():
                                             vp]
         L.fargo_planets_advance_async.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int]
         L.fargo_change_frame.argtypes = [vp, C.c_double]
+        L.fargo_track_frame.argtypes = [vp, vp, C.c_int, PD]
         L.fargo_set_planet_source.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.fargo_planet_torque_profile.argtypes = [vp, PD, C.c_double, C.c_int, vp, PD]
         L.fargo_debug_phase.argtypes = [vp, C.c_int, C.c_double]
@@ -298,6 +299,14 @@ class Fargo:
         """fargo_change_frame: the frame's rotation rate becomes omega_new at
         the current time (Eq. 13)."""
         _check(lib().fargo_change_frame(self.h, float(omega_new)), "fargo_change_frame")
+
+    def track_frame(self, y_ptr, index=0):
+        """fargo_track_frame: the frame rate becomes the angular velocity of
+        body `index` of the device planetary state at y_ptr (rows of 6
+        doubles), with the Eq. 13 correction; returns the new rate."""
+        om = C.c_double()
+        _check(lib().fargo_track_frame(self.h, C.c_void_p(y_ptr), int(index), C.byref(om)), "fargo_track_frame")
+        return om.value
 
     def planets_force_async(self, n, y_ptr, stride, eps, out_ptr, bm08=False):
         """fargo_planets_force_async: the gas force on n planets whose

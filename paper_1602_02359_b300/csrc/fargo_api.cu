@@ -1104,7 +1104,9 @@ extern "C" int fargo_planets_force_async(fargo_ctx *c, int n, const double *y, i
     if (c->geom == FARGO_CART || !aligned8(y) || !aligned8(out)) return FARGO_ERR_BADARG;
     if (n > kNbMax) return FARGO_ERR_SIZE;
     for (int i = 0; i < n; i++) {
-        const int rc = pforce_any(c, PfPlanet{0.0, 0.0, 0.0, y + (size_t)stride * i}, eps, bm08, out + 4 * i);
+        // positions and forces in the integrator's axes (the mesh turned by its frame angle)
+        const int rc = pforce_any(c, PfPlanet{0.0, 0.0, 0.0, y + (size_t)stride * i, c->m.fr0, c->m.omega, c->sc},
+                                  eps, bm08, out + 4 * i);
         if (rc) return rc;
     }
     return FARGO_OK;
@@ -1149,15 +1151,15 @@ extern "C" int fargo_planets_advance_async(fargo_ctx *c, int n, double *y, const
 {
     if (!c || !y || !mass || n < 1 || !(eps >= 0.0) || !isfinite(eps)) return FARGO_ERR_BADARG;
     if (c->geom == FARGO_CART || !aligned8(y) || !aligned8(mass)) return FARGO_ERR_BADARG;
-    // the integrator's star-centred coordinates are the mesh's only in a non-rotating frame
-    if (c->m.omega != 0.0) return FARGO_ERR_BADARG;
     if (n > kNbMax) return FARGO_ERR_SIZE;
     int rc = fargo_planets_force_async(c, n, y, 6, eps, bm08, c->pacc);
     if (rc) return rc;
     const double *star = nullptr;
     if (indirect) {
         // the star sits at the origin, which no cell of a cylindrical or spherical mesh contains
-        if ((rc = pforce_any(c, PfPlanet{0.0, 0.0, 0.0, nullptr}, 0.0, 0, c->pacc + 4 * kNbMax))) return rc;
+        if ((rc = pforce_any(c, PfPlanet{0.0, 0.0, 0.0, nullptr, c->m.fr0, c->m.omega, c->sc}, 0.0, 0,
+                             c->pacc + 4 * kNbMax)))
+            return rc;
         star = c->pacc + 4 * kNbMax;
     }
     return nbody_launch(n, y, mass, c->star_mass, 0.0, &c->sc->dt, c->pacc, 4, star, indirect, c->stream);
@@ -1181,8 +1183,12 @@ __global__ void __launch_bounds__(256) k_change_frame(T *vx, const double *Rd, d
     }
 }
 
+// rebase: in FP32, go through the v_x form and choose the references afresh
+// in the new frame (a change of any size); otherwise correct the stored
+// v_x - vref directly and refresh the frame shifts only (small changes, as
+// when the frame tracks a planet: the stored values stay small).
 template <typename T>
-static int change_frame_impl(fargo_ctx *c, Buffers<T> &b, double omega_new)
+static int change_frame_impl(fargo_ctx *c, Buffers<T> &b, double omega_new, bool rebase)
 {
     Scal sh;
     int rc = read_scal(c, &sh);   // the current time (synchronises)
@@ -1190,8 +1196,7 @@ static int change_frame_impl(fargo_ctx *c, Buffers<T> &b, double omega_new)
     MeshD &m = c->m;
     const double dom = omega_new - m.omega;
     const long long n = (long long)m.nx * m.nyt * m.nzt;
-    // (FP32: through the v_x form, and references chosen afresh in the new frame)
-    if ((rc = vref_launch<T>(c, b, VREF_ABS, nullptr, c->stream))) return rc;
+    if (rebase && (rc = vref_launch<T>(c, b, VREF_ABS, nullptr, c->stream))) return rc;
     k_change_frame<T><<<grid_for(n, 256), 256, 0, c->stream>>>(b.A.vx, b.tab.Rd, dom, m.nx, m.nyt, m.nzt, m.sj,
                                                                  m.sk);
     CK(cudaGetLastError());
@@ -1200,9 +1205,13 @@ static int change_frame_impl(fargo_ctx *c, Buffers<T> &b, double omega_new)
         m.php0 += dom * sh.t;
         m.om_rel -= dom;
     }
+    // and so does the mesh's angle to the planetary integrator's axes
+    m.fr0 -= dom * sh.t;
     m.omega = omega_new;
     b.tab.omega = (T)omega_new;
-    if ((rc = vref_refresh<T>(c, b, c->stream))) return rc;
+    if (rebase) rc = vref_refresh<T>(c, b, c->stream);
+    else rc = vref_launch<T>(c, b, VREF_TABLES, nullptr, c->stream);
+    if (rc) return rc;
     if (c->gexec) {   // the captured step holds the old frame
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -1215,14 +1224,31 @@ extern "C" int fargo_change_frame(fargo_ctx *c, double omega_new)
 {
     if (!c || !isfinite(omega_new) || c->geom == FARGO_CART) return FARGO_ERR_BADARG;
     if (c->batch_refs > 0) return FARGO_ERR_BADARG;
-    return c->prec == FARGO_F64 ? change_frame_impl<double>(c, c->b64, omega_new)
-                                : change_frame_impl<float>(c, c->b32, omega_new);
+    return c->prec == FARGO_F64 ? change_frame_impl<double>(c, c->b64, omega_new, true)
+                                : change_frame_impl<float>(c, c->b32, omega_new, true);
+}
+
+extern "C" int fargo_track_frame(fargo_ctx *c, const double *y, int index, double *omega_out)
+{
+    if (!c || !y || index < 0 || index >= kNbMax || c->geom == FARGO_CART || c->batch_refs > 0 || !aligned8(y))
+        return FARGO_ERR_BADARG;
+    double s[6];
+    CK(cudaMemcpyAsync(s, y + 6 * (size_t)index, sizeof(s), cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    // the body's angular velocity about the polar axis (Sec. 3.2: the x axis tracks it)
+    const double r2 = s[0] * s[0] + s[1] * s[1];
+    const double rate = (s[0] * s[4] - s[1] * s[3]) / r2;
+    if (!(r2 > 0.0) || !isfinite(rate)) return FARGO_ERR_BADARG;
+    const int rc = c->prec == FARGO_F64 ? change_frame_impl<double>(c, c->b64, rate, false)
+                                        : change_frame_impl<float>(c, c->b32, rate, false);
+    if (!rc && omega_out) *omega_out = rate;
+    return rc;
 }
 
 extern "C" int fargo_set_planet_source(fargo_ctx *c, const double *pos, int n, int stride, const double *mass)
 {
     if (!c || !c->m.has_planet || c->geom == FARGO_CART) return FARGO_ERR_BADARG;
-    if (c->m.omega != 0.0 || c->batch_refs > 0 || !aligned8(pos) || !aligned8(mass)) return FARGO_ERR_BADARG;
+    if (c->batch_refs > 0 || !aligned8(pos) || !aligned8(mass)) return FARGO_ERR_BADARG;
     if (pos && (n < 1 || stride < 3 || (n > 1 && !mass))) return FARGO_ERR_BADARG;
     if (pos && n > kPotPlanets) return FARGO_ERR_SIZE;
     c->m.pl_pos = pos;

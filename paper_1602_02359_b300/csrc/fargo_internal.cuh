@@ -19,6 +19,8 @@ struct MeshD {
     long long ntot;              // elements per field (below 2^31, checked at creation)
     double dx, xmin, gamma, g1, cq, cfl, omega, pq, pa, pa3, peps, peps2, av_c2, om_rel;
     double php0;                 // planet azimuth at t = 0 in the current frame (moved by frame changes)
+    double fr0;                  // the mesh's angle to the planetary integrator's non-rotating axes is
+                                 // fr0 + omega t (the frame rate piecewise constant; moved by frame changes)
     int shearing;                // Cartesian shearing sheet
     const double *pl_pos;        // planets' positions read on the device each step (x, y, z at pl_pos +
                                  // p * pl_stride), or null for the fixed circular orbit

@@ -320,7 +320,8 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
                 const double px = pos[0], py = pos[1];
                 zp = pos[2];
                 ap = sqrt(px * px + py * py);
-                php = ap > 0.0 ? atan2(py, px) : 0.0;
+                // the integrator's axes turned to the mesh's by the frame angle
+                php = (ap > 0.0 ? atan2(py, px) : 0.0) - (m.fr0 + m.omega * sc->t);
                 const double r2 = ap * ap + zp * zp;
                 irp3 = 1.0 / (r2 * sqrt(r2));
                 if (m.pl_mass) qp = m.pl_mass[p];
@@ -666,10 +667,11 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
 //                (v - m then holds v exactly); otherwise 0
 //   VREF_APPLY:  v' <- v - vref[r]; lane 0 also writes the frame shifts dAy,
 //                dAz of the X momenta from A = R vref + w (FP64, rounded once)
+//   VREF_TABLES: the frame shifts alone (after a change of the frame rate)
 // CHOOSE reads v_x values only, so the whole field may be in v_x form while
 // it runs; APPLY runs after it (a separate launch).
 // ---------------------------------------------------------------------------
-enum { VREF_ABS = 0, VREF_CHOOSE = 1, VREF_APPLY = 2 };
+enum { VREF_ABS = 0, VREF_CHOOSE = 1, VREF_APPLY = 2, VREF_TABLES = 3 };
 
 template <typename T>
 __device__ void vref_ring(const MeshD &m, const Tab<T> &tb, T *vx, T *dst, int ring, int mode)
@@ -682,9 +684,10 @@ __device__ void vref_ring(const MeshD &m, const Tab<T> &tb, T *vx, T *dst, int r
         for (int i = lane; i < m.nx; i += 32) dst[base + i] = vx[base + i] + r;
         return;
     }
-    if (mode == VREF_APPLY) {
+    if (mode == VREF_APPLY || mode == VREF_TABLES) {
         const T r = tb.vref[ring];
-        for (int i = lane; i < m.nx; i += 32) vx[base + i] = vx[base + i] - r;
+        if (mode == VREF_APPLY)
+            for (int i = lane; i < m.nx; i += 32) vx[base + i] = vx[base + i] - r;
         if (lane == 0) {
             auto A = [&](int q) {
                 const double R = tb.Rd[q];

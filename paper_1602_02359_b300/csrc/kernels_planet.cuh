@@ -26,10 +26,16 @@ namespace fk {
 
 // The planet's position: by value, or read from device memory (x, y, z at
 // dev) when dev is set, so that a planet integrated on the device needs no
-// round trip through the host.
+// round trip through the host.  With sc set, the position is in the
+// planetary integrator's non-rotating axes, which the mesh's axes make the
+// angle fr0 + om t with (t the device time); the force comes out in the
+// integrator's axes.  Without, position and force are in the mesh's axes.
 struct PfPlanet {
     double x, y, z;
     const double *dev;
+    double fr0 = 0.0, om = 0.0;
+    const Scal *sc = nullptr;
+    __device__ __forceinline__ double frame_angle() const { return sc ? fr0 + om * sc->t : 0.0; }
     __device__ __forceinline__ void get(double &px, double &py, double &pz) const
     {
         if (dev) {
@@ -70,7 +76,10 @@ __global__ void __launch_bounds__(256) k_pforce_tables(T *tab, int nx, int sj, d
     pl.get(px, py, pz);
     const double Rp = sqrt(px * px + py * py);
     if (t < nx) {
-        const double php = Rp > 0.0 ? atan2(py, px) : 0.0;
+        // the planet's azimuth on the mesh; the force is turned back by the
+        // azimuth in the planet's own axes (k_planet_force), so it comes out
+        // in those axes
+        const double php = (Rp > 0.0 ? atan2(py, px) : 0.0) - pl.frame_angle();
         const double d = (xmin + (t + 0.5) * dx) - php;
         const double h = sin(0.5 * d);
         tab[t] = (T)(h * h);

@@ -219,9 +219,6 @@ def test_clearing_the_planet_source_restores_the_circular_orbit():
         assert np.array_equal(ga[k], gb[k]), k
     with pytest.raises(fb.FargoError):
         make_ctx(W.random_box(W.CART, 16, 8, 1, seed=1, planet=False)).set_planet_source(pos.data_ptr())
-    wr = W.random_box(W.CYL, 32, 16, 1, seed=2, omega_f=0.5)
-    with pytest.raises(fb.FargoError):
-        make_ctx(wr).set_planet_source(pos.data_ptr())
     with pytest.raises(fb.FargoError):   # several planets need their masses
         a.set_planet_source(pos.data_ptr(), 2, 3)
     big = dev(np.zeros((9, 3)))
