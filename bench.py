@@ -722,6 +722,15 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
     t0 = time.perf_counter()
     mem, b, cells = make_batch(fb, ps, stream.cuda_stream)
     setup_s = time.perf_counter() - t0
+    # launch shapes picked by the batch autotuner (per-cell grouping, sweep
+    # segments: timed on snapshots of the state, which it leaves unchanged);
+    # the timed steps run with its choice
+    t0 = time.perf_counter()
+    tcfg, ms_def, ms_tuned = b.autotune(reps=3)
+    tune = {**tcfg, "ms_default": round(ms_def, 4), "ms_tuned": round(ms_tuned, 4),
+            "gain": round(ms_def / ms_tuned - 1.0, 4) if ms_tuned > 0 else None,
+            "s": round(time.perf_counter() - t0, 1),
+            "how": "fargo_batch_autotune: each candidate shape timed over 3 steps of a snapshot (CUDA events)"}
     nl = b.launches_per_step()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -775,7 +784,7 @@ def bench_batch(args, torch, fb, wname, dev, barrier, e2e_on=True):
         m.close()
     return {"workload": batch_label(len(ps)), "cells": cells, "members": len(ps), "ms": ms, "clocks": clocks,
             "fp32_error": fp32_err,
-            "roofline": roof, "e2e": e2e, "launches": nl, "setup_s": round(setup_s, 1),
+            "roofline": roof, "e2e": e2e, "launches": nl, "setup_s": round(setup_s, 1), "autotune": tune,
             "steps_advanced_min": int(min(nsteps)), "running": running,
             "state_gb": cells * 2 * 22 * 4 / 1e9}
 
@@ -960,6 +969,7 @@ def main():
             cfg.update({"members": r["members"], "engine": "batched, one launch per phase over all members, "
                                                             "per-member Courant step",
                         "steps_advanced_min": r["steps_advanced_min"], "setup_s": r["setup_s"],
+                        "autotune": r["autotune"],
                         "run_length": "500 orbits per disk in the sweep; the bench times per-step throughput"})
         else:
             cfg["steps_advanced"] = r["steps_advanced"]
