@@ -33,11 +33,12 @@ class OrParams(C.Structure):
                 ("star_mass", C.c_double), ("planet_q", C.c_double), ("planet_a", C.c_double),
                 ("planet_eps", C.c_double), ("indirect", C.c_int), ("planet_phase0", C.c_double),
                 ("shearing", C.c_int), ("oort_a", C.c_double), ("planet_live", C.c_int),
-                ("planet_pos", C.c_double * 24), ("planet_mass", C.c_double * 8)]
+                ("planet_pos", C.c_double * 24), ("planet_mass", C.c_double * 8),
+                ("mhd", C.c_int), ("mhd_passive", C.c_int), ("eta", C.c_double)]
 
 
 class OrState(C.Structure):
-    _fields_ = [("rho", P), ("e", P), ("vx", P), ("vy", P), ("vz", P)]
+    _fields_ = [("rho", P), ("e", P), ("vx", P), ("vy", P), ("vz", P), ("bx", P), ("by", P), ("bz", P)]
 
 
 def build(force=False):
@@ -91,6 +92,12 @@ def lib():
         L.or_vanleer_slope.restype = C.c_double
         L.or_ppa_faces.argtypes = [C.c_int, P, C.c_double, P]
         L.or_shift_ring.argtypes = [C.c_int, P, C.c_longlong]
+        L.or_mhd_pressure.argtypes = [pp, ps, C.c_double]
+        L.or_mhd_tension.argtypes = [pp, ps, C.c_double]
+        L.or_mhd_emf.argtypes = [pp, ps, C.c_double, P, P, P]
+        L.or_mhd_ct.argtypes = [pp, ps, P, P, P, C.c_double]
+        L.or_mhd_divb.argtypes = [pp, ps, C.c_int, C.c_int, C.c_int]
+        L.or_mhd_divb.restype = C.c_double
         L.or_nearest_int.argtypes = [C.c_double]
         L.or_nearest_int.restype = C.c_longlong
         _lib = L
@@ -122,14 +129,19 @@ class Oracle:
                           w.star_mass, w.planet_q, w.planet_a, w.planet_eps, int(w.indirect))
         self.p.shearing = int(bool(getattr(w, "shearing", False)))
         self.p.oort_a = float(getattr(w, "oort_a", 0.0))
+        self.p.mhd = int(bool(getattr(w, "mhd", False)))
+        self.p.mhd_passive = int(bool(getattr(w, "mhd_passive", False)))
+        self.p.eta = float(getattr(w, "eta", 0.0))
         self.shape = w.shape
         self.nrings = w.nz_t * w.ny_t
 
     def _state(self, st):
-        for k in ("rho", "e", "vx", "vy", "vz"):
+        names = ("rho", "e", "vx", "vy", "vz") + (("bx", "by", "bz") if self.p.mhd else ())
+        for k in names:
             a = st[k]
             assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == self.shape, k
-        return OrState(_ptr(st["rho"]), _ptr(st["e"]), _ptr(st["vx"]), _ptr(st["vy"]), _ptr(st["vz"]))
+        b = [_ptr(st[k]) if self.p.mhd else None for k in ("bx", "by", "bz")]
+        return OrState(_ptr(st["rho"]), _ptr(st["e"]), _ptr(st["vx"]), _ptr(st["vy"]), _ptr(st["vz"]), *b)
 
     def step(self, st, t, t_end=1e30, dt_fixed=0.0):
         """One full update in place; returns dt.  Raises on a nonzero status."""
@@ -198,6 +210,39 @@ class Oracle:
 
     def viscosity(self, st, dt):
         lib().or_viscosity(C.byref(self.p), C.byref(self._state(st)), dt)
+
+    def mhd_pressure(self, st, dt):
+        """Cell 7a's magnetic part: the gradient of the transverse magnetic
+        pressure on every velocity (Sec. 3.5, after Eq. 46)."""
+        lib().or_mhd_pressure(C.byref(self.p), C.byref(self._state(st)), dt)
+
+    def mhd_emf(self, st, dt):
+        """Cells 8a-8c: the EMF (Eq. 45, minus eta curl B) on the edges;
+        returns (e_x, e_y, e_z) as full arrays, zero outside the stencil's
+        reach."""
+        E = [np.zeros(self.shape) for _ in range(3)]
+        lib().or_mhd_emf(C.byref(self.p), C.byref(self._state(st)), dt, *[_ptr(a) for a in E])
+        return E
+
+    def mhd_tension(self, st, dt):
+        """Cell 8d: the magnetic tension on the velocities (Eq. 47)."""
+        lib().or_mhd_tension(C.byref(self.p), C.byref(self._state(st)), dt)
+
+    def mhd_ct(self, st, E, dt):
+        """Cell 10: constrained transport of B by the EMF (Eq. 39)."""
+        E = [np.ascontiguousarray(a, dtype=np.float64) for a in E]
+        lib().or_mhd_ct(C.byref(self.p), C.byref(self._state(st)), *[_ptr(a) for a in E], dt)
+
+    def mhd_divb(self, st):
+        """The discrete divergence of B, sum over the faces of B times area
+        (outward), of every active cell: shape (nz, ny, nx)."""
+        w, s = self.w, self._state(st)
+        out = np.zeros((w.nz, w.ny, w.nx))
+        for k in range(w.nz):
+            for j in range(w.ny):
+                for i in range(w.nx):
+                    out[k, j, i] = lib().or_mhd_divb(C.byref(self.p), C.byref(s), i, w.gy + j, w.gz + k)
+        return out
 
     def momenta(self, st):
         pis = [np.zeros(self.shape) for _ in range(6)]

@@ -1,11 +1,14 @@
 /*
- * Plain FP64 CPU oracle of one FARGO3D hydrodynamic time step.
+ * Plain FP64 CPU oracle of one FARGO3D hydrodynamic time step, with the
+ * magnetohydrodynamics of Sec. 3.5 (MOCCT) on Cartesian meshes.
  *
  * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
  * benchmark's CPU-baseline leg, never by the product path.  Written from the
  * paper (Benitez-Llambay & Masset 2016): every loop is a plain triple loop
  * over the mesh in the order of the flow chart (Fig. 2), with no blocking or
  * fusion.  Where the paper is silent the reading taken is stated at the spot.
+ * Pins: tests/test_oracle_pins.py, tests/test_bruteforce_pins.py (the
+ * hydrodynamic step), tests/test_mhd_oracle.py (the MHD functions).
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused: the
  * Courant step, the mean azimuthal velocity and the integer shift must be
@@ -105,6 +108,9 @@ static void mesh_free(mesh *m)
 #define IM(m, i) (((i) - 1 + (m)->nx) % (m)->nx)
 
 static double *zalloc(size_t n) { return calloc(n, sizeof(double)); }
+/* (MHD helpers, defined with the MHD sub-steps below) */
+static size_t mh_nb(const mesh *m, int i, int j, int k, int d, int off);
+static double *mh_b(const or_state *s, int d);
 static double *dup(const double *a, size_t n)
 {
     double *b = malloc(sizeof(double) * n);
@@ -316,29 +322,35 @@ void or_bc_fill(const or_params *p, or_state *s)
 {
     mesh m;
     mesh_init(&m, p);
-    double *f[5] = { s->rho, p->iso ? NULL : s->e, s->vx, s->vy, s->vz };
+    /* the magnetic field's components are filled as the velocity's (MHD),  */
+    /* but each of them is filled along every present axis: B_z, B_y stay   */
+    /* transverse fields of a mesh without Z or Y, where v_z, v_y are unused */
+    double *f[8] = { s->rho, p->iso ? NULL : s->e, s->vx, s->vy, s->vz,
+                     p->mhd ? s->bx : NULL, p->mhd ? s->by : NULL, p->mhd ? s->bz : NULL };
     if (m.hasY) {
         int bcs[2] = { p->bc_ylo, p->bc_yhi };
         for (int side = 0; side < 2; side++)
-            for (int q = 0; q < 5; q++) {
+            for (int q = 0; q < 8; q++) {
                 if (!f[q]) continue;
+                int zn = q == 4 || q == 7, yn = q == 3 || q == 6;
                 if (q == 4 && !m.hasZ) continue;
-                int kmax = (q == 4) ? m.nzt + 1 : m.nzt;
+                int kmax = zn ? m.nzt + 1 : m.nzt;
                 for (int k = 0; k < kmax; k++)
                     for (int i = 0; i < m.nx; i++)
-                        fill_y(&m, f[q], q == 3, side, bcs[side], k, i);
+                        fill_y(&m, f[q], yn, side, bcs[side], k, i);
             }
     }
     if (m.hasZ) {
         int bcs[2] = { p->bc_zlo, p->bc_zhi };
         for (int side = 0; side < 2; side++)
-            for (int q = 0; q < 5; q++) {
+            for (int q = 0; q < 8; q++) {
                 if (!f[q]) continue;
+                int zn = q == 4 || q == 7, yn = q == 3 || q == 6;
                 if (q == 3 && !m.hasY) continue;
-                int jmax = (q == 3) ? m.nyt + 1 : m.nyt;
+                int jmax = yn ? m.nyt + 1 : m.nyt;
                 for (int j = 0; j < jmax; j++)
                     for (int i = 0; i < m.nx; i++)
-                        fill_z(&m, f[q], q == 4, side, bcs[side], j, i);
+                        fill_z(&m, f[q], zn, side, bcs[side], j, i);
             }
     }
     mesh_free(&m);
@@ -379,6 +391,15 @@ static void periodic_state(const mesh *m, or_state *s, int velocities, int energ
         if (m->hasZ) periodic_images(m, s->vz, 0, 1);
     }
     if (energy && !m->p->iso) periodic_images(m, s->e, 0, 0);
+}
+
+/* The magnetic field's periodic images (MHD). */
+static void periodic_field(const mesh *m, or_state *s)
+{
+    if (!m->pery && !m->perz) return;
+    periodic_images(m, s->bx, 0, 0);
+    periodic_images(m, s->by, m->hasY, 0);
+    periodic_images(m, s->bz, 0, m->hasZ);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -444,6 +465,17 @@ int or_cfl(const or_params *p, const or_state *s, const double *v0, double t, do
                 }
                 if (!isfinite(rho) || rho <= 0.0) bad = 1;
                 double r1 = cs / dmin;
+                if (p->mhd) {
+                    /* fast magnetosonic speed: c_s^2 + B^2/rho, B from zone-centred
+                       two-point averages of the face fields (reading M5) */
+                    double b2 = 0.0;
+                    for (int a = 0; a < 3; a++) {
+                        const double *B = mh_b(s, a);
+                        double bc = 0.5 * (B[c] + B[mh_nb(&m, i, j, k, a, 1)]);
+                        b2 += bc * bc;
+                    }
+                    r1 = sqrt(cs * cs + b2 / rho) / dmin;
+                }
                 double r2 = 0.0, r3 = 0.0;
                 if (m.hasX) {
                     double a = fabs(s->vx[c] - v0r), b = fabs(s->vx[IDX(&m, IP(&m, i), j, k)] - v0r);
@@ -481,6 +513,10 @@ int or_cfl(const or_params *p, const or_state *s, const double *v0, double t, do
                 if (p->cq <= 0.0) r3 = 0.0;
                 double r4 = nu > 0.0 ? 4.0 * nu / (dmin * dmin) : 0.0;
                 double sum = r1 * r1 + r2 * r2 + r3 * r3 + r4 * r4;
+                if (p->mhd && p->eta > 0.0) {   /* Ohmic diffusion, as the viscosity */
+                    double r5 = 4.0 * p->eta / (dmin * dmin);
+                    sum += r5 * r5;
+                }
                 double local = 1.0 / sqrt(sum);
                 if (local < best) best = local;
             }
@@ -1406,10 +1442,21 @@ int or_step(const or_params *p, or_state *s, double t, double t_end, double dt_f
         or_potential(p, t, phi);                          /* cell 5 */
     }
     or_substep1(p, s, phi, dt);                           /* cell 7a */
+    if (p->mhd) or_mhd_pressure(p, s, dt);                /* cell 7a, magnetic pressure */
     or_artificial_viscosity(p, s, dt);                    /* cell 7b */
     or_compression_heating(p, s, dt);                     /* cell 7c */
     or_viscosity(p, s, dt);                               /* cell 7d */
+    double *em[3] = { NULL, NULL, NULL };
+    if (p->mhd) {
+        for (int o = 0; o < 3; o++) em[o] = zalloc(m.n);
+        or_mhd_emf(p, s, dt, em[0], em[1], em[2]);       /* cells 8a-8c */
+        or_mhd_tension(p, s, dt);                         /* cell 8d */
+    }
     or_bc_fill(p, s);                                     /* cell 9 */
+    if (p->mhd) {
+        or_mhd_ct(p, s, em[0], em[1], em[2], dt);         /* cell 10 */
+        for (int o = 0; o < 3; o++) free(em[o]);
+    }
     double *pi[6];
     for (int q = 0; q < 6; q++) pi[q] = zalloc(m.n);
     or_momenta(p, s, pi);                                 /* cell 12a */
@@ -1553,5 +1600,324 @@ void or_change_frame(or_params *p, or_state *s, double omega_new, double t)
         }
     p->planet_phase0 += dom * t;
     p->omega_f = omega_new;
+    mesh_free(&m);
+}
+
+/* ======================================================================== */
+/* Magnetohydrodynamics (Sec. 3.5, "Magnetohydrodynamics": the method of    */
+/* characteristics and constrained transport, MOCCT), Cartesian meshes,     */
+/* mu_0 = 1.  B is face centred like v (Sec. 2.3); the EMF of orientation o */
+/* lives on the edges along o (Fig. "cell").  Directions are numbered       */
+/* X = 0, Y = 1, Z = 2; an absent direction (one cell) has no neighbours:   */
+/* every difference along it vanishes and every average over it is the     */
+/* value itself.                                                             */
+/* ======================================================================== */
+
+/* Index of the cell `off` cells away from (i, j, k) along direction d (X    */
+/* periodic; an absent direction maps onto the cell itself).                */
+static size_t mh_nb(const mesh *m, int i, int j, int k, int d, int off)
+{
+    if (d == 0) return IDX(m, ((i + off) % m->nx + m->nx) % m->nx, j, k);
+    if (d == 1) return IDX(m, i, m->hasY ? j + off : j, k);
+    return IDX(m, i, j, m->hasZ ? k + off : k);
+}
+static int mh_has(const mesh *m, int d) { return d == 0 ? m->hasX : (d == 1 ? m->hasY : m->hasZ); }
+/* Index of (i, j, k) along d, and the cell width there (Cartesian). */
+static int mh_pos(int i, int j, int k, int d) { return d == 0 ? i : (d == 1 ? j : k); }
+static double mh_width(const mesh *m, int d, int n) { return d == 0 ? m->dx : (d == 1 ? m->dy[n] : m->dz[n]); }
+/* Centre-to-centre distance between cells n - 1 and n along d. */
+static double mh_dc(const mesh *m, int d, int n)
+{
+    return d == 0 ? m->dx : 0.5 * (mh_width(m, d, n - 1) + mh_width(m, d, n));
+}
+static double *mh_v(const or_state *s, int d) { return d == 0 ? s->vx : (d == 1 ? s->vy : s->vz); }
+static double *mh_b(const or_state *s, int d) { return d == 0 ? s->bx : (d == 1 ? s->by : s->bz); }
+
+/* Value at the face between cells n - 1 and n along e (cell (i, j, k) is n)  */
+/* of a quantity q that is cell centred along e, carried by the speed w     */
+/* over dt: the donor cell's value plus its van Leer slope times half the   */
+/* distance from the face to the point that reaches it at dt/2 - the        */
+/* interface value of Eq. 15 with w for the flow speed (the upwind estimate */
+/* "u" of Sec. 3.5) or for a characteristic speed C+- (the foot values of   */
+/* Eqs. 41-44).                                                              */
+static double mh_recon(const mesh *m, const double *q, int i, int j, int k, int e, double w, double dt)
+{
+    size_t c = IDX(m, i, j, k);
+    if (!mh_has(m, e)) return q[c];
+    int n = mh_pos(i, j, k, e);
+    double qm2 = q[mh_nb(m, i, j, k, e, -2)], qm1 = q[mh_nb(m, i, j, k, e, -1)], q0 = q[c],
+           qp1 = q[mh_nb(m, i, j, k, e, 1)];
+    int nn = e == 0 ? 2 : n;   /* X is uniform: any index serves for its widths */
+    if (w >= 0.0) {
+        double sl = or_vanleer_slope(qm2, qm1, q0, mh_dc(m, e, nn - 1), mh_dc(m, e, nn));
+        return qm1 + 0.5 * sl * (mh_width(m, e, nn - 1) - w * dt);
+    }
+    double sl = or_vanleer_slope(qm1, q0, qp1, mh_dc(m, e, nn), mh_dc(m, e, nn + 1));
+    return q0 - 0.5 * sl * (mh_width(m, e, nn) + w * dt);
+}
+
+/* Density at the edge at the lower a- and lower b-face of cell (i, j, k):   */
+/* the mean of the four cells around it (Sec. 3.5).                         */
+static double mh_rho_edge(const mesh *m, const double *rho, int i, int j, int k, int a, int b)
+{
+    size_t c00 = IDX(m, i, j, k), c10 = mh_nb(m, i, j, k, a, -1), c01 = mh_nb(m, i, j, k, b, -1);
+    int ia = a == 0 ? ((i - 1) % m->nx + m->nx) % m->nx : i, ja = a == 1 && m->hasY ? j - 1 : j,
+        ka = a == 2 && m->hasZ ? k - 1 : k;
+    size_t c11 = mh_nb(m, ia, ja, ka, b, -1);
+    return 0.25 * (rho[c00] + rho[c10] + rho[c01] + rho[c11]);
+}
+
+/* Star values at that edge of the pair (v_p, B_p), p one of the edge's two  */
+/* transverse directions, from the 1.5D problem along the other one, q      */
+/* (Eqs. 41-44): the Alfven characteristics C+- = U -+ W / sqrt(rho) carry   */
+/* psi+- = v_p +- B_p / sqrt(rho), taken at their feet from the van Leer     */
+/* reconstructions of v_p and B_p along q.  U, W: the velocity and field     */
+/* along q at the edge (U = 0 for the magnetic tension, Eq. 47).            */
+static void mh_star(const mesh *m, const or_state *s, int i, int j, int k, int p, int q, double U, double W,
+                    double rho, double dt, double *vs, double *bs)
+{
+    double sq = sqrt(rho);
+    double cp = U - W / sq, cm = U + W / sq;
+    const double *v = mh_v(s, p), *bf = mh_b(s, p);
+    double vp = mh_recon(m, v, i, j, k, q, cp, dt), bp = mh_recon(m, bf, i, j, k, q, cp, dt);
+    double vm = mh_recon(m, v, i, j, k, q, cm, dt), bm = mh_recon(m, bf, i, j, k, q, cm, dt);
+    *vs = 0.5 * (vp + vm + (bp - bm) / sq);
+    *bs = 0.5 * (bp + bm + sq * (vp - vm));
+}
+
+/* Cells 8a-8c.  EMF of orientation o, a = o + 1, b = o + 2 (mod 3), at the  */
+/* edge at the lower a- and b-face of cell (i, j, k) (Eq. 45):              */
+/*   e_o = (v_a* B_b^u + B_b* v_a^u - v_b* B_a^u - B_a* v_b^u) / 2,          */
+/* with v_a^u, B_a^u the upwind estimates along b at the mean flow speed    */
+/* along b of the edge's two b-faces, and v_a*, B_a* from the problem along */
+/* b at C+- = v_b^u -+ B_b^u / sqrt(rho) (and a, b swapped).  Then the      */
+/* resistive part: e_o -= eta (curl B)_o, by finite differences at the edge.*/
+static double mh_emf_edge(const mesh *m, const or_params *p, const or_state *s, int o, int i, int j, int k,
+                          double dt)
+{
+    int a = (o + 1) % 3, b = (o + 2) % 3;
+    double *va = mh_v(s, a), *vb = mh_v(s, b), *ba = mh_b(s, a), *bb = mh_b(s, b);
+    size_t c00 = IDX(m, i, j, k), ca = mh_nb(m, i, j, k, a, -1), cb = mh_nb(m, i, j, k, b, -1);
+    double rho = mh_rho_edge(m, s->rho, i, j, k, a, b);
+    double ub = 0.5 * (vb[c00] + vb[ca]);   /* mean speed along b at the edge (the b-faces at a and a-1) */
+    double ua = 0.5 * (va[c00] + va[cb]);   /* mean speed along a (the a-faces at b and b-1) */
+    double vau = mh_recon(m, va, i, j, k, b, ub, dt), bau = mh_recon(m, ba, i, j, k, b, ub, dt);
+    double vbu = mh_recon(m, vb, i, j, k, a, ua, dt), bbu = mh_recon(m, bb, i, j, k, a, ua, dt);
+    double vas, bas, vbs, bbs;
+    mh_star(m, s, i, j, k, a, b, vbu, bbu, rho, dt, &vas, &bas);   /* (v_a*, B_a*): along b */
+    mh_star(m, s, i, j, k, b, a, vau, bau, rho, dt, &vbs, &bbs);   /* (v_b*, B_b*): along a */
+    double e = 0.5 * (vas * bbu + bbs * vau - vbs * bau - bas * vbu);
+    if (p->eta > 0.0) {
+        double cur = 0.0;   /* (curl B)_o = d_a B_b - d_b B_a */
+        if (mh_has(m, a)) cur += (bb[c00] - bb[ca]) / mh_dc(m, a, a == 0 ? 1 : mh_pos(i, j, k, a));
+        if (mh_has(m, b)) cur -= (ba[c00] - ba[cb]) / mh_dc(m, b, b == 0 ? 1 : mh_pos(i, j, k, b));
+        e -= p->eta * cur;
+    }
+    return e;
+}
+
+/* Range of cell indices along d whose neighbours -2..+1 exist (the EMF     */
+/* stencil): the whole of an absent direction (its single index 0) and the  */
+/* whole periodic X.                                                         */
+static void mh_edge_range(const mesh *m, int d, int *lo, int *hi)
+{
+    int n = d == 0 ? m->nx : (d == 1 ? m->nyt : m->nzt);
+    if (d == 0 || !mh_has(m, d)) { *lo = 0; *hi = n; return; }
+    *lo = 2; *hi = n - 1;
+}
+
+void or_mhd_emf(const or_params *p, const or_state *s, double dt, double *ex, double *ey, double *ez)
+{
+    mesh m;
+    mesh_init(&m, p);
+    double *E[3] = { ex, ey, ez };
+    int jl, jh, kl, kh, il, ih;
+    mh_edge_range(&m, 0, &il, &ih);
+    mh_edge_range(&m, 1, &jl, &jh);
+    mh_edge_range(&m, 2, &kl, &kh);
+    for (int o = 0; o < 3; o++) {
+        for (size_t q = 0; q < m.n; q++) E[o][q] = 0.0;
+        PAR2
+        for (int k = kl; k < kh; k++)
+            for (int j = jl; j < jh; j++)
+                for (int i = il; i < ih; i++)
+                    E[o][IDX(&m, i, j, k)] = mh_emf_edge(&m, p, s, o, i, j, k, dt);
+    }
+    mesh_free(&m);
+}
+
+/* Face ranges the update of component d covers: active cells along the    */
+/* other directions; along d its interior faces (jf.., kf..), or the single */
+/* index of an absent direction.                                             */
+static void mh_face_range(const mesh *m, int d, int e, int *lo, int *hi)
+{
+    if (e == 0) { *lo = 0; *hi = m->nx; return; }
+    if (!mh_has(m, e)) { *lo = 0; *hi = 1; return; }
+    if (e == 1) { *lo = d == 1 ? m->jf : m->j0; *hi = m->j1; return; }
+    *lo = d == 2 ? m->kf : m->k0; *hi = m->k1;
+}
+
+/* Cell 10: constrained transport (Eq. 39 with the circulation of e = v x B */
+/* taken counterclockwise about each face's normal, Stokes' theorem: the    */
+/* printed signs are those of e = B x v; reading M3).  On the Cartesian     */
+/* mesh: dB_a/dt = d_b e_o - d_o e_b for the cyclic (a, b, o).              */
+void or_mhd_ct(const or_params *p, or_state *s, const double *ex, const double *ey, const double *ez, double dt)
+{
+    mesh m;
+    mesh_init(&m, p);
+    const double *E[3] = { ex, ey, ez };
+    for (int a = 0; a < 3; a++) {
+        int b = (a + 1) % 3, o = (a + 2) % 3;   /* dB_a/dt = d_b e_o - d_o e_b */
+        double *B = mh_b(s, a);
+        int il, ih, jl, jh, kl, kh;
+        mh_face_range(&m, a, 0, &il, &ih);
+        mh_face_range(&m, a, 1, &jl, &jh);
+        mh_face_range(&m, a, 2, &kl, &kh);
+        double *nb = dup(B, m.n);
+        PAR2
+        for (int k = kl; k < kh; k++)
+            for (int j = jl; j < jh; j++)
+                for (int i = il; i < ih; i++) {
+                    size_t c = IDX(&m, i, j, k);
+                    double d = 0.0;
+                    if (mh_has(&m, b))
+                        d += (E[o][mh_nb(&m, i, j, k, b, 1)] - E[o][c]) / mh_width(&m, b, mh_pos(i, j, k, b));
+                    if (mh_has(&m, o))
+                        d -= (E[b][mh_nb(&m, i, j, k, o, 1)] - E[b][c]) / mh_width(&m, o, mh_pos(i, j, k, o));
+                    nb[c] = B[c] + dt * d;
+                }
+        memcpy(B, nb, sizeof(double) * m.n);
+        free(nb);
+    }
+    periodic_field(&m, s);
+    mesh_free(&m);
+}
+
+double or_mhd_divb(const or_params *p, const or_state *s, int i, int j, int k)
+{
+    mesh m;
+    mesh_init(&m, p);
+    double w[3] = { m.dx, m.dy[j], m.dz[k] }, d = 0.0;
+    for (int a = 0; a < 3; a++) {
+        if (!mh_has(&m, a)) continue;
+        const double *B = mh_b(s, a);
+        double area = 1.0;
+        for (int e = 0; e < 3; e++)
+            if (e != a) area *= w[e];
+        d += (B[mh_nb(&m, i, j, k, a, 1)] - B[IDX(&m, i, j, k)]) * area;
+    }
+    mesh_free(&m);
+    return d;
+}
+
+/* Cell 8d: the magnetic tension (Eq. 47 and its permutations), for every   */
+/* interior face of v_a:                                                     */
+/*   dv_a = dt 2/(rho + rho_{-a}) sum_b Bbar_b (B_a*(b+1/2) - B_a*(b-1/2)) / D_b */
+/* over the other present directions b; Bbar_b the mean of the four b-faces */
+/* around the a-face; B_a* at the edges from the problem along b with no    */
+/* flow speed (U = 0, W the mean of the edge's two b-faces: reading M4).   */
+/* Jacobi: every component from the velocities on entry.                    */
+static double mh_tension_star(const mesh *m, const or_state *s, int i, int j, int k, int a, int b, double dt)
+{
+    const double *bb = mh_b(s, b);
+    double rho = mh_rho_edge(m, s->rho, i, j, k, a, b);
+    double W = 0.5 * (bb[IDX(m, i, j, k)] + bb[mh_nb(m, i, j, k, a, -1)]);
+    double vs, bs;
+    mh_star(m, s, i, j, k, a, b, 0.0, W, rho, dt, &vs, &bs);
+    return bs;
+}
+
+void or_mhd_tension(const or_params *p, or_state *s, double dt)
+{
+    if (!p->mhd || p->mhd_passive) return;
+    mesh m;
+    mesh_init(&m, p);
+    double *nv[3] = { NULL, NULL, NULL };
+    for (int a = 0; a < 3; a++) {
+        if (!mh_has(&m, a)) continue;
+        double *v = mh_v(s, a);
+        nv[a] = dup(v, m.n);
+        int il, ih, jl, jh, kl, kh;
+        mh_face_range(&m, a, 0, &il, &ih);
+        mh_face_range(&m, a, 1, &jl, &jh);
+        mh_face_range(&m, a, 2, &kl, &kh);
+        PAR2
+        for (int k = kl; k < kh; k++)
+            for (int j = jl; j < jh; j++)
+                for (int i = il; i < ih; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = mh_nb(&m, i, j, k, a, -1);
+                    double f = 0.0;
+                    for (int b = 0; b < 3; b++) {
+                        if (b == a || !mh_has(&m, b)) continue;
+                        const double *bb = mh_b(s, b);
+                        int ia = a == 0 ? ((i - 1) % m.nx + m.nx) % m.nx : i, ja = a == 1 ? j - 1 : j,
+                            ka = a == 2 ? k - 1 : k;
+                        double bbar = 0.25 * (bb[c] + bb[mh_nb(&m, i, j, k, b, 1)] + bb[cm] +
+                                              bb[mh_nb(&m, ia, ja, ka, b, 1)]);
+                        int ib = b == 0 ? (i + 1) % m.nx : i, jb = b == 1 ? j + 1 : j, kb = b == 2 ? k + 1 : k;
+                        double up = mh_tension_star(&m, s, ib, jb, kb, a, b, dt);
+                        double lo = mh_tension_star(&m, s, i, j, k, a, b, dt);
+                        f += bbar * (up - lo) / mh_width(&m, b, mh_pos(i, j, k, b));
+                    }
+                    nv[a][c] = v[c] + dt * 2.0 / (s->rho[c] + s->rho[cm]) * f;
+                }
+    }
+    for (int a = 0; a < 3; a++)
+        if (nv[a]) {
+            memcpy(mh_v(s, a), nv[a], sizeof(double) * m.n);
+            free(nv[a]);
+        }
+    periodic_state(&m, s, 1, 0);
+    mesh_free(&m);
+}
+
+/* Cell 7a, the magnetic part: the gradient of the magnetic pressure of the */
+/* transverse field, -(1/rho) d_a (B_b^2 + B_c^2)/2, with zone-centred two-  */
+/* point averages of B_b, B_c and the two-point face density, as the        */
+/* thermal pressure gradient (Sec. 3.5; Eq. 20).                            */
+static double mh_pmag(const mesh *m, const or_state *s, int i, int j, int k, int a)
+{
+    double pb = 0.0;
+    for (int b = 0; b < 3; b++) {
+        if (b == a) continue;
+        const double *B = mh_b(s, b);
+        double bc = 0.5 * (B[IDX(m, i, j, k)] + B[mh_nb(m, i, j, k, b, 1)]);
+        pb += 0.5 * bc * bc;
+    }
+    return pb;
+}
+
+void or_mhd_pressure(const or_params *p, or_state *s, double dt)
+{
+    if (!p->mhd || p->mhd_passive) return;
+    mesh m;
+    mesh_init(&m, p);
+    double *nv[3] = { NULL, NULL, NULL };
+    for (int a = 0; a < 3; a++) {
+        if (!mh_has(&m, a)) continue;
+        double *v = mh_v(s, a);
+        nv[a] = dup(v, m.n);
+        int il, ih, jl, jh, kl, kh;
+        mh_face_range(&m, a, 0, &il, &ih);
+        mh_face_range(&m, a, 1, &jl, &jh);
+        mh_face_range(&m, a, 2, &kl, &kh);
+        PAR2
+        for (int k = kl; k < kh; k++)
+            for (int j = jl; j < jh; j++)
+                for (int i = il; i < ih; i++) {
+                    size_t c = IDX(&m, i, j, k), cm = mh_nb(&m, i, j, k, a, -1);
+                    int ia = a == 0 ? ((i - 1) % m.nx + m.nx) % m.nx : i, ja = a == 1 ? j - 1 : j,
+                        ka = a == 2 ? k - 1 : k;
+                    double g = (mh_pmag(&m, s, i, j, k, a) - mh_pmag(&m, s, ia, ja, ka, a)) /
+                               mh_dc(&m, a, a == 0 ? 1 : mh_pos(i, j, k, a));
+                    nv[a][c] = v[c] - dt * 2.0 * g / (s->rho[c] + s->rho[cm]);
+                }
+    }
+    for (int a = 0; a < 3; a++)
+        if (nv[a]) {
+            memcpy(mh_v(s, a), nv[a], sizeof(double) * m.n);
+            free(nv[a]);
+        }
+    periodic_state(&m, s, 1, 0);
     mesh_free(&m);
 }

@@ -41,9 +41,13 @@ typedef struct {
     int planet_live;            /* n > 0: n integrated planets at planet_pos, masses planet_mass */
     double planet_pos[8][3];    /* their positions (x, y, z) */
     double planet_mass[8];      /* their masses */
+    int mhd;                    /* 1: magnetic field B (Sec. 3.5), Cartesian meshes, STANDARD transport */
+    int mhd_passive;            /* 1: B evolves passively: no magnetic force on the gas */
+    double eta;                 /* Ohmic diffusivity (uniform) */
 } or_params;
 
-typedef struct { double *rho, *e, *vx, *vy, *vz; } or_state;
+/* bx, by, bz: face-centred like vx, vy, vz (NULL without MHD). */
+typedef struct { double *rho, *e, *vx, *vy, *vz, *bx, *by, *bz; } or_state;
 
 /* Full step: cells 2..12 of the flow chart (Fig. 2).  dt_fixed > 0 skips the
  * Courant reduction and uses the given step.  Returns 0 or a negative code. */
@@ -71,6 +75,18 @@ void or_orbital_shift(const or_params *p, or_state *s, double *pi[6], const doub
 void or_transport_y(const or_params *p, or_state *s, double *pi[6], double dt);
 void or_transport_z(const or_params *p, or_state *s, double *pi[6], double dt);
 void or_new_velocities(const or_params *p, or_state *s, double *pi[6]);
+
+/* MHD (Sec. 3.5), Cartesian meshes, mu_0 = 1.  Cell 7a's magnetic pressure
+ * gradient; cells 8a-8c: the edge EMFs, e_x at (i, j-1/2, k-1/2), e_y at
+ * (i-1/2, j, k-1/2), e_z at (i-1/2, j-1/2, k) stored at index (i, j, k)
+ * (full arrays); cell 8d: the magnetic tension; cell 10: the constrained
+ * transport of the face fields. */
+void or_mhd_pressure(const or_params *p, or_state *s, double dt);
+void or_mhd_emf(const or_params *p, const or_state *s, double dt, double *ex, double *ey, double *ez);
+void or_mhd_tension(const or_params *p, or_state *s, double dt);
+void or_mhd_ct(const or_params *p, or_state *s, const double *ex, const double *ey, const double *ez, double dt);
+/* Discrete divergence of B of active cell (i, j, k) times its volume. */
+double or_mhd_divb(const or_params *p, const or_state *s, int i, int j, int k);
 
 /* Geometry of Appendix A, per ring (j,k): face areas, inverse volume,
  * volume and azimuthal cell length. Arrays [nz_t][ny_t] (sy, sz also use the

@@ -1,0 +1,325 @@
+"""Pins of the oracle's magnetohydrodynamics (Sec. 3.5, MOCCT on Cartesian
+meshes) against what the mathematics fixes: the divergence constraint
+(Eq. 39 conserves it to round-off), closed forms of each sub-step (the EMF
+of a uniform state is v x B, the constrained transport of a linear EMF is
+its curl, the tension of a linear field is B . grad B / rho, Ohmic decay of
+a Fourier mode by the discrete Laplacian's factor), the magnetostatic
+balance, and the waves of the linearised equations (the Alfven speed, the
+fast speed sqrt(c_s^2 + v_A^2)), plus the resistive current sheet of the
+paper's test section (Eq. currdiff)."""
+import math
+
+import numpy as np
+
+import oracle
+import workloads as W
+
+
+def run_to(o, st, t, t_end, max_steps=2000):
+    """Steps to t_end; a run that needs more steps than max_steps (a time
+    step collapsing on a growing instability) fails the test."""
+    n = 0
+    while t < t_end - 1e-15:
+        t += o.step(st, t, t_end=t_end)
+        n += 1
+        assert n <= max_steps, (t, t_end)
+    return t
+
+
+def phase_amp(w, a, x):
+    """Phase and amplitude of the k = 2 pi mode of a row a(x)."""
+    s = 2.0 * np.mean(a * np.sin(2 * math.pi * x))
+    c = 2.0 * np.mean(a * np.cos(2 * math.pi * x))
+    return math.atan2(c, s), math.hypot(s, c)
+
+
+def test_divergence_stays_at_round_off():
+    """Eq. 39: every edge's EMF enters the six face fluxes of a cell twice
+    with opposite signs, so the net flux out of each cell stays at its
+    initial round-off, whatever the EMFs are (here: compressive random
+    flows, magnetic forces and resistivity over ten steps)."""
+    for dims, eta in (((8, 6, 4), 0.02), ((16, 12, 1), 0.0), ((12, 1, 10), 0.01)):
+        w = W.random_mhd_box(*dims, seed=3, eta=eta)
+        o = oracle.Oracle(w)
+        st = w.copy().state
+        b0 = {k: st[k].copy() for k in W.MHD_FIELDS}
+        dx, dy, dz = (w.xmax - w.xmin) / w.nx, w.yf[1] - w.yf[0], w.zf[1] - w.zf[0]
+        area = max(dy * dz, dx * dz, dx * dy)
+        scale = max(np.abs(st[k]).max() for k in W.MHD_FIELDS) * area
+        assert np.abs(o.mhd_divb(st)).max() <= 1e-14 * scale
+        t = 0.0
+        for _ in range(10):
+            t += o.step(st, t)
+        assert np.abs(o.mhd_divb(st)).max() <= 1e-13 * scale, dims
+        moved = max(np.abs(w.active(st[k] - b0[k])).max() for k in W.MHD_FIELDS)
+        assert moved > 1e-4, dims          # the field did evolve
+
+
+def test_uniform_state_is_invariant_bit_for_bit():
+    w = W.uniform_mhd_box(8, 6, 4, rho=1.3, e=2.0, v=(0.2, -0.1, 0.15), b=(0.6, 0.3, -0.2), eta=0.05)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    t = 0.0
+    for _ in range(5):
+        t += o.step(st, t)
+    for k, a in st.items():
+        assert np.array_equal(w.active(a), w.active(w.state[k])), k
+
+
+def test_emf_of_a_uniform_state_is_v_cross_b():
+    """Eq. 45 on a uniform state: every star and upwind value equals the
+    field itself, so each component is (v x B) with the cyclic order
+    X -> Y -> Z (a transposed operand or a sign flips a component)."""
+    v, b = (0.3, -0.7, 0.45), (1.1, 0.25, -0.6)
+    w = W.uniform_mhd_box(8, 6, 4, rho=0.8, v=v, b=b)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    E = o.mhd_emf(st, 0.01)
+    cross = np.cross(v, b)
+    for q in range(3):
+        a = w.active(E[q])
+        assert np.allclose(a, cross[q], rtol=0, atol=4e-16), (q, a.min(), a.max(), cross[q])
+
+
+def test_constrained_transport_of_a_linear_emf_is_its_curl():
+    """Eq. 39 with EMFs linear in the edge coordinates: the circulation over
+    each face divided by its area is the curl, exactly up to rounding.  With
+    e_x = s y + p z, e_y = q z, e_z = r y: curl e = (r - q, p, -s)."""
+    s, p, q, r, dt = 0.7, -1.3, 0.4, 2.1, 0.05
+    w = W.uniform_mhd_box(8, 10, 6, periodic=False)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    yf = w.yf[:w.ny_t + 1]
+    zf = w.zf[:w.nz_t + 1]
+    Y = np.zeros(w.shape)
+    Z = np.zeros(w.shape)
+    Y[:, :, :] = yf[None, :, None]
+    Z[:, :, :] = zf[:, None, None]
+    E = [s * Y + p * Z, q * Z, r * Y]
+    o.mhd_ct(st, E, dt)
+    want = (r - q, p, -s)
+    gy, gz = w.gy, w.gz
+    rng = {"bx": (slice(gz, gz + w.nz), slice(gy, gy + w.ny)),
+           "by": (slice(gz, gz + w.nz), slice(gy + 1, gy + w.ny)),
+           "bz": (slice(gz + 1, gz + w.nz), slice(gy, gy + w.ny))}
+    for n, k in enumerate(W.MHD_FIELDS):
+        d = st[k][rng[k]] / dt
+        assert np.allclose(d, want[n], rtol=0, atol=1e-12), (k, d.min(), d.max(), want[n])
+
+
+def test_tension_of_a_linear_field_is_b_dot_grad_b_over_rho():
+    """Eq. 47 with B_y uniform and B_z = c + d y (divergence free), gas at
+    rest: the star values of a linear profile are its face values (van
+    Leer's slope of a straight line is its slope, the two feet average out),
+    so v_z gains dt B_y d / rho and v_y nothing."""
+    by, c, d, rho, dt = 0.8, 0.3, 1.7, 1.25, 0.02
+    w = W.uniform_mhd_box(8, 12, 10, rho=rho, b=(0.0, by, 0.0), periodic=False)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    yc = W.centres(w.yf)[:w.ny_t]
+    st["bz"][:, :w.ny_t, :] = (c + d * yc)[None, :, None]
+    o.mhd_tension(st, dt)
+    gy, gz = w.gy, w.gz
+    vz = st["vz"][gz + 1:gz + w.nz, gy + 1:gy + w.ny - 1]
+    assert np.allclose(vz, dt * by * d / rho, rtol=1e-12, atol=0), (vz.min(), vz.max(), dt * by * d / rho)
+    assert np.abs(w.active(st["vy"])).max() <= 1e-15
+    assert np.abs(w.active(st["vx"])).max() == 0.0
+
+
+def test_ohmic_decay_of_a_mode_by_the_discrete_laplacian():
+    """Resistive part of cells 8c and 10 alone (the gas at rest, the field
+    passive): the EMF -eta (curl B)_x by finite differences and its curl
+    give B_y += eta dt (B_{k+1} - 2 B_k + B_{k-1}) / dz^2, whose Fourier
+    mode m is multiplied each step by 1 - 4 eta dt / dz^2 sin^2(pi m / nz)."""
+    nz, m, eta = 32, 3, 0.1
+    w = W.resistive_mode(nz=nz, mode=m, eta=eta)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    dz = 1.0 / nz
+    dt = 0.2 * dz * dz / eta
+    f = 1.0 - 4.0 * eta * dt / dz ** 2 * math.sin(math.pi * m / nz) ** 2
+    b0 = w.active(w.state["by"])
+    for n in range(1, 41):
+        o.step(st, 0.0, dt_fixed=dt)
+        assert np.allclose(w.active(st["by"]), f ** n * b0, rtol=0, atol=1e-14), n
+    assert np.abs(w.active(st["vz"])).max() == 0.0
+
+
+def test_current_sheet_follows_the_erf_to_second_order():
+    """Sec. 5.2's current sheet: B_y = B0 erf(z / sqrt(4 eta t)), passive,
+    gas at rest.  With the same physical start and end times the L1 error
+    against the erf falls by about 4 per doubling of the resolution."""
+    errs = []
+    for nz in (64, 128, 256):
+        w = W.current_sheet(nz=nz, t0=0.002)
+        o = oracle.Oracle(w)
+        st = w.copy().state
+        t = run_to(o, st, w.t0, 0.01)
+        zc = W.centres(w.zf)[w.gz:w.gz + nz]
+        errs.append(np.mean(np.abs(w.active(st["by"])[:, 0, 0] - W.current_sheet_profile(zc, t))))
+    assert errs[0] / errs[1] > 3.6 and errs[1] / errs[2] > 3.6, errs
+    assert errs[2] < 2e-5
+
+
+def test_current_sheet_at_the_papers_resolution():
+    """512 cells on [-1, 1], eta = 0.25, B0 = 1, from t0 = (2.5 dz)^2 to
+    30 t0 (the test of Sec. 5.2): the numerical profile stays on the erf."""
+    w = W.current_sheet()
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    t = run_to(o, st, w.t0, 30.0 * w.t0, max_steps=4000)
+    zc = W.centres(w.zf)[w.gz:w.gz + w.nz]
+    err = np.abs(w.active(st["by"])[:, 0, 0] - W.current_sheet_profile(zc, t))
+    assert err.max() < 2e-3 and err.mean() < 1e-4, (err.max(), err.mean())
+    assert np.abs(w.active(st["vz"])).max() == 0.0
+
+
+def test_alfven_wave_moves_at_the_alfven_speed():
+    """A right-moving linear Alfven wave along X (v_A = 1) after one period:
+    back in phase to within 0.011 rad at 32 cells and 0.003 at 64; its
+    left-moving part (psi_+ of Eq. 43) stays under 2 % of the amplitude.
+    Eq. 45 pairs the MOC value v_Y* with the upwind value v_Y^u, which at
+    zero transverse flow is the one-sided reconstruction: the wave grows by
+    about 4 % per period at 32 cells (1 at 64) at the Courant number 0.44,
+    and this pin brackets that."""
+    for nx, tol, grow in ((32, 0.011, 1.06), (64, 0.003, 1.03)):
+        w = W.alfven_wave(nx=nx)
+        o = oracle.Oracle(w)
+        st = w.copy().state
+        run_to(o, st, 0.0, 1.0)
+        xc = W._mhd_coords(w)[0]
+        vy = w.active(st["vy"])[0, 0]
+        by = w.active(st["by"])[0, 0]
+        ph, amp = phase_amp(w, vy, xc)
+        assert abs(ph) < tol, (nx, ph)
+        assert 1.0 - 1e-3 < amp / 1e-3 < grow, (nx, amp)
+        assert np.abs(vy + by).max() < 0.02 * 1e-3, nx
+
+
+def test_alfven_wave_quarter_period_shift_and_reverse():
+    """At t = 1/4 the right-moving wave has moved a quarter wavelength in +x
+    (phase -pi/2); the left-moving one (B_y = +sqrt(rho) v_y) in -x."""
+    for right, want in ((True, -math.pi / 2), (False, math.pi / 2)):
+        w = W.alfven_wave(nx=64, right=right)
+        o = oracle.Oracle(w)
+        st = w.copy().state
+        run_to(o, st, 0.0, 0.25)
+        ph, _ = phase_amp(w, w.active(st["vy"])[0, 0], W._mhd_coords(w)[0])
+        assert abs(ph - want) < 0.01, (right, ph)
+
+
+def test_fast_wave_moves_at_the_magnetosonic_speed():
+    """A sound wave across a uniform B_z travels at sqrt(c_s^2 + B^2/rho)
+    (sqrt 2 here, against 1 for the gas alone): the magnetic pressure of
+    cell 7a with its factor 1/2.  Measured phase after a quarter crossing at
+    the fast speed: within 0.025 rad at 64 cells (the split scheme's
+    first-order lag, the same as the hydrodynamic sound wave's)."""
+    w = W.fast_wave(nx=64)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    cf = math.sqrt(2.0)
+    run_to(o, st, 0.0, 0.25 / cf)
+    xf = W._mhd_coords(w)[1]
+    ph, amp = phase_amp(w, w.active(st["vx"])[0, 0], xf)
+    assert abs(ph + math.pi / 2) < 0.025, ph
+    assert abs(amp / 1e-3 - 1.0) < 0.01, amp
+
+
+def test_magnetostatic_column_stays_at_rest():
+    """Gas pressure plus magnetic pressure uniform, no tension (B_z varies
+    along x only): the two gradients of cell 7a cancel to rounding, and so
+    the gas stays at rest; the field, unmoved, stays as it was."""
+    w = W.magnetostatic_column()
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    t = 0.0
+    for _ in range(5):
+        t += o.step(st, t)
+    for k in ("vx", "vy"):
+        assert np.abs(w.active(st[k])).max() < 1e-13, k
+    assert np.abs(w.active(st["bz"] - w.state["bz"])).max() < 1e-13
+
+
+def test_passive_field_leaves_the_gas_alone():
+    """mhd_passive: the field is transported, the gas update is the
+    hydrodynamic one bit for bit (same dt)."""
+    w = W.random_mhd_box(10, 8, 1, seed=5, passive=True)
+    h = w.copy()
+    h.mhd = False
+    om, oh = oracle.Oracle(w), oracle.Oracle(h)
+    sm, sh = w.copy().state, h.copy().state
+    for _ in range(4):
+        om.step(sm, 0.0, dt_fixed=2e-3)
+        oh.step(sh, 0.0, dt_fixed=2e-3)
+    for k in W.FIELDS:
+        assert np.array_equal(sm[k], sh[k]), k
+    assert np.abs(w.active(sm["by"] - w.state["by"])).max() > 1e-5
+
+
+FACE_AXIS = {"vx": 2, "bx": 2, "vy": 1, "by": 1, "vz": 0, "bz": 0}
+
+
+def mirror(w, st, axis):
+    """The state reflected about the box's mid-plane normal to `axis` (array
+    axis: 2 = X, 1 = Y, 0 = Z), on the active cells and faces: a cell-centred
+    value moves from n to N - 1 - n, a face value from face n to N - n with
+    its sign flipped when the face is normal to the axis (the velocity and,
+    the equations being even in B, the field both reflect as polar vectors)."""
+    n = {2: w.nx, 1: w.ny, 0: w.nz}[axis]
+    g = {2: 0, 1: w.gy, 0: w.gz}[axis]
+    out = {}
+    for k, a in st.items():
+        b = a.copy()
+        src = np.moveaxis(a, axis, 0)
+        dst = np.moveaxis(b, axis, 0)
+        if FACE_AXIS.get(k) == axis:
+            for f in range(n if axis == 2 else n + 1):     # X is periodic: face n is face 0
+                dst[g + f] = -src[(n - f) % n if axis == 2 else g + n - f]
+        else:
+            for c in range(n):
+                dst[g + c] = src[g + n - 1 - c]
+        out[k] = b
+    return out
+
+
+def test_mirror_symmetry():
+    """The method has no preferred side: a state reflected about a mid-plane
+    evolves into the reflection of the evolved state, for each axis (every
+    average of the EMF, the star values and the tension centred on its edge
+    or face; an average that leans to one side breaks this)."""
+    for dims in ((8, 6, 4), (10, 8, 1)):
+        w = W.random_mhd_box(*dims, seed=11, eta=0.01)
+        o = oracle.Oracle(w)
+        base = w.copy().state
+        ref = {k: a.copy() for k, a in base.items()}
+        t = 0.0
+        for _ in range(4):
+            t += o.step(ref, t)
+        for axis in ((2, 1, 0) if dims[2] > 1 else (2, 1)):
+            st = mirror(w, base, axis)
+            t = 0.0
+            for _ in range(4):
+                t += o.step(st, t)
+            want = mirror(w, ref, axis)
+            for k in st:
+                a, b = w.active(st[k]), w.active(want[k])
+                assert np.allclose(a, b, rtol=0, atol=1e-12 * max(1.0, np.abs(b).max())), (dims, axis, k,
+                                                                                          np.abs(a - b).max())
+
+
+def test_courant_step_uses_the_fast_speed_and_the_ohmic_rate():
+    """Gas at rest: dt = C / sqrt((c_f / d)^2 + (4 eta / d^2)^2) with
+    c_f^2 = c_s^2 + B^2 / rho (the fast magnetosonic speed), d the smallest
+    cell width, C the Courant number."""
+    rho, e, b = 2.5, 1.2, (0.4, -0.9, 0.3)
+    for eta in (0.0, 0.03):
+        w = W.uniform_mhd_box(16, 8, 4, rho=rho, e=e, b=b, eta=eta)
+        o = oracle.Oracle(w)
+        st = w.copy().state
+        rc, dt = o.cfl(st, o.v0(st))
+        assert rc == 0
+        d = 1.0 / 16
+        cs2 = w.gamma * (w.gamma - 1.0) * e / rho
+        cf = math.sqrt(cs2 + sum(x * x for x in b) / rho)
+        want = w.cfl / math.sqrt((cf / d) ** 2 + (4.0 * eta / d ** 2) ** 2)
+        assert abs(dt - want) <= 1e-14 * want, (eta, dt, want)

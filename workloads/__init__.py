@@ -63,6 +63,9 @@ class Workload:
     av_dt_literal: bool = False
     shearing: bool = False    # Cartesian shearing sheet (X along the shear flow)
     oort_a: float = 0.0       # its shear rate A: unperturbed v_x = 2 A y
+    mhd: bool = False         # magnetic field (state keys bx, by, bz), Cartesian, STANDARD transport
+    mhd_passive: bool = False # the field evolves passively (no magnetic force on the gas)
+    eta: float = 0.0          # Ohmic diffusivity
 
     @property
     def ny_t(self):
@@ -577,3 +580,230 @@ def regression_set(n, n_in, n_out, seed):
     a = rng.normal(size=(n_in, 64)) / math.sqrt(n_in)
     b = rng.normal(size=(64, n_out)) / 8.0
     return x, np.tanh(x @ a) @ b
+
+
+# ---------------------------------------------------------------------------
+# MHD (Sec. 3.5; tests of Sec. 5.2): Cartesian boxes with a face-centred B,
+# state keys bx, by, bz beside the hydrodynamic ones; STANDARD transport.
+# ---------------------------------------------------------------------------
+MHD_FIELDS = ("bx", "by", "bz")
+
+
+def _mhd_base(name, nx, ny, nz, g, xr, yr, zr, gamma, iso, cs, bcy, bcz, cfl=0.44, cq=1.41, eta=0.0,
+              passive=False, t_end=1e30):
+    yf = faces(ny, g, *yr)
+    zf = faces(nz, g, *zr)
+    w = Workload(name, CART, nx, ny, nz, g, xr[0], xr[1], yf, zf, gamma, iso, None, None, cfl, cq, False, 0.0,
+                 bcy, bcz, 0.0, 0.0, 1.0, 0.0, False, 0.0, t_end, {})
+    w.mhd, w.mhd_passive, w.eta = True, passive, eta
+    if iso:
+        w.cs = np.full((w.nz_t, w.ny_t), cs)
+    st = _empty(w.shape)
+    st.update({k: np.zeros(w.shape) for k in MHD_FIELDS})
+    w.state = st
+    return w
+
+
+def _mhd_coords(w):
+    """Cell-centre and face coordinates along X, Y, Z (full ghosted ranges)."""
+    dx = (w.xmax - w.xmin) / w.nx
+    xf = w.xmin + dx * np.arange(w.nx)
+    xc = xf + 0.5 * dx
+    return xc, xf, centres(w.yf), w.yf[:w.ny_t + 1], centres(w.zf), w.zf[:w.nz_t + 1], dx
+
+
+def curl_field(w, ax, ay, az):
+    """A face-centred B = curl A from a vector potential given as functions
+    A_x(x, y, z) at the X edges (x centre, y and z faces), A_y at the Y
+    edges, A_z at the Z edges: each face's B is the circulation of A around
+    it over its area, so the discrete divergence of every cell vanishes to
+    round-off (the constrained-transport invariant)."""
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+    nzt, nyt, nx = w.nz_t, w.ny_t, w.nx
+    xfp = np.append(xf, xf[-1] + dx)                  # x faces 0..nx (periodic wrap)
+    dy = np.diff(w.yf)[:nyt]
+    dz = np.diff(w.zf)[:nzt]
+    g = lambda f, z, y, x: f(x[None, None, :], y[None, :, None], z[:, None, None])  # noqa: E731
+    Ax = g(ax, zfa, yfa, xc)                          # (nzt+1, nyt+1, nx)
+    Ay = g(ay, zfa, yc, xfp)                          # (nzt+1, nyt, nx+1)
+    Az = g(az, zc, yfa, xfp)                          # (nzt, nyt+1, nx+1)
+    bx = np.zeros(w.shape)
+    by = np.zeros(w.shape)
+    bz = np.zeros(w.shape)
+    if w.ny > 1:
+        bx[:nzt, :nyt, :] += (Az[:, 1:, :nx] - Az[:, :nyt, :nx]) / dy[None, :, None]
+        bz[:, :nyt, :] -= (Ax[:, 1:, :] - Ax[:, :nyt, :]) / dy[None, :, None]
+    if w.nz > 1:
+        bx[:nzt, :nyt, :] -= (Ay[1:, :, :nx] - Ay[:nzt, :, :nx]) / dz[:, None, None]
+        by[:nzt, :, :] += (Ax[1:, :, :] - Ax[:nzt, :, :]) / dz[:, None, None]
+    by[:nzt, :, :] -= (Az[:, :, 1:] - Az[:, :, :nx]) / dx
+    bz[:, :nyt, :] += (Ay[:, :, 1:] - Ay[:, :, :nx]) / dx
+    return bx, by, bz
+
+
+def random_mhd_box(nx, ny, nz, g=3, seed=0, iso=False, b0=(0.6, 0.3, 0.2), amp=0.3, eta=0.0, passive=False,
+                   nu=0.0):
+    """A periodic Cartesian box (X, Y, Z all periodic) with a smooth random
+    state and a divergence-free random field: uniform b0 plus the curl of a
+    potential of a few integer Fourier modes of the box, evaluated at the
+    ghosts' positions too (their images one period away)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = (1.0, ny / nx if ny > 1 else 1.0, nz / nx if nz > 1 else 1.0)
+    w = _mhd_base("mhd_box", nx, ny, nz, g, (0.0, L[0]), (0.0, L[1]), (0.0, L[2]), 5.0 / 3.0, iso, 0.8,
+                  (BC_PERIODIC, BC_PERIODIC), (BC_PERIODIC, BC_PERIODIC), eta=eta, passive=passive)
+    if nu > 0:
+        w.nu = np.full((w.nz_t, w.ny_t), nu)
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+
+    def modes(a):
+        terms = []
+        for _ in range(3):
+            k = [rng.integers(0, 3), rng.integers(0, 3) if ny > 1 else 0, rng.integers(0, 3) if nz > 1 else 0]
+            ph = rng.uniform(0, 2 * math.pi)
+            c = a * rng.uniform(-1, 1)
+            terms.append((k, ph, c))
+
+        def f(x, y, z):
+            out = 0.0
+            for k, ph, c in terms:
+                out = out + c * np.cos(2 * math.pi * (k[0] * x / L[0] + k[1] * y / L[1] + k[2] * z / L[2]) + ph)
+            return out
+        return f
+
+    def cell(f, z, y, x):
+        return f(x[None, None, :], y[None, :, None], z[:, None, None]) + 0.0 * np.zeros((len(z), len(y), len(x)))
+
+    st = w.state
+    nzt, nyt = w.nz_t, w.ny_t
+    st["rho"][:nzt, :nyt] = 1.0 + cell(modes(0.2), zc, yc, xc)
+    if not iso:
+        st["e"][:nzt, :nyt] = 1.5 * (1.0 + cell(modes(0.2), zc, yc, xc))
+    st["vx"][:nzt, :nyt] = cell(modes(amp), zc, yc, xf)
+    st["vy"][:nzt, :nyt + 1] = cell(modes(amp), zc, yfa, xc)
+    if nz > 1:
+        st["vz"][:nzt + 1, :nyt] = cell(modes(amp), zfa, yc, xc)
+    bx, by, bz = curl_field(w, modes(0.05), modes(0.05), modes(0.05))
+    st["bx"][:] = bx
+    st["by"][:] = by
+    st["bz"][:] = bz
+    st["bx"][:nzt, :nyt] += b0[0]
+    st["by"][:nzt, :nyt + 1] += b0[1]
+    st["bz"][:nzt + 1, :nyt] += b0[2]
+    return w
+
+
+def current_sheet(nz=512, eta=0.25, b0=1.0, t0=None, g=3, cfl=0.44):
+    """Resistive spreading of a current sheet (Sec. 5.2): a 1.5D column along
+    Z on [-1, 1], gas at rest (rho = 1, P = 1, adiabatic), B_y = b0 erf(z /
+    sqrt(4 eta t)) at t = t0, the field passive, zero-gradient Z boundaries.
+    The field obeys dB_y/dt = eta d2B_y/dz2, whose solution stays the erf
+    with t growing (current_sheet_profile).  t0 defaults to the test's
+    (2.5 dz)^2 (with eta = 0.25: sqrt(4 eta t0) = 2.5 cells)."""
+    w = _mhd_base("current_sheet", 1, 1, nz, g, (0.0, 1.0), (0.0, 1.0), (-1.0, 1.0), 5.0 / 3.0, False, 0.0,
+                  (BC_ZEROGRAD, BC_ZEROGRAD), (BC_ZEROGRAD, BC_ZEROGRAD), cfl=cfl, eta=eta, passive=True)
+    dz = 2.0 / nz
+    if t0 is None:
+        t0 = (2.5 * dz) ** 2
+    w.t0 = t0
+    st = w.state
+    st["rho"][:] = 1.0
+    st["e"][:] = 1.0 / (w.gamma - 1.0)
+    zc = centres(w.zf)
+    st["by"][:w.nz_t, :, :] = current_sheet_profile(zc, t0, eta, b0)[:, None, None]
+    return w
+
+
+def current_sheet_profile(z, t, eta=0.25, b0=1.0):
+    return b0 * np.array([math.erf(v / math.sqrt(4.0 * eta * t)) for v in np.ravel(z)]).reshape(np.shape(z))
+
+
+def _wave_box(name, nx, ny, g, cfl=0.44):
+    return _mhd_base(name, nx, ny, 1, g, (0.0, 1.0), (0.0, ny / nx), (0.0, 1.0), 5.0 / 3.0, False, 0.0,
+                     (BC_PERIODIC, BC_PERIODIC), (BC_ZEROGRAD, BC_ZEROGRAD), cfl=cfl)
+
+
+def alfven_wave(nx=64, ny=4, amp=1e-3, bx=1.0, rho=1.0, pressure=0.6, g=3, modes=1, right=True):
+    """A linear Alfven wave along X in a periodic X-Y box (1 x ny/nx): uniform
+    rho and B_x, v_y = amp sin(k x), B_y = -+ amp sqrt(rho) sin(k x) (the
+    minus sign for the wave moving in +x at v_A = B_x / sqrt(rho)),
+    k = 2 pi modes.  Constant along Y; ny cells there keep v_y and B_y
+    dynamical (a present direction)."""
+    w = _wave_box("alfven_wave", nx, ny, g)
+    st = w.state
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+    k = 2.0 * math.pi * modes
+    s = np.sin(k * xc)[None, None, :]
+    nzt, nyt = w.nz_t, w.ny_t
+    st["rho"][:nzt, :nyt] = rho
+    st["e"][:nzt, :nyt] = pressure / (w.gamma - 1.0)
+    st["bx"][:nzt, :nyt] = bx
+    st["vy"][:nzt, :nyt + 1] = amp * s
+    st["by"][:nzt, :nyt + 1] = (-1.0 if right else 1.0) * amp * math.sqrt(rho) * s
+    return w
+
+
+def fast_wave(nx=64, ny=4, amp=1e-3, bz=1.0, rho=1.0, pressure=0.6, g=3, modes=1):
+    """A linear fast magnetosonic wave along X across a uniform B_z in a
+    periodic X-Y box: the sound wave of rho = 1, P = 0.6 (c_s = 1 with
+    gamma = 5/3) moving in +x, B_z compressed with the gas; it travels at
+    sqrt(c_s^2 + B_z^2 / rho).  v_x = amp sin(k x) at the X faces, the
+    density, pressure and B_z perturbed in phase: delta rho / rho =
+    delta B_z / B_z = v_x / c_f, delta P = gamma P delta rho / rho."""
+    w = _wave_box("fast_wave", nx, ny, g)
+    st = w.state
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+    k = 2.0 * math.pi * modes
+    cs2 = w.gamma * pressure / rho
+    cf = math.sqrt(cs2 + bz * bz / rho)
+    sc = np.sin(k * xc)[None, None, :]
+    nzt, nyt = w.nz_t, w.ny_t
+    d = amp / cf * sc
+    st["rho"][:nzt, :nyt] = rho * (1.0 + d)
+    st["e"][:nzt, :nyt] = (pressure * (1.0 + w.gamma * d)) / (w.gamma - 1.0)
+    st["bz"][:nzt, :nyt] = bz * (1.0 + d)
+    st["vx"][:nzt, :nyt] = amp * np.sin(k * xf)[None, None, :]
+    return w
+
+
+def magnetostatic_column(nx=64, ny=4, b0=1.0, p0=2.0, g=3):
+    """B_z(x) = b0 (1 + 0.5 sin 2 pi x) with the gas pressure P = p0 -
+    B_z^2 / 2 (total pressure uniform), rho = 1, at rest: a magnetostatic
+    equilibrium with no tension (B_z does not vary along z)."""
+    w = _wave_box("magnetostatic_column", nx, ny, g)
+    st = w.state
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+    b = b0 * (1.0 + 0.5 * np.sin(2.0 * math.pi * xc))[None, None, :]
+    nzt, nyt = w.nz_t, w.ny_t
+    st["rho"][:nzt, :nyt] = 1.0
+    st["bz"][:nzt, :nyt] = b
+    st["e"][:nzt, :nyt] = (p0 - 0.5 * b * b) / (w.gamma - 1.0)
+    return w
+
+
+def uniform_mhd_box(nx, ny, nz, rho=1.0, e=1.5, v=(0.0, 0.0, 0.0), b=(0.0, 0.0, 0.0), periodic=True, g=3,
+                    eta=0.0, passive=False):
+    """A Cartesian MHD box holding a uniform state (ghosts included);
+    periodic or zero-gradient Y and Z boundaries.  The starting point of
+    the closed-form pins (each test shapes the fields it needs)."""
+    bc = (BC_PERIODIC, BC_PERIODIC) if periodic else (BC_ZEROGRAD, BC_ZEROGRAD)
+    w = _mhd_base("mhd_uniform", nx, ny, nz, g, (0.0, 1.0), (0.0, ny / nx), (0.0, nz / nx), 5.0 / 3.0, False, 0.0,
+                  bc, bc, eta=eta, passive=passive)
+    st = w.state
+    for k, val in (("rho", rho), ("e", e), ("vx", v[0]), ("vy", v[1]), ("vz", v[2]),
+                   ("bx", b[0]), ("by", b[1]), ("bz", b[2])):
+        st[k][:] = val
+    return w
+
+
+def resistive_mode(nz=32, mode=2, eta=0.1, g=3):
+    """A passive field B_y = sin(2 pi mode z) in a periodic column along Z
+    (unit length) with the gas at rest: Ohmic diffusion alone, each Fourier
+    mode of the discrete Laplacian decaying by its own factor per step."""
+    w = _mhd_base("resistive_mode", 1, 1, nz, g, (0.0, 1.0), (0.0, 1.0), (0.0, 1.0), 5.0 / 3.0, False, 0.0,
+                  (BC_ZEROGRAD, BC_ZEROGRAD), (BC_PERIODIC, BC_PERIODIC), eta=eta, passive=True)
+    st = w.state
+    st["rho"][:] = 1.0
+    st["e"][:] = 1.5
+    zc = centres(w.zf)[:w.nz_t]
+    st["by"][:w.nz_t, :, :] = np.sin(2.0 * math.pi * mode * zc)[:, None, None]
+    return w
