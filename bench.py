@@ -528,6 +528,46 @@ def disk2d_fp32(torch, fb, dev, steps=200, warmup=10):
             "l2": "L2-resident (state about 17 MB), no flush", "clocks": clocks}
 
 
+# Algorithmic bytes per cell of the EMF kernel (cells 8a-8c): it reads
+# rho, v_x, v_y, v_z, B_x, B_y, B_z and writes e_x, e_y, e_z once.
+MHD_EMF_FIELDS = 10
+
+
+def mhd_box(torch, fb, dev, steps=20, warmup=5, dims=(256, 128, 128)):
+    """A 3D periodic MHD box (Sec. 3.5; 256 x 128 x 128 cells, random
+    divergence-free field, eta = 1e-3, artificial viscosity) in FP32 and
+    FP64: cell updates per second of the whole step, and the share and
+    roofline of the four MHD kernels from a kernel-by-kernel step (CUDA
+    events).  The state (about 0.5 GB in FP32) is larger than L2."""
+    w = W.random_mhd_box(*dims, seed=1602, eta=1e-3)
+    peak, kind = peaks()
+    out = {"workload": "mhd3d-cart-periodic-%dx%dx%d" % dims, "cells": w.cells, "hbm_peak_kind": kind}
+    for prec, name, esz in ((fb.F32, "f32", 4), (fb.F64, "f64", 8)):
+        stream = torch.cuda.Stream()
+        c = fb.Fargo(w, prec, stream=stream.cuda_stream)
+        c.set_state(w.state)
+        c.set_time(0.0, 1e30)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                c.step(want_dt=False)
+            ms, clocks = timed_steps(torch, stream, lambda: c.step(want_dt=False), steps, dev, lambda: None)
+            per = c.profile_step()
+        err = c.scalars()[3]
+        c.close()
+        tot = sum(t for _, t in per)
+        mk = {k: round(t, 4) for k, t in per if k.startswith("mhd_")}
+        emf = mk.get("mhd_emf")
+        ach = MHD_EMF_FIELDS * esz * w.cells / (emf * 1e-3) / 1e9 if emf else None
+        out[name] = {"value": w.cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": round(ms, 4),
+                     "steps": steps, "err": err, "clocks": clocks, "mhd_kernels_ms": mk,
+                     "mhd_share_of_step": round(sum(mk.values()) / tot, 4) if tot > 0 else None,
+                     "emf_roofline": {"kernel": "k_mhd_emf", "bound": "hbm" if esz == 4 else "alu",
+                                      "achieved_GBps": round(ach, 1) if ach else None,
+                                      "hbm_peak_GBps": peak, "hbm_frac": round(ach / peak, 4) if ach else None,
+                                      "bytes_per_cell": MHD_EMF_FIELDS * esz}}
+    return out
+
+
 def batch_fp32_error(mem, ps, picks):
     """FP32 error of sampled disks of the batch after the steps the bench
     gave them, against the FP64 oracle run from the same initial state for
@@ -955,6 +995,7 @@ def main():
     if rank == 0 and batched and not args.no_single:
         extra_lines["sod_fp64"] = sod_latency(torch, fb)
         extra_lines["disk2d_fp32"] = disk2d_fp32(torch, fb, dev)
+        extra_lines["mhd3d"] = mhd_box(torch, fb, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload not in ("disk3d-small", "batch-small", "batch-medium"):

@@ -60,7 +60,10 @@ enum { FARGO_F64 = 0, FARGO_F32 = 1 };
  * both, to 1e-12 relative), and the axis needs more active cells than
  * ghost layers. */
 enum { FARGO_BC_REFLECT = 0, FARGO_BC_FROZEN = 1, FARGO_BC_ZEROGRAD = 2, FARGO_BC_PERIODIC = 3 };
-enum { FARGO_RHO = 0, FARGO_ENERGY = 1, FARGO_VX = 2, FARGO_VY = 3, FARGO_VZ = 4 };
+/* Fields: the gas's five, and the magnetic field's face-centred components
+ * (stored like v_x, v_y, v_z; only once fargo_enable_mhd was called). */
+enum { FARGO_RHO = 0, FARGO_ENERGY = 1, FARGO_VX = 2, FARGO_VY = 3, FARGO_VZ = 4,
+       FARGO_BX = 5, FARGO_BY = 6, FARGO_BZ = 7 };
 enum { FARGO_ACTIVE = 0, FARGO_FULL = 1 };
 
 enum {
@@ -261,6 +264,29 @@ int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *
 #define FARGO_MAX_POT_PLANETS 8
 int fargo_set_planet_source(fargo_ctx *ctx, const double *pos, int n, int stride, const double *mass);
 
+/* Magnetic field (Sec. 3.5, the method of characteristics with constrained
+ * transport, MOCCT), mu_0 = 1, on Cartesian meshes with standard transport.
+ * Allocates B_x, B_y, B_z (face centred like the velocity, all zero until
+ * set with fargo_set_field(FARGO_BX..FARGO_BZ)), the edge EMFs and a third
+ * velocity set; from then on every step adds, in the flow chart's order:
+ * the gradient of the transverse magnetic pressure after sub-step 1 (cell
+ * 7a, B at time t), the EMFs of Eq. 45 minus eta curl B (cells 8a-8c) and
+ * the magnetic tension of Eq. 47 (cell 8d), both from the velocities after
+ * the source sub-steps, and after the ghost fill of cell 9 the constrained
+ * transport dB_a/dt = d_b e_o - d_o e_b for the cyclic (a, b, o), with
+ * e = v x B - eta curl B (cell 10; the paper prints Eq. 39 with the signs
+ * of B x v).  The Courant step takes the fast speed sqrt(c_s^2 + B^2/rho)
+ * for the sound speed and adds the Ohmic rate 4 eta / dmin^2.  B's ghosts
+ * are filled like the velocity's (zero gradient, reflection, images on a
+ * periodic axis), along every present axis.  passive != 0: the field is
+ * transported but the gas feels no magnetic force.  eta: the uniform Ohmic
+ * diffusivity (>= 0).  A second call changes passive and eta and keeps B.
+ * In an FP32 context the reference form of v_x is switched off (every vref
+ * is 0).  The net flux of B out of every cell is kept to round-off.
+ * Errors: BADARG (not Cartesian, FARGO transport or shearing sheet on,
+ * eta negative or not finite, context held by a batch), OOM, CUDA. */
+int fargo_enable_mhd(fargo_ctx *ctx, int passive, double eta);
+
 /* Change the frame's rotation rate to omega_new at the current time (Sec.
  * 3.2, Eq. 13): every azimuthal velocity, ghosts included, becomes
  * v_phi - (omega_new - Omega_f) R, R the cylindrical radius of its ring (the
@@ -344,14 +370,20 @@ int fargo_sums_noalloc(const void *rho, const void *e, const void *vx, int preci
  * phase: 0 ghost fill, 1 v0 + Courant reduction (the caller's dt is
  * ignored), 2 sub-step 1, 3 artificial viscosity + compression heating,
  * 4 viscosity, 5 momenta + residual X sweep, 6 Y sweep, 7 Z sweep,
- * 8 new velocities, 9 uniform orbital step (integer shift + PPA).
- * Phases 2-9 use the given dt.  Results land in the state fields; phases
+ * 8 new velocities, 9 uniform orbital step (integer shift + PPA); with a
+ * magnetic field: 10 magnetic pressure (cell 7a), 11 EMFs (cells 8a-8c,
+ * into aux 7-9), 12 magnetic tension (cell 8d), 13 constrained transport
+ * (cell 10, with the EMFs of aux 7-9).
+ * Phases 2-13 use the given dt.  Results land in the state fields; phases
  * 5-9 read and write the momenta, accessible with fargo_get_aux/set_aux;
  * phases 5 and 9 read v0 (fargo_set_aux(6) or phase 1). */
 int fargo_debug_phase(fargo_ctx *ctx, int phase, double dt);
 
 /* Auxiliary arrays: which = 0..5 momenta Pi-_x, Pi+_x, Pi-_y, Pi+_y, Pi-_z,
- * Pi+_z (FULL region, context precision); 6 = v0 per ring (nz_t*ny_t FP64).
+ * Pi+_z (FULL region, context precision); 6 = v0 per ring (nz_t*ny_t FP64);
+ * 7..9 = the EMFs e_x, e_y, e_z of the last step (FULL region, with a
+ * magnetic field; e_o at index (i, j, k) lies on the edge along o at the
+ * lower faces of cell (i, j, k) across the two other directions).
  * In an FP32 context the X momenta are held as Pi - rho (R vref + w), w the
  * frame term of Tab. "momenta" (R^2 Omega_f, or 2 Omega_f y on the shearing
  * sheet), and are exchanged in that form.  Host buffers.  Errors: BADARG,

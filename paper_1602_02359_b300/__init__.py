@@ -16,9 +16,11 @@ LIBPATH = os.path.join(HERE, "libfargo_b300.so")
 
 CART, CYL, SPH = 0, 1, 2
 F64, F32 = 0, 1
-RHO, ENERGY, VX, VY, VZ = range(5)
+RHO, ENERGY, VX, VY, VZ, BX, BY, BZ = range(8)
 ACTIVE, FULL = 0, 1
-FIELD_IDS = {"rho": RHO, "e": ENERGY, "vx": VX, "vy": VY, "vz": VZ}
+FIELD_IDS = {"rho": RHO, "e": ENERGY, "vx": VX, "vy": VY, "vz": VZ, "bx": BX, "by": BY, "bz": BZ}
+GAS_FIELDS = ("rho", "e", "vx", "vy", "vz")
+MHD_FIELDS = ("bx", "by", "bz")
 
 ERRORS = {0: "ok", -1: "BADARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "DT", -6: "SIZE",
           -7: "BARRIER_TIMEOUT", -8: "NOTBUILT"}
@@ -30,7 +32,7 @@ EXPORTED = ("fargo_create", "fargo_destroy", "fargo_set_field", "fargo_get_field
             "fargo_alu_peaks", "fargo_batch_create", "fargo_batch_destroy", "fargo_batch_step", "fargo_batch_status",
             "fargo_batch_run", "fargo_batch_use_graph", "fargo_batch_launches_per_step",
             "fargo_batch_profile_step", "fargo_batch_autotune", "fargo_batch_set_field_packed",
-            "fargo_batch_get_field_packed", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_track_frame", "fargo_set_planet_source", "fargo_planet_torque_profile", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
+            "fargo_batch_get_field_packed", "fargo_planet_force", "fargo_planet_force_async", "fargo_planets_force_async", "fargo_nbody_rk5_async", "fargo_planets_advance_async", "fargo_change_frame", "fargo_track_frame", "fargo_enable_mhd", "fargo_set_planet_source", "fargo_planet_torque_profile", "fargo_batch_set_field", "fargo_batch_get_field", "fargo_autotune", "fargo_set_launch_shape", "fargo_debug_wait_timeout",
             "fargo_mlp_create", "fargo_mlp_destroy", "fargo_mlp_num_params", "fargo_mlp_set_params",
             "fargo_mlp_get_params", "fargo_mlp_get_grads", "fargo_mlp_set_input_map", "fargo_mlp_set_output_map",
             "fargo_mlp_set_optimizer",
@@ -98,6 +100,7 @@ def lib():
                                             vp]
         L.fargo_planets_advance_async.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int]
         L.fargo_change_frame.argtypes = [vp, C.c_double]
+        L.fargo_enable_mhd.argtypes = [vp, C.c_int, C.c_double]
         L.fargo_track_frame.argtypes = [vp, vp, C.c_int, PD]
         L.fargo_set_planet_source.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.fargo_planet_torque_profile.argtypes = [vp, PD, C.c_double, C.c_int, vp, PD]
@@ -187,6 +190,9 @@ class Fargo:
         self.h = h
         self.shape = w.shape
         self.active_shape = (w.nz, w.ny, w.nx)
+        self.mhd = False
+        if getattr(w, "mhd", False):
+            self.enable_mhd(bool(getattr(w, "mhd_passive", False)), float(getattr(w, "eta", 0.0)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -221,11 +227,18 @@ class Fargo:
         return a
 
     def set_state(self, st, region=FULL):
-        for k in ("rho", "e", "vx", "vy", "vz"):
+        for k in GAS_FIELDS + (MHD_FIELDS if self.mhd else ()):
             self.set_field(k, st[k], region)
 
     def get_state(self, region=FULL):
-        return {k: self.get_field(k, region) for k in ("rho", "e", "vx", "vy", "vz")}
+        return {k: self.get_field(k, region) for k in GAS_FIELDS + (MHD_FIELDS if self.mhd else ())}
+
+    def enable_mhd(self, passive=False, eta=0.0):
+        """fargo_enable_mhd: a magnetic field (B_x, B_y, B_z, zero until set,
+        fields "bx", "by", "bz") on this Cartesian context; `passive` keeps
+        the gas free of magnetic forces, `eta` is the Ohmic diffusivity."""
+        _check(lib().fargo_enable_mhd(self.h, int(bool(passive)), float(eta)), "fargo_enable_mhd")
+        self.mhd = True
 
     # ---- time stepping
     def set_time(self, t, t_end=1e300):
@@ -338,10 +351,10 @@ class Fargo:
 
     def profile_step(self):
         """One step launched kernel by kernel; returns [(kernel, ms), ...]."""
-        ms = (C.c_float * 32)()
-        names = (C.c_char_p * 32)()
+        ms = (C.c_float * 64)()
+        names = (C.c_char_p * 64)()
         n = C.c_int()
-        _check(lib().fargo_profile_step(self.h, 32, ms, C.byref(n), names), "fargo_profile_step")
+        _check(lib().fargo_profile_step(self.h, 64, ms, C.byref(n), names), "fargo_profile_step")
         return [(names[i].decode(), ms[i]) for i in range(n.value)]
 
     def use_graph(self, on=True):

@@ -14,6 +14,7 @@
 #include "kernels_transport.cuh"
 #include "kernels_planet.cuh"
 #include "kernels_nbody.cuh"
+#include "kernels_mhd.cuh"
 
 namespace fk {
 
@@ -24,6 +25,10 @@ struct Buffers {
     T *piA[6] = {}, *piB[6] = {};
     T *rhoB = nullptr, *eB = nullptr;
     Tab<T> tab{};
+    // MHD (fargo_enable_mhd): the EMFs of the edges and the velocities after
+    // the magnetic tension (the field itself is tab.bfield)
+    T *ef[3] = {nullptr, nullptr, nullptr};
+    T *vM[3] = {nullptr, nullptr, nullptr};
 };
 
 struct HostGeom {
@@ -44,7 +49,12 @@ struct StepPlan {
     MeshD m;
     Tab<T> tb;
     Fld<T> A, VB;      // state and the scratch velocities of the source step
-    Fld<T> vsrc;       // post-source velocities (VB with viscosity, else A)
+    Fld<T> vsrc;       // post-source velocities (VB with viscosity, else A; with magnetic
+                       // forces, the tension's output VM)
+    Fld<T> vpre;       // the velocities the EMFs and the tension read (VB with viscosity, else A)
+    Fld<T> VM;         // the tension's output (MHD)
+    MagF<T> B;         // the field (null without MHD)
+    T *E[3];           // the EMFs (MHD)
     Fld<T> txin;       // input of the X sweep: state scalars, post-source velocities
     QSet<T> qx, qy, qz;   // outputs of the X, Y and Z sweeps
     QSet<T> qfin;      // quantity set after the sweeps (orbital step in place, new velocities)
@@ -133,6 +143,13 @@ static StepPlan<T> make_plan(const fargo_ctx *c, const Buffers<T> &b)
     p.A = b.A;
     p.VB = {b.A.rho, b.A.e, b.vB[0], b.vB[1], b.vB[2]};
     p.vsrc = m.has_nu ? p.VB : p.A;
+    p.vpre = p.vsrc;
+    for (int d = 0; d < 3; d++) {
+        p.B.b[d] = m.mhd ? b.tab.bfield[d] : nullptr;
+        p.E[d] = b.ef[d];
+    }
+    p.VM = {b.A.rho, b.A.e, b.vM[0], b.vM[1], b.vM[2]};
+    if (m.mhd && !m.mhd_passive) p.vsrc = p.VM;
     p.txin = {b.A.rho, b.A.e, p.vsrc.vx, p.vsrc.vy, p.vsrc.vz};
     for (int q = 0; q < 6; q++) p.tau.q[q] = b.piB[q];
     p.tau.nq = 6;

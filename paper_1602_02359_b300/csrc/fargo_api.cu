@@ -371,7 +371,7 @@ static int alloc_fields(fargo_ctx *c, Buffers<T> &b)
 // lands in the state buffers.
 // ---------------------------------------------------------------------------
 // Optional per-launch event marks (fargo_profile_step).
-constexpr int kProfMax = 48;   // launches of one step, periodic images included
+constexpr int kProfMax = 64;   // launches of one step, periodic images included
 struct Prof {
     cudaEvent_t ev[kProfMax + 1];
     const char *name[kProfMax];
@@ -396,8 +396,8 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     } while (0)
     const dim3 cb = cell_block(m, c->cell_bs), cg = cell_grid_all(m, c->cell_bs);
     // cell 2
-    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0, P.tb.vref); MARK("bc_y"); }
-    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0, P.tb.vref); MARK("bc_z"); }
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0, P.tb.vref, P.B); MARK("bc_y"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.A, P.sc, 0, P.tb.vref, P.B); MARK("bc_z"); }
     // cells 3-6
     k_cfl_screen<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_screen");
@@ -414,6 +414,9 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     } while (0)
     // cell 7
     launch_source<T>(SRC_SUB1, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("substep1");
+    // the magnetic pressure of the transverse field, with B at time t (cell 7a)
+    const dim3 fgrid(cg.x, m.nyt + 1, m.nzt + 1);
+    if (m.mhd && !m.mhd_passive) { k_mhd_pressure<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.VB, P.sc); MARK("mhd_pressure"); }
     PERIODIC(per_fields<T>(m, P.VB, true, false), "periodic");
     launch_source<T>(SRC_AV, m, cg, cb, s, P.tb, P.VB, P.A, P.tau, P.sc); MARK("artvisc");
     PERIODIC(per_fields<T>(m, P.A, true, true), "periodic");
@@ -426,9 +429,27 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         launch_source<T>(SRC_VAPPLY, m, cg, cb, s, P.tb, P.A, P.VB, P.tau, P.sc); MARK("visc_apply");
         PERIODIC(per_fields<T>(m, P.VB, true, false), "periodic");
     }
+    // cells 8a-8d: the EMFs and the magnetic tension, both from the velocities
+    // after the source sub-steps
+    if (m.mhd) {
+        k_mhd_emf<T><<<dim3(cg.x, mh_edge_rows(m), mh_edge_planes(m)), cb, 0, s>>>(m, P.tb, P.vpre, P.E[0], P.E[1],
+                                                                                 P.E[2], P.sc);
+        MARK("mhd_emf");
+        if (!m.mhd_passive) {
+            k_mhd_tension<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.vpre, P.VM, P.sc);
+            MARK("mhd_tension");
+            PERIODIC(per_fields<T>(m, P.VM, true, false), "periodic");
+        }
+    }
     // cell 9
-    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1, P.tb.vref); MARK("bc_y9"); }
-    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1, P.tb.vref); MARK("bc_z9"); }
+    if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1, P.tb.vref, P.B); MARK("bc_y9"); }
+    if (m.hasZ) { k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1, P.tb.vref, P.B); MARK("bc_z9"); }
+    // cell 10: constrained transport of the field
+    if (m.mhd) {
+        k_mhd_ct<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.E[0], P.E[1], P.E[2], P.sc);
+        MARK("mhd_ct");
+        PERIODIC(per_field<T>(m, P.tb), "periodic");
+    }
     // cell 12
     launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_rs, s);
     MARK("transport_x");
@@ -734,12 +755,21 @@ static void *field_ptr(fargo_ctx *c, int field)
 {
     if (c->prec == FARGO_F64) {
         Fld<double> &A = c->b64.A;
-        void *p[5] = {A.rho, A.e, A.vx, A.vy, A.vz};
+        double *const *B = c->b64.tab.bfield;
+        void *p[8] = {A.rho, A.e, A.vx, A.vy, A.vz, B[0], B[1], B[2]};
         return p[field];
     }
     Fld<float> &A = c->b32.A;
-    void *p[5] = {A.rho, A.e, A.vx, A.vy, A.vz};
+    float *const *B = c->b32.tab.bfield;
+    void *p[8] = {A.rho, A.e, A.vx, A.vy, A.vz, B[0], B[1], B[2]};
     return p[field];
+}
+
+// Fields a context holds: the five of the gas, and B_x, B_y, B_z once a
+// magnetic field is enabled.
+static bool field_ok(const fargo_ctx *c, int field)
+{
+    return field >= 0 && (field <= 4 || (field <= 7 && c->m.mhd));
 }
 
 // Queue the copies of one field region on `stream` (no synchronisation).
@@ -781,7 +811,7 @@ static int copy_region(fargo_ctx *c, void *dev, void *host, int region, size_t b
 // fargo_batch.cu): one field of member c queued on the batch's stream.
 int fargo_queue_field(fargo_ctx *c, int field, int region, void *buf, size_t bytes, int to_dev, cudaStream_t s)
 {
-    if (!c || !buf || field < 0 || field > 4) return FARGO_ERR_BADARG;
+    if (!c || !buf || !field_ok(c, field)) return FARGO_ERR_BADARG;
     if (c->prec == FARGO_F32 && field == FARGO_VX) {
         // v_x crosses the boundary in v_x form (the stored values are v_x - vref)
         Buffers<float> &b = c->b32;
@@ -803,7 +833,7 @@ int fargo_queue_field(fargo_ctx *c, int field, int region, void *buf, size_t byt
 extern "C" int fargo_set_field(fargo_ctx *c, int field, int region, const void *src, size_t bytes, int on_device)
 {
     (void)on_device;
-    if (!c || !src || field < 0 || field > 4) return FARGO_ERR_BADARG;
+    if (!c || !src || !field_ok(c, field)) return FARGO_ERR_BADARG;
     const int rc = fargo_queue_field(c, field, region, (void *)src, bytes, 1, c->stream);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
@@ -813,7 +843,7 @@ extern "C" int fargo_set_field(fargo_ctx *c, int field, int region, const void *
 extern "C" int fargo_get_field(fargo_ctx *c, int field, int region, void *dst, size_t bytes, int on_device)
 {
     (void)on_device;
-    if (!c || !dst || field < 0 || field > 4) return FARGO_ERR_BADARG;
+    if (!c || !dst || !field_ok(c, field)) return FARGO_ERR_BADARG;
     const int rc = fargo_queue_field(c, field, region, dst, bytes, 0, c->stream);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
@@ -1245,6 +1275,50 @@ extern "C" int fargo_track_frame(fargo_ctx *c, const double *y, int index, doubl
     return rc;
 }
 
+// ---------------------------------------------------------------------------
+// Magnetic field (Sec. 3.5): B, the EMFs and the tension's output
+// velocities, allocated once and zero.  FP32 contexts switch the reference
+// form of v_x off (every vref 0), since the MHD kernels read v_x itself.
+// ---------------------------------------------------------------------------
+template <typename T>
+static int enable_mhd_impl(fargo_ctx *c, Buffers<T> &b)
+{
+    const size_t n = (size_t)c->m.ntot * sizeof(T);
+    int rc;
+    void *p;
+    if (!b.tab.bfield[0])
+        for (int d = 0; d < 3; d++) {
+            if ((rc = dalloc(c, &p, n))) return rc;
+            b.tab.bfield[d] = (T *)p;
+            if ((rc = dalloc(c, &p, n))) return rc;
+            b.ef[d] = (T *)p;
+            if ((rc = dalloc(c, &p, n))) return rc;
+            b.vM[d] = (T *)p;
+        }
+    if ((rc = vref_launch<T>(c, b, VREF_ABS, nullptr, c->stream))) return rc;
+    c->m.mhd = 1;
+    if ((rc = vref_refresh<T>(c, b, c->stream))) return rc;
+    // the Y / Z sweeps read v_y, v_z through tensor maps: with magnetic
+    // forces they read the tension's output
+    return build_sweep_maps<T>(c, b);
+}
+
+extern "C" int fargo_enable_mhd(fargo_ctx *c, int passive, double eta)
+{
+    if (!c || c->geom != FARGO_CART || c->m.fargo || c->m.shearing || c->batch_refs > 0) return FARGO_ERR_BADARG;
+    if (!(eta >= 0.0) || !isfinite(eta)) return FARGO_ERR_BADARG;
+    c->m.mhd_passive = passive ? 1 : 0;
+    c->m.eta = eta;
+    const int rc = c->prec == FARGO_F64 ? enable_mhd_impl<double>(c, c->b64) : enable_mhd_impl<float>(c, c->b32);
+    if (rc) return rc;
+    if (c->gexec) {   // the captured step has no MHD launches
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return FARGO_OK;
+}
+
 extern "C" int fargo_set_planet_source(fargo_ctx *c, const double *pos, int n, int stride, const double *mass)
 {
     if (!c || !c->m.has_planet || c->geom == FARGO_CART) return FARGO_ERR_BADARG;
@@ -1303,10 +1377,16 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         return FARGO_OK;
     };
     T *va[3] = {A.vx, A.vy, A.vz};
+    MagF<T> MB{};
+    if (m.mhd)
+        for (int d = 0; d < 3; d++) MB.b[d] = b.tab.bfield[d];
+    if (phase >= 10 && !m.mhd) return FARGO_ERR_BADARG;
+    const dim3 fg(cell_grid_all(m, c->cell_bs).x, m.nyt + 1, m.nzt + 1);
+    const dim3 fb = cell_block(m, c->cell_bs);
     switch (phase) {
     case 0:
-        if (m.hasY) k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1, b.tab.vref);
-        if (m.hasZ) k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1, b.tab.vref);
+        if (m.hasY) k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1, b.tab.vref, MB);
+        if (m.hasZ) k_bc_z<T><<<grid_for((long long)m.nx * (m.nyt + 1) * 2, bs), bs, 0, s>>>(m, A, c->sc, 1, b.tab.vref, MB);
         break;
     case 1:
         k_cfl_screen<T><<<c->cfl_blocks, 256, 0, s>>>(m, b.tab, A, c->v0, c->ringmax, c->part, c->sc,
@@ -1370,6 +1450,27 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
             launch_periodic<T>(m, per_quantities<T>(qa, qa), c->sc, s);
         }
         break;
+    case 10:   // the magnetic pressure (cell 7a), in place on the state's velocities
+        if (!m.mhd_passive) k_mhd_pressure<T><<<fg, fb, 0, s>>>(m, b.tab, A, c->sc);
+        launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
+        break;
+    case 11:   // the EMFs (cells 8a-8c) of the state, into the aux arrays 7-9
+        k_mhd_emf<T><<<dim3(fg.x, mh_edge_rows(m), mh_edge_planes(m)), fb, 0, s>>>(m, b.tab, A, b.ef[0], b.ef[1],
+                                                                                 b.ef[2], c->sc);
+        break;
+    case 12: {  // the magnetic tension (cell 8d), back into the state's velocities
+        if (m.mhd_passive) break;
+        Fld<T> VM = {A.rho, A.e, b.vM[0], b.vM[1], b.vM[2]};
+        k_mhd_tension<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, c->sc);
+        if ((rc = copyv(va, b.vM))) return rc;
+        if (!m.hasZ) CK(cudaMemcpyAsync(va[2], b.vM[2], nbytes, cudaMemcpyDeviceToDevice, s));
+        launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
+        break;
+    }
+    case 13:   // the constrained transport (cell 10) with the aux EMFs
+        k_mhd_ct<T><<<fg, fb, 0, s>>>(m, b.tab, b.ef[0], b.ef[1], b.ef[2], c->sc);
+        launch_periodic<T>(m, per_field<T>(m, b.tab), c->sc, s);
+        break;
     default:
         return FARGO_ERR_BADARG;
     }
@@ -1407,6 +1508,12 @@ static int aux_ptr(fargo_ctx *c, int which, void **p, size_t *bytes, int *pitche
         *p = c->v0;
         *bytes = (size_t)c->nzt * c->nyt * sizeof(double);
         *pitched = 0;
+        return FARGO_OK;
+    }
+    if (which >= 7 && which < 10 && c->m.mhd) {   // the EMFs e_x, e_y, e_z
+        *p = c->prec == FARGO_F64 ? (void *)c->b64.ef[which - 7] : (void *)c->b32.ef[which - 7];
+        *bytes = (size_t)(c->nzt + 1) * (c->nyt + 1) * c->nx * c->esz;
+        *pitched = 1;
         return FARGO_OK;
     }
     return FARGO_ERR_BADARG;

@@ -690,6 +690,7 @@ extern "C" int fargo_batch_create(fargo_batch **out, fargo_ctx *const *members, 
         if (!members[i] || members[i]->prec != prec) return FARGO_ERR_BADARG;
         // the batched phases have no periodic-image launches between them
         if (members[i]->m.pery || members[i]->m.perz) return FARGO_ERR_BADARG;
+        if (members[i]->m.mhd) return FARGO_ERR_BADARG;   // no magnetic field in the batched engine
         for (int k = 0; k < i; k++)
             if (members[k] == members[i]) return FARGO_ERR_BADARG;
     }

@@ -26,6 +26,9 @@ struct MeshD {
                                  // p * pl_stride), or null for the fixed circular orbit
     const double *pl_mass;       // their masses (device), or null: the planet of creation's q
     int pl_n, pl_stride;
+    int mhd;                     // magnetic field (Sec. 3.5): Cartesian, standard transport
+    int mhd_passive;             // the field is transported but exerts no force on the gas
+    double eta;                  // Ohmic diffusivity
 };
 
 // Geometry tables (Appendix A) in the field precision T, plus the FP64
@@ -78,6 +81,15 @@ struct Tab {
     // rings' frames with dAy[r] = A(r) - A(r - 1), dAz[r] = A(r) - A(r - nyt).
     T *vref, *dAy, *dAz;
     double *vrefd;
+    // MHD: the face-centred field B_x, B_y, B_z (stored like v_x, v_y, v_z;
+    // null without a field)
+    T *bfield[3];
+};
+
+// The magnetic field's three components (null: no field).
+template <typename T>
+struct MagF {
+    T *b[3];
 };
 
 template <typename T>

@@ -67,9 +67,12 @@ __device__ __forceinline__ bool bc_skip(const Scal *sc, int mode)
     return !(sc->dt > 0.0);
 }
 
+// The magnetic field (MagF, MHD) is filled like the velocity, component d
+// like v_d, but along every present axis: B_z, B_y stay transverse fields
+// of a mesh without Z or Y, where v_z, v_y are unused.
 template <typename T>
 __device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid,
-                                          const T *vref = nullptr)
+                                          const T *vref = nullptr, MagF<T> mb = MagF<T>{})
 {
     long long n = (long long)m.nx * (m.nzt + 1) * 2;
     if (tid >= n || bc_skip(sc, mode)) return;
@@ -87,11 +90,16 @@ __device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const
         fill_line(fl[q], k * m.sk + i, m.sj, m.j0, m.j1, m.g, q == 3, side, bc,
                   q == 2 && vref ? vref + k * m.nyt : (const T *)nullptr, 1);
     }
+    if (mb.b[0])
+        for (int d = 0; d < 3; d++) {
+            if (k >= (d == 2 ? m.nzt + 1 : m.nzt)) continue;
+            fill_line(mb.b[d], k * m.sk + i, m.sj, m.j0, m.j1, m.g, d == 1, side, bc);
+        }
 }
 
 template <typename T>
 __device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid,
-                                          const T *vref = nullptr)
+                                          const T *vref = nullptr, MagF<T> mb = MagF<T>{})
 {
     long long n = (long long)m.nx * (m.nyt + 1) * 2;
     if (tid >= n || bc_skip(sc, mode)) return;
@@ -109,6 +117,11 @@ __device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const
         fill_line(fl[q], j * m.sj + i, m.sk, m.k0, m.k1, m.g, q == 4, side, bc,
                   q == 2 && vref ? vref + j : (const T *)nullptr, m.nyt);
     }
+    if (mb.b[0])
+        for (int d = 0; d < 3; d++) {
+            if (j >= (d == 1 ? m.nyt + 1 : m.nyt)) continue;
+            fill_line(mb.b[d], j * m.sj + i, m.sk, m.k0, m.k1, m.g, d == 2, side, bc);
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -215,14 +228,14 @@ static PerSet<T> per_quantities(const QSet<T> &dst, const QSet<T> &src)
 }
 
 template <typename T>
-__global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode, const T *vref)
+__global__ void k_bc_y(MeshD m, Fld<T> f, const Scal *sc, int mode, const T *vref, MagF<T> mb)
 {
-    bc_y_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x, vref);
+    bc_y_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x, vref, mb);
 }
 template <typename T>
-__global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode, const T *vref)
+__global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode, const T *vref, MagF<T> mb)
 {
-    bc_z_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x, vref);
+    bc_z_body(m, f, sc, mode, (long long)blockIdx.x * blockDim.x + threadIdx.x, vref, mb);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,7 +258,39 @@ __global__ void k_bc_z(MeshD m, Fld<T> f, const Scal *sc, int mode, const T *vre
 //    to t_end.
 // The screening launch also fills the per-step planet angle tables (sin^2 of
 // half the azimuth offset to the planet and its cosine) used by sub-step 1.
+// With a magnetic field (Sec. 3.5) the sound speed becomes the fast speed
+// sqrt(c_s^2 + B^2 / rho), B^2 from zone-centred two-point averages of the
+// face values, and the Ohmic rate 4 eta / dmin^2 joins the sum of squares
+// after the four others (the paper prints no MHD time-step condition).
 // ---------------------------------------------------------------------------
+// |B|^2 at the centre of cell c = (i, j, k): each component the mean of its
+// two faces (the single value along an absent direction), summed X, Y, Z;
+// FP64 round-to-nearest, or FP32 for the screen.
+template <typename T>
+__device__ __forceinline__ double mhd_b2(const MeshD &m, const Tab<T> &tb, idx_t c, int i)
+{
+    const idx_t n1[3] = {c - i + (i + 1 == m.nx ? 0 : i + 1), m.hasY ? c + m.sj : c, m.hasZ ? c + m.sk : c};
+    double b2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double bc = __dmul_rn(0.5, __dadd_rn((double)tb.bfield[d][c], (double)tb.bfield[d][n1[d]]));
+        b2 = __dadd_rn(b2, __dmul_rn(bc, bc));
+    }
+    return b2;
+}
+template <typename T>
+__device__ __forceinline__ float mhd_b2f(const MeshD &m, const Tab<T> &tb, idx_t c, int i)
+{
+    const idx_t n1[3] = {c - i + (i + 1 == m.nx ? 0 : i + 1), m.hasY ? c + m.sj : c, m.hasZ ? c + m.sk : c};
+    float b2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const float bc = 0.5f * ((float)tb.bfield[d][c] + (float)tb.bfield[d][n1[d]]);
+        b2 += bc * bc;
+    }
+    return b2;
+}
+
 __device__ __forceinline__ double warp_max(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -392,6 +437,7 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
         const float dmin = (float)tb.dminT[ring];
         const float idm2 = 1.0f / (dmin * dmin);
         const float r4 = m.has_nu ? (float)tb.r4[ring] : 0.0f;
+        const float r5 = m.mhd ? 4.0f * (float)m.eta * idm2 : 0.0f;
         const float csr = m.iso ? (float)tb.cs[ring] : 0.0f;
         const float c1 = m.iso ? csr * csr * idm2 : (float)tb.g1 * idm2;
         const bool lit = m.av_lit != 0;
@@ -451,7 +497,8 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
                     if (avon) r3 = fmaxf(r3, av_ratef(lit, k4, (float)(vp - vc), ilz));
                     if (!isfinite((float)vc)) bad = 1;
                 }
-                const float s = r1s + r2 * r2 + r3 * r3 + r4 * r4;
+                float s = r1s + r2 * r2 + r3 * r3 + r4 * r4;
+                if (m.mhd) s += __fdividef(mhd_b2f(m, tb, c + u, i0 + u), rho) * idm2 + r5 * r5;
                 smax = fmaxf(smax, s);
             }
         }
@@ -525,6 +572,8 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
         const float dmf = (float)tb.dminT[ring];
         const float idm2 = 1.0f / (dmf * dmf);
         const float r4f = m.has_nu ? (float)tb.r4[ring] : 0.0f;
+        const float r5f = m.mhd ? 4.0f * (float)m.eta * idm2 : 0.0f;
+        const double r5 = m.mhd && m.eta > 0.0 ? __ddiv_rn(__dmul_rn(4.0, m.eta), __dmul_rn(dmin, dmin)) : 0.0;
         const float c1 = m.iso ? (float)csr * (float)csr * idm2 : (float)tb.g1 * idm2;
         const bool lit = m.av_lit != 0, avon = m.has_av != 0;
         const float k4 = (float)tb.k4;
@@ -554,11 +603,14 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
                     if (avon) e3 = fmaxf(e3, av_ratef(lit, k4, (float)(vp - vc), ilz));
                 }
                 est += e2 * e2 + e3 * e3 + r4f * r4f;
+                if (m.mhd) est += __fdividef(mhd_b2f(m, tb, c, i), rf) * idm2 + r5f * r5f;
                 if ((double)est < thr) continue;
             }
             const double rho = (double)f.rho[c];
             const double cs = m.iso ? csr : __dsqrt_rn(__ddiv_rn(__dmul_rn(m.g1, (double)f.e[c]), rho));
-            const double r1 = __ddiv_rn(cs, dmin);
+            const double r1 = m.mhd ? __ddiv_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(cs, cs),
+                                                                     __ddiv_rn(mhd_b2(m, tb, c, i), rho))), dmin)
+                                    : __ddiv_rn(cs, dmin);
             double r2 = 0.0, r3 = 0.0;
             if (m.hasX) {
                 const double vc = (double)f.vx[c], vp = (double)f.vx[base + ip];
@@ -579,9 +631,10 @@ __device__ __forceinline__ void cfl_exact_body(const MeshD &m, const Tab<T> &tb,
                 r3 = fmax(r3, av_rate(m, __dsub_rn(vp, vc), lz));
             }
             if (m.cq <= 0.0) r3 = 0.0;
-            const double s = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(r1, r1), __dmul_rn(r2, r2)),
-                                                 __dmul_rn(r3, r3)),
-                                       __dmul_rn(r4, r4));
+            double s = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(r1, r1), __dmul_rn(r2, r2)),
+                                           __dmul_rn(r3, r3)),
+                                 __dmul_rn(r4, r4));
+            if (r5 > 0.0) s = __dadd_rn(s, __dmul_rn(r5, r5));
             smax = fmax(smax, s);
         }
     }
@@ -714,7 +767,8 @@ __device__ void vref_ring(const MeshD &m, const Tab<T> &tb, T *vx, T *dst, int r
     }
     mx = warp_max(mx);
     mn = warp_min(mn);
-    T r = fin ? (T)(0.5 * (mx + mn)) : T(0);
+    // (no reference with a magnetic field: the MHD kernels read v_x itself)
+    T r = fin && !m.mhd ? (T)(0.5 * (mx + mn)) : T(0);
     bool exact = fin;
     for (int i = lane; i < m.nx && exact; i += 32) {
         const T v = vx[bi + i];
