@@ -258,3 +258,29 @@ def test_mhd_rejected_where_it_does_not_apply():
         fb.FargoBatch([m])
     for c in (cyl, disk, box, m):
         c.close()
+
+
+def test_field_loop_on_the_gpu_matches_the_oracle_and_the_paper():
+    """The loop test of Sec. 5.2 (128 x 64, Y-Z plane, periodic) to t = 2:
+    FP64 on the oracle's run (1e-11 on B) and both precisions on the
+    paper's magnetic energy 1.235e-7 within 1 % (tests/golden)."""
+    import paper_1602_02359_b300 as fb
+    from tests.test_oracle_pins import read_golden
+    g = read_golden("field_loop_paper.txt")
+    w = W.field_loop()
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    o.run(st, 0.0, g["t"])
+    res = {}
+    for prec, name in ((fb.F64, "f64"), (fb.F32, "f32")):
+        c = make_ctx(w, prec, t_end=g["t"])
+        c.run_to(g["t"])
+        gs = {k: np.asarray(v, dtype=np.float64) for k, v in c.get_state().items()}
+        res[name] = W.magnetic_energy(w, gs)
+        if prec == fb.F64:
+            r = worst(w, gs, st, W.MHD_FIELDS)
+            assert max(r.values()) <= 1e-11, r
+        c.close()
+    record("field_loop_t2", oracle=W.magnetic_energy(w, st), **res)
+    for name, e in res.items():
+        assert abs(e - g["magnetic_energy_t2"]) <= 0.01 * g["magnetic_energy_t2"], (name, e)

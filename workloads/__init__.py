@@ -807,3 +807,52 @@ def resistive_mode(nz=32, mode=2, eta=0.1, g=3):
     zc = centres(w.zf)[:w.nz_t]
     st["by"][:w.nz_t, :, :] = np.sin(2.0 * math.pi * mode * zc)[:, None, None]
     return w
+
+
+def field_loop(ny=128, nz=64, vy=math.sqrt(5.0) / 2.0, vz=0.0, a0=1e-3, radius=0.3, g=3):
+    """The magnetic field loop advected across a periodic Y-Z box (Sec. 5.2,
+    the loop test): y in [-1, 1], z in [-0.5, 0.5], rho = 1, P = 1,
+    gamma = 5/3, uniform velocity (v_y, v_z), B = curl A with
+    A_x = a0 (radius - r) inside r < radius (r the distance to the box
+    centre, measured to the nearest periodic image), 0 outside."""
+    w = _mhd_base("field_loop", 1, ny, nz, g, (0.0, 1.0), (-1.0, 1.0), (-0.5, 0.5), 5.0 / 3.0, False, 0.0,
+                  (BC_PERIODIC, BC_PERIODIC), (BC_PERIODIC, BC_PERIODIC))
+    st = w.state
+    nzt, nyt = w.nz_t, w.ny_t
+    st["rho"][:] = 1.0
+    st["e"][:] = 1.0 / (w.gamma - 1.0)
+    st["vy"][:] = vy
+    st["vz"][:] = vz
+
+    def ax(x, y, z):
+        yy = (y + 1.0) % 2.0 - 1.0
+        zz = (z + 0.5) % 1.0 - 0.5
+        r = np.sqrt(yy * yy + zz * zz)
+        return np.where(r < radius, a0 * (radius - r), 0.0)
+
+    zero = lambda x, y, z: 0.0 * (x + y + z)  # noqa: E731
+    bx, by, bz = curl_field(w, ax, zero, zero)
+    st["bx"][:] = bx
+    st["by"][:] = by
+    st["bz"][:] = bz
+    return w
+
+
+def magnetic_energy(w, st):
+    """Mean over the active cells of B^2, each component the zone-centred
+    two-point mean of its faces (the single value along an absent axis)."""
+    out = 0.0
+    for d, k in enumerate(MHD_FIELDS):
+        b = st[k]
+        gz, gy = w.gz, w.gy
+        lo = b[gz:gz + w.nz, gy:gy + w.ny, :]
+        if d == 0:
+            up = np.roll(lo, -1, axis=2)
+        elif d == 1 and w.ny > 1:
+            up = b[gz:gz + w.nz, gy + 1:gy + w.ny + 1, :]
+        elif d == 2 and w.nz > 1:
+            up = b[gz + 1:gz + w.nz + 1, gy:gy + w.ny, :]
+        else:
+            up = lo
+        out = out + (0.5 * (lo + up)) ** 2
+    return float(np.mean(out))
