@@ -1286,7 +1286,7 @@ static int enable_mhd_impl(fargo_ctx *c, Buffers<T> &b)
     const size_t n = (size_t)c->m.ntot * sizeof(T);
     int rc;
     void *p;
-    if (!b.tab.bfield[0])
+    if (!b.tab.bfield[0]) {
         for (int d = 0; d < 3; d++) {
             if ((rc = dalloc(c, &p, n))) return rc;
             b.tab.bfield[d] = (T *)p;
@@ -1295,6 +1295,15 @@ static int enable_mhd_impl(fargo_ctx *c, Buffers<T> &b)
             if ((rc = dalloc(c, &p, n))) return rc;
             b.vM[d] = (T *)p;
         }
+        // inverse centre-to-centre distances along Y and Z, (w[n-1] + w[n]) / 2
+        auto idc = [](const std::vector<double> &w) {
+            std::vector<double> o(w.size(), 0.0);
+            for (size_t q = 1; q < w.size(); q++) o[q] = 1.0 / (0.5 * (w[q - 1] + w[q]));
+            return o;
+        };
+        if ((rc = upload<T>(c, &b.tab.mh_idcy, idc(c->hg.dy)))) return rc;
+        if ((rc = upload<T>(c, &b.tab.mh_idcz, idc(c->hg.dz)))) return rc;
+    }
     if ((rc = vref_launch<T>(c, b, VREF_ABS, nullptr, c->stream))) return rc;
     c->m.mhd = 1;
     if ((rc = vref_refresh<T>(c, b, c->stream))) return rc;

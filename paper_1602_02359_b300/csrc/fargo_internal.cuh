@@ -82,8 +82,10 @@ struct Tab {
     T *vref, *dAy, *dAz;
     double *vrefd;
     // MHD: the face-centred field B_x, B_y, B_z (stored like v_x, v_y, v_z;
-    // null without a field)
+    // null without a field), and per Y index j / Z index k the inverse of
+    // the distance (dy[j-1] + dy[j]) / 2 between cell centres (0 at j = 0)
     T *bfield[3];
+    const T *mh_idcy, *mh_idcz;
 };
 
 // The magnetic field's three components (null: no field).

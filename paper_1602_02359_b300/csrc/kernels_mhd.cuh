@@ -31,13 +31,15 @@ namespace fk {
 __device__ __forceinline__ bool mh_has(const MeshD &m, int d) { return d == 0 ? m.hasX : (d == 1 ? m.hasY : m.hasZ); }
 __device__ __forceinline__ int mh_pos(int i, int j, int k, int d) { return d == 0 ? i : (d == 1 ? j : k); }
 
-// (i, j, k) moved by off cells along d (X periodic; no move along an absent
-// direction).
+// (i, j, k) moved by off cells along d, |off| <= 2 (X periodic; no move
+// along an absent direction).
 __device__ __forceinline__ void mh_shift(const MeshD &m, int &i, int &j, int &k, int d, int off)
 {
     if (d == 0) {
-        i = (i + off) % m.nx;
-        if (i < 0) i += m.nx;
+        if (m.hasX) {
+            i += off;
+            i = i < 0 ? i + m.nx : (i >= m.nx ? i - m.nx : i);
+        }
     } else if (d == 1) {
         if (m.hasY) j += off;
     } else if (m.hasZ) {
@@ -50,41 +52,68 @@ __device__ __forceinline__ idx_t mh_nb(const MeshD &m, int i, int j, int k, int 
     return IX(m, i, j, k);
 }
 
-// Width of cell n along d, and the distance between the centres of cells
-// n - 1 and n (X uniform).
+// Width of cell n along d, and the inverse of the distance between the
+// centres of cells n - 1 and n (X uniform).
 template <typename T>
 __device__ __forceinline__ T mh_width(const Tab<T> &tb, int d, int n)
 {
     return d == 0 ? tb.dx : (d == 1 ? tb.dy[n] : tb.dz[n]);
 }
 template <typename T>
-__device__ __forceinline__ T mh_dc(const Tab<T> &tb, int d, int n)
+__device__ __forceinline__ T mh_idc(const Tab<T> &tb, int d, int n)
 {
-    return d == 0 ? tb.dx : T(0.5) * (mh_width(tb, d, n - 1) + mh_width(tb, d, n));
+    return d == 0 ? tb.idx : (d == 1 ? tb.mh_idcy[n] : tb.mh_idcz[n]);
 }
 
-// Value at the face between cells n - 1 and n along e (cell (i, j, k) is n)
-// of a quantity q cell centred along e, carried at speed w over dt: the
-// upwind cell's value plus its van Leer slope times half the distance from
-// the face to the point that reaches it at dt/2 (the interface value of
-// Eq. 15), with w the flow speed (the upwind estimates "u") or an Alfven
-// characteristic speed (the foot values of Eqs. 41-44).
+// The reconstructions of one quantity q, cell centred along e, at the face
+// between cells n - 1 and n: the upwind cell's value plus its van Leer
+// slope times half the distance from the face to the point that reaches
+// it at dt/2 (the interface value of Eq. 15), for any speed w: the flow
+// speed (the upwind estimates "u" of Eq. 45) or an Alfven characteristic
+// speed (the foot values of Eqs. 41-44).  The two slopes are formed once
+// and serve every speed.  Along an absent direction the value is q itself.
 template <typename T>
-__device__ __forceinline__ T mh_recon(const MeshD &m, const Tab<T> &tb, const T *q, int i, int j, int k, int e, T w,
-                                      T dt)
+struct MhLine {
+    T qm, q0, sm, s0, wm, w0;   // cells n - 1 and n: values, slopes, widths
+    __device__ __forceinline__ T at(T w, T dt) const
+    {
+        return w >= T(0) ? qm + T(0.5) * sm * (wm - w * dt) : q0 - T(0.5) * s0 * (w0 + w * dt);
+    }
+};
+
+// Line of q along e at the face of cell (i, j, k) (cell n); with `up` the
+// face of the next cell along e as well (cells n .. n + 1), sharing the
+// slope of cell n.
+template <typename T>
+__device__ __forceinline__ void mh_lines(const MeshD &m, const Tab<T> &tb, const T *q, int i, int j, int k, int e,
+                                         MhLine<T> &L, MhLine<T> *up = nullptr)
 {
     const idx_t c = IX(m, i, j, k);
-    if (!mh_has(m, e)) return q[c];
-    const int n = e == 0 ? 2 : mh_pos(i, j, k, e);   // X is uniform: any index serves
-    if (w >= T(0)) {
-        const T qm1 = q[mh_nb(m, i, j, k, e, -1)];
-        const T sl = vl_slope(q[mh_nb(m, i, j, k, e, -2)], qm1, q[c], mh_dc(tb, e, n - 1), mh_dc(tb, e, n));
-        return qm1 + T(0.5) * sl * (mh_width(tb, e, n - 1) - w * dt);
+    if (!mh_has(m, e)) {
+        L = {q[c], q[c], T(0), T(0), T(0), T(0)};
+        if (up) *up = L;
+        return;
     }
-    const T q0 = q[c];
-    const T sl = vl_slope(q[mh_nb(m, i, j, k, e, -1)], q0, q[mh_nb(m, i, j, k, e, 1)], mh_dc(tb, e, n),
-                          mh_dc(tb, e, n + 1));
-    return q0 - T(0.5) * sl * (mh_width(tb, e, n) + w * dt);
+    const int n = mh_pos(i, j, k, e);
+    const T qm2 = q[mh_nb(m, i, j, k, e, -2)], qm1 = q[mh_nb(m, i, j, k, e, -1)], q0 = q[c],
+            qp1 = q[mh_nb(m, i, j, k, e, 1)];
+    const int nn = e == 0 ? 2 : n;   // X is uniform: any index serves
+    const T im1 = mh_idc(tb, e, nn - 1), i0 = mh_idc(tb, e, nn), ip1 = mh_idc(tb, e, nn + 1);
+    L.qm = qm1;
+    L.q0 = q0;
+    L.sm = vl_slope_i(qm2, qm1, q0, im1, i0);
+    L.s0 = vl_slope_i(qm1, q0, qp1, i0, ip1);
+    L.wm = mh_width(tb, e, nn - 1);
+    L.w0 = mh_width(tb, e, nn);
+    if (up) {
+        const T qp2 = q[mh_nb(m, i, j, k, e, 2)];
+        up->qm = q0;
+        up->q0 = qp1;
+        up->sm = L.s0;
+        up->s0 = vl_slope_i(q0, qp1, qp2, ip1, mh_idc(tb, e, nn + 2));
+        up->wm = L.w0;
+        up->w0 = mh_width(tb, e, nn + 1);
+    }
 }
 
 // Density at the edge at the lower a- and b-faces of cell (i, j, k): the
@@ -99,18 +128,16 @@ __device__ __forceinline__ T mh_rho_edge(const MeshD &m, const T *rho, int i, in
     return T(0.25) * (rho[c00] + rho[c10] + rho[c01] + rho[c11]);
 }
 
-// Star values at that edge of the pair (v_p, B_p) from the 1.5D problem
-// along q (Eqs. 41-44): psi+- = v_p +- B_p / sqrt(rho), carried at
-// C+- = U -+ W / sqrt(rho), taken at their feet.
+// Star values at an edge of the pair (v_p, B_p) from the 1.5D problem along
+// the lines' direction (Eqs. 41-44): psi+- = v_p +- B_p / sqrt(rho), carried
+// at C+- = U -+ W / sqrt(rho), taken at their feet.
 template <typename T>
-__device__ __forceinline__ void mh_star(const MeshD &m, const Tab<T> &tb, const T *v, const T *bf, int i, int j, int k,
-                                        int q, T U, T W, T rho, T dt, T &vs, T &bs)
+__device__ __forceinline__ void mh_star(const MhLine<T> &Lv, const MhLine<T> &Lb, T U, T W, T sq, T isq, T dt,
+                                        T &vs, T &bs)
 {
-    const T sq = sqrt(rho);
-    const T cp = U - W / sq, cm = U + W / sq;
-    const T vp = mh_recon(m, tb, v, i, j, k, q, cp, dt), bp = mh_recon(m, tb, bf, i, j, k, q, cp, dt);
-    const T vm = mh_recon(m, tb, v, i, j, k, q, cm, dt), bm = mh_recon(m, tb, bf, i, j, k, q, cm, dt);
-    vs = T(0.5) * (vp + vm + (bp - bm) / sq);
+    const T cp = U - W * isq, cm = U + W * isq;
+    const T vp = Lv.at(cp, dt), bp = Lb.at(cp, dt), vm = Lv.at(cm, dt), bm = Lb.at(cm, dt);
+    vs = T(0.5) * (vp + vm + (bp - bm) * isq);
     bs = T(0.5) * (bp + bm + sq * (vp - vm));
 }
 
@@ -128,18 +155,24 @@ __device__ __forceinline__ T mh_emf_edge(const MeshD &m, const Tab<T> &tb, const
     constexpr int a = (O + 1) % 3, b = (O + 2) % 3;
     const idx_t c00 = IX(m, i, j, k), ca = mh_nb(m, i, j, k, a, -1), cb = mh_nb(m, i, j, k, b, -1);
     const T r = mh_rho_edge(m, rho, i, j, k, a, b);
+    const T sq = sqrt(r), isq = div_fast(T(1), sq);
     const T ub = T(0.5) * (vb[c00] + vb[ca]);
     const T ua = T(0.5) * (va[c00] + va[cb]);
-    const T vau = mh_recon(m, tb, va, i, j, k, b, ub, dt), bau = mh_recon(m, tb, ba, i, j, k, b, ub, dt);
-    const T vbu = mh_recon(m, tb, vb, i, j, k, a, ua, dt), bbu = mh_recon(m, tb, bb, i, j, k, a, ua, dt);
+    MhLine<T> Lva, Lba, Lvb, Lbb;
+    mh_lines(m, tb, va, i, j, k, b, Lva);
+    mh_lines(m, tb, ba, i, j, k, b, Lba);
+    mh_lines(m, tb, vb, i, j, k, a, Lvb);
+    mh_lines(m, tb, bb, i, j, k, a, Lbb);
+    const T vau = Lva.at(ub, dt), bau = Lba.at(ub, dt);
+    const T vbu = Lvb.at(ua, dt), bbu = Lbb.at(ua, dt);
     T vas, bas, vbs, bbs;
-    mh_star(m, tb, va, ba, i, j, k, b, vbu, bbu, r, dt, vas, bas);
-    mh_star(m, tb, vb, bb, i, j, k, a, vau, bau, r, dt, vbs, bbs);
+    mh_star(Lva, Lba, vbu, bbu, sq, isq, dt, vas, bas);
+    mh_star(Lvb, Lbb, vau, bau, sq, isq, dt, vbs, bbs);
     T e = T(0.5) * (vas * bbu + bbs * vau - vbs * bau - bas * vbu);
     if (m.eta > 0.0) {
         T cur = T(0);
-        if (mh_has(m, a)) cur += (bb[c00] - bb[ca]) / mh_dc(tb, a, a == 0 ? 1 : mh_pos(i, j, k, a));
-        if (mh_has(m, b)) cur -= (ba[c00] - ba[cb]) / mh_dc(tb, b, b == 0 ? 1 : mh_pos(i, j, k, b));
+        if (mh_has(m, a)) cur += (bb[c00] - bb[ca]) * mh_idc(tb, a, a == 0 ? 1 : mh_pos(i, j, k, a));
+        if (mh_has(m, b)) cur -= (ba[c00] - ba[cb]) * mh_idc(tb, b, b == 0 ? 1 : mh_pos(i, j, k, b));
         e -= (T)m.eta * cur;
     }
     return e;
@@ -204,24 +237,36 @@ __global__ void __launch_bounds__(256) k_mhd_pressure(MeshD m, Tab<T> tb, Fld<T>
         const idx_t c = IX(m, i, j, k), cm = mh_nb(m, i, j, k, a, -1);
         int ia = i, ja = j, ka = k;
         mh_shift(m, ia, ja, ka, a, -1);
-        const T g = (mh_pmag(m, tb, i, j, k, a) - mh_pmag(m, tb, ia, ja, ka, a)) /
-                    mh_dc(tb, a, a == 0 ? 1 : mh_pos(i, j, k, a));
+        const T g = (mh_pmag(m, tb, i, j, k, a) - mh_pmag(m, tb, ia, ja, ka, a)) *
+                    mh_idc(tb, a, a == 0 ? 1 : mh_pos(i, j, k, a));
         V[a][c] = V[a][c] - dt * T(2) * g / (f.rho[c] + f.rho[cm]);
     }
 }
 
-// B_a* at the edge of cell (i, j, k) at its lower a- and b-faces, from the
-// problem along b with no flow speed and W the mean of the edge's two
-// b-faces (Eq. 47).
+// B_a* at the edges of cell (i, j, k) and of the next cell along b, at
+// their lower a- and b-faces, from the problem along b with no flow speed
+// and W the mean of each edge's two b-faces (Eq. 47).
 template <typename T>
-__device__ __forceinline__ T mh_tension_star(const MeshD &m, const Tab<T> &tb, const T *va, const T *ba, const T *bb,
-                                             const T *rho, int i, int j, int k, int a, int b, T dt)
+__device__ __forceinline__ void mh_tension_stars(const MeshD &m, const Tab<T> &tb, const T *va, const T *ba,
+                                                 const T *bb, const T *rho, int i, int j, int k, int a, int b, T dt,
+                                                 T &lo, T &hi)
 {
-    const T r = mh_rho_edge(m, rho, i, j, k, a, b);
-    const T W = T(0.5) * (bb[IX(m, i, j, k)] + bb[mh_nb(m, i, j, k, a, -1)]);
-    T vs, bs;
-    mh_star(m, tb, va, ba, i, j, k, b, T(0), W, r, dt, vs, bs);
-    return bs;
+    MhLine<T> Lv, Lb, Lv1, Lb1;
+    mh_lines(m, tb, va, i, j, k, b, Lv, &Lv1);
+    mh_lines(m, tb, ba, i, j, k, b, Lb, &Lb1);
+    int ib = i, jb = j, kb = k;
+    mh_shift(m, ib, jb, kb, b, 1);
+    T vs;
+    {
+        const T r = mh_rho_edge(m, rho, i, j, k, a, b), sq = sqrt(r);
+        const T W = T(0.5) * (bb[IX(m, i, j, k)] + bb[mh_nb(m, i, j, k, a, -1)]);
+        mh_star(Lv, Lb, T(0), W, sq, div_fast(T(1), sq), dt, vs, lo);
+    }
+    {
+        const T r = mh_rho_edge(m, rho, ib, jb, kb, a, b), sq = sqrt(r);
+        const T W = T(0.5) * (bb[IX(m, ib, jb, kb)] + bb[mh_nb(m, ib, jb, kb, a, -1)]);
+        mh_star(Lv1, Lb1, T(0), W, sq, div_fast(T(1), sq), dt, vs, hi);
+    }
 }
 
 template <typename T>
@@ -246,10 +291,8 @@ __global__ void __launch_bounds__(256) k_mhd_tension(MeshD m, Tab<T> tb, Fld<T> 
                 if (b == a || !mh_has(m, b)) continue;
                 const T *bb = tb.bfield[b];
                 const T bbar = T(0.25) * (bb[c] + bb[mh_nb(m, i, j, k, b, 1)] + bb[cm] + bb[mh_nb(m, ia, ja, ka, b, 1)]);
-                int ib = i, jb = j, kb = k;
-                mh_shift(m, ib, jb, kb, b, 1);
-                const T up = mh_tension_star(m, tb, V[a], tb.bfield[a], bb, f.rho, ib, jb, kb, a, b, dt);
-                const T lo = mh_tension_star(m, tb, V[a], tb.bfield[a], bb, f.rho, i, j, k, a, b, dt);
+                T lo, up;
+                mh_tension_stars(m, tb, V[a], tb.bfield[a], bb, f.rho, i, j, k, a, b, dt, lo, up);
                 fa += bbar * (up - lo) / mh_width(tb, b, mh_pos(i, j, k, b));
             }
             v = v + dt * T(2) / (f.rho[c] + f.rho[cm]) * fa;
