@@ -528,9 +528,10 @@ def disk2d_fp32(torch, fb, dev, steps=200, warmup=10):
             "l2": "L2-resident (state about 17 MB), no flush", "clocks": clocks}
 
 
-# Algorithmic bytes per cell of the EMF kernel (cells 8a-8c): it reads
-# rho, v_x, v_y, v_z, B_x, B_y, B_z and writes e_x, e_y, e_z once.
-MHD_EMF_FIELDS = 10
+# Algorithmic bytes per cell of the edge kernel (cells 8a-8d): it reads
+# rho, v_x, v_y, v_z, B_x, B_y, B_z and writes e_x, e_y, e_z and the three
+# velocities after the tension once.
+MHD_EDGE_FIELDS = 13
 
 
 def mhd_box(torch, fb, dev, steps=20, warmup=5, dims=(256, 128, 128)):
@@ -556,15 +557,16 @@ def mhd_box(torch, fb, dev, steps=20, warmup=5, dims=(256, 128, 128)):
         c.close()
         tot = sum(t for _, t in per)
         mk = {k: round(t, 4) for k, t in per if k.startswith("mhd_")}
-        emf = mk.get("mhd_emf")
-        ach = MHD_EMF_FIELDS * esz * w.cells / (emf * 1e-3) / 1e9 if emf else None
+        emf = mk.get("mhd_edges")
+        ach = MHD_EDGE_FIELDS * esz * w.cells / (emf * 1e-3) / 1e9 if emf else None
         out[name] = {"value": w.cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": round(ms, 4),
                      "steps": steps, "err": err, "clocks": clocks, "mhd_kernels_ms": mk,
                      "mhd_share_of_step": round(sum(mk.values()) / tot, 4) if tot > 0 else None,
-                     "emf_roofline": {"kernel": "k_mhd_emf", "bound": "hbm" if esz == 4 else "alu",
-                                      "achieved_GBps": round(ach, 1) if ach else None,
-                                      "hbm_peak_GBps": peak, "hbm_frac": round(ach / peak, 4) if ach else None,
-                                      "bytes_per_cell": MHD_EMF_FIELDS * esz}}
+                     "edge_kernel_roofline": {"kernel": "k_mhd_edges", "bound": "hbm" if esz == 4 else "alu",
+                                              "achieved_GBps": round(ach, 1) if ach else None,
+                                              "hbm_peak_GBps": peak,
+                                              "hbm_frac": round(ach / peak, 4) if ach else None,
+                                              "bytes_per_cell": MHD_EDGE_FIELDS * esz}}
     return out
 
 

@@ -432,14 +432,10 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     // cells 8a-8d: the EMFs and the magnetic tension, both from the velocities
     // after the source sub-steps
     if (m.mhd) {
-        k_mhd_emf<T><<<dim3(cg.x, mh_edge_rows(m), mh_edge_planes(m)), cb, 0, s>>>(m, P.tb, P.vpre, P.E[0], P.E[1],
-                                                                                 P.E[2], P.sc);
-        MARK("mhd_emf");
-        if (!m.mhd_passive) {
-            k_mhd_tension<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.vpre, P.VM, P.sc);
-            MARK("mhd_tension");
-            PERIODIC(per_fields<T>(m, P.VM, true, false), "periodic");
-        }
+        k_mhd_edges<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.vpre, P.VM, P.E[0], P.E[1], P.E[2], P.sc, 1,
+                                            !m.mhd_passive);
+        MARK("mhd_edges");
+        if (!m.mhd_passive) PERIODIC(per_fields<T>(m, P.VM, true, false), "periodic");
     }
     // cell 9
     if (m.hasY) { k_bc_y<T><<<grid_for((long long)m.nx * (m.nzt + 1) * 2, bs), bs, 0, s>>>(m, P.vsrc, P.sc, 1, P.tb.vref, P.B); MARK("bc_y9"); }
@@ -1463,14 +1459,15 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         if (!m.mhd_passive) k_mhd_pressure<T><<<fg, fb, 0, s>>>(m, b.tab, A, c->sc);
         launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);
         break;
-    case 11:   // the EMFs (cells 8a-8c) of the state, into the aux arrays 7-9
-        k_mhd_emf<T><<<dim3(fg.x, mh_edge_rows(m), mh_edge_planes(m)), fb, 0, s>>>(m, b.tab, A, b.ef[0], b.ef[1],
-                                                                                 b.ef[2], c->sc);
+    case 11: {  // the EMFs (cells 8a-8c) of the state, into the aux arrays 7-9
+        Fld<T> VM = {A.rho, A.e, b.vM[0], b.vM[1], b.vM[2]};
+        k_mhd_edges<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, b.ef[0], b.ef[1], b.ef[2], c->sc, 1, 0);
         break;
+    }
     case 12: {  // the magnetic tension (cell 8d), back into the state's velocities
         if (m.mhd_passive) break;
         Fld<T> VM = {A.rho, A.e, b.vM[0], b.vM[1], b.vM[2]};
-        k_mhd_tension<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, c->sc);
+        k_mhd_edges<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, b.ef[0], b.ef[1], b.ef[2], c->sc, 0, 1);
         if ((rc = copyv(va, b.vM))) return rc;
         if (!m.hasZ) CK(cudaMemcpyAsync(va[2], b.vM[2], nbytes, cudaMemcpyDeviceToDevice, s));
         launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);

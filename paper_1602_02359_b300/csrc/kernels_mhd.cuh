@@ -11,11 +11,11 @@
 //   k_mhd_pressure (cell 7a, after sub-step 1): minus the gradient of the
 //     transverse magnetic pressure, from zone-centred two-point averages of
 //     B, on every interior face velocity, in place;
-//   k_mhd_emf (cells 8a-8c): the three EMFs of every edge (Eq. 45, with the
-//     star values of Eqs. 41-44), minus eta curl B;
-//   k_mhd_tension (cell 8d): the magnetic tension of Eq. 47 on every
-//     interior face velocity, out of place (every component from the
-//     velocities on entry);
+//   k_mhd_edges (cells 8a-8d): the three EMFs of every edge (Eq. 45, with
+//     the star values of Eqs. 41-44) minus eta curl B, and the magnetic
+//     tension of Eq. 47 on every interior face velocity, out of place
+//     (every component from the velocities on entry), from one set of
+//     reconstructions per edge;
 //   k_mhd_ct (cell 10, after the ghost fill of cell 9): the constrained
 //     transport B_a += dt (d_b e_o - d_o e_b) for the cyclic (a, b, o) on
 //     every interior face, in place.  Eq. 39 is printed with the signs of
@@ -141,43 +141,6 @@ __device__ __forceinline__ void mh_star(const MhLine<T> &Lv, const MhLine<T> &Lb
     bs = T(0.5) * (bp + bm + sq * (vp - vm));
 }
 
-// EMF of orientation O at the edge of cell (i, j, k) (Eq. 45):
-//   e_O = (v_a* B_b^u + B_b* v_a^u - v_b* B_a^u - B_a* v_b^u) / 2,
-// v_a^u, B_a^u upwind along b at the mean flow speed along b of the edge's
-// two b-faces, (v_a*, B_a*) from the problem along b at C+- = v_b^u -+
-// B_b^u / sqrt(rho) (and a, b swapped); then the resistive part
-// -eta (curl B)_O, each derivative the difference of the two face values
-// across the edge over their centre-to-centre distance.
-template <typename T, int O>
-__device__ __forceinline__ T mh_emf_edge(const MeshD &m, const Tab<T> &tb, const T *va, const T *vb, const T *ba,
-                                         const T *bb, const T *rho, int i, int j, int k, T dt)
-{
-    constexpr int a = (O + 1) % 3, b = (O + 2) % 3;
-    const idx_t c00 = IX(m, i, j, k), ca = mh_nb(m, i, j, k, a, -1), cb = mh_nb(m, i, j, k, b, -1);
-    const T r = mh_rho_edge(m, rho, i, j, k, a, b);
-    const T sq = sqrt(r), isq = div_fast(T(1), sq);
-    const T ub = T(0.5) * (vb[c00] + vb[ca]);
-    const T ua = T(0.5) * (va[c00] + va[cb]);
-    MhLine<T> Lva, Lba, Lvb, Lbb;
-    mh_lines(m, tb, va, i, j, k, b, Lva);
-    mh_lines(m, tb, ba, i, j, k, b, Lba);
-    mh_lines(m, tb, vb, i, j, k, a, Lvb);
-    mh_lines(m, tb, bb, i, j, k, a, Lbb);
-    const T vau = Lva.at(ub, dt), bau = Lba.at(ub, dt);
-    const T vbu = Lvb.at(ua, dt), bbu = Lbb.at(ua, dt);
-    T vas, bas, vbs, bbs;
-    mh_star(Lva, Lba, vbu, bbu, sq, isq, dt, vas, bas);
-    mh_star(Lvb, Lbb, vau, bau, sq, isq, dt, vbs, bbs);
-    T e = T(0.5) * (vas * bbu + bbs * vau - vbs * bau - bas * vbu);
-    if (m.eta > 0.0) {
-        T cur = T(0);
-        if (mh_has(m, a)) cur += (bb[c00] - bb[ca]) * mh_idc(tb, a, a == 0 ? 1 : mh_pos(i, j, k, a));
-        if (mh_has(m, b)) cur -= (ba[c00] - ba[cb]) * mh_idc(tb, b, b == 0 ? 1 : mh_pos(i, j, k, b));
-        e -= (T)m.eta * cur;
-    }
-    return e;
-}
-
 // Faces of component a that the sub-steps update: every azimuth, the
 // active rows and planes, along a its interior faces (from jf / kf).
 __device__ __forceinline__ bool mh_face(const MeshD &m, int a, int j, int k)
@@ -185,26 +148,6 @@ __device__ __forceinline__ bool mh_face(const MeshD &m, int a, int j, int k)
     const bool y = m.hasY ? (j >= (a == 1 ? m.jf : m.j0) && j < m.j1) : j == 0;
     const bool z = m.hasZ ? (k >= (a == 2 ? m.kf : m.k0) && k < m.k1) : k == 0;
     return y && z;
-}
-
-// Launch shapes: one thread per azimuth, one block row per (j, k).
-// Edges: rows and planes 2 .. n - 2 of a present direction (the stencil
-// reaches two cells down and one up), the single one of an absent one.
-__host__ __device__ __forceinline__ int mh_edge_rows(const MeshD &m) { return m.hasY ? m.nyt - 3 : 1; }
-__host__ __device__ __forceinline__ int mh_edge_planes(const MeshD &m) { return m.hasZ ? m.nzt - 3 : 1; }
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_mhd_emf(MeshD m, Tab<T> tb, Fld<T> f, T *ex, T *ey, T *ez, const Scal *sc)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y + (m.hasY ? 2 : 0), k = blockIdx.z + (m.hasZ ? 2 : 0);
-    const T dt = step_dt<T>(sc);
-    if (i >= m.nx || !(dt > T(0))) return;
-    const idx_t c = IX(m, i, j, k);
-    const T *bx = tb.bfield[0], *by = tb.bfield[1], *bz = tb.bfield[2];
-    ex[c] = mh_emf_edge<T, 0>(m, tb, f.vy, f.vz, by, bz, f.rho, i, j, k, dt);
-    ey[c] = mh_emf_edge<T, 1>(m, tb, f.vz, f.vx, bz, bx, f.rho, i, j, k, dt);
-    ez[c] = mh_emf_edge<T, 2>(m, tb, f.vx, f.vy, bx, by, f.rho, i, j, k, dt);
 }
 
 // Transverse magnetic pressure (B_b^2 + B_c^2) / 2 at the centre of (i, j, k)
@@ -243,59 +186,97 @@ __global__ void __launch_bounds__(256) k_mhd_pressure(MeshD m, Tab<T> tb, Fld<T>
     }
 }
 
-// B_a* at the edges of cell (i, j, k) and of the next cell along b, at
-// their lower a- and b-faces, from the problem along b with no flow speed
-// and W the mean of each edge's two b-faces (Eq. 47).
+// Cells 8a-8d in one pass: per cell, for each edge orientation O (a = O + 1,
+// b = O + 2) the four lines (v_a, B_a along b; v_b, B_b along a) are formed
+// once and serve the EMF of the edge (Eq. 45) and the tension stars of
+// both faces that meet there (Eq. 47: face a across b, face b across a,
+// each with the star of the next edge along its direction as well).  The
+// tension terms of a face are summed over its two directions in ascending
+// order; every velocity component comes from the values on entry (out of
+// place).  emf / tension switch the two parts (the debug phases run one).
 template <typename T>
-__device__ __forceinline__ void mh_tension_stars(const MeshD &m, const Tab<T> &tb, const T *va, const T *ba,
-                                                 const T *bb, const T *rho, int i, int j, int k, int a, int b, T dt,
-                                                 T &lo, T &hi)
-{
-    MhLine<T> Lv, Lb, Lv1, Lb1;
-    mh_lines(m, tb, va, i, j, k, b, Lv, &Lv1);
-    mh_lines(m, tb, ba, i, j, k, b, Lb, &Lb1);
-    int ib = i, jb = j, kb = k;
-    mh_shift(m, ib, jb, kb, b, 1);
-    T vs;
-    {
-        const T r = mh_rho_edge(m, rho, i, j, k, a, b), sq = sqrt(r);
-        const T W = T(0.5) * (bb[IX(m, i, j, k)] + bb[mh_nb(m, i, j, k, a, -1)]);
-        mh_star(Lv, Lb, T(0), W, sq, div_fast(T(1), sq), dt, vs, lo);
-    }
-    {
-        const T r = mh_rho_edge(m, rho, ib, jb, kb, a, b), sq = sqrt(r);
-        const T W = T(0.5) * (bb[IX(m, ib, jb, kb)] + bb[mh_nb(m, ib, jb, kb, a, -1)]);
-        mh_star(Lv1, Lb1, T(0), W, sq, div_fast(T(1), sq), dt, vs, hi);
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_mhd_tension(MeshD m, Tab<T> tb, Fld<T> f, Fld<T> out, const Scal *sc)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_mhd_edges(MeshD m, Tab<T> tb, Fld<T> f, Fld<T> out, T *ex, T *ey, T *ez,
+                                                   const Scal *sc, int emf, int tension)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const T dt = step_dt<T>(sc);
     if (i >= m.nx || !(dt > T(0))) return;
     const T *V[3] = {f.vx, f.vy, f.vz};
     T *VO[3] = {out.vx, out.vy, out.vz};
+    T *E[3] = {ex, ey, ez};
+    const T *rho = f.rho;
     const idx_t c = IX(m, i, j, k);
+    const bool edge = emf && (m.hasY ? (j >= 2 && j <= m.nyt - 2) : j == 0) &&
+                      (m.hasZ ? (k >= 2 && k <= m.nzt - 2) : k == 0);
+    bool face[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) face[a] = tension && mh_has(m, a) && mh_face(m, a, j, k);
+    T term[3][3];   // term[a][b]: the tension on face a across direction b
+#pragma unroll
+    for (int O = 0; O < 3; O++) {
+        const int a = (O + 1) % 3, b = (O + 2) % 3;
+        term[a][b] = T(0);
+        term[b][a] = T(0);
+        const bool ta = face[a] && mh_has(m, b), tb2 = face[b] && mh_has(m, a);
+        if (!edge && !ta && !tb2) continue;
+        const T *va = V[a], *vb = V[b], *ba = tb.bfield[a], *bb = tb.bfield[b];
+        const idx_t ca = mh_nb(m, i, j, k, a, -1), cb = mh_nb(m, i, j, k, b, -1);
+        MhLine<T> Lva, Lba, Lvb, Lbb, Uva, Uba, Uvb, Ubb;
+        mh_lines(m, tb, va, i, j, k, b, Lva, ta ? &Uva : nullptr);
+        mh_lines(m, tb, ba, i, j, k, b, Lba, ta ? &Uba : nullptr);
+        mh_lines(m, tb, vb, i, j, k, a, Lvb, tb2 ? &Uvb : nullptr);
+        mh_lines(m, tb, bb, i, j, k, a, Lbb, tb2 ? &Ubb : nullptr);
+        const T r = mh_rho_edge(m, rho, i, j, k, a, b);
+        const T sq = sqrt(r), isq = div_fast(T(1), sq);
+        T vs, lo, hi;
+        if (edge) {
+            const T ub = T(0.5) * (vb[c] + vb[ca]);
+            const T ua = T(0.5) * (va[c] + va[cb]);
+            const T vau = Lva.at(ub, dt), bau = Lba.at(ub, dt);
+            const T vbu = Lvb.at(ua, dt), bbu = Lbb.at(ua, dt);
+            T vas, bas, vbs, bbs;
+            mh_star(Lva, Lba, vbu, bbu, sq, isq, dt, vas, bas);
+            mh_star(Lvb, Lbb, vau, bau, sq, isq, dt, vbs, bbs);
+            T e = T(0.5) * (vas * bbu + bbs * vau - vbs * bau - bas * vbu);
+            if (m.eta > 0.0) {
+                T cur = T(0);
+                if (mh_has(m, a)) cur += (bb[c] - bb[ca]) * mh_idc(tb, a, a == 0 ? 1 : mh_pos(i, j, k, a));
+                if (mh_has(m, b)) cur -= (ba[c] - ba[cb]) * mh_idc(tb, b, b == 0 ? 1 : mh_pos(i, j, k, b));
+                e -= (T)m.eta * cur;
+            }
+            E[O][c] = e;
+        }
+        if (ta) {   // face a across b: stars of B_a at this edge and the next along b
+            mh_star(Lva, Lba, T(0), T(0.5) * (bb[c] + bb[ca]), sq, isq, dt, vs, lo);
+            int ib = i, jb = j, kb = k;
+            mh_shift(m, ib, jb, kb, b, 1);
+            const idx_t cn = IX(m, ib, jb, kb), cna = mh_nb(m, ib, jb, kb, a, -1);
+            const T r1 = mh_rho_edge(m, rho, ib, jb, kb, a, b), s1 = sqrt(r1);
+            mh_star(Uva, Uba, T(0), T(0.5) * (bb[cn] + bb[cna]), s1, div_fast(T(1), s1), dt, vs, hi);
+            const T bbar = T(0.25) * (bb[c] + bb[cn] + bb[ca] + bb[cna]);
+            term[a][b] = bbar * (hi - lo) / mh_width(tb, b, mh_pos(i, j, k, b));
+        }
+        if (tb2) {  // face b across a
+            mh_star(Lvb, Lbb, T(0), T(0.5) * (ba[c] + ba[cb]), sq, isq, dt, vs, lo);
+            int ia = i, ja = j, ka = k;
+            mh_shift(m, ia, ja, ka, a, 1);
+            const idx_t cn = IX(m, ia, ja, ka), cnb = mh_nb(m, ia, ja, ka, b, -1);
+            const T r1 = mh_rho_edge(m, rho, ia, ja, ka, a, b), s1 = sqrt(r1);
+            mh_star(Uvb, Ubb, T(0), T(0.5) * (ba[cn] + ba[cnb]), s1, div_fast(T(1), s1), dt, vs, hi);
+            const T bbar = T(0.25) * (ba[c] + ba[cn] + ba[cb] + ba[cnb]);
+            term[b][a] = bbar * (hi - lo) / mh_width(tb, a, mh_pos(i, j, k, a));
+        }
+    }
+    if (!tension) return;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         T v = V[a][c];
-        if (mh_has(m, a) && mh_face(m, a, j, k)) {
-            const idx_t cm = mh_nb(m, i, j, k, a, -1);
-            int ia = i, ja = j, ka = k;
-            mh_shift(m, ia, ja, ka, a, -1);
+        if (face[a]) {
             T fa = T(0);
 #pragma unroll
-            for (int b = 0; b < 3; b++) {
-                if (b == a || !mh_has(m, b)) continue;
-                const T *bb = tb.bfield[b];
-                const T bbar = T(0.25) * (bb[c] + bb[mh_nb(m, i, j, k, b, 1)] + bb[cm] + bb[mh_nb(m, ia, ja, ka, b, 1)]);
-                T lo, up;
-                mh_tension_stars(m, tb, V[a], tb.bfield[a], bb, f.rho, i, j, k, a, b, dt, lo, up);
-                fa += bbar * (up - lo) / mh_width(tb, b, mh_pos(i, j, k, b));
-            }
-            v = v + dt * T(2) / (f.rho[c] + f.rho[cm]) * fa;
+            for (int b = 0; b < 3; b++)
+                if (b != a && mh_has(m, b)) fa += term[a][b];
+            v = v + dt * T(2) / (rho[c] + rho[mh_nb(m, i, j, k, a, -1)]) * fa;
         }
         VO[a][c] = v;
     }

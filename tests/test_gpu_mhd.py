@@ -261,26 +261,42 @@ def test_mhd_rejected_where_it_does_not_apply():
 
 
 def test_field_loop_on_the_gpu_matches_the_oracle_and_the_paper():
-    """The loop test of Sec. 5.2 (128 x 64, Y-Z plane, periodic) to t = 2:
-    FP64 on the oracle's run (1e-11 on B) and both precisions on the
-    paper's magnetic energy 1.235e-7 within 1 % (tests/golden)."""
+    """The loop test of Sec. 5.2 (128 x 64, Y-Z plane, periodic).  FP64 on
+    the oracle's run for 100 steps (1e-12 on B and rho, measured 5e-14),
+    and both precisions to t = 2 on the paper's magnetic energy 1.235e-7
+    within 1 % (tests/golden) and on the oracle's (1e-6 in FP64, 5e-3 in
+    FP32).  Step-by-step parity is not carried to
+    t = 2: v_z stays near zero in this flow, and the upwind side of Eq. 45's
+    estimates along Z follows the sign of a v_z of order 1e-12, which
+    rounding flips; the flipped reconstructions then grow apart (1e-11
+    relative on rho by step 300).  The energy, an integral, does not."""
     import paper_1602_02359_b300 as fb
     from tests.test_oracle_pins import read_golden
     g = read_golden("field_loop_paper.txt")
     w = W.field_loop()
     o = oracle.Oracle(w)
     st = w.copy().state
-    o.run(st, 0.0, g["t"])
+    c = make_ctx(w)
+    t = 0.0
+    for _ in range(100):
+        dt_o = o.step(st, t)
+        dt_g = c.step()
+        assert abs(dt_g - dt_o) <= 1e-12 * dt_o
+        t += dt_o
+    r = worst(w, c.get_state(), st, ("rho",) + W.MHD_FIELDS)
+    c.close()
+    assert max(r.values()) <= 1e-12, r
+    o.run(st, t, g["t"])
     res = {}
     for prec, name in ((fb.F64, "f64"), (fb.F32, "f32")):
         c = make_ctx(w, prec, t_end=g["t"])
         c.run_to(g["t"])
         gs = {k: np.asarray(v, dtype=np.float64) for k, v in c.get_state().items()}
         res[name] = W.magnetic_energy(w, gs)
-        if prec == fb.F64:
-            r = worst(w, gs, st, W.MHD_FIELDS)
-            assert max(r.values()) <= 1e-11, r
         c.close()
-    record("field_loop_t2", oracle=W.magnetic_energy(w, st), **res)
+    e_o = W.magnetic_energy(w, st)
+    record("field_loop_t2", oracle=e_o, steps100_worst=max(r.values()), **res)
     for name, e in res.items():
         assert abs(e - g["magnetic_energy_t2"]) <= 0.01 * g["magnetic_energy_t2"], (name, e)
+    # measured: FP64 2e-10 and FP32 1.5e-3 of the oracle's energy
+    assert abs(res["f64"] - e_o) <= 1e-6 * e_o and abs(res["f32"] - e_o) <= 5e-3 * e_o, (res, e_o)
