@@ -318,15 +318,57 @@ static void fill_z(const mesh *m, double *a, int normal, int side, int bc, int j
     }
 }
 
+/* Ghosts of one magnetic-field component along one line across a Y or Z  */
+/* boundary (MHD; reading M11).  A wall's own face of the normal component */
+/* is never written: the constrained transport holds the flux through it   */
+/* (the EMFs tangential to a wall vanish on it).  Reflecting wall: every   */
+/* component mirrored evenly about the wall; zero gradient: the ghosts take */
+/* the wall face's value (normal) or the last active cell's (tangential);  */
+/* frozen: kept; periodic: the images one period away.                     */
+static void fill_b(double *a, size_t base, size_t stride, int lo, int hi, int g, int normal, int side, int bc)
+{
+    if (bc == OR_BC_FROZEN) return;
+    if (bc == OR_BC_PERIODIC) {
+        fill_periodic(a, base, stride, lo, hi, g, normal, side);
+        return;
+    }
+    for (int mm = 1; mm <= g; mm++) {
+        int dst, src;
+        if (normal) {   /* faces: the wall at lo (side 0) or hi (side 1) */
+            dst = side == 0 ? lo - mm : hi + mm;
+            src = bc == OR_BC_REFLECT ? (side == 0 ? lo + mm : hi - mm) : (side == 0 ? lo : hi);
+        } else {        /* cells: lo .. hi - 1 active */
+            dst = side == 0 ? lo - mm : hi - 1 + mm;
+            src = bc == OR_BC_REFLECT ? (side == 0 ? lo + mm - 1 : hi - mm) : (side == 0 ? lo : hi - 1);
+        }
+        a[base + (size_t)dst * stride] = a[base + (size_t)src * stride];
+    }
+}
+
 void or_bc_fill(const or_params *p, or_state *s)
 {
     mesh m;
     mesh_init(&m, p);
-    /* the magnetic field's components are filled as the velocity's (MHD),  */
-    /* but each of them is filled along every present axis: B_z, B_y stay   */
-    /* transverse fields of a mesh without Z or Y, where v_z, v_y are unused */
-    double *f[8] = { s->rho, p->iso ? NULL : s->e, s->vx, s->vy, s->vz,
-                     p->mhd ? s->bx : NULL, p->mhd ? s->by : NULL, p->mhd ? s->bz : NULL };
+    double *f[8] = { s->rho, p->iso ? NULL : s->e, s->vx, s->vy, s->vz, NULL, NULL, NULL };
+    /* the magnetic field (MHD): each component along every present axis    */
+    /* (B_z, B_y stay transverse fields of a mesh without Z or Y)           */
+    double *bf[3] = { p->mhd ? s->bx : NULL, p->mhd ? s->by : NULL, p->mhd ? s->bz : NULL };
+    if (m.hasY && bf[0]) {
+        int bcs[2] = { p->bc_ylo, p->bc_yhi };
+        for (int side = 0; side < 2; side++)
+            for (int d = 0; d < 3; d++)
+                for (int k = 0; k < (d == 2 ? m.nzt + 1 : m.nzt); k++)
+                    for (int i = 0; i < m.nx; i++)
+                        fill_b(bf[d], IDX(&m, i, 0, k), m.sj, m.j0, m.j1, m.p->g, d == 1, side, bcs[side]);
+    }
+    if (m.hasZ && bf[0]) {
+        int bcs[2] = { p->bc_zlo, p->bc_zhi };
+        for (int side = 0; side < 2; side++)
+            for (int d = 0; d < 3; d++)
+                for (int j = 0; j < (d == 1 ? m.nyt + 1 : m.nyt); j++)
+                    for (int i = 0; i < m.nx; i++)
+                        fill_b(bf[d], IDX(&m, i, j, 0), m.sk, m.k0, m.k1, m.p->g, d == 2, side, bcs[side]);
+    }
     if (m.hasY) {
         int bcs[2] = { p->bc_ylo, p->bc_yhi };
         for (int side = 0; side < 2; side++)
@@ -1743,6 +1785,28 @@ void or_mhd_emf(const or_params *p, const or_state *s, double dt, double *ex, do
                 for (int i = il; i < ih; i++)
                     E[o][IDX(&m, i, j, k)] = mh_emf_edge(&m, p, s, o, i, j, k, dt);
     }
+    /* Walls (every non-periodic Y or Z boundary; reading M11): the EMFs on  */
+    /* the edges that lie in a wall's plane vanish, the antisymmetric        */
+    /* condition on the tangential EMF, so that the flux through the wall   */
+    /* and the net flux out of every cell next to it are held.               */
+    if (m.hasY && !m.pery)
+        for (int w = 0; w < 2; w++) {
+            int j = w == 0 ? m.j0 : m.j1;
+            for (int k = 0; k < m.nzt + 1; k++)
+                for (int i = 0; i < m.nx; i++) {
+                    E[0][IDX(&m, i, j, k)] = 0.0;
+                    E[2][IDX(&m, i, j, k)] = 0.0;
+                }
+        }
+    if (m.hasZ && !m.perz)
+        for (int w = 0; w < 2; w++) {
+            int k = w == 0 ? m.k0 : m.k1;
+            for (int j = 0; j < m.nyt + 1; j++)
+                for (int i = 0; i < m.nx; i++) {
+                    E[0][IDX(&m, i, j, k)] = 0.0;
+                    E[1][IDX(&m, i, j, k)] = 0.0;
+                }
+        }
     mesh_free(&m);
 }
 

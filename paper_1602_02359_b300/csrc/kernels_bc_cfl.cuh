@@ -61,15 +61,43 @@ __device__ void fill_line(T *a, idx_t base, idx_t stride, int lo, int hi, int g,
     }
 }
 
+// Ghosts of one magnetic-field component (MHD) along one line across a Y
+// or Z boundary.  A wall's own face of the normal component is never
+// written: the constrained transport holds the flux through it (the EMFs
+// tangential to a wall vanish there).  Reflecting wall: every component
+// mirrored evenly about the wall; zero gradient: the ghosts take the wall
+// face's value (normal) or the last active cell's (tangential); frozen:
+// kept; periodic: the images one period away.
+template <typename T>
+__device__ void fill_bline(T *a, idx_t base, idx_t stride, int lo, int hi, int g, int normal, int side, int bc)
+{
+    if (bc == BC_FROZEN) return;
+    if (bc == BC_PERIODIC) {
+        fill_line(a, base, stride, lo, hi, g, normal, side, bc);
+        return;
+    }
+    for (int mm = 1; mm <= g; mm++) {
+        int dst, src;
+        if (normal) {
+            dst = side == 0 ? lo - mm : hi + mm;
+            src = bc == BC_REFLECT ? (side == 0 ? lo + mm : hi - mm) : (side == 0 ? lo : hi);
+        } else {
+            dst = side == 0 ? lo - mm : hi - 1 + mm;
+            src = bc == BC_REFLECT ? (side == 0 ? lo + mm - 1 : hi - mm) : (side == 0 ? lo : hi - 1);
+        }
+        a[base + dst * stride] = a[base + src * stride];
+    }
+}
+
 __device__ __forceinline__ bool bc_skip(const Scal *sc, int mode)
 {
     if (mode == 0) return sc->err != 0 || (!sc->fixed && sc->t >= sc->t_end);
     return !(sc->dt > 0.0);
 }
 
-// The magnetic field (MagF, MHD) is filled like the velocity, component d
-// like v_d, but along every present axis: B_z, B_y stay transverse fields
-// of a mesh without Z or Y, where v_z, v_y are unused.
+// The magnetic field (MagF, MHD) is filled by fill_bline, component d
+// staggered like v_d, along every present axis: B_z, B_y stay transverse
+// fields of a mesh without Z or Y, where v_z, v_y are unused.
 template <typename T>
 __device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const Scal *sc, int mode, long long tid,
                                           const T *vref = nullptr, MagF<T> mb = MagF<T>{})
@@ -93,7 +121,7 @@ __device__ __forceinline__ void bc_y_body(const MeshD &m, const Fld<T> &f, const
     if (mb.b[0])
         for (int d = 0; d < 3; d++) {
             if (k >= (d == 2 ? m.nzt + 1 : m.nzt)) continue;
-            fill_line(mb.b[d], k * m.sk + i, m.sj, m.j0, m.j1, m.g, d == 1, side, bc);
+            fill_bline(mb.b[d], k * m.sk + i, m.sj, m.j0, m.j1, m.g, d == 1, side, bc);
         }
 }
 
@@ -120,7 +148,7 @@ __device__ __forceinline__ void bc_z_body(const MeshD &m, const Fld<T> &f, const
     if (mb.b[0])
         for (int d = 0; d < 3; d++) {
             if (j >= (d == 1 ? m.nyt + 1 : m.nyt)) continue;
-            fill_line(mb.b[d], j * m.sj + i, m.sk, m.k0, m.k1, m.g, d == 2, side, bc);
+            fill_bline(mb.b[d], j * m.sj + i, m.sk, m.k0, m.k1, m.g, d == 2, side, bc);
         }
 }
 

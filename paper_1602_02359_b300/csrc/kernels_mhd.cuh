@@ -244,7 +244,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_mhd_edges(MeshD
                 if (mh_has(m, b)) cur -= (ba[c] - ba[cb]) * mh_idc(tb, b, b == 0 ? 1 : mh_pos(i, j, k, b));
                 e -= (T)m.eta * cur;
             }
-            E[O][c] = e;
+            // on the edges in a wall's plane (a non-periodic Y or Z boundary)
+            // the EMF vanishes: the flux through the wall and the net flux out
+            // of every cell next to it are held
+            const bool wy = O != 1 && m.hasY && !m.pery && (j == m.j0 || j == m.j1);
+            const bool wz = O != 2 && m.hasZ && !m.perz && (k == m.k0 || k == m.k1);
+            E[O][c] = wy || wz ? T(0) : e;
         }
         if (ta) {   // face a across b: stars of B_a at this edge and the next along b
             mh_star(Lva, Lba, T(0), T(0.5) * (bb[c] + bb[ca]), sq, isq, dt, vs, lo);

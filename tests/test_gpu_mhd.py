@@ -56,6 +56,8 @@ def boxes():
         ("yz", W.random_mhd_box(1, 24, 20, seed=3, eta=0.02)),
         ("xyz", W.random_mhd_box(300, 10, 6, seed=4, eta=0.01)),
         ("xyz-iso", W.random_mhd_box(40, 12, 8, seed=5, iso=True, eta=0.0, nu=1e-3)),
+        ("xyz-reflect", W.random_mhd_box(300, 10, 6, seed=6, eta=0.01, bc=W.BC_REFLECT)),
+        ("xy-zerograd", W.random_mhd_box(300, 20, 1, seed=7, eta=0.01, bc=W.BC_ZEROGRAD)),
     ]
 
 
@@ -300,3 +302,34 @@ def test_field_loop_on_the_gpu_matches_the_oracle_and_the_paper():
         assert abs(e - g["magnetic_energy_t2"]) <= 0.01 * g["magnetic_energy_t2"], (name, e)
     # measured: FP64 2e-10 and FP32 1.5e-3 of the oracle's energy
     assert abs(res["f64"] - e_o) <= 1e-6 * e_o and abs(res["f32"] - e_o) <= 5e-3 * e_o, (res, e_o)
+
+
+@pytest.mark.parametrize("name,w,steps", [
+    ("orszag_tang_yz", W.orszag_tang(64), 40),
+    ("orszag_tang_xy", W.orszag_tang(64, plane="xy"), 40),
+    ("brio_wu", W.brio_wu(400), 60),
+    ("rotor", W.mhd_rotor(64), 30),
+    ("current_sheet_2d", W.current_sheet_2d(64), 30),
+])
+def test_papers_mhd_setups_match_oracle(name, w, steps):
+    """The MHD tests of Sec. 5.2 at reduced resolution (Orszag-Tang in the
+    printed Y-Z plane and laid in X-Y, Brio-Wu with reflecting walls, the
+    rotor with reflecting walls, the 2D current sheet): FP64 steps on the
+    oracle's (1e-11), and the divergence at round-off."""
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    c = fresh(w)
+    t = 0.0
+    for n in range(steps):
+        dt_o = o.step(st, t)
+        dt_g = c.step()
+        assert abs(dt_g - dt_o) <= 1e-12 * dt_o, (n, dt_g, dt_o)
+        t += dt_o
+    g = c.get_state()
+    r = worst(w, g, st, GAS + W.MHD_FIELDS)
+    bmax = max(np.abs(st[k]).max() for k in W.MHD_FIELDS)
+    d = float(np.abs(o.mhd_divb({k: np.asarray(v, dtype=np.float64) for k, v in g.items()})).max())
+    record(f"mhd_setup_{name}", steps=steps, divb=d, **r)
+    assert max(r.values()) <= 1e-11, r
+    assert d <= 1e-13 * bmax
+    c.close()

@@ -38,9 +38,14 @@ def test_divergence_stays_at_round_off():
     """Eq. 39: every edge's EMF enters the six face fluxes of a cell twice
     with opposite signs, so the net flux out of each cell stays at its
     initial round-off, whatever the EMFs are (here: compressive random
-    flows, magnetic forces and resistivity over ten steps)."""
-    for dims, eta in (((8, 6, 4), 0.02), ((16, 12, 1), 0.0), ((12, 1, 10), 0.01)):
-        w = W.random_mhd_box(*dims, seed=3, eta=eta)
+    flows, magnetic forces and resistivity over ten steps), in periodic
+    boxes and, with the wall condition of reading M11 (no tangential EMF on
+    a wall), in boxes with reflecting, zero-gradient and frozen walls."""
+    for dims, eta, bc in (((8, 6, 4), 0.02, W.BC_PERIODIC), ((16, 12, 1), 0.0, W.BC_PERIODIC),
+                          ((12, 1, 10), 0.01, W.BC_PERIODIC), ((8, 6, 4), 0.02, W.BC_REFLECT),
+                          ((16, 12, 1), 0.01, W.BC_ZEROGRAD), ((12, 1, 10), 0.0, W.BC_REFLECT),
+                          ((8, 6, 4), 0.0, W.BC_FROZEN)):
+        w = W.random_mhd_box(*dims, seed=3, eta=eta, bc=bc)
         o = oracle.Oracle(w)
         st = w.copy().state
         b0 = {k: st[k].copy() for k in W.MHD_FIELDS}

@@ -642,15 +642,15 @@ def curl_field(w, ax, ay, az):
 
 
 def random_mhd_box(nx, ny, nz, g=3, seed=0, iso=False, b0=(0.6, 0.3, 0.2), amp=0.3, eta=0.0, passive=False,
-                   nu=0.0):
-    """A periodic Cartesian box (X, Y, Z all periodic) with a smooth random
-    state and a divergence-free random field: uniform b0 plus the curl of a
-    potential of a few integer Fourier modes of the box, evaluated at the
-    ghosts' positions too (their images one period away)."""
+                   nu=0.0, bc=BC_PERIODIC):
+    """A Cartesian box (X periodic; Y and Z periodic, or walls of type bc)
+    with a smooth random state and a divergence-free random field: uniform
+    b0 plus the curl of a potential of a few integer Fourier modes of the
+    box, evaluated at the ghosts' positions too."""
     rng = np.random.Generator(np.random.PCG64(seed))
     L = (1.0, ny / nx if ny > 1 else 1.0, nz / nx if nz > 1 else 1.0)
     w = _mhd_base("mhd_box", nx, ny, nz, g, (0.0, L[0]), (0.0, L[1]), (0.0, L[2]), 5.0 / 3.0, iso, 0.8,
-                  (BC_PERIODIC, BC_PERIODIC), (BC_PERIODIC, BC_PERIODIC), eta=eta, passive=passive)
+                  (bc, bc), (bc, bc), eta=eta, passive=passive)
     if nu > 0:
         w.nu = np.full((w.nz_t, w.ny_t), nu)
     xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
@@ -856,3 +856,104 @@ def magnetic_energy(w, st):
             up = lo
         out = out + (0.5 * (lo + up)) ** 2
     return float(np.mean(out))
+
+
+def _yz_box(name, ny, nz, yr, zr, gamma, bc, g=3, cfl=0.44):
+    """A Y-Z plane (one cell in X) Cartesian MHD box with the boundary
+    condition bc on both axes."""
+    return _mhd_base(name, 1, ny, nz, g, (0.0, 1.0), yr, zr, gamma, False, 0.0, (bc, bc), (bc, bc), cfl=cfl)
+
+
+def orszag_tang(n=128, plane="yz", g=3):
+    """The Orszag-Tang vortex (Sec. 5.2): the unit square, periodic,
+    gamma = 5/3, rho = 25/(36 pi), P = 5/(12 pi), v = (-sin 2 pi z,
+    sin 2 pi y), B = B0 (-sin 2 pi z, sin 4 pi y), B0 = (4 pi)^-1/2, in the
+    Y-Z plane as printed; plane="xy" lays the same problem in the X-Y plane
+    (y -> x, z -> y), where the azimuthal lanes of the kernels are filled."""
+    b0 = 1.0 / math.sqrt(4.0 * math.pi)
+    if plane == "yz":
+        w = _yz_box("orszag_tang", n, n, (0.0, 1.0), (0.0, 1.0), 5.0 / 3.0, BC_PERIODIC, g)
+        xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+        st = w.state
+        nzt, nyt = w.nz_t, w.ny_t
+        st["vy"][:nzt, :nyt + 1] = -np.sin(2 * math.pi * zc)[:, None, None]
+        st["vz"][:nzt + 1, :nyt] = np.sin(2 * math.pi * yc)[None, :, None]
+        st["by"][:nzt, :nyt + 1] = -b0 * np.sin(2 * math.pi * zc)[:, None, None]
+        st["bz"][:nzt + 1, :nyt] = b0 * np.sin(4 * math.pi * yc)[None, :, None]
+    else:
+        w = _mhd_base("orszag_tang_xy", n, n, 1, g, (0.0, 1.0), (0.0, 1.0), (0.0, 1.0), 5.0 / 3.0, False, 0.0,
+                      (BC_PERIODIC, BC_PERIODIC), (BC_ZEROGRAD, BC_ZEROGRAD))
+        xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+        st = w.state
+        nzt, nyt = w.nz_t, w.ny_t
+        st["vx"][:nzt, :nyt] = -np.sin(2 * math.pi * yc)[None, :, None]
+        st["vy"][:nzt, :nyt + 1] = np.sin(2 * math.pi * xc)[None, None, :]
+        st["bx"][:nzt, :nyt] = -b0 * np.sin(2 * math.pi * yc)[None, :, None]
+        st["by"][:nzt, :nyt + 1] = b0 * np.sin(4 * math.pi * xc)[None, None, :]
+    st["rho"][:] = 25.0 / (36.0 * math.pi)
+    st["e"][:] = 5.0 / (12.0 * math.pi) / (w.gamma - 1.0)
+    return w
+
+
+def brio_wu(nz=800, g=3):
+    """The MHD Riemann problem of Brio & Wu (Sec. 5.2) along Z: z in
+    [0, 800], the discontinuity at 400, rho = 1 / 0.1, P = 1 / 0.1,
+    B_z = 0.75, B_y = 1 / -1, gamma = 2, reflecting walls, shown at t = 80.
+    The paper runs it as a 1.5D problem; here Y holds four periodic cells
+    so that v_y and B_y, the transverse pair, are dynamical (an axis of a
+    single cell is absent in this implementation)."""
+    w = _mhd_base("brio_wu", 1, 4, nz, g, (0.0, 1.0), (0.0, 4.0), (0.0, 800.0), 2.0, False, 0.0,
+                  (BC_PERIODIC, BC_PERIODIC), (BC_REFLECT, BC_REFLECT), t_end=80.0)
+    zc = centres(w.zf)[:w.nz_t]
+    left = (zc < 400.0)[:, None, None]
+    st = w.state
+    st["rho"][:w.nz_t] = np.where(left, 1.0, 0.1)
+    st["e"][:w.nz_t] = np.where(left, 1.0, 0.1) / (w.gamma - 1.0)
+    st["by"][:w.nz_t] = np.where(left, 1.0, -1.0)
+    st["bz"][:] = 0.75
+    return w
+
+
+def mhd_rotor(n=128, g=3):
+    """The MHD rotor (Sec. 5.2), Cartesian, in the Y-Z plane: the unit box
+    centred on 0, reflecting walls, gamma = 1.4, P = 1, B_y = 5/sqrt(4 pi);
+    rho = 10 and a solid rotation of angular speed v0/r1 (v0 = 2) for
+    r0 <= r <= r1, with a linear taper to the background (rho = 1, at rest)
+    over r1 < r < r2, and the inner hole r < r0 at rest with rho = 1
+    (r0 = 0.05, r1 = 0.1, r2 = 0.115; r from the box centre)."""
+    w = _yz_box("mhd_rotor", n, n, (-0.5, 0.5), (-0.5, 0.5), 1.4, BC_REFLECT, g)
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+    r0, r1, r2, v0 = 0.05, 0.1, 0.115, 2.0
+
+    def prof(y, z):
+        r = np.sqrt(y * y + z * z)
+        f = np.clip((r2 - r) / (r2 - r1), 0.0, 1.0)
+        rho = np.where(r < r0, 1.0, np.where(r <= r1, 10.0, 1.0 + 9.0 * f))
+        s = np.where(r < r0, 0.0, np.where(r <= r1, 1.0, f))
+        return rho, s
+
+    st = w.state
+    rho, _ = prof(yc[None, :], zc[:, None])
+    st["rho"][:w.nz_t, :w.ny_t, 0] = rho
+    _, s = prof(yfa[None, :], zc[:, None])
+    st["vy"][:w.nz_t, :w.ny_t + 1, 0] = -s * v0 * zc[:, None] / r1
+    _, s = prof(yc[None, :], zfa[:, None])
+    st["vz"][:w.nz_t + 1, :w.ny_t, 0] = s * v0 * yc[None, :] / r1
+    st["e"][:] = 1.0 / (w.gamma - 1.0)
+    st["by"][:] = 5.0 / math.sqrt(4.0 * math.pi)
+    return w
+
+
+def current_sheet_2d(n=256, v0=0.1, g=3):
+    """The current sheet of Sec. 5.2 (after Gardiner & Stone): (y, z) in
+    [0, 2]^2, periodic, rho = 1, P = 0.1, gamma = 5/3, B_z = 1 where
+    |y - 1| < 0.5 and -1 elsewhere, v_y = v0 sin(pi z), no physical
+    resistivity."""
+    w = _yz_box("current_sheet_2d", n, n, (0.0, 2.0), (0.0, 2.0), 5.0 / 3.0, BC_PERIODIC, g)
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+    st = w.state
+    st["rho"][:] = 1.0
+    st["e"][:] = 0.1 / (w.gamma - 1.0)
+    st["bz"][:, :w.ny_t, 0] = np.where(np.abs(yc - 1.0) < 0.5, 1.0, -1.0)[None, :]
+    st["vy"][:w.nz_t, :, 0] = (v0 * np.sin(math.pi * zc))[:, None]
+    return w
