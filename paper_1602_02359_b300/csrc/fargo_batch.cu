@@ -183,11 +183,13 @@ struct BOrbOp {
         RingMeta<T> &e = meta[it];
         e.id = group_member(g, item, e.local);
         const StepPlan<T> &p = P[e.id];
-        if (!(step_dt<T>(p.sc) > T(0))) {
+        const T dt = step_dt<T>(p.sc);
+        if (!(dt > T(0))) {
             e.N = -1;
             return;
         }
         orb_prepare(p.m, p.tb, p.v0, p.sc, e.local, e.N, e.a, e.b);
+        orb_ring_consts(p.m, p.tb, dt, e.local, e);
     }
     __device__ void issue(int it, T *dst, uint64_t *bar)
     {
@@ -201,7 +203,7 @@ struct BOrbOp {
         if (e.N < 0) return;
         const StepPlan<T> &p = P[e.id];
         if constexpr (orb_uses_lanes<C>())
-            orb_compute_w<T, C>(p.m, p.tb, p.qfin, e.local, src, e.N, e.a, e.b, step_dt<T>(p.sc));
+            orb_compute_w<T, C>(p.qfin, p.m.nx, ring_row(p.m.sj), e, src);
         else
             orb_compute<T, C>(p.m, p.tb, p.qfin, e.local, src, e.N, e.a, e.b, step_dt<T>(p.sc));
     }

@@ -139,6 +139,10 @@ template <typename T>
 struct RingMeta {
     int id, local, N;
     T a, b;
+    // orbital step: first cell of the ring, its X face area and dt over its
+    // cell volume, so the ring's loop reads no table
+    idx_t base;
+    T S, dtVi;
 };
 
 // Persistent double-buffered loop over items first, first+step, ... < n.
@@ -178,7 +182,6 @@ __device__ __forceinline__ void ring_pipeline(Op &op, T *buf, size_t stride, uin
         }
         return;
     }
-    unsigned uses[2] = {0u, 0u};
     for (int it = 0; it < K; it++) {
         const int b = it & 1;
         if (threadIdx.x == 0 && it + 1 < K) {
@@ -186,12 +189,12 @@ __device__ __forceinline__ void ring_pipeline(Op &op, T *buf, size_t stride, uin
             fence_proxy_async_smem();
             op.issue(it + 1, buf + (size_t)(1 - b) * stride, &bar[1 - b]);
         }
-        const bool ok = __syncthreads_and(mbar_wait(&bar[b], uses[b] & 1u));
-        uses[b]++;
+        // iteration it is the (it / 2)-th use of buffer b
+        const bool ok = __syncthreads_and(mbar_wait(&bar[b], (unsigned)(it >> 1) & 1u));
         if (!ok) {
             if (threadIdx.x == 0) {
                 op.fail(it);
-                if (it + 1 < K) mbar_wait(&bar[1 - b], uses[1 - b] & 1u);
+                if (it + 1 < K) mbar_wait(&bar[1 - b], (unsigned)((it + 1) >> 1) & 1u);
             }
             return;
         }
@@ -409,6 +412,19 @@ __device__ __forceinline__ void orb_prepare(const MeshD &m, const Tab<T> &tb, co
     if (Nm == 0 && xs == T(0)) Nm = -1;
 }
 
+// Per-ring constants of the orbital step: the ring's first cell, its X face
+// area and dt over its cell volume.
+template <typename T>
+__device__ __forceinline__ void orb_ring_consts(const MeshD &m, const Tab<T> &tb, T dtT, int r, RingMeta<T> &e)
+{
+    const int ny = m.j1 - m.j0;
+    const int j = m.j0 + r % ny, k = m.k0 + r / ny;
+    const int ring = k * m.nyt + j;
+    e.base = IX(m, 0, j, k);
+    e.S = tb.sx[ring];
+    e.dtVi = dtT * tb.vinv[ring];
+}
+
 // Thread 0: copies of the nq rows of active ring r into dst (row q at
 // dst + q * ring_row(pitch) + kRingLead), or a plain arrive when the ring
 // needs no work (Nm < 0).
@@ -608,6 +624,118 @@ __device__ __forceinline__ void orb_lanes(const QSet<T> &qs, int nq, int rp, con
     }
 }
 
+// FP32 form of orb_lanes for even C, on the packed two-lane FP32 units of
+// sm_100+ (one instruction adds, multiplies or fuses two pairs).  The pairs
+// are the cells (s, s + C/2) of a lane: every stencil neighbour of a pair is
+// then the pair at the neighbouring index, so the ratios, Eq. 34 slopes,
+// Eq. 35 interface values, the monotonised face values and the fluxes are
+// formed two cells per instruction with no register moves between pairs;
+// comparisons and selections stay per cell.  Each value is the same IEEE
+// operation sequence as in orb_lanes, rounded to nearest.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b (a + (-1) b, exact before the one rounding)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// Eq. 34 slope of one cell from the pair values of its stencil.
+__device__ __forceinline__ float ppa_dm_pick(float pr, float dl, float dr, float d)
+{
+    if (!(pr > 0.f)) return 0.f;
+    const float mn = fminf(2.f * fminf(fabsf(dl), fabsf(dr)), fabsf(d));
+    return d > 0.f ? mn : -mn;
+}
+__device__ __forceinline__ float2 ppa_dm2(float2 qm, float2 q0, float2 qp)
+{
+    const float2 dr = sub2(qp, q0), dl = sub2(q0, qm);
+    const float2 pr = mul2(dr, dl);
+    const float2 d = mul2(pk(0.5f), sub2(qp, qm));
+    return pk(ppa_dm_pick(pr.x, dl.x, dr.x, d.x), ppa_dm_pick(pr.y, dl.y, dr.y, d.y));
+}
+
+template <int C, bool POS>
+__device__ __forceinline__ void orb_lanes2(const QSet<float> &qs, int nq, int rp, const float *win, idx_t base,
+                                           int i0, bool owner, int nx, float xi, float vR, float S, float dtVi)
+{
+    static_assert(C % 2 == 0 && C >= 4, "pairs (s, s + C/2) need an even chunk of at least 4");
+    constexpr int H = C / 2;
+    const float2 sixth2 = pk(1.f / 6.f), half2 = pk(0.5f), nhalf2 = pk(-0.5f);
+    const float2 ntwo2 = pk(-2.f), three2 = pk(3.f);
+    const float2 xi2 = pk(xi), xx2 = pk(xi * (1.f - xi)), vR2 = pk(vR), S2 = pk(S), ndt2 = pk(-dtVi);
+    float2 RI[H];   // reciprocal densities of the pairs
+#pragma unroll
+    for (int s = 0; s < H; s++) RI[s] = pk(1.f / win[s], 1.f / win[s + H]);
+    float2 F0[H];
+    #pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if (q >= nq) break;
+        const float *wq = win + (size_t)q * rp;
+        // AA[k] = (A[k], A[k + H]): ratios of cells k-2 and k-2+H, k = 0 .. H+2
+        float2 AA[H + 3];
+#pragma unroll
+        for (int s = 0; s < H; s++) {
+            const float2 w = pk(wq[s], wq[s + H]);
+            AA[s + 2] = q == 0 ? w : mul2(w, RI[s]);
+        }
+        AA[0] = pk(shfl_up1(AA[H].y), AA[H].x);
+        AA[1] = pk(shfl_up1(AA[H + 1].y), AA[H + 1].x);
+        AA[H + 2] = pk(AA[2].y, shfl_dn1(AA[2].x));
+        // DM[k] = (dm[k], dm[k + H]): Eq. 34 slopes of cells k and k+H
+        float2 DM[H + 1];
+#pragma unroll
+        for (int k = 0; k < H; k++) DM[k] = ppa_dm2(AA[k + 1], AA[k + 2], AA[k + 3]);
+        DM[H] = pk(DM[0].y, shfl_dn1(DM[0].x));
+        // QQ[k] = (QR[k], QR[k + H]): Eq. 35 right interface values of cells k-2, k-2+H
+        float2 QQ[H + 2];
+#pragma unroll
+        for (int k = 2; k < H + 2; k++)
+            QQ[k] = fma2(sub2(DM[k - 2], DM[k - 1]), sixth2, fma2(half2, sub2(AA[k + 1], AA[k]), AA[k]));
+        QQ[0] = pk(shfl_up1(QQ[H].y), QQ[H].x);
+        QQ[1] = pk(shfl_up1(QQ[H + 1].y), QQ[H + 1].x);
+        // upwind PPA values through the left faces u and u+H of the pair
+        float2 FF[H];
+#pragma unroll
+        for (int u = 0; u < H; u++) {
+            constexpr int sh = POS ? 0 : 1;
+            const float2 q0 = AA[u + 1 + sh], qm = AA[u + sh], qp = AA[u + 2 + sh];
+            const float2 l = QQ[u + sh], rr = QQ[u + 1 + sh];
+            const float2 pr = mul2(sub2(qp, q0), sub2(q0, qm));
+            const float2 D = sub2(rr, l);
+            const float2 Cc = fma2(nhalf2, add2(l, rr), q0);
+            const float2 DC = mul2(D, Cc), DD6 = mul2(mul2(D, D), sixth2);
+            const float2 q3 = mul2(three2, q0);
+            const float2 ln = fma2(ntwo2, rr, q3), rn = fma2(ntwo2, l, q3);
+            float2 L, R;
+            {
+                const bool ext = pr.x <= 0.f, c1 = DC.x > DD6.x, c2 = -DD6.x > DC.x;
+                L.x = ext ? q0.x : (c1 ? ln.x : l.x);
+                R.x = ext ? q0.x : (!c1 && c2 ? rn.x : rr.x);
+            }
+            {
+                const bool ext = pr.y <= 0.f, c1 = DC.y > DD6.y, c2 = -DD6.y > DC.y;
+                L.y = ext ? q0.y : (c1 ? ln.y : l.y);
+                R.y = ext ? q0.y : (!c1 && c2 ? rn.y : rr.y);
+            }
+            const float2 wgt = mul2(xx2, sub2(sub2(add2(q0, q0), R), L));
+            const float2 stv = POS ? add2(fma2(xi2, sub2(q0, R), R), wgt) : add2(fma2(xi2, sub2(q0, L), L), wgt);
+            if (q == 0) F0[u] = mul2(mul2(vR2, stv), S2);
+            FF[u] = q == 0 ? F0[u] : mul2(F0[u], stv);
+        }
+        const float Fr = shfl_dn1(FF[0].x);   // flux through the right face of the last own cell
+        float *out = qs.q[q] + base + i0;
+#pragma unroll
+        for (int u = 0; u < H; u++) {
+            const float2 fr = u + 1 < H ? FF[u + 1 < H ? u + 1 : u] : pk(FF[0].y, Fr);
+            // (the staged values again: they are the cells' old values)
+            const float2 v = fma2(ndt2, sub2(fr, FF[u]), pk(wq[u], wq[u + H]));
+            if (owner && i0 + u < nx) out[u] = v.x;
+            if (owner && i0 + u + H < nx) out[u + H] = v.y;
+        }
+    }
+}
+
 // The orbital step's form per cells-per-thread class: the lane-exchange form
 // for C = 3, 4, 6; the per-thread form for C = 1, 2 (too few cells for the
 // halo lanes) and C = 8 (rings beyond 2880 cells, too long for the halo
@@ -619,20 +747,18 @@ __host__ __device__ constexpr bool orb_uses_lanes()
 }
 
 template <typename T, int C>
-__device__ __forceinline__ void orb_compute_w(const MeshD &m, const Tab<T> &tb, const QSet<T> &qs, int r, T *buf,
-                                              int Nm, T xsT, T vR, T dtT)
+__device__ __forceinline__ void orb_compute_w(const QSet<T> &qs, int nx, int rp, const RingMeta<T> &e, T *buf)
 {
     // the left halo of a lane's interface values reaches three cells back,
     // and the halo lanes must own those cells: C >= 3
     static_assert(orb_uses_lanes<C>(), "the halo lanes need three cells");
+    const int Nm = e.N;
     if (Nm < 0) return;
-    const int nx = m.nx, nq = qs.nq, rp = ring_row(m.sj);
+    const int nq = qs.nq;
     ring_frame(buf, nq, rp, nx);
     const T *sm = buf + kRingLead;
-    const int ny = m.j1 - m.j0;
-    const int j = m.j0 + r % ny, k = m.k0 + r / ny;
-    const int ring = k * m.nyt + j;
-    const idx_t base = IX(m, 0, j, k);
+    const idx_t base = e.base;
+    const T xsT = e.a, vR = e.b;
     if (xsT == T(0)) {   // a pure shift
         for (int q = 0; q < nq; q++)
             for (int i = threadIdx.x; i < nx; i += blockDim.x)
@@ -645,10 +771,15 @@ __device__ __forceinline__ void orb_compute_w(const MeshD &m, const Tab<T> &tb, 
     // cells i0 .. i0+C-1 after the shift: the staged run from (i0 - N) mod nx
     int b = (i0 - Nm) % nx;
     if (b < 0) b += nx;
-    const T S = tb.sx[ring];
-    const T dtVi = dtT * tb.vinv[ring];
-    if (xsT >= T(0)) orb_lanes<T, C, true>(qs, nq, rp, sm + b, base, i0, owner, nx, xsT, vR, S, dtVi);
-    else orb_lanes<T, C, false>(qs, nq, rp, sm + b, base, i0, owner, nx, -xsT, vR, S, dtVi);
+    const bool pos = xsT >= T(0);
+    const T xi = pos ? xsT : -xsT;
+    if constexpr (sizeof(T) == 4 && C % 2 == 0) {
+        if (pos) orb_lanes2<C, true>(qs, nq, rp, sm + b, base, i0, owner, nx, xi, vR, e.S, e.dtVi);
+        else orb_lanes2<C, false>(qs, nq, rp, sm + b, base, i0, owner, nx, xi, vR, e.S, e.dtVi);
+    } else {
+        if (pos) orb_lanes<T, C, true>(qs, nq, rp, sm + b, base, i0, owner, nx, xi, vR, e.S, e.dtVi);
+        else orb_lanes<T, C, false>(qs, nq, rp, sm + b, base, i0, owner, nx, xi, vR, e.S, e.dtVi);
+    }
 }
 
 // Single-instance ring operations for ring_pipeline (meta: the per-iteration
@@ -689,12 +820,13 @@ struct OrbOp {
     {
         meta[it].local = r;
         orb_prepare(m, tb, v0, sc, r, meta[it].N, meta[it].a, meta[it].b);
+        orb_ring_consts(m, tb, dt, r, meta[it]);
     }
     __device__ void issue(int it, T *dst, uint64_t *bar) { orb_issue(m, qs, meta[it].local, meta[it].N, dst, bar); }
     __device__ void compute(int it, T *src)
     {
         const RingMeta<T> &e = meta[it];
-        if constexpr (orb_uses_lanes<C>()) orb_compute_w<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
+        if constexpr (orb_uses_lanes<C>()) orb_compute_w<T, C>(qs, m.nx, ring_row(m.sj), e, src);
         else orb_compute<T, C>(m, tb, qs, e.local, src, e.N, e.a, e.b, dt);
     }
     __device__ void fail(int) { atomicOr(&sc->err, kErrTimeout); }
