@@ -96,6 +96,8 @@ def lib():
         L.or_mhd_tension.argtypes = [pp, ps, C.c_double]
         L.or_mhd_emf.argtypes = [pp, ps, C.c_double, P, P, P]
         L.or_mhd_ct.argtypes = [pp, ps, P, P, P, C.c_double]
+        L.or_mhd_fargo_emf.argtypes = [pp, ps, P, C.c_double, P, P, P]
+        L.or_v0_all.argtypes = [pp, ps, P]
         L.or_mhd_divb.argtypes = [pp, ps, C.c_int, C.c_int, C.c_int]
         L.or_mhd_divb.restype = C.c_double
         L.or_nearest_int.argtypes = [C.c_double]
@@ -232,6 +234,22 @@ class Oracle:
         """Cell 10: constrained transport of B by the EMF (Eq. 39)."""
         E = [np.ascontiguousarray(a, dtype=np.float64) for a in E]
         lib().or_mhd_ct(C.byref(self.p), C.byref(self._state(st)), *[_ptr(a) for a in E], dt)
+
+    def v0_all(self, st):
+        """Eq. 37 on every ring, ghost rings included (the velocity whose
+        residual the MHD sub-steps see under orbital advection)."""
+        v0 = np.zeros(self.nrings)
+        lib().or_v0_all(C.byref(self.p), C.byref(self._state(st)), _ptr(v0))
+        return v0.reshape(self.w.nz_t, self.w.ny_t)
+
+    def mhd_fargo_emf(self, st, v0all, dt):
+        """Cell 11: the upstream averages of the orbital motion's EMF
+        (Sec. 3.6, Eq. 54) on the edges; returns (e_x, e_y, e_z), e_x = 0."""
+        E = [np.zeros(self.shape) for _ in range(3)]
+        v0all = np.ascontiguousarray(v0all, dtype=np.float64)
+        lib().or_mhd_fargo_emf(C.byref(self.p), C.byref(self._state(st)), _ptr(v0all), dt,
+                               *[_ptr(a) for a in E])
+        return E
 
     def mhd_divb(self, st):
         """The discrete divergence of B, sum over the faces of B times area

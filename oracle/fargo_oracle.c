@@ -111,6 +111,7 @@ static double *zalloc(size_t n) { return calloc(n, sizeof(double)); }
 /* (MHD helpers, defined with the MHD sub-steps below) */
 static size_t mh_nb(const mesh *m, int i, int j, int k, int d, int off);
 static double *mh_b(const or_state *s, int d);
+static void mhd_tension_from(const or_params *p, const or_state *chr, or_state *s, double dt);
 static double *dup(const double *a, size_t n)
 {
     double *b = malloc(sizeof(double) * n);
@@ -465,6 +466,26 @@ void or_v0(const or_params *p, const or_state *s, double *v0)
                 }
                 v0[(size_t)k * m.nyt + j] = 0.5 * (mx + mn);
             }
+    mesh_free(&m);
+}
+
+/* Eq. 37 on every ring, ghost rings included: the velocity whose residual  */
+/* the MHD sub-steps see when the field is advected orbitally (reading M13); */
+/* on the active rings it is the v0 of or_v0.                                */
+void or_v0_all(const or_params *p, const or_state *s, double *v0)
+{
+    mesh m;
+    mesh_init(&m, p);
+    for (int k = 0; k < m.nzt; k++)
+        for (int j = 0; j < m.nyt; j++) {
+            double mx = s->vx[IDX(&m, 0, j, k)], mn = mx;
+            for (int i = 1; i < m.nx; i++) {
+                double v = s->vx[IDX(&m, i, j, k)];
+                if (v > mx) mx = v;
+                if (v < mn) mn = v;
+            }
+            v0[(size_t)k * m.nyt + j] = 0.5 * (mx + mn);
+        }
     mesh_free(&m);
 }
 
@@ -1470,14 +1491,21 @@ int or_step(const or_params *p, or_state *s, double t, double t_end, double dt_f
     mesh m;
     mesh_init(&m, p);
     size_t nr = (size_t)m.nzt * m.nyt;
-    double *v0 = zalloc(nr);
+    double *v0 = zalloc(nr), *v0all = NULL;
     double dt;
     int rc = 0;
+    /* with orbital advection the MHD sub-steps see the residual velocity    */
+    /* and the field's orbital share is cell 11 (Sec. 3.6; reading M13)     */
+    int mfargo = p->mhd && p->fargo && m.hasX;
     or_bc_fill(p, s);                                     /* cell 2 */
     or_v0(p, s, v0);                                      /* cell 3 */
+    if (mfargo) {
+        v0all = zalloc(nr);
+        or_v0_all(p, s, v0all);
+    }
     if (dt_fixed > 0.0) dt = dt_fixed;
     else rc = or_cfl(p, s, v0, t, t_end, &dt);            /* cells 4-6 */
-    if (rc) { free(v0); mesh_free(&m); *dt_out = dt; return rc; }
+    if (rc) { free(v0); free(v0all); mesh_free(&m); *dt_out = dt; return rc; }
     double *phi = NULL;
     if (p->planet_q > 0.0 || (p->star_mass > 0.0 && p->geom != OR_CART)) {
         phi = zalloc(m.n);
@@ -1491,12 +1519,29 @@ int or_step(const or_params *p, or_state *s, double t, double t_end, double dt_f
     double *em[3] = { NULL, NULL, NULL };
     if (p->mhd) {
         for (int o = 0; o < 3; o++) em[o] = zalloc(m.n);
-        or_mhd_emf(p, s, dt, em[0], em[1], em[2]);       /* cells 8a-8c */
-        or_mhd_tension(p, s, dt);                         /* cell 8d */
+        if (mfargo) {
+            /* the residual state: v_x - v0 of its ring, every ring */
+            or_state r = *s;
+            double *dvx = dup(s->vx, m.n);
+            for (int k = 0; k < m.nzt; k++)
+                for (int j = 0; j < m.nyt; j++)
+                    for (int i = 0; i < m.nx; i++) dvx[IDX(&m, i, j, k)] -= v0all[(size_t)k * m.nyt + j];
+            r.vx = dvx;
+            or_mhd_emf(p, &r, dt, em[0], em[1], em[2]);  /* cells 8a-8c */
+            mhd_tension_from(p, &r, s, dt);               /* cell 8d */
+            free(dvx);
+        } else {
+            or_mhd_emf(p, s, dt, em[0], em[1], em[2]);   /* cells 8a-8c */
+            or_mhd_tension(p, s, dt);                     /* cell 8d */
+        }
     }
     or_bc_fill(p, s);                                     /* cell 9 */
     if (p->mhd) {
         or_mhd_ct(p, s, em[0], em[1], em[2], dt);         /* cell 10 */
+        if (mfargo) {
+            or_mhd_fargo_emf(p, s, v0all, dt, em[0], em[1], em[2]);
+            or_mhd_ct(p, s, em[0], em[1], em[2], dt);     /* cell 11 */
+        }
         for (int o = 0; o < 3; o++) free(em[o]);
     }
     double *pi[6];
@@ -1508,7 +1553,7 @@ int or_step(const or_params *p, or_state *s, double t, double t_end, double dt_f
     or_orbital_shift(p, s, pi, v0, dt);
     or_new_velocities(p, s, pi);                          /* cell 12d */
     for (int q = 0; q < 6; q++) free(pi[q]);
-    free(phi); free(v0);
+    free(phi); free(v0); free(v0all);
     mesh_free(&m);
     *dt_out = dt;
     return 0;
@@ -1857,6 +1902,81 @@ void or_mhd_ct(const or_params *p, or_state *s, const double *ex, const double *
     mesh_free(&m);
 }
 
+/* Cell 11: orbital advection of the field (Sec. 3.6).  The field's share   */
+/* of the orbital motion v0 x (uniform along each ring) is the induction    */
+/* equation dB/dt = curl(v0 x B) (Eq. 50), whose EMF has the components     */
+/* e_z = v0 B_y and e_y = -v0 B_z.  Over the step each edge takes the        */
+/* upstream average of that EMF along the arc v0 dt that reaches it (Eq. 54):*/
+/*   Ebar_z(i-1/2, j-1/2, k) = (1/dt) int_{x - v0 dt}^{x} B_y(x') dx',        */
+/*   Ebar_y(i-1/2, j, k-1/2) = -(1/dt) int_{x - v0 dt}^{x} B_z(x') dx',       */
+/* x the edge's azimuth, v0 the two-point mean of the ring velocities on     */
+/* both sides of the face that carries B_y (B_z), or the ring's own along an */
+/* absent direction.  With X = v0 dt / dX = N + xi (N = E(X), the nearest    */
+/* integer of Sec. 3.4.1), the integral in units of dX is the sum of the N   */
+/* whole cells upstream (with the opposite sign for N < 0) plus xi times     */
+/* the PPA value of Sec. 3.4.1 on the face N cells upstream: the parabolic  */
+/* interpolation of the residual arc.  For a uniform v0 and xi = 0 the       */
+/* constrained transport of these EMFs is the shift B_i <- B_{i-N} (Eqs.     */
+/* 60, 64) up to the round-off of the sums.  Ebar_x = 0.  Edges in a wall's  */
+/* plane (non-periodic Y or Z) get zero, as in the residual step (M11).     */
+/* ex, ey, ez are written on every edge of the arrays (zero where no arc).  */
+static void mhd_fargo_ring(int nx, const double *ring, double X, double *out)
+{
+    long long N = or_nearest_int(X);
+    double xs = X - (double)N;
+    double *fs = zalloc(nx);
+    if (xs != 0.0) or_ppa_faces(nx, ring, xs, fs);
+    for (int i = 0; i < nx; i++) {
+        double w = 0.0;
+        if (N > 0)
+            for (long long q = 1; q <= N; q++) w += ring[(int)((((long long)i - q) % nx + nx) % nx)];
+        else
+            for (long long q = 0; q < -N; q++) w -= ring[(int)((((long long)i + q) % nx + nx) % nx)];
+        int f = (int)((((long long)i - N) % nx + nx) % nx);
+        out[i] = w + xs * fs[f];
+    }
+    free(fs);
+}
+
+void or_mhd_fargo_emf(const or_params *p, const or_state *s, const double *v0all, double dt, double *ex,
+                      double *ey, double *ez)
+{
+    mesh m;
+    mesh_init(&m, p);
+    for (size_t q = 0; q < m.n; q++) ex[q] = ey[q] = ez[q] = 0.0;
+    if (m.hasX && p->fargo) {
+        int nx = m.nx;
+        double dX = m.dx;
+        double *ring = zalloc(nx), *out = zalloc(nx);
+        /* Ebar_z from B_y: edge rows j0..j1 (Y faces), active planes */
+        int jl = m.hasY ? m.j0 : 0, jh = m.hasY ? m.j1 + 1 : 1;
+        int kl = m.hasZ ? m.k0 : 0, kh = m.hasZ ? m.k1 : 1;
+        for (int k = kl; k < kh; k++)
+            for (int j = jl; j < jh; j++) {
+                if (m.hasY && !m.pery && (j == m.j0 || j == m.j1)) continue;   /* wall */
+                double v0f = m.hasY ? 0.5 * (v0all[(size_t)k * m.nyt + j - 1] + v0all[(size_t)k * m.nyt + j])
+                                    : v0all[(size_t)k * m.nyt + j];
+                for (int i = 0; i < nx; i++) ring[i] = s->by[IDX(&m, i, j, k)];
+                mhd_fargo_ring(nx, ring, v0f * dt / dX, out);
+                for (int i = 0; i < nx; i++) ez[IDX(&m, i, j, k)] = dX / dt * out[i];
+            }
+        /* Ebar_y from B_z: active rows, edge planes k0..k1 (Z faces) */
+        jl = m.hasY ? m.j0 : 0; jh = m.hasY ? m.j1 : 1;
+        kl = m.hasZ ? m.k0 : 0; kh = m.hasZ ? m.k1 + 1 : 1;
+        for (int k = kl; k < kh; k++)
+            for (int j = jl; j < jh; j++) {
+                if (m.hasZ && !m.perz && (k == m.k0 || k == m.k1)) continue;   /* wall */
+                double v0f = m.hasZ ? 0.5 * (v0all[(size_t)(k - 1) * m.nyt + j] + v0all[(size_t)k * m.nyt + j])
+                                    : v0all[(size_t)k * m.nyt + j];
+                for (int i = 0; i < nx; i++) ring[i] = s->bz[IDX(&m, i, j, k)];
+                mhd_fargo_ring(nx, ring, v0f * dt / dX, out);
+                for (int i = 0; i < nx; i++) ey[IDX(&m, i, j, k)] = -dX / dt * out[i];
+            }
+        free(ring); free(out);
+    }
+    mesh_free(&m);
+}
+
 double or_mhd_divb(const or_params *p, const or_state *s, int i, int j, int k)
 {
     mesh m;
@@ -1891,7 +2011,12 @@ static double mh_tension_star(const mesh *m, const or_state *s, int i, int j, in
     return bs;
 }
 
-void or_mhd_tension(const or_params *p, or_state *s, double dt)
+/* The tension's velocity update of s, its star values from the state chr  */
+/* (chr = s in the plain step; with orbital advection chr carries the       */
+/* residual velocity, reading M13).                                          */
+void or_mhd_tension(const or_params *p, or_state *s, double dt) { mhd_tension_from(p, s, s, dt); }
+
+static void mhd_tension_from(const or_params *p, const or_state *chr, or_state *s, double dt)
 {
     if (!p->mhd || p->mhd_passive) return;
     mesh m;
@@ -1919,8 +2044,8 @@ void or_mhd_tension(const or_params *p, or_state *s, double dt)
                         double bbar = 0.25 * (bb[c] + bb[mh_nb(&m, i, j, k, b, 1)] + bb[cm] +
                                               bb[mh_nb(&m, ia, ja, ka, b, 1)]);
                         int ib = b == 0 ? (i + 1) % m.nx : i, jb = b == 1 ? j + 1 : j, kb = b == 2 ? k + 1 : k;
-                        double up = mh_tension_star(&m, s, ib, jb, kb, a, b, dt);
-                        double lo = mh_tension_star(&m, s, i, j, k, a, b, dt);
+                        double up = mh_tension_star(&m, chr, ib, jb, kb, a, b, dt);
+                        double lo = mh_tension_star(&m, chr, i, j, k, a, b, dt);
                         f += bbar * (up - lo) / mh_width(&m, b, mh_pos(i, j, k, b));
                     }
                     nv[a][c] = v[c] + dt * 2.0 / (s->rho[c] + s->rho[cm]) * f;

@@ -63,6 +63,7 @@ void or_bc_fill(const or_params *p, or_state *s);
  * corrects v_x everywhere and updates p (omega_f, planet_phase0). */
 void or_change_frame(or_params *p, or_state *s, double omega_new, double t);
 void or_v0(const or_params *p, const or_state *s, double *v0 /* [nz_t][ny_t] */);
+void or_v0_all(const or_params *p, const or_state *s, double *v0 /* [nz_t][ny_t], every ring */);
 int  or_cfl(const or_params *p, const or_state *s, const double *v0, double t, double t_end, double *dt);
 void or_potential(const or_params *p, double t, double *phi /* full cell array */);
 void or_substep1(const or_params *p, or_state *s, const double *phi, double dt);
@@ -85,6 +86,8 @@ void or_mhd_pressure(const or_params *p, or_state *s, double dt);
 void or_mhd_emf(const or_params *p, const or_state *s, double dt, double *ex, double *ey, double *ez);
 void or_mhd_tension(const or_params *p, or_state *s, double dt);
 void or_mhd_ct(const or_params *p, or_state *s, const double *ex, const double *ey, const double *ez, double dt);
+void or_mhd_fargo_emf(const or_params *p, const or_state *s, const double *v0all, double dt, double *ex,
+                      double *ey, double *ez);
 /* Discrete divergence of B of active cell (i, j, k) times its volume. */
 double or_mhd_divb(const or_params *p, const or_state *s, int i, int j, int k);
 

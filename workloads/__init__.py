@@ -780,6 +780,62 @@ def magnetostatic_column(nx=64, ny=4, b0=1.0, p0=2.0, g=3):
     return w
 
 
+def mhd_shearing_sheet(nx=32, ny=32, nz=1, omega=1.0, oort_a=-0.75, cs=0.1, lx=1.0, ly=1.0, lz=0.5,
+                       b0=(0.0, 0.05, 0.0), amp=0.0, seed=0, fargo=True, bcy=BC_FROZEN, g=3, eta=0.0,
+                       passive=False, vamp=0.0):
+    """A Cartesian shearing sheet with a magnetic field (Sec. 2 and Sec. 3.6):
+    the frame turns at Omega, X runs along the shear flow v_x = 2 A y
+    (A = -3/4 Omega, Keplerian) over lx, Y across it on [-ly/2, ly/2] with
+    walls of type bcy (frozen: the initial state) or periodic, Z periodic
+    over lz.  Uniform density 1, isothermal (sound speed cs), no potential.
+    The field is the uniform b0 plus, with amp > 0, the curl of a seeded
+    vector potential of a few Fourier modes (divergence-free to round-off);
+    vamp > 0 adds a seeded smooth velocity perturbation."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    yf = faces(ny, g, -0.5 * ly, 0.5 * ly)
+    zf = faces(nz, g, -0.5 * lz, 0.5 * lz)
+    w = Workload("mhd_shearing_sheet", CART, nx, ny, nz, g, 0.0, lx, yf, zf, 5.0 / 3.0, True, None, None, 0.44,
+                 1.41, fargo, omega, (bcy, bcy), (BC_PERIODIC, BC_PERIODIC), 0.0, 0.0, 1.0, 0.0, False, 0.0,
+                 1e30, {}, shearing=True, oort_a=oort_a)
+    w.mhd, w.mhd_passive, w.eta = True, passive, eta
+    w.cs = np.full((w.nz_t, w.ny_t), cs)
+    st = _empty(w.shape)
+    st.update({k: np.zeros(w.shape) for k in MHD_FIELDS})
+    w.state = st
+    L = (lx, ly, lz)
+
+    def modes(a):
+        terms = []
+        for _ in range(3):
+            k = [rng.integers(1, 3), rng.integers(0, 3) if ny > 1 else 0, rng.integers(0, 3) if nz > 1 else 0]
+            terms.append((k, rng.uniform(0, 2 * math.pi), a * rng.uniform(-1, 1)))
+
+        def f(x, y, z):
+            out = 0.0
+            for k, ph, c in terms:
+                out = out + c * np.cos(2 * math.pi * (k[0] * x / L[0] + k[1] * y / L[1] + k[2] * z / L[2]) + ph)
+            return out
+        return f
+
+    xc, xf, yc, yfa, zc, zfa, dx = _mhd_coords(w)
+    nzt, nyt = w.nz_t, w.ny_t
+    st["rho"][:nzt, :nyt] = 1.0
+    st["vx"][:nzt, :nyt] = (2.0 * oort_a * yc[:nyt])[None, :, None]
+    if vamp > 0:
+        fx, fy = modes(vamp), modes(vamp)
+        st["vx"][:nzt, :nyt] += fx(xf[None, None, :], yc[None, :nyt, None], zc[:nzt, None, None])
+        st["vy"][:nzt, :nyt + 1] += fy(xc[None, None, :], yfa[None, :, None], zc[:nzt, None, None])
+    if amp > 0:
+        bx, by, bz = curl_field(w, modes(amp), modes(amp), modes(amp))
+        st["bx"][:] = bx
+        st["by"][:] = by
+        st["bz"][:] = bz
+    st["bx"][:nzt, :nyt] += b0[0]
+    st["by"][:nzt, :nyt + 1] += b0[1]
+    st["bz"][:nzt + 1, :nyt] += b0[2]
+    return w
+
+
 def uniform_mhd_box(nx, ny, nz, rho=1.0, e=1.5, v=(0.0, 0.0, 0.0), b=(0.0, 0.0, 0.0), periodic=True, g=3,
                     eta=0.0, passive=False):
     """A Cartesian MHD box holding a uniform state (ghosts included);
