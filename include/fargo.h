@@ -265,7 +265,8 @@ int fargo_planets_advance_async(fargo_ctx *ctx, int n, double *y, const double *
 int fargo_set_planet_source(fargo_ctx *ctx, const double *pos, int n, int stride, const double *mass);
 
 /* Magnetic field (Sec. 3.5, the method of characteristics with constrained
- * transport, MOCCT), mu_0 = 1, on Cartesian meshes with standard transport.
+ * transport, MOCCT), mu_0 = 1, on Cartesian meshes, with standard transport
+ * or with orbital advection (FARGO on, e.g. the shearing sheet; Sec. 3.6).
  * Allocates B_x, B_y, B_z (face centred like the velocity, all zero until
  * set with fargo_set_field(FARGO_BX..FARGO_BZ)), the edge EMFs and a third
  * velocity set; from then on every step adds, in the flow chart's order:
@@ -282,9 +283,17 @@ int fargo_set_planet_source(fargo_ctx *ctx, const double *pos, int n, int stride
  * transported but the gas feels no magnetic force.  eta: the uniform Ohmic
  * diffusivity (>= 0).  A second call changes passive and eta and keeps B.
  * In an FP32 context the reference form of v_x is switched off (every vref
- * is 0).  The net flux of B out of every cell is kept to round-off.
- * Errors: BADARG (not Cartesian, FARGO transport or shearing sheet on,
- * eta negative or not finite, context held by a batch), OOM, CUDA. */
+ * is 0).  With orbital advection the EMFs and the tension's characteristic
+ * values take the residual azimuthal velocity v_x - v0 (v0 of Eq. 37 on
+ * every ring, ghost rings included), and after cell 10 the field's orbital
+ * share is applied (cell 11): the EMFs e_z = v0 B_y and e_y = -v0 B_z
+ * averaged upstream over the arc v0 dt of each edge (Eq. 54: the whole
+ * cells upstream plus the PPA value of the residual arc), v0 the mean of
+ * the rings on both sides of the face, zero on wall edges, through the same
+ * constrained transport.  The net flux of B out of every cell is kept to
+ * round-off.  Errors: BADARG (not Cartesian, eta negative or not finite,
+ * context held by a batch), OOM, CUDA; a step whose orbital arc exceeds 16
+ * turns of a ring latches NONFINITE. */
 int fargo_enable_mhd(fargo_ctx *ctx, int passive, double eta);
 
 /* Change the frame's rotation rate to omega_new at the current time (Sec.

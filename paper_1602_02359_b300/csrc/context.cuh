@@ -29,6 +29,9 @@ struct Buffers {
     // the magnetic tension (the field itself is tab.bfield)
     T *ef[3] = {nullptr, nullptr, nullptr};
     T *vM[3] = {nullptr, nullptr, nullptr};
+    // MHD with orbital advection: Eq. 37 on every ring, and the residual v_x
+    double *v0all = nullptr;
+    T *dvx = nullptr;
 };
 
 struct HostGeom {
@@ -55,6 +58,8 @@ struct StepPlan {
     Fld<T> VM;         // the tension's output (MHD)
     MagF<T> B;         // the field (null without MHD)
     T *E[3];           // the EMFs (MHD)
+    double *v0all;     // MHD with orbital advection: every ring's v0
+    T *dvx;            //   and the residual v_x the EMFs and the tension read
     Fld<T> txin;       // input of the X sweep: state scalars, post-source velocities
     QSet<T> qx, qy, qz;   // outputs of the X, Y and Z sweeps
     QSet<T> qfin;      // quantity set after the sweeps (orbital step in place, new velocities)
@@ -149,6 +154,8 @@ static StepPlan<T> make_plan(const fargo_ctx *c, const Buffers<T> &b)
         p.E[d] = b.ef[d];
     }
     p.VM = {b.A.rho, b.A.e, b.vM[0], b.vM[1], b.vM[2]};
+    p.v0all = b.v0all;
+    p.dvx = b.dvx;
     if (m.mhd && !m.mhd_passive) p.vsrc = p.VM;
     p.txin = {b.A.rho, b.A.e, p.vsrc.vx, p.vsrc.vy, p.vsrc.vz};
     for (int q = 0; q < 6; q++) p.tau.q[q] = b.piB[q];

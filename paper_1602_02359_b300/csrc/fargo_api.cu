@@ -401,6 +401,11 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     // cells 3-6
     k_cfl_screen<T><<<P.cfl_blocks, 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_screen");
+    const bool mfargo = m.mhd && m.fargo && m.hasX;   // orbital advection of the field (Sec. 3.6)
+    if (mfargo) {
+        k_mhd_v0all<T><<<(m.nyt * m.nzt + 7) / 8, 256, 0, s>>>(m, P.A.vx, P.v0all);
+        MARK("mhd_v0all");
+    }
     k_cfl_exact<T><<<cfl_exact_grid(P.cfl_blocks), 256, 0, s>>>(m, P.tb, P.A, P.v0, P.ringmax, P.part, P.sc, P.nrings_active);
     MARK("cfl_exact");
     // periodic images between the phases (periodic Y/Z axes only)
@@ -432,8 +437,16 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
     // cells 8a-8d: the EMFs and the magnetic tension, both from the velocities
     // after the source sub-steps
     if (m.mhd) {
-        k_mhd_edges<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.vpre, P.VM, P.E[0], P.E[1], P.E[2], P.sc, 1,
-                                            !m.mhd_passive);
+        if (mfargo) {   // the EMFs and the tension's stars from the residual v_x
+            k_mhd_dvx<T><<<dim3(cg.x, m.nyt, m.nzt), cb, 0, s>>>(m, P.vpre.vx, P.v0all, P.dvx);
+            MARK("mhd_dvx");
+            const Fld<T> res = {P.vpre.rho, P.vpre.e, P.dvx, P.vpre.vy, P.vpre.vz};
+            k_mhd_edges<T><<<fgrid, cb, 0, s>>>(m, P.tb, res, P.VM, P.E[0], P.E[1], P.E[2], P.sc, 1,
+                                                !m.mhd_passive, P.vpre.vx);
+        } else {
+            k_mhd_edges<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.vpre, P.VM, P.E[0], P.E[1], P.E[2], P.sc, 1,
+                                                !m.mhd_passive, (const T *)nullptr);
+        }
         MARK("mhd_edges");
         if (!m.mhd_passive) PERIODIC(per_fields<T>(m, P.VM, true, false), "periodic");
     }
@@ -445,6 +458,15 @@ static int enqueue_step(fargo_ctx *c, Buffers<T> &b, Prof *prof = nullptr)
         k_mhd_ct<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.E[0], P.E[1], P.E[2], P.sc);
         MARK("mhd_ct");
         PERIODIC(per_field<T>(m, P.tb), "periodic");
+        // cell 11: the field's orbital advection, the upstream-averaged EMFs
+        // of the orbital motion through the same constrained transport
+        if (mfargo) {
+            k_mhd_fargo_emf<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.v0all, P.E[0], P.E[1], P.E[2], P.sc);
+            MARK("mhd_fargo_emf");
+            k_mhd_ct<T><<<fgrid, cb, 0, s>>>(m, P.tb, P.E[0], P.E[1], P.E[2], P.sc);
+            MARK("mhd_ct11");
+            PERIODIC(per_field<T>(m, P.tb), "periodic");
+        }
     }
     // cell 12
     launch_tx<T>(m, P.tb, P.txin, P.qx, P.v0, P.sc, c->tx_rs, s);
@@ -1300,6 +1322,12 @@ static int enable_mhd_impl(fargo_ctx *c, Buffers<T> &b)
         if ((rc = upload<T>(c, &b.tab.mh_idcy, idc(c->hg.dy)))) return rc;
         if ((rc = upload<T>(c, &b.tab.mh_idcz, idc(c->hg.dz)))) return rc;
     }
+    if (c->m.fargo && !b.v0all) {   // orbital advection of the field (Sec. 3.6)
+        if ((rc = dalloc(c, &p, sizeof(double) * (size_t)c->nyt * c->nzt))) return rc;
+        b.v0all = (double *)p;
+        if ((rc = dalloc(c, &p, n))) return rc;
+        b.dvx = (T *)p;
+    }
     if ((rc = vref_launch<T>(c, b, VREF_ABS, nullptr, c->stream))) return rc;
     c->m.mhd = 1;
     if ((rc = vref_refresh<T>(c, b, c->stream))) return rc;
@@ -1310,7 +1338,7 @@ static int enable_mhd_impl(fargo_ctx *c, Buffers<T> &b)
 
 extern "C" int fargo_enable_mhd(fargo_ctx *c, int passive, double eta)
 {
-    if (!c || c->geom != FARGO_CART || c->m.fargo || c->m.shearing || c->batch_refs > 0) return FARGO_ERR_BADARG;
+    if (!c || c->geom != FARGO_CART || c->batch_refs > 0) return FARGO_ERR_BADARG;
     if (!(eta >= 0.0) || !isfinite(eta)) return FARGO_ERR_BADARG;
     c->m.mhd_passive = passive ? 1 : 0;
     c->m.eta = eta;
@@ -1461,13 +1489,13 @@ static int debug_impl(fargo_ctx *c, Buffers<T> &b, int phase, double dt)
         break;
     case 11: {  // the EMFs (cells 8a-8c) of the state, into the aux arrays 7-9
         Fld<T> VM = {A.rho, A.e, b.vM[0], b.vM[1], b.vM[2]};
-        k_mhd_edges<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, b.ef[0], b.ef[1], b.ef[2], c->sc, 1, 0);
+        k_mhd_edges<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, b.ef[0], b.ef[1], b.ef[2], c->sc, 1, 0, (const T *)nullptr);
         break;
     }
     case 12: {  // the magnetic tension (cell 8d), back into the state's velocities
         if (m.mhd_passive) break;
         Fld<T> VM = {A.rho, A.e, b.vM[0], b.vM[1], b.vM[2]};
-        k_mhd_edges<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, b.ef[0], b.ef[1], b.ef[2], c->sc, 0, 1);
+        k_mhd_edges<T><<<fg, fb, 0, s>>>(m, b.tab, A, VM, b.ef[0], b.ef[1], b.ef[2], c->sc, 0, 1, (const T *)nullptr);
         if ((rc = copyv(va, b.vM))) return rc;
         if (!m.hasZ) CK(cudaMemcpyAsync(va[2], b.vM[2], nbytes, cudaMemcpyDeviceToDevice, s));
         launch_periodic<T>(m, per_fields<T>(m, A, true, false), c->sc, s);

@@ -194,9 +194,11 @@ __global__ void __launch_bounds__(256) k_mhd_pressure(MeshD m, Tab<T> tb, Fld<T>
 // tension terms of a face are summed over its two directions in ascending
 // order; every velocity component comes from the values on entry (out of
 // place).  emf / tension switch the two parts (the debug phases run one).
+// Under orbital advection f holds the residual v_x (Sec. 3.6) and vxb the
+// velocity the tension updates; otherwise vxb is null.
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_mhd_edges(MeshD m, Tab<T> tb, Fld<T> f, Fld<T> out, T *ex, T *ey, T *ez,
-                                                   const Scal *sc, int emf, int tension)
+                                                   const Scal *sc, int emf, int tension, const T *vxb)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const T dt = step_dt<T>(sc);
@@ -275,7 +277,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_mhd_edges(MeshD
     if (!tension) return;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        T v = V[a][c];
+        // (under orbital advection f carries the residual v_x; vxb the velocity itself)
+        T v = a == 0 && vxb ? vxb[c] : V[a][c];
         if (face[a]) {
             T fa = T(0);
 #pragma unroll
@@ -306,6 +309,129 @@ __global__ void __launch_bounds__(256) k_mhd_ct(MeshD m, Tab<T> tb, const T *ex,
         T *B = tb.bfield[a];
         B[c] = B[c] + dt * d;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Orbital advection of the field (Sec. 3.6).
+// ---------------------------------------------------------------------------
+
+// Eq. 37 on every ring, ghost rings included (cell 3): the ring velocities
+// whose residual the MHD sub-steps see.  One warp per ring; exact maximum
+// and minimum, so the active rings get the v0 of the X sweep.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mhd_v0all(MeshD m, const T *vx, double *v0all)
+{
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = (int)(threadIdx.x & 31);
+    if (w >= m.nyt * m.nzt) return;   // (warp-uniform)
+    const T *row = vx + IX(m, 0, w % m.nyt, w / m.nyt);
+    T mx = row[0], mn = row[0];
+    for (int i = lane; i < m.nx; i += 32) {
+        mx = row[i] > mx ? row[i] : mx;
+        mn = row[i] < mn ? row[i] : mn;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const T a = __shfl_xor_sync(0xffffffffu, mx, o), b = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = a > mx ? a : mx;
+        mn = b < mn ? b : mn;
+    }
+    if (lane == 0) v0all[w] = 0.5 * ((double)mx + (double)mn);
+}
+
+// The residual azimuthal velocity v_x - v0 of every cell's ring (cells 8a-8d
+// under orbital advection), rounded once.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mhd_dvx(MeshD m, const T *vx, const double *v0all, T *dvx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= m.nx || j >= m.nyt || k >= m.nzt) return;
+    const idx_t c = IX(m, i, j, k);
+    dvx[c] = (T)((double)vx[c] - v0all[k * m.nyt + j]);
+}
+
+// Upstream average of the orbital EMF at the edge at the lower X face of
+// cell i, for the ring row of B (B_y at a Y face, or B_z at a Z face) and
+// the arc v0f dt (Eq. 54): (1/dt) times the integral of B over the arc,
+// i.e. (dX/dt) (sum of the N whole cells upstream + xi times the PPA face
+// value N cells upstream), X = v0f dt / dX = N + xi.  An arc beyond 16 turns
+// of the ring, or not finite, records FARGO_ERR_NONFINITE and gives 0.
+template <typename T>
+__device__ __forceinline__ T mh_orbital_emf(const MeshD &m, const T *row, int i, double v0f, double dt, Scal *sc)
+{
+    const int nx = m.nx;
+    const double X = __ddiv_rn(__dmul_rn(v0f, dt), m.dx);
+    if (!(fabs(X) <= 16.0 * nx)) {
+        atomicOr(&sc->err, 1);
+        return T(0);
+    }
+    const long long N = llround(X);
+    const double xs = __dsub_rn(X, (double)N);
+    T w = T(0);
+    if (N > 0) {
+        int q = i;
+        for (long long n = 0; n < N; n++) {   // cells i-1, i-2, ... (the order of the sum)
+            q = q == 0 ? nx - 1 : q - 1;
+            w += row[q];
+        }
+    } else {
+        int q = i;
+        for (long long n = 0; n < -N; n++) {  // cells i, i+1, ...
+            w -= row[q];
+            q = q + 1 == nx ? 0 : q + 1;
+        }
+    }
+    T st = T(0);
+    if (xs != 0.0) {
+        int f = (int)(((long long)i - N) % nx);
+        if (f < 0) f += nx;
+        const bool pos = xs >= 0.0;
+        const int d = pos ? f - 1 : f;   // the donor cell of face f
+        T a[5];
+#pragma unroll
+        for (int s = 0; s < 5; s++) {
+            int q = (d - 2 + s) % nx;
+            a[s] = row[q < 0 ? q + nx : q];
+        }
+        st = ppa_face(a, (T)(pos ? xs : -xs), pos);
+    }
+    return (T)(m.dx / dt) * (w + (T)xs * st);
+}
+
+// Cell 11: e_z = v0 B_y and e_y = -v0 B_z averaged upstream on every edge
+// (e_x = 0), v0 the two-point mean of the rings across the face carrying
+// B_y (B_z), or the ring's own along an absent direction; zero on the edges
+// in a wall's plane (non-periodic Y or Z) and off the active range.  The
+// constrained transport k_mhd_ct then applies them.  Grid: every row and
+// plane of the arrays (the face kernels' grid).
+template <typename T>
+__global__ void __launch_bounds__(256) k_mhd_fargo_emf(MeshD m, Tab<T> tb, const double *v0all, T *ex, T *ey,
+                                                       T *ez, Scal *sc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= m.nx || j > m.nyt || k > m.nzt) return;
+    const idx_t c = IX(m, i, j, k);
+    const double dt = sc->dt;
+    T vz = T(0), vy = T(0);
+    if (dt > 0.0) {
+        // e_z: Y-face rows j0..j1 (walls excluded), active planes
+        const bool jz = m.hasY ? (j >= m.j0 && j <= m.j1 && (m.pery || (j != m.j0 && j != m.j1))) : j == 0;
+        const bool kz = m.hasZ ? (k >= m.k0 && k < m.k1) : k == 0;
+        if (jz && kz) {
+            const int r = k * m.nyt + j;
+            const double v0f = m.hasY ? 0.5 * (v0all[r - 1] + v0all[r]) : v0all[r];
+            vz = mh_orbital_emf(m, tb.bfield[1] + IX(m, 0, j, k), i, v0f, dt, sc);
+        }
+        // e_y: active rows, Z-face planes k0..k1 (walls excluded)
+        const bool jy = m.hasY ? (j >= m.j0 && j < m.j1) : j == 0;
+        const bool ky = m.hasZ ? (k >= m.k0 && k <= m.k1 && (m.perz || (k != m.k0 && k != m.k1))) : k == 0;
+        if (jy && ky) {
+            const int r = k * m.nyt + j;
+            const double v0f = m.hasZ ? 0.5 * (v0all[r - m.nyt] + v0all[r]) : v0all[r];
+            vy = -mh_orbital_emf(m, tb.bfield[2] + IX(m, 0, j, k), i, v0f, dt, sc);
+        }
+    }
+    ex[c] = T(0);
+    ey[c] = vy;
+    ez[c] = vz;
 }
 
 // Periodic images of the field (periodic Y / Z axes): B_y face-centred
