@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(512, 2) kb_tx(const StepPlan<T> *__restrict__ 
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2) kb_orb(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems,
+__global__ void __launch_bounds__(orb_max_threads(C), orb_min_blocks(C)) kb_orb(const StepPlan<T> *__restrict__ P, Group g, int stride, int nitems,
                                                  int nbuf)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];

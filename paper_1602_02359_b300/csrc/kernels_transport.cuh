@@ -746,6 +746,14 @@ __host__ __device__ constexpr bool orb_uses_lanes()
     return C >= 3 && C <= 6;
 }
 
+// Launch bounds of the orbital kernels per chunk: the FP32 lane form's
+// packed stencils of C = 4 and 6 get 72 registers (no spills) under a lower
+// thread cap that keeps the CTAs per SM of the 64-register budget; ring_chunk
+// keeps every ring within its chunk's cap.
+__host__ __device__ constexpr int orb_max_threads(int C) { return C == 6 ? 288 : (C == 4 ? 416 : 512); }
+__host__ __device__ constexpr int orb_min_blocks(int C) { return C == 6 ? 3 : 2; }
+__host__ __device__ constexpr int orb_regs(int C) { return C == 4 || C == 6 ? 72 : 64; }
+
 template <typename T, int C>
 __device__ __forceinline__ void orb_compute_w(const QSet<T> &qs, int nx, int rp, const RingMeta<T> &e, T *buf)
 {
@@ -858,7 +866,7 @@ __global__ void __launch_bounds__(512, 2)
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(orb_max_threads(C), orb_min_blocks(C))
     k_orbital(const __grid_constant__ MeshD m, const __grid_constant__ Tab<T> tb, const __grid_constant__ QSet<T> qs,
               const double *v0, Scal *sc, int nrings, int stride, int nbuf)
 {
@@ -895,12 +903,12 @@ static inline int ring_chunk(int nx, int rows, int pitch, int esz, bool halo, in
     int best = 0;
     for (int c : cs) {
         const int th = ring_threads(nx, c, halo);
-        if (th > 512) continue;
+        if (th > (halo ? orb_max_threads(c) : 512)) continue;
         if (c == 8 && best) break;
         if (th < 192 && best) break;
         int per = (int)(233472 / smem);
         per = std::min(per, 2048 / th);
-        per = std::min(per, 65536 / (64 * th));
+        per = std::min(per, 65536 / ((halo ? orb_regs(c) : 64) * th));
         per = std::min(per, 32);
         if (best == 0 || per * th >= 768) best = c;
     }
