@@ -73,8 +73,9 @@ __global__ void __launch_bounds__(256) kb_bc(const StepPlan<T> *__restrict__ P, 
     else bc_z_body(p.m, mode == 0 ? p.A : p.vsrc, p.sc, mode, tid, p.tb.vref);
 }
 
+// (64 registers: no spills; see k_cfl_screen)
 template <typename T>
-__global__ void __launch_bounds__(256, 6) kb_cfl_screen(const StepPlan<T> *__restrict__ P, Group g)
+__global__ void __launch_bounds__(256, 4) kb_cfl_screen(const StepPlan<T> *__restrict__ P, Group g)
 {
     int local;
     __shared__ PlanSmem<T> sp;

@@ -439,6 +439,8 @@ __device__ __forceinline__ void cfl_screen_body(const MeshD &m, const Tab<T> &tb
         if (m.fargo) {
             // max and min are exact in the field precision
             T mx = f.vx[base], mn = mx;
+            // (unrolled: several loads of a lane in flight at once)
+#pragma unroll 4
             for (int i0 = lane * W; i0 < nx; i0 += 32 * W) {
                 const Pack<T> pv = ldpack(f.vx + base + i0);
 #pragma unroll
@@ -819,10 +821,10 @@ __global__ void __launch_bounds__(256) k_vref(MeshD m, Tab<T> tb, T *vx, T *dst,
 // Blocks of the exact pass for a screen of cfl_blocks blocks (eight rings each).
 __host__ __device__ __forceinline__ int cfl_exact_grid(int cfl_blocks) { return (cfl_blocks + 7) / 8; }
 
-// (six blocks per SM: the screen is latency-bound, and the occupancy a
-// 40-register budget buys outweighs its few spills)
+// (four blocks per SM at 64 registers: at 40 the screen spilled, and the
+// batched screen measured 0.66 ms against 0.53 ms with no spills)
 template <typename T>
-__global__ void __launch_bounds__(256, 6) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f, double *v0, float *ringmax,
+__global__ void __launch_bounds__(256, 4) k_cfl_screen(MeshD m, Tab<T> tb, Fld<T> f, double *v0, float *ringmax,
                                                     double *part, Scal *sc, int nrings)
 {
     cfl_screen_body(m, tb, f, v0, ringmax, part, sc, nrings, blockIdx.x, gridDim.x);
