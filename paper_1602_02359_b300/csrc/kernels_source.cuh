@@ -81,6 +81,10 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
     const T om = tb.omega;
     const int im = i == 0 ? m.nx - 1 : i - 1;
     const int ip = i + 1 == m.nx ? 0 : i + 1;
+    // the three face values are stored at the end: no store sits between the
+    // loads, so the compiler may keep every loaded value for all three faces
+    T ox = T(0), oy = T(0), oz = T(0);
+    bool wx = false, wy = false, wz = false;
     if (j < m.nyt && k < m.nzt) {
         T v = in.vx[c];
         if (F::hasX(m) && jact && kact) {
@@ -92,7 +96,8 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
                 acc -= (phi_planet<T, F>(m, tb, i, ring) - phi_planet<T, F>(m, tb, im, ring)) * id;
             v = v + dt * acc;
         }
-        out.vx[c] = v;
+        ox = v;
+        wx = true;
     }
     if (k < m.nzt) {
         T v = in.vy[c];
@@ -126,7 +131,8 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
             }
             v = v + dt * acc;
         }
-        out.vy[c] = v;
+        oy = v;
+        wy = true;
     }
     if (F::hasZ(m) && j < m.nyt) {
         T v = in.vz[c];
@@ -148,8 +154,12 @@ __device__ __forceinline__ void substep1_body(const MeshD &m, const Tab<T> &tb, 
             }
             v = v + dt * acc;
         }
-        out.vz[c] = v;
+        oz = v;
+        wz = true;
     }
+    if (wx) out.vx[c] = ox;
+    if (wy) out.vy[c] = oy;
+    if (wz) out.vz[c] = oz;
 }
 
 // ---------------------------------------------------------------------------
@@ -183,8 +193,15 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     const int ipp = ip + 1 == m.nx ? 0 : ip + 1;
     const T *vx = in.vx, *vy = in.vy, *vz = in.vz, *rho = in.rho;
     const idx_t sj = m.sj, sk = m.sk;
-    // own lower faces
+    // own lower faces (stored at the end: no store sits between the loads,
+    // so the compiler may keep every loaded value for all faces and e)
     T vxl = 0, vyl = 0, vzl = 0;
+    bool wx = false, wy = false, wz = false;
+    auto store_v = [&]() {
+        if (wx) out.vx[c] = vxl;
+        if (wy) out.vy[c] = vyl;
+        if (wz) out.vz[c] = vzl;
+    };
     if (j < m.nyt && k < m.nzt) {
         T v = vx[c];
         if (av && F::hasX(m) && jact && kact) {
@@ -193,8 +210,8 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
             const T qm = qvisc(c2, rho[cm], vx[c] - vx[cm]);
             v -= div_fast(dt * T(2) * (q0 - qm) * tb.ilenx[ring], rho[c] + rho[cm]);
         }
-        out.vx[c] = v;
         vxl = v;
+        wx = true;
     }
     if (k < m.nzt) {
         T v = vy[c];
@@ -204,8 +221,8 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
             const T qm = qvisc(c2, rho[cm], vy[c] - vy[cm]);
             v -= div_fast(dt * T(2) * (q0 - qm) * tb.idyc[j], rho[c] + rho[cm]);
         }
-        out.vy[c] = v;
         vyl = v;
+        wy = true;
     }
     if (F::hasZ(m) && j < m.nyt) {
         T v = vz[c];
@@ -215,10 +232,13 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
             const T qm = qvisc(c2, rho[cm], vz[c] - vz[cm]);
             v -= div_fast(dt * T(2) * (q0 - qm) * tb.idzc[ring], rho[c] + rho[cm]);
         }
-        out.vz[c] = v;
         vzl = v;
+        wz = true;
     }
-    if (F::iso(m) || !(jact && kact)) return;
+    if (F::iso(m) || !(jact && kact)) {
+        store_v();
+        return;
+    }
     // heating by the artificial viscosity of the cell itself
     T e = in.e[c];
     T h = 0;
@@ -271,6 +291,7 @@ __device__ __forceinline__ void artvisc_body(const MeshD &m, const Tab<T> &tb, c
     }
     div *= tb.vinv[ring];
     const T th = tb.half_gm1 * dt * div;
+    store_v();
     out.e[c] = e * (T(1) - th) / (T(1) + th);
 }
 
