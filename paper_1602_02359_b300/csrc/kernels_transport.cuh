@@ -1347,7 +1347,10 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
     const T *pmy = qsel(fin, oy), *ppy = qsel(fin, oy + 1);
     const T *pmz = qsel(fin, oz), *ppz = qsel(fin, oz + 1);
     // interior faces from the momenta; every other face from the post-source
-    // velocities, read only there (and not at all when they are the state)
+    // velocities, read only there (and not at all when they are the state).
+    // The three values are stored at the end: no store sits between the loads.
+    T nvx = T(0), nvy = T(0), nvz = T(0);
+    bool wx = false, wy = false, wz = false;
     if (j < m.nyt && k < m.nzt) {
         if (jact && kact) {
             const idx_t cm = c - i + (i == 0 ? m.nx - 1 : i - 1);
@@ -1357,36 +1360,47 @@ __device__ __forceinline__ void newvel_body(const MeshD &m, const Tab<T> &tb, co
             // In the reference form the momenta hold rho (R v_x + w) - rho A with
             // A = R vref + w, so the quotient is R (v_x - vref), the stored value.
             if (sizeof(T) == 4 && tb.vref) {
-                state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c])) / R;
+                nvx = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c])) / R;
+                wx = true;
             } else {
                 const T w = F::geom(m) == CART ? tb.wfr[ring] : R * R * tb.omega;
-                state.vx[c] = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
+                nvx = ((ppx[cm] + pmx[c]) / (rho[cm] + rho[c]) - w) / R;
+                wx = true;
             }
         } else if (vsrc.vx != state.vx) {
-            state.vx[c] = vsrc.vx[c];
-        }
-        if (copy_scalars) {
-            state.rho[c] = rho[c];
-            if (!F::iso(m)) state.e[c] = fin.q[1][c];
+            nvx = vsrc.vx[c];
+            wx = true;
         }
     }
     if (k < m.nzt) {
         if (F::hasY(m) && j >= m.jf && j < m.j1 && kact) {
             const idx_t cm = c - m.sj;
-            state.vy[c] = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
+            nvy = (ppy[cm] + pmy[c]) / (rho[cm] + rho[c]);
+            wy = true;
         } else if (vsrc.vy != state.vy) {
-            state.vy[c] = vsrc.vy[c];
+            nvy = vsrc.vy[c];
+            wy = true;
         }
     }
     if (F::hasZ(m) && j < m.nyt) {
         if (k >= m.kf && k < m.k1 && jact) {
             const idx_t cm = c - m.sk;
-            state.vz[c] = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
+            nvz = (ppz[cm] + pmz[c]) / (rho[cm] + rho[c]) / tb.fz[ring];
+            wz = true;
         } else if (vsrc.vz != state.vz) {
-            state.vz[c] = vsrc.vz[c];
+            nvz = vsrc.vz[c];
+            wz = true;
         }
     }
+    if (copy_scalars && j < m.nyt && k < m.nzt) {
+        state.rho[c] = rho[c];
+        if (!F::iso(m)) state.e[c] = fin.q[1][c];
+    }
+    if (wx) state.vx[c] = nvx;
+    if (wy) state.vy[c] = nvy;
+    if (wz) state.vz[c] = nvz;
 }
+
 
 template <typename T, class F = CfgRun>
 __global__ void __launch_bounds__(256) k_newvel(MeshD m, Tab<T> tb, QSet<T> fin, Fld<T> vsrc, Fld<T> state,
