@@ -74,15 +74,15 @@ ALG_FIELDS_2D_ISO = {
 # profiles/disk3d_fp32_step_ncu.md).  Traffic grows in proportion to the
 # cells, so a full launch is this figure times the cells; once the sources
 # change the figures no longer apply and the bench reports null.
-TRAFFIC_PER_CELL_3D = {"cfl_screen": 21.52, "substep1": 33.07, "artvisc": 36.21, "visc_tau": 36.22, "visc_apply": 54.28, "transport_x": 56.26, "transport_y": 64.36, "transport_z": 65.56, "orbital": 57.45, "newvel": 41.31}
-KERNEL_SRC_HASH = "d1291438e9af3f79"
+TRAFFIC_PER_CELL_3D = {"cfl_screen": 21.53, "substep1": 33.01, "artvisc": 36.07, "visc_tau": 36.22, "visc_apply": 54.3, "transport_x": 56.23, "transport_y": 64.36, "transport_z": 65.51, "orbital": 57.46, "newvel": 41.23}
+KERNEL_SRC_HASH = "815003752373fcff"
 
 # The same for the batched step: DRAM bytes per active cell of every batched
 # phase (all its launches of one step summed), measured on batch-medium (the
 # first 32 disks of the 256-disk sweep, 1.6 GB of state), with the sources
 # whose hash is BATCH_SRC_HASH (profiles/batch256_fp32_step_ncu.md).
-TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 12.95, "substep1": 17.97, "artvisc": 18.02, "visc_tau": 20.63, "visc_apply": 33.43, "transport_x": 24.44, "transport_y": 41.06, "orbital": 32.24, "newvel": 27.17}
-BATCH_SRC_HASH = "59d4c2799d0cb53f"
+TRAFFIC_PER_CELL_BATCH = {"cfl_screen": 12.96, "substep1": 18.67, "artvisc": 19.2, "visc_tau": 21.82, "visc_apply": 33.29, "transport_x": 24.43, "transport_y": 42.82, "orbital": 32.25, "newvel": 27.0}
+BATCH_SRC_HASH = "4b76d5a7c7c5f691"
 
 
 # DRAM bytes per launch of the direct-sum planet force on the 3D disk (ncu,
@@ -458,7 +458,7 @@ def fp64_plain_disk2d(torch, fb, steps=50, warmup=5):
 # cells), valid while the step's sources keep FP64_FLOPS_SRC_HASH
 # (profiles/fp64_disk2d_step_ncu.md).
 FP64_FLOPS_PER_CELL_2D = 1107.8
-FP64_FLOPS_SRC_HASH = "d1291438e9af3f79"
+FP64_FLOPS_SRC_HASH = "815003752373fcff"
 
 
 def fp64_roofline(fp64, alu):
