@@ -534,16 +534,21 @@ def disk2d_fp32(torch, fb, dev, steps=200, warmup=10):
 MHD_EDGE_FIELDS = 13
 
 
-def mhd_box(torch, fb, dev, steps=20, warmup=5, dims=(256, 128, 128)):
+def mhd_box(torch, fb, dev, steps=20, warmup=5, dims=(256, 128, 128), w=None, label=None, fp64=True):
     """A 3D periodic MHD box (Sec. 3.5; 256 x 128 x 128 cells, random
     divergence-free field, eta = 1e-3, artificial viscosity) in FP32 and
     FP64: cell updates per second of the whole step, and the share and
-    roofline of the four MHD kernels from a kernel-by-kernel step (CUDA
-    events).  The state (about 0.5 GB in FP32) is larger than L2."""
-    w = W.random_mhd_box(*dims, seed=1602, eta=1e-3)
+    roofline of the MHD kernels from a kernel-by-kernel step (CUDA
+    events).  The state (about 0.5 GB in FP32) is larger than L2.  w and
+    label give another MHD workload (the shearing sheet with orbital
+    advection of the field); fp64=False measures FP32 only."""
+    if w is None:
+        w = W.random_mhd_box(*dims, seed=1602, eta=1e-3)
+        label = "mhd3d-cart-periodic-%dx%dx%d" % dims
     peak, kind = peaks()
-    out = {"workload": "mhd3d-cart-periodic-%dx%dx%d" % dims, "cells": w.cells, "hbm_peak_kind": kind}
-    for prec, name, esz in ((fb.F32, "f32", 4), (fb.F64, "f64", 8)):
+    out = {"workload": label, "cells": w.cells, "hbm_peak_kind": kind}
+    precs = ((fb.F32, "f32", 4), (fb.F64, "f64", 8)) if fp64 else ((fb.F32, "f32", 4),)
+    for prec, name, esz in precs:
         stream = torch.cuda.Stream()
         c = fb.Fargo(w, prec, stream=stream.cuda_stream)
         c.set_state(w.state)
@@ -998,6 +1003,11 @@ def main():
         extra_lines["sod_fp64"] = sod_latency(torch, fb)
         extra_lines["disk2d_fp32"] = disk2d_fp32(torch, fb, dev)
         extra_lines["mhd3d"] = mhd_box(torch, fb, dev)
+        # the Keplerian MHD shearing sheet with orbital advection of the field
+        # (Sec. 3.6): 512 x 192 x 64 cells, about 0.4 GB of FP32 state
+        sheet = W.mhd_shearing_sheet(512, 192, 64, amp=0.002, seed=1602, vamp=0.02, lx=2.0, ly=0.75, lz=0.25)
+        extra_lines["mhd_sheet_fargo"] = mhd_box(torch, fb, dev, w=sheet, fp64=False,
+                                                 label="mhd3d-cart-shearing-sheet-fargo-512x192x64")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1 and args.workload not in ("disk3d-small", "batch-small", "batch-medium"):

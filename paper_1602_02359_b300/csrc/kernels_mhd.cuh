@@ -348,23 +348,40 @@ __global__ void __launch_bounds__(256) k_mhd_dvx(MeshD m, const T *vx, const dou
     dvx[c] = (T)((double)vx[c] - v0all[k * m.nyt + j]);
 }
 
+// The arc of one ring row: X = v0f dt / dX = N + xi (N the nearest integer,
+// FP64), N modulo the ring, and whether the row takes part.  An arc beyond 16
+// turns of the ring, or not finite, records FARGO_ERR_NONFINITE and the row
+// takes no part.
+struct OrbArc {
+    long long N;
+    int Nm, on;
+    double xs;
+};
+__device__ __forceinline__ OrbArc mh_orbital_arc(const MeshD &m, double v0f, double dt, Scal *sc)
+{
+    OrbArc a{0, 0, 0, 0.0};
+    const double X = __ddiv_rn(__dmul_rn(v0f, dt), m.dx);
+    if (!(fabs(X) <= 16.0 * m.nx)) {
+        atomicOr(&sc->err, 1);
+        return a;
+    }
+    a.N = llround(X);
+    a.xs = __dsub_rn(X, (double)a.N);
+    a.Nm = (int)(((a.N % m.nx) + m.nx) % m.nx);
+    a.on = 1;
+    return a;
+}
+
 // Upstream average of the orbital EMF at the edge at the lower X face of
 // cell i, for the ring row of B (B_y at a Y face, or B_z at a Z face) and
-// the arc v0f dt (Eq. 54): (1/dt) times the integral of B over the arc,
-// i.e. (dX/dt) (sum of the N whole cells upstream + xi times the PPA face
-// value N cells upstream), X = v0f dt / dX = N + xi.  An arc beyond 16 turns
-// of the ring, or not finite, records FARGO_ERR_NONFINITE and gives 0.
+// the row's arc (Eq. 54): (1/dt) times the integral of B over the arc, i.e.
+// (dX/dt) (sum of the N whole cells upstream + xi times the PPA face value N
+// cells upstream).
 template <typename T>
-__device__ __forceinline__ T mh_orbital_emf(const MeshD &m, const T *row, int i, double v0f, double dt, Scal *sc)
+__device__ __forceinline__ T mh_orbital_emf(const MeshD &m, const T *row, int i, const OrbArc &a, double dt)
 {
     const int nx = m.nx;
-    const double X = __ddiv_rn(__dmul_rn(v0f, dt), m.dx);
-    if (!(fabs(X) <= 16.0 * nx)) {
-        atomicOr(&sc->err, 1);
-        return T(0);
-    }
-    const long long N = llround(X);
-    const double xs = __dsub_rn(X, (double)N);
+    const long long N = a.N;
     T w = T(0);
     if (N > 0) {
         int q = i;
@@ -380,20 +397,22 @@ __device__ __forceinline__ T mh_orbital_emf(const MeshD &m, const T *row, int i,
         }
     }
     T st = T(0);
-    if (xs != 0.0) {
-        int f = (int)(((long long)i - N) % nx);
+    if (a.xs != 0.0) {
+        int f = i - a.Nm;
         if (f < 0) f += nx;
-        const bool pos = xs >= 0.0;
-        const int d = pos ? f - 1 : f;   // the donor cell of face f
-        T a[5];
+        const bool pos = a.xs >= 0.0;
+        const int d = pos ? f - 1 : f;   // the donor cell of face f, -1 .. nx-1
+        T q5[5];
 #pragma unroll
         for (int s = 0; s < 5; s++) {
-            int q = (d - 2 + s) % nx;
-            a[s] = row[q < 0 ? q + nx : q];
+            int q = d - 2 + s;           // -3 .. nx+1
+            while (q < 0) q += nx;       // (at most three turns, for rings of one cell)
+            while (q >= nx) q -= nx;
+            q5[s] = row[q];
         }
-        st = ppa_face(a, (T)(pos ? xs : -xs), pos);
+        st = ppa_face(q5, (T)(pos ? a.xs : -a.xs), pos);
     }
-    return (T)(m.dx / dt) * (w + (T)xs * st);
+    return (T)(m.dx / dt) * (w + (T)a.xs * st);
 }
 
 // Cell 11: e_z = v0 B_y and e_y = -v0 B_z averaged upstream on every edge
@@ -401,37 +420,42 @@ __device__ __forceinline__ T mh_orbital_emf(const MeshD &m, const T *row, int i,
 // B_y (B_z), or the ring's own along an absent direction; zero on the edges
 // in a wall's plane (non-periodic Y or Z) and off the active range.  The
 // constrained transport k_mhd_ct then applies them.  Grid: every row and
-// plane of the arrays (the face kernels' grid).
+// plane of the arrays (the face kernels' grid); a block's threads share one
+// row (j, k), whose two arcs thread 0 forms once in FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_mhd_fargo_emf(MeshD m, Tab<T> tb, const double *v0all, T *ex, T *ey,
                                                        T *ez, Scal *sc)
 {
+    __shared__ OrbArc arc[2];   // e_z's row, e_y's row
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= m.nx || j > m.nyt || k > m.nzt) return;
-    const idx_t c = IX(m, i, j, k);
     const double dt = sc->dt;
-    T vz = T(0), vy = T(0);
-    if (dt > 0.0) {
-        // e_z: Y-face rows j0..j1 (walls excluded), active planes
-        const bool jz = m.hasY ? (j >= m.j0 && j <= m.j1 && (m.pery || (j != m.j0 && j != m.j1))) : j == 0;
-        const bool kz = m.hasZ ? (k >= m.k0 && k < m.k1) : k == 0;
-        if (jz && kz) {
-            const int r = k * m.nyt + j;
-            const double v0f = m.hasY ? 0.5 * (v0all[r - 1] + v0all[r]) : v0all[r];
-            vz = mh_orbital_emf(m, tb.bfield[1] + IX(m, 0, j, k), i, v0f, dt, sc);
-        }
-        // e_y: active rows, Z-face planes k0..k1 (walls excluded)
-        const bool jy = m.hasY ? (j >= m.j0 && j < m.j1) : j == 0;
-        const bool ky = m.hasZ ? (k >= m.k0 && k <= m.k1 && (m.perz || (k != m.k0 && k != m.k1))) : k == 0;
-        if (jy && ky) {
-            const int r = k * m.nyt + j;
-            const double v0f = m.hasZ ? 0.5 * (v0all[r - m.nyt] + v0all[r]) : v0all[r];
-            vy = -mh_orbital_emf(m, tb.bfield[2] + IX(m, 0, j, k), i, v0f, dt, sc);
+    if (threadIdx.x == 0) {
+        arc[0] = OrbArc{0, 0, 0, 0.0};
+        arc[1] = OrbArc{0, 0, 0, 0.0};
+        if (dt > 0.0 && j <= m.nyt && k <= m.nzt) {
+            // e_z: Y-face rows j0..j1 (walls excluded), active planes
+            const bool jz = m.hasY ? (j >= m.j0 && j <= m.j1 && (m.pery || (j != m.j0 && j != m.j1))) : j == 0;
+            const bool kz = m.hasZ ? (k >= m.k0 && k < m.k1) : k == 0;
+            if (jz && kz) {
+                const int r = k * m.nyt + j;
+                arc[0] = mh_orbital_arc(m, m.hasY ? 0.5 * (v0all[r - 1] + v0all[r]) : v0all[r], dt, sc);
+            }
+            // e_y: active rows, Z-face planes k0..k1 (walls excluded)
+            const bool jy = m.hasY ? (j >= m.j0 && j < m.j1) : j == 0;
+            const bool ky = m.hasZ ? (k >= m.k0 && k <= m.k1 && (m.perz || (k != m.k0 && k != m.k1))) : k == 0;
+            if (jy && ky) {
+                const int r = k * m.nyt + j;
+                arc[1] = mh_orbital_arc(m, m.hasZ ? 0.5 * (v0all[r - m.nyt] + v0all[r]) : v0all[r], dt, sc);
+            }
         }
     }
+    __syncthreads();
+    if (i >= m.nx || j > m.nyt || k > m.nzt) return;
+    const idx_t c = IX(m, i, j, k);
+    const OrbArc az = arc[0], ay = arc[1];
     ex[c] = T(0);
-    ey[c] = vy;
-    ez[c] = vz;
+    ey[c] = ay.on ? -mh_orbital_emf(m, tb.bfield[2] + IX(m, 0, j, k), i, ay, dt) : T(0);
+    ez[c] = az.on ? mh_orbital_emf(m, tb.bfield[1] + IX(m, 0, j, k), i, az, dt) : T(0);
 }
 
 // Periodic images of the field (periodic Y / Z axes): B_y face-centred
