@@ -399,6 +399,31 @@ def test_fp32_longest_ring_within_stated_tolerance():
     assert e_mom < 1e-4
 
 
+@pytest.mark.parametrize("nx", [700, 1101, 1700])
+def test_fp32_orbital_chunk_classes_within_stated_tolerance(nx):
+    """Rings whose orbital step takes each FP32 form: 700 cells (four per
+    lane, packed cell pairs), 1101 (six per lane, packed pairs, a ragged last
+    warp), 1700 (beyond the packed forms' thread caps: the per-thread form
+    with eight cells per thread); ten steps of a perturbed disk against the
+    FP64 oracle at the FP32 tolerances."""
+    w = W.perturb(W.disk2d(nx=nx, ny=6), seed=43, amp=1e-2)
+    o = oracle.Oracle(w)
+    st = w.copy().state
+    import paper_1602_02359_b300 as fb
+    c = make_ctx(w, fb.F32, t=0.0, t_end=w.t_end)
+    t = 0.0
+    for n in range(10):
+        t += o.step(st, t, w.t_end)
+        c.step(want_dt=False)
+    g = c.get_state()
+    e_rho = rel_l1(w.active(g["rho"]), w.active(st["rho"]))
+    e_mom = rel_l1(momentum_density(w, g), momentum_density(w, st))
+    record(f"fp32_orbital_ring_{nx}x6_10steps", rel_l1_rho=e_rho, rel_l1_momentum=e_mom)
+    assert e_rho < 2e-5
+    assert e_mom < 1e-4
+    c.close()
+
+
 def test_fp32_courant_step_bit_exact_on_promoted_state():
     """dt and v0 are FP64 islands: from the FP32 fields promoted to FP64 they
     equal the oracle's bit for bit."""
