@@ -674,8 +674,22 @@ def bench_single(args, torch, fb, wname, dev, barrier, e2e_on=True, steps=None):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             c.step(want_dt=False)
+        # launch shapes picked by the context's autotuner (per-cell block
+        # width, Y/Z sweep segments: timed on snapshots of the state, which it
+        # leaves unchanged); the timed steps run with its choice, and the
+        # step time with the hand-set shapes is reported beside it
+        ms_default, _ = timed_steps(torch, stream, lambda: c.step(want_dt=False), 5, dev, lambda: None)
+        t0 = time.perf_counter()
+        pick = c.autotune(reps=3)
+        tune = {"cell_block": pick[0], "seg_y": pick[1], "seg_z": pick[2], "ms_default": round(ms_default, 4),
+                "s": round(time.perf_counter() - t0, 1),
+                "how": "fargo_autotune: each candidate shape timed on snapshot-restored trial steps (CUDA events)"}
+        for _ in range(2):
+            c.step(want_dt=False)
         torch.cuda.synchronize()
         ms, clocks = timed_steps(torch, stream, lambda: c.step(want_dt=False), steps, dev, barrier)
+        tune["ms_tuned"] = round(ms, 4)
+        tune["gain"] = round(ms_default / ms - 1.0, 4) if ms > 0 else None
         per = {}
         for _ in range(steps):
             add_step_times(per, c.profile_step())
@@ -718,7 +732,7 @@ def bench_single(args, torch, fb, wname, dev, barrier, e2e_on=True, steps=None):
     c.close()
     return {"workload": label, "cells": w.cells, "fp32": fp32, "ms": ms, "clocks": clocks, "roofline": roof,
             "e2e": e2e, "launches": nl, "steps_advanced": int(nsteps),
-            "state_gb": w.cells * 21 * esz / 1e9, "planet_force": pforce}
+            "state_gb": w.cells * 21 * esz / 1e9, "planet_force": pforce, "autotune": tune}
 
 
 def planet_force_timing(torch, c, stream, w, esz, dev, reps=20):
@@ -986,7 +1000,7 @@ def main():
                                                                  "step_alg_GBps", "step_frac", "method_GBps",
                                                                  "method_frac", "traffic")},
                   "per_kernel": s["roofline"]["per_kernel"], "clocks": s["clocks"],
-                  "planet_force": s["planet_force"]}
+                  "planet_force": s["planet_force"], "autotune": s["autotune"]}
 
     surrogate = None
     if rank == 0 and batched and not args.no_surrogate:
@@ -1026,6 +1040,7 @@ def main():
                         "run_length": "500 orbits per disk in the sweep; the bench times per-step throughput"})
         else:
             cfg["steps_advanced"] = r["steps_advanced"]
+            cfg["autotune"] = r["autotune"]
         line = {
             "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
